@@ -1,0 +1,979 @@
+/*
+ * gwn_oracle.c -- FP64 CPU reference for generalized winding numbers.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may call this file;
+ * it is used by the tests, by the smoke check and by the CPU baseline leg of
+ * the bench.  It shares no code with the CUDA library.
+ *
+ * Every floating-point input is a float32 value promoted exactly to double.
+ * Exact predicate signs are computed with integer arithmetic on the float32
+ * bit patterns (a fixed-width big integer), after a plain float64 filter.
+ *
+ * Contents (paper sections cited per function):
+ *   - 3D definition: sum of per-triangle solid angles (Background, 3D GWN).
+ *   - signed crossing count of one ray (Eq. chi) by brute force over all
+ *     triangles with exact orientation predicates and a symbolic perturbation
+ *     of the ray direction.
+ *   - boundary edge multiplicities and the boundary term relative to one ray
+ *     direction (one-shot algorithm, Lemma 1/Lemma 2 and the closure used in
+ *     the proof of Appendix A).
+ *   - gradient of the 3D definition (analytic derivative of the per-triangle
+ *     solid angle, chain rule).
+ *   - 2D definition: per-segment adaptive Gauss-Kronrod quadrature of the
+ *     subtended angle (Background, 2D GWN).
+ *   - 2D one-shot by Algorithm 1 (project the boundary points on the circle,
+ *     two regions, one ray in the largest region, pairwise difference, sum).
+ *   - 2D closed form relative to the +x ray (chord closure).
+ */
+#include <math.h>
+#include <pthread.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORACLE_API __attribute__((visibility("default")))
+
+/* ======================================================================== */
+/* Exact sign of a sum of products of float32 values                        */
+/* ======================================================================== */
+/* A float32 x equals mant * 2^ex with |mant| < 2^24.  A product of up to
+ * three such numbers is an integer of at most 72 bits times a power of two;
+ * a sum of such products is accumulated exactly in a two's-complement big
+ * integer of BIG_LIMBS 64-bit words.  The exponent span of float32 triple
+ * products is below 800 bits, so 16 limbs (1024 bits) always suffice. */
+#define BIG_LIMBS 18
+
+typedef struct { uint64_t w[BIG_LIMBS]; } big_t;
+
+static void split_f32(float x, int64_t *mant, int *ex) {
+    if (x == 0.0f) { *mant = 0; *ex = 0; return; }
+    int k;
+    double f = frexp((double)x, &k);           /* x = f * 2^k, 0.5 <= |f| < 1 */
+    *mant = (int64_t)ldexp(f, 24);              /* exact: float has 24 bits */
+    *ex = k - 24;
+}
+
+typedef struct { __int128 mant; int ex; } term_t;
+
+/* add (mag << shift) with sign to the accumulator */
+static void big_add_shifted(big_t *acc, unsigned __int128 mag, int neg, int shift) {
+    uint64_t limbs[BIG_LIMBS];
+    memset(limbs, 0, sizeof limbs);
+    int q = shift / 64, r = shift % 64;
+    uint64_t lo = (uint64_t)mag, hi = (uint64_t)(mag >> 64);
+    /* place the 128-bit magnitude at bit offset shift (spans up to 3 limbs) */
+    uint64_t parts[3];
+    if (r == 0) { parts[0] = lo; parts[1] = hi; parts[2] = 0; }
+    else {
+        parts[0] = lo << r;
+        parts[1] = (hi << r) | (lo >> (64 - r));
+        parts[2] = hi >> (64 - r);
+    }
+    for (int i = 0; i < 3; i++)
+        if (q + i < BIG_LIMBS) limbs[q + i] = parts[i];
+    if (neg) {           /* two's complement negate of the full width */
+        unsigned __int128 carry = 1;
+        for (int i = 0; i < BIG_LIMBS; i++) {
+            unsigned __int128 v = (unsigned __int128)(~limbs[i]) + carry;
+            limbs[i] = (uint64_t)v;
+            carry = v >> 64;
+        }
+    }
+    unsigned __int128 carry = 0;
+    for (int i = 0; i < BIG_LIMBS; i++) {
+        unsigned __int128 v = (unsigned __int128)acc->w[i] + limbs[i] + carry;
+        acc->w[i] = (uint64_t)v;
+        carry = v >> 64;
+    }
+}
+
+static int big_sign(const big_t *acc) {
+    if ((int64_t)acc->w[BIG_LIMBS - 1] < 0) return -1;
+    for (int i = 0; i < BIG_LIMBS; i++) if (acc->w[i]) return 1;
+    return 0;
+}
+
+/* exact sign of sum_i terms[i] */
+static int exact_sign_terms(const term_t *t, int n) {
+    int emin = 1 << 30;
+    for (int i = 0; i < n; i++) if (t[i].mant != 0 && t[i].ex < emin) emin = t[i].ex;
+    if (emin == (1 << 30)) return 0;
+    big_t acc;
+    memset(&acc, 0, sizeof acc);
+    for (int i = 0; i < n; i++) {
+        if (t[i].mant == 0) continue;
+        int neg = t[i].mant < 0;
+        unsigned __int128 mag = neg ? (unsigned __int128)(-t[i].mant) : (unsigned __int128)t[i].mant;
+        big_add_shifted(&acc, mag, neg, t[i].ex - emin);
+    }
+    return big_sign(&acc);
+}
+
+/* A factor is the exact difference x - y of two float32 values (y may be 0). */
+typedef struct { float x, y; } fac_t;
+
+/* append the expansion of sgn * f0 * f1 [* f2] (each factor a difference) */
+static int expand_product(term_t *out, int sgn, const fac_t *f, int nf) {
+    int n = 0;
+    int combos = 1 << nf;
+    for (int c = 0; c < combos; c++) {
+        int s = sgn;
+        __int128 m = 1;
+        int e = 0;
+        int zero = 0;
+        for (int k = 0; k < nf; k++) {
+            float v = (c >> k & 1) ? f[k].y : f[k].x;
+            if ((c >> k) & 1) s = -s;
+            int64_t mm; int ee;
+            split_f32(v, &mm, &ee);
+            if (mm == 0) { zero = 1; break; }
+            m *= mm; e += ee;
+        }
+        if (zero) continue;
+        out[n].mant = s < 0 ? -m : m;
+        out[n].ex = e;
+        n++;
+    }
+    return n;
+}
+
+static const int PERM3[6][3] = {{0,1,2},{1,2,0},{2,0,1},{0,2,1},{2,1,0},{1,0,2}};
+static const int PSGN3[6] = {1, 1, 1, -1, -1, -1};
+
+/* exact sign of det[A-P, B-P, D] */
+static int exact_det_abd(const float *A, const float *B, const float *P, const float *D) {
+    term_t t[6 * 8];
+    int n = 0;
+    for (int k = 0; k < 6; k++) {
+        const int *s = PERM3[k];
+        fac_t f[3] = {{A[s[0]], P[s[0]]}, {B[s[1]], P[s[1]]}, {D[s[2]], 0.0f}};
+        n += expand_product(t + n, PSGN3[k], f, 3);
+    }
+    return exact_sign_terms(t, n);
+}
+
+/* exact sign of ((A-P) x (B-P))_k */
+static int exact_cross_comp(const float *A, const float *B, const float *P, int k) {
+    int i = (k + 1) % 3, j = (k + 2) % 3;
+    term_t t[8];
+    int n = 0;
+    fac_t f1[2] = {{A[i], P[i]}, {B[j], P[j]}};
+    fac_t f2[2] = {{A[j], P[j]}, {B[i], P[i]}};
+    n += expand_product(t + n, 1, f1, 2);
+    n += expand_product(t + n, -1, f2, 2);
+    return exact_sign_terms(t, n);
+}
+
+/* exact sign of det[V0-P, V1-P, V2-P] */
+static int exact_orient(const float *V0, const float *V1, const float *V2, const float *P) {
+    term_t t[6 * 8];
+    int n = 0;
+    for (int k = 0; k < 6; k++) {
+        const int *s = PERM3[k];
+        fac_t f[3] = {{V0[s[0]], P[s[0]]}, {V1[s[1]], P[s[1]]}, {V2[s[2]], P[s[2]]}};
+        n += expand_product(t + n, PSGN3[k], f, 3);
+    }
+    return exact_sign_terms(t, n);
+}
+
+/* ---- float64 filters: accept the float64 sign only when |value| exceeds a
+ * generous bound (16 ulp of the permanent); otherwise use the exact sign. */
+static const double FILTER_U = 16.0 * 1.1102230246251565e-16;
+
+static int sign_det_abd(const float *A, const float *B, const float *P, const float *D) {
+    double a[3], b[3], d[3];
+    for (int i = 0; i < 3; i++) {
+        a[i] = (double)A[i] - (double)P[i];
+        b[i] = (double)B[i] - (double)P[i];
+        d[i] = (double)D[i];
+    }
+    double c0 = a[1] * b[2] - a[2] * b[1];
+    double c1 = a[2] * b[0] - a[0] * b[2];
+    double c2 = a[0] * b[1] - a[1] * b[0];
+    double det = d[0] * c0 + d[1] * c1 + d[2] * c2;
+    double perm = fabs(d[0]) * (fabs(a[1] * b[2]) + fabs(a[2] * b[1]))
+                + fabs(d[1]) * (fabs(a[2] * b[0]) + fabs(a[0] * b[2]))
+                + fabs(d[2]) * (fabs(a[0] * b[1]) + fabs(a[1] * b[0]));
+    if (fabs(det) > FILTER_U * perm && perm > 1e-280) return det > 0 ? 1 : -1;
+    return exact_det_abd(A, B, P, D);
+}
+
+static int sign_orient(const float *V0, const float *V1, const float *V2, const float *P) {
+    double a[3], b[3], c[3];
+    for (int i = 0; i < 3; i++) {
+        a[i] = (double)V0[i] - (double)P[i];
+        b[i] = (double)V1[i] - (double)P[i];
+        c[i] = (double)V2[i] - (double)P[i];
+    }
+    double det = a[0] * (b[1] * c[2] - b[2] * c[1]) + a[1] * (b[2] * c[0] - b[0] * c[2])
+               + a[2] * (b[0] * c[1] - b[1] * c[0]);
+    double perm = fabs(a[0]) * (fabs(b[1] * c[2]) + fabs(b[2] * c[1]))
+                + fabs(a[1]) * (fabs(b[2] * c[0]) + fabs(b[0] * c[2]))
+                + fabs(a[2]) * (fabs(b[0] * c[1]) + fabs(b[1] * c[0]));
+    if (fabs(det) > FILTER_U * perm && perm > 1e-280) return det > 0 ? 1 : -1;
+    return exact_orient(V0, V1, V2, P);
+}
+
+/* Sign of det[A-P, B-P, d_eps] with d_eps = d + eps e_x + eps^2 e_y + eps^3 e_z
+ * (symbolic perturbation of the ray direction): the first nonzero of
+ * det[a,b,d], (a x b)_x, (a x b)_y, (a x b)_z.  Zero only when P lies on the
+ * line through A and B. */
+static int sos_edge(const float *A, const float *B, const float *P, const float *D) {
+    int s = sign_det_abd(A, B, P, D);
+    if (s) return s;
+    for (int k = 0; k < 3; k++) {
+        s = exact_cross_comp(A, B, P, k);
+        if (s) return s;
+    }
+    return 0;
+}
+
+ORACLE_API int oracle_sign_edge(const float *A, const float *B, const float *P, const float *D) {
+    return sos_edge(A, B, P, D);
+}
+ORACLE_API int oracle_exact_det_abd(const float *A, const float *B, const float *P, const float *D) {
+    return exact_det_abd(A, B, P, D);
+}
+ORACLE_API int oracle_sign_orient(const float *V0, const float *V1, const float *V2, const float *P) {
+    return sign_orient(V0, V1, V2, P);
+}
+ORACLE_API int oracle_exact_orient(const float *V0, const float *V1, const float *V2, const float *P) {
+    return exact_orient(V0, V1, V2, P);
+}
+
+/* ======================================================================== */
+/* thread pool helper: static partition of [0, n) over nthreads             */
+/* ======================================================================== */
+typedef void (*range_fn)(void *ctx, int64_t lo, int64_t hi);
+typedef struct { range_fn fn; void *ctx; int64_t lo, hi; } job_t;
+
+static void *job_main(void *p) {
+    job_t *j = (job_t *)p;
+    j->fn(j->ctx, j->lo, j->hi);
+    return NULL;
+}
+
+static void parallel_for(int64_t n, int nthreads, range_fn fn, void *ctx) {
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > 256) nthreads = 256;
+    if (n < nthreads) nthreads = (int)(n > 0 ? n : 1);
+    if (nthreads == 1) { fn(ctx, 0, n); return; }
+    pthread_t th[256];
+    job_t jobs[256];
+    int created[256];
+    int64_t chunk = (n + nthreads - 1) / nthreads;
+    for (int t = 0; t < nthreads; t++) {
+        jobs[t].fn = fn;
+        jobs[t].ctx = ctx;
+        jobs[t].lo = t * chunk < n ? t * chunk : n;
+        jobs[t].hi = (t + 1) * chunk < n ? (t + 1) * chunk : n;
+        created[t] = 0;
+        if (jobs[t].lo >= jobs[t].hi) continue;
+        if (pthread_create(&th[t], NULL, job_main, &jobs[t]) == 0) created[t] = 1;
+        else job_main(&jobs[t]);               /* no thread: run inline */
+    }
+    for (int t = 0; t < nthreads; t++)
+        if (created[t]) pthread_join(th[t], NULL);
+}
+
+/* ======================================================================== */
+/* 3D definition: w(p) = (1/4pi) sum_T Omega_T(p)                           */
+/* ======================================================================== */
+/* Solid angle of triangle (a, b, c) seen from the origin, by the
+ * Van Oosterom-Strackee half-angle formula. */
+static double solid_angle(const double *a, const double *b, const double *c) {
+    double la = sqrt(a[0]*a[0] + a[1]*a[1] + a[2]*a[2]);
+    double lb = sqrt(b[0]*b[0] + b[1]*b[1] + b[2]*b[2]);
+    double lc = sqrt(c[0]*c[0] + c[1]*c[1] + c[2]*c[2]);
+    double num = a[0] * (b[1]*c[2] - b[2]*c[1]) + a[1] * (b[2]*c[0] - b[0]*c[2])
+               + a[2] * (b[0]*c[1] - b[1]*c[0]);
+    double ab = a[0]*b[0] + a[1]*b[1] + a[2]*b[2];
+    double ac = a[0]*c[0] + a[1]*c[1] + a[2]*c[2];
+    double bc = b[0]*c[0] + b[1]*c[1] + b[2]*c[2];
+    double den = la * lb * lc + ab * lc + ac * lb + bc * la;
+    return 2.0 * atan2(num, den);
+}
+
+ORACLE_API double oracle_solid_angle(const double *a, const double *b, const double *c) {
+    return solid_angle(a, b, c);
+}
+
+typedef struct {
+    const float *V; const int32_t *F; int64_t nf;
+    const float *P; double *w;
+} vos_ctx;
+
+static void vos_range(void *p, int64_t lo, int64_t hi) {
+    vos_ctx *c = (vos_ctx *)p;
+    for (int64_t q = lo; q < hi; q++) {
+        const float *pp = c->P + 3 * q;
+        double acc = 0.0;
+        for (int64_t t = 0; t < c->nf; t++) {
+            double v[3][3];
+            for (int k = 0; k < 3; k++) {
+                const float *x = c->V + 3 * (int64_t)c->F[3 * t + k];
+                for (int i = 0; i < 3; i++) v[k][i] = (double)x[i] - (double)pp[i];
+            }
+            acc += solid_angle(v[0], v[1], v[2]);
+        }
+        c->w[q] = acc / (4.0 * M_PI);
+    }
+}
+
+ORACLE_API void oracle_w3d_vos(const float *V, const int32_t *F, int64_t nf, const float *P,
+                               int64_t nq, double *w, int nthreads) {
+    vos_ctx c = {V, F, nf, P, w};
+    parallel_for(nq, nthreads, vos_range, &c);
+}
+
+/* ======================================================================== */
+/* Signed crossing count chi_d(p) (Eq. chi), brute force over triangles     */
+/* ======================================================================== */
+/* Triangle T = (v0, v1, v2) with normal n = (v1-v0) x (v2-v0).  The ray
+ * p + t d_eps (t > 0) crosses T iff the three edge orientations
+ * det[vi-p, vj-p, d_eps] share one sign s, and det[v0-p, v1-p, v2-p] has the
+ * same sign s (t > 0).  The three edge determinants sum to d_eps . n, so the
+ * contribution sign(d_eps . n) equals s.  det[v0-p, v1-p, v2-p] = 0 means p
+ * lies in the plane of T: such a triangle is not counted. */
+static int tri_crossing(const float *v0, const float *v1, const float *v2, const float *p,
+                        const float *d) {
+    int s0 = sos_edge(v0, v1, p, d);
+    if (s0 == 0) return 0;
+    int s1 = sos_edge(v1, v2, p, d);
+    if (s1 != s0) return 0;
+    int s2 = sos_edge(v2, v0, p, d);
+    if (s2 != s0) return 0;
+    int o = sign_orient(v0, v1, v2, p);
+    return o == s0 ? s0 : 0;
+}
+
+ORACLE_API int oracle_tri_crossing(const float *v0, const float *v1, const float *v2,
+                                   const float *p, const float *d) {
+    return tri_crossing(v0, v1, v2, p, d);
+}
+
+typedef struct {
+    const float *V; const int32_t *F; int64_t nf;
+    const float *P; const float *d; int32_t *chi;
+} chi_ctx;
+
+static void chi_range(void *p, int64_t lo, int64_t hi) {
+    chi_ctx *c = (chi_ctx *)p;
+    for (int64_t q = lo; q < hi; q++) {
+        const float *pp = c->P + 3 * q;
+        int acc = 0;
+        for (int64_t t = 0; t < c->nf; t++) {
+            const float *v0 = c->V + 3 * (int64_t)c->F[3 * t];
+            const float *v1 = c->V + 3 * (int64_t)c->F[3 * t + 1];
+            const float *v2 = c->V + 3 * (int64_t)c->F[3 * t + 2];
+            /* cheap exact rejection: the triangle lies entirely on one side of
+             * the ray's supporting planes is not used; every triangle is tested
+             * with the exact predicates (plain brute force). */
+            acc += tri_crossing(v0, v1, v2, pp, c->d);
+        }
+        c->chi[q] = acc;
+    }
+}
+
+ORACLE_API void oracle_chi3d(const float *V, const int32_t *F, int64_t nf, const float *P,
+                             int64_t nq, const float *d, int32_t *chi, int nthreads) {
+    chi_ctx c = {V, F, nf, P, d, chi};
+    parallel_for(nq, nthreads, chi_range, &c);
+}
+
+/* ======================================================================== */
+/* Boundary edges with multiplicity                                         */
+/* ======================================================================== */
+/* Each triangle (i, j, k) contributes directed edges i->j, j->k, k->i.  The
+ * net multiplicity of the undirected pair {u < v} is (#u->v) - (#v->u); a
+ * pair with nonzero net multiplicity is a boundary edge, reported as
+ * u->v with m > 0 or v->u with m > 0. */
+typedef struct { int32_t u, v; int32_t s; } dedge_t;
+
+static int cmp_dedge(const void *x, const void *y) {
+    const dedge_t *a = (const dedge_t *)x, *b = (const dedge_t *)y;
+    if (a->u != b->u) return a->u < b->u ? -1 : 1;
+    if (a->v != b->v) return a->v < b->v ? -1 : 1;
+    return 0;
+}
+
+ORACLE_API int64_t oracle_boundary_edges(const int32_t *F, int64_t nf, int32_t *src,
+                                         int32_t *dst, int32_t *mult) {
+    dedge_t *e = (dedge_t *)malloc(sizeof(dedge_t) * 3 * (size_t)(nf > 0 ? nf : 1));
+    if (!e) return -1;
+    for (int64_t t = 0; t < nf; t++) {
+        for (int k = 0; k < 3; k++) {
+            int32_t a = F[3 * t + k], b = F[3 * t + (k + 1) % 3];
+            dedge_t *x = &e[3 * t + k];
+            if (a < b) { x->u = a; x->v = b; x->s = 1; }
+            else { x->u = b; x->v = a; x->s = -1; }
+        }
+    }
+    qsort(e, 3 * (size_t)nf, sizeof(dedge_t), cmp_dedge);
+    int64_t n = 0;
+    for (int64_t i = 0; i < 3 * nf;) {
+        int64_t j = i;
+        int32_t m = 0;
+        while (j < 3 * nf && e[j].u == e[i].u && e[j].v == e[i].v) { m += e[j].s; j++; }
+        if (m > 0) { src[n] = e[i].u; dst[n] = e[i].v; mult[n] = m; n++; }
+        else if (m < 0) { src[n] = e[i].v; dst[n] = e[i].u; mult[n] = -m; n++; }
+        i = j;
+    }
+    free(e);
+    return n;
+}
+
+/* ======================================================================== */
+/* Boundary term relative to direction d                                    */
+/* ======================================================================== */
+/* Closing M with the curtain {x - s d : x in dM, s >= 0} gives a closed
+ * surface whose winding number at p is the signed crossing count of the ray
+ * p + t d with M (the curtain is never met by that ray).  Hence
+ *     w(p) = chi_d(p) - w_curtain(p),
+ * and the curtain's solid angle is the sum over directed boundary edges A->B
+ * of the solid angle of the spherical triangle (A-p, B-p, -d) with a minus
+ * sign, giving
+ *     B_d(p) = (1/4pi) sum_e m_e Omega(A_e - p, B_e - p, -d).
+ * Omega jumps by 4pi where the ray p + t d crosses the edge; there the sign of
+ * the numerator (= -det[A-p, B-p, d]/|d|) is taken from the exact, perturbed
+ * predicate whenever the float64 value is within its error bound, so the jump
+ * sits exactly where chi_d changes. */
+typedef struct {
+    const float *V; const int32_t *src, *dst, *mult; int64_t ne;
+    const float *P; const float *d; double *B;
+} bterm_ctx;
+
+static void bterm_range(void *p, int64_t lo, int64_t hi) {
+    bterm_ctx *c = (bterm_ctx *)p;
+    double dn = sqrt((double)c->d[0] * c->d[0] + (double)c->d[1] * c->d[1]
+                     + (double)c->d[2] * c->d[2]);
+    double cdir[3] = {-(double)c->d[0] / dn, -(double)c->d[1] / dn, -(double)c->d[2] / dn};
+    for (int64_t q = lo; q < hi; q++) {
+        const float *pp = c->P + 3 * q;
+        double acc = 0.0;
+        for (int64_t e = 0; e < c->ne; e++) {
+            const float *A = c->V + 3 * (int64_t)c->src[e];
+            const float *Bv = c->V + 3 * (int64_t)c->dst[e];
+            double a[3], b[3];
+            for (int i = 0; i < 3; i++) {
+                a[i] = (double)A[i] - (double)pp[i];
+                b[i] = (double)Bv[i] - (double)pp[i];
+            }
+            double la = sqrt(a[0]*a[0] + a[1]*a[1] + a[2]*a[2]);
+            double lb = sqrt(b[0]*b[0] + b[1]*b[1] + b[2]*b[2]);
+            double x0 = a[1]*b[2] - a[2]*b[1], x1 = a[2]*b[0] - a[0]*b[2], x2 = a[0]*b[1] - a[1]*b[0];
+            double num = cdir[0]*x0 + cdir[1]*x1 + cdir[2]*x2;
+            double perm = fabs(cdir[0]) * (fabs(a[1]*b[2]) + fabs(a[2]*b[1]))
+                        + fabs(cdir[1]) * (fabs(a[2]*b[0]) + fabs(a[0]*b[2]))
+                        + fabs(cdir[2]) * (fabs(a[0]*b[1]) + fabs(a[1]*b[0]));
+            double ab = a[0]*b[0] + a[1]*b[1] + a[2]*b[2];
+            double ac = a[0]*cdir[0] + a[1]*cdir[1] + a[2]*cdir[2];
+            double bc = b[0]*cdir[0] + b[1]*cdir[1] + b[2]*cdir[2];
+            double den = la * lb + ab + ac * lb + bc * la;
+            if (den < 0.0 && fabs(num) <= 4.0 * FILTER_U * perm + 1e-300) {
+                int s = sos_edge(A, Bv, pp, c->d);      /* sign(num) = -s */
+                if (s > 0) num = -fabs(num);
+                else if (s < 0) num = fabs(num);
+            }
+            acc += (double)c->mult[e] * 2.0 * atan2(num, den);
+        }
+        c->B[q] = acc / (4.0 * M_PI);
+    }
+}
+
+ORACLE_API void oracle_bterm3d(const float *V, const int32_t *src, const int32_t *dst,
+                               const int32_t *mult, int64_t ne, const float *P, int64_t nq,
+                               const float *d, double *B, int nthreads) {
+    bterm_ctx c = {V, src, dst, mult, ne, P, d, B};
+    parallel_for(nq, nthreads, bterm_range, &c);
+}
+
+/* ======================================================================== */
+/* Gradient of the 3D definition                                            */
+/* ======================================================================== */
+/* Omega = 2 atan2(N, D) with N = a.(b x c), D = |a||b||c| + (a.b)|c| +
+ * (a.c)|b| + (b.c)|a|, a = v0 - p, b = v1 - p, c = v2 - p.
+ * dOmega = 2 (D dN - N dD) / (N^2 + D^2);  d/dp = -(d/da + d/db + d/dc). */
+static void solid_angle_grad(const double *a, const double *b, const double *c,
+                             double *ga, double *gb, double *gc) {
+    double la = sqrt(a[0]*a[0] + a[1]*a[1] + a[2]*a[2]);
+    double lb = sqrt(b[0]*b[0] + b[1]*b[1] + b[2]*b[2]);
+    double lc = sqrt(c[0]*c[0] + c[1]*c[1] + c[2]*c[2]);
+    double bxc[3] = {b[1]*c[2] - b[2]*c[1], b[2]*c[0] - b[0]*c[2], b[0]*c[1] - b[1]*c[0]};
+    double cxa[3] = {c[1]*a[2] - c[2]*a[1], c[2]*a[0] - c[0]*a[2], c[0]*a[1] - c[1]*a[0]};
+    double axb[3] = {a[1]*b[2] - a[2]*b[1], a[2]*b[0] - a[0]*b[2], a[0]*b[1] - a[1]*b[0]};
+    double N = a[0]*bxc[0] + a[1]*bxc[1] + a[2]*bxc[2];
+    double ab = a[0]*b[0] + a[1]*b[1] + a[2]*b[2];
+    double ac = a[0]*c[0] + a[1]*c[1] + a[2]*c[2];
+    double bc = b[0]*c[0] + b[1]*c[1] + b[2]*c[2];
+    double D = la * lb * lc + ab * lc + ac * lb + bc * la;
+    double k = 2.0 / (N * N + D * D);
+    for (int i = 0; i < 3; i++) {
+        double dDa = a[i] / la * (lb * lc + bc) + b[i] * lc + c[i] * lb;
+        double dDb = b[i] / lb * (la * lc + ac) + a[i] * lc + c[i] * la;
+        double dDc = c[i] / lc * (la * lb + ab) + a[i] * lb + b[i] * la;
+        ga[i] = k * (D * bxc[i] - N * dDa);
+        gb[i] = k * (D * cxa[i] - N * dDb);
+        gc[i] = k * (D * axb[i] - N * dDc);
+    }
+}
+
+typedef struct {
+    const float *V; int64_t nv; const int32_t *F; int64_t nf;
+    const float *P; int64_t nq; const double *gw;
+    double *grad_p; double *grad_V_parts; int nparts;
+} grad_ctx;
+
+static void grad_range(void *p, int64_t lo, int64_t hi) {
+    grad_ctx *c = (grad_ctx *)p;
+    int64_t chunk = (c->nq + c->nparts - 1) / c->nparts;
+    int part = (int)(chunk > 0 ? lo / chunk : 0);
+    double *gV = c->grad_V_parts ? c->grad_V_parts + (size_t)part * 3 * c->nv : NULL;
+    for (int64_t q = lo; q < hi; q++) {
+        const float *pp = c->P + 3 * q;
+        double g = c->gw ? c->gw[q] : 1.0;
+        double gp[3] = {0, 0, 0};
+        for (int64_t t = 0; t < c->nf; t++) {
+            double v[3][3], gr[3][3];
+            for (int k = 0; k < 3; k++) {
+                const float *x = c->V + 3 * (int64_t)c->F[3 * t + k];
+                for (int i = 0; i < 3; i++) v[k][i] = (double)x[i] - (double)pp[i];
+            }
+            solid_angle_grad(v[0], v[1], v[2], gr[0], gr[1], gr[2]);
+            for (int k = 0; k < 3; k++) {
+                for (int i = 0; i < 3; i++) {
+                    gp[i] -= gr[k][i];
+                    if (gV) gV[3 * (int64_t)c->F[3 * t + k] + i] += g * gr[k][i] / (4.0 * M_PI);
+                }
+            }
+        }
+        if (c->grad_p)
+            for (int i = 0; i < 3; i++) c->grad_p[3 * q + i] = g * gp[i] / (4.0 * M_PI);
+    }
+}
+
+/* grad_p[q] = gw[q] * dw_q/dp ; grad_V = sum_q gw[q] * dw_q/dV (gw NULL = 1).
+ * Either output may be NULL. */
+ORACLE_API int oracle_grad3d_vos(const float *V, int64_t nv, const int32_t *F, int64_t nf,
+                                 const float *P, int64_t nq, const double *gw, double *grad_p,
+                                 double *grad_V, int nthreads) {
+    if (nthreads < 1) nthreads = 1;
+    if (nq < nthreads) nthreads = (int)(nq > 0 ? nq : 1);
+    double *parts = NULL;
+    if (grad_V) {
+        parts = (double *)calloc((size_t)nthreads * 3 * (size_t)nv, sizeof(double));
+        if (!parts) return -1;
+    }
+    grad_ctx c = {V, nv, F, nf, P, nq, gw, grad_p, parts, nthreads};
+    parallel_for(nq, nthreads, grad_range, &c);
+    if (grad_V) {
+        for (int64_t i = 0; i < 3 * nv; i++) {
+            double s = 0.0;
+            for (int t = 0; t < nthreads; t++) s += parts[(size_t)t * 3 * nv + i];
+            grad_V[i] = s;
+        }
+        free(parts);
+    }
+    return 0;
+}
+
+/* ======================================================================== */
+/* 2D: cubic Bezier chains                                                  */
+/* ======================================================================== */
+static void bez_eval(const double *c, double u, double *x, double *y) {
+    double v = 1.0 - u;
+    double b0 = v * v * v, b1 = 3 * u * v * v, b2 = 3 * u * u * v, b3 = u * u * u;
+    *x = b0 * c[0] + b1 * c[2] + b2 * c[4] + b3 * c[6];
+    *y = b0 * c[1] + b1 * c[3] + b2 * c[5] + b3 * c[7];
+}
+
+static void bez_deriv(const double *c, double u, double *dx, double *dy) {
+    double v = 1.0 - u;
+    *dx = 3 * (v * v * (c[2] - c[0]) + 2 * u * v * (c[4] - c[2]) + u * u * (c[6] - c[4]));
+    *dy = 3 * (v * v * (c[3] - c[1]) + 2 * u * v * (c[5] - c[3]) + u * u * (c[7] - c[5]));
+}
+
+/* integrand of the subtended angle: cross(B - p, B') / |B - p|^2 */
+static double angle_rate(const double *c, const double *p, double u) {
+    double x, y, dx, dy;
+    bez_eval(c, u, &x, &y);
+    bez_deriv(c, u, &dx, &dy);
+    x -= p[0]; y -= p[1];
+    return (x * dy - y * dx) / (x * x + y * y);
+}
+
+/* Gauss-Kronrod 7-15 nodes/weights on [-1, 1] */
+static const double GK_X[8] = {0.991455371120812639206854697526329, 0.949107912342758524526189684047851,
+                               0.864864423359769072789712788640926, 0.741531185599394439863864773280788,
+                               0.586087235467691130294144845693013, 0.405845151377397166906606412076961,
+                               0.207784955007898467600689403773245, 0.0};
+static const double GK_WK[8] = {0.022935322010529224963732008058970, 0.063092092629978553290700663189204,
+                                0.104790010322250183839876322541518, 0.140653259715525918745189590510238,
+                                0.169004726639267902826583426598550, 0.190350578064785409913256402421014,
+                                0.204432940075298892414161999234649, 0.209482141084727828012999174891714};
+static const double GK_WG[4] = {0.129484966168869693270611432679082, 0.279705391489276667901467771423780,
+                                0.381830050505118944950369775488975, 0.417959183673469387755102040816327};
+
+/* Gauss-Kronrod 7-15 on [a, b] with the QUADPACK-style error estimate
+ * (the Kronrod-Gauss difference scaled by the integral of |f - mean|). */
+static double gk15(const double *c, const double *p, double a, double b, double *err,
+                   double *resabs) {
+    double m = 0.5 * (a + b), h = 0.5 * (b - a);
+    double fv[15];
+    fv[7] = angle_rate(c, p, m);
+    double k = GK_WK[7] * fv[7], g = GK_WG[3] * fv[7], ka = GK_WK[7] * fabs(fv[7]);
+    for (int i = 0; i < 7; i++) {
+        double f1 = angle_rate(c, p, m - h * GK_X[i]);
+        double f2 = angle_rate(c, p, m + h * GK_X[i]);
+        fv[i] = f1; fv[14 - i] = f2;
+        k += GK_WK[i] * (f1 + f2);
+        ka += GK_WK[i] * (fabs(f1) + fabs(f2));
+        if (i & 1) g += GK_WG[i / 2] * (f1 + f2);
+    }
+    double mean = 0.5 * k;
+    double asc = GK_WK[7] * fabs(fv[7] - mean);
+    for (int i = 0; i < 7; i++) asc += GK_WK[i] * (fabs(fv[i] - mean) + fabs(fv[14 - i] - mean));
+    double e = fabs((k - g) * h);
+    asc *= fabs(h);
+    if (asc != 0.0 && e != 0.0) {
+        double r = pow(200.0 * e / asc, 1.5);
+        e = asc * (r < 1.0 ? r : 1.0);
+    }
+    *err = e;
+    *resabs = ka * fabs(h);
+    return k * h;
+}
+
+/* Adaptive bisection: a subinterval is accepted when its error estimate is
+ * below tol times its length, or below the round-off floor (50 ulps of the
+ * integral of |f| over it), or when it is shorter than 1e-12.  A non-finite
+ * value (p on the curve) is returned as is. */
+static double adapt(const double *c, const double *p, double a, double b, double tol, int depth) {
+    double err, resabs;
+    double v = gk15(c, p, a, b, &err, &resabs);
+    if (!isfinite(v) || !isfinite(err)) return v;
+    if (err <= tol * (b - a) || err <= 50.0 * 2.220446049250313e-16 * resabs || depth >= 48
+        || b - a < 1e-12)
+        return v;
+    double m = 0.5 * (a + b);
+    return adapt(c, p, a, m, tol, depth + 1) + adapt(c, p, m, b, tol, depth + 1);
+}
+
+typedef struct {
+    const double *ctrl; int64_t nseg; const double *P; double *w; double tol;
+} quad_ctx;
+
+static void quad_range(void *p, int64_t lo, int64_t hi) {
+    quad_ctx *c = (quad_ctx *)p;
+    for (int64_t q = lo; q < hi; q++) {
+        double acc = 0.0;
+        for (int64_t s = 0; s < c->nseg; s++)
+            acc += adapt(c->ctrl + 6 * s, c->P + 2 * q, 0.0, 1.0, c->tol, 0);
+        c->w[q] = acc / (2.0 * M_PI);
+    }
+}
+
+/* 2D definition: w(p) = (1/2pi) sum_segments int_0^1 cross(B-p, B')/|B-p|^2 du
+ * ctrl: 3*nseg+1 points (x, y) of one C0 chain. */
+ORACLE_API void oracle_w2d_quad(const double *ctrl, int64_t nseg, const double *P, int64_t nq,
+                                double *w, double tol, int nthreads) {
+    quad_ctx c = {ctrl, nseg, P, w, tol};
+    parallel_for(nq, nthreads, quad_range, &c);
+}
+
+/* Real roots in [0, 1] of g(u) = sum_k g_k B_k(u) (cubic Bernstein), sorted,
+ * found by splitting [0,1] at the roots of g' into monotone intervals and
+ * bisecting each interval whose end values straddle zero.  With the
+ * half-open rule of a ray perturbed towards g > 0 (the ray is taken as
+ * g = 0+): an interval from g(u0) to g(u1) holds a crossing iff
+ * min(g0, g1) <= 0 < max(g0, g1).  Returns the number of crossings; for
+ * each, the parameter and the direction (+1 when g increases). */
+static double bern3(const double *g, double u) {
+    double v = 1.0 - u;
+    return v * v * v * g[0] + 3 * u * v * v * g[1] + 3 * u * u * v * g[2] + u * u * u * g[3];
+}
+
+static int monotone_crossings(const double *g, double *us, int *dirs) {
+    /* derivative coefficients (quadratic Bernstein, times 3) */
+    double d0 = g[1] - g[0], d1 = g[2] - g[1], d2 = g[3] - g[2];
+    /* power basis of d(u) = d0 (1-u)^2 + 2 d1 u (1-u) + d2 u^2 */
+    double A = d0 - 2 * d1 + d2, B = 2 * (d1 - d0), C = d0;
+    double cuts[4];
+    int nc = 0;
+    cuts[nc++] = 0.0;
+    double r[2];
+    int nr = 0;
+    if (fabs(A) < 1e-300 * (fabs(B) + fabs(C) + 1e-300)) {
+        if (B != 0.0) r[nr++] = -C / B;
+    } else {
+        double disc = B * B - 4 * A * C;
+        if (disc > 0) {
+            double sq = sqrt(disc);
+            double qq = -0.5 * (B + (B >= 0 ? sq : -sq));
+            r[nr++] = qq / A;
+            if (qq != 0.0) r[nr++] = C / qq;
+        }
+    }
+    if (nr == 2 && r[0] > r[1]) { double t = r[0]; r[0] = r[1]; r[1] = t; }
+    for (int i = 0; i < nr; i++) if (r[i] > 0.0 && r[i] < 1.0) cuts[nc++] = r[i];
+    cuts[nc++] = 1.0;
+    int n = 0;
+    for (int i = 0; i + 1 < nc; i++) {
+        double u0 = cuts[i], u1 = cuts[i + 1];
+        double g0 = bern3(g, u0), g1 = bern3(g, u1);
+        if (i == 0) g0 = g[0];
+        if (i + 2 == nc) g1 = g[3];
+        double lo = g0 < g1 ? g0 : g1, hi = g0 < g1 ? g1 : g0;
+        if (!(lo <= 0.0 && 0.0 < hi)) continue;
+        double a = u0, b = u1;
+        int inc = g1 > g0;
+        for (int it = 0; it < 200 && b - a > 0.0; it++) {
+            double m = 0.5 * (a + b);
+            if (m <= a || m >= b) break;
+            double gm = bern3(g, m);
+            if ((gm > 0.0) == inc) b = m; else a = m;
+        }
+        us[n] = 0.5 * (a + b);
+        dirs[n] = inc ? 1 : -1;
+        n++;
+    }
+    return n;
+}
+
+/* signed crossings of the ray p + t q (t > 0) with one cubic segment; the
+ * ray is perturbed to its left (towards cross(q, x - p) > 0). */
+static int seg_ray_crossings(const double *c, const double *p, const double *q) {
+    double g[4];
+    for (int k = 0; k < 4; k++) {
+        double x = c[2 * k] - p[0], y = c[2 * k + 1] - p[1];
+        g[k] = q[0] * y - q[1] * x;            /* cross(q, B_k - p) */
+    }
+    double us[3];
+    int dirs[3];
+    int n = monotone_crossings(g, us, dirs);
+    int chi = 0;
+    for (int i = 0; i < n; i++) {
+        double x, y;
+        bez_eval(c, us[i], &x, &y);
+        double t = (x - p[0]) * q[0] + (y - p[1]) * q[1];
+        if (t > 0.0) chi += dirs[i];
+    }
+    return chi;
+}
+
+static int chain_ray_crossings(const double *ctrl, int64_t nseg, const double *p, const double *q) {
+    int chi = 0;
+    for (int64_t s = 0; s < nseg; s++) chi += seg_ray_crossings(ctrl + 6 * s, p, q);
+    return chi;
+}
+
+typedef struct {
+    const double *ctrl; int64_t nseg; const double *P; double *w; int32_t *chi;
+} alg1_ctx;
+
+/* Algorithm 1 in 2D.  The boundary of an open chain is its end points s, e;
+ * their directions from p split the unit circle into two arcs:
+ * A1 from e counter-clockwise to s, A2 from s counter-clockwise to e.  One
+ * ray through the middle of the larger arc gives its chi; crossing the
+ * direction of e counter-clockwise lowers chi by one (the in-plane normal
+ * rule of Lemma 2 for the positively oriented end point), so
+ * chi(A1) = chi(A2) - 1.  w = (|A1| chi(A1) + |A2| chi(A2)) / 2pi. */
+static void alg1_range(void *pv, int64_t lo, int64_t hi) {
+    alg1_ctx *c = (alg1_ctx *)pv;
+    const double *s = c->ctrl;
+    const double *e = c->ctrl + 6 * c->nseg;
+    for (int64_t qi = lo; qi < hi; qi++) {
+        const double *p = c->P + 2 * qi;
+        double as = atan2(s[1] - p[1], s[0] - p[0]);
+        double ae = atan2(e[1] - p[1], e[0] - p[0]);
+        double L1 = fmod(as - ae, 2 * M_PI);
+        if (L1 < 0) L1 += 2 * M_PI;
+        double L2 = 2 * M_PI - L1;
+        double mid;
+        int chi1, chi2;
+        if (L1 >= L2) {
+            mid = ae + 0.5 * L1;
+            double q[2] = {cos(mid), sin(mid)};
+            chi1 = chain_ray_crossings(c->ctrl, c->nseg, p, q);
+            chi2 = chi1 + 1;
+        } else {
+            mid = as + 0.5 * L2;
+            double q[2] = {cos(mid), sin(mid)};
+            chi2 = chain_ray_crossings(c->ctrl, c->nseg, p, q);
+            chi1 = chi2 - 1;
+        }
+        c->w[qi] = (L1 * chi1 + L2 * chi2) / (2 * M_PI);
+        if (c->chi) c->chi[qi] = L1 >= L2 ? chi1 : chi2;
+    }
+}
+
+ORACLE_API void oracle_w2d_alg1(const double *ctrl, int64_t nseg, const double *P, int64_t nq,
+                                double *w, int nthreads) {
+    alg1_ctx c = {ctrl, nseg, P, w, NULL};
+    parallel_for(nq, nthreads, alg1_range, &c);
+}
+
+/* Closed form relative to the +x ray (ray perturbed towards +y, i.e. a
+ * crossing counts when the curve's y range is [lo, hi) around y_p):
+ *   w = chi_x(C) + chi_x(chord e->s) + atan2(cross(s-p, e-p), dot(s-p, e-p))/2pi.
+ * chi_out receives chi_x(C) + chi_x(chord). */
+typedef struct {
+    const double *ctrl; int64_t nseg; const double *P; double *w; int32_t *chi;
+} cx_ctx;
+
+static int chord_crossing_x(const double *e, const double *s, const double *p) {
+    /* segment e -> s against the ray p + t(1,0), perturbed to y_p + 0 */
+    double y0 = e[1] - p[1], y1 = s[1] - p[1];
+    double lo = y0 < y1 ? y0 : y1, hi = y0 < y1 ? y1 : y0;
+    if (!(lo <= 0.0 && 0.0 < hi)) return 0;
+    /* x at y = y_p on the segment, compared with x_p via the orientation */
+    double cr = (e[0] - p[0]) * (s[1] - p[1]) - (e[1] - p[1]) * (s[0] - p[0]);
+    int up = y1 > y0;
+    /* the crossing is to the right of p iff p is left of the upward segment */
+    int right = up ? (cr > 0) : (cr < 0);
+    return right ? (up ? 1 : -1) : 0;
+}
+
+static void cx_range(void *pv, int64_t lo, int64_t hi) {
+    cx_ctx *c = (cx_ctx *)pv;
+    const double *s = c->ctrl;
+    const double *e = c->ctrl + 6 * c->nseg;
+    const double q[2] = {1.0, 0.0};
+    for (int64_t qi = lo; qi < hi; qi++) {
+        const double *p = c->P + 2 * qi;
+        int chi = chain_ray_crossings(c->ctrl, c->nseg, p, q) + chord_crossing_x(e, s, p);
+        double sx = s[0] - p[0], sy = s[1] - p[1], ex = e[0] - p[0], ey = e[1] - p[1];
+        double ang = atan2(sx * ey - sy * ex, sx * ex + sy * ey);
+        c->w[qi] = (double)chi + ang / (2 * M_PI);
+        if (c->chi) c->chi[qi] = chi;
+    }
+}
+
+ORACLE_API void oracle_w2d_closed_x(const double *ctrl, int64_t nseg, const double *P, int64_t nq,
+                                    double *w, int32_t *chi, int nthreads) {
+    cx_ctx c = {ctrl, nseg, P, w, chi};
+    parallel_for(nq, nthreads, cx_range, &c);
+}
+
+/* signed crossings of an arbitrary ray with a chain (exposed for tests) */
+ORACLE_API int oracle_chain_ray_crossings(const double *ctrl, int64_t nseg, const double *p,
+                                          const double *q) {
+    return chain_ray_crossings(ctrl, nseg, p, q);
+}
+
+/* ======================================================================== */
+/* Distances (test filtering only: w is undefined on M)                     */
+/* ======================================================================== */
+static double dot3(const double *a, const double *b) { return a[0]*b[0] + a[1]*b[1] + a[2]*b[2]; }
+
+/* squared distance from p to triangle (a, b, c): closest point by Voronoi
+ * region classification of the triangle's vertices, edges and face. */
+static double tri_dist2(const double *a, const double *b, const double *c, const double *p) {
+    double ab[3], ac[3], ap[3], q[3];
+    for (int i = 0; i < 3; i++) { ab[i] = b[i] - a[i]; ac[i] = c[i] - a[i]; ap[i] = p[i] - a[i]; }
+    double d1 = dot3(ab, ap), d2 = dot3(ac, ap);
+    if (d1 <= 0 && d2 <= 0) { for (int i = 0; i < 3; i++) q[i] = a[i]; goto done; }
+    double bp[3];
+    for (int i = 0; i < 3; i++) bp[i] = p[i] - b[i];
+    double d3 = dot3(ab, bp), d4 = dot3(ac, bp);
+    if (d3 >= 0 && d4 <= d3) { for (int i = 0; i < 3; i++) q[i] = b[i]; goto done; }
+    double vc = d1 * d4 - d3 * d2;
+    if (vc <= 0 && d1 >= 0 && d3 <= 0) {
+        double v = d1 / (d1 - d3);
+        for (int i = 0; i < 3; i++) q[i] = a[i] + v * ab[i];
+        goto done;
+    }
+    double cp[3];
+    for (int i = 0; i < 3; i++) cp[i] = p[i] - c[i];
+    double d5 = dot3(ab, cp), d6 = dot3(ac, cp);
+    if (d6 >= 0 && d5 <= d6) { for (int i = 0; i < 3; i++) q[i] = c[i]; goto done; }
+    double vb = d5 * d2 - d1 * d6;
+    if (vb <= 0 && d2 >= 0 && d6 <= 0) {
+        double w = d2 / (d2 - d6);
+        for (int i = 0; i < 3; i++) q[i] = a[i] + w * ac[i];
+        goto done;
+    }
+    double va = d3 * d6 - d5 * d4;
+    if (va <= 0 && (d4 - d3) >= 0 && (d5 - d6) >= 0) {
+        double w = (d4 - d3) / ((d4 - d3) + (d5 - d6));
+        for (int i = 0; i < 3; i++) q[i] = b[i] + w * (c[i] - b[i]);
+        goto done;
+    }
+    {
+        double den = 1.0 / (va + vb + vc);
+        double v = vb * den, w = vc * den;
+        for (int i = 0; i < 3; i++) q[i] = a[i] + ab[i] * v + ac[i] * w;
+    }
+done:;
+    double r = 0;
+    for (int i = 0; i < 3; i++) r += (p[i] - q[i]) * (p[i] - q[i]);
+    return r;
+}
+
+typedef struct { const float *V; const int32_t *F; int64_t nf; const float *P; double *out; } dist_ctx;
+
+static void dist_range(void *pv, int64_t lo, int64_t hi) {
+    dist_ctx *c = (dist_ctx *)pv;
+    for (int64_t q = lo; q < hi; q++) {
+        double p[3] = {c->P[3*q], c->P[3*q+1], c->P[3*q+2]};
+        double best = INFINITY;
+        for (int64_t t = 0; t < c->nf; t++) {
+            double v[3][3];
+            for (int k = 0; k < 3; k++)
+                for (int i = 0; i < 3; i++) v[k][i] = c->V[3 * (int64_t)c->F[3*t+k] + i];
+            double d2 = tri_dist2(v[0], v[1], v[2], p);
+            if (d2 < best) best = d2;
+        }
+        c->out[q] = sqrt(best);
+    }
+}
+
+ORACLE_API void oracle_dist3d(const float *V, const int32_t *F, int64_t nf, const float *P,
+                              int64_t nq, double *out, int nthreads) {
+    dist_ctx c = {V, F, nf, P, out};
+    parallel_for(nq, nthreads, dist_range, &c);
+}
+
+typedef struct { const double *ctrl; int64_t nseg; const double *P; double *out; } dist2_ctx;
+
+static void dist2_range(void *pv, int64_t lo, int64_t hi) {
+    dist2_ctx *c = (dist2_ctx *)pv;
+    for (int64_t q = lo; q < hi; q++) {
+        const double *p = c->P + 2 * q;
+        double best = INFINITY;
+        for (int64_t s = 0; s < c->nseg; s++) {
+            const double *cc = c->ctrl + 6 * s;
+            int ns = 256;
+            double bu = 0, bd = INFINITY;
+            for (int k = 0; k <= ns; k++) {
+                double x, y, u = (double)k / ns;
+                bez_eval(cc, u, &x, &y);
+                double d2 = (x - p[0]) * (x - p[0]) + (y - p[1]) * (y - p[1]);
+                if (d2 < bd) { bd = d2; bu = u; }
+            }
+            /* golden-section refinement around the best sample */
+            double a = bu - 1.0 / ns, b = bu + 1.0 / ns;
+            if (a < 0) a = 0;
+            if (b > 1) b = 1;
+            for (int it = 0; it < 80; it++) {
+                double m1 = a + 0.381966 * (b - a), m2 = b - 0.381966 * (b - a);
+                double x1, y1, x2, y2;
+                bez_eval(cc, m1, &x1, &y1);
+                bez_eval(cc, m2, &x2, &y2);
+                double f1 = (x1 - p[0]) * (x1 - p[0]) + (y1 - p[1]) * (y1 - p[1]);
+                double f2 = (x2 - p[0]) * (x2 - p[0]) + (y2 - p[1]) * (y2 - p[1]);
+                if (f1 < f2) b = m2; else a = m1;
+                if (f1 < bd) bd = f1;
+                if (f2 < bd) bd = f2;
+            }
+            if (bd < best) best = bd;
+        }
+        c->out[q] = sqrt(best);
+    }
+}
+
+ORACLE_API void oracle_dist2d(const double *ctrl, int64_t nseg, const double *P, int64_t nq,
+                              double *out, int nthreads) {
+    dist2_ctx c = {ctrl, nseg, P, out};
+    parallel_for(nq, nthreads, dist2_range, &c);
+}
