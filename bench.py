@@ -1,0 +1,349 @@
+#!/usr/bin/env python3
+"""Benchmark: one-shot GWN queries/s on the capped-icosphere workload.
+
+Workload (one step): the generalized winding number of an icosphere at
+subdivision 6 with the polar cap z > 0.8 removed (73,724 triangles, 252
+boundary edges, vertex noise 1e-3) at every point of a 256^3 grid on
+[-1.2, 1.2]^3 (16,777,216 queries), for one seeded ray direction: exact
+crossing counts (LBVH traversal) + float32 boundary term + epilogue, with the
+mesh, its boundary loops and its LBVH resident on the device.
+
+JSON keys beyond the common contract:
+  roofline      dominant kernel (boundary term) vs the FP32 issue roofline
+  kernels       per-kernel average time from CUDA events on the launch stream
+  prep_ms       per-geometry preparation (host boundary extraction + upload,
+                device LBVH build), outside `value`
+  bruteforce_gpu  the brute-force per-triangle solid-angle sum on the same GPU
+  cpu_baseline  the FP64 oracle on this host's cores (bounded sample)
+  e2e           through the C ABI from host buffers: mesh creation from host
+                V/F, LBVH build, evaluation and the copy of w back, per step
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "GWN queries/sec, one-shot vs brute-force solid-angle sum on 1 GB300 at |Δw|≤1e-6"
+UNIT = "queries/s"
+WORKLOAD = "icosphere_cap_s6_73724tris_256^3grid"
+
+# FP32 lane operations per boundary record (vertex) and per boundary edge of
+# the boundary-term kernel, counted from its formulation (an FMA counts as
+# one operation):
+#   vertex: a = A - p (3), projection on e1, e2, n (9), |a_perp|^2, |a|^2 (3),
+#           rsqrt + scale + clamp (3), s = |a|+a_n or |a_perp|^2/(|a|-a_n) (6)  -> 24
+#   edge:   num (2), den (3), atan2 (20: min/max 2, reciprocal + product 2,
+#           degree-8 polynomial 10, reduction/quadrant fix-ups 6),
+#           cut test (2), compensated accumulation (4)                          -> 31
+W_VERTEX = 24
+W_EDGE = 31
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"gwn_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.out, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.out.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def workload(rank: int = 0, world: int = 1):
+    import gen
+    from paper_2408_04466_gb300.shard import shard_grid
+    m = gen.icosphere_cap()
+    lo, hi, dims, span = shard_grid(m.grid.lo, m.grid.hi, m.grid.dims, rank, world, weak=True)
+    return m, (lo, hi, dims)
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle (baseline / reference arm)
+# ----------------------------------------------------------------------------
+def oracle_rate(m, n_sample: int, seed: int):
+    import gen
+    import oracle
+    rng = np.random.default_rng(seed)
+    idx = np.sort(rng.choice(m.grid.n, n_sample, replace=False))
+    P = gen.grid_points(m.grid, index=idx)
+    edges = oracle.boundary_edges(m.F)
+    t0 = time.perf_counter()
+    oracle.w3d_oneshot(m.V, m.F, P, m.d, edges=edges)
+    dt = time.perf_counter() - t0
+    return n_sample / dt, dt
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    m, _ = workload()
+    cores = oracle.default_threads()
+    n = args.ref_sample
+    for w in range(args.warmup):
+        oracle_rate(m, n, 1000 + w)
+    times = []
+    for s in range(args.steps):
+        r, dt = oracle_rate(m, n, 2000 + s)
+        times.append(dt)
+    tot = sum(times)
+    value = n * args.steps / tot
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "queries_per_step": n, "l2": "n/a (host)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{n} seeded queries of the 256^3 grid per step; FP64 one-shot "
+                                   f"(exact crossing count by brute force over all 73,724 triangles + "
+                                   f"boundary term)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ----------------------------------------------------------------------------
+# GPU arm
+# ----------------------------------------------------------------------------
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_2408_04466_gb300 import build as gbuild
+    if rank == 0 or world == 1:
+        gbuild.build()
+    if world > 1:
+        dist.barrier()
+    import paper_2408_04466_gb300 as gwn
+
+    m, (lo, hi, dims) = workload(rank, world)
+    nq = int(np.prod(dims))
+    stream = torch.cuda.Stream(device=dev)
+    torch.cuda.set_stream(stream)
+    ctx = gwn.Context(local, stream)
+    t0 = time.perf_counter()
+    mesh = gwn.Mesh(ctx, m.V, m.F)
+    t1 = time.perf_counter()
+    mesh.prepare(m.d)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    prep = {"boundary_extract_upload_ms": 1e3 * (t1 - t0), "lbvh_build_ms": 1e3 * (t2 - t1)}
+    info = mesh.info()
+    E, L = info["n_boundary_edges"], info["n_loops"]
+    grid = gwn.Grid(lo, hi, dims)
+    w = torch.empty(nq, dtype=torch.float32, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    # stats run (also a warm-up): per-kernel times and counters
+    st = mesh.eval(grid, m.d, stats=True, out=w)["stats"]
+    for _ in range(args.warmup):
+        mesh.eval(grid, m.d, out=w)
+    torch.cuda.synchronize()
+
+    # timed region: per step, flush L2 (256 MiB write), then time the step with
+    # events on the launch stream; a second pair of events splits the kernels
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    wall0 = time.perf_counter()
+    for s in range(args.steps):
+        flush.fill_(float(s))
+        ev[s][0].record(stream)
+        mesh.eval(grid, m.d, out=w)
+        ev[s][1].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    tot_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([tot_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.barrier()
+        tot_ms = float(t.item())
+    value = world * nq * args.steps / (tot_ms * 1e-3)
+
+    # per-kernel split: a stats call times traverse and boundary separately
+    ks = []
+    for _ in range(5):
+        ks.append(mesh.eval(grid, m.d, stats=True, out=w)["stats"])
+    ms_trav = statistics.median(k["ms_traverse"] for k in ks)
+    ms_bterm = statistics.median(k["ms_boundary"] for k in ks)
+
+    line = None
+    if rank == 0:
+        peaks, peak_kind = _peaks()
+        clk_hz = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+        alu_peak = SM_COUNT * FP32_LANES_PER_SM * clk_hz / 1e12          # Tops/s
+        ops = nq * ((E + L) * W_VERTEX + E * W_EDGE)
+        achieved = ops / (ms_bterm * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tops/s (FP32 lane ops)",
+                "frac": achieved / alu_peak, "traffic": None, "kernel": "bterm3d_kernel",
+                "peak_source": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x sm_max_mhz "
+                               f"({peak_kind} MEASURED_PEAKS)" if peak_kind == "measured" else "fallback clock"}
+        # brute-force comparator on a sub-grid (first 4 planes: 262,144 queries)
+        sub = gwn.Grid(lo, (hi[0], hi[1], lo[2] + (hi[2] - lo[2]) * 3 / (dims[2] - 1)), (dims[0], dims[1], 4))
+        bw = torch.empty(sub.n, dtype=torch.float32, device=dev)
+        mesh.bruteforce(sub)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(3):
+            bw = mesh.bruteforce(sub)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        bf_rate = 3 * sub.n / (e0.elapsed_time(e1) * 1e-3)
+
+        # end to end: host V/F (pinned) -> mesh, LBVH, eval, w -> pinned host
+        Vh = torch.as_tensor(m.V).pin_memory()
+        Fh = torch.as_tensor(m.F).pin_memory()
+        wh = torch.empty(nq, dtype=torch.float32).pin_memory()
+        import ctypes as C
+        from paper_2408_04466_gb300 import _capi
+        e2e_steps = max(3, min(args.steps, 10))
+        times = []
+        for s in range(e2e_steps + 1):
+            torch.cuda.synchronize()
+            a = time.perf_counter()
+            mh = gwn.Mesh(ctx, Vh, Fh)
+            qc = grid.to_c()
+            _capi.check(ctx.lib.gwn_eval_host(mh.h, C.byref(qc), np.ascontiguousarray(m.d).ctypes.data_as(C.c_void_p),
+                                              C.c_void_p(wh.data_ptr())), "gwn_eval_host")
+            b = time.perf_counter()
+            mh.close()
+            if s > 0:
+                times.append(b - a)
+        e2e = {"value": nq / statistics.median(times), "unit": UNIT,
+               "h2d_bytes_per_step": int(m.V.nbytes + m.F.nbytes), "d2h_bytes_per_step": int(nq * 4),
+               "includes": "host boundary extraction, uploads, LBVH build, traversal, boundary term, copy of w"}
+
+        # CPU baseline: the oracle on this host's cores, bounded sample
+        import oracle
+        oracle.build()
+        n_cpu = args.cpu_sample
+        rate, dt = oracle_rate(m, n_cpu, 7)
+        cpu = {"value": rate, "unit": UNIT, "cores": oracle.default_threads(), "kind": "oracle",
+               "sample": f"{n_cpu} seeded queries of the 256^3 grid; FP64 one-shot (brute-force exact crossing "
+                         f"count over all triangles + boundary term); {dt:.1f} s"}
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "queries_per_gpu": nq, "boundary_edges": E, "boundary_loops": L,
+                       "triangles": int(len(m.F)), "l2": "flushed (256 MiB write before every step)",
+                       "parallelism": f"queries sharded in z-slabs over {world} GPU(s), geometry replicated"},
+            "roofline": roof,
+            "kernels": {"traverse_ms": ms_trav, "bterm3d_ms": ms_bterm,
+                        "n_tri_tests_per_query": st["n_tri_tests"] / nq,
+                        "n_cut_sign_per_query": st["n_cut_sign"] / nq,
+                        "n_fp64_filter": st["n_fp64_filter"], "n_exact": st["n_exact"]},
+            "prep_ms": prep,
+            "bruteforce_gpu": {"value": bf_rate, "unit": UNIT, "sample": f"{sub.n} grid queries x 73,724 triangles"},
+            "speedup_vs_bruteforce_gpu": value / world / bf_rate,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": 2 * args.steps,
+            "clocks": clk,
+            "wall_s_timed": wall,
+        }
+        print(json.dumps(line))
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--cpu-sample", type=int, default=4096)
+    ap.add_argument("--ref-sample", type=int, default=1024)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -387,7 +387,9 @@ ORACLE_API void oracle_chi3d(const float *V, const int32_t *F, int64_t nf, const
 /* Each triangle (i, j, k) contributes directed edges i->j, j->k, k->i.  The
  * net multiplicity of the undirected pair {u < v} is (#u->v) - (#v->u); a
  * pair with nonzero net multiplicity is a boundary edge, reported as
- * u->v with m > 0 or v->u with m > 0. */
+ * u->v with m > 0 or v->u with m > 0.  A face with a repeated index has a
+ * zero-length edge u->u; it bounds nothing (its solid angle is 0) and is
+ * skipped. */
 typedef struct { int32_t u, v; int32_t s; } dedge_t;
 
 static int cmp_dedge(const void *x, const void *y) {
@@ -401,20 +403,22 @@ ORACLE_API int64_t oracle_boundary_edges(const int32_t *F, int64_t nf, int32_t *
                                          int32_t *dst, int32_t *mult) {
     dedge_t *e = (dedge_t *)malloc(sizeof(dedge_t) * 3 * (size_t)(nf > 0 ? nf : 1));
     if (!e) return -1;
+    int64_t ne = 0;
     for (int64_t t = 0; t < nf; t++) {
         for (int k = 0; k < 3; k++) {
             int32_t a = F[3 * t + k], b = F[3 * t + (k + 1) % 3];
-            dedge_t *x = &e[3 * t + k];
+            if (a == b) continue;          /* zero-length edge of a degenerate face */
+            dedge_t *x = &e[ne++];
             if (a < b) { x->u = a; x->v = b; x->s = 1; }
             else { x->u = b; x->v = a; x->s = -1; }
         }
     }
-    qsort(e, 3 * (size_t)nf, sizeof(dedge_t), cmp_dedge);
+    qsort(e, (size_t)ne, sizeof(dedge_t), cmp_dedge);
     int64_t n = 0;
-    for (int64_t i = 0; i < 3 * nf;) {
+    for (int64_t i = 0; i < ne;) {
         int64_t j = i;
         int32_t m = 0;
-        while (j < 3 * nf && e[j].u == e[i].u && e[j].v == e[i].v) { m += e[j].s; j++; }
+        while (j < ne && e[j].u == e[i].u && e[j].v == e[i].v) { m += e[j].s; j++; }
         if (m > 0) { src[n] = e[i].u; dst[n] = e[i].v; mult[n] = m; n++; }
         else if (m < 0) { src[n] = e[i].v; dst[n] = e[i].u; mult[n] = -m; n++; }
         i = j;

@@ -1,0 +1,216 @@
+// backward.cu -- gradient of w with respect to the query points and the mesh
+// vertices.  chi_d is piecewise constant, so dw = dB_d: only the boundary term
+// contributes, and its derivative does not depend on d.
+//
+// Moving the boundary by delta x changes the solid angle by the flux of the
+// swept strip; for a straight edge r(s) = a + s E (a = A - p, E = B - A,
+// s in [0, 1]) with linearly interpolated motion this gives
+//     dOmega/dA = -(a x E) (I0 - I1),   dOmega/dB = -(a x E) I1,
+//     dOmega/dp =  (a x E) I0           (= -(dOmega/dA + dOmega/dB))
+// with I0 = int_0^1 |r|^-3 ds and I1 = int_0^1 s |r|^-3 ds in closed form:
+//     I0 = (E.b/|b| - E.a/|a|) / |a x E|^2,
+//     I1 = ((1/|a| - 1/|b|) - (a.E) I0) / |E|^2.
+// Both are evaluated without cancellation for short edges:
+//     E.b/|b| - E.a/|a| = (|E|^2 |a| - (E.a) E.(a+b) / (|a|+|b|)) / (|a||b|)
+//     1/|a| - 1/|b|     = E.(a+b) / (|a||b| (|a|+|b|)).
+// The p-gradient sum over edges is the Biot-Savart line integral of the
+// boundary; it is checked against finite differences and against the
+// gradient of the per-triangle solid-angle sum.
+//
+// Kernels: (1) grad_p, one thread per K queries looping over the boundary
+// records (deterministic per query); (2) grad_V partials, one thread per
+// boundary record looping over a chunk of queries staged in shared memory,
+// one partial per (chunk, record); (3) a fixed-order reduction over chunks
+// and a scatter to vertices through a per-vertex record list.
+#include "gwn_internal.h"
+#include "query.cuh"
+
+namespace gwn {
+
+#define GWN_INV_4PI 0.07957747154594767f
+
+struct EdgeGrad {
+    float cx, cy, cz, i0, i1;
+};
+
+__device__ __forceinline__ EdgeGrad edge_grad(float ax, float ay, float az, float bx, float by, float bz,
+                                              float ex, float ey, float ez) {
+    EdgeGrad g;
+    g.cx = ay * ez - az * ey;
+    g.cy = az * ex - ax * ez;
+    g.cz = ax * ey - ay * ex;
+    float del = fmaxf(g.cx * g.cx + g.cy * g.cy + g.cz * g.cz, 1e-37f);
+    float la = sqrtf(ax * ax + ay * ay + az * az);
+    float lb = sqrtf(bx * bx + by * by + bz * bz);
+    float e2 = fmaxf(ex * ex + ey * ey + ez * ez, 1e-37f);
+    float ea = ex * ax + ey * ay + ez * az;
+    float eab = 2.f * ea + e2;                       // E.(a+b) = |b|^2 - |a|^2
+    float s = la + lb;
+    float num0 = e2 * la - ea * eab / s;
+    float inv_ab = 1.f / (la * lb);
+    g.i0 = num0 * inv_ab / del;
+    float invdiff = eab * inv_ab / s;                // 1/|a| - 1/|b|
+    g.i1 = (invdiff - ea * g.i0) / e2;
+    return g;
+}
+
+template <int K>
+__global__ void __launch_bounds__(256) grad_p_kernel(const float4 *__restrict__ bseq, int nb, QuerySrc q,
+                                                     const float *__restrict__ grad_w, float *__restrict__ grad_p) {
+    const int64_t base = (int64_t)blockIdx.x * blockDim.x * K + threadIdx.x;
+    float px[K], py[K], pz[K], gx[K], gy[K], gz[K];
+#pragma unroll
+    for (int j = 0; j < K; j++) {
+        int64_t idx = base + (int64_t)j * blockDim.x;
+        float3 p = idx < q.n ? query_point3(q, idx) : make_float3(0.f, 0.f, 0.f);
+        px[j] = p.x; py[j] = p.y; pz[j] = p.z;
+        gx[j] = gy[j] = gz[j] = 0.f;
+    }
+    for (int k = 1; k < nb; k++) {
+        float4 A = __ldg(&bseq[k - 1]), B = __ldg(&bseq[k]);
+        if (B.w == 0.f) continue;
+        float ex = B.x - A.x, ey = B.y - A.y, ez = B.z - A.z;
+#pragma unroll
+        for (int j = 0; j < K; j++) {
+            EdgeGrad g = edge_grad(A.x - px[j], A.y - py[j], A.z - pz[j], B.x - px[j], B.y - py[j], B.z - pz[j],
+                                   ex, ey, ez);
+            float w = g.i0 * B.w;
+            gx[j] = fmaf(g.cx, w, gx[j]);
+            gy[j] = fmaf(g.cy, w, gy[j]);
+            gz[j] = fmaf(g.cz, w, gz[j]);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < K; j++) {
+        int64_t idx = base + (int64_t)j * blockDim.x;
+        if (idx < q.n) {
+            float s = grad_w[idx] * GWN_INV_4PI;
+            grad_p[3 * idx] = gx[j] * s;
+            grad_p[3 * idx + 1] = gy[j] * s;
+            grad_p[3 * idx + 2] = gz[j] * s;
+        }
+    }
+}
+
+constexpr int GV_THREADS = 128;
+constexpr int GV_QTILE = 256;
+
+// partial[(chunk * nb + k) * 6 + {0..2}] = sum over the chunk of dw/dA of the
+// edge ending at record k, {3..5} = dw/dB.
+__global__ void __launch_bounds__(GV_THREADS) grad_v_partial_kernel(const float4 *__restrict__ bseq, int nb,
+                                                                    QuerySrc q, const float *__restrict__ grad_w,
+                                                                    int64_t chunk_len, float *__restrict__ partial) {
+    __shared__ float4 qs[GV_QTILE];
+    int k = blockIdx.x * GV_THREADS + threadIdx.x;
+    int chunk = blockIdx.y;
+    int64_t q0 = (int64_t)chunk * chunk_len;
+    int64_t q1 = q0 + chunk_len < q.n ? q0 + chunk_len : q.n;
+    bool active = k >= 1 && k < nb;
+    float4 A = active ? bseq[k - 1] : make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 B = active ? bseq[k] : make_float4(0.f, 0.f, 0.f, 0.f);
+    active = active && B.w != 0.f;
+    float ex = B.x - A.x, ey = B.y - A.y, ez = B.z - A.z;
+    float sA[3] = {0.f, 0.f, 0.f}, sB[3] = {0.f, 0.f, 0.f};
+    for (int64_t t0 = q0; t0 < q1; t0 += GV_QTILE) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < GV_QTILE; i += GV_THREADS) {
+            int64_t qi = t0 + i;
+            if (qi < q1) {
+                float3 p = query_point3(q, qi);
+                qs[i] = make_float4(p.x, p.y, p.z, grad_w[qi] * GWN_INV_4PI);
+            } else {
+                qs[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        }
+        __syncthreads();
+        if (active) {
+            int cnt = (int)(q1 - t0 < GV_QTILE ? q1 - t0 : GV_QTILE);
+            for (int i = 0; i < cnt; i++) {
+                float4 p = qs[i];
+                EdgeGrad g = edge_grad(A.x - p.x, A.y - p.y, A.z - p.z, B.x - p.x, B.y - p.y, B.z - p.z, ex, ey, ez);
+                float wa = -(g.i0 - g.i1) * p.w, wb = -g.i1 * p.w;
+                sA[0] = fmaf(g.cx, wa, sA[0]); sA[1] = fmaf(g.cy, wa, sA[1]); sA[2] = fmaf(g.cz, wa, sA[2]);
+                sB[0] = fmaf(g.cx, wb, sB[0]); sB[1] = fmaf(g.cy, wb, sB[1]); sB[2] = fmaf(g.cz, wb, sB[2]);
+            }
+        }
+    }
+    if (k < nb) {
+        float *o = partial + ((int64_t)chunk * nb + k) * 6;
+        o[0] = sA[0]; o[1] = sA[1]; o[2] = sA[2];
+        o[3] = sB[0]; o[4] = sB[1]; o[5] = sB[2];
+    }
+}
+
+// per record: total gradient of its vertex from the edge ending there (as B)
+// and the edge starting there (as A of record k+1), summed over chunks in
+// chunk order.
+__global__ void grad_v_record_kernel(const float *__restrict__ partial, int n_chunks, int nb,
+                                     const float4 *__restrict__ bseq, float *__restrict__ rec_grad) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nb) return;
+    float g[3] = {0.f, 0.f, 0.f};
+    bool asB = bseq[k].w != 0.f;
+    bool asA = k + 1 < nb && bseq[k + 1].w != 0.f;
+    for (int c = 0; c < n_chunks; c++) {
+        const float *pk = partial + ((int64_t)c * nb + k) * 6;
+        if (asB) { g[0] += pk[3]; g[1] += pk[4]; g[2] += pk[5]; }
+        if (asA) {
+            const float *pn = partial + ((int64_t)c * nb + k + 1) * 6;
+            g[0] += pn[0]; g[1] += pn[1]; g[2] += pn[2];
+        }
+    }
+    rec_grad[3 * k] = g[0];
+    rec_grad[3 * k + 1] = g[1];
+    rec_grad[3 * k + 2] = g[2];
+}
+
+// per boundary vertex: sum its records in list order
+__global__ void grad_v_scatter_kernel(const float *__restrict__ rec_grad, const int32_t *__restrict__ bvert,
+                                      const int64_t *__restrict__ rec_off, const int32_t *__restrict__ recs,
+                                      int64_t n_bvert, float *__restrict__ grad_V) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_bvert) return;
+    float g[3] = {0.f, 0.f, 0.f};
+    for (int64_t r = rec_off[i]; r < rec_off[i + 1]; r++) {
+        int k = recs[r];
+        g[0] += rec_grad[3 * k]; g[1] += rec_grad[3 * k + 1]; g[2] += rec_grad[3 * k + 2];
+    }
+    int64_t v = bvert[i];
+    grad_V[3 * v] = g[0];
+    grad_V[3 * v + 1] = g[1];
+    grad_V[3 * v + 2] = g[2];
+}
+
+cudaError_t launch_grad_p(const float4 *bseq, int64_t nb, const QuerySrc &q, const float *grad_w, float *grad_p,
+                          cudaStream_t st) {
+    if (q.n == 0) return cudaSuccess;
+    constexpr int K = 2;
+    int64_t blocks = (q.n + 256 * K - 1) / (256 * K);
+    grad_p_kernel<K><<<(unsigned)blocks, 256, 0, st>>>(bseq, (int)nb, q, grad_w, grad_p);
+    return cudaGetLastError();
+}
+
+int grad_v_chunks(int64_t nq, int64_t nb, int sm_count) {
+    int64_t eblocks = (nb + GV_THREADS - 1) / GV_THREADS;
+    int64_t want = (int64_t)sm_count * 8 / (eblocks > 0 ? eblocks : 1);
+    if (want < 1) want = 1;
+    int64_t maxc = (nq + GV_QTILE - 1) / GV_QTILE;
+    if (want > maxc) want = maxc;
+    if (want > 4096) want = 4096;
+    return (int)(want > 0 ? want : 1);
+}
+
+cudaError_t launch_grad_v(const float4 *bseq, int64_t nb, const QuerySrc &q, const float *grad_w, int n_chunks,
+                          float *partial, float *rec_grad, const int32_t *bvert, const int64_t *rec_off,
+                          const int32_t *recs, int64_t n_bvert, float *grad_V, cudaStream_t st) {
+    if (nb == 0 || n_bvert == 0) return cudaSuccess;
+    int64_t chunk_len = (q.n + n_chunks - 1) / n_chunks;
+    dim3 grid((unsigned)((nb + GV_THREADS - 1) / GV_THREADS), (unsigned)n_chunks);
+    grad_v_partial_kernel<<<grid, GV_THREADS, 0, st>>>(bseq, (int)nb, q, grad_w, chunk_len, partial);
+    grad_v_record_kernel<<<(unsigned)((nb + 255) / 256), 256, 0, st>>>(partial, n_chunks, (int)nb, bseq, rec_grad);
+    grad_v_scatter_kernel<<<(unsigned)((n_bvert + 255) / 256), 256, 0, st>>>(rec_grad, bvert, rec_off, recs, n_bvert,
+                                                                              grad_V);
+    return cudaGetLastError();
+}
+
+}  // namespace gwn

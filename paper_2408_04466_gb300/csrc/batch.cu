@@ -1,0 +1,315 @@
+// batch.cu -- host side of the 2D evaluation: one chain set on one grid
+// (gwn_eval), and many independent chains each on its own grid in one
+// persistent launch (gwn_eval_batch) with an autotuned work-item shape and a
+// CUDA graph replayed on later calls.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <map>
+#include <new>
+#include <vector>
+
+#include "gwn_internal.h"
+
+namespace gwn {
+
+
+
+
+static const int64_t MAX_NX = 16384;
+
+// items (set, row block), most expensive sets first
+static void make_items(const std::vector<Set2D> &sets, int rows_per_item, std::vector<int2> &items) {
+    std::vector<std::pair<double, int>> order;
+    for (size_t s = 0; s < sets.size(); s++)
+        order.emplace_back(-(double)(sets[s].p_hi - sets[s].p_lo + 1) * (double)sets[s].nx, (int)s);
+    std::stable_sort(order.begin(), order.end());
+    items.clear();
+    for (auto &o : order) {
+        const Set2D &S = sets[o.second];
+        int64_t nb = (S.ny + rows_per_item - 1) / rows_per_item;
+        for (int64_t b = 0; b < nb; b++) items.push_back(make_int2(o.second, (int)b));
+    }
+}
+
+static void axis_fill(double lo, double hi, int64_t n, int dtype, char *dst) {
+    double step = n > 1 ? (hi - lo) / (double)(n - 1) : 0.0;
+    for (int64_t i = 0; i < n; i++) {
+        double v = n == 1 ? lo : lo + (double)i * step;
+        if (dtype == GWN_F64) ((double *)dst)[i] = v;
+        else ((float *)dst)[i] = (float)v;
+    }
+}
+
+gwn_status eval2d_single(gwn_geom *g, const QuerySrc &src, void *w_out, int32_t *chi_out, void *b_out,
+                         unsigned long long *cnt) {
+    gwn_ctx *ctx = g->ctx;
+    const ChainSet &cs = g->cs;
+    if (src.dims[0] > MAX_NX) { set_error("gwn_eval: 2D grids are limited to 16384 columns"); return GWN_E_UNSUPPORTED; }
+    Set2D S;
+    S.c_lo = 0;
+    S.c_hi = cs.n_chains;
+    S.p_lo = 0;
+    S.p_hi = cs.n_pieces;
+    S.nx = src.dims[0];
+    S.ny = src.dims[1];
+    S.ax = cs.dtype == GWN_F64 ? (const void *)src.ax64[0] : (const void *)src.ax[0];
+    S.ay = cs.dtype == GWN_F64 ? (const void *)src.ax64[1] : (const void *)src.ax[1];
+    S.out_off = 0;
+    const int rows = 1;
+    std::vector<Set2D> sets(1, S);
+    std::vector<int2> items;
+    make_items(sets, rows, items);
+    size_t bytes = sizeof(Set2D) + sizeof(int2) * items.size() + 64;
+    cudaError_t e;
+    char *buf = (char *)arena_get(ctx, 2, bytes, &e);
+    if (!buf) return cuda_fail(e, "2D work list");
+    unsigned long long *counter = (unsigned long long *)buf;
+    Set2D *d_sets = (Set2D *)(buf + 16);
+    int2 *d_items = (int2 *)(buf + 16 + sizeof(Set2D));
+    std::vector<char> host(bytes - 16);
+    memcpy(host.data(), &S, sizeof(Set2D));
+    memcpy(host.data() + sizeof(Set2D), items.data(), sizeof(int2) * items.size());
+    e = cudaMemcpyAsync(buf + 16, host.data(), sizeof(Set2D) + sizeof(int2) * items.size(), cudaMemcpyHostToDevice,
+                        ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "2D work list upload");
+    e = cudaStreamSynchronize(ctx->stream);   // host staging buffer is released below
+    if (e != cudaSuccess) return cuda_fail(e, "2D work list upload");
+    e = launch_eval2d_items(cs, d_sets, d_items, (int64_t)items.size(), counter, rows, 128, S.nx, w_out, chi_out,
+                            b_out, cnt, ctx->d_status, ctx->sm_count, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "2D evaluation");
+    return GWN_OK;
+}
+
+// ---- batched evaluation ------------------------------------------------------
+struct BatchPlan {
+    std::vector<double> key;         // grids + offsets fingerprint
+    int threads = 128, rows = 4;
+    void *dev = nullptr;             // axis tables + sets + items + counter
+    size_t dev_bytes = 0;
+    Set2D *d_sets = nullptr;
+    int2 *d_items = nullptr;
+    unsigned long long *d_counter = nullptr;
+    int64_t n_items = 0, max_nx = 0;
+    void *w_out = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t stream = nullptr;
+    float tuned_ms = 0.f;
+};
+
+struct BatchCache {
+    std::vector<BatchPlan *> plans;
+};
+
+void batch_cache_free(void *p) {
+    BatchCache *c = (BatchCache *)p;
+    for (BatchPlan *b : c->plans) {
+        if (b->exec) cudaGraphExecDestroy(b->exec);
+        if (b->graph) cudaGraphDestroy(b->graph);
+        if (b->dev) cudaFree(b->dev);
+        delete b;
+    }
+    delete c;
+}
+
+static gwn_status plan_upload(gwn_geom *g, const gwn_queries *qs, int64_t n, const int64_t *out_off,
+                              BatchPlan *P, int rows) {
+    const ChainSet &cs = g->cs;
+    size_t esz = cs.dtype == GWN_F64 ? 8 : 4;
+    std::vector<Set2D> sets(n);
+    size_t axis_bytes = 0;
+    for (int64_t c = 0; c < n; c++) axis_bytes += esz * (qs[c].dims[0] + qs[c].dims[1]);
+    axis_bytes = (axis_bytes + 255) & ~(size_t)255;
+    std::vector<int2> items;
+    int64_t max_nx = 0;
+    for (int64_t c = 0; c < n; c++) {
+        sets[c].nx = qs[c].dims[0];
+        sets[c].ny = qs[c].dims[1];
+        sets[c].c_lo = c;
+        sets[c].c_hi = c + 1;
+        sets[c].p_lo = cs.h_chain_piece_off[c];
+        sets[c].p_hi = cs.h_chain_piece_off[c + 1];
+        sets[c].out_off = out_off[c];
+        max_nx = std::max(max_nx, sets[c].nx);
+    }
+    make_items(sets, rows, items);
+    size_t sets_off = axis_bytes, items_off = sets_off + sizeof(Set2D) * n;
+    size_t ctr_off = (items_off + sizeof(int2) * items.size() + 15) & ~(size_t)15;
+    size_t total = ctr_off + 16;
+    if (P->dev) { cudaFree(P->dev); P->dev = nullptr; }
+    cudaError_t e = cudaMalloc(&P->dev, total);
+    if (e != cudaSuccess) return cuda_fail(e, "batch plan");
+    std::vector<char> host(total, 0);
+    size_t off = 0;
+    for (int64_t c = 0; c < n; c++) {
+        axis_fill(qs[c].lo[0], qs[c].hi[0], qs[c].dims[0], cs.dtype, host.data() + off);
+        sets[c].ax = (char *)P->dev + off;
+        off += esz * qs[c].dims[0];
+        axis_fill(qs[c].lo[1], qs[c].hi[1], qs[c].dims[1], cs.dtype, host.data() + off);
+        sets[c].ay = (char *)P->dev + off;
+        off += esz * qs[c].dims[1];
+    }
+    memcpy(host.data() + sets_off, sets.data(), sizeof(Set2D) * n);
+    memcpy(host.data() + items_off, items.data(), sizeof(int2) * items.size());
+    e = cudaMemcpy(P->dev, host.data(), total, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "batch plan upload");
+    P->dev_bytes = total;
+    P->d_sets = (Set2D *)((char *)P->dev + sets_off);
+    P->d_items = (int2 *)((char *)P->dev + items_off);
+    P->d_counter = (unsigned long long *)((char *)P->dev + ctr_off);
+    P->n_items = (int64_t)items.size();
+    P->max_nx = max_nx;
+    P->rows = rows;
+    return GWN_OK;
+}
+
+}  // namespace gwn
+
+using namespace gwn;
+
+extern "C" GWN_API gwn_status gwn_eval_batch(gwn_geom *g, const gwn_queries *queries, int64_t n_chains,
+                                             const int64_t *out_offsets, void *w_out, const gwn_plan *plan,
+                                             gwn_stats *stats) {
+    if (!g || g->kind != GWN_GEOM_BEZIER2D || !queries || !out_offsets || !w_out) {
+        set_error("gwn_eval_batch: bad arguments");
+        return GWN_E_INVALID;
+    }
+    if (n_chains != g->cs.n_chains) { set_error("gwn_eval_batch: one query grid per chain is required"); return GWN_E_INVALID; }
+    for (int64_t c = 0; c < n_chains; c++) {
+        const gwn_queries &q = queries[c];
+        if (q.kind != GWN_QUERY_GRID || q.dim != 2 || q.dims[0] < 1 || q.dims[1] < 1 || q.dims[0] > MAX_NX ||
+            q.dims[1] > (1 << 24) || out_offsets[c] < 0) {
+            set_error("gwn_eval_batch: every chain needs a 2D grid (at most 16384 columns)");
+            return GWN_E_INVALID;
+        }
+    }
+    gwn_ctx *ctx = g->ctx;
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    if (!g->batch_cache) g->batch_cache = new (std::nothrow) BatchCache();
+    if (!g->batch_cache) { set_error("gwn_eval_batch: out of host memory"); return GWN_E_OOM; }
+    BatchCache *C = (BatchCache *)g->batch_cache;
+    // fingerprint of the request
+    std::vector<double> key;
+    key.reserve(6 * n_chains + 4);
+    for (int64_t c = 0; c < n_chains; c++) {
+        key.push_back(queries[c].lo[0]); key.push_back(queries[c].lo[1]);
+        key.push_back(queries[c].hi[0]); key.push_back(queries[c].hi[1]);
+        key.push_back((double)queries[c].dims[0]); key.push_back((double)queries[c].dims[1]);
+        key.push_back((double)out_offsets[c]);
+    }
+    int want_threads = plan && plan->threads_per_block > 0 ? plan->threads_per_block : 0;
+    int want_rows = plan && plan->rows_per_item > 0 ? plan->rows_per_item : 0;
+    int use_graph = plan ? plan->use_graph : 1;
+    key.push_back((double)want_threads);
+    key.push_back((double)want_rows);
+    BatchPlan *P = nullptr;
+    for (BatchPlan *b : C->plans)
+        if (b->key == key) P = b;
+    if (!P) {
+        P = new (std::nothrow) BatchPlan();
+        if (!P) { set_error("gwn_eval_batch: out of host memory"); return GWN_E_OOM; }
+        P->key = key;
+        // autotune: time each candidate shape once (after a warm-up) on the
+        // real work list and keep the fastest
+        std::vector<std::pair<int, int>> cands;
+        if (want_threads && want_rows) cands.emplace_back(want_threads, want_rows);
+        else {
+            int ts[2] = {128, 256};
+            int rs[4] = {1, 2, 4, 8};
+            for (int t : ts)
+                for (int r : rs)
+                    if ((!want_threads || t == want_threads) && (!want_rows || r == want_rows)) cands.emplace_back(t, r);
+        }
+        float best = 1e30f;
+        int bt = cands[0].first, br = cands[0].second;
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        for (auto &cd : cands) {
+            gwn_status s = plan_upload(g, queries, n_chains, out_offsets, P, cd.second);
+            if (s != GWN_OK) { delete P; cudaEventDestroy(e0); cudaEventDestroy(e1); return s; }
+            float ms = 0.f;
+            for (int rep = 0; rep < 2; rep++) {
+                cudaEventRecord(e0, ctx->stream);
+                e = launch_eval2d_items(g->cs, P->d_sets, P->d_items, P->n_items, P->d_counter, cd.second, cd.first,
+                                        P->max_nx, w_out, nullptr, nullptr, nullptr, ctx->d_status, ctx->sm_count,
+                                        ctx->stream);
+                cudaEventRecord(e1, ctx->stream);
+                if (e != cudaSuccess) break;
+                cudaEventSynchronize(e1);
+                cudaEventElapsedTime(&ms, e0, e1);
+            }
+            if (e != cudaSuccess) { delete P; cudaEventDestroy(e0); cudaEventDestroy(e1); return cuda_fail(e, "autotune"); }
+            if (ms < best) { best = ms; bt = cd.first; br = cd.second; }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        gwn_status s = plan_upload(g, queries, n_chains, out_offsets, P, br);
+        if (s != GWN_OK) { delete P; return s; }
+        P->threads = bt;
+        P->tuned_ms = best;
+        C->plans.push_back(P);
+    }
+    if (stats) {
+        memset(stats, 0, sizeof(*stats));
+        cudaEventRecord(ctx->ev[0], ctx->stream);
+    }
+    bool graph_ok = use_graph && P->w_out == w_out && P->stream == ctx->stream && P->exec;
+    if (use_graph && !graph_ok) {
+        if (P->exec) { cudaGraphExecDestroy(P->exec); P->exec = nullptr; }
+        if (P->graph) { cudaGraphDestroy(P->graph); P->graph = nullptr; }
+        cudaStream_t cap = ctx->stream;
+        bool own = false;
+        if (cap == nullptr) {    // the legacy stream cannot be captured
+            e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+            if (e != cudaSuccess) return cuda_fail(e, "capture stream");
+            own = true;
+        }
+        e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaError_t le = launch_eval2d_items(g->cs, P->d_sets, P->d_items, P->n_items, P->d_counter, P->rows,
+                                                 P->threads, P->max_nx, w_out, nullptr, nullptr, nullptr,
+                                                 ctx->d_status, ctx->sm_count, cap);
+            e = cudaStreamEndCapture(cap, &P->graph);
+            if (le != cudaSuccess) e = le;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&P->exec, P->graph, 0);
+        if (own) cudaStreamDestroy(cap);
+        if (e != cudaSuccess) return cuda_fail(e, "graph capture");
+        P->w_out = w_out;
+        P->stream = ctx->stream;
+    }
+    if (use_graph) e = cudaGraphLaunch(P->exec, ctx->stream);
+    else
+        e = launch_eval2d_items(g->cs, P->d_sets, P->d_items, P->n_items, P->d_counter, P->rows, P->threads, P->max_nx,
+                                w_out, nullptr, nullptr, nullptr, ctx->d_status, ctx->sm_count, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "batched launch");
+    if (stats) {
+        cudaEventRecord(ctx->ev[3], ctx->stream);
+        e = cudaEventSynchronize(ctx->ev[3]);
+        if (e != cudaSuccess) return cuda_fail(e, "sync");
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[3]);
+        int64_t nq = 0;
+        for (int64_t c = 0; c < n_chains; c++) nq += queries[c].dims[0] * queries[c].dims[1];
+        stats->n_queries = nq;
+        stats->n_pairs = g->cs.n_pieces;
+        stats->ms_boundary = ms;
+        stats->ms_total = ms;
+        stats->ms_prepare = P->tuned_ms;
+    }
+    return GWN_OK;
+}
+
+extern "C" GWN_API gwn_status gwn_batch_plan_get(gwn_geom *g, int32_t *threads, int32_t *rows) {
+    if (!g || !g->batch_cache) { set_error("gwn_batch_plan_get: no batched plan yet"); return GWN_E_INVALID; }
+    BatchCache *C = (BatchCache *)g->batch_cache;
+    if (C->plans.empty()) { set_error("gwn_batch_plan_get: no batched plan yet"); return GWN_E_INVALID; }
+    if (threads) *threads = C->plans.back()->threads;
+    if (rows) *rows = C->plans.back()->rows;
+    return GWN_OK;
+}

@@ -1,0 +1,279 @@
+// bezier2d.cu -- one-shot winding numbers of open cubic Bezier chains on
+// regular grids, with one ray (+x) per grid row.
+//
+// For an open chain C from s to e, closing it with the chord e -> s gives a
+// closed curve whose winding number at p is the signed crossing count of any
+// ray from p; hence, relative to the +x ray,
+//     w_C(p) = chi_x(C; p) + chi_x(chord e->s; p)
+//              + (1/2pi) atan2(cross(s-p, e-p), dot(s-p, e-p)),
+// the last term being minus the angle the chord subtends.  (Algorithm 1 in 2D:
+// the boundary is the two end points, the circle has two arcs, and the arc
+// areas and pairwise difference collapse to this form.)
+//
+// All queries of one grid row share the ray direction and the ray line, so
+// the crossings of that line with the chain are computed once per row and
+// every query counts the crossings to its right (the "Optimization" of the
+// one-shot algorithm: one ray serves all points on it).
+//
+// Crossings: each segment is split on the host into y-monotone pieces at the
+// roots of dy/du.  A piece with end values y0, y1 is crossed by the row y_r
+// iff min(y0,y1) <= y_r < max(y0,y1) (the ray is taken infinitesimally above
+// the row, which makes shared end points count once); its direction is
+// sign(y1 - y0) (the curve's normal is the tangent turned clockwise: Eq. chi
+// counts +1 where the curve crosses the ray upward).  The crossing parameter
+// is found by safeguarded Newton iteration on the monotone piece, in the
+// chain's precision.
+//
+// Work: a persistent kernel pops work items (set, block of rows) from an
+// atomic counter.  Per row, pieces are scanned in chunks of at most
+// CHUNK pieces (each contributes at most one crossing), crossings are
+// collected in shared memory, and every query of the row adds the signed
+// crossings to its right.  The epilogue adds the chord terms and writes w.
+#include "gwn_internal.h"
+
+namespace gwn {
+
+template <typename T> struct Num;
+template <> struct Num<float> {
+    static __device__ __forceinline__ float atan2_(float y, float x) { return atan2f(y, x); }
+    static constexpr float inv2pi = 0.15915494309189535f;
+    static constexpr int max_iter = 60;
+    static constexpr float tol = 1e-7f;
+};
+template <> struct Num<double> {
+    static __device__ __forceinline__ double atan2_(double y, double x) { return atan2(y, x); }
+    static constexpr double inv2pi = 0.15915494309189533577;
+    static constexpr int max_iter = 200;
+    static constexpr double tol = 1e-16;
+};
+
+template <typename T>
+__device__ __forceinline__ T bern(T p0, T p1, T p2, T p3, T u) {
+    T v = T(1) - u;
+    return v * v * v * p0 + T(3) * u * v * v * p1 + T(3) * u * u * v * p2 + u * u * u * p3;
+}
+template <typename T>
+__device__ __forceinline__ T dbern(T p0, T p1, T p2, T p3, T u) {
+    T v = T(1) - u;
+    return T(3) * (v * v * (p1 - p0) + T(2) * u * v * (p2 - p1) + u * u * (p3 - p2));
+}
+
+// x of the crossing of the monotone piece [u0, u1] of the segment with
+// control points c[0..7] (x0 y0 x1 y1 ...) with the row y = yr.
+template <typename T>
+__device__ T piece_root_x(const T *c, T u0, T u1, T ya, T yb, T yr, int *iters_out) {
+    // orient the bracket so that g(lo) <= 0 < g(hi) with g = y(u) - yr
+    T lo = u0, hi = u1;
+    bool inc = yb > ya;
+    if (!inc) { lo = u1; hi = u0; }
+    T yl = inc ? ya : yb, yh = inc ? yb : ya;
+    T u = lo + (hi - lo) * ((yr - yl) / (yh - yl));
+    int it = 0;
+    for (; it < Num<T>::max_iter; it++) {
+        T g = bern(c[1], c[3], c[5], c[7], u) - yr;
+        if (g <= T(0)) lo = u; else hi = u;
+        T dg = dbern(c[1], c[3], c[5], c[7], u);
+        T un = u - g / dg;
+        T mn = lo < hi ? lo : hi, mx = lo < hi ? hi : lo;
+        if (!(un > mn && un < mx)) un = T(0.5) * (lo + hi);
+        T step = un - u;
+        u = un;
+        if ((step < T(0) ? -step : step) <= Num<T>::tol || (mx - mn) <= Num<T>::tol) break;
+    }
+    *iters_out = it;
+    return bern(c[0], c[2], c[4], c[6], u);
+}
+
+
+constexpr int CHUNK = 1024;
+
+template <typename T>
+__global__ void eval2d_kernel(const T *__restrict__ ctrl, const int64_t *__restrict__ chain_off,
+                              const int64_t *__restrict__ piece_seg, const double *__restrict__ piece_u,
+                              const double *__restrict__ piece_y, const Set2D *__restrict__ sets,
+                              const int2 *__restrict__ items, int64_t n_items, unsigned long long *counter,
+                              int rows_per_item, T *__restrict__ w_out, int32_t *__restrict__ chi_out,
+                              T *__restrict__ b_out, unsigned long long *cnt, int *status, int max_nx) {
+    extern __shared__ unsigned char smem_raw[];
+    T *xs = (T *)smem_raw;                                    // CHUNK crossings
+    int *dirs = (int *)(xs + CHUNK);                          // CHUNK directions
+    int *chi_row = dirs + CHUNK;                              // max_nx counts
+    __shared__ int ncross;
+    __shared__ long long item_sh;
+    for (int64_t guard = 0; guard <= n_items; guard++) {
+        if (threadIdx.x == 0) item_sh = (long long)atomicAdd(counter, 1ull);
+        __syncthreads();
+        long long item = item_sh;
+        __syncthreads();
+        if (item >= n_items) break;
+        int2 it = items[item];
+        const Set2D S = sets[it.x];
+        const T *ax = (const T *)S.ax;
+        const T *ay = (const T *)S.ay;
+        int64_t r0 = (int64_t)it.y * rows_per_item;
+        int64_t r1 = r0 + rows_per_item < S.ny ? r0 + rows_per_item : S.ny;
+        for (int64_t r = r0; r < r1; r++) {
+            T yr = ay[r];
+            for (int64_t i = threadIdx.x; i < S.nx; i += blockDim.x) chi_row[i] = 0;
+            for (int64_t c0 = S.p_lo; c0 < S.p_hi; c0 += CHUNK) {
+                if (threadIdx.x == 0) ncross = 0;
+                __syncthreads();
+                int64_t c1 = c0 + CHUNK < S.p_hi ? c0 + CHUNK : S.p_hi;
+                for (int64_t p = c0 + threadIdx.x; p < c1; p += blockDim.x) {
+                    T ya = (T)piece_y[2 * p], yb = (T)piece_y[2 * p + 1];
+                    T lo = ya < yb ? ya : yb, hi = ya < yb ? yb : ya;
+                    if (!(lo <= yr && yr < hi)) continue;
+                    const T *cp = ctrl + 2 * piece_seg[p];
+                    T c[8];
+#pragma unroll
+                    for (int k = 0; k < 8; k++) c[k] = cp[k];
+                    int iters;
+                    T x = piece_root_x<T>(c, (T)piece_u[2 * p], (T)piece_u[2 * p + 1], ya, yb, yr, &iters);
+                    if (iters >= Num<T>::max_iter && status) atomicOr(status, ST_TIMEOUT);
+                    int slot = atomicAdd(&ncross, 1);
+                    xs[slot] = x;
+                    dirs[slot] = yb > ya ? 1 : -1;
+                    if (cnt) atomicAdd(&cnt[CNT_ROOTS], 1ull);
+                }
+                __syncthreads();
+                int nc = ncross;
+                if (nc > 0) {
+                    for (int64_t i = threadIdx.x; i < S.nx; i += blockDim.x) {
+                        T xq = ax[i];
+                        int acc = 0;
+                        for (int k = 0; k < nc; k++) acc += xs[k] > xq ? dirs[k] : 0;
+                        chi_row[i] += acc;
+                    }
+                }
+                __syncthreads();
+            }
+            // epilogue: chord terms of every chain of the set
+            for (int64_t i = threadIdx.x; i < S.nx; i += blockDim.x) {
+                T xq = ax[i];
+                int chi = chi_row[i];
+                T term = T(0);
+                for (int64_t c = S.c_lo; c < S.c_hi; c++) {
+                    const T *sp = ctrl + 2 * chain_off[c];
+                    const T *ep = ctrl + 2 * (chain_off[c + 1] - 1);
+                    T sx = sp[0] - xq, sy = sp[1] - yr, ex = ep[0] - xq, ey = ep[1] - yr;
+                    // chord e -> s against the +x ray (half-open in y)
+                    T cr = ex * sy - ey * sx;             // cross(e - p, s - p)
+                    T lo = ey < sy ? ey : sy, hi = ey < sy ? sy : ey;
+                    if (lo <= T(0) && T(0) < hi) {
+                        bool up = sy > ey;
+                        bool right = up ? (cr > T(0)) : (cr < T(0));
+                        if (right) chi += up ? 1 : -1;
+                    }
+                    term += Num<T>::atan2_(-cr, sx * ex + sy * ey) * Num<T>::inv2pi;
+                }
+                int64_t o = S.out_off + r * S.nx + i;
+                if (w_out) w_out[o] = (T)chi + term;
+                if (chi_out) chi_out[o] = chi;
+                if (b_out) b_out[o] = term;
+            }
+            __syncthreads();
+        }
+    }
+}
+
+size_t eval2d_smem(int dtype, int64_t max_nx) {
+    size_t esz = dtype == GWN_F64 ? 8 : 4;
+    return esz * CHUNK + sizeof(int) * CHUNK + sizeof(int) * (size_t)max_nx;
+}
+
+cudaError_t launch_eval2d_items(const ChainSet &cs, const Set2D *d_sets, const int2 *d_items, int64_t n_items,
+                                unsigned long long *d_counter, int rows_per_item, int threads, int64_t max_nx,
+                                void *w_out, int32_t *chi_out, void *b_out, unsigned long long *cnt, int *status,
+                                int sm_count, cudaStream_t st) {
+    if (n_items == 0) return cudaSuccess;
+    size_t smem = eval2d_smem(cs.dtype, max_nx);
+    cudaError_t e = cudaMemsetAsync(d_counter, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+    int per_sm = threads <= 128 ? 8 : 4;
+    int64_t blocks = (int64_t)sm_count * per_sm;
+    if (blocks > n_items) blocks = n_items;
+    if (cs.dtype == GWN_F64) {
+        if (smem > 48 * 1024)
+            cudaFuncSetAttribute(eval2d_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        eval2d_kernel<double><<<(unsigned)blocks, threads, smem, st>>>(
+            (const double *)cs.ctrl, cs.chain_off, cs.piece_seg, cs.piece_u, cs.piece_y, d_sets, d_items, n_items,
+            d_counter, rows_per_item, (double *)w_out, chi_out, (double *)b_out, cnt, status, (int)max_nx);
+    } else {
+        if (smem > 48 * 1024)
+            cudaFuncSetAttribute(eval2d_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        eval2d_kernel<float><<<(unsigned)blocks, threads, smem, st>>>(
+            (const float *)cs.ctrl, cs.chain_off, cs.piece_seg, cs.piece_u, cs.piece_y, d_sets, d_items, n_items,
+            d_counter, rows_per_item, (float *)w_out, chi_out, (float *)b_out, cnt, status, (int)max_nx);
+    }
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// brute-force comparator: per (query, segment) the subtended angle by
+// Gauss-Legendre quadrature on 2^L equal subintervals, L doubled until two
+// consecutive levels agree to the working tolerance (capped).
+// ---------------------------------------------------------------------------
+__constant__ double GL8_X[8] = {-0.9602898564975363, -0.7966664774136267, -0.5255324099163290, -0.1834346424956498,
+                                0.1834346424956498, 0.5255324099163290, 0.7966664774136267, 0.9602898564975363};
+__constant__ double GL8_W[8] = {0.1012285362903763, 0.2223810344533745, 0.3137066458778873, 0.3626837833783620,
+                                0.3626837833783620, 0.3137066458778873, 0.2223810344533745, 0.1012285362903763};
+
+template <typename T>
+__device__ T seg_angle_gl(const T *c, T px, T py, int nsub) {
+    T acc = T(0);
+    T h = T(1) / (T)nsub;
+    for (int s = 0; s < nsub; s++) {
+        T a = s * h;
+        for (int k = 0; k < 8; k++) {
+            T u = a + T(0.5) * h * (T(1) + (T)GL8_X[k]);
+            T x = bern(c[0], c[2], c[4], c[6], u) - px, y = bern(c[1], c[3], c[5], c[7], u) - py;
+            T dx = dbern(c[0], c[2], c[4], c[6], u), dy = dbern(c[1], c[3], c[5], c[7], u);
+            acc += (T)GL8_W[k] * (x * dy - y * dx) / (x * x + y * y);
+        }
+    }
+    return acc * T(0.5) * h;
+}
+
+template <typename T>
+__global__ void bruteforce2d_kernel(const T *__restrict__ ctrl, const int64_t *__restrict__ chain_off, int64_t n_chains,
+                                    const T *__restrict__ ax, const T *__restrict__ ay, int64_t nx, int64_t n,
+                                    T *__restrict__ w_out, T tol) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    T px = ax[i % nx], py = ay[i / nx];
+    T total = T(0);
+    for (int64_t ch = 0; ch < n_chains; ch++) {
+        for (int64_t s = chain_off[ch]; s + 3 < chain_off[ch + 1]; s += 3) {
+            T c[8];
+            for (int k = 0; k < 8; k++) c[k] = ctrl[2 * s + k];
+            int nsub = 1;
+            T prev = seg_angle_gl<T>(c, px, py, nsub);
+            for (int lvl = 0; lvl < 10; lvl++) {
+                nsub *= 2;
+                T cur = seg_angle_gl<T>(c, px, py, nsub);
+                T dlt = cur - prev;
+                prev = cur;
+                if ((dlt < T(0) ? -dlt : dlt) <= tol) break;
+            }
+            total += prev;
+        }
+    }
+    w_out[i] = total * Num<T>::inv2pi;
+}
+
+cudaError_t launch_bruteforce2d(const ChainSet &cs, const QuerySrc &q, void *w_out, int sm_count, cudaStream_t st) {
+    (void)sm_count;
+    if (q.n == 0) return cudaSuccess;
+    int64_t blocks = (q.n + 127) / 128;
+    if (cs.dtype == GWN_F64)
+        bruteforce2d_kernel<double><<<(unsigned)blocks, 128, 0, st>>>((const double *)cs.ctrl, cs.chain_off,
+                                                                       cs.n_chains, q.ax64[0], q.ax64[1], q.dims[0],
+                                                                       q.n, (double *)w_out, 1e-13);
+    else
+        bruteforce2d_kernel<float><<<(unsigned)blocks, 128, 0, st>>>((const float *)cs.ctrl, cs.chain_off, cs.n_chains,
+                                                                      q.ax[0], q.ax[1], q.dims[0], q.n,
+                                                                      (float *)w_out, 1e-6f);
+    return cudaGetLastError();
+}
+
+}  // namespace gwn

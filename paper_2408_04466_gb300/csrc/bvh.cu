@@ -1,0 +1,452 @@
+// bvh.cu -- on-device LBVH over triangles in the frame of the ray direction.
+//
+// Steps (all on the context's stream):
+//   1. per triangle: frame coordinates (e1, e2, dh) of its vertices, a padded
+//      box (x0, x1, y0, y1, zmax) and its centroid;
+//   2. centroid bounds (block reduction + atomics on order-preserving ints);
+//   3. 63-bit Morton codes (21 bits per frame axis) of the centroids;
+//   4. stable LSD radix sort of (code, triangle) pairs, 8 bits per pass,
+//      passes whose digit is constant over all keys are skipped;
+//   5. binary radix tree from the sorted codes (Karras 2012: each internal
+//      node finds its key range by the longest-common-prefix search, ties of
+//      equal codes broken by the key index);
+//   6. bottom-up box refit: one thread per leaf climbs while it is the second
+//      child to arrive at a node (atomic counter per node);
+//   7. packing: each internal node stores both children's boxes and refs;
+//      triangles are re-laid out in sorted order as 3 float4.
+// The boxes are padded by a bound on the float32 rounding of the frame
+// coordinates (4e-7 times the vertex's 1-norm), so culling is conservative.
+#include <string.h>
+
+#include "gwn_internal.h"
+
+namespace gwn {
+
+namespace {
+
+constexpr int SORT_THREADS = 256;
+constexpr int SORT_ITEMS = 16;
+constexpr int SORT_TILE = SORT_THREADS * SORT_ITEMS;
+constexpr int BINS = 256;
+
+__device__ __forceinline__ unsigned f2ord(float f) {
+    unsigned u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float ord2f(unsigned u) {
+    return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
+}
+
+__global__ void tri_prep_kernel(const float *__restrict__ V, const int32_t *__restrict__ F, int64_t nf, Frame fr,
+                                float4 *__restrict__ box_xy, float *__restrict__ box_z,
+                                float4 *__restrict__ cen, unsigned *bounds) {
+    __shared__ unsigned smin[3], smax[3];
+    if (threadIdx.x < 3) { smin[threadIdx.x] = 0xffffffffu; smax[threadIdx.x] = 0u; }
+    __syncthreads();
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < nf) {
+        float x0 = 3.4e38f, x1 = -3.4e38f, y0 = 3.4e38f, y1 = -3.4e38f, z1 = -3.4e38f;
+        float cx = 0.f, cy = 0.f, cz = 0.f, pad = 0.f;
+        for (int k = 0; k < 3; k++) {
+            int vi = F[3 * t + k];
+            float vx = V[3 * (int64_t)vi], vy = V[3 * (int64_t)vi + 1], vz = V[3 * (int64_t)vi + 2];
+            float a = fmaf(vz, fr.e1[2], fmaf(vy, fr.e1[1], vx * fr.e1[0]));
+            float b = fmaf(vz, fr.e2[2], fmaf(vy, fr.e2[1], vx * fr.e2[0]));
+            float c = fmaf(vz, fr.dh[2], fmaf(vy, fr.dh[1], vx * fr.dh[0]));
+            x0 = fminf(x0, a); x1 = fmaxf(x1, a);
+            y0 = fminf(y0, b); y1 = fmaxf(y1, b);
+            z1 = fmaxf(z1, c);
+            cx += a; cy += b; cz += c;
+            pad = fmaxf(pad, fabsf(vx) + fabsf(vy) + fabsf(vz));
+        }
+        pad = pad * 4e-7f + 1e-30f;
+        box_xy[t] = make_float4(x0 - pad, x1 + pad, y0 - pad, y1 + pad);
+        box_z[t] = z1 + pad;
+        cx *= (1.f / 3.f); cy *= (1.f / 3.f); cz *= (1.f / 3.f);
+        cen[t] = make_float4(cx, cy, cz, 0.f);
+        atomicMin(&smin[0], f2ord(cx)); atomicMax(&smax[0], f2ord(cx));
+        atomicMin(&smin[1], f2ord(cy)); atomicMax(&smax[1], f2ord(cy));
+        atomicMin(&smin[2], f2ord(cz)); atomicMax(&smax[2], f2ord(cz));
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        atomicMin(&bounds[threadIdx.x], smin[threadIdx.x]);
+        atomicMax(&bounds[3 + threadIdx.x], smax[threadIdx.x]);
+    }
+}
+
+__device__ __forceinline__ unsigned long long spread21(unsigned v) {
+    unsigned long long x = v & 0x1fffffull;
+    x = (x | (x << 32)) & 0x1f00000000ffffull;
+    x = (x | (x << 16)) & 0x1f0000ff0000ffull;
+    x = (x | (x << 8)) & 0x100f00f00f00f00full;
+    x = (x | (x << 4)) & 0x10c30c30c30c30c3ull;
+    x = (x | (x << 2)) & 0x1249249249249249ull;
+    return x;
+}
+
+__global__ void morton_kernel(const float4 *__restrict__ cen, int64_t n, const unsigned *bounds,
+                              unsigned long long *__restrict__ keys, int32_t *__restrict__ vals) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    float lo[3], ext[3];
+    for (int k = 0; k < 3; k++) {
+        lo[k] = ord2f(bounds[k]);
+        ext[k] = ord2f(bounds[3 + k]) - lo[k];
+    }
+    float4 c = cen[t];
+    float cc[3] = {c.x, c.y, c.z};
+    unsigned long long code = 0;
+    for (int k = 0; k < 3; k++) {
+        float u = ext[k] > 0.f ? (cc[k] - lo[k]) / ext[k] : 0.f;
+        u = fminf(fmaxf(u, 0.f), 1.f);
+        unsigned q = (unsigned)(u * 2097151.0f);
+        code |= spread21(q) << k;
+    }
+    keys[t] = code;
+    vals[t] = (int32_t)t;
+}
+
+// ---- stable LSD radix sort --------------------------------------------------
+__global__ void hist_kernel(const unsigned long long *__restrict__ keys, int64_t n, int shift,
+                            unsigned *__restrict__ hist, int nblocks) {
+    __shared__ unsigned h[BINS];
+    for (int i = threadIdx.x; i < BINS; i += blockDim.x) h[i] = 0;
+    __syncthreads();
+    int64_t base = (int64_t)blockIdx.x * SORT_TILE;
+    for (int r = 0; r < SORT_ITEMS; r++) {
+        int64_t i = base + (int64_t)r * SORT_THREADS + threadIdx.x;
+        if (i < n) atomicAdd(&h[(unsigned)(keys[i] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < BINS; i += blockDim.x) hist[(int64_t)i * nblocks + blockIdx.x] = h[i];
+}
+
+// exclusive scan of `n` counts by one block (chunked, Hillis-Steele over the
+// per-thread chunk sums)
+__global__ void scan_kernel(unsigned *data, int64_t n) {
+    __shared__ unsigned long long partial[1024];
+    int tid = threadIdx.x;
+    int64_t chunk = (n + blockDim.x - 1) / blockDim.x;
+    int64_t lo = tid * chunk, hi = lo + chunk < n ? lo + chunk : n;
+    unsigned long long s = 0;
+    for (int64_t i = lo; i < hi; i++) s += data[i];
+    partial[tid] = s;
+    __syncthreads();
+    for (int off = 1; off < blockDim.x; off <<= 1) {
+        unsigned long long v = tid >= off ? partial[tid - off] : 0;
+        __syncthreads();
+        partial[tid] += v;
+        __syncthreads();
+    }
+    unsigned long long run = tid > 0 ? partial[tid - 1] : 0;
+    for (int64_t i = lo; i < hi; i++) {
+        unsigned v = data[i];
+        data[i] = (unsigned)run;
+        run += v;
+    }
+}
+
+// flags the pass as skippable when one digit value holds every key
+__global__ void bin_total_kernel(const unsigned *scanned, int nblocks, int64_t total, int *skip) {
+    int b = threadIdx.x;
+    if (b >= BINS) return;
+    unsigned long long start = scanned[(int64_t)b * nblocks];
+    unsigned long long end = b + 1 < BINS ? scanned[(int64_t)(b + 1) * nblocks] : (unsigned long long)total;
+    if (end - start == (unsigned long long)total) *skip = 1;
+}
+
+__global__ void scatter_kernel(const unsigned long long *__restrict__ kin, const int32_t *__restrict__ vin,
+                               unsigned long long *__restrict__ kout, int32_t *__restrict__ vout, int64_t n,
+                               int shift, const unsigned *__restrict__ scanned, int nblocks, const int *skip) {
+    __shared__ unsigned wcount[SORT_THREADS / 32][BINS + 1];
+    __shared__ unsigned running[BINS];
+    __shared__ unsigned dbase[BINS];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const bool skip_pass = *skip != 0;
+    int64_t base = (int64_t)blockIdx.x * SORT_TILE;
+    if (skip_pass) {   // copy through unchanged
+        for (int r = 0; r < SORT_ITEMS; r++) {
+            int64_t i = base + (int64_t)r * SORT_THREADS + threadIdx.x;
+            if (i < n) { kout[i] = kin[i]; vout[i] = vin[i]; }
+        }
+        return;
+    }
+    for (int i = threadIdx.x; i < BINS; i += blockDim.x) {
+        running[i] = 0;
+        dbase[i] = scanned[(int64_t)i * nblocks + blockIdx.x];
+    }
+    for (int i = threadIdx.x; i < (SORT_THREADS / 32) * (BINS + 1); i += blockDim.x) (&wcount[0][0])[i] = 0;
+    __syncthreads();
+    unsigned lanemask_lt = (1u << lane) - 1u;
+    for (int r = 0; r < SORT_ITEMS; r++) {
+        int64_t i = base + (int64_t)r * SORT_THREADS + threadIdx.x;
+        bool valid = i < n;
+        unsigned long long k = valid ? kin[i] : 0ull;
+        int32_t v = valid ? vin[i] : 0;
+        unsigned digit = valid ? ((unsigned)(k >> shift) & 255u) : (unsigned)BINS;
+        unsigned peers = __match_any_sync(0xffffffffu, digit);
+        unsigned rank = __popc(peers & lanemask_lt);
+        int leader = __ffs(peers) - 1;
+        if (lane == leader) wcount[warp][digit] = __popc(peers);
+        __syncthreads();
+        if (valid) {
+            unsigned off = 0;
+            for (int w = 0; w < warp; w++) off += wcount[w][digit];
+            unsigned pos = dbase[digit] + running[digit] + off + rank;
+            if ((int64_t)pos < n) {
+                kout[pos] = k;
+                vout[pos] = v;
+            }
+        }
+        __syncthreads();
+        for (int b = threadIdx.x; b < BINS; b += blockDim.x) {
+            unsigned s = 0;
+            for (int w = 0; w < SORT_THREADS / 32; w++) { s += wcount[w][b]; wcount[w][b] = 0; }
+            running[b] += s;
+        }
+        for (int w = 0; w < SORT_THREADS / 32; w++)
+            if (threadIdx.x == 0) wcount[w][BINS] = 0;
+        __syncthreads();
+    }
+}
+
+// ---- Karras binary radix tree ------------------------------------------------
+__device__ __forceinline__ int delta(const unsigned long long *keys, int64_t n, int64_t i, int64_t j) {
+    if (j < 0 || j >= n) return -1;
+    unsigned long long a = keys[i], b = keys[j];
+    if (a == b) return 64 + __clz((unsigned)(i ^ j));
+    return __clzll(a ^ b);
+}
+
+__global__ void karras_kernel(const unsigned long long *__restrict__ keys, int64_t n, int2 *__restrict__ child,
+                              int32_t *__restrict__ parent_int, int32_t *__restrict__ parent_leaf) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n - 1) return;
+    int dr = delta(keys, n, i, i + 1), dl = delta(keys, n, i, i - 1);
+    int d = dr > dl ? 1 : -1;
+    int dmin = d > 0 ? dl : dr;
+    int64_t lmax = 2;
+    while (delta(keys, n, i, i + lmax * d) > dmin) lmax <<= 1;
+    int64_t l = 0;
+    for (int64_t t = lmax >> 1; t >= 1; t >>= 1)
+        if (delta(keys, n, i, i + (l + t) * d) > dmin) l += t;
+    int64_t j = i + l * d;
+    int dnode = delta(keys, n, i, j);
+    int64_t s = 0;
+    int64_t t = l;
+    do {
+        t = (t + 1) >> 1;
+        if (delta(keys, n, i, i + (s + t) * d) > dnode) s += t;
+    } while (t > 1);
+    int64_t gamma = i + s * d + (d < 0 ? -1 : 0);
+    int64_t lo = i < j ? i : j, hi = i < j ? j : i;
+    int left = (lo == gamma) ? ~(int)gamma : (int)gamma;
+    int right = (hi == gamma + 1) ? ~(int)(gamma + 1) : (int)(gamma + 1);
+    child[i] = make_int2(left, right);
+    if (left < 0) parent_leaf[~left] = (int32_t)i; else parent_int[left] = (int32_t)i;
+    if (right < 0) parent_leaf[~right] = (int32_t)i; else parent_int[right] = (int32_t)i;
+    if (i == 0) parent_int[0] = -1;
+}
+
+struct Box5 { float x0, x1, y0, y1, z1; };
+
+__device__ __forceinline__ bool ref_ok(int r, int64_t n) { return r < 0 ? (int64_t)(~r) < n : (int64_t)r < n - 1; }
+
+__device__ __forceinline__ Box5 load_box(const float4 *xy, const float *z, int64_t i) {
+    float4 a = __ldcg(&xy[i]);
+    Box5 b = {a.x, a.y, a.z, a.w, __ldcg(&z[i])};
+    return b;
+}
+
+__global__ void refit_kernel(const int32_t *__restrict__ sorted_tri, int64_t n, const float4 *__restrict__ tbox_xy,
+                             const float *__restrict__ tbox_z, const int2 *__restrict__ child,
+                             const int32_t *__restrict__ parent_int, const int32_t *__restrict__ parent_leaf,
+                             float4 *leaf_xy, float *leaf_z, float4 *int_xy, float *int_z, unsigned *flags) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    int t = sorted_tri[k];
+    float4 bx = tbox_xy[t];
+    float bz = tbox_z[t];
+    __stcg(&leaf_xy[k], bx);
+    __stcg(&leaf_z[k], bz);
+    __threadfence();
+    int node = parent_leaf[k];
+    for (int64_t guard = 0; node >= 0 && node < n - 1 && guard < n; guard++) {
+        unsigned old = atomicAdd(&flags[node], 1u);
+        if (old == 0) return;          // first arrival: the sibling finishes
+        __threadfence();
+        int2 c = child[node];
+        if (!ref_ok(c.x, n) || !ref_ok(c.y, n)) return;
+        Box5 a = c.x < 0 ? load_box(leaf_xy, leaf_z, ~c.x) : load_box(int_xy, int_z, c.x);
+        Box5 b = c.y < 0 ? load_box(leaf_xy, leaf_z, ~c.y) : load_box(int_xy, int_z, c.y);
+        float4 u = make_float4(fminf(a.x0, b.x0), fmaxf(a.x1, b.x1), fminf(a.y0, b.y0), fmaxf(a.y1, b.y1));
+        __stcg(&int_xy[node], u);
+        __stcg(&int_z[node], fmaxf(a.z1, b.z1));
+        __threadfence();
+        node = parent_int[node];
+    }
+}
+
+__global__ void pack_kernel(const int2 *__restrict__ child, int64_t n, const float4 *__restrict__ leaf_xy,
+                            const float *__restrict__ leaf_z, const float4 *__restrict__ int_xy,
+                            const float *__restrict__ int_z, BvhNode *__restrict__ nodes) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n - 1) return;
+    int2 c = child[i];
+    if (!ref_ok(c.x, n) || !ref_ok(c.y, n)) {   // never dereference a corrupt reference
+        BvhNode bad;
+        bad.lo = bad.hi = make_float4(1.f, -1.f, 1.f, -1.f);
+        bad.z = make_float4(-3.4e38f, -3.4e38f, __int_as_float(~0), __int_as_float(~0));
+        nodes[i] = bad;
+        return;
+    }
+    float4 a = c.x < 0 ? leaf_xy[~c.x] : int_xy[c.x];
+    float4 b = c.y < 0 ? leaf_xy[~c.y] : int_xy[c.y];
+    float za = c.x < 0 ? leaf_z[~c.x] : int_z[c.x];
+    float zb = c.y < 0 ? leaf_z[~c.y] : int_z[c.y];
+    BvhNode nd;
+    nd.lo = a;
+    nd.hi = b;
+    nd.z = make_float4(za, zb, __int_as_float(c.x), __int_as_float(c.y));
+    nodes[i] = nd;
+}
+
+__global__ void tris_kernel(const float *__restrict__ V, const int32_t *__restrict__ F,
+                            const int32_t *__restrict__ sorted_tri, int64_t n, float4 *__restrict__ tris) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    int t = sorted_tri[k];
+    for (int c = 0; c < 3; c++) {
+        int vi = F[3 * (int64_t)t + c];
+        tris[3 * k + c] = make_float4(V[3 * (int64_t)vi], V[3 * (int64_t)vi + 1], V[3 * (int64_t)vi + 2], 0.f);
+    }
+}
+
+__global__ void radius_kernel(const float *__restrict__ V, int64_t nv, unsigned *out) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    float r = 0.f;
+    if (i < nv) {
+        float x = V[3 * i], y = V[3 * i + 1], z = V[3 * i + 2];
+        r = sqrtf(x * x + y * y + z * z) * 1.000001f;
+    }
+    for (int o = 16; o > 0; o >>= 1) r = fmaxf(r, __shfl_xor_sync(0xffffffffu, r, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(r));
+}
+
+inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+void bvh_free(MeshBvh &b) {
+    if (b.nodes) cudaFree(b.nodes);
+    if (b.tris) cudaFree(b.tris);
+    if (b.tri_id) cudaFree(b.tri_id);
+    b.nodes = nullptr;
+    b.tris = nullptr;
+    b.tri_id = nullptr;
+    b.valid = false;
+}
+
+#define GWN_TRY(x)                           \
+    do {                                     \
+        cudaError_t e_ = (x);                \
+        if (e_ != cudaSuccess) { err = e_; goto done; } \
+    } while (0)
+
+cudaError_t bvh_build(gwn_geom *g, const Frame &fr, cudaStream_t st) {
+    cudaError_t err = cudaSuccess;
+    MeshBvh &b = g->bvh;
+    bvh_free(b);
+    const int64_t n = g->nf;
+    b.n = n;
+    b.frame = fr;
+    for (int k = 0; k < 3; k++) b.dkey[k] = fr.d[k];
+    // temporaries
+    float4 *tbox_xy = nullptr, *cen = nullptr, *leaf_xy = nullptr, *int_xy = nullptr;
+    float *tbox_z = nullptr, *leaf_z = nullptr, *int_z = nullptr;
+    unsigned *bounds = nullptr, *hist = nullptr, *flags = nullptr, *rad = nullptr;
+    unsigned long long *k0 = nullptr, *k1 = nullptr;
+    int32_t *v0 = nullptr, *v1 = nullptr, *parent_int = nullptr, *parent_leaf = nullptr;
+    int2 *child = nullptr;
+    int *skip = nullptr;
+    int nblocks = (int)((n + SORT_TILE - 1) / SORT_TILE);
+    if (n == 0) {
+        b.valid = true;
+        return cudaSuccess;
+    }
+    GWN_TRY(cudaMalloc(&b.tris, sizeof(float4) * 3 * n));
+    GWN_TRY(cudaMalloc(&b.tri_id, sizeof(int32_t) * n));
+    GWN_TRY(cudaMalloc(&tbox_xy, sizeof(float4) * n));
+    GWN_TRY(cudaMalloc(&tbox_z, sizeof(float) * n));
+    GWN_TRY(cudaMalloc(&cen, sizeof(float4) * n));
+    GWN_TRY(cudaMalloc(&bounds, sizeof(unsigned) * 8));
+    GWN_TRY(cudaMalloc(&rad, sizeof(unsigned)));
+    GWN_TRY(cudaMalloc(&k0, sizeof(unsigned long long) * n));
+    GWN_TRY(cudaMalloc(&k1, sizeof(unsigned long long) * n));
+    GWN_TRY(cudaMalloc(&v0, sizeof(int32_t) * n));
+    GWN_TRY(cudaMalloc(&v1, sizeof(int32_t) * n));
+    GWN_TRY(cudaMalloc(&hist, sizeof(unsigned) * (size_t)BINS * nblocks));
+    GWN_TRY(cudaMalloc(&skip, sizeof(int)));
+    {
+        unsigned init[8] = {0xffffffffu, 0xffffffffu, 0xffffffffu, 0u, 0u, 0u, 0u, 0u};
+        GWN_TRY(cudaMemcpyAsync(bounds, init, sizeof(init), cudaMemcpyHostToDevice, st));
+        GWN_TRY(cudaMemsetAsync(rad, 0, sizeof(unsigned), st));
+        radius_kernel<<<blocks_for(g->nv, 256), 256, 0, st>>>(g->dV, g->nv, rad);
+        tri_prep_kernel<<<blocks_for(n, 256), 256, 0, st>>>(g->dV, g->dF, n, fr, tbox_xy, tbox_z, cen, bounds);
+        morton_kernel<<<blocks_for(n, 256), 256, 0, st>>>(cen, n, bounds, k0, v0);
+        GWN_TRY(cudaGetLastError());
+        for (int pass = 0; pass < 8; pass++) {
+            int shift = pass * 8;
+            hist_kernel<<<nblocks, SORT_THREADS, 0, st>>>(k0, n, shift, hist, nblocks);
+            scan_kernel<<<1, 1024, 0, st>>>(hist, (int64_t)BINS * nblocks);
+            GWN_TRY(cudaMemsetAsync(skip, 0, sizeof(int), st));
+            bin_total_kernel<<<1, BINS, 0, st>>>(hist, nblocks, n, skip);
+            scatter_kernel<<<nblocks, SORT_THREADS, 0, st>>>(k0, v0, k1, v1, n, shift, hist, nblocks, skip);
+            GWN_TRY(cudaGetLastError());
+            unsigned long long *tk = k0; k0 = k1; k1 = tk;
+            int32_t *tv = v0; v0 = v1; v1 = tv;
+        }
+        GWN_TRY(cudaMemcpyAsync(b.tri_id, v0, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, st));
+        tris_kernel<<<blocks_for(n, 256), 256, 0, st>>>(g->dV, g->dF, v0, n, b.tris);
+        GWN_TRY(cudaGetLastError());
+        unsigned rbits = 0;
+        GWN_TRY(cudaMemcpyAsync(&rbits, rad, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+        GWN_TRY(cudaStreamSynchronize(st));
+        float rr;
+        memcpy(&rr, &rbits, sizeof(float));
+        b.scene_radius = rr;
+        if (n == 1) {
+            b.root = ~0;
+            b.valid = true;
+            goto done;
+        }
+        GWN_TRY(cudaMalloc(&b.nodes, sizeof(BvhNode) * (n - 1)));
+        GWN_TRY(cudaMalloc(&child, sizeof(int2) * (n - 1)));
+        GWN_TRY(cudaMalloc(&parent_int, sizeof(int32_t) * (n - 1)));
+        GWN_TRY(cudaMalloc(&parent_leaf, sizeof(int32_t) * n));
+        GWN_TRY(cudaMalloc(&leaf_xy, sizeof(float4) * n));
+        GWN_TRY(cudaMalloc(&leaf_z, sizeof(float) * n));
+        GWN_TRY(cudaMalloc(&int_xy, sizeof(float4) * (n - 1)));
+        GWN_TRY(cudaMalloc(&int_z, sizeof(float) * (n - 1)));
+        GWN_TRY(cudaMalloc(&flags, sizeof(unsigned) * (n - 1)));
+        GWN_TRY(cudaMemsetAsync(flags, 0, sizeof(unsigned) * (n - 1), st));
+        karras_kernel<<<blocks_for(n - 1, 256), 256, 0, st>>>(k0, n, child, parent_int, parent_leaf);
+        refit_kernel<<<blocks_for(n, 256), 256, 0, st>>>(v0, n, tbox_xy, tbox_z, child, parent_int, parent_leaf,
+                                                        leaf_xy, leaf_z, int_xy, int_z, flags);
+        pack_kernel<<<blocks_for(n - 1, 256), 256, 0, st>>>(child, n, leaf_xy, leaf_z, int_xy, int_z, b.nodes);
+        GWN_TRY(cudaGetLastError());
+        GWN_TRY(cudaStreamSynchronize(st));
+        b.root = 0;
+        b.valid = true;
+    }
+done:
+    cudaFree(tbox_xy); cudaFree(tbox_z); cudaFree(cen); cudaFree(bounds); cudaFree(rad);
+    cudaFree(k0); cudaFree(k1); cudaFree(v0); cudaFree(v1); cudaFree(hist); cudaFree(skip);
+    cudaFree(child); cudaFree(parent_int); cudaFree(parent_leaf);
+    cudaFree(leaf_xy); cudaFree(leaf_z); cudaFree(int_xy); cudaFree(int_z); cudaFree(flags);
+    if (err != cudaSuccess) bvh_free(b);
+    return err;
+}
+
+}  // namespace gwn

@@ -1,0 +1,184 @@
+// gwn_internal.h -- structures shared by the host library and the kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/gwn.h"
+
+namespace gwn {
+
+// device counter slots (unsigned long long array of CNT_NUM)
+enum {
+    CNT_CUT_SIGN = 0,
+    CNT_FP64 = 1,
+    CNT_EXACT = 2,
+    CNT_STACK_OVERFLOW = 3,
+    CNT_TRI_TESTS = 4,
+    CNT_PAIRS = 5,
+    CNT_ROOTS = 6,
+    CNT_TIMEOUT = 7,
+    CNT_NUM = 16
+};
+
+// device status bits (int32)
+enum {
+    ST_STACK_OVERFLOW = 1,
+    ST_TIMEOUT = 2,
+    ST_EXPANSION_OVERFLOW = 4,
+    ST_BAD_INPUT = 8
+};
+
+// Orthonormal frame of the ray direction: n = -d/|d| (pole of the boundary
+// term), e1, e2 span the plane orthogonal to d, dh = d/|d| (depth axis of the
+// crossing hierarchy).  d keeps the caller's float32 bits for the exact
+// predicates.
+struct Frame {
+    float e1[3], e2[3], n[3], dh[3];
+    float d[3];
+};
+
+// Grid or point query source (device side view).
+struct QuerySrc {
+    int kind;             // GWN_QUERY_POINTS / GWN_QUERY_GRID
+    int dim;
+    const float *pts;     // POINTS, float32 (3D)
+    const double *pts64;  // POINTS, float64 (2D f64)
+    const float *ax[3];   // GRID: per-axis float32 coordinate tables
+    const double *ax64[3];
+    int64_t dims[3];
+    int64_t n;
+};
+
+struct BvhNode {          // internal node: boxes of both children in the d-frame
+    float4 lo;            // child0: x0, x1, y0, y1
+    float4 hi;            // child1: x0, x1, y0, y1
+    float4 z;             // child0 zmax, child1 zmax, child0 ref (int bits), child1 ref (int bits)
+};
+// child ref: >= 0 internal node index; < 0 leaf ~(sorted triangle index)
+
+struct MeshBvh {
+    bool valid = false;
+    float dkey[3] = {0, 0, 0};
+    int64_t n = 0;             // triangles
+    BvhNode *nodes = nullptr;  // n - 1
+    float4 *tris = nullptr;    // 3 float4 per sorted triangle (xyz of v0, v1, v2)
+    int32_t *tri_id = nullptr; // original triangle index per sorted position
+    int root = 0;              // ref of the root
+    float scene_radius = 0.f;  // max |v|_2 over the mesh vertices
+    Frame frame;
+};
+
+// Device pointers of one 2D chain set.
+struct ChainSet {
+    int dtype = GWN_F32;
+    int64_t n_chains = 0, n_ctrl = 0, n_seg = 0, n_pieces = 0;
+    void *ctrl = nullptr;          // [n_ctrl][2] of dtype
+    int64_t *chain_off = nullptr;  // device [n_chains + 1] control point offsets
+    // y-monotone pieces: segment start index (control point index of P0),
+    // parameter interval, y range, direction, owning chain
+    int64_t *piece_seg = nullptr;
+    double *piece_u = nullptr;     // [n_pieces][2]
+    double *piece_y = nullptr;     // [n_pieces][2] (y at u0, y at u1)
+    int32_t *piece_chain = nullptr;
+    int64_t *chain_piece_off = nullptr;  // device [n_chains + 1]
+    std::vector<int64_t> h_chain_off, h_chain_piece_off;
+};
+
+// One 2D evaluation set: chains [c_lo, c_hi) (their pieces [p_lo, p_hi)) on
+// one nx x ny grid written at out_off.
+struct Set2D {
+    int64_t c_lo, c_hi;
+    int64_t p_lo, p_hi;
+    int64_t nx, ny;
+    const void *ax, *ay;      // device axis tables (chain dtype)
+    int64_t out_off;
+};
+
+struct Arena {            // grow-only scratch owned by a context
+    void *ptr = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace gwn
+
+struct gwn_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int sm_count = 0;
+    int *d_status = nullptr;                  // device status bits
+    unsigned long long *d_cnt = nullptr;      // device counters [CNT_NUM]
+    gwn::Arena scratch[4];
+    cudaEvent_t ev[8];
+    bool events = false;
+};
+
+struct gwn_geom {
+    gwn_ctx *ctx = nullptr;
+    int kind = 0;
+    int dtype = GWN_F32;
+    // mesh
+    int64_t nv = 0, nf = 0;
+    float *dV = nullptr;
+    int32_t *dF = nullptr;
+    std::vector<int64_t> loop_off;     // host, n_loops + 1 (in edges)
+    std::vector<int32_t> loop_vid;     // host, n_edges vertex ids
+    float4 *bseq = nullptr;            // device loop sequence (n_edges + n_loops records)
+    int32_t *bseq_vid = nullptr;       // device vertex id per record
+    int64_t n_bseq = 0;
+    // boundary vertex -> records lists (gradient scatter), built on demand
+    int32_t *d_bvert = nullptr;
+    int64_t *d_brec_off = nullptr;
+    int32_t *d_brecs = nullptr;
+    int64_t n_bvert = 0;
+    gwn::MeshBvh bvh;
+    // 2D
+    gwn::ChainSet cs;
+    // batched launch cache
+    void *batch_cache = nullptr;
+};
+
+namespace gwn {
+
+// ---- helpers implemented in api.cpp -------------------------------------
+void set_error(const std::string &msg);
+gwn_status cuda_fail(cudaError_t e, const char *what);
+void *arena_get(gwn_ctx *ctx, int slot, size_t bytes, cudaError_t *err);
+Frame make_frame(const float d[3]);
+
+// ---- launchers (return the first CUDA error) -------------------------------
+cudaError_t bvh_build(gwn_geom *g, const Frame &fr, cudaStream_t st);
+void bvh_free(MeshBvh &b);
+
+cudaError_t launch_traverse(const MeshBvh &b, const QuerySrc &q, int32_t *chi, unsigned long long *cnt,
+                            int *status, int sm_count, cudaStream_t st);
+
+cudaError_t launch_bterm3d(const float4 *bseq, int64_t n_bseq, const Frame &fr, const QuerySrc &q,
+                           const int32_t *chi, float *w_out, float *b_out, unsigned long long *cnt,
+                           int *status, int sm_count, cudaStream_t st);
+
+cudaError_t launch_grad_p(const float4 *bseq, int64_t nb, const QuerySrc &q, const float *grad_w, float *grad_p,
+                          cudaStream_t st);
+int grad_v_chunks(int64_t nq, int64_t nb, int sm_count);
+cudaError_t launch_grad_v(const float4 *bseq, int64_t nb, const QuerySrc &q, const float *grad_w, int n_chunks,
+                          float *partial, float *rec_grad, const int32_t *bvert, const int64_t *rec_off,
+                          const int32_t *recs, int64_t n_bvert, float *grad_V, cudaStream_t st);
+
+cudaError_t launch_bruteforce3d(const float *V, const int32_t *F, int64_t nf, const QuerySrc &q, float *w_out,
+                                int sm_count, cudaStream_t st);
+
+// 2D
+cudaError_t launch_eval2d_items(const ChainSet &cs, const Set2D *d_sets, const int2 *d_items, int64_t n_items,
+                                unsigned long long *d_counter, int rows_per_item, int threads, int64_t max_nx,
+                                void *w_out, int32_t *chi_out, void *b_out, unsigned long long *cnt, int *status,
+                                int sm_count, cudaStream_t st);
+gwn_status eval2d_single(gwn_geom *g, const QuerySrc &src, void *w_out, int32_t *chi_out, void *b_out,
+                         unsigned long long *cnt);
+void batch_cache_free(void *p);
+
+cudaError_t launch_bruteforce2d(const ChainSet &cs, const QuerySrc &q, void *w_out, int sm_count,
+                                cudaStream_t st);
+
+}  // namespace gwn

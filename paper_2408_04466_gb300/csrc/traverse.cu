@@ -1,0 +1,153 @@
+// traverse.cu -- signed crossing count chi_d(p) of the ray p + t d (Eq. chi).
+//
+// All rays share the direction d, so the hierarchy is built in the frame
+// (e1, e2, dh) of d: a ray is a point (p.e1, p.e2) of the projection plane
+// plus the half-line of depths > p.dh.  A child box (x0, x1, y0, y1, zmax)
+// can hold a crossing only if the projected point lies in [x0,x1]x[y0,y1] and
+// zmax >= p.dh: five comparisons per child instead of a slab test.  Boxes
+// and the query point are padded by bounds on their float32 rounding and on
+// the residual non-orthogonality of the rounded frame, so culling never drops
+// a crossing; every surviving triangle is decided by exact predicates.
+//
+// The signed crossings are accumulated per query (one thread per query);
+// the traversal stack holds at most the tree depth, bounded by GWN_STACK;
+// overflow or the iteration limit sets a status bit and a counter and marks
+// the query result as invalid (INT32_MIN).
+#include "gwn_internal.h"
+#include "predicates.cuh"
+#include "query.cuh"
+
+namespace gwn {
+
+#define GWN_STACK 64
+
+struct TravParams {
+    float pad_rel;    // relative pad on |p|_1
+    float pad_abs;    // absolute pad (frame non-orthogonality x scene radius)
+    int64_t max_iter; // iteration limit per query
+    int n_internal;   // valid internal refs are [0, n_internal)
+    int n_leaves;     // valid leaf refs are ~[0, n_leaves)
+};
+
+__device__ __forceinline__ bool box_hit(float x0, float x1, float y0, float y1, float zm, float xlo, float xhi,
+                                        float ylo, float yhi, float zlo) {
+    return x0 <= xhi && xlo <= x1 && y0 <= yhi && ylo <= y1 && zm >= zlo;
+}
+
+__global__ void __launch_bounds__(128) traverse_kernel(const BvhNode *__restrict__ nodes,
+                                                       const float4 *__restrict__ tris, int root, Frame fr,
+                                                       TravParams tp, QuerySrc q, int32_t *__restrict__ chi,
+                                                       unsigned long long *cnt, int *status) {
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= q.n) return;
+    float3 p = query_point3(q, idx);
+    float3 D = make_float3(fr.d[0], fr.d[1], fr.d[2]);
+    float p1 = fmaf(p.z, fr.e1[2], fmaf(p.y, fr.e1[1], p.x * fr.e1[0]));
+    float p2 = fmaf(p.z, fr.e2[2], fmaf(p.y, fr.e2[1], p.x * fr.e2[0]));
+    float p3 = fmaf(p.z, fr.dh[2], fmaf(p.y, fr.dh[1], p.x * fr.dh[0]));
+    float pad = fmaf(tp.pad_rel, fabsf(p.x) + fabsf(p.y) + fabsf(p.z), tp.pad_abs);
+    float xlo = p1 - pad, xhi = p1 + pad, ylo = p2 - pad, yhi = p2 + pad, zlo = p3 - pad;
+
+    int acc = 0;
+    int stack[GWN_STACK];
+    int sp = 0;
+    int node = root;
+    int64_t iter = 0;
+    bool bad = false;
+    while (true) {
+        if (++iter > tp.max_iter) {
+            atomicOr(status, ST_TIMEOUT);
+            if (cnt) atomicAdd(&cnt[CNT_TIMEOUT], 1ull);
+            bad = true;
+            break;
+        }
+        if (node >= tp.n_internal || ~node >= tp.n_leaves) {   // corrupt reference: report, never read
+            atomicOr(status, ST_BAD_INPUT);
+            bad = true;
+            break;
+        }
+        if (node < 0) {
+            int t = ~node;
+            float4 a = __ldg(&tris[3 * t]), b = __ldg(&tris[3 * t + 1]), c = __ldg(&tris[3 * t + 2]);
+            if (cnt) atomicAdd(&cnt[CNT_TRI_TESTS], 1ull);
+            acc += tri_crossing(make_float3(a.x, a.y, a.z), make_float3(b.x, b.y, b.z),
+                                make_float3(c.x, c.y, c.z), p, D, cnt, status);
+            if (sp == 0) break;
+            node = stack[--sp];
+            continue;
+        }
+        const BvhNode nd = nodes[node];
+        bool h0 = box_hit(nd.lo.x, nd.lo.y, nd.lo.z, nd.lo.w, nd.z.x, xlo, xhi, ylo, yhi, zlo);
+        bool h1 = box_hit(nd.hi.x, nd.hi.y, nd.hi.z, nd.hi.w, nd.z.y, xlo, xhi, ylo, yhi, zlo);
+        int c0 = __float_as_int(nd.z.z), c1 = __float_as_int(nd.z.w);
+        if (h0 && h1) {
+            if (sp >= GWN_STACK) {
+                atomicOr(status, ST_STACK_OVERFLOW);
+                if (cnt) atomicAdd(&cnt[CNT_STACK_OVERFLOW], 1ull);
+                bad = true;
+                break;
+            }
+            stack[sp++] = c1;
+            node = c0;
+        } else if (h0) {
+            node = c0;
+        } else if (h1) {
+            node = c1;
+        } else {
+            if (sp == 0) break;
+            node = stack[--sp];
+        }
+    }
+    chi[idx] = bad ? INT32_MIN : acc;
+}
+
+// Root is a single leaf (one triangle) or the mesh is empty.
+__global__ void traverse_single_kernel(const float4 *__restrict__ tris, int ntri, Frame fr, QuerySrc q,
+                                       int32_t *__restrict__ chi, unsigned long long *cnt, int *status) {
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= q.n) return;
+    int acc = 0;
+    if (ntri == 1) {
+        float3 p = query_point3(q, idx);
+        float3 D = make_float3(fr.d[0], fr.d[1], fr.d[2]);
+        float4 a = tris[0], b = tris[1], c = tris[2];
+        acc = tri_crossing(make_float3(a.x, a.y, a.z), make_float3(b.x, b.y, b.z), make_float3(c.x, c.y, c.z),
+                           p, D, cnt, status);
+    }
+    chi[idx] = acc;
+}
+
+cudaError_t launch_traverse(const MeshBvh &b, const QuerySrc &q, int32_t *chi, unsigned long long *cnt,
+                            int *status, int sm_count, cudaStream_t st) {
+    (void)sm_count;
+    if (q.n == 0) return cudaSuccess;
+    const int threads = 128;
+    int64_t blocks = (q.n + threads - 1) / threads;
+    if (blocks > 0x7fffffff) return cudaErrorInvalidValue;
+    if (b.n <= 1) {
+        traverse_single_kernel<<<(unsigned)blocks, threads, 0, st>>>(b.tris, (int)b.n, b.frame, q, chi, cnt,
+                                                                      status);
+        return cudaGetLastError();
+    }
+    // frame non-orthogonality: |d_hat . e_i| for the rounded frame, times the
+    // largest distance a crossing can lie from the query along the ray
+    const Frame &fr = b.frame;
+    double dn = sqrt((double)fr.d[0] * fr.d[0] + (double)fr.d[1] * fr.d[1] + (double)fr.d[2] * fr.d[2]);
+    double c1 = fabs((fr.d[0] * (double)fr.e1[0] + fr.d[1] * (double)fr.e1[1] + fr.d[2] * (double)fr.e1[2]) / dn);
+    double c2 = fabs((fr.d[0] * (double)fr.e2[0] + fr.d[1] * (double)fr.e2[1] + fr.d[2] * (double)fr.e2[2]) / dn);
+    double perp = (c1 > c2 ? c1 : c2) * 1.01 + 1e-12;
+    TravParams tp;
+    // |p.e - fl(p.e)| <= 3u |p|_1 for unit-norm float32 frame rows; a crossing
+    // at distance t|d| <= |p|_2 + R along the ray (R = largest vertex norm)
+    // shifts its projection by at most perp * t|d|.
+    tp.pad_rel = (float)(4e-7 + 2.0 * perp);
+    tp.pad_abs = (float)(2.0 * perp * (double)b.scene_radius + 1e-30);
+    tp.max_iter = 8 * b.n + 64;
+    tp.n_internal = (int)(b.n - 1);
+    tp.n_leaves = (int)b.n;
+    traverse_kernel<<<(unsigned)blocks, threads, 0, st>>>(b.nodes, b.tris, b.root, b.frame, tp, q, chi, cnt,
+                                                          status);
+    return cudaGetLastError();
+}
+
+}  // namespace gwn

@@ -1,0 +1,157 @@
+"""GPU parity of the 2D one-shot path (one +x ray per grid row) against the
+FP64 oracle: crossing counts bit-exact; |dw| <= 1e-12 (float64 chains) or
+1e-6 (float32 chains) at queries farther than 1e-4 x bbox diagonal from the
+curve; batched evaluation identical to per-chain evaluation."""
+import math
+
+import numpy as np
+import pytest
+
+import gen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gwn(cuda_available):
+    import paper_2408_04466_gb300 as pkg
+    from paper_2408_04466_gb300 import build
+    build.build()
+    return pkg
+
+
+@pytest.fixture(scope="module")
+def ctx(gwn):
+    return gwn.Context(0)
+
+
+def _grid(gwn, g):
+    return gwn.Grid(g.lo, g.hi, g.dims)
+
+
+def _compare_chain(ctrl64, grid, w, chi, tol):
+    P = gen.grid_points(grid, np.float64 if w.dtype == np.float64 else np.float32).astype(np.float64)
+    wq = oracle.w2d_quad(ctrl64, P)
+    wc, chic = oracle.w2d_closed_x(ctrl64, P)
+    diag = math.hypot(grid.hi[0] - grid.lo[0], grid.hi[1] - grid.lo[1])
+    keep = oracle.dist2d(ctrl64, P) > 1e-4 * diag
+    assert np.array_equal(chi[keep], chic[keep]), (chi[keep] != chic[keep]).sum()
+    err = np.abs(w.astype(np.float64) - wq)[keep].max()
+    assert err <= tol, err
+    return keep
+
+
+def test_circle_chain_fp64_full_grid(gwn, ctx):
+    c = gen.bezier_circle_chain()
+    ch = gwn.Bezier2D(ctx, c.ctrl, c.offsets)
+    r = ch.eval(_grid(gwn, c.grids[0]), want_chi=True, want_b=True)
+    w = r["w"].cpu().numpy()
+    chi = r["chi"].cpu().numpy()
+    assert w.dtype == np.float64
+    _compare_chain(c.ctrl, c.grids[0], w, chi, 1e-12)
+    # the chord term is the boundary part: w - chi
+    assert np.array_equal(w - chi, r["b"].cpu().numpy()) or np.abs(w - chi - r["b"].cpu().numpy()).max() < 1e-15
+
+
+def test_straight_and_closed_chains(gwn, ctx):
+    # a closed chain gives integers; a straight segment gives the subtended angle
+    m = 3 * 16
+    th = 2 * np.pi * np.arange(m + 1) / m
+    ctrl = np.stack([np.cos(th), np.sin(th)], 1)
+    ctrl[-1] = ctrl[0]
+    ch = gwn.Bezier2D(ctx, ctrl, [0, m + 1])
+    g = gen.Grid((-1.5, -1.5), (1.5, 1.5), (64, 48))
+    w = ch.eval(_grid(gwn, g)).cpu().numpy()
+    P = gen.grid_points(g, np.float64)
+    keep = oracle.dist2d(ctrl, P) > 1e-3
+    assert np.all((np.abs(w - 1) < 1e-12) | (np.abs(w) < 1e-12) | ~keep)
+    _compare_chain(ctrl, g, w, ch.eval(_grid(gwn, g), want_chi=True)["chi"].cpu().numpy(), 1e-12)
+
+
+def test_star_chains_fp32_and_batch(gwn, ctx):
+    import torch
+    cs = gen.star_chains(n_chains=12, seg_hi=300, grid_n=48, seed=4)
+    ch = gwn.Bezier2D(ctx, cs.ctrl, cs.offsets)
+    grids = [_grid(gwn, g) for g in cs.grids]
+    wb, offs = ch.eval_batch(grids)
+    wb2, _ = ch.eval_batch(grids)      # graph replay
+    torch.cuda.synchronize()
+    assert torch.equal(wb, wb2)
+    wb = wb.cpu().numpy()
+    for c in range(cs.meta["n_chains"]):
+        ctrl = cs.ctrl[cs.offsets[c]:cs.offsets[c + 1]]
+        single = gwn.Bezier2D(ctx, ctrl, [0, len(ctrl)])
+        r = single.eval(grids[c], want_chi=True)
+        ws = r["w"].cpu().numpy()
+        n = grids[c].n
+        assert np.array_equal(ws, wb[offs[c]:offs[c] + n]), c
+        _compare_chain(ctrl.astype(np.float64), cs.grids[c], ws, r["chi"].cpu().numpy(), 1e-6)
+    t, rows = ch.batch_plan()
+    assert t in (128, 256) and rows in (1, 2, 4, 8)
+    # a forced plan gives the same numbers
+    wf, _ = ch.eval_batch(grids, threads=256, rows=1, use_graph=False)
+    assert np.array_equal(wf.cpu().numpy(), wb)
+
+
+def test_multi_chain_union(gwn, ctx):
+    """gwn_eval on a geometry with several chains sums their winding numbers."""
+    cs = gen.star_chains(n_chains=3, seg_hi=40, grid_n=20, seed=9, dtype=np.float64)
+    ch = gwn.Bezier2D(ctx, cs.ctrl, cs.offsets)
+    g = gen.Grid((-1.6, -1.6), (1.6, 1.6), (40, 36))
+    w = ch.eval(_grid(gwn, g)).cpu().numpy()
+    P = gen.grid_points(g, np.float64)
+    tot = np.zeros(len(P))
+    keep = np.ones(len(P), bool)
+    for c in range(3):
+        ctrl = cs.ctrl[cs.offsets[c]:cs.offsets[c + 1]]
+        tot += oracle.w2d_quad(ctrl, P)
+        keep &= oracle.dist2d(ctrl, P) > 1e-3
+    assert np.abs(w - tot)[keep].max() < 1e-11
+
+
+def test_bruteforce_2d(gwn, ctx):
+    c = gen.bezier_circle_chain(grid_n=24)
+    ch = gwn.Bezier2D(ctx, c.ctrl, c.offsets)
+    wb = ch.bruteforce(_grid(gwn, c.grids[0])).cpu().numpy()
+    P = gen.grid_points(c.grids[0], np.float64)
+    keep = oracle.dist2d(c.ctrl, P) > 0.05
+    assert np.abs(wb - oracle.w2d_quad(c.ctrl, P))[keep].max() < 1e-9
+
+
+def test_errors_2d(gwn, ctx):
+    with pytest.raises(gwn.GwnError):
+        gwn.Bezier2D(ctx, np.zeros((5, 2)), [0, 5])       # not 3k+1
+    c = gen.bezier_circle_chain(grid_n=8)
+    ch = gwn.Bezier2D(ctx, c.ctrl, c.offsets)
+    import torch
+    with pytest.raises(gwn.GwnError):
+        q = gwn.Points(torch.zeros((4, 2), dtype=torch.float64, device="cuda"))
+        w = torch.empty(4, dtype=torch.float64, device="cuda")
+        import ctypes as C
+        gwn._capi.check(ch.lib.gwn_eval(ch.h, C.byref(q.to_c()), None, w.data_ptr(), None, None, None), "eval")
+
+
+def test_star_chains_full_size_sampled(gwn, ctx):
+    """The batched workload at full size: 1024 chains, 256^2 grid each, one
+    persistent graph launch; a sample of chains is checked query by query."""
+    import torch
+    cs = gen.star_chains()
+    ch = gwn.Bezier2D(ctx, cs.ctrl, cs.offsets)
+    grids = [_grid(gwn, g) for g in cs.grids]
+    w, offs = ch.eval_batch(grids)
+    torch.cuda.synchronize()
+    ctx.check()
+    rng = np.random.default_rng(5)
+    nseg = (np.diff(cs.offsets) - 1) // 3
+    pick = list(rng.choice(len(grids), 6, replace=False)) + [int(np.argmax(nseg))]
+    for c in pick:
+        ctrl = cs.ctrl[cs.offsets[c]:cs.offsets[c + 1]].astype(np.float64)
+        n = grids[c].n
+        sub = np.sort(rng.choice(n, 1500, replace=False))
+        wc = w[int(offs[c]):int(offs[c]) + n].cpu().numpy()[sub]
+        P = gen.grid_points(cs.grids[c], np.float32, index=sub).astype(np.float64)
+        wq = oracle.w2d_quad(ctrl, P)
+        g = cs.grids[c]
+        keep = oracle.dist2d(ctrl, P) > 1e-4 * math.hypot(g.hi[0] - g.lo[0], g.hi[1] - g.lo[1])
+        assert np.abs(wc.astype(np.float64) - wq)[keep].max() <= 1e-6, c
