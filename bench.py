@@ -110,10 +110,10 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def workload(rank: int = 0, world: int = 1):
+def workload(rank: int = 0, world: int = 1, grid_n: int = 256):
     import gen
     from paper_2408_04466_gb300.shard import shard_grid
-    m = gen.icosphere_cap()
+    m = gen.icosphere_cap(grid_n=grid_n)
     lo, hi, dims, span = shard_grid(m.grid.lo, m.grid.hi, m.grid.dims, rank, world, weak=True)
     return m, (lo, hi, dims)
 
@@ -188,7 +188,7 @@ def run_gpu(args):
         dist.barrier()
     import paper_2408_04466_gb300 as gwn
 
-    m, (lo, hi, dims) = workload(rank, world)
+    m, (lo, hi, dims) = workload(rank, world, args.grid)
     nq = int(np.prod(dims))
     stream = torch.cuda.Stream(device=dev)
     torch.cuda.set_stream(stream)
@@ -247,7 +247,11 @@ def run_gpu(args):
     ms_bterm = statistics.median(k["ms_boundary"] for k in ks)
 
     line = None
-    if rank == 0:
+    if rank == 0 and args.no_extras:
+        print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                          "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "grid": args.grid,
+                          "kernels": {"traverse_ms": ms_trav, "bterm3d_ms": ms_bterm}}))
+    elif rank == 0:
         peaks, peak_kind = _peaks()
         clk_hz = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
         alu_peak = SM_COUNT * FP32_LANES_PER_SM * clk_hz / 1e12          # Tops/s
@@ -337,6 +341,9 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--cpu-sample", type=int, default=4096)
     ap.add_argument("--ref-sample", type=int, default=1024)
+    ap.add_argument("--grid", type=int, default=256, help="grid resolution (256 = the benchmark workload; "
+                                                          "smaller values only for profiling captures)")
+    ap.add_argument("--no-extras", action="store_true", help="skip comparator, e2e and CPU baseline legs")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

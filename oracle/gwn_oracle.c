@@ -648,19 +648,70 @@ static double gk15(const double *c, const double *p, double a, double b, double 
     return k * h;
 }
 
-/* Adaptive bisection: a subinterval is accepted when its error estimate is
- * below tol times its length, or below the round-off floor (50 ulps of the
- * integral of |f| over it), or when it is shorter than 1e-12.  A non-finite
- * value (p on the curve) is returned as is. */
-static double adapt(const double *c, const double *p, double a, double b, double tol, int depth) {
-    double err, resabs;
-    double v = gk15(c, p, a, b, &err, &resabs);
-    if (!isfinite(v) || !isfinite(err)) return v;
-    if (err <= tol * (b - a) || err <= 50.0 * 2.220446049250313e-16 * resabs || depth >= 48
-        || b - a < 1e-12)
-        return v;
-    double m = 0.5 * (a + b);
-    return adapt(c, p, a, m, tol, depth + 1) + adapt(c, p, m, b, tol, depth + 1);
+/* Globally adaptive Gauss-Kronrod: keep a heap of subintervals ordered by
+ * their error estimate, bisect the worst one, and stop when the summed error
+ * estimate is below tol (or below the round-off floor, 50 ulps of the integral
+ * of |f|), when the worst interval is shorter than 1e-13, or after
+ * QUAD_LIMIT intervals.  The cap bounds the work for queries arbitrarily close
+ * to the curve (where w is undefined and no comparison is made). */
+#define QUAD_LIMIT 2048
+typedef struct { double a, b, v, e, ra; } qint_t;
+
+static void heap_push(qint_t *h, int *n, qint_t x) {
+    int i = (*n)++;
+    h[i] = x;
+    while (i > 0) {
+        int p = (i - 1) / 2;
+        if (h[p].e >= h[i].e) break;
+        qint_t t = h[p]; h[p] = h[i]; h[i] = t;
+        i = p;
+    }
+}
+
+static qint_t heap_pop(qint_t *h, int *n) {
+    qint_t top = h[0];
+    h[0] = h[--(*n)];
+    int i = 0;
+    for (;;) {
+        int l = 2 * i + 1, r = l + 1, m = i;
+        if (l < *n && h[l].e > h[m].e) m = l;
+        if (r < *n && h[r].e > h[m].e) m = r;
+        if (m == i) break;
+        qint_t t = h[m]; h[m] = h[i]; h[i] = t;
+        i = m;
+    }
+    return top;
+}
+
+static double adapt(const double *c, const double *p, double a, double b, double tol) {
+    qint_t heap[QUAD_LIMIT + 2];
+    int n = 0;
+    qint_t x;
+    x.a = a; x.b = b;
+    x.v = gk15(c, p, a, b, &x.e, &x.ra);
+    if (!isfinite(x.v) || !isfinite(x.e)) return x.v;
+    heap_push(heap, &n, x);
+    double tot = x.v, err = x.e, rabs = x.ra;
+    while (n < QUAD_LIMIT) {
+        if (err <= tol || err <= 50.0 * 2.220446049250313e-16 * rabs) break;
+        qint_t w = heap_pop(heap, &n);
+        if (w.b - w.a < 1e-13) { heap_push(heap, &n, w); break; }
+        double m = 0.5 * (w.a + w.b);
+        qint_t l, r;
+        l.a = w.a; l.b = m; l.v = gk15(c, p, w.a, m, &l.e, &l.ra);
+        r.a = m; r.b = w.b; r.v = gk15(c, p, m, w.b, &r.e, &r.ra);
+        if (!isfinite(l.v) || !isfinite(r.v)) return l.v + r.v;
+        tot += l.v + r.v - w.v;
+        err += l.e + r.e - w.e;
+        rabs += l.ra + r.ra - w.ra;
+        heap_push(heap, &n, l);
+        heap_push(heap, &n, r);
+    }
+    /* re-sum the accepted intervals (avoids drift of the running total) */
+    double s = 0.0;
+    for (int i = 0; i < n; i++) s += heap[i].v;
+    (void)tot;
+    return s;
 }
 
 typedef struct {
@@ -672,7 +723,7 @@ static void quad_range(void *p, int64_t lo, int64_t hi) {
     for (int64_t q = lo; q < hi; q++) {
         double acc = 0.0;
         for (int64_t s = 0; s < c->nseg; s++)
-            acc += adapt(c->ctrl + 6 * s, c->P + 2 * q, 0.0, 1.0, c->tol, 0);
+            acc += adapt(c->ctrl + 6 * s, c->P + 2 * q, 0.0, 1.0, c->tol);
         c->w[q] = acc / (2.0 * M_PI);
     }
 }

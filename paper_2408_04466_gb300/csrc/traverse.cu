@@ -34,12 +34,12 @@ __device__ __forceinline__ bool box_hit(float x0, float x1, float y0, float y1, 
     return x0 <= xhi && xlo <= x1 && y0 <= yhi && ylo <= y1 && zm >= zlo;
 }
 
-__global__ void __launch_bounds__(128) traverse_kernel(const BvhNode *__restrict__ nodes,
+__global__ void __launch_bounds__(256) traverse_kernel(const BvhNode *__restrict__ nodes,
                                                        const float4 *__restrict__ tris, int root, Frame fr,
                                                        TravParams tp, QuerySrc q, int32_t *__restrict__ chi,
                                                        unsigned long long *cnt, int *status) {
-    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= q.n) return;
+    int64_t idx = q.kind == GWN_QUERY_GRID ? grid_tile_query(q) : (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx < 0 || idx >= q.n) return;
     float3 p = query_point3(q, idx);
     float3 D = make_float3(fr.d[0], fr.d[1], fr.d[2]);
     float p1 = fmaf(p.z, fr.e1[2], fmaf(p.y, fr.e1[1], p.x * fr.e1[0]));
@@ -145,8 +145,10 @@ cudaError_t launch_traverse(const MeshBvh &b, const QuerySrc &q, int32_t *chi, u
     tp.max_iter = 8 * b.n + 64;
     tp.n_internal = (int)(b.n - 1);
     tp.n_leaves = (int)b.n;
-    traverse_kernel<<<(unsigned)blocks, threads, 0, st>>>(b.nodes, b.tris, b.root, b.frame, tp, q, chi, cnt,
-                                                          status);
+    int64_t tblocks = q.kind == GWN_QUERY_GRID ? grid_tile_blocks(q) : (q.n + 255) / 256;
+    if (tblocks > 0x7fffffff) return cudaErrorInvalidValue;
+    traverse_kernel<<<(unsigned)tblocks, 256, 0, st>>>(b.nodes, b.tris, b.root, b.frame, tp, q, chi, cnt,
+                                                       status);
     return cudaGetLastError();
 }
 
