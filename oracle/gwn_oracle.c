@@ -164,6 +164,27 @@ static int exact_cross_comp(const float *A, const float *B, const float *P, int 
     return exact_sign_terms(t, n);
 }
 
+/* exact sign of ((X-P) x D)_k */
+static int exact_cross_xd(const float *X, const float *P, const float *D, int k) {
+    int i = (k + 1) % 3, j = (k + 2) % 3;
+    term_t t[4];
+    int n = 0;
+    fac_t f1[2] = {{X[i], P[i]}, {D[j], 0.0f}};
+    fac_t f2[2] = {{X[j], P[j]}, {D[i], 0.0f}};
+    n += expand_product(t + n, 1, f1, 2);
+    n += expand_product(t + n, -1, f2, 2);
+    return exact_sign_terms(t, n);
+}
+
+/* X lies exactly on the forward ray from P: (X-P) x D = 0 and (X-P).D > 0 */
+static int on_forward_ray(const float *X, const float *P, const float *D) {
+    double dot = ((double)X[0] - P[0]) * D[0] + ((double)X[1] - P[1]) * D[1] + ((double)X[2] - P[2]) * D[2];
+    if (!(dot > 0.0)) return 0;
+    for (int k = 0; k < 3; k++)
+        if (exact_cross_xd(X, P, D, k) != 0) return 0;
+    return 1;
+}
+
 /* exact sign of det[V0-P, V1-P, V2-P] */
 static int exact_orient(const float *V0, const float *V1, const float *V2, const float *P) {
     term_t t[6 * 8];
@@ -441,7 +462,14 @@ ORACLE_API int64_t oracle_boundary_edges(const int32_t *F, int64_t nf, int32_t *
  * Omega jumps by 4pi where the ray p + t d crosses the edge; there the sign of
  * the numerator (= -det[A-p, B-p, d]/|d|) is taken from the exact, perturbed
  * predicate whenever the float64 value is within its error bound, so the jump
- * sits exactly where chi_d changes. */
+ * sits exactly where chi_d changes.
+ * A boundary vertex lying exactly on the forward ray (ray through a vertex)
+ * makes its two spherical triangles degenerate (0/0).  The crossing count
+ * resolves that case with the perturbed direction d_eps; the boundary term
+ * takes the limit under the same perturbation: the perturbed ray sees the
+ * vertex in the direction -dp (dp = the first of e_x, e_y, e_z not parallel
+ * to d, projected orthogonally to d), which gives the closed-form limits
+ * below. */
 typedef struct {
     const float *V; const int32_t *src, *dst, *mult; int64_t ne;
     const float *P; const float *d; double *B;
@@ -451,7 +479,18 @@ static void bterm_range(void *p, int64_t lo, int64_t hi) {
     bterm_ctx *c = (bterm_ctx *)p;
     double dn = sqrt((double)c->d[0] * c->d[0] + (double)c->d[1] * c->d[1]
                      + (double)c->d[2] * c->d[2]);
-    double cdir[3] = {-(double)c->d[0] / dn, -(double)c->d[1] / dn, -(double)c->d[2] / dn};
+    double dh[3] = {(double)c->d[0] / dn, (double)c->d[1] / dn, (double)c->d[2] / dn};
+    double cdir[3] = {-dh[0], -dh[1], -dh[2]};
+    /* perturbation direction: the first of e_x, e_y, e_z not parallel to d,
+     * minus its component along d */
+    double dp[3] = {0, 0, 0};
+    for (int k = 0; k < 3; k++) {
+        double e[3] = {0, 0, 0};
+        e[k] = 1.0;
+        double t = e[0] * dh[0] + e[1] * dh[1] + e[2] * dh[2];
+        double q[3] = {e[0] - t * dh[0], e[1] - t * dh[1], e[2] - t * dh[2]};
+        if (fabs(q[0]) + fabs(q[1]) + fabs(q[2]) > 1e-12) { dp[0] = q[0]; dp[1] = q[1]; dp[2] = q[2]; break; }
+    }
     for (int64_t q = lo; q < hi; q++) {
         const float *pp = c->P + 3 * q;
         double acc = 0.0;
@@ -463,17 +502,38 @@ static void bterm_range(void *p, int64_t lo, int64_t hi) {
                 a[i] = (double)A[i] - (double)pp[i];
                 b[i] = (double)Bv[i] - (double)pp[i];
             }
-            double la = sqrt(a[0]*a[0] + a[1]*a[1] + a[2]*a[2]);
-            double lb = sqrt(b[0]*b[0] + b[1]*b[1] + b[2]*b[2]);
-            double x0 = a[1]*b[2] - a[2]*b[1], x1 = a[2]*b[0] - a[0]*b[2], x2 = a[0]*b[1] - a[1]*b[0];
-            double num = cdir[0]*x0 + cdir[1]*x1 + cdir[2]*x2;
-            double perm = fabs(cdir[0]) * (fabs(a[1]*b[2]) + fabs(a[2]*b[1]))
-                        + fabs(cdir[1]) * (fabs(a[2]*b[0]) + fabs(a[0]*b[2]))
-                        + fabs(cdir[2]) * (fabs(a[0]*b[1]) + fabs(a[1]*b[0]));
-            double ab = a[0]*b[0] + a[1]*b[1] + a[2]*b[2];
-            double ac = a[0]*cdir[0] + a[1]*cdir[1] + a[2]*cdir[2];
-            double bc = b[0]*cdir[0] + b[1]*cdir[1] + b[2]*cdir[2];
-            double den = la * lb + ab + ac * lb + bc * la;
+            int ra = on_forward_ray(A, pp, c->d), rb = on_forward_ray(Bv, pp, c->d);
+            double num, den, perm;
+            if (ra && rb) {
+                num = 0.0; den = 1.0; perm = 1.0;      /* edge along the ray: limit 0 */
+            } else if (ra) {
+                /* A on the ray: the perturbed ray sees A in direction -dp, so
+                 * Omega/2 -> atan2(dp.(b x dh), -(b.dp)) */
+                double bx[3] = {b[1] * dh[2] - b[2] * dh[1], b[2] * dh[0] - b[0] * dh[2], b[0] * dh[1] - b[1] * dh[0]};
+                num = dp[0] * bx[0] + dp[1] * bx[1] + dp[2] * bx[2];
+                den = -(b[0] * dp[0] + b[1] * dp[1] + b[2] * dp[2]);
+                perm = fabs(dp[0]) * (fabs(b[1] * dh[2]) + fabs(b[2] * dh[1]))
+                     + fabs(dp[1]) * (fabs(b[2] * dh[0]) + fabs(b[0] * dh[2]))
+                     + fabs(dp[2]) * (fabs(b[0] * dh[1]) + fabs(b[1] * dh[0]));
+            } else if (rb) {
+                /* B on the ray: Omega/2 -> atan2(det[a, dp, dh], -(a.dp)) */
+                double px[3] = {dp[1] * dh[2] - dp[2] * dh[1], dp[2] * dh[0] - dp[0] * dh[2], dp[0] * dh[1] - dp[1] * dh[0]};
+                num = a[0] * px[0] + a[1] * px[1] + a[2] * px[2];
+                den = -(a[0] * dp[0] + a[1] * dp[1] + a[2] * dp[2]);
+                perm = fabs(a[0]) * fabs(px[0]) + fabs(a[1]) * fabs(px[1]) + fabs(a[2]) * fabs(px[2]) + 1e-300;
+            } else {
+                double la = sqrt(a[0]*a[0] + a[1]*a[1] + a[2]*a[2]);
+                double lb = sqrt(b[0]*b[0] + b[1]*b[1] + b[2]*b[2]);
+                double x0 = a[1]*b[2] - a[2]*b[1], x1 = a[2]*b[0] - a[0]*b[2], x2 = a[0]*b[1] - a[1]*b[0];
+                num = cdir[0]*x0 + cdir[1]*x1 + cdir[2]*x2;
+                perm = fabs(cdir[0]) * (fabs(a[1]*b[2]) + fabs(a[2]*b[1]))
+                     + fabs(cdir[1]) * (fabs(a[2]*b[0]) + fabs(a[0]*b[2]))
+                     + fabs(cdir[2]) * (fabs(a[0]*b[1]) + fabs(a[1]*b[0]));
+                double ab = a[0]*b[0] + a[1]*b[1] + a[2]*b[2];
+                double ac = a[0]*cdir[0] + a[1]*cdir[1] + a[2]*cdir[2];
+                double bc = b[0]*cdir[0] + b[1]*cdir[1] + b[2]*cdir[2];
+                den = la * lb + ab + ac * lb + bc * la;
+            }
             if (den < 0.0 && fabs(num) <= 4.0 * FILTER_U * perm + 1e-300) {
                 int s = sos_edge(A, Bv, pp, c->d);      /* sign(num) = -s */
                 if (s > 0) num = -fabs(num);

@@ -76,6 +76,41 @@ Frame make_frame(const float d[3]) {
     return f;
 }
 
+Frame64 make_frame64(const float d[3]) {
+    Frame64 f;
+    double dd[3] = {d[0], d[1], d[2]};
+    double len = sqrt(dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2]);
+    double dh[3] = {dd[0] / len, dd[1] / len, dd[2] / len};
+    double n[3] = {-dh[0], -dh[1], -dh[2]};
+    int k = 0;
+    for (int i = 1; i < 3; i++)
+        if (fabs(n[i]) < fabs(n[k])) k = i;
+    double h[3] = {0, 0, 0};
+    h[k] = 1.0;
+    double e1[3] = {h[1] * n[2] - h[2] * n[1], h[2] * n[0] - h[0] * n[2], h[0] * n[1] - h[1] * n[0]};
+    double l1 = sqrt(e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2]);
+    for (int i = 0; i < 3; i++) e1[i] /= l1;
+    double e2[3] = {n[1] * e1[2] - n[2] * e1[1], n[2] * e1[0] - n[0] * e1[2], n[0] * e1[1] - n[1] * e1[0]};
+    for (int i = 0; i < 3; i++) {
+        f.e1[i] = e1[i];
+        f.e2[i] = e2[i];
+        f.n[i] = n[i];
+        f.dh[i] = dh[i];
+        f.dp[i] = 0.0;
+    }
+    for (int c = 0; c < 3; c++) {
+        double e[3] = {0, 0, 0};
+        e[c] = 1.0;
+        double t = e[0] * dh[0] + e[1] * dh[1] + e[2] * dh[2];
+        double q[3] = {e[0] - t * dh[0], e[1] - t * dh[1], e[2] - t * dh[2]};
+        if (fabs(q[0]) + fabs(q[1]) + fabs(q[2]) > 1e-12) {
+            for (int i = 0; i < 3; i++) f.dp[i] = q[i];
+            break;
+        }
+    }
+    return f;
+}
+
 // ---------------------------------------------------------------------------
 // boundary extraction (host)
 // ---------------------------------------------------------------------------
@@ -754,8 +789,8 @@ GWN_API gwn_status gwn_eval(gwn_geom *g, const gwn_queries *q, const float *d, v
         e = launch_traverse(g->bvh, src, chi, stats ? ctx->d_cnt : nullptr, ctx->d_status, ctx->sm_count, ctx->stream);
         if (e != cudaSuccess) return cuda_fail(e, "crossing traversal");
         if (stats) CK(cudaEventRecord(ctx->ev[2], ctx->stream), "event");
-        e = launch_bterm3d(g->bseq, g->n_bseq, g->bvh.frame, src, chi, (float *)w_out, (float *)b_out,
-                           stats ? ctx->d_cnt : nullptr, ctx->d_status, ctx->sm_count, ctx->stream);
+        e = launch_bterm3d(g->bseq, g->n_bseq, g->bvh.frame, make_frame64(d), src, chi, (float *)w_out,
+                           (float *)b_out, stats ? ctx->d_cnt : nullptr, ctx->d_status, ctx->sm_count, ctx->stream);
         if (e != cudaSuccess) return cuda_fail(e, "boundary term");
         if (stats) CK(cudaEventRecord(ctx->ev[3], ctx->stream), "event");
         int64_t edges = (int64_t)g->loop_vid.size();

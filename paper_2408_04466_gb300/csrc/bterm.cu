@@ -14,20 +14,33 @@
 // (the stereographic form: den = |a||b| + a.b + a_n|b| + b_n|a| regrouped).
 // s_x cancels when x points along -n = d; there s_x = (x1^2 + x2^2)/(|x| - x_n)
 // is used instead, so every factor is computed to a few ulps.  Each vertex's
-// (a1, a2, s_a) is computed once per query and shared by its two edges.
+// (a1, a2, s_a) is computed once per query and shared by its two edges, so
+// the rounding of a vertex's direction cancels to first order between them.
 //
-// Where the ray p + t d crosses edge AB, num changes sign with den < 0 and
-// Omega jumps by 4pi while chi_d jumps by -1.  Pairs with |Omega/2| within
-// 0.01 of pi take the sign of num from the exact perturbed predicate
-// -sign det[A-p, B-p, d_eps] (the same predicate the crossing count uses), so
-// both jumps happen at exactly the same place.
+// Exact-sign cases (rare, decided by the predicates the crossing count uses):
+// * the ray p + t d crosses edge AB: num changes sign with den < 0 and Omega
+//   jumps by 4pi while chi_d jumps by -1.  Pairs with |Omega/2| within 0.01 of
+//   pi take the sign of num from -sign det[A-p, B-p, d_eps];
+// * a boundary vertex within 1e-3 rad of the forward ray: its azimuth around
+//   the ray is ill-conditioned in float32, so both incident edges are
+//   recomputed in float64; a vertex exactly on the ray (decided exactly) is
+//   seen by the perturbed ray d_eps in the direction -dp (dp = the first of
+//   e_x, e_y, e_z not parallel to d, projected orthogonally to d), and its
+//   edges take the limit of Omega under that perturbation.
+//
+// Arithmetic: two queries per 64-bit register pair; plain add/mul/fma run as
+// packed f32x2 instructions (Blackwell), min/max, MUFU (rsqrt, reciprocal),
+// compares and selects per element.  atan2 is a degree-8 minimax polynomial
+// of atan(t) on [0, 1] (t = min/max of |num|, |den|) with octant fix-ups; its
+// coefficients were fitted by Lawson-weighted least squares to the relative
+// error of t*P(t^2) ~ atan(t) (1.5e-8 in exact arithmetic, <= 3 ulp in
+// float32 against float64 atan2).  Accumulation over edges is compensated
+// (Kahan).
 //
 // Layout: bseq holds the boundary loops as float4 records (x, y, z, w) in loop
 // order; each loop is v0 (w = 0), v1 .. v_{n-1} (w = 1), v0 again (w = 1).
-// w is the weight of the edge from the previous record.  All lanes of a warp
-// read the same record (broadcast); every thread carries K queries.
-#include <stdlib.h>
-
+// w = 1 marks an edge from the previous record.  All lanes of a warp read the
+// same record (broadcast); every thread carries 2*KP queries.
 #include "gwn_internal.h"
 #include "predicates.cuh"
 #include "query.cuh"
@@ -36,10 +49,85 @@ namespace gwn {
 
 #define GWN_CUT_THRESHOLD 3.1315926f   // pi - 0.01
 #define GWN_INV_2PI 0.15915494309189535f
+#define GWN_NEAR_RAY2 1e-6f            // (1e-3 rad)^2: slow path for vertices this close to the ray
 
-// Take the sign of num from the exact predicate (rare path).
+// ---- exact helpers for the slow path ---------------------------------------
+// exact sign of ((X-P) x D)_k (products of two float32 values are exact in float64)
+static __device__ __noinline__ int exact_cross_xd(float3 X, float3 P, float3 D, int k) {
+    int i = (k + 1) % 3, j = (k + 2) % 3;
+    Expansion<4> E;
+    E.init();
+    float xi = comp(X, i), xj = comp(X, j), pi = comp(P, i), pj = comp(P, j), di = comp(D, i), dj = comp(D, j);
+    E.add((double)xi * dj); E.add(-(double)pi * dj); E.add(-(double)xj * di); E.add((double)pj * di);
+    return E.sign();
+}
+
+// X lies exactly on the forward ray from P: (X-P) x D = 0 and (X-P).D > 0
+static __device__ __noinline__ bool on_forward_ray(float3 X, float3 P, float3 D) {
+    double x[3] = {(double)X.x - P.x, (double)X.y - P.y, (double)X.z - P.z};
+    double dd[3] = {D.x, D.y, D.z};
+    if (!(x[0] * dd[0] + x[1] * dd[1] + x[2] * dd[2] > 0.0)) return false;
+    for (int k = 0; k < 3; k++) {
+        int i = (k + 1) % 3, j = (k + 2) % 3;
+        double c = x[i] * dd[j] - x[j] * dd[i];
+        double bound = GWN_F64_BOUND * (fabs(x[i] * dd[j]) + fabs(x[j] * dd[i]));
+        if (fabs(c) > bound) return false;
+    }
+    for (int k = 0; k < 3; k++)
+        if (exact_cross_xd(X, P, D, k) != 0) return false;
+    return true;
+}
+
+// Omega/2 of edge A->B in float64, with the exact-sign rules above.
+static __device__ __noinline__ float slow_theta(float4 va, float4 vb, float3 p, Frame fr, Frame64 f,
+                                                unsigned long long *cnt, int *status) {
+    float3 A = make_float3(va.x, va.y, va.z), B = make_float3(vb.x, vb.y, vb.z);
+    float3 D = make_float3(fr.d[0], fr.d[1], fr.d[2]);
+    double a[3] = {(double)A.x - p.x, (double)A.y - p.y, (double)A.z - p.z};
+    double b[3] = {(double)B.x - p.x, (double)B.y - p.y, (double)B.z - p.z};
+    bool ra = on_forward_ray(A, p, D), rb = on_forward_ray(B, p, D);
+    double num, den, perm;
+    if (ra && rb) {
+        num = 0.0; den = 1.0; perm = 1.0;           // edge along the ray: limit 0
+    } else if (ra) {                                  // A seen in direction -dp
+        double bx0 = b[1] * f.dh[2] - b[2] * f.dh[1], bx1 = b[2] * f.dh[0] - b[0] * f.dh[2],
+               bx2 = b[0] * f.dh[1] - b[1] * f.dh[0];
+        num = f.dp[0] * bx0 + f.dp[1] * bx1 + f.dp[2] * bx2;
+        den = -(b[0] * f.dp[0] + b[1] * f.dp[1] + b[2] * f.dp[2]);
+        perm = fabs(f.dp[0] * bx0) + fabs(f.dp[1] * bx1) + fabs(f.dp[2] * bx2) + 1e-300;
+    } else if (rb) {                                  // B seen in direction -dp
+        double px0 = f.dp[1] * f.dh[2] - f.dp[2] * f.dh[1], px1 = f.dp[2] * f.dh[0] - f.dp[0] * f.dh[2],
+               px2 = f.dp[0] * f.dh[1] - f.dp[1] * f.dh[0];
+        num = a[0] * px0 + a[1] * px1 + a[2] * px2;
+        den = -(a[0] * f.dp[0] + a[1] * f.dp[1] + a[2] * f.dp[2]);
+        perm = fabs(a[0] * px0) + fabs(a[1] * px1) + fabs(a[2] * px2) + 1e-300;
+    } else {
+        double a1 = a[0] * f.e1[0] + a[1] * f.e1[1] + a[2] * f.e1[2];
+        double a2 = a[0] * f.e2[0] + a[1] * f.e2[1] + a[2] * f.e2[2];
+        double an = a[0] * f.n[0] + a[1] * f.n[1] + a[2] * f.n[2];
+        double b1 = b[0] * f.e1[0] + b[1] * f.e1[1] + b[2] * f.e1[2];
+        double b2 = b[0] * f.e2[0] + b[1] * f.e2[1] + b[2] * f.e2[2];
+        double bn = b[0] * f.n[0] + b[1] * f.n[1] + b[2] * f.n[2];
+        double ra2 = a1 * a1 + a2 * a2, rb2 = b1 * b1 + b2 * b2;
+        double la = sqrt(ra2 + an * an), lb = sqrt(rb2 + bn * bn);
+        double sa = an >= 0.0 ? la + an : ra2 / (la - an);
+        double sb = bn >= 0.0 ? lb + bn : rb2 / (lb - bn);
+        num = a1 * b2 - a2 * b1;
+        den = sa * sb + a1 * b1 + a2 * b2;
+        perm = fabs(a1 * b2) + fabs(a2 * b1) + 1e-300;
+    }
+    if (den < 0.0 && fabs(num) <= 64.0 * 1.1102230246251565e-16 * perm) {
+        int s = edge_sign_slow(A, B, p, D, cnt, status);   // sign(num) = -s
+        if (s > 0) num = -fabs(num);
+        else if (s < 0) num = fabs(num);
+    }
+    if (cnt) atomicAdd(&cnt[CNT_CUT_SIGN], 1ull);
+    return (float)atan2(num, den);
+}
+
+// Take the sign of num from the exact predicate (ray close to crossing AB).
 static __device__ __noinline__ float cut_fix(float th, float4 va, float4 vb, float3 p, Frame fr,
-                                      unsigned long long *cnt, int *status) {
+                                             unsigned long long *cnt, int *status) {
     float3 A = make_float3(va.x, va.y, va.z), B = make_float3(vb.x, vb.y, vb.z);
     float3 D = make_float3(fr.d[0], fr.d[1], fr.d[2]);
     int s = edge_sign_slow(A, B, p, D, cnt, status);   // sign(num) = -s
@@ -49,86 +137,7 @@ static __device__ __noinline__ float cut_fix(float th, float4 va, float4 vb, flo
     return th;
 }
 
-struct VertexProj {
-    float a1, a2, s;
-};
-
-__device__ __forceinline__ VertexProj project(float4 v, float px, float py, float pz, const Frame &fr) {
-    float ax = v.x - px, ay = v.y - py, az = v.z - pz;
-    VertexProj o;
-    o.a1 = fmaf(az, fr.e1[2], fmaf(ay, fr.e1[1], ax * fr.e1[0]));
-    o.a2 = fmaf(az, fr.e2[2], fmaf(ay, fr.e2[1], ax * fr.e2[0]));
-    float an = fmaf(az, fr.n[2], fmaf(ay, fr.n[1], ax * fr.n[0]));
-    float rp = fmaf(o.a1, o.a1, o.a2 * o.a2);
-    float r2 = fmaxf(fmaf(an, an, rp), 1e-37f);
-    float r = r2 * rsqrtf(r2);
-    o.s = an >= 0.f ? r + an : __fdividef(rp, r - an);
-    return o;
-}
-
-template <int K>
-__global__ void __launch_bounds__(256) bterm3d_kernel(const float4 *__restrict__ bseq, int nb, Frame fr,
-                                                      QuerySrc q, const int32_t *__restrict__ chi,
-                                                      float *__restrict__ w_out, float *__restrict__ b_out,
-                                                      unsigned long long *cnt, int *status) {
-    const int64_t base = (int64_t)blockIdx.x * blockDim.x * K + threadIdx.x;
-    float px[K], py[K], pz[K];
-    float pa1[K], pa2[K], ps[K], sum[K], cmp[K];
-#pragma unroll
-    for (int j = 0; j < K; j++) {
-        int64_t idx = base + (int64_t)j * blockDim.x;
-        float3 p = idx < q.n ? query_point3(q, idx) : make_float3(0.f, 0.f, 0.f);
-        px[j] = p.x; py[j] = p.y; pz[j] = p.z;
-        sum[j] = 0.f; cmp[j] = 0.f;
-    }
-    if (nb > 0) {
-        float4 v0 = __ldg(&bseq[0]);
-#pragma unroll
-        for (int j = 0; j < K; j++) {
-            VertexProj o = project(v0, px[j], py[j], pz[j], fr);
-            pa1[j] = o.a1; pa2[j] = o.a2; ps[j] = o.s;
-        }
-        float4 vprev = v0;
-#pragma unroll 2
-        for (int k = 1; k < nb; k++) {
-            float4 v = __ldg(&bseq[k]);
-#pragma unroll
-            for (int j = 0; j < K; j++) {
-                VertexProj o = project(v, px[j], py[j], pz[j], fr);
-                float num = fmaf(pa1[j], o.a2, -(pa2[j] * o.a1));
-                float den = fmaf(ps[j], o.s, fmaf(pa1[j], o.a1, pa2[j] * o.a2));
-                float th = atan2f(num, den);
-                if (fabsf(th) > GWN_CUT_THRESHOLD && v.w != 0.f)
-                    th = cut_fix(th, vprev, v, make_float3(px[j], py[j], pz[j]), fr, cnt, status);
-                // compensated (Kahan) accumulation of w * th
-                float y = fmaf(th, v.w, -cmp[j]);
-                float t = sum[j] + y;
-                cmp[j] = (t - sum[j]) - y;
-                sum[j] = t;
-                pa1[j] = o.a1; pa2[j] = o.a2; ps[j] = o.s;
-            }
-            vprev = v;
-        }
-    }
-#pragma unroll
-    for (int j = 0; j < K; j++) {
-        int64_t idx = base + (int64_t)j * blockDim.x;
-        if (idx < q.n) {
-            float B = (sum[j] - cmp[j]) * GWN_INV_2PI;
-            if (b_out) b_out[idx] = B;
-            if (w_out) w_out[idx] = B + (chi ? (float)chi[idx] : 0.f);
-        }
-    }
-}
-
-// ---- packed variant: two queries per 64-bit register pair (f32x2) ----------
-// Blackwell executes add/sub/mul/fma.rn.f32x2 on two float32 lanes per
-// instruction.  Every per-query operation that is a plain add/mul/fma runs
-// packed on a pair of queries; min/max, MUFU (rsqrt, reciprocal), compares and
-// selects run per element.  atan2 is a degree-8 minimax polynomial of
-// atan(t) on [0, 1] (t = min/max of |num|, |den|) with octant fix-ups; the
-// coefficients were fitted by Lawson-weighted least squares to the relative
-// error of t*P(t^2) ~ atan(t) (max 1.5e-8 in exact arithmetic).
+// ---- packed float32 pairs ---------------------------------------------------
 typedef unsigned long long f2;
 
 __device__ __forceinline__ f2 pk(float a, float b) {
@@ -146,7 +155,7 @@ __device__ __forceinline__ float hi2(f2 v) {
     asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
     return b;
 }
-// MUFU reciprocal (rcp.approx: about 1 ulp); arguments here are normal floats
+// MUFU reciprocal (rcp.approx, about 1 ulp); arguments here are normal floats
 __device__ __forceinline__ float frcp(float x) {
     float r;
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
@@ -198,12 +207,13 @@ __device__ __forceinline__ f2 atan2_2(f2 y, f2 x) {
 }
 
 template <int KP>   // KP query pairs per thread
-__global__ void __launch_bounds__(256) bterm3d_x2_kernel(const float4 *__restrict__ bseq, int nb, Frame fr,
-                                                         QuerySrc q, const int32_t *__restrict__ chi,
-                                                         float *__restrict__ w_out, float *__restrict__ b_out,
-                                                         unsigned long long *cnt, int *status) {
+__global__ void __launch_bounds__(256) bterm3d_kernel(const float4 *__restrict__ bseq, int nb, Frame fr, Frame64 f64,
+                                                      QuerySrc q, const int32_t *__restrict__ chi,
+                                                      float *__restrict__ w_out, float *__restrict__ b_out,
+                                                      unsigned long long *cnt, int *status) {
     const int64_t base = (int64_t)blockIdx.x * blockDim.x * (2 * KP) + threadIdx.x;
     f2 px[KP], py[KP], pz[KP], pa1[KP], pa2[KP], ps[KP], sum[KP], cmp[KP];
+    int pnear[KP];
     const f2 e1x = pk(fr.e1[0], fr.e1[0]), e1y = pk(fr.e1[1], fr.e1[1]), e1z = pk(fr.e1[2], fr.e1[2]);
     const f2 e2x = pk(fr.e2[0], fr.e2[0]), e2y = pk(fr.e2[1], fr.e2[1]), e2z = pk(fr.e2[2], fr.e2[2]);
     const f2 nx = pk(fr.n[0], fr.n[0]), ny = pk(fr.n[1], fr.n[1]), nz = pk(fr.n[2], fr.n[2]);
@@ -215,7 +225,9 @@ __global__ void __launch_bounds__(256) bterm3d_x2_kernel(const float4 *__restric
         px[j] = pk(p0.x, p1.x); py[j] = pk(p0.y, p1.y); pz[j] = pk(p0.z, p1.z);
         sum[j] = pk(0.f, 0.f); cmp[j] = pk(0.f, 0.f);
     }
-    auto project = [&](float4 v, int j, f2 &a1, f2 &a2, f2 &s) {
+    // (a1, a2, s) of record v for query pair j; `near` gets one bit per
+    // element whose vertex lies within 1e-3 rad of the forward ray
+    auto project = [&](float4 v, int j, f2 &a1, f2 &a2, f2 &s, int &near) {
         f2 ax = sub2(pk(v.x, v.x), px[j]), ay = sub2(pk(v.y, v.y), py[j]), az = sub2(pk(v.z, v.z), pz[j]);
         a1 = fma2(az, e1z, fma2(ay, e1y, mul2(ax, e1x)));
         a2 = fma2(az, e2z, fma2(ay, e2y, mul2(ax, e2x)));
@@ -226,12 +238,14 @@ __global__ void __launch_bounds__(256) bterm3d_x2_kernel(const float4 *__restric
         f2 r = mul2(pk(r20, r21), pk(rsqrtf(r20), rsqrtf(r21)));
         f2 sp = add2(r, an), dm = sub2(r, an);
         f2 sn = mul2(rp, pk(frcp(lo2(dm)), frcp(hi2(dm))));
-        s = pk(lo2(an) >= 0.f ? lo2(sp) : lo2(sn), hi2(an) >= 0.f ? hi2(sp) : hi2(sn));
+        float an0 = lo2(an), an1 = hi2(an);
+        s = pk(an0 >= 0.f ? lo2(sp) : lo2(sn), an1 >= 0.f ? hi2(sp) : hi2(sn));
+        near = ((an0 < 0.f) & (lo2(rp) < GWN_NEAR_RAY2 * r20)) | (((an1 < 0.f) & (hi2(rp) < GWN_NEAR_RAY2 * r21)) << 1);
     };
     if (nb > 0) {
         float4 v0 = __ldg(&bseq[0]);
 #pragma unroll
-        for (int j = 0; j < KP; j++) project(v0, j, pa1[j], pa2[j], ps[j]);
+        for (int j = 0; j < KP; j++) project(v0, j, pa1[j], pa2[j], ps[j], pnear[j]);
         float4 vprev = v0;
         for (int k = 1; k < nb; k++) {
             float4 v = __ldg(&bseq[k]);
@@ -239,23 +253,29 @@ __global__ void __launch_bounds__(256) bterm3d_x2_kernel(const float4 *__restric
 #pragma unroll
             for (int j = 0; j < KP; j++) {
                 f2 a1, a2, s;
-                project(v, j, a1, a2, s);
+                int near;
+                project(v, j, a1, a2, s, near);
                 if (edge) {
                     f2 num = sub2(mul2(pa1[j], a2), mul2(pa2[j], a1));
                     f2 den = fma2(ps[j], s, fma2(pa1[j], a1, mul2(pa2[j], a2)));
                     f2 th = atan2_2(num, den);
                     float t0 = lo2(th), t1 = hi2(th);
-                    if (fabsf(t0) > GWN_CUT_THRESHOLD)
+                    int slow = pnear[j] | near;
+                    if (slow & 1)
+                        t0 = slow_theta(vprev, v, make_float3(lo2(px[j]), lo2(py[j]), lo2(pz[j])), fr, f64, cnt, status);
+                    else if (fabsf(t0) > GWN_CUT_THRESHOLD)
                         t0 = cut_fix(t0, vprev, v, make_float3(lo2(px[j]), lo2(py[j]), lo2(pz[j])), fr, cnt, status);
-                    if (fabsf(t1) > GWN_CUT_THRESHOLD)
+                    if (slow & 2)
+                        t1 = slow_theta(vprev, v, make_float3(hi2(px[j]), hi2(py[j]), hi2(pz[j])), fr, f64, cnt, status);
+                    else if (fabsf(t1) > GWN_CUT_THRESHOLD)
                         t1 = cut_fix(t1, vprev, v, make_float3(hi2(px[j]), hi2(py[j]), hi2(pz[j])), fr, cnt, status);
                     th = pk(t0, t1);
-                    f2 y = sub2(th, cmp[j]);
+                    f2 y = sub2(th, cmp[j]);          // compensated (Kahan) accumulation
                     f2 t = add2(sum[j], y);
                     cmp[j] = sub2(sub2(t, sum[j]), y);
                     sum[j] = t;
                 }
-                pa1[j] = a1; pa2[j] = a2; ps[j] = s;
+                pa1[j] = a1; pa2[j] = a2; ps[j] = s; pnear[j] = near;
             }
             vprev = v;
         }
@@ -274,32 +294,18 @@ __global__ void __launch_bounds__(256) bterm3d_x2_kernel(const float4 *__restric
     }
 }
 
-cudaError_t launch_bterm3d(const float4 *bseq, int64_t n_bseq, const Frame &fr, const QuerySrc &q,
-                           const int32_t *chi, float *w_out, float *b_out, unsigned long long *cnt,
-                           int *status, int sm_count, cudaStream_t st) {
+cudaError_t launch_bterm3d(const float4 *bseq, int64_t n_bseq, const Frame &fr, const Frame64 &f64,
+                           const QuerySrc &q, const int32_t *chi, float *w_out, float *b_out,
+                           unsigned long long *cnt, int *status, int sm_count, cudaStream_t st) {
     (void)sm_count;
     if (q.n == 0) return cudaSuccess;
+    constexpr int KP = 2;
     const int threads = 256;
-    static int impl = -1;
-    if (impl < 0) {
-        const char *e = getenv("GWN_BTERM_IMPL");
-        impl = e ? atoi(e) : 0;
-    }
-    if (impl == 1) {
-        constexpr int KP = 2;
-        int64_t per_block = (int64_t)threads * 2 * KP;
-        int64_t blocks = (q.n + per_block - 1) / per_block;
-        if (blocks > 0x7fffffff) return cudaErrorInvalidValue;
-        bterm3d_x2_kernel<KP><<<(unsigned)blocks, threads, 0, st>>>(bseq, (int)n_bseq, fr, q, chi, w_out, b_out,
-                                                                   cnt, status);
-        return cudaGetLastError();
-    }
-    constexpr int K = 4;
-    int64_t per_block = (int64_t)threads * K;
+    int64_t per_block = (int64_t)threads * 2 * KP;
     int64_t blocks = (q.n + per_block - 1) / per_block;
     if (blocks > 0x7fffffff) return cudaErrorInvalidValue;
-    bterm3d_kernel<K><<<(unsigned)blocks, threads, 0, st>>>(bseq, (int)n_bseq, fr, q, chi, w_out, b_out,
-                                                            cnt, status);
+    bterm3d_kernel<KP><<<(unsigned)blocks, threads, 0, st>>>(bseq, (int)n_bseq, fr, f64, q, chi, w_out, b_out, cnt,
+                                                             status);
     return cudaGetLastError();
 }
 

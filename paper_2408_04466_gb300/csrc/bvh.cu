@@ -313,10 +313,14 @@ __global__ void pack_kernel(const int2 *__restrict__ child, int64_t n, const flo
 }
 
 __global__ void tris_kernel(const float *__restrict__ V, const int32_t *__restrict__ F,
-                            const int32_t *__restrict__ sorted_tri, int64_t n, float4 *__restrict__ tris) {
+                            const int32_t *__restrict__ sorted_tri, int64_t n, float4 *__restrict__ tris,
+                            const float4 *__restrict__ tbox_xy, const float *__restrict__ tbox_z,
+                            float4 *__restrict__ tbox) {
     int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     int t = sorted_tri[k];
+    tbox[2 * k] = tbox_xy[t];
+    tbox[2 * k + 1] = make_float4(tbox_z[t], 0.f, 0.f, 0.f);
     for (int c = 0; c < 3; c++) {
         int vi = F[3 * (int64_t)t + c];
         tris[3 * k + c] = make_float4(V[3 * (int64_t)vi], V[3 * (int64_t)vi + 1], V[3 * (int64_t)vi + 2], 0.f);
@@ -342,6 +346,8 @@ void bvh_free(MeshBvh &b) {
     if (b.nodes) cudaFree(b.nodes);
     if (b.tris) cudaFree(b.tris);
     if (b.tri_id) cudaFree(b.tri_id);
+    if (b.tbox) cudaFree(b.tbox);
+    b.tbox = nullptr;
     b.nodes = nullptr;
     b.tris = nullptr;
     b.tri_id = nullptr;
@@ -377,6 +383,7 @@ cudaError_t bvh_build(gwn_geom *g, const Frame &fr, cudaStream_t st) {
     }
     GWN_TRY(cudaMalloc(&b.tris, sizeof(float4) * 3 * n));
     GWN_TRY(cudaMalloc(&b.tri_id, sizeof(int32_t) * n));
+    GWN_TRY(cudaMalloc(&b.tbox, sizeof(float4) * 2 * n));
     GWN_TRY(cudaMalloc(&tbox_xy, sizeof(float4) * n));
     GWN_TRY(cudaMalloc(&tbox_z, sizeof(float) * n));
     GWN_TRY(cudaMalloc(&cen, sizeof(float4) * n));
@@ -408,7 +415,7 @@ cudaError_t bvh_build(gwn_geom *g, const Frame &fr, cudaStream_t st) {
             int32_t *tv = v0; v0 = v1; v1 = tv;
         }
         GWN_TRY(cudaMemcpyAsync(b.tri_id, v0, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, st));
-        tris_kernel<<<blocks_for(n, 256), 256, 0, st>>>(g->dV, g->dF, v0, n, b.tris);
+        tris_kernel<<<blocks_for(n, 256), 256, 0, st>>>(g->dV, g->dF, v0, n, b.tris, tbox_xy, tbox_z, b.tbox);
         GWN_TRY(cudaGetLastError());
         unsigned rbits = 0;
         GWN_TRY(cudaMemcpyAsync(&rbits, rad, sizeof(unsigned), cudaMemcpyDeviceToHost, st));

@@ -40,6 +40,12 @@ struct Frame {
     float d[3];
 };
 
+// The same frame in float64 plus the symbolic-perturbation direction dp: the
+// first of e_x, e_y, e_z not parallel to d, minus its component along d.
+struct Frame64 {
+    double e1[3], e2[3], n[3], dh[3], dp[3];
+};
+
 // Grid or point query source (device side view).
 struct QuerySrc {
     int kind;             // GWN_QUERY_POINTS / GWN_QUERY_GRID
@@ -66,6 +72,7 @@ struct MeshBvh {
     BvhNode *nodes = nullptr;  // n - 1
     float4 *tris = nullptr;    // 3 float4 per sorted triangle (xyz of v0, v1, v2)
     int32_t *tri_id = nullptr; // original triangle index per sorted position
+    float4 *tbox = nullptr;    // 2 float4 per sorted triangle: (x0, x1, y0, y1), (zmax, 0, 0, 0)
     int root = 0;              // ref of the root
     float scene_radius = 0.f;  // max |v|_2 over the mesh vertices
     Frame frame;
@@ -147,6 +154,7 @@ void set_error(const std::string &msg);
 gwn_status cuda_fail(cudaError_t e, const char *what);
 void *arena_get(gwn_ctx *ctx, int slot, size_t bytes, cudaError_t *err);
 Frame make_frame(const float d[3]);
+Frame64 make_frame64(const float d[3]);
 
 // ---- launchers (return the first CUDA error) -------------------------------
 cudaError_t bvh_build(gwn_geom *g, const Frame &fr, cudaStream_t st);
@@ -155,9 +163,9 @@ void bvh_free(MeshBvh &b);
 cudaError_t launch_traverse(const MeshBvh &b, const QuerySrc &q, int32_t *chi, unsigned long long *cnt,
                             int *status, int sm_count, cudaStream_t st);
 
-cudaError_t launch_bterm3d(const float4 *bseq, int64_t n_bseq, const Frame &fr, const QuerySrc &q,
-                           const int32_t *chi, float *w_out, float *b_out, unsigned long long *cnt,
-                           int *status, int sm_count, cudaStream_t st);
+cudaError_t launch_bterm3d(const float4 *bseq, int64_t n_bseq, const Frame &fr, const Frame64 &f64,
+                           const QuerySrc &q, const int32_t *chi, float *w_out, float *b_out,
+                           unsigned long long *cnt, int *status, int sm_count, cudaStream_t st);
 
 cudaError_t launch_grad_p(const float4 *bseq, int64_t nb, const QuerySrc &q, const float *grad_w, float *grad_p,
                           cudaStream_t st);

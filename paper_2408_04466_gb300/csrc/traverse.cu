@@ -13,6 +13,8 @@
 // the traversal stack holds at most the tree depth, bounded by GWN_STACK;
 // overflow or the iteration limit sets a status bit and a counter and marks
 // the query result as invalid (INT32_MIN).
+#include <stdlib.h>
+
 #include "gwn_internal.h"
 #include "predicates.cuh"
 #include "query.cuh"
@@ -101,6 +103,90 @@ __global__ void __launch_bounds__(256) traverse_kernel(const BvhNode *__restrict
     chi[idx] = bad ? INT32_MIN : acc;
 }
 
+// Warp-packet traversal for grid queries: the 32 rays of a warp (a 4x4x2
+// grid tile, neighbours in the projection plane) walk the tree together.
+// The stack is warp-uniform (every lane holds the same copy); at a node each
+// lane tests its own ray against both child boxes and the warp descends into
+// a child if any lane's ray hits it; at a leaf only the lanes whose ray box
+// hits the triangle run the exact crossing test.  Node and triangle loads are
+// warp-uniform (one broadcast per warp).  Lanes outside the grid take part
+// with an empty box.
+__global__ void __launch_bounds__(256) traverse_packet_kernel(const BvhNode *__restrict__ nodes,
+                                                              const float4 *__restrict__ tris,
+                                                              const float4 *__restrict__ tbox, int root, Frame fr,
+                                                              TravParams tp, QuerySrc q, int32_t *__restrict__ chi,
+                                                              unsigned long long *cnt, int *status) {
+    int64_t idx = grid_tile_query(q);
+    bool valid = idx >= 0 && idx < q.n;
+    float3 p = valid ? query_point3(q, idx) : make_float3(0.f, 0.f, 0.f);
+    float3 D = make_float3(fr.d[0], fr.d[1], fr.d[2]);
+    float p1 = fmaf(p.z, fr.e1[2], fmaf(p.y, fr.e1[1], p.x * fr.e1[0]));
+    float p2 = fmaf(p.z, fr.e2[2], fmaf(p.y, fr.e2[1], p.x * fr.e2[0]));
+    float p3 = fmaf(p.z, fr.dh[2], fmaf(p.y, fr.dh[1], p.x * fr.dh[0]));
+    float pad = fmaf(tp.pad_rel, fabsf(p.x) + fabsf(p.y) + fabsf(p.z), tp.pad_abs);
+    float xlo = p1 - pad, xhi = p1 + pad, ylo = p2 - pad, yhi = p2 + pad, zlo = p3 - pad;
+    if (!valid) { xlo = 3.4e38f; xhi = -3.4e38f; }     // never hits
+    int acc = 0;
+    int stack[GWN_STACK];
+    int sp = 0;
+    int node = root;
+    bool bad = false;
+    for (int64_t iter = 0;; iter++) {
+        if (iter > tp.max_iter) {
+            if ((threadIdx.x & 31) == 0) {
+                atomicOr(status, ST_TIMEOUT);
+                if (cnt) atomicAdd(&cnt[CNT_TIMEOUT], 1ull);
+            }
+            bad = true;
+            break;
+        }
+        if (node >= tp.n_internal || ~node >= tp.n_leaves) {   // corrupt reference: report, never read
+            atomicOr(status, ST_BAD_INPUT);
+            bad = true;
+            break;
+        }
+        if (node < 0) {
+            int t = ~node;
+            float4 bx = __ldg(&tbox[2 * t]), bz = __ldg(&tbox[2 * t + 1]);
+            bool hit = box_hit(bx.x, bx.y, bx.z, bx.w, bz.x, xlo, xhi, ylo, yhi, zlo);
+            if (hit) {
+                float4 a = __ldg(&tris[3 * t]), b = __ldg(&tris[3 * t + 1]), c = __ldg(&tris[3 * t + 2]);
+                if (cnt) atomicAdd(&cnt[CNT_TRI_TESTS], 1ull);
+                acc += tri_crossing(make_float3(a.x, a.y, a.z), make_float3(b.x, b.y, b.z),
+                                    make_float3(c.x, c.y, c.z), p, D, cnt, status);
+            }
+            if (sp == 0) break;
+            node = stack[--sp];
+            continue;
+        }
+        const BvhNode nd = nodes[node];
+        bool h0 = box_hit(nd.lo.x, nd.lo.y, nd.lo.z, nd.lo.w, nd.z.x, xlo, xhi, ylo, yhi, zlo);
+        bool h1 = box_hit(nd.hi.x, nd.hi.y, nd.hi.z, nd.hi.w, nd.z.y, xlo, xhi, ylo, yhi, zlo);
+        bool a0 = __any_sync(0xffffffffu, h0), a1 = __any_sync(0xffffffffu, h1);
+        int c0 = __float_as_int(nd.z.z), c1 = __float_as_int(nd.z.w);
+        if (a0 && a1) {
+            if (sp >= GWN_STACK) {
+                if ((threadIdx.x & 31) == 0) {
+                    atomicOr(status, ST_STACK_OVERFLOW);
+                    if (cnt) atomicAdd(&cnt[CNT_STACK_OVERFLOW], 1ull);
+                }
+                bad = true;
+                break;
+            }
+            stack[sp++] = c1;
+            node = c0;
+        } else if (a0) {
+            node = c0;
+        } else if (a1) {
+            node = c1;
+        } else {
+            if (sp == 0) break;
+            node = stack[--sp];
+        }
+    }
+    if (valid) chi[idx] = bad ? INT32_MIN : acc;
+}
+
 // Root is a single leaf (one triangle) or the mesh is empty.
 __global__ void traverse_single_kernel(const float4 *__restrict__ tris, int ntri, Frame fr, QuerySrc q,
                                        int32_t *__restrict__ chi, unsigned long long *cnt, int *status) {
@@ -147,8 +233,17 @@ cudaError_t launch_traverse(const MeshBvh &b, const QuerySrc &q, int32_t *chi, u
     tp.n_leaves = (int)b.n;
     int64_t tblocks = q.kind == GWN_QUERY_GRID ? grid_tile_blocks(q) : (q.n + 255) / 256;
     if (tblocks > 0x7fffffff) return cudaErrorInvalidValue;
-    traverse_kernel<<<(unsigned)tblocks, 256, 0, st>>>(b.nodes, b.tris, b.root, b.frame, tp, q, chi, cnt,
-                                                       status);
+    static int impl = -1;
+    if (impl < 0) {
+        const char *e = getenv("GWN_TRAV_IMPL");
+        impl = e ? atoi(e) : 1;
+    }
+    if (q.kind == GWN_QUERY_GRID && impl == 1 && b.tbox)
+        traverse_packet_kernel<<<(unsigned)tblocks, 256, 0, st>>>(b.nodes, b.tris, b.tbox, b.root, b.frame, tp, q,
+                                                                  chi, cnt, status);
+    else
+        traverse_kernel<<<(unsigned)tblocks, 256, 0, st>>>(b.nodes, b.tris, b.root, b.frame, tp, q, chi, cnt,
+                                                           status);
     return cudaGetLastError();
 }
 

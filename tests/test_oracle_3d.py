@@ -374,3 +374,27 @@ def test_gradient_against_fd_biot_savart_and_invariants():
     interior = np.setdiff1d(np.unique(m.F), bverts)
     assert np.abs(gV1[interior]).max() < 1e-10
     assert np.abs(gV1[bverts]).max() > 1e-4
+
+
+def _grid_plate():
+    V = np.array([[x, y, 0.0] for x in range(4) for y in range(4)], np.float32)
+    F = []
+    for i in range(3):
+        for j in range(3):
+            a, b, c, dd = 4 * i + j, 4 * (i + 1) + j, 4 * (i + 1) + j + 1, 4 * i + j + 1
+            F += [(a, b, c), (a, c, dd)]
+    return V, np.array(F, np.int32)
+
+
+def test_rays_exactly_through_boundary_vertices():
+    """Axis-aligned directions on grid-aligned data: rays pass exactly through
+    boundary vertices and along edge lines.  The one-shot value (crossing count
+    under the perturbed direction + boundary term as the limit under the same
+    perturbation) must equal the per-triangle definition."""
+    V, F = _grid_plate()
+    g = np.arange(-1, 5, 0.5, dtype=np.float32)
+    P = np.array([[x, y, z] for x in g for y in g for z in (-1.0, -0.5, 0.5, 1.0)], np.float32)
+    wv = oracle.w3d_vos(V, F, P)
+    for d in ([0, 0, 1], [0, 0, -1], [1, 0, 0], [0, 1, 1], [1, 1, 0], [0, 0, 3]):
+        w, chi, B = oracle.w3d_oneshot(V, F, P, np.array(d, np.float32))
+        assert np.abs(w - wv).max() < 1e-12, d
