@@ -333,6 +333,112 @@ def run_gpu(args):
     return 0
 
 
+# ----------------------------------------------------------------------------
+# other workloads (parity-test configurations), measured with --workload
+# ----------------------------------------------------------------------------
+def _timed(fn, steps, warmup, stream):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for a, b in ev:
+        a.record(stream)
+        fn()
+        b.record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in ev]
+
+
+def run_other(args):
+    import torch
+    import gen
+    import oracle
+    from paper_2408_04466_gb300 import build as gbuild
+    gbuild.build()
+    oracle.build()
+    import paper_2408_04466_gb300 as gwn
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(device=dev)
+    torch.cuda.set_stream(stream)
+    ctx = gwn.Context(0, stream)
+    name = args.workload
+    out = {"workload": name, "unit": UNIT, "higher_is_better": True, "data": "synthetic", "n_gpus": 1,
+           "steps": args.steps, "warmup": args.warmup}
+    if name in ("circle_chain_fp64", "star_chains"):
+        ch = gen.bezier_circle_chain() if name == "circle_chain_fp64" else gen.star_chains()
+        geo = gwn.Bezier2D(ctx, ch.ctrl, ch.offsets)
+        grids = [gwn.Grid(g.lo, g.hi, g.dims) for g in ch.grids]
+        nq = sum(g.n for g in grids)
+        if name == "circle_chain_fp64":
+            w = torch.empty(nq, dtype=torch.float64, device=dev)
+            fn = lambda: geo.eval(grids[0])
+            out["dtype"] = "f64"
+        else:
+            w = torch.empty(nq, dtype=torch.float32, device=dev)
+            fn = lambda: geo.eval_batch(grids, out=w)
+            out["dtype"] = "f32"
+        ms = _timed(fn, args.steps, args.warmup, stream)
+        out["ms_per_step"] = statistics.median(ms)
+        out["value"] = nq / (out["ms_per_step"] * 1e-3)
+        out["queries_per_step"] = nq
+        if name == "star_chains":
+            out["plan"] = dict(zip(("threads", "rows_per_item"), geo.batch_plan()))
+        # brute-force comparator (per-segment quadrature) on one chain's grid
+        c0 = int(np.argmax(np.diff(ch.offsets))) if name == "star_chains" else 0
+        ctrl0 = ch.ctrl[ch.offsets[c0]:ch.offsets[c0 + 1]]
+        g0 = ch.grids[c0]
+        one = gwn.Bezier2D(ctx, ctrl0, [0, len(ctrl0)])
+        gq = gwn.Grid(g0.lo, g0.hi, g0.dims)
+        bms = _timed(lambda: one.bruteforce(gq), 3, 1, stream)
+        out["bruteforce_gpu"] = {"value": gq.n / (statistics.median(bms) * 1e-3), "unit": UNIT,
+                                 "sample": f"chain {c0} ({(len(ctrl0) - 1) // 3} segments) on its {g0.dims} grid"}
+        P = gen.grid_points(g0, np.float64)[:4096]
+        t0 = time.perf_counter()
+        oracle.w2d_closed_x(ctrl0.astype(np.float64), P)
+        dt = time.perf_counter() - t0
+        out["cpu_baseline"] = {"value": len(P) / dt, "unit": UNIT, "cores": oracle.default_threads(), "kind": "oracle",
+                               "sample": f"{len(P)} queries of chain {c0}, FP64 closed form (+x ray per query)"}
+    elif name == "slit_torus":
+        m = gen.slit_torus()
+        mesh = gwn.Mesh(ctx, m.V, m.F)
+        mesh.prepare(m.d)
+        Pt = torch.as_tensor(m.points).to(dev)
+        gw = torch.ones(len(Pt), device=dev)
+        w = torch.empty(len(Pt), dtype=torch.float32, device=dev)
+
+        def step():
+            mesh.eval(gwn.Points(Pt), m.d, out=w)
+            mesh.backward(Pt, gw)
+        ms = _timed(step, args.steps, args.warmup, stream)
+        fms = _timed(lambda: mesh.eval(gwn.Points(Pt), m.d, out=w), args.steps, args.warmup, stream)
+        out.update({"metric": "queries/s, forward + backward (dw/dp, dw/dV)", "dtype": "f32",
+                    "ms_per_step": statistics.median(ms), "forward_ms": statistics.median(fms),
+                    "value": len(Pt) / (statistics.median(ms) * 1e-3), "queries_per_step": len(Pt),
+                    "boundary_edges": mesh.info()["n_boundary_edges"], "triangles": int(len(m.F))})
+    elif name == "holey_heightfield":
+        m = gen.holey_heightfield()
+        mesh = gwn.Mesh(ctx, m.V, m.F)
+        t0 = time.perf_counter()
+        mesh.prepare(m.d)
+        torch.cuda.synchronize()
+        prep = time.perf_counter() - t0
+        g = gwn.Grid(m.grid.lo, m.grid.hi, m.grid.dims)
+        w = torch.empty(g.n, dtype=torch.float32, device=dev)
+        st = mesh.eval(g, m.d, stats=True, out=w)["stats"]
+        ms = _timed(lambda: mesh.eval(g, m.d, out=w), args.steps, min(args.warmup, 1), stream)
+        out.update({"metric": METRIC, "dtype": "f32", "ms_per_step": statistics.median(ms),
+                    "value": g.n / (statistics.median(ms) * 1e-3), "queries_per_step": g.n,
+                    "boundary_edges": mesh.info()["n_boundary_edges"], "boundary_loops": mesh.info()["n_loops"],
+                    "triangles": int(len(m.F)), "lbvh_build_ms": 1e3 * prep,
+                    "kernels": {"traverse_ms": st["ms_traverse"], "bterm3d_ms": st["ms_boundary"]}})
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    print(json.dumps(out))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -344,11 +450,16 @@ def main():
     ap.add_argument("--grid", type=int, default=256, help="grid resolution (256 = the benchmark workload; "
                                                           "smaller values only for profiling captures)")
     ap.add_argument("--no-extras", action="store_true", help="skip comparator, e2e and CPU baseline legs")
+    ap.add_argument("--workload", default="icosphere_cap",
+                    choices=["icosphere_cap", "circle_chain_fp64", "star_chains", "slit_torus", "holey_heightfield"],
+                    help="icosphere_cap is the benchmark; the others print their own measurement line")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload != "icosphere_cap":
+        return run_other(args)
     return run_gpu(args)
 
 

@@ -9,6 +9,16 @@ import oracle
 
 pytestmark = pytest.mark.gpu
 RTOL = 1e-4
+# Where dw/dp nearly vanishes, the float32 sum over boundary edges cancels
+# and relative error loses meaning; the per-query bar is
+#   |g_gpu - g_oracle| <= RTOL * |g_oracle| + ATOL,
+# with ATOL far below the gradient magnitudes of these workloads (1e-2 .. 1):
+# a float32 sum of ~2000 edge terms of size ~1e-3 .. 1 cancels to ~1e-7.
+ATOL = 1e-7
+
+
+def _close(g, ref):
+    return np.linalg.norm(g - ref) <= RTOL * np.linalg.norm(ref) + ATOL
 
 
 @pytest.fixture(scope="module")
@@ -40,7 +50,7 @@ def test_small_torus_gradients(gwn, ctx):
     gV = gV.cpu().numpy().astype(np.float64)
     ogp, ogV = oracle.grad3d_vos(m.V, m.F, P, gw=gw.astype(np.float64))
     for q in range(len(P)):
-        assert _rel(gp[q], ogp[q]) < RTOL, q
+        assert _close(gp[q], ogp[q]), (q, gp[q], ogp[q])
     assert _rel(gV, ogV) < RTOL
     # finite differences of the oracle's w on a few queries
     for q in range(4):
@@ -101,7 +111,7 @@ def test_torus_full_size_sampled(gwn, ctx):
     ogp, _ = oracle.grad3d_vos(m.V, m.F, P, want_V=False)
     g = gp.cpu().numpy()[idx].astype(np.float64)
     for q in range(len(idx)):
-        assert _rel(g[q], ogp[q]) < RTOL, q
+        assert _close(g[q], ogp[q]), (q, g[q], ogp[q])
     # translation invariance of the summed gradients: sum_q dw/dp = -sum_v dw/dV
     s_p = gp.double().sum(0).cpu().numpy()
     s_v = gV.double().sum(0).cpu().numpy()
