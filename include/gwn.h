@@ -238,6 +238,32 @@ GWN_API gwn_status gwn_batch_plan_get(gwn_geom *g, int32_t *threads, int32_t *ro
 GWN_API gwn_status gwn_backward(gwn_geom *g, const gwn_queries *q, const float *d,
                                 const float *grad_w, float *grad_p, float *grad_V);
 
+/* Mesh evaluation that allocates no device memory (no counterpart in the
+ * paper: a deployment variant of gwn_eval for device-resident points).
+ *
+ * For callers that reserve all device memory up front and cannot call
+ * cudaMalloc afterwards -- it can stall the whole device and can fail under
+ * memory pressure in the middle of a request.  gwn_eval keeps the per-query
+ * crossing counts (scratch between the traversal and the boundary-term
+ * kernel) in a buffer it allocates on demand; this entry point keeps them in
+ * a fixed array inside the library instead and calls no cudaMalloc,
+ * cudaFree or allocating library routine.
+ *   pts:   device float32 [n x 3] query points; n <= GWN_NOALLOC_MAX_QUERIES
+ *          (larger n returns GWN_E_INVALID without doing any work).
+ *   d:     the direction the mesh was prepared for with gwn_mesh_prepare
+ *          (preparation allocates, so it must happen earlier); otherwise
+ *          GWN_E_INVALID.
+ *   w_out: device float32 [n]; same values as gwn_eval on the same input.
+ * The array takes 16 MiB on every GPU that loads the library, until the
+ * process exits.  The first call on a device resolves the array's device
+ * address (cudaGetSymbolAddress with that device current); make that first
+ * call before any stream capture.  All calls share the one array and it keeps
+ * the last call's contents: calls whose work overlaps on the GPU (other
+ * streams or contexts on the same device) race on it -- serialise them. */
+#define GWN_NOALLOC_MAX_QUERIES 4194304
+GWN_API gwn_status gwn_eval_points_noalloc(gwn_geom *g, const float *pts, int64_t n, const float d[3],
+                                           float *w_out);
+
 /* Brute-force comparator on the same device: 3D, the sum of per-triangle
  * solid angles over every triangle (float32); 2D, per-segment angle integral
  * by fixed-order Gauss-Legendre on an adaptive subdivision.  w_out as for

@@ -8,6 +8,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libgwn.so")
 
 GWN_OK = 0
+NOALLOC_MAX_QUERIES = 4194304
 STATUS = {0: "GWN_OK", -1: "GWN_E_INVALID", -2: "GWN_E_OOM", -3: "GWN_E_CUDA", -4: "GWN_E_STACK_OVERFLOW",
           -5: "GWN_E_TIMEOUT", -6: "GWN_E_UNSUPPORTED", -7: "GWN_E_INTERNAL"}
 MEM_HOST, MEM_DEVICE = 0, 1
@@ -68,6 +69,7 @@ _SIGS = {
     "gwn_batch_plan_get": (ST, [P, C.POINTER(I32), C.POINTER(I32)]),
     "gwn_backward": (ST, [P, C.POINTER(gwn_queries), P, P, P, P]),
     "gwn_eval_bruteforce": (ST, [P, C.POINTER(gwn_queries), P]),
+    "gwn_eval_points_noalloc": (ST, [P, P, I64, P, P]),
 }
 
 _lib = None
