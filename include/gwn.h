@@ -106,7 +106,7 @@ typedef struct gwn_queries {
 typedef struct gwn_stats {
     int64_t n_queries;
     int64_t n_pairs;            /* query x boundary-edge (3D) or row x piece (2D) pairs */
-    int64_t n_cut_sign;         /* boundary-term pairs whose sign came from a predicate */
+    int64_t n_cut_sign;         /* boundary-term pairs taken off the float32 path (exact branch or float64) */
     int64_t n_fp64_filter;      /* predicates settled by the float64 filter */
     int64_t n_exact;            /* predicates settled by exact expansion arithmetic */
     int64_t n_stack_overflow;   /* traversals that overflowed (result invalid) */
@@ -115,6 +115,8 @@ typedef struct gwn_stats {
     float ms_traverse;          /* crossing counts */
     float ms_boundary;          /* boundary term + epilogue */
     float ms_total;
+    int64_t n_deferred_traverse;  /* queries recounted with the full predicates (float32 filter unsettled) */
+    int64_t n_deferred_boundary;  /* queries whose boundary term was recomputed by the careful pass */
 } gwn_stats;
 
 /* Geometry summary. */
@@ -245,16 +247,18 @@ GWN_API gwn_status gwn_backward(gwn_geom *g, const gwn_queries *q, const float *
  * cudaMalloc afterwards -- it can stall the whole device and can fail under
  * memory pressure in the middle of a request.  gwn_eval keeps the per-query
  * crossing counts (scratch between the traversal and the boundary-term
- * kernel) in a buffer it allocates on demand; this entry point keeps them in
- * a fixed array inside the library instead and calls no cudaMalloc,
- * cudaFree or allocating library routine.
+ * kernel) and the boundary term's deferred-query list in buffers it
+ * allocates on demand; this entry point keeps both in a fixed array inside
+ * the library instead (the list length in a counter the context allocated at
+ * creation) and calls no cudaMalloc, cudaFree or allocating library
+ * routine.
  *   pts:   device float32 [n x 3] query points; n <= GWN_NOALLOC_MAX_QUERIES
  *          (larger n returns GWN_E_INVALID without doing any work).
  *   d:     the direction the mesh was prepared for with gwn_mesh_prepare
  *          (preparation allocates, so it must happen earlier); otherwise
  *          GWN_E_INVALID.
  *   w_out: device float32 [n]; same values as gwn_eval on the same input.
- * The array takes 16 MiB on every GPU that loads the library, until the
+ * The array takes 32 MiB on every GPU that loads the library, until the
  * process exits.  The first call on a device resolves the array's device
  * address (cudaGetSymbolAddress with that device current); make that first
  * call before any stream capture.  All calls share the one array and it keeps

@@ -77,6 +77,22 @@ class Points:
         return q
 
 
+
+class BatchQueries:
+    """One grid per chain, marshalled once into the C array that
+    gwn_eval_batch takes, with each chain's offset in the flat output."""
+
+    def __init__(self, grids, dtype: int = F32):
+        self.n_chains = len(grids)
+        self.arr = (gwn_queries * self.n_chains)()
+        self.offs = np.zeros(self.n_chains, np.int64)
+        tot = 0
+        for c, g in enumerate(grids):
+            self.arr[c] = g.to_c(dtype)
+            self.offs[c] = tot
+            tot += g.n
+        self.total = tot
+
 class Context:
     """A library context on one CUDA device, bound to a CUDA stream (default:
     torch's current stream at construction)."""
@@ -295,26 +311,27 @@ class Bezier2D(_Geom):
         check(self.lib.gwn_eval_host(self.h, C.byref(qc), None, out.ctypes.data_as(C.c_void_p)), "gwn_eval_host")
         return out
 
+    def batch_queries(self, grids):
+        """Marshal one grid per chain once (a BatchQueries), for repeated
+        eval_batch calls on the same grids."""
+        return BatchQueries(grids, self.dtype)
+
     def eval_batch(self, grids, out=None, threads=0, rows=0, use_graph=True, stats=False):
-        """Each chain c on its own grid grids[c]; returns one flat tensor with
-        chain c's grid at offsets[c] (and the offsets)."""
+        """Each chain c on its own grid grids[c] (a list of Grid or a
+        BatchQueries); returns one flat tensor with chain c's grid at
+        offsets[c] (and the offsets)."""
         torch = _torch()
-        assert len(grids) == self.n_chains
-        arr = (gwn_queries * len(grids))()
-        offs = np.zeros(len(grids), np.int64)
-        tot = 0
-        for c, g in enumerate(grids):
-            arr[c] = g.to_c(self.dtype)
-            offs[c] = tot
-            tot += g.n
-        w = out if out is not None else torch.empty(tot, dtype=self.tdtype, device=torch.device("cuda", self.ctx.device))
+        bq = grids if isinstance(grids, BatchQueries) else BatchQueries(grids, self.dtype)
+        assert bq.n_chains == self.n_chains
+        w = out if out is not None else torch.empty(bq.total, dtype=self.tdtype,
+                                                    device=torch.device("cuda", self.ctx.device))
         plan = gwn_plan(threads, rows, 0, 1 if use_graph else 0)
         st = gwn_stats() if stats else None
-        check(self.lib.gwn_eval_batch(self.h, arr, len(grids), offs.ctypes.data_as(C.c_void_p), w.data_ptr(),
+        check(self.lib.gwn_eval_batch(self.h, bq.arr, bq.n_chains, bq.offs.ctypes.data_as(C.c_void_p), w.data_ptr(),
                                       C.byref(plan), C.byref(st) if st is not None else None), "gwn_eval_batch")
         if stats:
-            return w, offs, st.as_dict()
-        return w, offs
+            return w, bq.offs, st.as_dict()
+        return w, bq.offs
 
     def batch_plan(self):
         t, r = C.c_int32(), C.c_int32()

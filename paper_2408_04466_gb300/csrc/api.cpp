@@ -282,6 +282,7 @@ GWN_API gwn_status gwn_ctx_create(gwn_ctx **out, int device, void *cuda_stream) 
     cudaError_t e = cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
     if (e == cudaSuccess) e = cudaMalloc(&c->d_status, sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&c->d_cnt, sizeof(unsigned long long) * CNT_NUM);
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_defer_count, sizeof(int32_t));
     if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(c->d_cnt, 0, sizeof(unsigned long long) * CNT_NUM);
     for (int i = 0; i < 8 && e == cudaSuccess; i++) e = cudaEventCreate(&c->ev[i]);
@@ -323,6 +324,7 @@ GWN_API void gwn_ctx_destroy(gwn_ctx *ctx) {
         if (a.ptr) cudaFree(a.ptr);
     if (ctx->d_status) cudaFree(ctx->d_status);
     if (ctx->d_cnt) cudaFree(ctx->d_cnt);
+    if (ctx->d_defer_count) cudaFree(ctx->d_defer_count);
     if (ctx->events)
         for (int i = 0; i < 8; i++) cudaEventDestroy(ctx->ev[i]);
     delete ctx;
@@ -740,6 +742,8 @@ static gwn_status read_stats(gwn_ctx *ctx, gwn_stats *st, int64_t nq, int64_t pa
     st->n_exact = (int64_t)c[CNT_EXACT];
     st->n_stack_overflow = (int64_t)c[CNT_STACK_OVERFLOW];
     st->n_tri_tests = (int64_t)(c[CNT_TRI_TESTS] + c[CNT_ROOTS]);
+    st->n_deferred_traverse = (int64_t)c[CNT_DEFER_TRAV];
+    st->n_deferred_boundary = (int64_t)c[CNT_DEFER_BTERM];
     float a = 0, b = 0, t = 0, p = 0;
     cudaEventElapsedTime(&a, ctx->ev[1], ctx->ev[2]);
     cudaEventElapsedTime(&b, ctx->ev[2], ctx->ev[3]);
@@ -785,12 +789,16 @@ GWN_API gwn_status gwn_eval(gwn_geom *g, const gwn_queries *q, const float *d, v
             chi = (int32_t *)arena_get(ctx, 0, sizeof(int32_t) * nq, &e);
             if (!chi) return cuda_fail(e, "chi buffer");
         }
+        int32_t *defer = (int32_t *)arena_get(ctx, 4, sizeof(int32_t) * nq, &e);
+        if (!defer) return cuda_fail(e, "deferred-query list");
         if (stats) CK(cudaEventRecord(ctx->ev[1], ctx->stream), "event");
-        e = launch_traverse(g->bvh, src, chi, stats ? ctx->d_cnt : nullptr, ctx->d_status, ctx->sm_count, ctx->stream);
+        e = launch_traverse(g->bvh, src, chi, defer, ctx->d_defer_count, stats ? ctx->d_cnt : nullptr, ctx->d_status,
+                            ctx->sm_count, ctx->stream);
         if (e != cudaSuccess) return cuda_fail(e, "crossing traversal");
         if (stats) CK(cudaEventRecord(ctx->ev[2], ctx->stream), "event");
         e = launch_bterm3d(g->bseq, g->n_bseq, g->bvh.frame, make_frame64(d), src, chi, (float *)w_out,
-                           (float *)b_out, stats ? ctx->d_cnt : nullptr, ctx->d_status, ctx->sm_count, ctx->stream);
+                           (float *)b_out, defer, ctx->d_defer_count, stats ? ctx->d_cnt : nullptr, ctx->d_status,
+                           ctx->sm_count, ctx->stream);
         if (e != cudaSuccess) return cuda_fail(e, "boundary term");
         if (stats) CK(cudaEventRecord(ctx->ev[3], ctx->stream), "event");
         int64_t edges = (int64_t)g->loop_vid.size();

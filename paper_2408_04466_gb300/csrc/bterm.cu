@@ -22,11 +22,17 @@
 //   jumps by 4pi while chi_d jumps by -1.  Pairs with |Omega/2| within 0.01 of
 //   pi take their branch from -sign det[A-p, B-p, d_eps] (a wrong branch moves
 //   by 2pi, the continuous extension of the right one);
-// * a boundary vertex within 1e-3 rad of the forward ray: its azimuth around
-//   the ray is ill-conditioned in float32, so both incident edges are
-//   recomputed in float64 (they are flagged by |num + i den| < 2e-3 |a||b|,
-//   which every edge of such a vertex satisfies); a vertex exactly on the ray
-//   (decided exactly) is
+// * a boundary vertex within T = 2e-4 rad of the forward ray: rounding moves
+//   its azimuth around the ray by up to ~4u/T = 1.2e-3 rad, which could hide
+//   a branch flip from the 0.01 cut band above, so both incident edges are
+//   recomputed with that vertex in float64 (they are flagged by
+//   |num + i den| < 1.01 T |a||b|, which every edge of such a vertex
+//   satisfies since |z|/(|a||b|) <= sin(delta) + 2 sin^2(delta) for an
+//   endpoint at angle delta from the ray).  Farther vertices need nothing:
+//   each vertex enters both of its edges only through its stereographic
+//   coordinate zeta = (a1 + i a2)/s_a, so its rounding acts as one ~2u
+//   perturbation of its direction, shared by both edges.  A vertex exactly
+//   on the ray (decided exactly) is
 //   seen by the perturbed ray d_eps in the direction -dp (dp = the first of
 //   e_x, e_y, e_z not parallel to d, projected orthogonally to d), and its
 //   edges take the limit of Omega under that perturbation.
@@ -88,15 +94,15 @@ static __device__ __noinline__ bool on_forward_ray(float3 X, float3 P, float3 D)
 // by 2pi, which is the continuous extension of the correct branch (a sign
 // flip would not be, and would break the first-order cancellation of vertex
 // rounding between adjacent edges).
-__device__ __forceinline__ double branch_fix(double th, int s_num) {
-    if (s_num < 0 && th > 0.0) return th - 6.283185307179586;
-    if (s_num > 0 && th < 0.0) return th + 6.283185307179586;
+__device__ __forceinline__ float branch_fix(float th, int s_num) {
+    if (s_num < 0 && th > 0.f) return th - 6.2831853071795865f;
+    if (s_num > 0 && th < 0.f) return th + 6.2831853071795865f;
     return th;
 }
 
 // Omega/2 of edge A->B in float64 for flagged pairs (|z| small relative to
 // |a||b|: an endpoint near the forward ray, or p near the edge).  Each
-// endpoint within 1e-3 rad of the forward ray is recomputed in float64, or,
+// endpoint within 2e-4 rad of the forward ray is recomputed in float64, or,
 // when it lies exactly on the ray, replaced by the perturbation limit
 // (x_perp = u = -dp in the frame, s_x = 0).  Other endpoints keep their
 // float32 projection (fa*, fb*), the values their other edge uses, so the
@@ -121,7 +127,7 @@ static __device__ __noinline__ float slow_theta(float4 va, float4 vb, float fa1,
         double a2 = x[0] * f.e2[0] + x[1] * f.e2[1] + x[2] * f.e2[2];
         double an = x[0] * f.n[0] + x[1] * f.n[1] + x[2] * f.n[2];
         double rp = a1 * a1 + a2 * a2;
-        bool near = an < 0.0 && rp < 1e-6 * (rp + an * an);
+        bool near = an < 0.0 && rp < 4e-8 * (rp + an * an);          // sin^2 < T^2
         if (!near) {
             x1[e] = f1[e]; x2[e] = f2v[e]; xs[e] = fs[e];
             continue;
@@ -141,12 +147,17 @@ static __device__ __noinline__ float slow_theta(float4 va, float4 vb, float fa1,
         num = x1[0] * x2[1] - x2[0] * x1[1];
         den = xs[0] * xs[1] + x1[0] * x1[1] + x2[0] * x2[1];
     }
-    double th = atan2(num, den);
+    // num and den are accurate to float64 rounding; the angle itself is only
+    // needed to float32 accuracy, so it is taken in float32 (float64 is a
+    // narrow pipe on this part) after scaling both by a power of two.
+    double mx = fmax(fabs(num), fabs(den));
+    int ex = mx > 0.0 ? ilogb(mx) : 0;
+    float th = atan2f((float)scalbn(num, -ex), (float)scalbn(den, -ex));
     double perm = fabs(x1[0] * x2[1]) + fabs(x2[0] * x1[1]) + 1e-300;
     if (den < 0.0 && fabs(num) <= 1e-2 * fabs(den) + 1e-5 * perm)   // close to the cut: exact branch
         th = branch_fix(th, -edge_sign_slow(A, B, p, D, cnt, status));  // sign(num) = -sign det[a, b, d]
     if (cnt) atomicAdd(&cnt[CNT_CUT_SIGN], 1ull);
-    return (float)th;
+    return th;
 }
 
 // Exact branch for a pair whose |Omega/2| is within 0.01 of pi (ray close to
@@ -192,30 +203,67 @@ __device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) { return __ffma2_rn(a, b, c
 #define GWN_AT_C1 -0.33333073f
 #define GWN_AT_C0 0.99999998f
 
-// Packed constants, materialised once per thread.
+// Packed constants (kernel parameters: both elements of each pair equal).
 struct PackedConsts {
     f2 e1x, e1y, e1z, e2x, e2y, e2z, nx, ny, nz;
     f2 c[9];
     f2 pi;
-    f2 near2;
+    f2 near2n;   // -(1.01 T)^2, T = 2e-4
+    f2 cut2n;    // -1e-4
 };
 
 __device__ __forceinline__ f2 abs2(f2 v) { return make_float2(fabsf(v.x), fabsf(v.y)); }
+// MUFU reciprocal square root (rsqrt.approx, about 2 ulp); arguments here are
+// normal floats (clamped to >= 1e-37)
+__device__ __forceinline__ float frsqrt(float x) {
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
 
-// Omega/2 = atan2(num, den) for two queries through the half-angle identity:
-// with |z| = sqrt(num^2 + den^2) and v = num / (|z| + |den|) in [-1, 1],
-//   atan2(num, den) = 2 atan(v)             if den >= 0
+// One boundary record seen from a query pair: frame coordinates (a1, a2),
+// stereographic scale s = |a| + a_n (or |a_perp|^2 / (|a| - a_n) when
+// a_n < 0) and |a|^2.
+struct VState {
+    f2 a1, a2, s, r2;
+};
+
+__device__ __forceinline__ void project(f2 vx, f2 vy, f2 vz, f2 px, f2 py, f2 pz, const PackedConsts &K,
+                                        VState &o) {
+    f2 ax = sub2(vx, px), ay = sub2(vy, py), az = sub2(vz, pz);
+    o.a1 = fma2(az, K.e1z, fma2(ay, K.e1y, mul2(ax, K.e1x)));
+    o.a2 = fma2(az, K.e2z, fma2(ay, K.e2y, mul2(ax, K.e2x)));
+    f2 an = fma2(az, K.nz, fma2(ay, K.ny, mul2(ax, K.nx)));
+    f2 rp = fma2(o.a1, o.a1, mul2(o.a2, o.a2));
+    f2 r2 = fma2(an, an, rp);
+    float r20 = fmaxf(lo2(r2), 1e-37f), r21 = fmaxf(hi2(r2), 1e-37f);
+    o.r2 = pk(r20, r21);
+    f2 r = mul2(o.r2, pk(frsqrt(r20), frsqrt(r21)));
+    f2 sp = add2(r, an), dm = sub2(r, an);
+    f2 sn = mul2(rp, pk(frcp(lo2(dm)), frcp(hi2(dm))));
+    o.s = pk(lo2(an) >= 0.f ? lo2(sp) : lo2(sn), hi2(an) >= 0.f ? hi2(sp) : hi2(sn));
+}
+
+// Omega/2 = atan2(num, den) of edge P -> Q for a query pair, through the
+// half-angle identity: with |z| = sqrt(num^2 + den^2) and
+// v = num / (|z| + |den|) in [-1, 1],
+//   atan2(num, den) = 2 atan(v)                      if den >= 0
 //                   = copysign(pi, num) - 2 atan(v)  if den < 0,
-// atan(v) = v P(v^2) (odd minimax polynomial, valid on [-1, 1]).  `cut` gets
-// one bit per element where den < 0 and |v| < 0.005, i.e. |Omega/2| within
-// 0.01 of pi (the ray passes close to the edge: exact sign needed).
-__device__ __forceinline__ f2 half_angle_atan2(f2 num, f2 den, const PackedConsts &K, int &cut, f2 &z2out) {
-    f2 z2 = fma2(num, num, mul2(den, den));
-    z2out = z2;
+// atan(v) = v P(v^2) (odd minimax polynomial, valid on [-1, 1]).
+// f0 / f1 get a set sign bit when element 0 / 1 needs the slow path:
+//   cut:  den < 0 and num^2 < 1e-4 |z|^2 (|Omega/2| within ~0.01 of pi: the
+//         ray passes close to the edge, the branch needs the exact sign);
+//   near: |z|^2 < (1.01 T)^2 |a|^2 |b|^2 (an endpoint near the forward ray).
+__device__ __forceinline__ f2 edge_theta(const VState &P, const VState &Q, const PackedConsts &K, unsigned &f0,
+                                         unsigned &f1) {
+    f2 num = sub2(mul2(P.a1, Q.a2), mul2(P.a2, Q.a1));
+    f2 den = fma2(P.s, Q.s, fma2(P.a1, Q.a1, mul2(P.a2, Q.a2)));
+    f2 nn = mul2(num, num);
+    f2 z2 = fma2(den, den, nn);
     float z20 = fmaxf(lo2(z2), 1e-37f), z21 = fmaxf(hi2(z2), 1e-37f);
-    f2 za = mul2(pk(z20, z21), pk(rsqrtf(z20), rsqrtf(z21)));
-    f2 D = add2(za, abs2(den));
-    f2 v = mul2(num, pk(frcp(lo2(D)), frcp(hi2(D))));
+    f2 za = mul2(pk(z20, z21), pk(frsqrt(z20), frsqrt(z21)));
+    f2 Dn = add2(za, abs2(den));
+    f2 v = mul2(num, pk(frcp(lo2(Dn)), frcp(hi2(Dn))));
     f2 v2 = mul2(v, v);
     f2 p = fma2(K.c[8], v2, K.c[7]);
     p = fma2(p, v2, K.c[6]);
@@ -229,27 +277,53 @@ __device__ __forceinline__ f2 half_angle_atan2(f2 num, f2 den, const PackedConst
     f2 a2 = add2(a, a);
     f2 cpi = make_float2(copysignf(lo2(K.pi), num.x), copysignf(hi2(K.pi), num.y));   // copysign(pi, num)
     f2 neg = sub2(cpi, a2);
+    f2 tc = fma2(z2, K.cut2n, nn);
+    f2 ts = fma2(mul2(P.r2, Q.r2), K.near2n, z2);
+    f0 = (__float_as_uint(lo2(den)) & __float_as_uint(lo2(tc))) | __float_as_uint(lo2(ts));
+    f1 = (__float_as_uint(hi2(den)) & __float_as_uint(hi2(tc))) | __float_as_uint(hi2(ts));
     float d0 = lo2(den), d1 = hi2(den);
-    cut = ((d0 < 0.f) & (fabsf(lo2(v)) < 0.005f)) | (((d1 < 0.f) & (fabsf(hi2(v)) < 0.005f)) << 1);
     return pk(d0 >= 0.f ? lo2(a2) : lo2(neg), d1 >= 0.f ? hi2(a2) : hi2(neg));
 }
 
+// Record vq after the previous record for KP query pairs: project vq into Q
+// and, when vq closes an edge (w != 0), add Omega/2 of P -> Q to the
+// compensated sums and its slow-path bits to the per-query flags.  Called
+// with the roles of P and Q alternating, so no state is copied.
+template <int KP>
+__device__ __forceinline__ void bterm_step(const VState (&P)[KP], VState (&Q)[KP], float4 vq,
+                                           const f2 (&px)[KP], const f2 (&py)[KP], const f2 (&pz)[KP],
+                                           f2 (&sum)[KP], f2 (&cmp)[KP], unsigned (&fl)[KP][2],
+                                           const PackedConsts &K) {
+    f2 vx = pk(vq.x, vq.x), vy = pk(vq.y, vq.y), vz = pk(vq.z, vq.z);
+#pragma unroll
+    for (int j = 0; j < KP; j++) project(vx, vy, vz, px[j], py[j], pz[j], K, Q[j]);
+    if (vq.w == 0.f) return;                  // first record of a loop (uniform)
+#pragma unroll
+    for (int j = 0; j < KP; j++) {
+        unsigned f0, f1;
+        f2 th = edge_theta(P[j], Q[j], K, f0, f1);
+        fl[j][0] |= f0;
+        fl[j][1] |= f1;
+        f2 y = sub2(th, cmp[j]);              // compensated (Kahan) accumulation
+        f2 t = add2(sum[j], y);
+        cmp[j] = sub2(sub2(t, sum[j]), y);
+        sum[j] = t;
+    }
+}
+
+// Main pass: every query, float32 only.  A query with a flagged pair is not
+// written; its index goes to the deferred list, which the careful pass
+// recomputes in full.
 template <int KP, int MINB>   // KP query pairs per thread, MINB blocks per SM
-__global__ void __launch_bounds__(256, MINB) bterm3d_kernel(const float4 *__restrict__ bseq, int nb, Frame fr,
-                                                            Frame64 f64, QuerySrc q, const int32_t *__restrict__ chi,
+__global__ void __launch_bounds__(256, MINB) bterm3d_kernel(const float4 *__restrict__ bseq, int nb,
+                                                            const __grid_constant__ PackedConsts Kp, QuerySrc q,
+                                                            const int32_t *__restrict__ chi,
                                                             float *__restrict__ w_out, float *__restrict__ b_out,
-                                                            unsigned long long *cnt, int *status) {
+                                                            int32_t *__restrict__ defer, int32_t *defer_count) {
     const int64_t base = (int64_t)blockIdx.x * blockDim.x * (2 * KP) + threadIdx.x;
-    PackedConsts K;
-    K.e1x = pk(fr.e1[0], fr.e1[0]); K.e1y = pk(fr.e1[1], fr.e1[1]); K.e1z = pk(fr.e1[2], fr.e1[2]);
-    K.e2x = pk(fr.e2[0], fr.e2[0]); K.e2y = pk(fr.e2[1], fr.e2[1]); K.e2z = pk(fr.e2[2], fr.e2[2]);
-    K.nx = pk(fr.n[0], fr.n[0]); K.ny = pk(fr.n[1], fr.n[1]); K.nz = pk(fr.n[2], fr.n[2]);
-    K.c[0] = pk(GWN_AT_C0, GWN_AT_C0); K.c[1] = pk(GWN_AT_C1, GWN_AT_C1); K.c[2] = pk(GWN_AT_C2, GWN_AT_C2);
-    K.c[3] = pk(GWN_AT_C3, GWN_AT_C3); K.c[4] = pk(GWN_AT_C4, GWN_AT_C4); K.c[5] = pk(GWN_AT_C5, GWN_AT_C5);
-    K.c[6] = pk(GWN_AT_C6, GWN_AT_C6); K.c[7] = pk(GWN_AT_C7, GWN_AT_C7); K.c[8] = pk(GWN_AT_C8, GWN_AT_C8);
-    K.pi = pk(3.14159265358979f, 3.14159265358979f);
-    K.near2 = pk(4e-6f, 4e-6f);
-    f2 px[KP], py[KP], pz[KP], pa1[KP], pa2[KP], ps[KP], pr2[KP], sum[KP], cmp[KP];
+    const PackedConsts K = Kp;           // materialised in registers once per thread
+    f2 px[KP], py[KP], pz[KP], sum[KP], cmp[KP];
+    unsigned fl[KP][2];
 #pragma unroll
     for (int j = 0; j < KP; j++) {
         int64_t i0 = base + (int64_t)(2 * j) * blockDim.x, i1 = i0 + blockDim.x;
@@ -257,71 +331,22 @@ __global__ void __launch_bounds__(256, MINB) bterm3d_kernel(const float4 *__rest
         float3 p1 = i1 < q.n ? query_point3(q, i1) : make_float3(0.f, 0.f, 0.f);
         px[j] = pk(p0.x, p1.x); py[j] = pk(p0.y, p1.y); pz[j] = pk(p0.z, p1.z);
         sum[j] = pk(0.f, 0.f); cmp[j] = pk(0.f, 0.f);
+        fl[j][0] = 0u; fl[j][1] = 0u;
     }
-    // (a1, a2, s, |a|^2) of record v for query pair j
-    auto project = [&](const f2 &vx, const f2 &vy, const f2 &vz, int j, f2 &a1, f2 &a2, f2 &s, f2 &r2out) {
-        f2 ax = sub2(vx, px[j]), ay = sub2(vy, py[j]), az = sub2(vz, pz[j]);
-        a1 = fma2(az, K.e1z, fma2(ay, K.e1y, mul2(ax, K.e1x)));
-        a2 = fma2(az, K.e2z, fma2(ay, K.e2y, mul2(ax, K.e2x)));
-        f2 an = fma2(az, K.nz, fma2(ay, K.ny, mul2(ax, K.nx)));
-        f2 rp = fma2(a1, a1, mul2(a2, a2));
-        f2 r2 = fma2(an, an, rp);
-        float r20 = fmaxf(lo2(r2), 1e-37f), r21 = fmaxf(hi2(r2), 1e-37f);
-        r2out = pk(r20, r21);
-        f2 r = mul2(r2out, pk(rsqrtf(r20), rsqrtf(r21)));
-        f2 sp = add2(r, an), dm = sub2(r, an);
-        f2 sn = mul2(rp, pk(frcp(lo2(dm)), frcp(hi2(dm))));
-        s = pk(lo2(an) >= 0.f ? lo2(sp) : lo2(sn), hi2(an) >= 0.f ? hi2(sp) : hi2(sn));
-    };
     if (nb > 0) {
-        float4 v0 = __ldg(&bseq[0]);
+        VState SA[KP], SB[KP];
+        float4 va = __ldg(&bseq[0]);
         {
-            f2 vx = pk(v0.x, v0.x), vy = pk(v0.y, v0.y), vz = pk(v0.z, v0.z);
+            f2 vx = pk(va.x, va.x), vy = pk(va.y, va.y), vz = pk(va.z, va.z);
 #pragma unroll
-            for (int j = 0; j < KP; j++) project(vx, vy, vz, j, pa1[j], pa2[j], ps[j], pr2[j]);
+            for (int j = 0; j < KP; j++) project(vx, vy, vz, px[j], py[j], pz[j], K, SA[j]);
         }
-        float4 vprev = v0;
-        for (int k = 1; k < nb; k++) {
-            float4 v = __ldg(&bseq[k]);
-            const bool edge = v.w != 0.f;     // uniform across the block
-            f2 vx = pk(v.x, v.x), vy = pk(v.y, v.y), vz = pk(v.z, v.z);
-#pragma unroll
-            for (int j = 0; j < KP; j++) {
-                f2 a1, a2, s, r2;
-                project(vx, vy, vz, j, a1, a2, s, r2);
-                if (edge) {
-                    f2 num = sub2(mul2(pa1[j], a2), mul2(pa2[j], a1));
-                    f2 den = fma2(ps[j], s, fma2(pa1[j], a1, mul2(pa2[j], a2)));
-                    int cut;
-                    f2 z2;
-                    f2 th = half_angle_atan2(num, den, K, cut, z2);
-                    // |z|^2 < (2e-3)^2 |a|^2 |b|^2: an endpoint within ~1e-3 rad of
-                    // the forward ray (or p near the edge): float64 slow path
-                    f2 lim = mul2(mul2(pr2[j], r2), K.near2);
-                    int slow = (lo2(z2) < lo2(lim)) | ((hi2(z2) < hi2(lim)) << 1);
-                    if (slow | cut) {                     // rare: exact branches / float64
-                        float t0 = lo2(th), t1 = hi2(th);
-                        if (slow & 1)
-                            t0 = slow_theta(vprev, v, lo2(pa1[j]), lo2(pa2[j]), lo2(ps[j]), lo2(a1), lo2(a2), lo2(s),
-                                            make_float3(lo2(px[j]), lo2(py[j]), lo2(pz[j])), fr, f64, cnt, status);
-                        else if (cut & 1)
-                            t0 = cut_fix(t0, vprev, v, make_float3(lo2(px[j]), lo2(py[j]), lo2(pz[j])), fr, cnt, status);
-                        if (slow & 2)
-                            t1 = slow_theta(vprev, v, hi2(pa1[j]), hi2(pa2[j]), hi2(ps[j]), hi2(a1), hi2(a2), hi2(s),
-                                            make_float3(hi2(px[j]), hi2(py[j]), hi2(pz[j])), fr, f64, cnt, status);
-                        else if (cut & 2)
-                            t1 = cut_fix(t1, vprev, v, make_float3(hi2(px[j]), hi2(py[j]), hi2(pz[j])), fr, cnt, status);
-                        th = pk(t0, t1);
-                    }
-                    f2 y = sub2(th, cmp[j]);          // compensated (Kahan) accumulation
-                    f2 t = add2(sum[j], y);
-                    cmp[j] = sub2(sub2(t, sum[j]), y);
-                    sum[j] = t;
-                }
-                pa1[j] = a1; pa2[j] = a2; ps[j] = s; pr2[j] = r2;
-            }
-            vprev = v;
+        int k = 1;
+        for (; k + 1 < nb; k += 2) {         // two records per trip: SA -> SB -> SA
+            bterm_step<KP>(SA, SB, __ldg(&bseq[k]), px, py, pz, sum, cmp, fl, K);
+            bterm_step<KP>(SB, SA, __ldg(&bseq[k + 1]), px, py, pz, sum, cmp, fl, K);
         }
+        if (k < nb) bterm_step<KP>(SA, SB, __ldg(&bseq[k]), px, py, pz, sum, cmp, fl, K);
     }
 #pragma unroll
     for (int j = 0; j < KP; j++) {
@@ -330,42 +355,145 @@ __global__ void __launch_bounds__(256, MINB) bterm3d_kernel(const float4 *__rest
         for (int h = 0; h < 2; h++) {
             int64_t idx = base + (int64_t)(2 * j + h) * blockDim.x;
             if (idx < q.n) {
-                if (b_out) b_out[idx] = Bv[h];
-                if (w_out) w_out[idx] = Bv[h] + (chi ? (float)chi[idx] : 0.f);
+                if (fl[j][h] >> 31) {
+                    int slot = atomicAdd(defer_count, 1);       // < q.n: one slot per query at most
+                    defer[slot] = (int32_t)idx;
+                } else {
+                    if (b_out) b_out[idx] = Bv[h];
+                    if (w_out) w_out[idx] = Bv[h] + (chi ? (float)chi[idx] : 0.f);
+                }
             }
         }
     }
 }
 
+// ---- careful pass: deferred queries, one per thread, scalar ----------------
+struct VState1 {
+    float a1, a2, s, r2;
+};
+
+__device__ __forceinline__ VState1 project1(float4 v, float3 p, const Frame &fr) {
+    float ax = v.x - p.x, ay = v.y - p.y, az = v.z - p.z;
+    VState1 o;
+    o.a1 = fmaf(az, fr.e1[2], fmaf(ay, fr.e1[1], ax * fr.e1[0]));
+    o.a2 = fmaf(az, fr.e2[2], fmaf(ay, fr.e2[1], ax * fr.e2[0]));
+    float an = fmaf(az, fr.n[2], fmaf(ay, fr.n[1], ax * fr.n[0]));
+    float rp = fmaf(o.a1, o.a1, o.a2 * o.a2);
+    o.r2 = fmaxf(fmaf(an, an, rp), 1e-37f);
+    float r = o.r2 * frsqrt(o.r2);
+    o.s = an >= 0.f ? r + an : rp * frcp(r - an);
+    return o;
+}
+
+// the same float32 formulation as edge_theta (one element), with the
+// flagged cases resolved: float64 near the forward ray, exact branch at the
+// cut
+__device__ __forceinline__ float edge_theta_careful(const VState1 &A, const VState1 &B, float4 va, float4 vb,
+                                                    float3 p, const Frame &fr, const Frame64 &f64,
+                                                    unsigned long long *cnt, int *status) {
+    float num = A.a1 * B.a2 - A.a2 * B.a1;
+    float den = fmaf(A.s, B.s, fmaf(A.a1, B.a1, A.a2 * B.a2));
+    float nn = num * num;
+    float z2 = fmaf(den, den, nn);
+    if (fmaf(A.r2 * B.r2, -4.1e-8f, z2) < 0.f)
+        return slow_theta(va, vb, A.a1, A.a2, A.s, B.a1, B.a2, B.s, p, fr, f64, cnt, status);
+    float zc = fmaxf(z2, 1e-37f);
+    float v = num * frcp(zc * frsqrt(zc) + fabsf(den));
+    float v2 = v * v;
+    float q = fmaf(GWN_AT_C8, v2, GWN_AT_C7);
+    q = fmaf(q, v2, GWN_AT_C6);
+    q = fmaf(q, v2, GWN_AT_C5);
+    q = fmaf(q, v2, GWN_AT_C4);
+    q = fmaf(q, v2, GWN_AT_C3);
+    q = fmaf(q, v2, GWN_AT_C2);
+    q = fmaf(q, v2, GWN_AT_C1);
+    q = fmaf(q, v2, GWN_AT_C0);
+    float a2 = 2.f * (q * v);
+    float th = den >= 0.f ? a2 : copysignf(3.14159265358979f, num) - a2;
+    if (den < 0.f && fmaf(z2, -1e-4f, nn) < 0.f) th = cut_fix(th, va, vb, p, fr, cnt, status);
+    return th;
+}
+
+__global__ void __launch_bounds__(128) bterm3d_careful_kernel(const float4 *__restrict__ bseq, int nb, Frame fr,
+                                                              Frame64 f64, QuerySrc q, const int32_t *chi,
+                                                              float *w_out, float *b_out,
+                                                              const int32_t *__restrict__ defer,
+                                                              const int32_t *defer_count, unsigned long long *cnt,
+                                                              int *status) {
+    int64_t n = *defer_count;
+    if (n > q.n) n = q.n;
+    if (cnt && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&cnt[CNT_DEFER_BTERM], (unsigned long long)n);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t idx = defer[i];
+        if (idx < 0 || idx >= q.n) { atomicOr(status, ST_BAD_INPUT); continue; }
+        float3 p = query_point3(q, idx);
+        float sum = 0.f, cmp = 0.f;
+        if (nb > 0) {
+            float4 vp = __ldg(&bseq[0]);
+            VState1 A = project1(vp, p, fr);
+            for (int k = 1; k < nb; k++) {
+                float4 v = __ldg(&bseq[k]);
+                VState1 B = project1(v, p, fr);
+                if (v.w != 0.f) {
+                    float th = edge_theta_careful(A, B, vp, v, p, fr, f64, cnt, status);
+                    float y = th - cmp;
+                    float t = sum + y;
+                    cmp = (t - sum) - y;
+                    sum = t;
+                }
+                A = B;
+                vp = v;
+            }
+        }
+        float Bv = (sum - cmp) * GWN_INV_2PI;
+        if (b_out) b_out[idx] = Bv;
+        if (w_out) w_out[idx] = Bv + (chi ? (float)chi[idx] : 0.f);
+    }
+}
+
 template <int KP, int MINB>
 static cudaError_t launch_bt(const float4 *bseq, int64_t n_bseq, const Frame &fr, const Frame64 &f64,
-                             const QuerySrc &q, const int32_t *chi, float *w_out, float *b_out,
-                             unsigned long long *cnt, int *status, cudaStream_t st) {
+                             const QuerySrc &q, const int32_t *chi, float *w_out, float *b_out, int32_t *defer,
+                             int32_t *defer_count, unsigned long long *cnt, int *status, int sm_count,
+                             cudaStream_t st) {
     const int threads = 256;
     int64_t per_block = (int64_t)threads * 2 * KP;
     int64_t blocks = (q.n + per_block - 1) / per_block;
-    if (blocks > 0x7fffffff) return cudaErrorInvalidValue;
-    bterm3d_kernel<KP, MINB><<<(unsigned)blocks, threads, 0, st>>>(bseq, (int)n_bseq, fr, f64, q, chi, w_out,
-                                                                   b_out, cnt, status);
+    if (blocks > 0x7fffffff || q.n > 0x7fffffff) return cudaErrorInvalidValue;
+    PackedConsts K;
+    auto dup = [](float x) { return make_float2(x, x); };
+    K.e1x = dup(fr.e1[0]); K.e1y = dup(fr.e1[1]); K.e1z = dup(fr.e1[2]);
+    K.e2x = dup(fr.e2[0]); K.e2y = dup(fr.e2[1]); K.e2z = dup(fr.e2[2]);
+    K.nx = dup(fr.n[0]); K.ny = dup(fr.n[1]); K.nz = dup(fr.n[2]);
+    const float c[9] = {GWN_AT_C0, GWN_AT_C1, GWN_AT_C2, GWN_AT_C3, GWN_AT_C4, GWN_AT_C5, GWN_AT_C6, GWN_AT_C7,
+                        GWN_AT_C8};
+    for (int i = 0; i < 9; i++) K.c[i] = dup(c[i]);
+    K.pi = dup(3.14159265358979f);
+    K.near2n = dup(-4.1e-8f);     // -(1.01 T)^2, T = 2e-4
+    K.cut2n = dup(-1e-4f);
+    cudaError_t e = cudaMemsetAsync(defer_count, 0, sizeof(int32_t), st);
+    if (e != cudaSuccess) return e;
+    bterm3d_kernel<KP, MINB><<<(unsigned)blocks, threads, 0, st>>>(bseq, (int)n_bseq, K, q, chi, w_out, b_out,
+                                                                   defer, defer_count);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    // deferred queries (a fraction of a percent): persistent grid over the list
+    int cblocks = (sm_count > 0 ? sm_count : 152) * 4;
+    bterm3d_careful_kernel<<<cblocks, 128, 0, st>>>(bseq, (int)n_bseq, fr, f64, q, chi, w_out, b_out, defer,
+                                                    defer_count, cnt, status);
     return cudaGetLastError();
 }
 
 cudaError_t launch_bterm3d(const float4 *bseq, int64_t n_bseq, const Frame &fr, const Frame64 &f64,
-                           const QuerySrc &q, const int32_t *chi, float *w_out, float *b_out,
-                           unsigned long long *cnt, int *status, int sm_count, cudaStream_t st) {
-    (void)sm_count;
+                           const QuerySrc &q, const int32_t *chi, float *w_out, float *b_out, int32_t *defer,
+                           int32_t *defer_count, unsigned long long *cnt, int *status, int sm_count,
+                           cudaStream_t st) {
     if (q.n == 0) return cudaSuccess;
-    static int impl = -1;
-    if (impl < 0) {
-        const char *e = getenv("GWN_BTERM_CFG");
-        impl = e ? atoi(e) : 0;
-    }
-    switch (impl) {
-        case 1: return launch_bt<1, 3>(bseq, n_bseq, fr, f64, q, chi, w_out, b_out, cnt, status, st);
-        case 2: return launch_bt<2, 2>(bseq, n_bseq, fr, f64, q, chi, w_out, b_out, cnt, status, st);
-        case 3: return launch_bt<1, 4>(bseq, n_bseq, fr, f64, q, chi, w_out, b_out, cnt, status, st);
-        default: return launch_bt<1, 2>(bseq, n_bseq, fr, f64, q, chi, w_out, b_out, cnt, status, st);
-    }
+    // Two query pairs per thread at two blocks per SM (128 registers): the
+    // fastest of the (pairs, blocks) shapes measured for 16.8M queries x 252
+    // boundary edges.
+    return launch_bt<2, 2>(bseq, n_bseq, fr, f64, q, chi, w_out, b_out, defer, defer_count, cnt, status, sm_count,
+                           st);
 }
 
 }  // namespace gwn

@@ -20,6 +20,8 @@ enum {
     CNT_PAIRS = 5,
     CNT_ROOTS = 6,
     CNT_TIMEOUT = 7,
+    CNT_DEFER_TRAV = 8,
+    CNT_DEFER_BTERM = 9,
     CNT_NUM = 16
 };
 
@@ -117,7 +119,8 @@ struct gwn_ctx {
     int sm_count = 0;
     int *d_status = nullptr;                  // device status bits
     unsigned long long *d_cnt = nullptr;      // device counters [CNT_NUM]
-    gwn::Arena scratch[4];
+    int32_t *d_defer_count = nullptr;         // length of the boundary term's deferred-query list
+    gwn::Arena scratch[5];                    // 0 chi, 1 staged points, 2 2D batch, 3 host-eval w, 4 deferred list
     cudaEvent_t ev[8];
     bool events = false;
 };
@@ -160,12 +163,19 @@ Frame64 make_frame64(const float d[3]);
 cudaError_t bvh_build(gwn_geom *g, const Frame &fr, cudaStream_t st);
 void bvh_free(MeshBvh &b);
 
-cudaError_t launch_traverse(const MeshBvh &b, const QuerySrc &q, int32_t *chi, unsigned long long *cnt,
-                            int *status, int sm_count, cudaStream_t st);
+// Crossing counts chi[q.n].  defer / defer_count: the same deferred-list
+// scratch as launch_bterm3d (used and emptied before it returns in stream
+// order, so the two may share it).
+cudaError_t launch_traverse(const MeshBvh &b, const QuerySrc &q, int32_t *chi, int32_t *defer,
+                            int32_t *defer_count, unsigned long long *cnt, int *status, int sm_count,
+                            cudaStream_t st);
 
+// Boundary term + epilogue (w = chi + B).  defer: int32 scratch of q.n
+// entries for the deferred-query list; defer_count: one device int32.
 cudaError_t launch_bterm3d(const float4 *bseq, int64_t n_bseq, const Frame &fr, const Frame64 &f64,
-                           const QuerySrc &q, const int32_t *chi, float *w_out, float *b_out,
-                           unsigned long long *cnt, int *status, int sm_count, cudaStream_t st);
+                           const QuerySrc &q, const int32_t *chi, float *w_out, float *b_out, int32_t *defer,
+                           int32_t *defer_count, unsigned long long *cnt, int *status, int sm_count,
+                           cudaStream_t st);
 
 cudaError_t launch_grad_p(const float4 *bseq, int64_t nb, const QuerySrc &q, const float *grad_w, float *grad_p,
                           cudaStream_t st);

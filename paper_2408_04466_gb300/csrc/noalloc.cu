@@ -7,12 +7,14 @@
 // memory pressure in the middle of a request).  This variant takes its
 // scratch -- the per-query crossing counts between the traversal and the
 // boundary-term kernel -- from a fixed array in the library's own device
-// data, so a call allocates nothing.
+// data, so a call allocates nothing.  The same array holds the boundary
+// term's deferred-query list (indices of the queries its careful pass
+// recomputes); the list's length lives in the context's preallocated counter.
 //
 // Limits and rules (also stated in include/gwn.h):
 //   * at most GWN_NOALLOC_MAX_QUERIES (4,194,304) queries per call; the array
-//     occupies 16 MiB on every GPU that loads the library, until the process
-//     exits;
+//     (two int32 entries per query) occupies 32 MiB on every GPU that loads
+//     the library, until the process exits;
 //   * query points must already be in device memory, and the mesh's
 //     hierarchy must already be built for d (gwn_mesh_prepare);
 //   * the first call on a device resolves the array's device address (and
@@ -28,9 +30,10 @@
 
 namespace gwn {
 
-// crossing counts of the current call; every entry read is written first by
-// the traversal kernel of the same call, so no clearing is needed
-static __device__ __align__(256) int32_t g_noalloc_chi[GWN_NOALLOC_MAX_QUERIES];
+// [0, MAX): crossing counts of the current call; [MAX, 2 MAX): its deferred-
+// query list.  Every entry read is written first in the same call, so no
+// clearing is needed.
+static __device__ __align__(256) int32_t g_noalloc_chi[2 * GWN_NOALLOC_MAX_QUERIES];
 
 static std::mutex g_noalloc_mu;
 static int32_t *g_noalloc_ptr[256];
@@ -85,10 +88,12 @@ extern "C" GWN_API gwn_status gwn_eval_points_noalloc(gwn_geom *g, const float *
     src.dim = 3;
     src.pts = pts;
     src.n = n;
-    e = launch_traverse(g->bvh, src, chi, nullptr, ctx->d_status, ctx->sm_count, ctx->stream);
+    e = launch_traverse(g->bvh, src, chi, chi + GWN_NOALLOC_MAX_QUERIES, ctx->d_defer_count, nullptr,
+                        ctx->d_status, ctx->sm_count, ctx->stream);
     if (e != cudaSuccess) return cuda_fail(e, "gwn_eval_points_noalloc: traversal");
-    e = launch_bterm3d(g->bseq, g->n_bseq, g->bvh.frame, make_frame64(d), src, chi, w_out, nullptr, nullptr,
-                       ctx->d_status, ctx->sm_count, ctx->stream);
+    e = launch_bterm3d(g->bseq, g->n_bseq, g->bvh.frame, make_frame64(d), src, chi, w_out, nullptr,
+                       chi + GWN_NOALLOC_MAX_QUERIES, ctx->d_defer_count, nullptr, ctx->d_status, ctx->sm_count,
+                       ctx->stream);
     if (e != cudaSuccess) return cuda_fail(e, "gwn_eval_points_noalloc: boundary term");
     return GWN_OK;
 }

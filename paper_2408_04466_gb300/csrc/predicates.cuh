@@ -204,6 +204,45 @@ __device__ __forceinline__ int orient_sign(float3 a, float3 b, float3 c, float3 
     return orient_sign_f64(V0, V1, V2, P, cnt, status);
 }
 
+// Float32 filter alone: +-1 when the float32 determinant settles the sign,
+// 0 when it does not (the caller defers to the full predicate).
+__device__ __forceinline__ int edge_sign_f32(float3 a, float3 b, float3 D) {
+    float c0 = a.y * b.z - a.z * b.y;
+    float c1 = a.z * b.x - a.x * b.z;
+    float c2 = a.x * b.y - a.y * b.x;
+    float det = D.x * c0 + D.y * c1 + D.z * c2;
+    float perm = fabsf(D.x) * fmaf(fabsf(a.y), fabsf(b.z), fabsf(a.z) * fabsf(b.y))
+               + fabsf(D.y) * fmaf(fabsf(a.z), fabsf(b.x), fabsf(a.x) * fabsf(b.z))
+               + fabsf(D.z) * fmaf(fabsf(a.x), fabsf(b.y), fabsf(a.y) * fabsf(b.x));
+    if (fabsf(det) > GWN_F32_BOUND * perm && perm > 1e-30f) return det > 0.f ? 1 : -1;
+    return 0;
+}
+
+__device__ __forceinline__ int orient_sign_f32(float3 a, float3 b, float3 c) {
+    float det = a.x * (b.y * c.z - b.z * c.y) + a.y * (b.z * c.x - b.x * c.z) + a.z * (b.x * c.y - b.y * c.x);
+    float perm = fabsf(a.x) * fmaf(fabsf(b.y), fabsf(c.z), fabsf(b.z) * fabsf(c.y))
+               + fabsf(a.y) * fmaf(fabsf(b.z), fabsf(c.x), fabsf(b.x) * fabsf(c.z))
+               + fabsf(a.z) * fmaf(fabsf(b.x), fabsf(c.y), fabsf(b.y) * fabsf(c.x));
+    if (fabsf(det) > GWN_F32_BOUND * perm && perm > 1e-30f) return det > 0.f ? 1 : -1;
+    return 0;
+}
+
+// tri_crossing (below) from float32 filters only: the result when every sign
+// it depends on is settled in float32 (two settled edge signs that differ
+// already rule a crossing out); otherwise `unsure` is set and 0 returned, and
+// the caller recomputes the query with the full predicates.
+__device__ __forceinline__ int tri_crossing_fast(float3 v0, float3 v1, float3 v2, float3 p, float3 d, bool &unsure) {
+    float3 a = make_float3(v0.x - p.x, v0.y - p.y, v0.z - p.z);
+    float3 b = make_float3(v1.x - p.x, v1.y - p.y, v1.z - p.z);
+    float3 c = make_float3(v2.x - p.x, v2.y - p.y, v2.z - p.z);
+    int s0 = edge_sign_f32(a, b, d), s1 = edge_sign_f32(b, c, d), s2 = edge_sign_f32(c, a, d);
+    if (s0 * s1 < 0 || s1 * s2 < 0 || s0 * s2 < 0) return 0;
+    if (s0 == 0 || s1 == 0 || s2 == 0) { unsure = true; return 0; }
+    int o = orient_sign_f32(a, b, c);
+    if (o == 0) { unsure = true; return 0; }
+    return o == s0 ? s0 : 0;
+}
+
 // Signed crossing of the ray p + t d_eps (t > 0) with triangle (v0, v1, v2):
 // +-1 when the three perturbed edge signs agree (their sum is d . n) and the
 // origin is on the same side of the plane (t > 0); 0 otherwise (including p

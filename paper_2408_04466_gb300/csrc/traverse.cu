@@ -9,8 +9,11 @@
 // the residual non-orthogonality of the rounded frame, so culling never drops
 // a crossing; every surviving triangle is decided by exact predicates.
 //
-// The signed crossings are accumulated per query (one thread per query);
-// the traversal stack holds at most the tree depth, bounded by GWN_STACK;
+// The signed crossings are accumulated per query with float32-filtered
+// predicates; a query one of whose signs the float32 filter cannot settle is
+// appended to a deferred list and recounted by a second kernel with the full
+// predicates (float64 filter, then exact expansions), so the hot loop holds
+// no call.  The traversal stack holds at most the tree depth, bounded by GWN_STACK;
 // overflow or the iteration limit sets a status bit and a counter and marks
 // the query result as invalid (INT32_MIN).
 #include <stdlib.h>
@@ -36,45 +39,45 @@ __device__ __forceinline__ bool box_hit(float x0, float x1, float y0, float y1, 
     return x0 <= xhi && xlo <= x1 && y0 <= yhi && ylo <= y1 && zm >= zlo;
 }
 
-__global__ void __launch_bounds__(256) traverse_kernel(const BvhNode *__restrict__ nodes,
-                                                       const float4 *__restrict__ tris, int root, Frame fr,
-                                                       TravParams tp, QuerySrc q, int32_t *__restrict__ chi,
-                                                       unsigned long long *cnt, int *status) {
-    int64_t idx = q.kind == GWN_QUERY_GRID ? grid_tile_query(q) : (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx < 0 || idx >= q.n) return;
-    float3 p = query_point3(q, idx);
+// One ray per thread.  FAST: float32 predicates only, `unsure` set when one
+// of them cannot settle a sign; otherwise the full predicates (float64 and
+// exact fallbacks).  Returns false on stack overflow, iteration limit or a
+// corrupt node reference (status bits set).
+template <bool FAST>
+__device__ __forceinline__ bool traverse_ray(const BvhNode *__restrict__ nodes, const float4 *__restrict__ tris,
+                                             int root, const Frame &fr, const TravParams &tp, float3 p, int &acc,
+                                             bool &unsure, unsigned long long *cnt, int *status) {
     float3 D = make_float3(fr.d[0], fr.d[1], fr.d[2]);
     float p1 = fmaf(p.z, fr.e1[2], fmaf(p.y, fr.e1[1], p.x * fr.e1[0]));
     float p2 = fmaf(p.z, fr.e2[2], fmaf(p.y, fr.e2[1], p.x * fr.e2[0]));
     float p3 = fmaf(p.z, fr.dh[2], fmaf(p.y, fr.dh[1], p.x * fr.dh[0]));
     float pad = fmaf(tp.pad_rel, fabsf(p.x) + fabsf(p.y) + fabsf(p.z), tp.pad_abs);
     float xlo = p1 - pad, xhi = p1 + pad, ylo = p2 - pad, yhi = p2 + pad, zlo = p3 - pad;
-
-    int acc = 0;
+    acc = 0;
     int stack[GWN_STACK];
     int sp = 0;
     int node = root;
     int64_t iter = 0;
-    bool bad = false;
     while (true) {
         if (++iter > tp.max_iter) {
             atomicOr(status, ST_TIMEOUT);
             if (cnt) atomicAdd(&cnt[CNT_TIMEOUT], 1ull);
-            bad = true;
-            break;
+            return false;
         }
         if (node >= tp.n_internal || ~node >= tp.n_leaves) {   // corrupt reference: report, never read
             atomicOr(status, ST_BAD_INPUT);
-            bad = true;
-            break;
+            return false;
         }
         if (node < 0) {
             int t = ~node;
             float4 a = __ldg(&tris[3 * t]), b = __ldg(&tris[3 * t + 1]), c = __ldg(&tris[3 * t + 2]);
             if (cnt) atomicAdd(&cnt[CNT_TRI_TESTS], 1ull);
-            acc += tri_crossing(make_float3(a.x, a.y, a.z), make_float3(b.x, b.y, b.z),
-                                make_float3(c.x, c.y, c.z), p, D, cnt, status);
-            if (sp == 0) break;
+            float3 v0 = make_float3(a.x, a.y, a.z), v1 = make_float3(b.x, b.y, b.z), v2 = make_float3(c.x, c.y, c.z);
+            if (FAST)
+                acc += tri_crossing_fast(v0, v1, v2, p, D, unsure);
+            else
+                acc += tri_crossing(v0, v1, v2, p, D, cnt, status);
+            if (sp == 0) return true;
             node = stack[--sp];
             continue;
         }
@@ -86,8 +89,7 @@ __global__ void __launch_bounds__(256) traverse_kernel(const BvhNode *__restrict
             if (sp >= GWN_STACK) {
                 atomicOr(status, ST_STACK_OVERFLOW);
                 if (cnt) atomicAdd(&cnt[CNT_STACK_OVERFLOW], 1ull);
-                bad = true;
-                break;
+                return false;
             }
             stack[sp++] = c1;
             node = c0;
@@ -96,11 +98,57 @@ __global__ void __launch_bounds__(256) traverse_kernel(const BvhNode *__restrict
         } else if (h1) {
             node = c1;
         } else {
-            if (sp == 0) break;
+            if (sp == 0) return true;
             node = stack[--sp];
         }
     }
-    chi[idx] = bad ? INT32_MIN : acc;
+}
+
+// Append query idx to the deferred list (at most one entry per query, so the
+// list never outgrows its q.n entries).
+__device__ __forceinline__ void defer_query(int32_t *defer, int32_t *defer_count, int64_t idx) {
+    int slot = atomicAdd(defer_count, 1);
+    defer[slot] = (int32_t)idx;
+}
+
+// Scattered points: one ray per thread, float32 predicates; unsettled
+// queries are deferred.
+__global__ void __launch_bounds__(256) traverse_kernel(const BvhNode *__restrict__ nodes,
+                                                       const float4 *__restrict__ tris, int root, Frame fr,
+                                                       TravParams tp, QuerySrc q, int32_t *__restrict__ chi,
+                                                       int32_t *defer, int32_t *defer_count,
+                                                       unsigned long long *cnt, int *status) {
+    int64_t idx = q.kind == GWN_QUERY_GRID ? grid_tile_query(q) : (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx < 0 || idx >= q.n) return;
+    int acc;
+    bool unsure = false;
+    bool ok = traverse_ray<true>(nodes, tris, root, fr, tp, query_point3(q, idx), acc, unsure, cnt, status);
+    if (ok && unsure)
+        defer_query(defer, defer_count, idx);
+    else
+        chi[idx] = ok ? acc : INT32_MIN;
+}
+
+// Deferred queries (a float32 predicate could not settle a sign): the same
+// traversal with the full predicates, persistent grid over the list.
+__global__ void __launch_bounds__(128) traverse_careful_kernel(const BvhNode *__restrict__ nodes,
+                                                               const float4 *__restrict__ tris, int root, Frame fr,
+                                                               TravParams tp, QuerySrc q,
+                                                               int32_t *__restrict__ chi,
+                                                               const int32_t *__restrict__ defer,
+                                                               const int32_t *defer_count, unsigned long long *cnt,
+                                                               int *status) {
+    int64_t n = *defer_count;
+    if (n > q.n) n = q.n;
+    if (cnt && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&cnt[CNT_DEFER_TRAV], (unsigned long long)n);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t idx = defer[i];
+        if (idx < 0 || idx >= q.n) { atomicOr(status, ST_BAD_INPUT); continue; }
+        int acc;
+        bool unsure = false;
+        bool ok = traverse_ray<false>(nodes, tris, root, fr, tp, query_point3(q, idx), acc, unsure, cnt, status);
+        chi[idx] = ok ? acc : INT32_MIN;
+    }
 }
 
 // Warp-packet traversal for grid queries: the 32 rays of a warp (a 4x4x2
@@ -108,13 +156,15 @@ __global__ void __launch_bounds__(256) traverse_kernel(const BvhNode *__restrict
 // The stack is warp-uniform (every lane holds the same copy); at a node each
 // lane tests its own ray against both child boxes and the warp descends into
 // a child if any lane's ray hits it; at a leaf only the lanes whose ray box
-// hits the triangle run the exact crossing test.  Node and triangle loads are
+// hits the triangle run the float32 crossing test (a query whose test needs
+// more is deferred to traverse_careful_kernel).  Node and triangle loads are
 // warp-uniform (one broadcast per warp).  Lanes outside the grid take part
 // with an empty box.
 __global__ void __launch_bounds__(256) traverse_packet_kernel(const BvhNode *__restrict__ nodes,
                                                               const float4 *__restrict__ tris,
                                                               const float4 *__restrict__ tbox, int root, Frame fr,
                                                               TravParams tp, QuerySrc q, int32_t *__restrict__ chi,
+                                                              int32_t *defer, int32_t *defer_count,
                                                               unsigned long long *cnt, int *status) {
     int64_t idx = grid_tile_query(q);
     bool valid = idx >= 0 && idx < q.n;
@@ -127,7 +177,12 @@ __global__ void __launch_bounds__(256) traverse_packet_kernel(const BvhNode *__r
     float xlo = p1 - pad, xhi = p1 + pad, ylo = p2 - pad, yhi = p2 + pad, zlo = p3 - pad;
     if (!valid) { xlo = 3.4e38f; xhi = -3.4e38f; }     // never hits
     int acc = 0;
-    int stack[GWN_STACK];
+    bool unsure = false;
+    // The traversal order is warp-uniform (every decision goes through
+    // __any_sync), so the warp shares one stack in shared memory; every lane
+    // writes the same value on a push.
+    __shared__ int s_stack[256 / 32][GWN_STACK];
+    int *stack = s_stack[threadIdx.x >> 5];
     int sp = 0;
     int node = root;
     bool bad = false;
@@ -152,8 +207,8 @@ __global__ void __launch_bounds__(256) traverse_packet_kernel(const BvhNode *__r
             if (hit) {
                 float4 a = __ldg(&tris[3 * t]), b = __ldg(&tris[3 * t + 1]), c = __ldg(&tris[3 * t + 2]);
                 if (cnt) atomicAdd(&cnt[CNT_TRI_TESTS], 1ull);
-                acc += tri_crossing(make_float3(a.x, a.y, a.z), make_float3(b.x, b.y, b.z),
-                                    make_float3(c.x, c.y, c.z), p, D, cnt, status);
+                acc += tri_crossing_fast(make_float3(a.x, a.y, a.z), make_float3(b.x, b.y, b.z),
+                                         make_float3(c.x, c.y, c.z), p, D, unsure);
             }
             if (sp == 0) break;
             node = stack[--sp];
@@ -174,6 +229,7 @@ __global__ void __launch_bounds__(256) traverse_packet_kernel(const BvhNode *__r
                 break;
             }
             stack[sp++] = c1;
+            __syncwarp();
             node = c0;
         } else if (a0) {
             node = c0;
@@ -184,7 +240,12 @@ __global__ void __launch_bounds__(256) traverse_packet_kernel(const BvhNode *__r
             node = stack[--sp];
         }
     }
-    if (valid) chi[idx] = bad ? INT32_MIN : acc;
+    if (valid) {
+        if (!bad && unsure)
+            defer_query(defer, defer_count, idx);
+        else
+            chi[idx] = bad ? INT32_MIN : acc;
+    }
 }
 
 // Root is a single leaf (one triangle) or the mesh is empty.
@@ -203,10 +264,11 @@ __global__ void traverse_single_kernel(const float4 *__restrict__ tris, int ntri
     chi[idx] = acc;
 }
 
-cudaError_t launch_traverse(const MeshBvh &b, const QuerySrc &q, int32_t *chi, unsigned long long *cnt,
-                            int *status, int sm_count, cudaStream_t st) {
-    (void)sm_count;
+cudaError_t launch_traverse(const MeshBvh &b, const QuerySrc &q, int32_t *chi, int32_t *defer,
+                            int32_t *defer_count, unsigned long long *cnt, int *status, int sm_count,
+                            cudaStream_t st) {
     if (q.n == 0) return cudaSuccess;
+    if (q.n > 0x7fffffff) return cudaErrorInvalidValue;
     const int threads = 128;
     int64_t blocks = (q.n + threads - 1) / threads;
     if (blocks > 0x7fffffff) return cudaErrorInvalidValue;
@@ -233,17 +295,21 @@ cudaError_t launch_traverse(const MeshBvh &b, const QuerySrc &q, int32_t *chi, u
     tp.n_leaves = (int)b.n;
     int64_t tblocks = q.kind == GWN_QUERY_GRID ? grid_tile_blocks(q) : (q.n + 255) / 256;
     if (tblocks > 0x7fffffff) return cudaErrorInvalidValue;
-    static int impl = -1;
-    if (impl < 0) {
-        const char *e = getenv("GWN_TRAV_IMPL");
-        impl = e ? atoi(e) : 1;
-    }
-    if (q.kind == GWN_QUERY_GRID && impl == 1 && b.tbox)
+    cudaError_t e = cudaMemsetAsync(defer_count, 0, sizeof(int32_t), st);
+    if (e != cudaSuccess) return e;
+    // Grid queries come in spatially coherent warp tiles: one warp-uniform
+    // stack per tile.  Scattered points take one stack per thread.
+    if (q.kind == GWN_QUERY_GRID && b.tbox)
         traverse_packet_kernel<<<(unsigned)tblocks, 256, 0, st>>>(b.nodes, b.tris, b.tbox, b.root, b.frame, tp, q,
-                                                                  chi, cnt, status);
+                                                                  chi, defer, defer_count, cnt, status);
     else
-        traverse_kernel<<<(unsigned)tblocks, 256, 0, st>>>(b.nodes, b.tris, b.root, b.frame, tp, q, chi, cnt,
-                                                           status);
+        traverse_kernel<<<(unsigned)tblocks, 256, 0, st>>>(b.nodes, b.tris, b.root, b.frame, tp, q, chi, defer,
+                                                           defer_count, cnt, status);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    int cblocks = (sm_count > 0 ? sm_count : 152) * 4;
+    traverse_careful_kernel<<<cblocks, 128, 0, st>>>(b.nodes, b.tris, b.root, b.frame, tp, q, chi, defer,
+                                                     defer_count, cnt, status);
     return cudaGetLastError();
 }
 
