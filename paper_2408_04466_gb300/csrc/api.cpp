@@ -796,7 +796,7 @@ GWN_API gwn_status gwn_eval(gwn_geom *g, const gwn_queries *q, const float *d, v
                             ctx->sm_count, ctx->stream);
         if (e != cudaSuccess) return cuda_fail(e, "crossing traversal");
         if (stats) CK(cudaEventRecord(ctx->ev[2], ctx->stream), "event");
-        e = launch_bterm3d(g->bseq, g->n_bseq, g->bvh.frame, make_frame64(d), src, chi, (float *)w_out,
+        e = launch_bterm3d(g->bseq, g->bvh.bframe, g->n_bseq, g->bvh.frame, make_frame64(d), src, chi, (float *)w_out,
                            (float *)b_out, defer, ctx->d_defer_count, stats ? ctx->d_cnt : nullptr, ctx->d_status,
                            ctx->sm_count, ctx->stream);
         if (e != cudaSuccess) return cuda_fail(e, "boundary term");

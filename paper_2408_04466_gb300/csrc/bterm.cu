@@ -22,17 +22,21 @@
 //   jumps by 4pi while chi_d jumps by -1.  Pairs with |Omega/2| within 0.01 of
 //   pi take their branch from -sign det[A-p, B-p, d_eps] (a wrong branch moves
 //   by 2pi, the continuous extension of the right one);
-// * a boundary vertex within T = 2e-4 rad of the forward ray: rounding moves
-//   its azimuth around the ray by up to ~4u/T = 1.2e-3 rad, which could hide
-//   a branch flip from the 0.01 cut band above, so both incident edges are
-//   recomputed with that vertex in float64 (they are flagged by
+// * a boundary vertex close to the forward ray: its azimuth around the ray
+//   must be accurate to well inside the 0.01 cut band, or a branch flip
+//   could hide from it.  Each vertex enters both of its edges only through
+//   its stereographic coordinate zeta = (a1 + i a2)/s_a, so rounding acts as
+//   one perturbation of its direction shared by both edges; only the azimuth
+//   error matters.  The main pass forms (a1, a2, a_n) as double-float
+//   differences (project below): azimuth error ~2u + u^2 (|A|+|p|)/|a_perp|,
+//   so it flags only vertices within T = 1e-6 rad (margin ~100 for
+//   |a| >= 1e-4).  The careful pass uses plain float32 projections of A - p
+//   (azimuth error ~4u/delta) with T = 2e-4 (error <= 1.2e-3) and recomputes
+//   the edges of such vertices in float64.  Edges are flagged by
 //   |num + i den| < 1.01 T |a||b|, which every edge of such a vertex
 //   satisfies since |z|/(|a||b|) <= sin(delta) + 2 sin^2(delta) for an
-//   endpoint at angle delta from the ray).  Farther vertices need nothing:
-//   each vertex enters both of its edges only through its stereographic
-//   coordinate zeta = (a1 + i a2)/s_a, so its rounding acts as one ~2u
-//   perturbation of its direction, shared by both edges.  A vertex exactly
-//   on the ray (decided exactly) is
+//   endpoint at angle delta from the ray.  A vertex exactly on the ray
+//   (decided exactly) is
 //   seen by the perturbed ray d_eps in the direction -dp (dp = the first of
 //   e_x, e_y, e_z not parallel to d, projected orthogonally to d), and its
 //   edges take the limit of Omega under that perturbation.
@@ -40,7 +44,7 @@
 // Arithmetic: two queries per 64-bit register pair; plain add/mul/fma run as
 // packed f32x2 instructions (Blackwell), min/max, MUFU (rsqrt, reciprocal),
 // compares and selects per element.  atan2(num, den) uses the half-angle
-// identity (see half_angle_atan2) so that a single odd polynomial on [-1, 1]
+// identity (see edge_theta) so that a single odd polynomial on [-1, 1]
 // serves every quadrant: a degree-8 minimax polynomial P with atan(v) ~
 // v P(v^2), fitted by Lawson-weighted least squares to the relative error
 // (1.5e-8 in exact arithmetic).  Accumulation over edges is compensated
@@ -205,10 +209,9 @@ __device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) { return __ffma2_rn(a, b, c
 
 // Packed constants (kernel parameters: both elements of each pair equal).
 struct PackedConsts {
-    f2 e1x, e1y, e1z, e2x, e2y, e2z, nx, ny, nz;
     f2 c[9];
     f2 pi;
-    f2 near2n;   // -(1.01 T)^2, T = 2e-4
+    f2 near2n;   // -(1.01 T)^2
     f2 cut2n;    // -1e-4
 };
 
@@ -228,12 +231,23 @@ struct VState {
     f2 a1, a2, s, r2;
 };
 
-__device__ __forceinline__ void project(f2 vx, f2 vy, f2 vz, f2 px, f2 py, f2 pz, const PackedConsts &K,
-                                        VState &o) {
-    f2 ax = sub2(vx, px), ay = sub2(vy, py), az = sub2(vz, pz);
-    o.a1 = fma2(az, K.e1z, fma2(ay, K.e1y, mul2(ax, K.e1x)));
-    o.a2 = fma2(az, K.e2z, fma2(ay, K.e2y, mul2(ax, K.e2x)));
-    f2 an = fma2(az, K.nz, fma2(ay, K.ny, mul2(ax, K.nx)));
+// Frame coordinates of a = A - p as double-float differences: the record
+// holds A.e (e = e1, e2, n) as hi + lo floats (computed per direction in
+// float64), the query -p.e as hi + lo (error-free float32 transforms), so
+//   a_e = (A_hi - p_hi) + (A_lo - p_lo)
+// is correct to about 2u |a_e| + u^2 (|A| + |p|): relative to the component
+// itself, not to |a| as a float32 projection of A - p would be, which keeps
+// a vertex's azimuth around the ray well conditioned down to tiny angles.
+struct QPair {
+    f2 n1h, n2h, nnh, n1l, n2l, nnl;      // -(p.e1), -(p.e2), -(p.n) as hi + lo, two queries
+};
+
+__device__ __forceinline__ void project(float4 rh, float4 rl, const QPair &Q, VState &o) {
+    f2 h1 = pk(rh.x, rh.x), h2 = pk(rh.y, rh.y), hn = pk(rh.z, rh.z);
+    f2 l1 = pk(rl.x, rl.x), l2 = pk(rl.y, rl.y), ln = pk(rl.z, rl.z);
+    o.a1 = add2(add2(h1, Q.n1h), add2(l1, Q.n1l));
+    o.a2 = add2(add2(h2, Q.n2h), add2(l2, Q.n2l));
+    f2 an = add2(add2(hn, Q.nnh), add2(ln, Q.nnl));
     f2 rp = fma2(o.a1, o.a1, mul2(o.a2, o.a2));
     f2 r2 = fma2(an, an, rp);
     float r20 = fmaxf(lo2(r2), 1e-37f), r21 = fmaxf(hi2(r2), 1e-37f);
@@ -242,6 +256,20 @@ __device__ __forceinline__ void project(f2 vx, f2 vy, f2 vz, f2 px, f2 py, f2 pz
     f2 sp = add2(r, an), dm = sub2(r, an);
     f2 sn = mul2(rp, pk(frcp(lo2(dm)), frcp(hi2(dm))));
     o.s = pk(lo2(an) >= 0.f ? lo2(sp) : lo2(sn), hi2(an) >= 0.f ? hi2(sp) : hi2(sn));
+}
+
+// -(p.e) as hi + lo from float32 arithmetic: exact products (FMA), TwoSum
+// of the high parts, float sum of the (small) error terms, renormalised.
+__device__ __forceinline__ void neg_dot_df(float3 p, const float e[3], float &hi, float &lo) {
+    float hx = p.x * e[0], lx = fmaf(p.x, e[0], -hx);
+    float hy = p.y * e[1], ly = fmaf(p.y, e[1], -hy);
+    float hz = p.z * e[2], lz = fmaf(p.z, e[2], -hz);
+    float s = hx + hy, bs = s - hx, es = (hx - (s - bs)) + (hy - bs);
+    float t = s + hz, bt = t - s, et = (s - (t - bt)) + (hz - bt);
+    float l = ((lx + ly) + lz) + (es + et);
+    float h = t + l;
+    lo = -(l - (h - t));
+    hi = -h;
 }
 
 // Omega/2 = atan2(num, den) of edge P -> Q for a query pair, through the
@@ -253,7 +281,8 @@ __device__ __forceinline__ void project(f2 vx, f2 vy, f2 vz, f2 px, f2 py, f2 pz
 // f0 / f1 get a set sign bit when element 0 / 1 needs the slow path:
 //   cut:  den < 0 and num^2 < 1e-4 |z|^2 (|Omega/2| within ~0.01 of pi: the
 //         ray passes close to the edge, the branch needs the exact sign);
-//   near: |z|^2 < (1.01 T)^2 |a|^2 |b|^2 (an endpoint near the forward ray).
+//   near: |z|^2 < (1.01 T)^2 |a|^2 |b|^2 (an endpoint within T of the forward
+//         ray, T = 1e-6 here).
 __device__ __forceinline__ f2 edge_theta(const VState &P, const VState &Q, const PackedConsts &K, unsigned &f0,
                                          unsigned &f1) {
     f2 num = sub2(mul2(P.a1, Q.a2), mul2(P.a2, Q.a1));
@@ -290,13 +319,12 @@ __device__ __forceinline__ f2 edge_theta(const VState &P, const VState &Q, const
 // compensated sums and its slow-path bits to the per-query flags.  Called
 // with the roles of P and Q alternating, so no state is copied.
 template <int KP>
-__device__ __forceinline__ void bterm_step(const VState (&P)[KP], VState (&Q)[KP], float4 vq,
-                                           const f2 (&px)[KP], const f2 (&py)[KP], const f2 (&pz)[KP],
-                                           f2 (&sum)[KP], f2 (&cmp)[KP], unsigned (&fl)[KP][2],
-                                           const PackedConsts &K) {
-    f2 vx = pk(vq.x, vq.x), vy = pk(vq.y, vq.y), vz = pk(vq.z, vq.z);
+__device__ __forceinline__ void bterm_step(const VState (&P)[KP], VState (&Q)[KP], float4 rh, float4 rl,
+                                           const QPair (&qp)[KP], f2 (&sum)[KP], f2 (&cmp)[KP],
+                                           unsigned (&fl)[KP][2], const PackedConsts &K) {
 #pragma unroll
-    for (int j = 0; j < KP; j++) project(vx, vy, vz, px[j], py[j], pz[j], K, Q[j]);
+    for (int j = 0; j < KP; j++) project(rh, rl, qp[j], Q[j]);
+    float4 vq = rh;
     if (vq.w == 0.f) return;                  // first record of a loop (uniform)
 #pragma unroll
     for (int j = 0; j < KP; j++) {
@@ -315,38 +343,44 @@ __device__ __forceinline__ void bterm_step(const VState (&P)[KP], VState (&Q)[KP
 // written; its index goes to the deferred list, which the careful pass
 // recomputes in full.
 template <int KP, int MINB>   // KP query pairs per thread, MINB blocks per SM
-__global__ void __launch_bounds__(256, MINB) bterm3d_kernel(const float4 *__restrict__ bseq, int nb,
+__global__ void __launch_bounds__(256, MINB) bterm3d_kernel(const float4 *__restrict__ bframe, int nb, Frame fr,
                                                             const __grid_constant__ PackedConsts Kp, QuerySrc q,
                                                             const int32_t *__restrict__ chi,
                                                             float *__restrict__ w_out, float *__restrict__ b_out,
                                                             int32_t *__restrict__ defer, int32_t *defer_count) {
     const int64_t base = (int64_t)blockIdx.x * blockDim.x * (2 * KP) + threadIdx.x;
     const PackedConsts K = Kp;           // materialised in registers once per thread
-    f2 px[KP], py[KP], pz[KP], sum[KP], cmp[KP];
+    QPair qp[KP];
+    f2 sum[KP], cmp[KP];
     unsigned fl[KP][2];
 #pragma unroll
     for (int j = 0; j < KP; j++) {
         int64_t i0 = base + (int64_t)(2 * j) * blockDim.x, i1 = i0 + blockDim.x;
         float3 p0 = i0 < q.n ? query_point3(q, i0) : make_float3(0.f, 0.f, 0.f);
         float3 p1 = i1 < q.n ? query_point3(q, i1) : make_float3(0.f, 0.f, 0.f);
-        px[j] = pk(p0.x, p1.x); py[j] = pk(p0.y, p1.y); pz[j] = pk(p0.z, p1.z);
+        float h0, l0, h1, l1;
+        neg_dot_df(p0, fr.e1, h0, l0); neg_dot_df(p1, fr.e1, h1, l1);
+        qp[j].n1h = pk(h0, h1); qp[j].n1l = pk(l0, l1);
+        neg_dot_df(p0, fr.e2, h0, l0); neg_dot_df(p1, fr.e2, h1, l1);
+        qp[j].n2h = pk(h0, h1); qp[j].n2l = pk(l0, l1);
+        neg_dot_df(p0, fr.n, h0, l0); neg_dot_df(p1, fr.n, h1, l1);
+        qp[j].nnh = pk(h0, h1); qp[j].nnl = pk(l0, l1);
         sum[j] = pk(0.f, 0.f); cmp[j] = pk(0.f, 0.f);
         fl[j][0] = 0u; fl[j][1] = 0u;
     }
     if (nb > 0) {
         VState SA[KP], SB[KP];
-        float4 va = __ldg(&bseq[0]);
         {
-            f2 vx = pk(va.x, va.x), vy = pk(va.y, va.y), vz = pk(va.z, va.z);
+            float4 rh = __ldg(&bframe[0]), rl = __ldg(&bframe[1]);
 #pragma unroll
-            for (int j = 0; j < KP; j++) project(vx, vy, vz, px[j], py[j], pz[j], K, SA[j]);
+            for (int j = 0; j < KP; j++) project(rh, rl, qp[j], SA[j]);
         }
         int k = 1;
         for (; k + 1 < nb; k += 2) {         // two records per trip: SA -> SB -> SA
-            bterm_step<KP>(SA, SB, __ldg(&bseq[k]), px, py, pz, sum, cmp, fl, K);
-            bterm_step<KP>(SB, SA, __ldg(&bseq[k + 1]), px, py, pz, sum, cmp, fl, K);
+            bterm_step<KP>(SA, SB, __ldg(&bframe[2 * k]), __ldg(&bframe[2 * k + 1]), qp, sum, cmp, fl, K);
+            bterm_step<KP>(SB, SA, __ldg(&bframe[2 * k + 2]), __ldg(&bframe[2 * k + 3]), qp, sum, cmp, fl, K);
         }
-        if (k < nb) bterm_step<KP>(SA, SB, __ldg(&bseq[k]), px, py, pz, sum, cmp, fl, K);
+        if (k < nb) bterm_step<KP>(SA, SB, __ldg(&bframe[2 * k]), __ldg(&bframe[2 * k + 1]), qp, sum, cmp, fl, K);
     }
 #pragma unroll
     for (int j = 0; j < KP; j++) {
@@ -365,6 +399,29 @@ __global__ void __launch_bounds__(256, MINB) bterm3d_kernel(const float4 *__rest
             }
         }
     }
+}
+
+// Boundary records in the frame of d as double-float values: for record k,
+// out[2k] = (hi of A.e1, A.e2, A.n, w), out[2k + 1] = (lo parts, 0).
+__global__ void bframe_kernel(const float4 *__restrict__ bseq, int64_t n, Frame fr, float4 *__restrict__ out) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    float4 v = bseq[k];
+    const float *e[3] = {fr.e1, fr.e2, fr.n};
+    float h[3], l[3];
+    for (int c = 0; c < 3; c++) {
+        double x = (double)v.x * e[c][0] + (double)v.y * e[c][1] + (double)v.z * e[c][2];
+        h[c] = (float)x;
+        l[c] = (float)(x - (double)h[c]);
+    }
+    out[2 * k] = make_float4(h[0], h[1], h[2], v.w);
+    out[2 * k + 1] = make_float4(l[0], l[1], l[2], 0.f);
+}
+
+cudaError_t launch_bframe(const float4 *bseq, int64_t n, const Frame &fr, float4 *out, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    bframe_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(bseq, n, fr, out);
+    return cudaGetLastError();
 }
 
 // ---- careful pass: deferred queries, one per thread, scalar ----------------
@@ -395,7 +452,7 @@ __device__ __forceinline__ float edge_theta_careful(const VState1 &A, const VSta
     float den = fmaf(A.s, B.s, fmaf(A.a1, B.a1, A.a2 * B.a2));
     float nn = num * num;
     float z2 = fmaf(den, den, nn);
-    if (fmaf(A.r2 * B.r2, -4.1e-8f, z2) < 0.f)
+    if (fmaf(A.r2 * B.r2, -4.1e-8f, z2) < 0.f)           // T = 2e-4 for float32 projections
         return slow_theta(va, vb, A.a1, A.a2, A.s, B.a1, B.a2, B.s, p, fr, f64, cnt, status);
     float zc = fmaxf(z2, 1e-37f);
     float v = num * frcp(zc * frsqrt(zc) + fabsf(den));
@@ -452,28 +509,25 @@ __global__ void __launch_bounds__(128) bterm3d_careful_kernel(const float4 *__re
 }
 
 template <int KP, int MINB>
-static cudaError_t launch_bt(const float4 *bseq, int64_t n_bseq, const Frame &fr, const Frame64 &f64,
-                             const QuerySrc &q, const int32_t *chi, float *w_out, float *b_out, int32_t *defer,
-                             int32_t *defer_count, unsigned long long *cnt, int *status, int sm_count,
-                             cudaStream_t st) {
+static cudaError_t launch_bt(const float4 *bseq, const float4 *bframe, int64_t n_bseq, const Frame &fr,
+                             const Frame64 &f64, const QuerySrc &q, const int32_t *chi, float *w_out, float *b_out,
+                             int32_t *defer, int32_t *defer_count, unsigned long long *cnt, int *status,
+                             int sm_count, cudaStream_t st) {
     const int threads = 256;
     int64_t per_block = (int64_t)threads * 2 * KP;
     int64_t blocks = (q.n + per_block - 1) / per_block;
     if (blocks > 0x7fffffff || q.n > 0x7fffffff) return cudaErrorInvalidValue;
     PackedConsts K;
     auto dup = [](float x) { return make_float2(x, x); };
-    K.e1x = dup(fr.e1[0]); K.e1y = dup(fr.e1[1]); K.e1z = dup(fr.e1[2]);
-    K.e2x = dup(fr.e2[0]); K.e2y = dup(fr.e2[1]); K.e2z = dup(fr.e2[2]);
-    K.nx = dup(fr.n[0]); K.ny = dup(fr.n[1]); K.nz = dup(fr.n[2]);
     const float c[9] = {GWN_AT_C0, GWN_AT_C1, GWN_AT_C2, GWN_AT_C3, GWN_AT_C4, GWN_AT_C5, GWN_AT_C6, GWN_AT_C7,
                         GWN_AT_C8};
     for (int i = 0; i < 9; i++) K.c[i] = dup(c[i]);
     K.pi = dup(3.14159265358979f);
-    K.near2n = dup(-4.1e-8f);     // -(1.01 T)^2, T = 2e-4
+    K.near2n = dup(-1.0201e-12f);   // -(1.01 T)^2, T = 1e-6 (double-float projections)
     K.cut2n = dup(-1e-4f);
     cudaError_t e = cudaMemsetAsync(defer_count, 0, sizeof(int32_t), st);
     if (e != cudaSuccess) return e;
-    bterm3d_kernel<KP, MINB><<<(unsigned)blocks, threads, 0, st>>>(bseq, (int)n_bseq, K, q, chi, w_out, b_out,
+    bterm3d_kernel<KP, MINB><<<(unsigned)blocks, threads, 0, st>>>(bframe, (int)n_bseq, fr, K, q, chi, w_out, b_out,
                                                                    defer, defer_count);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -484,16 +538,15 @@ static cudaError_t launch_bt(const float4 *bseq, int64_t n_bseq, const Frame &fr
     return cudaGetLastError();
 }
 
-cudaError_t launch_bterm3d(const float4 *bseq, int64_t n_bseq, const Frame &fr, const Frame64 &f64,
-                           const QuerySrc &q, const int32_t *chi, float *w_out, float *b_out, int32_t *defer,
-                           int32_t *defer_count, unsigned long long *cnt, int *status, int sm_count,
+cudaError_t launch_bterm3d(const float4 *bseq, const float4 *bframe, int64_t n_bseq, const Frame &fr,
+                           const Frame64 &f64, const QuerySrc &q, const int32_t *chi, float *w_out, float *b_out,
+                           int32_t *defer, int32_t *defer_count, unsigned long long *cnt, int *status, int sm_count,
                            cudaStream_t st) {
     if (q.n == 0) return cudaSuccess;
-    // Two query pairs per thread at two blocks per SM (128 registers): the
-    // fastest of the (pairs, blocks) shapes measured for 16.8M queries x 252
-    // boundary edges.
-    return launch_bt<2, 2>(bseq, n_bseq, fr, f64, q, chi, w_out, b_out, defer, defer_count, cnt, status, sm_count,
-                           st);
+    // Two query pairs per thread at two blocks per SM: the fastest of the
+    // (pairs, blocks) shapes measured for 16.8M queries x 252 boundary edges.
+    return launch_bt<2, 2>(bseq, bframe, n_bseq, fr, f64, q, chi, w_out, b_out, defer, defer_count, cnt, status,
+                           sm_count, st);
 }
 
 }  // namespace gwn

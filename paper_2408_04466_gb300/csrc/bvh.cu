@@ -347,7 +347,9 @@ void bvh_free(MeshBvh &b) {
     if (b.tris) cudaFree(b.tris);
     if (b.tri_id) cudaFree(b.tri_id);
     if (b.tbox) cudaFree(b.tbox);
+    if (b.bframe) cudaFree(b.bframe);
     b.tbox = nullptr;
+    b.bframe = nullptr;
     b.nodes = nullptr;
     b.tris = nullptr;
     b.tri_id = nullptr;
@@ -377,6 +379,10 @@ cudaError_t bvh_build(gwn_geom *g, const Frame &fr, cudaStream_t st) {
     int2 *child = nullptr;
     int *skip = nullptr;
     int nblocks = (int)((n + SORT_TILE - 1) / SORT_TILE);
+    if (g->n_bseq > 0) {                 // boundary records in this frame
+        GWN_TRY(cudaMalloc(&b.bframe, sizeof(float4) * 2 * g->n_bseq));
+        GWN_TRY(launch_bframe(g->bseq, g->n_bseq, fr, b.bframe, st));
+    }
     if (n == 0) {
         b.valid = true;
         return cudaSuccess;

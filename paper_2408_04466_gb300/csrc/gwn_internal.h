@@ -78,6 +78,7 @@ struct MeshBvh {
     int root = 0;              // ref of the root
     float scene_radius = 0.f;  // max |v|_2 over the mesh vertices
     Frame frame;
+    float4 *bframe = nullptr;  // 2 float4 per boundary record: A.(e1, e2, n) hi (+ w), lo
 };
 
 // Device pointers of one 2D chain set.
@@ -172,10 +173,12 @@ cudaError_t launch_traverse(const MeshBvh &b, const QuerySrc &q, int32_t *chi, i
 
 // Boundary term + epilogue (w = chi + B).  defer: int32 scratch of q.n
 // entries for the deferred-query list; defer_count: one device int32.
-cudaError_t launch_bterm3d(const float4 *bseq, int64_t n_bseq, const Frame &fr, const Frame64 &f64,
-                           const QuerySrc &q, const int32_t *chi, float *w_out, float *b_out, int32_t *defer,
-                           int32_t *defer_count, unsigned long long *cnt, int *status, int sm_count,
+cudaError_t launch_bterm3d(const float4 *bseq, const float4 *bframe, int64_t n_bseq, const Frame &fr,
+                           const Frame64 &f64, const QuerySrc &q, const int32_t *chi, float *w_out, float *b_out,
+                           int32_t *defer, int32_t *defer_count, unsigned long long *cnt, int *status, int sm_count,
                            cudaStream_t st);
+// Boundary records in the frame of d (double-float), 2 float4 per record.
+cudaError_t launch_bframe(const float4 *bseq, int64_t n, const Frame &fr, float4 *out, cudaStream_t st);
 
 cudaError_t launch_grad_p(const float4 *bseq, int64_t nb, const QuerySrc &q, const float *grad_w, float *grad_p,
                           cudaStream_t st);

@@ -178,67 +178,72 @@ static __device__ __noinline__ int edge_sign_slow(float3 A, float3 B, float3 P, 
     return sos_tiebreak(A, B, P);
 }
 
-// Edge sign from float32 differences a = A-P, b = B-P (already computed) with
-// the float32 filter; falls back to the slow path.  The bound covers the
-// rounding of the differences (relative u each) and of the determinant.
+// Float32 filters alone: +-1 when the float32 determinant settles the sign,
+// 0 when it does not (the caller defers to the full predicate).
+//
+// They take edge vectors rather than the vectors to both end points:
+// det[A-p, B-p, d] = det[A-p, B-A, d] exactly, and for a small triangle far
+// from p the second form has permanent ~|A-p||B-A| instead of ~|A-p||B-p|,
+// so the filter fails ~|B-A|/|A-p| times less often.  a = fl(A-p) and
+// E = fl(B-A) each carry a relative rounding of u per component; with the
+// products and sums the error stays below 16u times the permanent.
+__device__ __forceinline__ int det3_sign_f32(float3 a, float3 b, float3 c) {
+    float c0 = b.y * c.z - b.z * c.y;
+    float c1 = b.z * c.x - b.x * c.z;
+    float c2 = b.x * c.y - b.y * c.x;
+    float det = a.x * c0 + a.y * c1 + a.z * c2;
+    float perm = fabsf(a.x) * fmaf(fabsf(b.y), fabsf(c.z), fabsf(b.z) * fabsf(c.y))
+               + fabsf(a.y) * fmaf(fabsf(b.z), fabsf(c.x), fabsf(b.x) * fabsf(c.z))
+               + fabsf(a.z) * fmaf(fabsf(b.x), fabsf(c.y), fabsf(b.y) * fabsf(c.x));
+    if (fabsf(det) > GWN_F32_BOUND * perm && perm > 1e-30f) return det > 0.f ? 1 : -1;
+    return 0;
+}
+
+// Edge sign with the float32 filter (det3_sign_f32, on a = A-P and
+// the edge vector B-A) first; falls back to the float64 filter, the exact
+// expansion and the symbolic perturbation.
 __device__ __forceinline__ int edge_sign(float3 a, float3 b, float3 A, float3 B, float3 P, float3 D,
                                          unsigned long long *cnt, int *status) {
-    float c0 = a.y * b.z - a.z * b.y;
-    float c1 = a.z * b.x - a.x * b.z;
-    float c2 = a.x * b.y - a.y * b.x;
-    float det = D.x * c0 + D.y * c1 + D.z * c2;
-    float perm = fabsf(D.x) * fmaf(fabsf(a.y), fabsf(b.z), fabsf(a.z) * fabsf(b.y))
-               + fabsf(D.y) * fmaf(fabsf(a.z), fabsf(b.x), fabsf(a.x) * fabsf(b.z))
-               + fabsf(D.z) * fmaf(fabsf(a.x), fabsf(b.y), fabsf(a.y) * fabsf(b.x));
-    if (fabsf(det) > GWN_F32_BOUND * perm && perm > 1e-30f) return det > 0.f ? 1 : -1;
+    (void)b;
+    float3 E = make_float3(B.x - A.x, B.y - A.y, B.z - A.z);
+    int s = det3_sign_f32(D, a, E);
+    if (s) return s;
     return edge_sign_slow(A, B, P, D, cnt, status);
 }
 
+// Orientation det[V0-P, V1-P, V2-P] with the float32 filter on
+// -det[a, V1-V0, V0-V2] first, then float64 and exact.
 __device__ __forceinline__ int orient_sign(float3 a, float3 b, float3 c, float3 V0, float3 V1, float3 V2,
                                            float3 P, unsigned long long *cnt, int *status) {
-    float det = a.x * (b.y * c.z - b.z * c.y) + a.y * (b.z * c.x - b.x * c.z) + a.z * (b.x * c.y - b.y * c.x);
-    float perm = fabsf(a.x) * fmaf(fabsf(b.y), fabsf(c.z), fabsf(b.z) * fabsf(c.y))
-               + fabsf(a.y) * fmaf(fabsf(b.z), fabsf(c.x), fabsf(b.x) * fabsf(c.z))
-               + fabsf(a.z) * fmaf(fabsf(b.x), fabsf(c.y), fabsf(b.y) * fabsf(c.x));
-    if (fabsf(det) > GWN_F32_BOUND * perm && perm > 1e-30f) return det > 0.f ? 1 : -1;
+    (void)b; (void)c;
+    float3 e0 = make_float3(V1.x - V0.x, V1.y - V0.y, V1.z - V0.z);
+    float3 e2 = make_float3(V0.x - V2.x, V0.y - V2.y, V0.z - V2.z);
+    int s = det3_sign_f32(a, e0, e2);
+    if (s) return -s;
     return orient_sign_f64(V0, V1, V2, P, cnt, status);
 }
 
-// Float32 filter alone: +-1 when the float32 determinant settles the sign,
-// 0 when it does not (the caller defers to the full predicate).
-__device__ __forceinline__ int edge_sign_f32(float3 a, float3 b, float3 D) {
-    float c0 = a.y * b.z - a.z * b.y;
-    float c1 = a.z * b.x - a.x * b.z;
-    float c2 = a.x * b.y - a.y * b.x;
-    float det = D.x * c0 + D.y * c1 + D.z * c2;
-    float perm = fabsf(D.x) * fmaf(fabsf(a.y), fabsf(b.z), fabsf(a.z) * fabsf(b.y))
-               + fabsf(D.y) * fmaf(fabsf(a.z), fabsf(b.x), fabsf(a.x) * fabsf(b.z))
-               + fabsf(D.z) * fmaf(fabsf(a.x), fabsf(b.y), fabsf(a.y) * fabsf(b.x));
-    if (fabsf(det) > GWN_F32_BOUND * perm && perm > 1e-30f) return det > 0.f ? 1 : -1;
-    return 0;
-}
-
-__device__ __forceinline__ int orient_sign_f32(float3 a, float3 b, float3 c) {
-    float det = a.x * (b.y * c.z - b.z * c.y) + a.y * (b.z * c.x - b.x * c.z) + a.z * (b.x * c.y - b.y * c.x);
-    float perm = fabsf(a.x) * fmaf(fabsf(b.y), fabsf(c.z), fabsf(b.z) * fabsf(c.y))
-               + fabsf(a.y) * fmaf(fabsf(b.z), fabsf(c.x), fabsf(b.x) * fabsf(c.z))
-               + fabsf(a.z) * fmaf(fabsf(b.x), fabsf(c.y), fabsf(b.y) * fabsf(c.x));
-    if (fabsf(det) > GWN_F32_BOUND * perm && perm > 1e-30f) return det > 0.f ? 1 : -1;
-    return 0;
-}
+// sign det[a, E, d] = sign det[A-p, B-p, d] (a = A-p, E = B-A)
+__device__ __forceinline__ int edge_sign_f32(float3 a, float3 E, float3 D) { return det3_sign_f32(D, a, E); }
 
 // tri_crossing (below) from float32 filters only: the result when every sign
 // it depends on is settled in float32 (two settled edge signs that differ
 // already rule a crossing out); otherwise `unsure` is set and 0 returned, and
 // the caller recomputes the query with the full predicates.
+//   edge (v0, v1): det[v0-p, v1-v0, d];  (v1, v2): det[v1-p, v2-v1, d];
+//   (v2, v0): det[v2-p, v0-v2, d];  orientation det[v0-p, v1-p, v2-p] =
+//   det[v0-p, v1-v0, v2-v0] = -det[v0-p, v1-v0, v0-v2].
 __device__ __forceinline__ int tri_crossing_fast(float3 v0, float3 v1, float3 v2, float3 p, float3 d, bool &unsure) {
     float3 a = make_float3(v0.x - p.x, v0.y - p.y, v0.z - p.z);
     float3 b = make_float3(v1.x - p.x, v1.y - p.y, v1.z - p.z);
     float3 c = make_float3(v2.x - p.x, v2.y - p.y, v2.z - p.z);
-    int s0 = edge_sign_f32(a, b, d), s1 = edge_sign_f32(b, c, d), s2 = edge_sign_f32(c, a, d);
+    float3 e0 = make_float3(v1.x - v0.x, v1.y - v0.y, v1.z - v0.z);
+    float3 e1 = make_float3(v2.x - v1.x, v2.y - v1.y, v2.z - v1.z);
+    float3 e2 = make_float3(v0.x - v2.x, v0.y - v2.y, v0.z - v2.z);
+    int s0 = edge_sign_f32(a, e0, d), s1 = edge_sign_f32(b, e1, d), s2 = edge_sign_f32(c, e2, d);
     if (s0 * s1 < 0 || s1 * s2 < 0 || s0 * s2 < 0) return 0;
     if (s0 == 0 || s1 == 0 || s2 == 0) { unsure = true; return 0; }
-    int o = orient_sign_f32(a, b, c);
+    int o = -det3_sign_f32(a, e0, e2);
     if (o == 0) { unsure = true; return 0; }
     return o == s0 ? s0 : 0;
 }

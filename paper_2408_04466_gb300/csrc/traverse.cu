@@ -46,7 +46,7 @@ __device__ __forceinline__ bool box_hit(float x0, float x1, float y0, float y1, 
 template <bool FAST>
 __device__ __forceinline__ bool traverse_ray(const BvhNode *__restrict__ nodes, const float4 *__restrict__ tris,
                                              int root, const Frame &fr, const TravParams &tp, float3 p, int &acc,
-                                             bool &unsure, unsigned long long *cnt, int *status) {
+                                             bool &unsure, int &ntests, unsigned long long *cnt, int *status) {
     float3 D = make_float3(fr.d[0], fr.d[1], fr.d[2]);
     float p1 = fmaf(p.z, fr.e1[2], fmaf(p.y, fr.e1[1], p.x * fr.e1[0]));
     float p2 = fmaf(p.z, fr.e2[2], fmaf(p.y, fr.e2[1], p.x * fr.e2[0]));
@@ -71,7 +71,7 @@ __device__ __forceinline__ bool traverse_ray(const BvhNode *__restrict__ nodes, 
         if (node < 0) {
             int t = ~node;
             float4 a = __ldg(&tris[3 * t]), b = __ldg(&tris[3 * t + 1]), c = __ldg(&tris[3 * t + 2]);
-            if (cnt) atomicAdd(&cnt[CNT_TRI_TESTS], 1ull);
+            ntests++;
             float3 v0 = make_float3(a.x, a.y, a.z), v1 = make_float3(b.x, b.y, b.z), v2 = make_float3(c.x, c.y, c.z);
             if (FAST)
                 acc += tri_crossing_fast(v0, v1, v2, p, D, unsure);
@@ -120,9 +120,14 @@ __global__ void __launch_bounds__(256) traverse_kernel(const BvhNode *__restrict
                                                        unsigned long long *cnt, int *status) {
     int64_t idx = q.kind == GWN_QUERY_GRID ? grid_tile_query(q) : (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx < 0 || idx >= q.n) return;
-    int acc;
+    int acc, ntests = 0;
     bool unsure = false;
-    bool ok = traverse_ray<true>(nodes, tris, root, fr, tp, query_point3(q, idx), acc, unsure, cnt, status);
+    bool ok = traverse_ray<true>(nodes, tris, root, fr, tp, query_point3(q, idx), acc, unsure, ntests, cnt, status);
+    if (cnt) {                                   // statistics: one atomic per warp
+        unsigned m = __activemask();
+        int tot = __reduce_add_sync(m, ntests);
+        if ((threadIdx.x & 31) == __ffs(m) - 1) atomicAdd(&cnt[CNT_TRI_TESTS], (unsigned long long)tot);
+    }
     if (ok && unsure)
         defer_query(defer, defer_count, idx);
     else
@@ -144,28 +149,39 @@ __global__ void __launch_bounds__(128) traverse_careful_kernel(const BvhNode *__
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         int64_t idx = defer[i];
         if (idx < 0 || idx >= q.n) { atomicOr(status, ST_BAD_INPUT); continue; }
-        int acc;
+        int acc, ntests = 0;
         bool unsure = false;
-        bool ok = traverse_ray<false>(nodes, tris, root, fr, tp, query_point3(q, idx), acc, unsure, cnt, status);
+        bool ok = traverse_ray<false>(nodes, tris, root, fr, tp, query_point3(q, idx), acc, unsure, ntests, cnt,
+                                      status);
+        if (cnt) atomicAdd(&cnt[CNT_TRI_TESTS], (unsigned long long)ntests);
         chi[idx] = ok ? acc : INT32_MIN;
     }
 }
 
 // Warp-packet traversal for grid queries: the 32 rays of a warp (a 4x4x2
 // grid tile, neighbours in the projection plane) walk the tree together.
-// The stack is warp-uniform (every lane holds the same copy); at a node each
-// lane tests its own ray against both child boxes and the warp descends into
-// a child if any lane's ray hits it; at a leaf only the lanes whose ray box
-// hits the triangle run the float32 crossing test (a query whose test needs
-// more is deferred to traverse_careful_kernel).  Node and triangle loads are
-// warp-uniform (one broadcast per warp).  Lanes outside the grid take part
-// with an empty box.
+// The traversal order is warp-uniform: at a node each lane tests its own ray
+// against both child boxes and the warp descends into a child if any lane's
+// ray hits it; the stack lives in shared memory (one per warp).  Node loads
+// are warp-uniform (one broadcast per warp).
+//
+// Leaves are compacted: a leaf hit by the ray boxes of a few lanes appends
+// one (triangle, lane) pair per such lane to a per-warp buffer, and whenever
+// 32 pairs are pending every lane tests one pair (the float32 crossing test,
+// for the query of the pair's lane, whose point it fetches with a shuffle)
+// and adds the result to that lane's count in shared memory.  So a triangle
+// test costs one lane-slot instead of a warp-wide pass per visited leaf.
+// A query with an unsettled float32 sign is deferred to
+// traverse_careful_kernel.  Lanes outside the grid take part with an empty
+// box.  Requires fewer than 2^26 triangles (pair = triangle << 5 | lane).
 __global__ void __launch_bounds__(256) traverse_packet_kernel(const BvhNode *__restrict__ nodes,
                                                               const float4 *__restrict__ tris,
                                                               const float4 *__restrict__ tbox, int root, Frame fr,
                                                               TravParams tp, QuerySrc q, int32_t *__restrict__ chi,
                                                               int32_t *defer, int32_t *defer_count,
                                                               unsigned long long *cnt, int *status) {
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     int64_t idx = grid_tile_query(q);
     bool valid = idx >= 0 && idx < q.n;
     float3 p = valid ? query_point3(q, idx) : make_float3(0.f, 0.f, 0.f);
@@ -176,19 +192,47 @@ __global__ void __launch_bounds__(256) traverse_packet_kernel(const BvhNode *__r
     float pad = fmaf(tp.pad_rel, fabsf(p.x) + fabsf(p.y) + fabsf(p.z), tp.pad_abs);
     float xlo = p1 - pad, xhi = p1 + pad, ylo = p2 - pad, yhi = p2 + pad, zlo = p3 - pad;
     if (!valid) { xlo = 3.4e38f; xhi = -3.4e38f; }     // never hits
-    int acc = 0;
-    bool unsure = false;
-    // The traversal order is warp-uniform (every decision goes through
-    // __any_sync), so the warp shares one stack in shared memory; every lane
-    // writes the same value on a push.
     __shared__ int s_stack[256 / 32][GWN_STACK];
-    int *stack = s_stack[threadIdx.x >> 5];
+    __shared__ int s_pair[256 / 32][64];
+    __shared__ int s_acc[256 / 32][32];
+    __shared__ unsigned s_uns[256 / 32];
+    int *stack = s_stack[w];
+    int *pairs = s_pair[w];
+    s_acc[w][lane] = 0;
+    if (lane == 0) s_uns[w] = 0u;
+    __syncwarp();
+    int ntests = 0;
+    int npairs = 0;                               // warp-uniform
+    // test the first min(npairs, 32) pending pairs, one per lane, and move
+    // the rest to the front; returns the number still pending (< 32)
+    auto flush = [&](int n) -> int {
+        int m = n < 32 ? n : 32;
+        int pr = lane < m ? pairs[lane] : -1;
+        int ql = pr >= 0 ? (pr & 31) : lane;
+        float qx = __shfl_sync(FULL, p.x, ql), qy = __shfl_sync(FULL, p.y, ql), qz = __shfl_sync(FULL, p.z, ql);
+        if (pr >= 0) {
+            int t = pr >> 5;
+            float4 a = __ldg(&tris[3 * t]), b = __ldg(&tris[3 * t + 1]), c = __ldg(&tris[3 * t + 2]);
+            bool uns = false;
+            int r = tri_crossing_fast(make_float3(a.x, a.y, a.z), make_float3(b.x, b.y, b.z),
+                                      make_float3(c.x, c.y, c.z), make_float3(qx, qy, qz), D, uns);
+            if (r) atomicAdd(&s_acc[w][ql], r);
+            if (uns) atomicOr(&s_uns[w], 1u << ql);
+        }
+        int rem = n - m;
+        __syncwarp();
+        int moved = lane < rem ? pairs[m + lane] : 0;
+        __syncwarp();
+        if (lane < rem) pairs[lane] = moved;
+        __syncwarp();
+        return rem;
+    };
     int sp = 0;
     int node = root;
     bool bad = false;
     for (int64_t iter = 0;; iter++) {
         if (iter > tp.max_iter) {
-            if ((threadIdx.x & 31) == 0) {
+            if (lane == 0) {
                 atomicOr(status, ST_TIMEOUT);
                 if (cnt) atomicAdd(&cnt[CNT_TIMEOUT], 1ull);
             }
@@ -204,11 +248,13 @@ __global__ void __launch_bounds__(256) traverse_packet_kernel(const BvhNode *__r
             int t = ~node;
             float4 bx = __ldg(&tbox[2 * t]), bz = __ldg(&tbox[2 * t + 1]);
             bool hit = box_hit(bx.x, bx.y, bx.z, bx.w, bz.x, xlo, xhi, ylo, yhi, zlo);
-            if (hit) {
-                float4 a = __ldg(&tris[3 * t]), b = __ldg(&tris[3 * t + 1]), c = __ldg(&tris[3 * t + 2]);
-                if (cnt) atomicAdd(&cnt[CNT_TRI_TESTS], 1ull);
-                acc += tri_crossing_fast(make_float3(a.x, a.y, a.z), make_float3(b.x, b.y, b.z),
-                                         make_float3(c.x, c.y, c.z), p, D, unsure);
+            unsigned m = __ballot_sync(FULL, hit);
+            if (m) {
+                if (hit) pairs[npairs + __popc(m & ((1u << lane) - 1u))] = (t << 5) | lane;
+                npairs += __popc(m);
+                ntests += hit;
+                __syncwarp();
+                if (npairs >= 32) npairs = flush(npairs);
             }
             if (sp == 0) break;
             node = stack[--sp];
@@ -217,11 +263,11 @@ __global__ void __launch_bounds__(256) traverse_packet_kernel(const BvhNode *__r
         const BvhNode nd = nodes[node];
         bool h0 = box_hit(nd.lo.x, nd.lo.y, nd.lo.z, nd.lo.w, nd.z.x, xlo, xhi, ylo, yhi, zlo);
         bool h1 = box_hit(nd.hi.x, nd.hi.y, nd.hi.z, nd.hi.w, nd.z.y, xlo, xhi, ylo, yhi, zlo);
-        bool a0 = __any_sync(0xffffffffu, h0), a1 = __any_sync(0xffffffffu, h1);
+        bool a0 = __any_sync(FULL, h0), a1 = __any_sync(FULL, h1);
         int c0 = __float_as_int(nd.z.z), c1 = __float_as_int(nd.z.w);
         if (a0 && a1) {
             if (sp >= GWN_STACK) {
-                if ((threadIdx.x & 31) == 0) {
+                if (lane == 0) {
                     atomicOr(status, ST_STACK_OVERFLOW);
                     if (cnt) atomicAdd(&cnt[CNT_STACK_OVERFLOW], 1ull);
                 }
@@ -240,11 +286,24 @@ __global__ void __launch_bounds__(256) traverse_packet_kernel(const BvhNode *__r
             node = stack[--sp];
         }
     }
+    if (!bad)
+        while (npairs > 0) npairs = flush(npairs);
+    __syncwarp();
+    int acc = s_acc[w][lane];
+    bool unsure = (s_uns[w] >> lane) & 1u;
     if (valid) {
         if (!bad && unsure)
             defer_query(defer, defer_count, idx);
         else
             chi[idx] = bad ? INT32_MIN : acc;
+    }
+    if (cnt) {                                   // statistics: one atomic per block
+        __shared__ unsigned s_tests;
+        if (threadIdx.x == 0) s_tests = 0;
+        __syncthreads();
+        atomicAdd(&s_tests, (unsigned)ntests);
+        __syncthreads();
+        if (threadIdx.x == 0) atomicAdd(&cnt[CNT_TRI_TESTS], (unsigned long long)s_tests);
     }
 }
 
@@ -299,7 +358,7 @@ cudaError_t launch_traverse(const MeshBvh &b, const QuerySrc &q, int32_t *chi, i
     if (e != cudaSuccess) return e;
     // Grid queries come in spatially coherent warp tiles: one warp-uniform
     // stack per tile.  Scattered points take one stack per thread.
-    if (q.kind == GWN_QUERY_GRID && b.tbox)
+    if (q.kind == GWN_QUERY_GRID && b.tbox && b.n < (int64_t(1) << 26))
         traverse_packet_kernel<<<(unsigned)tblocks, 256, 0, st>>>(b.nodes, b.tris, b.tbox, b.root, b.frame, tp, q,
                                                                   chi, defer, defer_count, cnt, status);
     else
