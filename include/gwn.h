@@ -115,7 +115,8 @@ typedef struct gwn_stats {
     float ms_traverse;          /* crossing counts */
     float ms_boundary;          /* boundary term + epilogue */
     float ms_total;
-    int64_t n_deferred_traverse;  /* queries recounted with the full predicates (float32 filter unsettled) */
+    int64_t n_deferred_traverse;  /* (query, triangle) pairs the float32 filter left unsettled, settled with the
+                                     full predicates (plus any query recounted whole when the pair list is full) */
     int64_t n_deferred_boundary;  /* queries whose boundary term was recomputed by the careful pass */
 } gwn_stats;
 
@@ -211,9 +212,9 @@ GWN_API gwn_status gwn_eval_host(gwn_geom *g, const gwn_queries *q, const float 
 
 /* Tuning plan for batched evaluation. */
 typedef struct gwn_plan {
-    int32_t threads_per_block;  /* 0 = autotuned */
-    int32_t rows_per_item;      /* 2D query-phase work item height (rows) */
-    int32_t pieces_per_item;    /* 2D root-phase work item size */
+    int32_t threads_per_block;  /* 0 = autotuned (128 or 256) */
+    int32_t rows_per_item;      /* 2D work item height in grid rows, 1..256; 0 = autotuned */
+    int32_t pieces_per_item;    /* reserved, 0 */
     int32_t use_graph;          /* 1 = capture the launch sequence in a CUDA graph */
 } gwn_plan;
 

@@ -283,6 +283,8 @@ GWN_API gwn_status gwn_ctx_create(gwn_ctx **out, int device, void *cuda_stream) 
     if (e == cudaSuccess) e = cudaMalloc(&c->d_status, sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&c->d_cnt, sizeof(unsigned long long) * CNT_NUM);
     if (e == cudaSuccess) e = cudaMalloc(&c->d_defer_count, sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_tpairs, sizeof(int2) * GWN_TPAIR_CAP);
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_tpair_count, sizeof(int32_t));
     if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(c->d_cnt, 0, sizeof(unsigned long long) * CNT_NUM);
     for (int i = 0; i < 8 && e == cudaSuccess; i++) e = cudaEventCreate(&c->ev[i]);
@@ -325,6 +327,8 @@ GWN_API void gwn_ctx_destroy(gwn_ctx *ctx) {
     if (ctx->d_status) cudaFree(ctx->d_status);
     if (ctx->d_cnt) cudaFree(ctx->d_cnt);
     if (ctx->d_defer_count) cudaFree(ctx->d_defer_count);
+    if (ctx->d_tpairs) cudaFree(ctx->d_tpairs);
+    if (ctx->d_tpair_count) cudaFree(ctx->d_tpair_count);
     if (ctx->events)
         for (int i = 0; i < 8; i++) cudaEventDestroy(ctx->ev[i]);
     delete ctx;
@@ -792,8 +796,8 @@ GWN_API gwn_status gwn_eval(gwn_geom *g, const gwn_queries *q, const float *d, v
         int32_t *defer = (int32_t *)arena_get(ctx, 4, sizeof(int32_t) * nq, &e);
         if (!defer) return cuda_fail(e, "deferred-query list");
         if (stats) CK(cudaEventRecord(ctx->ev[1], ctx->stream), "event");
-        e = launch_traverse(g->bvh, src, chi, defer, ctx->d_defer_count, stats ? ctx->d_cnt : nullptr, ctx->d_status,
-                            ctx->sm_count, ctx->stream);
+        e = launch_traverse(g->bvh, src, chi, defer, ctx->d_defer_count, ctx->d_tpairs, ctx->d_tpair_count,
+                            stats ? ctx->d_cnt : nullptr, ctx->d_status, ctx->sm_count, ctx->stream);
         if (e != cudaSuccess) return cuda_fail(e, "crossing traversal");
         if (stats) CK(cudaEventRecord(ctx->ev[2], ctx->stream), "event");
         e = launch_bterm3d(g->bseq, g->bvh.bframe, g->n_bseq, g->bvh.frame, make_frame64(d), src, chi, (float *)w_out,

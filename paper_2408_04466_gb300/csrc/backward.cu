@@ -33,24 +33,41 @@ struct EdgeGrad {
     float cx, cy, cz, i0, i1;
 };
 
+// MUFU reciprocal and reciprocal square root (rcp/rsqrt.approx, ~1-2 ulp):
+// the gradient is needed to ~1e-4 relative, and these replace two IEEE
+// square roots and five divisions per (query, edge) pair.  Arguments are
+// clamped to normal floats.
+__device__ __forceinline__ float grcp(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float grsqrt(float x) {
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// inv_e2 = 1/|E|^2 of the edge (computed once per edge)
 __device__ __forceinline__ EdgeGrad edge_grad(float ax, float ay, float az, float bx, float by, float bz,
-                                              float ex, float ey, float ez) {
+                                              float ex, float ey, float ez, float e2, float inv_e2) {
     EdgeGrad g;
     g.cx = ay * ez - az * ey;
     g.cy = az * ex - ax * ez;
     g.cz = ax * ey - ay * ex;
     float del = fmaxf(g.cx * g.cx + g.cy * g.cy + g.cz * g.cz, 1e-37f);
-    float la = sqrtf(ax * ax + ay * ay + az * az);
-    float lb = sqrtf(bx * bx + by * by + bz * bz);
-    float e2 = fmaxf(ex * ex + ey * ey + ez * ez, 1e-37f);
+    float ra2 = fmaxf(ax * ax + ay * ay + az * az, 1e-37f);
+    float rb2 = fmaxf(bx * bx + by * by + bz * bz, 1e-37f);
+    float ia = grsqrt(ra2), ib = grsqrt(rb2);
+    float la = ra2 * ia, lb = rb2 * ib;
     float ea = ex * ax + ey * ay + ez * az;
     float eab = 2.f * ea + e2;                       // E.(a+b) = |b|^2 - |a|^2
-    float s = la + lb;
-    float num0 = e2 * la - ea * eab / s;
-    float inv_ab = 1.f / (la * lb);
-    g.i0 = num0 * inv_ab / del;
-    float invdiff = eab * inv_ab / s;                // 1/|a| - 1/|b|
-    g.i1 = (invdiff - ea * g.i0) / e2;
+    float inv_s = grcp(la + lb);
+    float inv_ab = ia * ib;                          // 1/(|a||b|)
+    float num0 = e2 * la - ea * eab * inv_s;
+    g.i0 = num0 * inv_ab * grcp(del);
+    float invdiff = eab * inv_ab * inv_s;            // 1/|a| - 1/|b|
+    g.i1 = (invdiff - ea * g.i0) * inv_e2;
     return g;
 }
 
@@ -70,10 +87,11 @@ __global__ void __launch_bounds__(256) grad_p_kernel(const float4 *__restrict__ 
         float4 A = __ldg(&bseq[k - 1]), B = __ldg(&bseq[k]);
         if (B.w == 0.f) continue;
         float ex = B.x - A.x, ey = B.y - A.y, ez = B.z - A.z;
+        float e2 = fmaxf(ex * ex + ey * ey + ez * ez, 1e-37f), inv_e2 = grcp(e2);
 #pragma unroll
         for (int j = 0; j < K; j++) {
             EdgeGrad g = edge_grad(A.x - px[j], A.y - py[j], A.z - pz[j], B.x - px[j], B.y - py[j], B.z - pz[j],
-                                   ex, ey, ez);
+                                   ex, ey, ez, e2, inv_e2);
             float w = g.i0 * B.w;
             gx[j] = fmaf(g.cx, w, gx[j]);
             gy[j] = fmaf(g.cy, w, gy[j]);
@@ -110,6 +128,7 @@ __global__ void __launch_bounds__(GV_THREADS) grad_v_partial_kernel(const float4
     float4 B = active ? bseq[k] : make_float4(0.f, 0.f, 0.f, 0.f);
     active = active && B.w != 0.f;
     float ex = B.x - A.x, ey = B.y - A.y, ez = B.z - A.z;
+    float e2 = fmaxf(ex * ex + ey * ey + ez * ez, 1e-37f), inv_e2 = grcp(e2);
     float sA[3] = {0.f, 0.f, 0.f}, sB[3] = {0.f, 0.f, 0.f};
     for (int64_t t0 = q0; t0 < q1; t0 += GV_QTILE) {
         __syncthreads();
@@ -127,7 +146,8 @@ __global__ void __launch_bounds__(GV_THREADS) grad_v_partial_kernel(const float4
             int cnt = (int)(q1 - t0 < GV_QTILE ? q1 - t0 : GV_QTILE);
             for (int i = 0; i < cnt; i++) {
                 float4 p = qs[i];
-                EdgeGrad g = edge_grad(A.x - p.x, A.y - p.y, A.z - p.z, B.x - p.x, B.y - p.y, B.z - p.z, ex, ey, ez);
+                EdgeGrad g = edge_grad(A.x - p.x, A.y - p.y, A.z - p.z, B.x - p.x, B.y - p.y, B.z - p.z, ex, ey, ez,
+                                       e2, inv_e2);
                 float wa = -(g.i0 - g.i1) * p.w, wb = -g.i1 * p.w;
                 sA[0] = fmaf(g.cx, wa, sA[0]); sA[1] = fmaf(g.cy, wa, sA[1]); sA[2] = fmaf(g.cz, wa, sA[2]);
                 sB[0] = fmaf(g.cx, wb, sB[0]); sB[1] = fmaf(g.cy, wb, sB[1]); sB[2] = fmaf(g.cz, wb, sB[2]);

@@ -58,7 +58,9 @@ gwn_status eval2d_single(gwn_geom *g, const QuerySrc &src, void *w_out, int32_t 
     S.ax = cs.dtype == GWN_F64 ? (const void *)src.ax64[0] : (const void *)src.ax[0];
     S.ay = cs.dtype == GWN_F64 ? (const void *)src.ax64[1] : (const void *)src.ax[1];
     S.out_off = 0;
-    const int rows = 1;
+    // rows per work item: enough items to fill the device twice, at most 32
+    int64_t rows64 = S.ny / (2 * (int64_t)(ctx->sm_count > 0 ? ctx->sm_count : 152));
+    const int rows = (int)(rows64 < 1 ? 1 : (rows64 > 32 ? 32 : rows64));
     std::vector<Set2D> sets(1, S);
     std::vector<int2> items;
     make_items(sets, rows, items);
@@ -203,6 +205,12 @@ extern "C" GWN_API gwn_status gwn_eval_batch(gwn_geom *g, const gwn_queries *que
     }
     int want_threads = plan && plan->threads_per_block > 0 ? plan->threads_per_block : 0;
     int want_rows = plan && plan->rows_per_item > 0 ? plan->rows_per_item : 0;
+    if (want_rows > 256 || (plan && (plan->threads_per_block < 0 || plan->threads_per_block > 1024 ||
+                                     plan->threads_per_block % 32 != 0))) {
+        set_error("gwn_eval_batch: plan rows_per_item must be 0..256 and threads_per_block 0 or a multiple of 32 up "
+                  "to 1024");
+        return GWN_E_INVALID;
+    }
     int use_graph = plan ? plan->use_graph : 1;
     key.push_back((double)want_threads);
     key.push_back((double)want_rows);
@@ -219,7 +227,7 @@ extern "C" GWN_API gwn_status gwn_eval_batch(gwn_geom *g, const gwn_queries *que
         if (want_threads && want_rows) cands.emplace_back(want_threads, want_rows);
         else {
             int ts[2] = {128, 256};
-            int rs[4] = {1, 2, 4, 8};
+            int rs[4] = {4, 16, 64, 256};
             for (int t : ts)
                 for (int r : rs)
                     if ((!want_threads || t == want_threads) && (!want_rows || r == want_rows)) cands.emplace_back(t, r);

@@ -85,8 +85,88 @@ __device__ T piece_root_x(const T *c, T u0, T u1, T ya, T yb, T yr, int *iters_o
 }
 
 
-constexpr int CHUNK = 1024;
+constexpr int CHUNK = 1024;          // crossings per pass of the per-row fallback
+constexpr int MAX_ROWS = 256;        // rows per work item
+constexpr int CAP = 8192;            // crossings binned per work item
 
+// shared-memory layout: xs[CAP] (T), ys[MAX_ROWS] (T), roff[MAX_ROWS + 1],
+// rcur[MAX_ROWS] (int), dirs[CAP] (int8), then the fallback's chi_row
+template <typename T>
+__host__ __device__ constexpr size_t eval2d_fallback_off() {
+    return ((sizeof(T) * (CAP + MAX_ROWS) + sizeof(int) * (2 * MAX_ROWS + 1) + CAP) + 15) & ~(size_t)15;
+}
+
+// Fast float32 atan2 for the chord term (half-angle form: v = y/(|z| + |x|)
+// in [-1, 1], atan2 = 2 atan(v) or copysign(pi, y) - 2 atan(v) for x < 0;
+// atan(v) = v P(v^2) with the degree-8 odd minimax polynomial of the 3D
+// boundary term, relative error 1.5e-8).
+__device__ __forceinline__ float atan2_fast(float y, float x) {
+    float z = sqrtf(fmaf(x, x, y * y));
+    float d = z + fabsf(x);
+    if (!(d > 0.f)) return 0.f;
+    float v = y / d, v2 = v * v;
+    float q = fmaf(0.00284989f, v2, -0.01606863f);
+    q = fmaf(q, v2, 0.04269152f);
+    q = fmaf(q, v2, -0.07504295f);
+    q = fmaf(q, v2, 0.10640934f);
+    q = fmaf(q, v2, -0.14203644f);
+    q = fmaf(q, v2, 0.19992619f);
+    q = fmaf(q, v2, -0.33333073f);
+    q = fmaf(q, v2, 0.99999998f);
+    float a2 = 2.f * (q * v);
+    return x >= 0.f ? a2 : copysignf(3.14159265358979f, y) - a2;
+}
+template <typename T> struct Chord;
+template <> struct Chord<float> {
+    static __device__ __forceinline__ float atan2_(float y, float x) { return atan2_fast(y, x); }
+};
+template <> struct Chord<double> {
+    static __device__ __forceinline__ double atan2_(double y, double x) { return atan2(y, x); }
+};
+
+// first index i in [0, n) with ys[i] >= v (n if none); ys non-decreasing
+template <typename T>
+__device__ __forceinline__ int lower_bound_rows(const T *ys, int n, T v) {
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (ys[mid] < v) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+// chord terms of the set's chains at (xq, yr): the chord's crossing with the
+// +x ray (half-open in y) and minus the angle it subtends, / 2 pi
+template <typename T>
+__device__ __forceinline__ T chord_terms(const T *__restrict__ ctrl, const int64_t *__restrict__ chain_off,
+                                         const Set2D &S, T xq, T yr, int &chi) {
+    T term = T(0);
+    for (int64_t c = S.c_lo; c < S.c_hi; c++) {
+        const T *sp = ctrl + 2 * chain_off[c];
+        const T *ep = ctrl + 2 * (chain_off[c + 1] - 1);
+        T sx = sp[0] - xq, sy = sp[1] - yr, ex = ep[0] - xq, ey = ep[1] - yr;
+        T cr = ex * sy - ey * sx;             // cross(e - p, s - p)
+        T lo = ey < sy ? ey : sy, hi = ey < sy ? sy : ey;
+        if (lo <= T(0) && T(0) < hi) {
+            bool up = sy > ey;
+            bool right = up ? (cr > T(0)) : (cr < T(0));
+            if (right) chi += up ? 1 : -1;
+        }
+        term += Chord<T>::atan2_(-cr, sx * ex + sy * ey) * Num<T>::inv2pi;
+    }
+    return term;
+}
+
+// Work items are (set, block of rows).  An item finds the rows each of the
+// set's pieces crosses: a piece with end values y0, y1 is crossed by row r
+// iff min <= y_r < max, and since the row values are non-decreasing those
+// rows form one range, found by binary search in the item's row values.
+// Crossings are binned by row in shared memory (a counting pass, a prefix
+// sum, a filling pass that finds each root), so the work is proportional to
+// the pieces plus the crossings rather than to rows x pieces.  Then every
+// query of a row adds the signed crossings to its right and the chord terms.
+// An item with more than CAP crossings falls back to scanning the pieces
+// once per row, CHUNK crossings at a time.
 template <typename T>
 __global__ void eval2d_kernel(const T *__restrict__ ctrl, const int64_t *__restrict__ chain_off,
                               const int64_t *__restrict__ piece_seg, const double *__restrict__ piece_u,
@@ -94,10 +174,13 @@ __global__ void eval2d_kernel(const T *__restrict__ ctrl, const int64_t *__restr
                               const int2 *__restrict__ items, int64_t n_items, unsigned long long *counter,
                               int rows_per_item, T *__restrict__ w_out, int32_t *__restrict__ chi_out,
                               T *__restrict__ b_out, unsigned long long *cnt, int *status, int max_nx) {
-    extern __shared__ unsigned char smem_raw[];
-    T *xs = (T *)smem_raw;                                    // CHUNK crossings
-    int *dirs = (int *)(xs + CHUNK);                          // CHUNK directions
-    int *chi_row = dirs + CHUNK;                              // max_nx counts
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *xs = (T *)smem_raw;                                    // CAP crossings
+    T *ys = xs + CAP;                                         // MAX_ROWS row values
+    int *roff = (int *)(ys + MAX_ROWS);                       // MAX_ROWS + 1 offsets
+    int *rcur = roff + MAX_ROWS + 1;                          // MAX_ROWS counts / cursors
+    signed char *dirs = (signed char *)(rcur + MAX_ROWS);     // CAP directions
+    int *chi_row = (int *)(smem_raw + eval2d_fallback_off<T>());   // max_nx counts (fallback)
     __shared__ int ncross;
     __shared__ long long item_sh;
     for (int64_t guard = 0; guard <= n_items; guard++) {
@@ -112,73 +195,123 @@ __global__ void eval2d_kernel(const T *__restrict__ ctrl, const int64_t *__restr
         const T *ay = (const T *)S.ay;
         int64_t r0 = (int64_t)it.y * rows_per_item;
         int64_t r1 = r0 + rows_per_item < S.ny ? r0 + rows_per_item : S.ny;
-        for (int64_t r = r0; r < r1; r++) {
-            T yr = ay[r];
-            for (int64_t i = threadIdx.x; i < S.nx; i += blockDim.x) chi_row[i] = 0;
-            for (int64_t c0 = S.p_lo; c0 < S.p_hi; c0 += CHUNK) {
-                if (threadIdx.x == 0) ncross = 0;
-                __syncthreads();
-                int64_t c1 = c0 + CHUNK < S.p_hi ? c0 + CHUNK : S.p_hi;
-                for (int64_t p = c0 + threadIdx.x; p < c1; p += blockDim.x) {
-                    T ya = (T)piece_y[2 * p], yb = (T)piece_y[2 * p + 1];
-                    T lo = ya < yb ? ya : yb, hi = ya < yb ? yb : ya;
-                    if (!(lo <= yr && yr < hi)) continue;
-                    const T *cp = ctrl + 2 * piece_seg[p];
-                    T c[8];
+        const int nr = (int)(r1 - r0);
+        for (int i = threadIdx.x; i < nr; i += blockDim.x) {
+            ys[i] = ay[r0 + i];
+            rcur[i] = 0;
+        }
+        __syncthreads();
+        // pass 1: crossings per row
+        for (int64_t p = S.p_lo + threadIdx.x; p < S.p_hi; p += blockDim.x) {
+            T ya = (T)piece_y[2 * p], yb = (T)piece_y[2 * p + 1];
+            T lo = ya < yb ? ya : yb, hi = ya < yb ? yb : ya;
+            int ra = lower_bound_rows(ys, nr, lo), rb = lower_bound_rows(ys, nr, hi);
+            for (int r = ra; r < rb; r++) atomicAdd(&rcur[r], 1);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int acc = 0;
+            for (int r = 0; r < nr; r++) {
+                roff[r] = acc;
+                acc += rcur[r];
+            }
+            roff[nr] = acc;
+        }
+        __syncthreads();
+        const int total = roff[nr];
+        if (cnt && threadIdx.x == 0) atomicAdd(&cnt[CNT_ROOTS], (unsigned long long)total);
+        if (total <= CAP) {
+            for (int i = threadIdx.x; i < nr; i += blockDim.x) rcur[i] = 0;
+            __syncthreads();
+            // pass 2: the roots, binned by row
+            for (int64_t p = S.p_lo + threadIdx.x; p < S.p_hi; p += blockDim.x) {
+                T ya = (T)piece_y[2 * p], yb = (T)piece_y[2 * p + 1];
+                T lo = ya < yb ? ya : yb, hi = ya < yb ? yb : ya;
+                int ra = lower_bound_rows(ys, nr, lo), rb = lower_bound_rows(ys, nr, hi);
+                if (ra >= rb) continue;
+                const T *cp = ctrl + 2 * piece_seg[p];
+                T c[8];
 #pragma unroll
-                    for (int k = 0; k < 8; k++) c[k] = cp[k];
+                for (int k = 0; k < 8; k++) c[k] = cp[k];
+                T u0 = (T)piece_u[2 * p], u1 = (T)piece_u[2 * p + 1];
+                signed char dir = yb > ya ? 1 : -1;
+                for (int r = ra; r < rb; r++) {
                     int iters;
-                    T x = piece_root_x<T>(c, (T)piece_u[2 * p], (T)piece_u[2 * p + 1], ya, yb, yr, &iters);
+                    T x = piece_root_x<T>(c, u0, u1, ya, yb, ys[r], &iters);
                     if (iters >= Num<T>::max_iter && status) atomicOr(status, ST_TIMEOUT);
-                    int slot = atomicAdd(&ncross, 1);
+                    int slot = roff[r] + atomicAdd(&rcur[r], 1);
                     xs[slot] = x;
-                    dirs[slot] = yb > ya ? 1 : -1;
-                    if (cnt) atomicAdd(&cnt[CNT_ROOTS], 1ull);
+                    dirs[slot] = dir;
                 }
-                __syncthreads();
-                int nc = ncross;
-                if (nc > 0) {
+            }
+            __syncthreads();
+            // queries: signed crossings to the right + chord terms
+            for (int r = 0; r < nr; r++) {
+                const T yr = ys[r];
+                const int k0 = roff[r], k1 = roff[r + 1];
+                for (int64_t i = threadIdx.x; i < S.nx; i += blockDim.x) {
+                    T xq = ax[i];
+                    int chi = 0;
+                    for (int k = k0; k < k1; k++) chi += xs[k] > xq ? (int)dirs[k] : 0;
+                    T term = chord_terms<T>(ctrl, chain_off, S, xq, yr, chi);
+                    int64_t o = S.out_off + (r0 + r) * S.nx + i;
+                    if (w_out) w_out[o] = (T)chi + term;
+                    if (chi_out) chi_out[o] = chi;
+                    if (b_out) b_out[o] = term;
+                }
+            }
+        } else {
+            // fallback: one row at a time, CHUNK crossings per pass
+            for (int r = 0; r < nr; r++) {
+                const T yr = ys[r];
+                for (int64_t i = threadIdx.x; i < S.nx; i += blockDim.x) chi_row[i] = 0;
+                for (int64_t c0 = S.p_lo; c0 < S.p_hi; c0 += CHUNK) {
+                    if (threadIdx.x == 0) ncross = 0;
+                    __syncthreads();
+                    int64_t c1 = c0 + CHUNK < S.p_hi ? c0 + CHUNK : S.p_hi;
+                    for (int64_t p = c0 + threadIdx.x; p < c1; p += blockDim.x) {
+                        T ya = (T)piece_y[2 * p], yb = (T)piece_y[2 * p + 1];
+                        T lo = ya < yb ? ya : yb, hi = ya < yb ? yb : ya;
+                        if (!(lo <= yr && yr < hi)) continue;
+                        const T *cp = ctrl + 2 * piece_seg[p];
+                        T c[8];
+#pragma unroll
+                        for (int k = 0; k < 8; k++) c[k] = cp[k];
+                        int iters;
+                        T x = piece_root_x<T>(c, (T)piece_u[2 * p], (T)piece_u[2 * p + 1], ya, yb, yr, &iters);
+                        if (iters >= Num<T>::max_iter && status) atomicOr(status, ST_TIMEOUT);
+                        int slot = atomicAdd(&ncross, 1);
+                        xs[slot] = x;
+                        dirs[slot] = yb > ya ? 1 : -1;
+                    }
+                    __syncthreads();
+                    int nc = ncross;
                     for (int64_t i = threadIdx.x; i < S.nx; i += blockDim.x) {
                         T xq = ax[i];
                         int acc = 0;
-                        for (int k = 0; k < nc; k++) acc += xs[k] > xq ? dirs[k] : 0;
+                        for (int k = 0; k < nc; k++) acc += xs[k] > xq ? (int)dirs[k] : 0;
                         chi_row[i] += acc;
                     }
+                    __syncthreads();
+                }
+                for (int64_t i = threadIdx.x; i < S.nx; i += blockDim.x) {
+                    int chi = chi_row[i];
+                    T term = chord_terms<T>(ctrl, chain_off, S, ax[i], yr, chi);
+                    int64_t o = S.out_off + (r0 + r) * S.nx + i;
+                    if (w_out) w_out[o] = (T)chi + term;
+                    if (chi_out) chi_out[o] = chi;
+                    if (b_out) b_out[o] = term;
                 }
                 __syncthreads();
             }
-            // epilogue: chord terms of every chain of the set
-            for (int64_t i = threadIdx.x; i < S.nx; i += blockDim.x) {
-                T xq = ax[i];
-                int chi = chi_row[i];
-                T term = T(0);
-                for (int64_t c = S.c_lo; c < S.c_hi; c++) {
-                    const T *sp = ctrl + 2 * chain_off[c];
-                    const T *ep = ctrl + 2 * (chain_off[c + 1] - 1);
-                    T sx = sp[0] - xq, sy = sp[1] - yr, ex = ep[0] - xq, ey = ep[1] - yr;
-                    // chord e -> s against the +x ray (half-open in y)
-                    T cr = ex * sy - ey * sx;             // cross(e - p, s - p)
-                    T lo = ey < sy ? ey : sy, hi = ey < sy ? sy : ey;
-                    if (lo <= T(0) && T(0) < hi) {
-                        bool up = sy > ey;
-                        bool right = up ? (cr > T(0)) : (cr < T(0));
-                        if (right) chi += up ? 1 : -1;
-                    }
-                    term += Num<T>::atan2_(-cr, sx * ex + sy * ey) * Num<T>::inv2pi;
-                }
-                int64_t o = S.out_off + r * S.nx + i;
-                if (w_out) w_out[o] = (T)chi + term;
-                if (chi_out) chi_out[o] = chi;
-                if (b_out) b_out[o] = term;
-            }
-            __syncthreads();
         }
+        __syncthreads();
     }
 }
 
 size_t eval2d_smem(int dtype, int64_t max_nx) {
-    size_t esz = dtype == GWN_F64 ? 8 : 4;
-    return esz * CHUNK + sizeof(int) * CHUNK + sizeof(int) * (size_t)max_nx;
+    size_t off = dtype == GWN_F64 ? eval2d_fallback_off<double>() : eval2d_fallback_off<float>();
+    return off + sizeof(int) * (size_t)max_nx;
 }
 
 cudaError_t launch_eval2d_items(const ChainSet &cs, const Set2D *d_sets, const int2 *d_items, int64_t n_items,
@@ -186,21 +319,28 @@ cudaError_t launch_eval2d_items(const ChainSet &cs, const Set2D *d_sets, const i
                                 void *w_out, int32_t *chi_out, void *b_out, unsigned long long *cnt, int *status,
                                 int sm_count, cudaStream_t st) {
     if (n_items == 0) return cudaSuccess;
+    if (rows_per_item < 1 || rows_per_item > MAX_ROWS) return cudaErrorInvalidValue;
     size_t smem = eval2d_smem(cs.dtype, max_nx);
     cudaError_t e = cudaMemsetAsync(d_counter, 0, sizeof(unsigned long long), st);
     if (e != cudaSuccess) return e;
-    int per_sm = threads <= 128 ? 8 : 4;
+    // persistent grid: as many blocks as fit on the device at once
+    int per_sm = 0;
+    if (cs.dtype == GWN_F64) {
+        e = cudaFuncSetAttribute(eval2d_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, eval2d_kernel<double>, threads, smem);
+    } else {
+        e = cudaFuncSetAttribute(eval2d_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, eval2d_kernel<float>, threads, smem);
+    }
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
     int64_t blocks = (int64_t)sm_count * per_sm;
     if (blocks > n_items) blocks = n_items;
     if (cs.dtype == GWN_F64) {
-        if (smem > 48 * 1024)
-            cudaFuncSetAttribute(eval2d_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         eval2d_kernel<double><<<(unsigned)blocks, threads, smem, st>>>(
             (const double *)cs.ctrl, cs.chain_off, cs.piece_seg, cs.piece_u, cs.piece_y, d_sets, d_items, n_items,
             d_counter, rows_per_item, (double *)w_out, chi_out, (double *)b_out, cnt, status, (int)max_nx);
     } else {
-        if (smem > 48 * 1024)
-            cudaFuncSetAttribute(eval2d_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         eval2d_kernel<float><<<(unsigned)blocks, threads, smem, st>>>(
             (const float *)cs.ctrl, cs.chain_off, cs.piece_seg, cs.piece_u, cs.piece_y, d_sets, d_items, n_items,
             d_counter, rows_per_item, (float *)w_out, chi_out, (float *)b_out, cnt, status, (int)max_nx);

@@ -424,7 +424,7 @@ cudaError_t launch_bframe(const float4 *bseq, int64_t n, const Frame &fr, float4
     return cudaGetLastError();
 }
 
-// ---- careful pass: deferred queries, one per thread, scalar ----------------
+// ---- careful pass: deferred queries, scalar ------------------------------------
 struct VState1 {
     float a1, a2, s, r2;
 };
@@ -471,24 +471,37 @@ __device__ __forceinline__ float edge_theta_careful(const VState1 &A, const VSta
     return th;
 }
 
+// One warp per deferred query: lane l sums the edges ending at records
+// [k0, k1), a contiguous run of about (nb - 1)/32 records, starting from the
+// projection of record k0 - 1.  A vertex on a run boundary is projected by
+// both lanes with the same arithmetic, so its rounding still cancels between
+// its two edges.  The lanes' compensated sums are combined by a TwoSum tree.
 __global__ void __launch_bounds__(128) bterm3d_careful_kernel(const float4 *__restrict__ bseq, int nb, Frame fr,
                                                               Frame64 f64, QuerySrc q, const int32_t *chi,
                                                               float *w_out, float *b_out,
                                                               const int32_t *__restrict__ defer,
                                                               const int32_t *defer_count, unsigned long long *cnt,
                                                               int *status) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     int64_t n = *defer_count;
     if (n > q.n) n = q.n;
     if (cnt && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&cnt[CNT_DEFER_BTERM], (unsigned long long)n);
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int per = nb > 1 ? (nb - 1 + 31) / 32 : 0;
+    for (int64_t i = warp; i < n; i += nwarps) {
         int64_t idx = defer[i];
-        if (idx < 0 || idx >= q.n) { atomicOr(status, ST_BAD_INPUT); continue; }
+        if (idx < 0 || idx >= q.n) {
+            if (lane == 0) atomicOr(status, ST_BAD_INPUT);
+            continue;
+        }
         float3 p = query_point3(q, idx);
         float sum = 0.f, cmp = 0.f;
-        if (nb > 0) {
-            float4 vp = __ldg(&bseq[0]);
+        int k0 = 1 + lane * per, k1 = k0 + per < nb ? k0 + per : nb;
+        if (k0 < k1) {
+            float4 vp = __ldg(&bseq[k0 - 1]);
             VState1 A = project1(vp, p, fr);
-            for (int k = 1; k < nb; k++) {
+            for (int k = k0; k < k1; k++) {
                 float4 v = __ldg(&bseq[k]);
                 VState1 B = project1(v, p, fr);
                 if (v.w != 0.f) {
@@ -502,9 +515,19 @@ __global__ void __launch_bounds__(128) bterm3d_careful_kernel(const float4 *__re
                 vp = v;
             }
         }
-        float Bv = (sum - cmp) * GWN_INV_2PI;
-        if (b_out) b_out[idx] = Bv;
-        if (w_out) w_out[idx] = Bv + (chi ? (float)chi[idx] : 0.f);
+        // combine (value, error) pairs across the warp with TwoSum
+        float s = sum, e = -cmp;
+        for (int off = 16; off > 0; off >>= 1) {
+            float s2 = __shfl_down_sync(0xffffffffu, s, off), e2 = __shfl_down_sync(0xffffffffu, e, off);
+            float t = s + s2, bv = t - s, err = (s - (t - bv)) + (s2 - bv);
+            s = t;
+            e = e + e2 + err;
+        }
+        if (lane == 0) {
+            float Bv = (s + e) * GWN_INV_2PI;
+            if (b_out) b_out[idx] = Bv;
+            if (w_out) w_out[idx] = Bv + (chi ? (float)chi[idx] : 0.f);
+        }
     }
 }
 

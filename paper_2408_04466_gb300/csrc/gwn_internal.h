@@ -120,7 +120,9 @@ struct gwn_ctx {
     int sm_count = 0;
     int *d_status = nullptr;                  // device status bits
     unsigned long long *d_cnt = nullptr;      // device counters [CNT_NUM]
-    int32_t *d_defer_count = nullptr;         // length of the boundary term's deferred-query list
+    int32_t *d_defer_count = nullptr;         // length of the deferred-query list
+    int2 *d_tpairs = nullptr;                 // traversal: unsettled (query, triangle) pairs [GWN_TPAIR_CAP]
+    int32_t *d_tpair_count = nullptr;
     gwn::Arena scratch[5];                    // 0 chi, 1 staged points, 2 2D batch, 3 host-eval w, 4 deferred list
     cudaEvent_t ev[8];
     bool events = false;
@@ -166,10 +168,12 @@ void bvh_free(MeshBvh &b);
 
 // Crossing counts chi[q.n].  defer / defer_count: the same deferred-list
 // scratch as launch_bterm3d (used and emptied before it returns in stream
-// order, so the two may share it).
+// order, so the two may share it); pairs / pair_count: GWN_TPAIR_CAP
+// unsettled (query, triangle) pairs.
+#define GWN_TPAIR_CAP 65536
 cudaError_t launch_traverse(const MeshBvh &b, const QuerySrc &q, int32_t *chi, int32_t *defer,
-                            int32_t *defer_count, unsigned long long *cnt, int *status, int sm_count,
-                            cudaStream_t st);
+                            int32_t *defer_count, int2 *pairs, int32_t *pair_count, unsigned long long *cnt,
+                            int *status, int sm_count, cudaStream_t st);
 
 // Boundary term + epilogue (w = chi + B).  defer: int32 scratch of q.n
 // entries for the deferred-query list; defer_count: one device int32.

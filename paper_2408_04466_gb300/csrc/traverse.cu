@@ -43,10 +43,25 @@ __device__ __forceinline__ bool box_hit(float x0, float x1, float y0, float y1, 
 // of them cannot settle a sign; otherwise the full predicates (float64 and
 // exact fallbacks).  Returns false on stack overflow, iteration limit or a
 // corrupt node reference (status bits set).
+// Unsettled pair (query idx, triangle t) of a float32 pass: appended to the
+// pair list when it has room (the pair is then settled by
+// traverse_pairs_kernel and added to chi), otherwise the whole query is
+// deferred.
+__device__ __forceinline__ void defer_pair(int2 *pairs, int32_t *pair_count, int64_t idx, int t, bool &unsure) {
+    int slot = atomicAdd(pair_count, 1);
+    if (slot < GWN_TPAIR_CAP) pairs[slot] = make_int2((int)idx, t);
+    else unsure = true;
+}
+
+// One ray per thread.  FAST: float32 predicates only; a pair they cannot
+// settle goes through defer_pair; otherwise the full predicates (float64 and
+// exact fallbacks).  Returns false on stack overflow, iteration limit or a
+// corrupt node reference (status bits set).
 template <bool FAST>
 __device__ __forceinline__ bool traverse_ray(const BvhNode *__restrict__ nodes, const float4 *__restrict__ tris,
-                                             int root, const Frame &fr, const TravParams &tp, float3 p, int &acc,
-                                             bool &unsure, int &ntests, unsigned long long *cnt, int *status) {
+                                             int root, const Frame &fr, const TravParams &tp, float3 p, int64_t idx,
+                                             int &acc, bool &unsure, int2 *pairs, int32_t *pair_count, int &ntests,
+                                             unsigned long long *cnt, int *status) {
     float3 D = make_float3(fr.d[0], fr.d[1], fr.d[2]);
     float p1 = fmaf(p.z, fr.e1[2], fmaf(p.y, fr.e1[1], p.x * fr.e1[0]));
     float p2 = fmaf(p.z, fr.e2[2], fmaf(p.y, fr.e2[1], p.x * fr.e2[0]));
@@ -73,9 +88,11 @@ __device__ __forceinline__ bool traverse_ray(const BvhNode *__restrict__ nodes, 
             float4 a = __ldg(&tris[3 * t]), b = __ldg(&tris[3 * t + 1]), c = __ldg(&tris[3 * t + 2]);
             ntests++;
             float3 v0 = make_float3(a.x, a.y, a.z), v1 = make_float3(b.x, b.y, b.z), v2 = make_float3(c.x, c.y, c.z);
-            if (FAST)
-                acc += tri_crossing_fast(v0, v1, v2, p, D, unsure);
-            else
+            if (FAST) {
+                bool u = false;
+                acc += tri_crossing_fast(v0, v1, v2, p, D, u);
+                if (u) defer_pair(pairs, pair_count, idx, t, unsure);
+            } else
                 acc += tri_crossing(v0, v1, v2, p, D, cnt, status);
             if (sp == 0) return true;
             node = stack[--sp];
@@ -116,13 +133,14 @@ __device__ __forceinline__ void defer_query(int32_t *defer, int32_t *defer_count
 __global__ void __launch_bounds__(256) traverse_kernel(const BvhNode *__restrict__ nodes,
                                                        const float4 *__restrict__ tris, int root, Frame fr,
                                                        TravParams tp, QuerySrc q, int32_t *__restrict__ chi,
-                                                       int32_t *defer, int32_t *defer_count,
-                                                       unsigned long long *cnt, int *status) {
+                                                       int32_t *defer, int32_t *defer_count, int2 *pairs,
+                                                       int32_t *pair_count, unsigned long long *cnt, int *status) {
     int64_t idx = q.kind == GWN_QUERY_GRID ? grid_tile_query(q) : (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx < 0 || idx >= q.n) return;
     int acc, ntests = 0;
     bool unsure = false;
-    bool ok = traverse_ray<true>(nodes, tris, root, fr, tp, query_point3(q, idx), acc, unsure, ntests, cnt, status);
+    bool ok = traverse_ray<true>(nodes, tris, root, fr, tp, query_point3(q, idx), idx, acc, unsure, pairs,
+                                 pair_count, ntests, cnt, status);
     if (cnt) {                                   // statistics: one atomic per warp
         unsigned m = __activemask();
         int tot = __reduce_add_sync(m, ntests);
@@ -151,10 +169,33 @@ __global__ void __launch_bounds__(128) traverse_careful_kernel(const BvhNode *__
         if (idx < 0 || idx >= q.n) { atomicOr(status, ST_BAD_INPUT); continue; }
         int acc, ntests = 0;
         bool unsure = false;
-        bool ok = traverse_ray<false>(nodes, tris, root, fr, tp, query_point3(q, idx), acc, unsure, ntests, cnt,
-                                      status);
+        bool ok = traverse_ray<false>(nodes, tris, root, fr, tp, query_point3(q, idx), idx, acc, unsure, nullptr,
+                                      nullptr, ntests, cnt, status);
         if (cnt) atomicAdd(&cnt[CNT_TRI_TESTS], (unsigned long long)ntests);
         chi[idx] = ok ? acc : INT32_MIN;
+    }
+}
+
+// Unsettled (query, triangle) pairs of the float32 passes: one thread per
+// pair, full predicates, the signed crossing added to the query's count
+// (left alone when the query's traversal failed and its count is invalid).
+__global__ void __launch_bounds__(128) traverse_pairs_kernel(const float4 *__restrict__ tris, Frame fr, QuerySrc q,
+                                                             int32_t *chi, const int2 *__restrict__ pairs,
+                                                             const int32_t *pair_count, unsigned long long *cnt,
+                                                             int *status) {
+    int64_t n = *pair_count;
+    if (n > GWN_TPAIR_CAP) n = GWN_TPAIR_CAP;
+    if (cnt && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&cnt[CNT_DEFER_TRAV], (unsigned long long)n);
+    float3 D = make_float3(fr.d[0], fr.d[1], fr.d[2]);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        int2 pr = pairs[i];
+        if (pr.x < 0 || pr.x >= q.n) { atomicOr(status, ST_BAD_INPUT); continue; }
+        if (chi[pr.x] == INT32_MIN) continue;
+        float3 p = query_point3(q, pr.x);
+        float4 a = __ldg(&tris[3 * pr.y]), b = __ldg(&tris[3 * pr.y + 1]), c = __ldg(&tris[3 * pr.y + 2]);
+        int r = tri_crossing(make_float3(a.x, a.y, a.z), make_float3(b.x, b.y, b.z), make_float3(c.x, c.y, c.z), p,
+                             D, cnt, status);
+        if (r) atomicAdd(&chi[pr.x], r);
     }
 }
 
@@ -178,8 +219,9 @@ __global__ void __launch_bounds__(256) traverse_packet_kernel(const BvhNode *__r
                                                               const float4 *__restrict__ tris,
                                                               const float4 *__restrict__ tbox, int root, Frame fr,
                                                               TravParams tp, QuerySrc q, int32_t *__restrict__ chi,
-                                                              int32_t *defer, int32_t *defer_count,
-                                                              unsigned long long *cnt, int *status) {
+                                                              int32_t *defer, int32_t *defer_count, int2 *tpairs,
+                                                              int32_t *tpair_count, unsigned long long *cnt,
+                                                              int *status) {
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     int64_t idx = grid_tile_query(q);
@@ -210,6 +252,7 @@ __global__ void __launch_bounds__(256) traverse_packet_kernel(const BvhNode *__r
         int pr = lane < m ? pairs[lane] : -1;
         int ql = pr >= 0 ? (pr & 31) : lane;
         float qx = __shfl_sync(FULL, p.x, ql), qy = __shfl_sync(FULL, p.y, ql), qz = __shfl_sync(FULL, p.z, ql);
+        int qi = __shfl_sync(FULL, (int)idx, ql);
         if (pr >= 0) {
             int t = pr >> 5;
             float4 a = __ldg(&tris[3 * t]), b = __ldg(&tris[3 * t + 1]), c = __ldg(&tris[3 * t + 2]);
@@ -217,7 +260,11 @@ __global__ void __launch_bounds__(256) traverse_packet_kernel(const BvhNode *__r
             int r = tri_crossing_fast(make_float3(a.x, a.y, a.z), make_float3(b.x, b.y, b.z),
                                       make_float3(c.x, c.y, c.z), make_float3(qx, qy, qz), D, uns);
             if (r) atomicAdd(&s_acc[w][ql], r);
-            if (uns) atomicOr(&s_uns[w], 1u << ql);
+            if (uns) {
+                bool whole = false;
+                defer_pair(tpairs, tpair_count, qi, t, whole);
+                if (whole) atomicOr(&s_uns[w], 1u << ql);
+            }
         }
         int rem = n - m;
         __syncwarp();
@@ -324,8 +371,8 @@ __global__ void traverse_single_kernel(const float4 *__restrict__ tris, int ntri
 }
 
 cudaError_t launch_traverse(const MeshBvh &b, const QuerySrc &q, int32_t *chi, int32_t *defer,
-                            int32_t *defer_count, unsigned long long *cnt, int *status, int sm_count,
-                            cudaStream_t st) {
+                            int32_t *defer_count, int2 *pairs, int32_t *pair_count, unsigned long long *cnt,
+                            int *status, int sm_count, cudaStream_t st) {
     if (q.n == 0) return cudaSuccess;
     if (q.n > 0x7fffffff) return cudaErrorInvalidValue;
     const int threads = 128;
@@ -355,18 +402,25 @@ cudaError_t launch_traverse(const MeshBvh &b, const QuerySrc &q, int32_t *chi, i
     int64_t tblocks = q.kind == GWN_QUERY_GRID ? grid_tile_blocks(q) : (q.n + 255) / 256;
     if (tblocks > 0x7fffffff) return cudaErrorInvalidValue;
     cudaError_t e = cudaMemsetAsync(defer_count, 0, sizeof(int32_t), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(pair_count, 0, sizeof(int32_t), st);
     if (e != cudaSuccess) return e;
     // Grid queries come in spatially coherent warp tiles: one warp-uniform
     // stack per tile.  Scattered points take one stack per thread.
     if (q.kind == GWN_QUERY_GRID && b.tbox && b.n < (int64_t(1) << 26))
         traverse_packet_kernel<<<(unsigned)tblocks, 256, 0, st>>>(b.nodes, b.tris, b.tbox, b.root, b.frame, tp, q,
-                                                                  chi, defer, defer_count, cnt, status);
+                                                                  chi, defer, defer_count, pairs, pair_count, cnt,
+                                                                  status);
     else
         traverse_kernel<<<(unsigned)tblocks, 256, 0, st>>>(b.nodes, b.tris, b.root, b.frame, tp, q, chi, defer,
-                                                           defer_count, cnt, status);
+                                                           defer_count, pairs, pair_count, cnt, status);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    // settle the unsettled pairs (adds to chi), then recount the queries whose
+    // pairs did not fit in the list (overwrites chi): in this order
     int cblocks = (sm_count > 0 ? sm_count : 152) * 4;
+    traverse_pairs_kernel<<<cblocks, 128, 0, st>>>(b.tris, b.frame, q, chi, pairs, pair_count, cnt, status);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
     traverse_careful_kernel<<<cblocks, 128, 0, st>>>(b.nodes, b.tris, b.root, b.frame, tp, q, chi, defer,
                                                      defer_count, cnt, status);
     return cudaGetLastError();

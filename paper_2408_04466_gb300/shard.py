@@ -1,9 +1,14 @@
 """Query sharding across ranks (one process per GPU).
 
-Queries are independent, so a grid is split into contiguous z-slabs, one per
-rank, with no data-path collective; every rank keeps a full copy of the
-geometry.  With ``weak=True`` the global grid grows with the world size so
-each rank keeps the single-GPU number of queries.
+Queries are independent, so a grid is split into contiguous z-slabs (a point
+list into contiguous ranges), one per rank, with no collective on the
+forward path; every rank keeps a full copy of the geometry.  With
+``weak=True`` the global grid grows with the world size so each rank keeps
+the single-GPU number of queries.
+
+The backward pass has one exchange step: dw/dV is a sum over queries, so each
+rank's gradient over its own queries is summed across ranks
+(``allreduce_grad_vertices``); dw/dp stays with the rank that owns the query.
 """
 from __future__ import annotations
 
@@ -29,3 +34,20 @@ def shard_grid(lo, hi, dims, rank: int, world: int, weak: bool = True):
     z0 = lo[-1] + k0 * step
     z1 = lo[-1] + (k1 - 1) * step
     return tuple(lo[:-1] + [z0]), tuple(hi[:-1] + [z1]), tuple(dims[:-1] + [k1 - k0]), (k0, k1, nz)
+
+
+def shard_range(n: int, rank: int, world: int):
+    """[i0, i1) of a list of n queries owned by `rank` (contiguous, sizes
+    differ by at most one)."""
+    base, extra = divmod(int(n), world)
+    i0 = rank * base + min(rank, extra)
+    return i0, i0 + base + (1 if rank < extra else 0)
+
+
+def allreduce_grad_vertices(grad_v):
+    """Sum dw/dV (a tensor, in place) over the ranks of the default process
+    group; a no-op without one or with a single rank."""
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(grad_v, op=dist.ReduceOp.SUM)
+    return grad_v

@@ -253,3 +253,40 @@ def test_icosphere_cap_full_size_sampled(gwn, ctx):
     assert torch.isfinite(w).all()
     vals = torch.unique(chi_all).cpu().numpy()
     assert set(vals.tolist()) <= {-2, -1, 0, 1, 2}
+
+
+def test_degenerate_rays_overflow_pair_list(gwn, ctx):
+    """Every ray through a mesh vertex exactly (axis-aligned flat grid mesh,
+    queries under its vertices, d = +z): every triangle test is left
+    unsettled by the float32 filter, far more pairs than the deferred-pair
+    list holds, so queries are recounted whole as well.  Grid queries (packet
+    traversal) and point queries (per-thread traversal) must both match the
+    oracle's symbolically perturbed counts exactly."""
+    import torch
+    nv = 97
+    Vg = np.array([[x, y, 0.0] for x in range(nv) for y in range(nv)], np.float32)
+    Fg = []
+    for i in range(nv - 1):
+        for j in range(nv - 1):
+            a, b, c, dd = nv * i + j, nv * (i + 1) + j, nv * (i + 1) + j + 1, nv * i + j + 1
+            Fg += [(a, b, c), (a, c, dd)]
+    Fg = np.array(Fg, np.int32)
+    d = np.array([0, 0, 1], np.float32)
+    mesh = gwn.Mesh(ctx, Vg, Fg)
+    grid = gwn.Grid((-1.0, -1.0, -1.0), (nv, nv, -0.25), (nv + 2, nv + 2, 4))
+    r = mesh.eval(grid, d, want_chi=True, stats=True)
+    torch.cuda.synchronize()
+    ctx.check()
+    st = r["stats"]
+    assert st["n_deferred_traverse"] > 65536            # the pair list overflowed
+    P = gen.grid_points(gen.Grid(grid.lo, grid.hi, grid.dims))
+    rng = np.random.default_rng(3)
+    sub = np.sort(rng.choice(len(P), 3000, replace=False))
+    chio = oracle.chi3d(Vg, Fg, P[sub], d)
+    assert np.array_equal(r["chi"].cpu().numpy()[sub], chio)
+    # the same queries as a point list
+    Pt = torch.as_tensor(P).cuda()
+    rp = mesh.eval(gwn.Points(Pt), d, want_chi=True)
+    torch.cuda.synchronize()
+    ctx.check()
+    assert np.array_equal(rp["chi"].cpu().numpy(), r["chi"].cpu().numpy())

@@ -58,3 +58,48 @@ def test_weak_sharding_two_gloo_ranks():
     assert spans[0][0] == 0 and spans[0][1] == spans[1][0] and spans[1][1] == 16
     assert all(s[3] == 8 for s in spans)          # weak: every rank keeps 8 planes
     assert np.isclose(lo[2], -1.2)
+
+
+def _grad_worker(rank, world, port, q):
+    import torch
+    import torch.distributed as dist
+    import gen
+    import oracle
+    from paper_2408_04466_gb300.shard import allreduce_grad_vertices, shard_range
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    m = gen.icosphere_cap(subdiv=2, seed=4)
+    P = np.random.default_rng(0).uniform(-1.3, 1.3, (96, 3)).astype(np.float32)
+    gw = np.linspace(-1.0, 2.0, len(P))
+    i0, i1 = shard_range(len(P), rank, world)
+    gp, gv = oracle.grad3d_vos(m.V, m.F, P[i0:i1], gw=gw[i0:i1])
+    gv = torch.as_tensor(gv)
+    allreduce_grad_vertices(gv)
+    dist.barrier()
+    if rank == 0:
+        q.put((gv.numpy(), i0, i1))
+    dist.destroy_process_group()
+
+
+def test_backward_allreduce_two_gloo_ranks():
+    """dw/dV summed over two ranks' query shards equals dw/dV over all
+    queries (the one exchange step of the sharded backward)."""
+    import gen
+    import oracle
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = 30500 + (os.getpid() % 1000)
+    procs = [ctx.Process(target=_grad_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    gv, i0, i1 = q.get(timeout=180)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert (i0, i1) == (0, 48)
+    m = gen.icosphere_cap(subdiv=2, seed=4)
+    P = np.random.default_rng(0).uniform(-1.3, 1.3, (96, 3)).astype(np.float32)
+    gw = np.linspace(-1.0, 2.0, len(P))
+    _, full = oracle.grad3d_vos(m.V, m.F, P, gw=gw)
+    assert np.allclose(gv, full, rtol=1e-12, atol=1e-14)
