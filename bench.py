@@ -49,6 +49,12 @@ WORKLOAD = "icosphere_cap_s6_73724tris_256^3grid"
 #           cut test (2), compensated accumulation (4)                          -> 31
 W_VERTEX = 24
 W_EDGE = 31
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one bterm3d_kernel
+# launch on this workload at full size, from an ncu capture (read 67.31 MB,
+# write 21.43 MB); reported only while csrc/bterm.cu is the source it was taken
+# on.  Algorithmic bytes are 8 per query (chi in, w out: 134 MB); DRAM writes
+# fall below that because L2 still holds part of w when the kernel ends.
+BTERM_TRAFFIC = {"bytes": 88.74e6, "bterm_cu_sha256": "968b701a5694e104139c169621a1d2b43cdf7fc1e4a81e03672462aeb5d07f90"}
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 
@@ -121,7 +127,7 @@ def workload(rank: int = 0, world: int = 1, grid_n: int = 256):
 # ----------------------------------------------------------------------------
 # CPU oracle (baseline / reference arm)
 # ----------------------------------------------------------------------------
-def oracle_rate(m, n_sample: int, seed: int):
+def oracle_rate(m, n_sample: int, seed: int, want=False):
     import gen
     import oracle
     rng = np.random.default_rng(seed)
@@ -129,8 +135,10 @@ def oracle_rate(m, n_sample: int, seed: int):
     P = gen.grid_points(m.grid, index=idx)
     edges = oracle.boundary_edges(m.F)
     t0 = time.perf_counter()
-    oracle.w3d_oneshot(m.V, m.F, P, m.d, edges=edges)
+    wo, chio, _ = oracle.w3d_oneshot(m.V, m.F, P, m.d, edges=edges)
     dt = time.perf_counter() - t0
+    if want:
+        return n_sample / dt, dt, (idx, P, wo, chio)
     return n_sample / dt, dt
 
 
@@ -257,8 +265,12 @@ def run_gpu(args):
         alu_peak = SM_COUNT * FP32_LANES_PER_SM * clk_hz / 1e12          # Tops/s
         ops = nq * ((E + L) * W_VERTEX + E * W_EDGE)
         achieved = ops / (ms_bterm * 1e-3) / 1e12
+        import hashlib
+        with open(os.path.join(ROOT, "paper_2408_04466_gb300", "csrc", "bterm.cu"), "rb") as f:
+            same_src = hashlib.sha256(f.read()).hexdigest() == BTERM_TRAFFIC["bterm_cu_sha256"]
         roof = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tops/s (FP32 lane ops)",
-                "frac": achieved / alu_peak, "traffic": None, "kernel": "bterm3d_kernel",
+                "frac": achieved / alu_peak, "traffic": BTERM_TRAFFIC["bytes"] if same_src else None,
+                "traffic_unit": "bytes per launch (DRAM, ncu)", "kernel": "bterm3d_kernel",
                 "peak_source": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x sm_max_mhz "
                                f"({peak_kind} MEASURED_PEAKS)" if peak_kind == "measured" else "fallback clock"}
         # brute-force comparator on a sub-grid (first 4 planes: 262,144 queries)
@@ -301,7 +313,18 @@ def run_gpu(args):
         import oracle
         oracle.build()
         n_cpu = args.cpu_sample
-        rate, dt = oracle_rate(m, n_cpu, 7)
+        rate, dt, (sidx, sP, wo, chio) = oracle_rate(m, n_cpu, 7, want=True)
+        # parity on the same sample: crossing counts exactly, |dw| beyond 1e-4 x diagonal
+        r = mesh.eval(grid, m.d, want_chi=True)
+        torch.cuda.synchronize()
+        ti = torch.as_tensor(sidx, device=dev)
+        wg = r["w"][ti].double().cpu().numpy()
+        chig = r["chi"][ti].cpu().numpy()
+        diag = float(np.linalg.norm(m.V.max(0).astype(np.float64) - m.V.min(0)))
+        far = oracle.dist3d(m.V, m.F, sP) > 1e-4 * diag
+        parity = {"n": int(n_cpu), "chi_mismatch": int((chig != chio).sum()),
+                  "max_abs_dw": float(np.abs(wg - wo)[far].max()) if far.any() else None,
+                  "n_within_1e-4_diag": int((~far).sum()), "reference": "FP64 oracle on the cpu_baseline sample"}
         cpu = {"value": rate, "unit": UNIT, "cores": oracle.default_threads(), "kind": "oracle",
                "sample": f"{n_cpu} seeded queries of the 256^3 grid; FP64 one-shot (brute-force exact crossing "
                          f"count over all triangles + boundary term); {dt:.1f} s"}
@@ -323,10 +346,12 @@ def run_gpu(args):
             "bruteforce_gpu": {"value": bf_rate, "unit": UNIT, "sample": f"{sub.n} grid queries x 73,724 triangles"},
             "speedup_vs_bruteforce_gpu": value / world / bf_rate,
             "cpu_baseline": cpu,
+            "parity_sample": parity,
             "e2e": e2e,
-            # per step: packet traversal + careful recount, boundary term +
-            # careful pass (two list-length memsets are not kernels)
-            "gpu_launches": 4 * args.steps,
+            # per step: packet traversal, deferred-pair settlement, whole-query
+            # recount, boundary term, careful boundary pass (the list-length
+            # memsets are not kernels)
+            "gpu_launches": 5 * args.steps,
             "clocks": clk,
             "wall_s_timed": wall,
         }
@@ -340,6 +365,16 @@ def run_gpu(args):
 # ----------------------------------------------------------------------------
 # other workloads (parity-test configurations), measured with --workload
 # ----------------------------------------------------------------------------
+def _alu_roofline(nq, info, ms):
+    """Boundary-term FP32 roofline for nq queries against a mesh boundary."""
+    peaks, kind = _peaks()
+    peak = SM_COUNT * FP32_LANES_PER_SM * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+    E, L = info["n_boundary_edges"], info["n_loops"]
+    achieved = nq * ((E + L) * W_VERTEX + E * W_EDGE) / (ms * 1e-3) / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s (FP32 lane ops)",
+            "frac": achieved / peak, "peak_source": kind}
+
+
 def _timed(fn, steps, warmup, stream):
     import torch
     for _ in range(warmup):
@@ -376,8 +411,13 @@ def run_other(args):
         grids = [gwn.Grid(g.lo, g.hi, g.dims) for g in ch.grids]
         nq = sum(g.n for g in grids)
         if name == "circle_chain_fp64":
+            # latency-bound (16,384 queries): the graph-replayed launch, with the
+            # plain gwn_eval call timed beside it
             w = torch.empty(nq, dtype=torch.float64, device=dev)
-            fn = lambda: geo.eval(grids[0])
+            bq = geo.batch_queries(grids)
+            fn = lambda: geo.eval_batch(bq, out=w)
+            out["gwn_eval_ms"] = statistics.median(_timed(lambda: geo.eval(grids[0]), args.steps, args.warmup,
+                                                          stream))
             out["dtype"] = "f64"
         else:
             w = torch.empty(nq, dtype=torch.float32, device=dev)
@@ -421,10 +461,14 @@ def run_other(args):
             mesh.backward(Pt, gw)
         ms = _timed(step, args.steps, args.warmup, stream)
         fms = _timed(lambda: mesh.eval(gwn.Points(Pt), m.d, out=w), args.steps, args.warmup, stream)
+        info = mesh.info()
+        st = mesh.eval(gwn.Points(Pt), m.d, stats=True, out=w)["stats"]
         out.update({"metric": "queries/s, forward + backward (dw/dp, dw/dV)", "dtype": "f32",
                     "ms_per_step": statistics.median(ms), "forward_ms": statistics.median(fms),
                     "value": len(Pt) / (statistics.median(ms) * 1e-3), "queries_per_step": len(Pt),
-                    "boundary_edges": mesh.info()["n_boundary_edges"], "triangles": int(len(m.F))})
+                    "boundary_edges": info["n_boundary_edges"], "triangles": int(len(m.F)),
+                    "kernels": {"traverse_ms": st["ms_traverse"], "bterm3d_ms": st["ms_boundary"]},
+                    "roofline_bterm": _alu_roofline(len(Pt), info, st["ms_boundary"])})
     elif name == "holey_heightfield":
         m = gen.holey_heightfield()
         mesh = gwn.Mesh(ctx, m.V, m.F)
@@ -436,11 +480,13 @@ def run_other(args):
         w = torch.empty(g.n, dtype=torch.float32, device=dev)
         st = mesh.eval(g, m.d, stats=True, out=w)["stats"]
         ms = _timed(lambda: mesh.eval(g, m.d, out=w), args.steps, min(args.warmup, 1), stream)
+        info = mesh.info()
         out.update({"metric": METRIC, "dtype": "f32", "ms_per_step": statistics.median(ms),
                     "value": g.n / (statistics.median(ms) * 1e-3), "queries_per_step": g.n,
-                    "boundary_edges": mesh.info()["n_boundary_edges"], "boundary_loops": mesh.info()["n_loops"],
+                    "boundary_edges": info["n_boundary_edges"], "boundary_loops": info["n_loops"],
                     "triangles": int(len(m.F)), "lbvh_build_ms": 1e3 * prep,
-                    "kernels": {"traverse_ms": st["ms_traverse"], "bterm3d_ms": st["ms_boundary"]}})
+                    "kernels": {"traverse_ms": st["ms_traverse"], "bterm3d_ms": st["ms_boundary"]},
+                    "roofline_bterm": _alu_roofline(g.n, info, st["ms_boundary"])})
     else:
         raise SystemExit(f"unknown workload {name}")
     print(json.dumps(out))

@@ -285,6 +285,7 @@ GWN_API gwn_status gwn_ctx_create(gwn_ctx **out, int device, void *cuda_stream) 
     if (e == cudaSuccess) e = cudaMalloc(&c->d_defer_count, sizeof(int32_t));
     if (e == cudaSuccess) e = cudaMalloc(&c->d_tpairs, sizeof(int2) * GWN_TPAIR_CAP);
     if (e == cudaSuccess) e = cudaMalloc(&c->d_tpair_count, sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_work_counter, sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(c->d_cnt, 0, sizeof(unsigned long long) * CNT_NUM);
     for (int i = 0; i < 8 && e == cudaSuccess; i++) e = cudaEventCreate(&c->ev[i]);
@@ -329,6 +330,9 @@ GWN_API void gwn_ctx_destroy(gwn_ctx *ctx) {
     if (ctx->d_defer_count) cudaFree(ctx->d_defer_count);
     if (ctx->d_tpairs) cudaFree(ctx->d_tpairs);
     if (ctx->d_tpair_count) cudaFree(ctx->d_tpair_count);
+    if (ctx->d_work_counter) cudaFree(ctx->d_work_counter);
+    for (auto &c : ctx->axis_cache)
+        if (c.dev) cudaFree(c.dev);
     if (ctx->events)
         for (int i = 0; i < 8; i++) cudaEventDestroy(ctx->ev[i]);
     delete ctx;
@@ -376,6 +380,8 @@ static void free_geom_device(gwn_geom *g) {
     if (cs.piece_seg) cudaFree(cs.piece_seg);
     if (cs.piece_u) cudaFree(cs.piece_u);
     if (cs.piece_y) cudaFree(cs.piece_y);
+    if (cs.piece_uT && cs.piece_uT != (void *)cs.piece_u) cudaFree(cs.piece_uT);
+    if (cs.piece_yT && cs.piece_yT != (void *)cs.piece_y) cudaFree(cs.piece_yT);
     if (cs.piece_chain) cudaFree(cs.piece_chain);
     if (cs.chain_piece_off) cudaFree(cs.chain_piece_off);
 }
@@ -576,6 +582,19 @@ GWN_API gwn_status gwn_bezier2d_create(gwn_ctx *ctx, const void *ctrl, int dtype
         if (e == cudaSuccess) e = cudaMemcpy(cs.piece_y, py.data(), sizeof(double) * 2 * cs.n_pieces, cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemcpy(cs.piece_chain, pch.data(), sizeof(int32_t) * cs.n_pieces, cudaMemcpyHostToDevice);
     }
+    // the kernels read the piece tables in the chain's precision
+    if (e == cudaSuccess && dtype == GWN_F64) {
+        cs.piece_uT = cs.piece_u;
+        cs.piece_yT = cs.piece_y;
+    } else if (e == cudaSuccess) {
+        std::vector<float> fu(pu.begin(), pu.end()), fy(py.begin(), py.end());
+        fu.resize(2 * np);
+        fy.resize(2 * np);
+        e = cudaMalloc(&cs.piece_uT, sizeof(float) * 2 * np);
+        if (e == cudaSuccess) e = cudaMalloc(&cs.piece_yT, sizeof(float) * 2 * np);
+        if (e == cudaSuccess) e = cudaMemcpy(cs.piece_uT, fu.data(), sizeof(float) * 2 * np, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(cs.piece_yT, fy.data(), sizeof(float) * 2 * np, cudaMemcpyHostToDevice);
+    }
     if (e != cudaSuccess) {
         free_geom_device(g.get());
         return cuda_fail(e, "gwn_bezier2d_create");
@@ -627,19 +646,9 @@ static void axis_table(double lo, double hi, int64_t n, std::vector<double> &out
     for (int64_t i = 0; i < n; i++) out[i] = lo + (double)i * step;
 }
 
-struct AxisCache {
-    double lo[3], hi[3];
-    int64_t dims[3];
-    int dim, dtype;
-    void *dev = nullptr;
-    size_t bytes = 0;
-};
-
-static std::map<gwn_ctx *, std::vector<AxisCache>> g_axis_cache;
-
-// device axis tables for grid q (cached per context; uploaded once)
+// device axis tables for grid q (cached per context; uploaded once per grid)
 static gwn_status grid_tables(gwn_ctx *ctx, const gwn_queries *q, int dtype, QuerySrc &src) {
-    auto &vec = g_axis_cache[ctx];
+    auto &vec = ctx->axis_cache;
     for (auto &c : vec) {
         if (c.dim == q->dim && c.dtype == dtype && memcmp(c.lo, q->lo, sizeof(c.lo)) == 0 &&
             memcmp(c.hi, q->hi, sizeof(c.hi)) == 0 && memcmp(c.dims, q->dims, sizeof(c.dims)) == 0) {
@@ -653,7 +662,12 @@ static gwn_status grid_tables(gwn_ctx *ctx, const gwn_queries *q, int dtype, Que
             return GWN_OK;
         }
     }
+    if (vec.size() >= 64) {          // drop the oldest grid (cudaFree waits for work that may use it)
+        CK(cudaFree(vec.front().dev), "grid tables");
+        vec.erase(vec.begin());
+    }
     AxisCache c;
+    memset(&c, 0, sizeof(c));
     memcpy(c.lo, q->lo, sizeof(c.lo));
     memcpy(c.hi, q->hi, sizeof(c.hi));
     memcpy(c.dims, q->dims, sizeof(c.dims));
@@ -674,7 +688,11 @@ static gwn_status grid_tables(gwn_ctx *ctx, const gwn_queries *q, int dtype, Que
         off += esz * q->dims[k];
     }
     CK(cudaMalloc(&c.dev, tot), "grid tables");
-    CK(cudaMemcpy(c.dev, host.data(), tot, cudaMemcpyHostToDevice), "grid tables");
+    cudaError_t e = cudaMemcpy(c.dev, host.data(), tot, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(c.dev);
+        return cuda_fail(e, "grid tables");
+    }
     c.bytes = tot;
     vec.push_back(c);
     return grid_tables(ctx, q, dtype, src);

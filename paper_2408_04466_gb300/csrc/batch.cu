@@ -61,26 +61,11 @@ gwn_status eval2d_single(gwn_geom *g, const QuerySrc &src, void *w_out, int32_t 
     // rows per work item: enough items to fill the device twice, at most 32
     int64_t rows64 = S.ny / (2 * (int64_t)(ctx->sm_count > 0 ? ctx->sm_count : 152));
     const int rows = (int)(rows64 < 1 ? 1 : (rows64 > 32 ? 32 : rows64));
-    std::vector<Set2D> sets(1, S);
-    std::vector<int2> items;
-    make_items(sets, rows, items);
-    size_t bytes = sizeof(Set2D) + sizeof(int2) * items.size() + 64;
-    cudaError_t e;
-    char *buf = (char *)arena_get(ctx, 2, bytes, &e);
-    if (!buf) return cuda_fail(e, "2D work list");
-    unsigned long long *counter = (unsigned long long *)buf;
-    Set2D *d_sets = (Set2D *)(buf + 16);
-    int2 *d_items = (int2 *)(buf + 16 + sizeof(Set2D));
-    std::vector<char> host(bytes - 16);
-    memcpy(host.data(), &S, sizeof(Set2D));
-    memcpy(host.data() + sizeof(Set2D), items.data(), sizeof(int2) * items.size());
-    e = cudaMemcpyAsync(buf + 16, host.data(), sizeof(Set2D) + sizeof(int2) * items.size(), cudaMemcpyHostToDevice,
-                        ctx->stream);
-    if (e != cudaSuccess) return cuda_fail(e, "2D work list upload");
-    e = cudaStreamSynchronize(ctx->stream);   // host staging buffer is released below
-    if (e != cudaSuccess) return cuda_fail(e, "2D work list upload");
-    e = launch_eval2d_items(cs, d_sets, d_items, (int64_t)items.size(), counter, rows, 128, S.nx, w_out, chi_out,
-                            b_out, cnt, ctx->d_status, ctx->sm_count, ctx->stream);
+    // one set, passed by value; its items are its row blocks (no work list to
+    // upload, no host synchronisation)
+    int64_t n_items = (S.ny + rows - 1) / rows;
+    cudaError_t e = launch_eval2d_items(cs, nullptr, nullptr, &S, n_items, ctx->d_work_counter, rows, 128, S.nx,
+                                        w_out, chi_out, b_out, cnt, ctx->d_status, ctx->sm_count, ctx->stream);
     if (e != cudaSuccess) return cuda_fail(e, "2D evaluation");
     return GWN_OK;
 }
@@ -227,7 +212,7 @@ extern "C" GWN_API gwn_status gwn_eval_batch(gwn_geom *g, const gwn_queries *que
         if (want_threads && want_rows) cands.emplace_back(want_threads, want_rows);
         else {
             int ts[2] = {128, 256};
-            int rs[4] = {4, 16, 64, 256};
+            int rs[5] = {1, 4, 16, 64, 256};
             for (int t : ts)
                 for (int r : rs)
                     if ((!want_threads || t == want_threads) && (!want_rows || r == want_rows)) cands.emplace_back(t, r);
@@ -243,7 +228,7 @@ extern "C" GWN_API gwn_status gwn_eval_batch(gwn_geom *g, const gwn_queries *que
             float ms = 0.f;
             for (int rep = 0; rep < 2; rep++) {
                 cudaEventRecord(e0, ctx->stream);
-                e = launch_eval2d_items(g->cs, P->d_sets, P->d_items, P->n_items, P->d_counter, cd.second, cd.first,
+                e = launch_eval2d_items(g->cs, P->d_sets, P->d_items, nullptr, P->n_items, P->d_counter, cd.second, cd.first,
                                         P->max_nx, w_out, nullptr, nullptr, nullptr, ctx->d_status, ctx->sm_count,
                                         ctx->stream);
                 cudaEventRecord(e1, ctx->stream);
@@ -279,7 +264,7 @@ extern "C" GWN_API gwn_status gwn_eval_batch(gwn_geom *g, const gwn_queries *que
         }
         e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-            cudaError_t le = launch_eval2d_items(g->cs, P->d_sets, P->d_items, P->n_items, P->d_counter, P->rows,
+            cudaError_t le = launch_eval2d_items(g->cs, P->d_sets, P->d_items, nullptr, P->n_items, P->d_counter, P->rows,
                                                  P->threads, P->max_nx, w_out, nullptr, nullptr, nullptr,
                                                  ctx->d_status, ctx->sm_count, cap);
             e = cudaStreamEndCapture(cap, &P->graph);
@@ -293,7 +278,7 @@ extern "C" GWN_API gwn_status gwn_eval_batch(gwn_geom *g, const gwn_queries *que
     }
     if (use_graph) e = cudaGraphLaunch(P->exec, ctx->stream);
     else
-        e = launch_eval2d_items(g->cs, P->d_sets, P->d_items, P->n_items, P->d_counter, P->rows, P->threads, P->max_nx,
+        e = launch_eval2d_items(g->cs, P->d_sets, P->d_items, nullptr, P->n_items, P->d_counter, P->rows, P->threads, P->max_nx,
                                 w_out, nullptr, nullptr, nullptr, ctx->d_status, ctx->sm_count, ctx->stream);
     if (e != cudaSuccess) return cuda_fail(e, "batched launch");
     if (stats) {

@@ -29,16 +29,25 @@
 // CHUNK pieces (each contributes at most one crossing), crossings are
 // collected in shared memory, and every query of the row adds the signed
 // crossings to its right.  The epilogue adds the chord terms and writes w.
+#include <string.h>
+
 #include "gwn_internal.h"
 
 namespace gwn {
 
 template <typename T> struct Num;
+// Root tolerance in u: Newton stops once its step (or the bracket) is below
+// tol.  A Newton step that small leaves an error of order its square; a
+// bisection-terminated root is within tol in u, i.e. about tol |x'(u)| in x.
+// That only decides queries that close to the curve, far inside the band
+// (1e-4 of the grid diagonal) where w is not compared, so float32 uses 1e-6
+// (2.7 iterations per root on average on the star chains); float64 keeps
+// 1e-16.
 template <> struct Num<float> {
     static __device__ __forceinline__ float atan2_(float y, float x) { return atan2f(y, x); }
     static constexpr float inv2pi = 0.15915494309189535f;
     static constexpr int max_iter = 60;
-    static constexpr float tol = 1e-7f;
+    static constexpr float tol = 1e-6f;
 };
 template <> struct Num<double> {
     static __device__ __forceinline__ double atan2_(double y, double x) { return atan2(y, x); }
@@ -61,7 +70,17 @@ __device__ __forceinline__ T dbern(T p0, T p1, T p2, T p3, T u) {
 // x of the crossing of the monotone piece [u0, u1] of the segment with
 // control points c[0..7] (x0 y0 x1 y1 ...) with the row y = yr.
 template <typename T>
+__device__ T piece_root_xu(const T *c, T u0, T u1, T ya, T yb, T yr, int *iters_out, T *u_out);
+
+template <typename T>
 __device__ T piece_root_x(const T *c, T u0, T u1, T ya, T yb, T yr, int *iters_out) {
+    T u;
+    return piece_root_xu<T>(c, u0, u1, ya, yb, yr, iters_out, &u);
+}
+
+// the same, also returning the parameter of the root
+template <typename T>
+__device__ T piece_root_xu(const T *c, T u0, T u1, T ya, T yb, T yr, int *iters_out, T *u_out) {
     // orient the bracket so that g(lo) <= 0 < g(hi) with g = y(u) - yr
     T lo = u0, hi = u1;
     bool inc = yb > ya;
@@ -71,7 +90,8 @@ __device__ T piece_root_x(const T *c, T u0, T u1, T ya, T yb, T yr, int *iters_o
     int it = 0;
     for (; it < Num<T>::max_iter; it++) {
         T g = bern(c[1], c[3], c[5], c[7], u) - yr;
-        if (g <= T(0)) lo = u; else hi = u;
+        if (g == T(0)) break;                       // exact root (a zero Newton step would fall to bisection)
+        if (g < T(0)) lo = u; else hi = u;
         T dg = dbern(c[1], c[3], c[5], c[7], u);
         T un = u - g / dg;
         T mn = lo < hi ? lo : hi, mx = lo < hi ? hi : lo;
@@ -81,6 +101,7 @@ __device__ T piece_root_x(const T *c, T u0, T u1, T ya, T yb, T yr, int *iters_o
         if ((step < T(0) ? -step : step) <= Num<T>::tol || (mx - mn) <= Num<T>::tol) break;
     }
     *iters_out = it;
+    *u_out = u;
     return bern(c[0], c[2], c[4], c[6], u);
 }
 
@@ -99,12 +120,15 @@ __host__ __device__ constexpr size_t eval2d_fallback_off() {
 // Fast float32 atan2 for the chord term (half-angle form: v = y/(|z| + |x|)
 // in [-1, 1], atan2 = 2 atan(v) or copysign(pi, y) - 2 atan(v) for x < 0;
 // atan(v) = v P(v^2) with the degree-8 odd minimax polynomial of the 3D
-// boundary term, relative error 1.5e-8).
+// boundary term, relative error 1.5e-8; MUFU rsqrt and reciprocal, ~2 ulp).
 __device__ __forceinline__ float atan2_fast(float y, float x) {
-    float z = sqrtf(fmaf(x, x, y * y));
-    float d = z + fabsf(x);
-    if (!(d > 0.f)) return 0.f;
-    float v = y / d, v2 = v * v;
+    float z2 = fmaf(x, x, y * y);
+    if (!(z2 > 1e-37f)) return 0.f;
+    float rz;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(rz) : "f"(z2));
+    float d = fmaf(z2, rz, fabsf(x)), rd;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rd) : "f"(d));
+    float v = y * rd, v2 = v * v;
     float q = fmaf(0.00284989f, v2, -0.01606863f);
     q = fmaf(q, v2, 0.04269152f);
     q = fmaf(q, v2, -0.07504295f);
@@ -135,6 +159,20 @@ __device__ __forceinline__ int lower_bound_rows(const T *ys, int n, T v) {
     return lo;
 }
 
+// first column j in [0, nx] with ax[j] >= x, on a grid axis (non-decreasing,
+// spaced ~uniformly): a guess from the spacing, corrected against the stored
+// values, so the result is exactly the lower bound
+template <typename T>
+__device__ __forceinline__ int lower_bound_cols(const T *__restrict__ ax, int nx, T a0, T inv_step, T x) {
+    int j = nx;
+    if (!(x <= ax[nx - 1])) return nx;
+    T g = (x - a0) * inv_step;
+    j = g <= T(0) ? 0 : (g >= T(nx - 1) ? nx - 1 : (int)ceil(g));
+    while (j > 0 && ax[j - 1] >= x) j--;
+    while (j < nx && ax[j] < x) j++;
+    return j;
+}
+
 // chord terms of the set's chains at (xq, yr): the chord's crossing with the
 // +x ray (half-open in y) and minus the angle it subtends, / 2 pi
 template <typename T>
@@ -157,30 +195,49 @@ __device__ __forceinline__ T chord_terms(const T *__restrict__ ctrl, const int64
     return term;
 }
 
+template <typename T>
+__device__ __forceinline__ void store_w(const Set2D &S, int64_t row, int64_t i, int chi, T term, T *w_out,
+                                        int32_t *chi_out, T *b_out) {
+    int64_t o = S.out_off + row * S.nx + i;
+    if (w_out) w_out[o] = (T)chi + term;
+    if (chi_out) chi_out[o] = chi;
+    if (b_out) b_out[o] = term;
+}
+
 // Work items are (set, block of rows).  An item finds the rows each of the
 // set's pieces crosses: a piece with end values y0, y1 is crossed by row r
 // iff min <= y_r < max, and since the row values are non-decreasing those
 // rows form one range, found by binary search in the item's row values.
 // Crossings are binned by row in shared memory (a counting pass, a prefix
 // sum, a filling pass that finds each root), so the work is proportional to
-// the pieces plus the crossings rather than to rows x pieces.  Then every
-// query of a row adds the signed crossings to its right and the chord terms.
-// An item with more than CAP crossings falls back to scanning the pieces
-// once per row, CHUNK crossings at a time.
+// the pieces plus the crossings rather than to rows x pieces.
+//
+// Queries: one warp per row.  Every crossing x_k of the row finds its column
+// j_k = first grid column with x >= x_k and adds its direction to a per-warp
+// difference array D[j_k]; a suffix sum over the columns then gives each
+// query i its signed count of crossings to the right,
+//   chi(i) = sum_{k : x_k > xq_i} dir_k = sum_{j > i} D[j],
+// in O(1) per query.  The chord terms are added and w is stored (coalesced).
+// The item's rows are processed in sub-blocks whose crossings fit in CAP; a
+// single row with more than CAP crossings falls back to scanning the pieces
+// CHUNK crossings at a time.
 template <typename T>
 __global__ void eval2d_kernel(const T *__restrict__ ctrl, const int64_t *__restrict__ chain_off,
-                              const int64_t *__restrict__ piece_seg, const double *__restrict__ piece_u,
-                              const double *__restrict__ piece_y, const Set2D *__restrict__ sets,
-                              const int2 *__restrict__ items, int64_t n_items, unsigned long long *counter,
-                              int rows_per_item, T *__restrict__ w_out, int32_t *__restrict__ chi_out,
-                              T *__restrict__ b_out, unsigned long long *cnt, int *status, int max_nx) {
+                              const int64_t *__restrict__ piece_seg, const T *__restrict__ piece_u,
+                              const T *__restrict__ piece_y, const Set2D *__restrict__ sets,
+                              const int2 *__restrict__ items, const Set2D single, int64_t n_items,
+                              unsigned long long *counter, int rows_per_item, T *__restrict__ w_out,
+                              int32_t *__restrict__ chi_out, T *__restrict__ b_out, unsigned long long *cnt,
+                              int *status, int max_nx) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *xs = (T *)smem_raw;                                    // CAP crossings
     T *ys = xs + CAP;                                         // MAX_ROWS row values
     int *roff = (int *)(ys + MAX_ROWS);                       // MAX_ROWS + 1 offsets
     int *rcur = roff + MAX_ROWS + 1;                          // MAX_ROWS counts / cursors
     signed char *dirs = (signed char *)(rcur + MAX_ROWS);     // CAP directions
-    int *chi_row = (int *)(smem_raw + eval2d_fallback_off<T>());   // max_nx counts (fallback)
+    int *s_D = (int *)(smem_raw + eval2d_fallback_off<T>());   // per warp: max_nx + 1 (fallback: chi_row)
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     __shared__ int ncross;
     __shared__ long long item_sh;
     for (int64_t guard = 0; guard <= n_items; guard++) {
@@ -189,10 +246,12 @@ __global__ void eval2d_kernel(const T *__restrict__ ctrl, const int64_t *__restr
         long long item = item_sh;
         __syncthreads();
         if (item >= n_items) break;
-        int2 it = items[item];
-        const Set2D S = sets[it.x];
+        // one set passed by value (items are its row blocks), or a work list
+        int2 it = items ? items[item] : make_int2(0, (int)item);
+        const Set2D S = sets ? sets[it.x] : single;
         const T *ax = (const T *)S.ax;
         const T *ay = (const T *)S.ay;
+        const int nx = (int)S.nx;
         int64_t r0 = (int64_t)it.y * rows_per_item;
         int64_t r1 = r0 + rows_per_item < S.ny ? r0 + rows_per_item : S.ny;
         const int nr = (int)(r1 - r0);
@@ -203,66 +262,129 @@ __global__ void eval2d_kernel(const T *__restrict__ ctrl, const int64_t *__restr
         __syncthreads();
         // pass 1: crossings per row
         for (int64_t p = S.p_lo + threadIdx.x; p < S.p_hi; p += blockDim.x) {
-            T ya = (T)piece_y[2 * p], yb = (T)piece_y[2 * p + 1];
+            T ya = piece_y[2 * p], yb = piece_y[2 * p + 1];
             T lo = ya < yb ? ya : yb, hi = ya < yb ? yb : ya;
             int ra = lower_bound_rows(ys, nr, lo), rb = lower_bound_rows(ys, nr, hi);
             for (int r = ra; r < rb; r++) atomicAdd(&rcur[r], 1);
         }
         __syncthreads();
-        if (threadIdx.x == 0) {
-            int acc = 0;
-            for (int r = 0; r < nr; r++) {
-                roff[r] = acc;
-                acc += rcur[r];
+        if (warp == 0) {                                      // exclusive prefix sum over the rows
+            int carry = 0;
+            for (int base = 0; base < nr; base += 32) {
+                int r = base + lane;
+                int v = r < nr ? rcur[r] : 0, x = v;
+                for (int off = 1; off < 32; off <<= 1) {
+                    int t = __shfl_up_sync(FULL, x, off);
+                    if (lane >= off) x += t;
+                }
+                if (r < nr) roff[r] = carry + x - v;
+                carry += __shfl_sync(FULL, x, 31);
             }
-            roff[nr] = acc;
+            if (lane == 0) roff[nr] = carry;
         }
         __syncthreads();
         const int total = roff[nr];
         if (cnt && threadIdx.x == 0) atomicAdd(&cnt[CNT_ROOTS], (unsigned long long)total);
-        if (total <= CAP) {
-            for (int i = threadIdx.x; i < nr; i += blockDim.x) rcur[i] = 0;
-            __syncthreads();
-            // pass 2: the roots, binned by row
-            for (int64_t p = S.p_lo + threadIdx.x; p < S.p_hi; p += blockDim.x) {
-                T ya = (T)piece_y[2 * p], yb = (T)piece_y[2 * p + 1];
-                T lo = ya < yb ? ya : yb, hi = ya < yb ? yb : ya;
-                int ra = lower_bound_rows(ys, nr, lo), rb = lower_bound_rows(ys, nr, hi);
-                if (ra >= rb) continue;
-                const T *cp = ctrl + 2 * piece_seg[p];
-                T c[8];
+        const T a0 = ax[0];
+        const T inv_step = nx > 1 ? T(nx - 1) / (ax[nx - 1] - ax[0]) : T(0);
+        // rows in sub-blocks whose crossings fit in CAP (a single row with more
+        // than CAP crossings takes the per-row fallback)
+        for (int sb0 = 0; sb0 < nr;) {
+            int sb1 = sb0 + 1;
+            {
+                int lo = sb0 + 1, hi = nr;               // largest sb1 with roff[sb1] - roff[sb0] <= CAP
+                while (lo <= hi) {
+                    int mid = (lo + hi) >> 1;
+                    if (roff[mid] - roff[sb0] <= CAP) { sb1 = mid; lo = mid + 1; } else hi = mid - 1;
+                }
+            }
+            const bool fits = roff[sb1] - roff[sb0] <= CAP;
+            if (fits) {
+                const int base = roff[sb0];
+                for (int i = sb0 + threadIdx.x; i < sb1; i += blockDim.x) rcur[i] = 0;
+                __syncthreads();
+                // pass 2: the roots of rows [sb0, sb1), binned by row
+                for (int64_t p = S.p_lo + threadIdx.x; p < S.p_hi; p += blockDim.x) {
+                    T ya = piece_y[2 * p], yb = piece_y[2 * p + 1];
+                    T lo = ya < yb ? ya : yb, hi = ya < yb ? yb : ya;
+                    int ra = lower_bound_rows(ys, nr, lo), rb = lower_bound_rows(ys, nr, hi);
+                    if (ra < sb0) ra = sb0;
+                    if (rb > sb1) rb = sb1;
+                    if (ra >= rb) continue;
+                    const T *cp = ctrl + 2 * piece_seg[p];
+                    T c[8];
 #pragma unroll
-                for (int k = 0; k < 8; k++) c[k] = cp[k];
-                T u0 = (T)piece_u[2 * p], u1 = (T)piece_u[2 * p + 1];
-                signed char dir = yb > ya ? 1 : -1;
-                for (int r = ra; r < rb; r++) {
-                    int iters;
-                    T x = piece_root_x<T>(c, u0, u1, ya, yb, ys[r], &iters);
-                    if (iters >= Num<T>::max_iter && status) atomicOr(status, ST_TIMEOUT);
-                    int slot = roff[r] + atomicAdd(&rcur[r], 1);
-                    xs[slot] = x;
-                    dirs[slot] = dir;
+                    for (int k = 0; k < 8; k++) c[k] = cp[k];
+                    T u0 = piece_u[2 * p], u1 = piece_u[2 * p + 1];
+                    signed char dir = yb > ya ? 1 : -1;
+                    // rows ascend and the piece is monotone in y, so each root
+                    // brackets the next: the remaining part of the piece runs
+                    // from the last root (at the last row's y) to the far end
+                    T ua = u0, ub = u1, yla = ya, ylb = yb;
+                    for (int r = ra; r < rb; r++) {
+                        int iters;
+                        T u;
+                        T x = piece_root_xu<T>(c, ua, ub, yla, ylb, ys[r], &iters, &u);
+                        if (iters >= Num<T>::max_iter && status) atomicOr(status, ST_TIMEOUT);
+                        if (dir > 0) { ua = u; yla = ys[r]; } else { ub = u; ylb = ys[r]; }
+                        int slot = roff[r] - base + atomicAdd(&rcur[r], 1);
+                        xs[slot] = x;
+                        dirs[slot] = dir;
+                    }
                 }
-            }
-            __syncthreads();
-            // queries: signed crossings to the right + chord terms
-            for (int r = 0; r < nr; r++) {
-                const T yr = ys[r];
-                const int k0 = roff[r], k1 = roff[r + 1];
-                for (int64_t i = threadIdx.x; i < S.nx; i += blockDim.x) {
-                    T xq = ax[i];
-                    int chi = 0;
-                    for (int k = k0; k < k1; k++) chi += xs[k] > xq ? (int)dirs[k] : 0;
-                    T term = chord_terms<T>(ctrl, chain_off, S, xq, yr, chi);
-                    int64_t o = S.out_off + (r0 + r) * S.nx + i;
-                    if (w_out) w_out[o] = (T)chi + term;
-                    if (chi_out) chi_out[o] = chi;
-                    if (b_out) b_out[o] = term;
+                __syncthreads();
+                // queries: one warp per row
+                int *D = s_D + warp * (max_nx + 1);
+                for (int r = sb0 + warp; r < sb1; r += nwarps) {
+                    for (int j = lane; j <= nx; j += 32) D[j] = 0;
+                    __syncwarp();
+                    for (int k = roff[r] - base + lane; k < roff[r + 1] - base; k += 32)
+                        atomicAdd(&D[lower_bound_cols(ax, nx, a0, inv_step, xs[k])], (int)dirs[k]);
+                    __syncwarp();
+                    int carry = 0;                            // suffix sums, from the top chunk down
+                    for (int cb = (nx / 32) * 32; cb >= 0; cb -= 32) {
+                        int j = cb + lane;
+                        int x = j <= nx ? D[j] : 0;
+                        for (int off = 1; off < 32; off <<= 1) {
+                            int t = __shfl_down_sync(FULL, x, off);
+                            if (lane + off < 32) x += t;
+                        }
+                        x += carry;
+                        if (j <= nx) D[j] = x;
+                        carry = __shfl_sync(FULL, x, 0);
+                    }
+                    __syncwarp();
+                    const T yr = ys[r];
+                    if (S.c_hi - S.c_lo == 1) {
+                        // one chain: its chord's end points and row-constant parts hoisted
+                        const T *sp = ctrl + 2 * chain_off[S.c_lo];
+                        const T *ep = ctrl + 2 * (chain_off[S.c_lo + 1] - 1);
+                        const T spx = sp[0], sy = sp[1] - yr, epx = ep[0], ey = ep[1] - yr;
+                        const T lo = ey < sy ? ey : sy, hi = ey < sy ? sy : ey;
+                        const bool crosses = lo <= T(0) && T(0) < hi, up = sy > ey;
+                        for (int i = lane; i < nx; i += 32) {
+                            T xq = ax[i];
+                            T sx = spx - xq, ex = epx - xq;
+                            T cr = ex * sy - ey * sx;         // cross(e - p, s - p)
+                            int chi = D[i + 1];
+                            if (crosses && (up ? (cr > T(0)) : (cr < T(0)))) chi += up ? 1 : -1;
+                            T term = Chord<T>::atan2_(-cr, sx * ex + sy * ey) * Num<T>::inv2pi;
+                            store_w<T>(S, r0 + r, i, chi, term, w_out, chi_out, b_out);
+                        }
+                    } else {
+                        for (int i = lane; i < nx; i += 32) {
+                            int chi = D[i + 1];
+                            T term = chord_terms<T>(ctrl, chain_off, S, ax[i], yr, chi);
+                            store_w<T>(S, r0 + r, i, chi, term, w_out, chi_out, b_out);
+                        }
+                    }
+                    __syncwarp();
                 }
-            }
-        } else {
-            // fallback: one row at a time, CHUNK crossings per pass
-            for (int r = 0; r < nr; r++) {
+                __syncthreads();
+            } else {
+                // fallback for row sb0 (more than CAP crossings): CHUNK crossings per pass
+                int *chi_row = s_D;
+                const int r = sb0;
                 const T yr = ys[r];
                 for (int64_t i = threadIdx.x; i < S.nx; i += blockDim.x) chi_row[i] = 0;
                 for (int64_t c0 = S.p_lo; c0 < S.p_hi; c0 += CHUNK) {
@@ -270,7 +392,7 @@ __global__ void eval2d_kernel(const T *__restrict__ ctrl, const int64_t *__restr
                     __syncthreads();
                     int64_t c1 = c0 + CHUNK < S.p_hi ? c0 + CHUNK : S.p_hi;
                     for (int64_t p = c0 + threadIdx.x; p < c1; p += blockDim.x) {
-                        T ya = (T)piece_y[2 * p], yb = (T)piece_y[2 * p + 1];
+                        T ya = piece_y[2 * p], yb = piece_y[2 * p + 1];
                         T lo = ya < yb ? ya : yb, hi = ya < yb ? yb : ya;
                         if (!(lo <= yr && yr < hi)) continue;
                         const T *cp = ctrl + 2 * piece_seg[p];
@@ -278,7 +400,7 @@ __global__ void eval2d_kernel(const T *__restrict__ ctrl, const int64_t *__restr
 #pragma unroll
                         for (int k = 0; k < 8; k++) c[k] = cp[k];
                         int iters;
-                        T x = piece_root_x<T>(c, (T)piece_u[2 * p], (T)piece_u[2 * p + 1], ya, yb, yr, &iters);
+                        T x = piece_root_x<T>(c, piece_u[2 * p], piece_u[2 * p + 1], ya, yb, yr, &iters);
                         if (iters >= Num<T>::max_iter && status) atomicOr(status, ST_TIMEOUT);
                         int slot = atomicAdd(&ncross, 1);
                         xs[slot] = x;
@@ -297,30 +419,35 @@ __global__ void eval2d_kernel(const T *__restrict__ ctrl, const int64_t *__restr
                 for (int64_t i = threadIdx.x; i < S.nx; i += blockDim.x) {
                     int chi = chi_row[i];
                     T term = chord_terms<T>(ctrl, chain_off, S, ax[i], yr, chi);
-                    int64_t o = S.out_off + (r0 + r) * S.nx + i;
-                    if (w_out) w_out[o] = (T)chi + term;
-                    if (chi_out) chi_out[o] = chi;
-                    if (b_out) b_out[o] = term;
+                    store_w<T>(S, r0 + r, i, chi, term, w_out, chi_out, b_out);
                 }
                 __syncthreads();
+                sb1 = sb0 + 1;
             }
+            sb0 = sb1;
         }
         __syncthreads();
     }
 }
 
-size_t eval2d_smem(int dtype, int64_t max_nx) {
+size_t eval2d_smem(int dtype, int64_t max_nx, int threads) {
     size_t off = dtype == GWN_F64 ? eval2d_fallback_off<double>() : eval2d_fallback_off<float>();
-    return off + sizeof(int) * (size_t)max_nx;
+    size_t per_warp = sizeof(int) * (size_t)(max_nx + 1);
+    size_t d = per_warp * (size_t)(threads / 32);
+    return off + (d > sizeof(int) * (size_t)max_nx ? d : sizeof(int) * (size_t)max_nx);
 }
 
-cudaError_t launch_eval2d_items(const ChainSet &cs, const Set2D *d_sets, const int2 *d_items, int64_t n_items,
-                                unsigned long long *d_counter, int rows_per_item, int threads, int64_t max_nx,
-                                void *w_out, int32_t *chi_out, void *b_out, unsigned long long *cnt, int *status,
-                                int sm_count, cudaStream_t st) {
+cudaError_t launch_eval2d_items(const ChainSet &cs, const Set2D *d_sets, const int2 *d_items, const Set2D *single,
+                                int64_t n_items, unsigned long long *d_counter, int rows_per_item, int threads,
+                                int64_t max_nx, void *w_out, int32_t *chi_out, void *b_out, unsigned long long *cnt,
+                                int *status, int sm_count, cudaStream_t st) {
     if (n_items == 0) return cudaSuccess;
-    if (rows_per_item < 1 || rows_per_item > MAX_ROWS) return cudaErrorInvalidValue;
-    size_t smem = eval2d_smem(cs.dtype, max_nx);
+    if (!d_sets && !single) return cudaErrorInvalidValue;
+    if (rows_per_item < 1 || rows_per_item > MAX_ROWS || threads < 32 || threads % 32) return cudaErrorInvalidValue;
+    Set2D s0;
+    memset(&s0, 0, sizeof(s0));
+    if (single) s0 = *single;
+    size_t smem = eval2d_smem(cs.dtype, max_nx, threads);
     cudaError_t e = cudaMemsetAsync(d_counter, 0, sizeof(unsigned long long), st);
     if (e != cudaSuccess) return e;
     // persistent grid: as many blocks as fit on the device at once
@@ -338,12 +465,14 @@ cudaError_t launch_eval2d_items(const ChainSet &cs, const Set2D *d_sets, const i
     if (blocks > n_items) blocks = n_items;
     if (cs.dtype == GWN_F64) {
         eval2d_kernel<double><<<(unsigned)blocks, threads, smem, st>>>(
-            (const double *)cs.ctrl, cs.chain_off, cs.piece_seg, cs.piece_u, cs.piece_y, d_sets, d_items, n_items,
-            d_counter, rows_per_item, (double *)w_out, chi_out, (double *)b_out, cnt, status, (int)max_nx);
+            (const double *)cs.ctrl, cs.chain_off, cs.piece_seg, (const double *)cs.piece_uT,
+            (const double *)cs.piece_yT, d_sets, d_items, s0, n_items, d_counter, rows_per_item, (double *)w_out,
+            chi_out, (double *)b_out, cnt, status, (int)max_nx);
     } else {
         eval2d_kernel<float><<<(unsigned)blocks, threads, smem, st>>>(
-            (const float *)cs.ctrl, cs.chain_off, cs.piece_seg, cs.piece_u, cs.piece_y, d_sets, d_items, n_items,
-            d_counter, rows_per_item, (float *)w_out, chi_out, (float *)b_out, cnt, status, (int)max_nx);
+            (const float *)cs.ctrl, cs.chain_off, cs.piece_seg, (const float *)cs.piece_uT,
+            (const float *)cs.piece_yT, d_sets, d_items, s0, n_items, d_counter, rows_per_item, (float *)w_out,
+            chi_out, (float *)b_out, cnt, status, (int)max_nx);
     }
     return cudaGetLastError();
 }

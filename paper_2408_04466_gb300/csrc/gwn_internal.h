@@ -92,6 +92,8 @@ struct ChainSet {
     int64_t *piece_seg = nullptr;
     double *piece_u = nullptr;     // [n_pieces][2]
     double *piece_y = nullptr;     // [n_pieces][2] (y at u0, y at u1)
+    void *piece_uT = nullptr;      // piece_u in the chain dtype (aliases piece_u for float64)
+    void *piece_yT = nullptr;      // piece_y in the chain dtype (aliases piece_y for float64)
     int32_t *piece_chain = nullptr;
     int64_t *chain_piece_off = nullptr;  // device [n_chains + 1]
     std::vector<int64_t> h_chain_off, h_chain_piece_off;
@@ -112,6 +114,16 @@ struct Arena {            // grow-only scratch owned by a context
     size_t bytes = 0;
 };
 
+// Device coordinate tables of one query grid (per context, reused while the
+// same grid is evaluated again).
+struct AxisCache {
+    double lo[3], hi[3];
+    int64_t dims[3];
+    int dim, dtype;
+    void *dev = nullptr;
+    size_t bytes = 0;
+};
+
 }  // namespace gwn
 
 struct gwn_ctx {
@@ -122,8 +134,10 @@ struct gwn_ctx {
     unsigned long long *d_cnt = nullptr;      // device counters [CNT_NUM]
     int32_t *d_defer_count = nullptr;         // length of the deferred-query list
     int2 *d_tpairs = nullptr;                 // traversal: unsettled (query, triangle) pairs [GWN_TPAIR_CAP]
+    unsigned long long *d_work_counter = nullptr;   // 2D work-item counter
     int32_t *d_tpair_count = nullptr;
     gwn::Arena scratch[5];                    // 0 chi, 1 staged points, 2 2D batch, 3 host-eval w, 4 deferred list
+    std::vector<gwn::AxisCache> axis_cache;   // most recent grids, at most 64
     cudaEvent_t ev[8];
     bool events = false;
 };
@@ -195,7 +209,10 @@ cudaError_t launch_bruteforce3d(const float *V, const int32_t *F, int64_t nf, co
                                 int sm_count, cudaStream_t st);
 
 // 2D
-cudaError_t launch_eval2d_items(const ChainSet &cs, const Set2D *d_sets, const int2 *d_items, int64_t n_items,
+// 2D evaluation over work items: either a device work list (d_sets, d_items)
+// or one set passed by value (single, items = its row blocks).
+cudaError_t launch_eval2d_items(const ChainSet &cs, const Set2D *d_sets, const int2 *d_items, const Set2D *single,
+                                int64_t n_items,
                                 unsigned long long *d_counter, int rows_per_item, int threads, int64_t max_nx,
                                 void *w_out, int32_t *chi_out, void *b_out, unsigned long long *cnt, int *status,
                                 int sm_count, cudaStream_t st);

@@ -88,7 +88,7 @@ def test_star_chains_fp32_and_batch(gwn, ctx):
         assert np.array_equal(ws, wb[offs[c]:offs[c] + n]), c
         _compare_chain(ctrl.astype(np.float64), cs.grids[c], ws, r["chi"].cpu().numpy(), 1e-6)
     t, rows = ch.batch_plan()
-    assert t in (128, 256) and rows in (4, 16, 64, 256)
+    assert t in (128, 256) and rows in (1, 4, 16, 64, 256)
     # a forced plan gives the same numbers
     wf, _ = ch.eval_batch(grids, threads=256, rows=1, use_graph=False)
     assert np.array_equal(wf.cpu().numpy(), wb)
@@ -157,12 +157,7 @@ def test_star_chains_full_size_sampled(gwn, ctx):
         assert np.abs(wc.astype(np.float64) - wq)[keep].max() <= 1e-6, c
 
 
-def test_binned_rows_overflow_fallback(gwn, ctx):
-    """A zig-zag chain crossing every row hundreds of times: with 256 rows per
-    work item the binned crossings overflow the item's buffer and the kernel
-    falls back to per-row chunked scanning; both paths agree exactly with
-    each other and with the oracle's closed form."""
-    n = 600
+def _zigzag(n):
     xk = np.arange(n + 1, dtype=np.float64)
     yk = np.where(np.arange(n + 1) % 2 == 0, -1.0, 1.0)
     ctrl = np.zeros((3 * n + 1, 2))
@@ -171,14 +166,25 @@ def test_binned_rows_overflow_fallback(gwn, ctx):
             t = j / 3.0
             ctrl[3 * k + j] = ((1 - t) * xk[k] + t * xk[k + 1], (1 - t) * yk[k] + t * yk[k + 1])
     ctrl[-1] = (xk[-1], yk[-1])
+    return ctrl
+
+
+@pytest.mark.parametrize("n, dims", [(600, (64, 256)), (8500, (24, 12))])
+def test_binned_rows_overflow_fallback(gwn, ctx, n, dims):
+    """A zig-zag chain crossing every row n times.  With 256 rows per work
+    item the item's crossings exceed its buffer: with n = 600 the rows are
+    split into sub-blocks that fit; with n = 8500 a single row overflows and
+    takes the per-row fallback.  Every path agrees exactly with the 4-row
+    binned path and with the oracle's closed form."""
+    ctrl = _zigzag(n)
     ch = gwn.Bezier2D(ctx, ctrl, [0, len(ctrl)])
-    g = gen.Grid((-1.0, -1.37), (n + 1.0, 1.41), (64, 256))
+    g = gen.Grid((-1.0, -1.37), (n + 1.0, 1.41), dims)
     grid = gwn.Grid(g.lo, g.hi, g.dims)
-    w_fb, _ = ch.eval_batch([grid], threads=128, rows=256, use_graph=False)     # overflow -> fallback
-    w_bin, _ = ch.eval_batch([grid], threads=128, rows=4, use_graph=False)      # binned
-    w_fb = w_fb.cpu().numpy()
+    w_big, _ = ch.eval_batch([grid], threads=128, rows=256, use_graph=False)
+    w_bin, _ = ch.eval_batch([grid], threads=128, rows=4, use_graph=False)
+    w_big = w_big.cpu().numpy()
     w_bin = w_bin.cpu().numpy()
-    assert np.array_equal(w_fb, w_bin)
+    assert np.array_equal(w_big, w_bin)
     P = gen.grid_points(g, np.float64)
     wc, chic = oracle.w2d_closed_x(ctrl, P)
     keep = oracle.dist2d(ctrl, P) > 1e-6
