@@ -469,6 +469,62 @@ def run_other(args):
                     "boundary_edges": info["n_boundary_edges"], "triangles": int(len(m.F)),
                     "kernels": {"traverse_ms": st["ms_traverse"], "bterm3d_ms": st["ms_boundary"]},
                     "roofline_bterm": _alu_roofline(len(Pt), info, st["ms_boundary"])})
+    elif name == "chain_points":
+        # 2D point queries (one +x ray per point, no ray reuse): the largest
+        # star chain (float32, 4,194,304 uniform points in its grid's box) and
+        # the circle chain (float64, 1,048,576 points)
+        res = {}
+        cs = gen.star_chains()
+        c = int(np.argmax(np.diff(cs.offsets)))
+        cases = [("star_chain_f32", cs.ctrl[cs.offsets[c]:cs.offsets[c + 1]], cs.grids[c], 1 << 22, np.float32),
+                 ("circle_chain_f64", gen.bezier_circle_chain().ctrl, gen.bezier_circle_chain().grids[0], 1 << 20,
+                  np.float64)]
+        for label, ctrl, g, npts, dt in cases:
+            geo = gwn.Bezier2D(ctx, np.ascontiguousarray(ctrl, dt), [0, len(ctrl)])
+            rng = np.random.default_rng(5)
+            P = np.stack([rng.uniform(g.lo[0], g.hi[0], npts), rng.uniform(g.lo[1], g.hi[1], npts)], 1).astype(dt)
+            Pt = gwn.Points(torch.as_tensor(P).to(dev))
+            ms = _timed(lambda: geo.eval(Pt), args.steps, args.warmup, stream)
+            sub = P[:4096].astype(np.float64)
+            t0 = time.perf_counter()
+            oracle.w2d_closed_x(np.asarray(ctrl, np.float64), sub)
+            dto = time.perf_counter() - t0
+            res[label] = {"segments": (len(ctrl) - 1) // 3, "points": npts, "ms": statistics.median(ms),
+                          "queries_per_s": npts / (statistics.median(ms) * 1e-3),
+                          "cpu_baseline_queries_per_s": len(sub) / dto}
+        out.update({"metric": "2D point queries/s (one +x ray per point)", "dtype": "f32/f64", "cases": res,
+                    "value": res["star_chain_f32"]["queries_per_s"],
+                    "ms_per_step": res["star_chain_f32"]["ms"]})
+    elif name == "icosphere_cap_axis":
+        # the benchmark mesh and grid with d = +z: one ray per grid line
+        m, (lo, hi, dims) = workload(0, 1, args.grid)
+        mesh = gwn.Mesh(ctx, m.V, m.F)
+        g = gwn.Grid(lo, hi, dims)
+        w = torch.empty(g.n, dtype=torch.float32, device=dev)
+        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+        out_k = {}
+        for label, d in (("axis_z", np.array([0, 0, 1], np.float32)), ("random", m.d)):
+            mesh.prepare(d)
+            st = mesh.eval(g, d, stats=True, out=w)["stats"]
+
+            times = []
+            for it in range(args.warmup + args.steps):
+                flush.fill_(1.0)                               # L2 flushed before every step
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                mesh.eval(g, d, out=w)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                if it >= args.warmup:
+                    times.append(e0.elapsed_time(e1))
+            out_k[label] = {"ms_per_step": statistics.median(times), "traverse_ms": st["ms_traverse"],
+                            "bterm3d_ms": st["ms_boundary"], "n_tri_tests_per_query": st["n_tri_tests"] / g.n}
+        out.update({"metric": METRIC, "dtype": "f32", "queries_per_step": g.n,
+                    "ms_per_step": out_k["axis_z"]["ms_per_step"],
+                    "value": g.n / (out_k["axis_z"]["ms_per_step"] * 1e-3),
+                    "directions": out_k,
+                    "note": "d = +z reuses one ray per grid line; the random-d run of the same mesh and grid is "
+                            "beside it"})
     elif name == "holey_heightfield":
         m = gen.holey_heightfield()
         mesh = gwn.Mesh(ctx, m.V, m.F)
@@ -505,7 +561,8 @@ def main():
                                                           "smaller values only for profiling captures)")
     ap.add_argument("--no-extras", action="store_true", help="skip comparator, e2e and CPU baseline legs")
     ap.add_argument("--workload", default="icosphere_cap",
-                    choices=["icosphere_cap", "circle_chain_fp64", "star_chains", "slit_torus", "holey_heightfield"],
+                    choices=["icosphere_cap", "circle_chain_fp64", "star_chains", "slit_torus", "holey_heightfield",
+                             "icosphere_cap_axis", "chain_points"],
                     help="icosphere_cap is the benchmark; the others print their own measurement line")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -146,6 +146,9 @@ GWN_API gwn_status gwn_ctx_set_stream(gwn_ctx *ctx, void *cuda_stream);
 /* Synchronise the context's stream and report any device-side error flag
  * raised by earlier evaluations since the last check (then clear it). */
 GWN_API gwn_status gwn_ctx_check(gwn_ctx *ctx);
+/* Geometries created on ctx keep it alive: its resources are released when
+ * both this call has been made and its last geometry has been destroyed, in
+ * either order. */
 GWN_API void gwn_ctx_destroy(gwn_ctx *ctx);
 
 /* Triangle mesh: V float32 [nv x 3], F int32 [nf x 3] in `mem_kind` memory.
@@ -195,6 +198,11 @@ GWN_API gwn_status gwn_bezier_monotone_split_host(const double ctrl[8], double u
                                                   int32_t *n_out);
 
 /* Evaluate w at the queries.
+ *   q:      mesh: a 3D grid or float32 points.  2D: a grid (one +x ray per
+ *           grid row, Optimization of Alg. 1) or points in the chain's dtype
+ *           (one +x ray per point, through a y-bucket index of the pieces).
+ *           Mesh grids with d parallel to a grid axis traverse once per grid
+ *           line.
  *   d:      ray direction.  Mesh: float32[3], nonzero (need not be unit).
  *           2D: must be NULL or (1, 0) (the +x ray).
  *   w_out:  device buffer of n_queries values: float32 for meshes and float32

@@ -13,7 +13,9 @@ library is missing, construction raises.
 """
 from __future__ import annotations
 
+import atexit
 import ctypes as C
+import weakref
 from dataclasses import dataclass
 
 import numpy as np
@@ -93,6 +95,21 @@ class BatchQueries:
             tot += g.n
         self.total = tot
 
+# Live handles, closed geometries-first at interpreter exit (while CUDA and
+# the streams they use are still alive); the library itself keeps a context
+# alive until its last geometry is destroyed.
+_live_geoms = weakref.WeakSet()
+_live_ctxs = weakref.WeakSet()
+
+
+@atexit.register
+def _close_all():
+    for g in list(_live_geoms):
+        g.close()
+    for c in list(_live_ctxs):
+        c.close()
+
+
 class Context:
     """A library context on one CUDA device, bound to a CUDA stream (default:
     torch's current stream at construction)."""
@@ -109,6 +126,7 @@ class Context:
         h = C.c_void_p()
         check(self.lib.gwn_ctx_create(C.byref(h), device, C.c_void_p(stream.cuda_stream)), "gwn_ctx_create")
         self.h = h
+        _live_ctxs.add(self)
 
     def set_stream(self, stream):
         self.stream = stream
@@ -177,6 +195,7 @@ class Mesh(_Geom):
                                        Ft.data_ptr() if self.nf else None, self.nf, mem, C.byref(h)),
               "gwn_mesh_create")
         self.h = h
+        _live_geoms.add(self)
 
     def prepare(self, d):
         dd, dp = _dir(d)
@@ -282,12 +301,15 @@ class Bezier2D(_Geom):
                                            self.offsets.ctypes.data_as(C.c_void_p), len(self.offsets) - 1, mem,
                                            C.byref(h)), "gwn_bezier2d_create")
         self.h = h
+        _live_geoms.add(self)
         self.n_chains = len(self.offsets) - 1
 
-    def eval(self, grid: Grid, want_chi=False, want_b=False, stats=False):
+    def eval(self, queries, want_chi=False, want_b=False, stats=False):
+        """w at a Grid (one +x ray per grid row) or at Points [n, 2] in the
+        chain dtype (one +x ray per point)."""
         torch = _torch()
-        qc = grid.to_c(self.dtype)
-        n = grid.n
+        qc = queries.to_c(self.dtype)
+        n = queries.n
         dev = torch.device("cuda", self.ctx.device)
         w = torch.empty(n, dtype=self.tdtype, device=dev)
         chi = torch.empty(n, dtype=torch.int32, device=dev) if want_chi else None

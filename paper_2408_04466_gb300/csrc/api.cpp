@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <cstdio>
 #include <map>
 #include <memory>
@@ -319,9 +320,14 @@ GWN_API gwn_status gwn_ctx_check(gwn_ctx *ctx) {
     return GWN_OK;
 }
 
-GWN_API void gwn_ctx_destroy(gwn_ctx *ctx) {
-    if (!ctx) return;
-    cudaSetDevice(ctx->device);
+static std::mutex g_ctx_life_mu;
+
+// release the context's resources (no geometry refers to it any more)
+static void ctx_release(gwn_ctx *ctx) {
+    if (cudaSetDevice(ctx->device) == cudaErrorCudartUnloading) {   // process exit: the driver reclaims memory
+        delete ctx;
+        return;
+    }
     cudaStreamSynchronize(ctx->stream);
     for (auto &a : ctx->scratch)
         if (a.ptr) cudaFree(a.ptr);
@@ -336,6 +342,32 @@ GWN_API void gwn_ctx_destroy(gwn_ctx *ctx) {
     if (ctx->events)
         for (int i = 0; i < 8; i++) cudaEventDestroy(ctx->ev[i]);
     delete ctx;
+}
+
+GWN_API void gwn_ctx_destroy(gwn_ctx *ctx) {
+    if (!ctx) return;
+    bool now;
+    {
+        std::lock_guard<std::mutex> lk(g_ctx_life_mu);
+        ctx->destroy_requested = true;
+        now = ctx->geom_refs == 0;
+    }
+    if (now) ctx_release(ctx);
+}
+
+// a new geometry on ctx / a geometry of ctx destroyed
+static void ctx_ref(gwn_ctx *ctx) {
+    std::lock_guard<std::mutex> lk(g_ctx_life_mu);
+    ctx->geom_refs++;
+}
+
+static void ctx_unref(gwn_ctx *ctx) {
+    bool now;
+    {
+        std::lock_guard<std::mutex> lk(g_ctx_life_mu);
+        now = --ctx->geom_refs == 0 && ctx->destroy_requested;
+    }
+    if (now) ctx_release(ctx);
 }
 
 GWN_API gwn_status gwn_boundary_extract_host(const int32_t *F, int64_t nf, int64_t nv, int64_t *loop_offsets,
@@ -382,19 +414,27 @@ static void free_geom_device(gwn_geom *g) {
     if (cs.piece_y) cudaFree(cs.piece_y);
     if (cs.piece_uT && cs.piece_uT != (void *)cs.piece_u) cudaFree(cs.piece_uT);
     if (cs.piece_yT && cs.piece_yT != (void *)cs.piece_y) cudaFree(cs.piece_yT);
+    if (cs.piece_xT) cudaFree(cs.piece_xT);
+    if (cs.bucket_off) cudaFree(cs.bucket_off);
+    if (cs.bucket_idx) cudaFree(cs.bucket_idx);
     if (cs.piece_chain) cudaFree(cs.piece_chain);
     if (cs.chain_piece_off) cudaFree(cs.chain_piece_off);
 }
 
 GWN_API void gwn_geom_destroy(gwn_geom *g) {
     if (!g) return;
+    bool unloading = false;
     if (g->ctx) {
-        cudaSetDevice(g->ctx->device);
-        cudaStreamSynchronize(g->ctx->stream);
+        unloading = cudaSetDevice(g->ctx->device) == cudaErrorCudartUnloading;
+        if (!unloading) cudaStreamSynchronize(g->ctx->stream);
     }
-    if (g->batch_cache) batch_cache_free(g->batch_cache);
-    free_geom_device(g);
+    if (!unloading) {                      // at process exit the driver reclaims device memory
+        if (g->batch_cache) batch_cache_free(g->batch_cache);
+        free_geom_device(g);
+    }
+    gwn_ctx *ctx = g->ctx;
     delete g;
+    if (ctx) ctx_unref(ctx);
 }
 
 GWN_API gwn_status gwn_mesh_create(gwn_ctx *ctx, const float *V, int64_t nv, const int32_t *F, int64_t nf,
@@ -478,6 +518,7 @@ GWN_API gwn_status gwn_mesh_create(gwn_ctx *ctx, const float *V, int64_t nv, con
         free_geom_device(g.get());
         return cuda_fail(e, "gwn_mesh_create");
     }
+    ctx_ref(ctx);
     *out = g.release();
     return GWN_OK;
 }
@@ -495,6 +536,108 @@ GWN_API gwn_status gwn_mesh_prepare(gwn_geom *g, const float d[3]) {
     if (e != cudaSuccess) return cuda_fail(e, "LBVH build");
     return GWN_OK;
 }
+
+}  // extern "C"
+
+namespace {
+
+// Index for 2D point queries (one +x ray per query, no ray reuse): the
+// y-range [ymin, ymax] of all pieces is cut into buckets; a piece is listed in
+// every bucket its y-range touches, widened by one bucket on each side so that
+// the rounding of the bucket map cannot drop it (the exact half-open y-test is
+// made per piece on the device).  Each piece also gets a conservative x-range,
+// the x-range of its segment's control points (convex hull property).
+template <typename T>
+static int bucket_of(T y, T y0, T inv_h, int nb) {
+    T v = (y - y0) * inv_h;
+    if (!(v >= T(0))) return 0;
+    if (v >= T(nb)) return nb - 1;
+    int b = (int)v;
+    return b < nb ? b : nb - 1;
+}
+
+static cudaError_t build_point_index(ChainSet &cs, const std::vector<double> &P, const std::vector<int64_t> &pseg,
+                                     const std::vector<double> &py, int dtype) {
+    const int64_t np = cs.n_pieces;
+    const size_t npa = (size_t)std::max<int64_t>(np, 1);
+    std::vector<double> xr(2 * npa, 0.0);
+    double ylo = 0.0, yhi = 0.0;
+    for (int64_t p = 0; p < np; p++) {
+        const double *c = &P[2 * pseg[p]];
+        double x0 = c[0], x1 = c[0];
+        for (int k = 1; k < 4; k++) {
+            x0 = std::min(x0, c[2 * k]);
+            x1 = std::max(x1, c[2 * k]);
+        }
+        xr[2 * p] = x0;
+        xr[2 * p + 1] = x1;
+        double a = std::min(py[2 * p], py[2 * p + 1]), b = std::max(py[2 * p], py[2 * p + 1]);
+        if (p == 0 || a < ylo) ylo = a;
+        if (p == 0 || b > yhi) yhi = b;
+    }
+    // about two pieces per bucket, fewer buckets while tall pieces would make
+    // the index exceed 2^26 entries
+    int nb = (int)std::min<int64_t>(std::max<int64_t>(np / 2, 1), 1 << 22);
+    double span = yhi - ylo;
+    double inv_h = 0.0;
+    std::vector<int32_t> b0(npa), b1(npa);
+    for (;;) {
+        inv_h = span > 0.0 ? (double)nb / span : 0.0;
+        int64_t total = 0;
+        for (int64_t p = 0; p < np; p++) {
+            // bucket range of every piece, in the chain precision (the device map)
+            double a = std::min(py[2 * p], py[2 * p + 1]), b = std::max(py[2 * p], py[2 * p + 1]);
+            int lo, hi;
+            if (dtype == GWN_F64) {
+                lo = bucket_of<double>(a, ylo, inv_h, nb);
+                hi = bucket_of<double>(b, ylo, inv_h, nb);
+            } else {
+                lo = bucket_of<float>((float)a, (float)ylo, (float)inv_h, nb);
+                hi = bucket_of<float>((float)b, (float)ylo, (float)inv_h, nb);
+            }
+            b0[p] = std::max(lo - 1, 0);
+            b1[p] = std::min(hi + 1, nb - 1);
+            total += b1[p] - b0[p] + 1;
+        }
+        if (total <= (int64_t(1) << 26) || nb == 1) break;
+        nb = std::max(nb / 4, 1);
+    }
+    cs.n_buckets = nb;
+    cs.bucket_y0 = ylo;
+    cs.bucket_inv_h = inv_h;
+    std::vector<int32_t> cnt(nb + 1, 0);
+    for (int64_t p = 0; p < np; p++)
+        for (int k = b0[p]; k <= b1[p]; k++) cnt[k + 1]++;
+    for (int k = 0; k < nb; k++) cnt[k + 1] += cnt[k];
+    std::vector<int32_t> idx(std::max<int32_t>(cnt[nb], 1));
+    std::vector<int32_t> fill(cnt.begin(), cnt.end() - 1);
+    for (int64_t p = 0; p < np; p++)
+        for (int k = b0[p]; k <= b1[p]; k++) idx[fill[k]++] = (int32_t)p;
+    size_t esz = dtype == GWN_F64 ? 8 : 4;
+    std::vector<char> xt(esz * 2 * npa);
+    for (size_t i = 0; i < 2 * npa; i++) {
+        if (dtype == GWN_F64) ((double *)xt.data())[i] = xr[i];
+        else ((float *)xt.data())[i] = (float)xr[i];
+    }
+    // float32 chains: a conservative x-range after rounding (round outward)
+    if (dtype == GWN_F32)
+        for (size_t p = 0; p < npa; p++) {
+            float *f = (float *)xt.data();
+            f[2 * p] = nextafterf(f[2 * p], -INFINITY);
+            f[2 * p + 1] = nextafterf(f[2 * p + 1], INFINITY);
+        }
+    cudaError_t e = cudaMalloc(&cs.piece_xT, xt.size());
+    if (e == cudaSuccess) e = cudaMemcpy(cs.piece_xT, xt.data(), xt.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&cs.bucket_off, sizeof(int32_t) * (nb + 1));
+    if (e == cudaSuccess) e = cudaMemcpy(cs.bucket_off, cnt.data(), sizeof(int32_t) * (nb + 1), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&cs.bucket_idx, sizeof(int32_t) * idx.size());
+    if (e == cudaSuccess) e = cudaMemcpy(cs.bucket_idx, idx.data(), sizeof(int32_t) * idx.size(), cudaMemcpyHostToDevice);
+    return e;
+}
+
+}  // namespace
+
+extern "C" {
 
 GWN_API gwn_status gwn_bezier2d_create(gwn_ctx *ctx, const void *ctrl, int dtype, const int64_t *chain_offsets,
                                        int64_t n_chains, int mem_kind, gwn_geom **out) {
@@ -595,10 +738,12 @@ GWN_API gwn_status gwn_bezier2d_create(gwn_ctx *ctx, const void *ctrl, int dtype
         if (e == cudaSuccess) e = cudaMemcpy(cs.piece_uT, fu.data(), sizeof(float) * 2 * np, cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemcpy(cs.piece_yT, fy.data(), sizeof(float) * 2 * np, cudaMemcpyHostToDevice);
     }
+    if (e == cudaSuccess) e = build_point_index(cs, P, pseg, py, dtype);
     if (e != cudaSuccess) {
         free_geom_device(g.get());
         return cuda_fail(e, "gwn_bezier2d_create");
     }
+    ctx_ref(ctx);
     *out = g.release();
     return GWN_OK;
 }
@@ -814,7 +959,13 @@ GWN_API gwn_status gwn_eval(gwn_geom *g, const gwn_queries *q, const float *d, v
         int32_t *defer = (int32_t *)arena_get(ctx, 4, sizeof(int32_t) * nq, &e);
         if (!defer) return cuda_fail(e, "deferred-query list");
         if (stats) CK(cudaEventRecord(ctx->ev[1], ctx->stream), "event");
-        e = launch_traverse(g->bvh, src, chi, defer, ctx->d_defer_count, ctx->d_tpairs, ctx->d_tpair_count,
+        int32_t *lines = nullptr;
+        size_t lbytes = traverse_lines_bytes(g->bvh, src);
+        if (lbytes) {
+            lines = (int32_t *)arena_get(ctx, 5, lbytes, &e);
+            if (!lines) return cuda_fail(e, "per-line crossing lists");
+        }
+        e = launch_traverse(g->bvh, src, chi, defer, ctx->d_defer_count, ctx->d_tpairs, ctx->d_tpair_count, lines,
                             stats ? ctx->d_cnt : nullptr, ctx->d_status, ctx->sm_count, ctx->stream);
         if (e != cudaSuccess) return cuda_fail(e, "crossing traversal");
         if (stats) CK(cudaEventRecord(ctx->ev[2], ctx->stream), "event");
@@ -830,12 +981,21 @@ GWN_API gwn_status gwn_eval(gwn_geom *g, const gwn_queries *q, const float *d, v
         gwn_status s = check_queries(q, 2);
         if (s != GWN_OK) return s;
         if (d && !(d[0] > 0.f && d[1] == 0.f)) { set_error("gwn_eval: 2D chains use the +x ray only"); return GWN_E_UNSUPPORTED; }
-        if (q->kind != GWN_QUERY_GRID) { set_error("gwn_eval: 2D evaluation takes grid queries"); return GWN_E_UNSUPPORTED; }
         int64_t nq = query_count(q);
-        if (nq > 0 && !w_out) { set_error("gwn_eval: w_out is NULL"); return GWN_E_INVALID; }
+        if (nq > 0 && !w_out && !chi_out && !b_out) { set_error("gwn_eval: no output requested"); return GWN_E_INVALID; }
         QuerySrc src;
         s = make_query_src(ctx, q, g->dtype, src);
         if (s != GWN_OK) return s;
+        if (q->kind == GWN_QUERY_POINTS) {                 // one ray per query
+            if (stats) {
+                CK(cudaMemsetAsync(ctx->d_cnt, 0, sizeof(unsigned long long) * CNT_NUM, ctx->stream), "clear counters");
+                for (int k = 0; k < 3; k++) CK(cudaEventRecord(ctx->ev[k], ctx->stream), "event");
+            }
+            CK(launch_eval2d_points(g->cs, src, w_out, chi_out, b_out, stats ? ctx->d_cnt : nullptr, ctx->d_status,
+                                    ctx->stream), "2D point evaluation");
+            if (stats) CK(cudaEventRecord(ctx->ev[3], ctx->stream), "event");
+            return read_stats(ctx, stats, nq, 0, false);
+        }
         if (stats) {
             CK(cudaMemsetAsync(ctx->d_cnt, 0, sizeof(unsigned long long) * CNT_NUM, ctx->stream), "clear counters");
             CK(cudaEventRecord(ctx->ev[0], ctx->stream), "event");

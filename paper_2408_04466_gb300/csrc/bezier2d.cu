@@ -204,6 +204,99 @@ __device__ __forceinline__ void store_w(const Set2D &S, int64_t row, int64_t i, 
     if (b_out) b_out[o] = term;
 }
 
+// per-warp difference-array stride: the grid width rounded up to 256 columns
+__host__ __device__ constexpr int eval2d_dstride(int max_nx) { return (max_nx + 255) & ~255; }
+
+// The queries of one grid row, by one warp.  The row's nk crossings (x, dir)
+// are binned by column: crossing k lies to the right of the queries
+// i < j_k (j_k = first column with x >= x_k), so D[j_k - 1] += dir_k and
+//   chi(i) = sum_{j >= i} D[j].
+// Lane l takes 8 consecutive columns of every 256: local suffix sums in
+// registers, one warp suffix scan of the lane totals per 256 columns, the
+// chunks taken from the right so the carry is known.  Then the chord term
+// is added and w stored (two 16-byte stores per lane when aligned).
+template <typename T>
+__device__ __forceinline__ void row_queries(const Set2D &S, const T *__restrict__ ctrl,
+                                            const int64_t *__restrict__ chain_off, const T *__restrict__ ax,
+                                            int nx, T a0, T inv_step, const T *xs, const signed char *dirs, int nk,
+                                            T yr, int64_t row, int *D, int lane, T *w_out, int32_t *chi_out,
+                                            T *b_out) {
+    const unsigned FULL = 0xffffffffu;
+    const int nxp = eval2d_dstride(nx);
+    for (int c0 = 0; c0 < nxp; c0 += 256) {
+        int4 *d4 = (int4 *)(D + c0 + 8 * lane);
+        d4[0] = make_int4(0, 0, 0, 0);
+        d4[1] = make_int4(0, 0, 0, 0);
+    }
+    __syncwarp();
+    for (int k = lane; k < nk; k += 32) {
+        int j = lower_bound_cols(ax, nx, a0, inv_step, xs[k]);
+        if (j > 0) atomicAdd(&D[j - 1], (int)dirs[k]);
+    }
+    __syncwarp();
+    // chord of a single-chain set: end points and row constants hoisted
+    const bool one = S.c_hi - S.c_lo == 1;
+    T spx = T(0), sy = T(0), epx = T(0), ey = T(0);
+    bool crosses = false, up = false;
+    if (one) {
+        const T *sp = ctrl + 2 * chain_off[S.c_lo];
+        const T *ep = ctrl + 2 * (chain_off[S.c_lo + 1] - 1);
+        spx = sp[0]; sy = sp[1] - yr; epx = ep[0]; ey = ep[1] - yr;
+        const T lo = ey < sy ? ey : sy, hi = ey < sy ? sy : ey;
+        crosses = lo <= T(0) && T(0) < hi;
+        up = sy > ey;
+    }
+    const int64_t obase = S.out_off + row * S.nx;
+    int carry = 0;
+    for (int c0 = nxp - 256; c0 >= 0; c0 -= 256) {
+        const int i0 = c0 + 8 * lane;
+        const int4 da = *(const int4 *)(D + i0), db = *(const int4 *)(D + i0 + 4);
+        int t[8];
+        t[7] = db.w; t[6] = db.z + t[7]; t[5] = db.y + t[6]; t[4] = db.x + t[5];
+        t[3] = da.w + t[4]; t[2] = da.z + t[3]; t[1] = da.y + t[2]; t[0] = da.x + t[1];
+        int x = t[0];
+        for (int off = 1; off < 32; off <<= 1) {
+            int y = __shfl_down_sync(FULL, x, off);
+            if (lane + off < 32) x += y;
+        }
+        const int before = carry + x - t[0];        // crossings right of this lane's 8 columns
+        carry += __shfl_sync(FULL, x, 0);
+        if (i0 >= nx) continue;
+        T out[8];
+#pragma unroll
+        for (int m = 0; m < 8; m++) {
+            const int i = i0 + m;
+            if (i < nx) {
+                int chi = before + t[m];
+                T xq = ax[i], term;
+                if (one) {
+                    T sx = spx - xq, ex = epx - xq;
+                    T cr = ex * sy - ey * sx;                 // cross(e - p, s - p)
+                    if (crosses && (up ? (cr > T(0)) : (cr < T(0)))) chi += up ? 1 : -1;
+                    term = Chord<T>::atan2_(-cr, sx * ex + sy * ey) * Num<T>::inv2pi;
+                } else {
+                    term = chord_terms<T>(ctrl, chain_off, S, xq, yr, chi);
+                }
+                out[m] = (T)chi + term;
+                if (b_out) b_out[obase + i] = term;
+                if (chi_out) chi_out[obase + i] = chi;
+            }
+        }
+        if (w_out) {
+            T *wp = w_out + obase + i0;
+            if (sizeof(T) == 4 && i0 + 8 <= nx && ((uintptr_t)wp & 15) == 0) {
+                ((float4 *)wp)[0] = make_float4((float)out[0], (float)out[1], (float)out[2], (float)out[3]);
+                ((float4 *)wp)[1] = make_float4((float)out[4], (float)out[5], (float)out[6], (float)out[7]);
+            } else {
+#pragma unroll
+                for (int m = 0; m < 8; m++)
+                    if (i0 + m < nx) wp[m] = out[m];
+            }
+        }
+    }
+    __syncwarp();
+}
+
 // Work items are (set, block of rows).  An item finds the rows each of the
 // set's pieces crosses: a piece with end values y0, y1 is crossed by row r
 // iff min <= y_r < max, and since the row values are non-decreasing those
@@ -334,52 +427,11 @@ __global__ void eval2d_kernel(const T *__restrict__ ctrl, const int64_t *__restr
                 }
                 __syncthreads();
                 // queries: one warp per row
-                int *D = s_D + warp * (max_nx + 1);
-                for (int r = sb0 + warp; r < sb1; r += nwarps) {
-                    for (int j = lane; j <= nx; j += 32) D[j] = 0;
-                    __syncwarp();
-                    for (int k = roff[r] - base + lane; k < roff[r + 1] - base; k += 32)
-                        atomicAdd(&D[lower_bound_cols(ax, nx, a0, inv_step, xs[k])], (int)dirs[k]);
-                    __syncwarp();
-                    int carry = 0;                            // suffix sums, from the top chunk down
-                    for (int cb = (nx / 32) * 32; cb >= 0; cb -= 32) {
-                        int j = cb + lane;
-                        int x = j <= nx ? D[j] : 0;
-                        for (int off = 1; off < 32; off <<= 1) {
-                            int t = __shfl_down_sync(FULL, x, off);
-                            if (lane + off < 32) x += t;
-                        }
-                        x += carry;
-                        if (j <= nx) D[j] = x;
-                        carry = __shfl_sync(FULL, x, 0);
-                    }
-                    __syncwarp();
-                    const T yr = ys[r];
-                    if (S.c_hi - S.c_lo == 1) {
-                        // one chain: its chord's end points and row-constant parts hoisted
-                        const T *sp = ctrl + 2 * chain_off[S.c_lo];
-                        const T *ep = ctrl + 2 * (chain_off[S.c_lo + 1] - 1);
-                        const T spx = sp[0], sy = sp[1] - yr, epx = ep[0], ey = ep[1] - yr;
-                        const T lo = ey < sy ? ey : sy, hi = ey < sy ? sy : ey;
-                        const bool crosses = lo <= T(0) && T(0) < hi, up = sy > ey;
-                        for (int i = lane; i < nx; i += 32) {
-                            T xq = ax[i];
-                            T sx = spx - xq, ex = epx - xq;
-                            T cr = ex * sy - ey * sx;         // cross(e - p, s - p)
-                            int chi = D[i + 1];
-                            if (crosses && (up ? (cr > T(0)) : (cr < T(0)))) chi += up ? 1 : -1;
-                            T term = Chord<T>::atan2_(-cr, sx * ex + sy * ey) * Num<T>::inv2pi;
-                            store_w<T>(S, r0 + r, i, chi, term, w_out, chi_out, b_out);
-                        }
-                    } else {
-                        for (int i = lane; i < nx; i += 32) {
-                            int chi = D[i + 1];
-                            T term = chord_terms<T>(ctrl, chain_off, S, ax[i], yr, chi);
-                            store_w<T>(S, r0 + r, i, chi, term, w_out, chi_out, b_out);
-                        }
-                    }
-                    __syncwarp();
-                }
+                int *D = s_D + warp * eval2d_dstride(max_nx);
+                for (int r = sb0 + warp; r < sb1; r += nwarps)
+                    row_queries<T>(S, ctrl, chain_off, ax, nx, a0, inv_step, xs + roff[r] - base,
+                                   dirs + roff[r] - base, roff[r + 1] - roff[r], ys[r], r0 + r, D, lane, w_out,
+                                   chi_out, b_out);
                 __syncthreads();
             } else {
                 // fallback for row sb0 (more than CAP crossings): CHUNK crossings per pass
@@ -432,7 +484,7 @@ __global__ void eval2d_kernel(const T *__restrict__ ctrl, const int64_t *__restr
 
 size_t eval2d_smem(int dtype, int64_t max_nx, int threads) {
     size_t off = dtype == GWN_F64 ? eval2d_fallback_off<double>() : eval2d_fallback_off<float>();
-    size_t per_warp = sizeof(int) * (size_t)(max_nx + 1);
+    size_t per_warp = sizeof(int) * (size_t)eval2d_dstride((int)max_nx);
     size_t d = per_warp * (size_t)(threads / 32);
     return off + (d > sizeof(int) * (size_t)max_nx ? d : sizeof(int) * (size_t)max_nx);
 }
@@ -474,6 +526,82 @@ cudaError_t launch_eval2d_items(const ChainSet &cs, const Set2D *d_sets, const i
             (const float *)cs.piece_yT, d_sets, d_items, s0, n_items, d_counter, rows_per_item, (float *)w_out,
             chi_out, (float *)b_out, cnt, status, (int)max_nx);
     }
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Point queries (no ray reuse): one +x ray per query.  The query's y picks a
+// bucket of the y-bucket index; for each listed piece the exact half-open
+// y-test decides whether the ray's line crosses it, and the piece's
+// conservative x-range decides most crossings outright (entirely right of the
+// query: counted; entirely left: not); only a piece whose x-range straddles
+// the query needs its root.  Then the chord terms of every chain.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ int bucket_of_dev(T y, T y0, T inv_h, int nb) {
+    T v = (y - y0) * inv_h;
+    if (!(v >= T(0))) return 0;
+    if (v >= T(nb)) return nb - 1;
+    int b = (int)v;
+    return b < nb ? b : nb - 1;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) eval2d_points_kernel(
+    const T *__restrict__ ctrl, const int64_t *__restrict__ chain_off, int64_t n_chains,
+    const int64_t *__restrict__ piece_seg, const T *__restrict__ piece_u, const T *__restrict__ piece_y,
+    const T *__restrict__ piece_x, const int32_t *__restrict__ bucket_off, const int32_t *__restrict__ bucket_idx,
+    int nb, T y0, T inv_h, const T *__restrict__ pts, int64_t n, T *__restrict__ w_out, int32_t *__restrict__ chi_out,
+    T *__restrict__ b_out, unsigned long long *cnt, int *status) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const T px = pts[2 * i], py = pts[2 * i + 1];
+    const int b = bucket_of_dev<T>(py, y0, inv_h, nb);
+    int chi = 0, nroots = 0;
+    for (int j = bucket_off[b]; j < bucket_off[b + 1]; j++) {
+        const int p = bucket_idx[j];
+        const T ya = piece_y[2 * p], yb = piece_y[2 * p + 1];
+        const T lo = ya < yb ? ya : yb, hi = ya < yb ? yb : ya;
+        if (!(lo <= py && py < hi)) continue;
+        const int dir = yb > ya ? 1 : -1;
+        if (px < piece_x[2 * p]) { chi += dir; continue; }      // crossing certainly to the right
+        if (px >= piece_x[2 * p + 1]) continue;                 // certainly not to the right
+        const T *cp = ctrl + 2 * piece_seg[p];
+        T c[8];
+#pragma unroll
+        for (int k = 0; k < 8; k++) c[k] = cp[k];
+        int iters;
+        T x = piece_root_x<T>(c, piece_u[2 * p], piece_u[2 * p + 1], ya, yb, py, &iters);
+        if (iters >= Num<T>::max_iter && status) atomicOr(status, ST_TIMEOUT);
+        if (x > px) chi += dir;
+        nroots++;
+    }
+    if (cnt && nroots) atomicAdd(&cnt[CNT_ROOTS], (unsigned long long)nroots);
+    Set2D S;
+    S.c_lo = 0;
+    S.c_hi = n_chains;
+    const T term = chord_terms<T>(ctrl, chain_off, S, px, py, chi);
+    if (w_out) w_out[i] = (T)chi + term;
+    if (chi_out) chi_out[i] = chi;
+    if (b_out) b_out[i] = term;
+}
+
+cudaError_t launch_eval2d_points(const ChainSet &cs, const QuerySrc &q, void *w_out, int32_t *chi_out, void *b_out,
+                                 unsigned long long *cnt, int *status, cudaStream_t st) {
+    if (q.n == 0) return cudaSuccess;
+    int64_t blocks = (q.n + 255) / 256;
+    if (blocks > 0x7fffffff) return cudaErrorInvalidValue;
+    if (cs.dtype == GWN_F64)
+        eval2d_points_kernel<double><<<(unsigned)blocks, 256, 0, st>>>(
+            (const double *)cs.ctrl, cs.chain_off, cs.n_chains, cs.piece_seg, (const double *)cs.piece_uT,
+            (const double *)cs.piece_yT, (const double *)cs.piece_xT, cs.bucket_off, cs.bucket_idx, cs.n_buckets,
+            cs.bucket_y0, cs.bucket_inv_h, q.pts64, q.n, (double *)w_out, chi_out, (double *)b_out, cnt, status);
+    else
+        eval2d_points_kernel<float><<<(unsigned)blocks, 256, 0, st>>>(
+            (const float *)cs.ctrl, cs.chain_off, cs.n_chains, cs.piece_seg, (const float *)cs.piece_uT,
+            (const float *)cs.piece_yT, (const float *)cs.piece_xT, cs.bucket_off, cs.bucket_idx, cs.n_buckets,
+            (float)cs.bucket_y0, (float)cs.bucket_inv_h, q.pts, q.n, (float *)w_out, chi_out, (float *)b_out, cnt,
+            status);
     return cudaGetLastError();
 }
 

@@ -94,6 +94,13 @@ struct ChainSet {
     double *piece_y = nullptr;     // [n_pieces][2] (y at u0, y at u1)
     void *piece_uT = nullptr;      // piece_u in the chain dtype (aliases piece_u for float64)
     void *piece_yT = nullptr;      // piece_y in the chain dtype (aliases piece_y for float64)
+    // point queries: the pieces' conservative x ranges (control hull of their
+    // segment, chain dtype, [n_pieces][2]) and a y-bucket index of the pieces
+    void *piece_xT = nullptr;
+    int32_t *bucket_off = nullptr;     // [n_buckets + 1]
+    int32_t *bucket_idx = nullptr;     // piece indices, bucket by bucket
+    int32_t n_buckets = 0;
+    double bucket_y0 = 0.0, bucket_inv_h = 0.0;   // bucket(y) = floor((y - y0) * inv_h), in the chain dtype
     int32_t *piece_chain = nullptr;
     int64_t *chain_piece_off = nullptr;  // device [n_chains + 1]
     std::vector<int64_t> h_chain_off, h_chain_piece_off;
@@ -136,10 +143,15 @@ struct gwn_ctx {
     int2 *d_tpairs = nullptr;                 // traversal: unsettled (query, triangle) pairs [GWN_TPAIR_CAP]
     unsigned long long *d_work_counter = nullptr;   // 2D work-item counter
     int32_t *d_tpair_count = nullptr;
-    gwn::Arena scratch[5];                    // 0 chi, 1 staged points, 2 2D batch, 3 host-eval w, 4 deferred list
+    gwn::Arena scratch[6];                    // 0 chi, 1 staged points, 2 2D batch, 3 host-eval w, 4 deferred list,
+                                              // 5 per-line crossing lists
     std::vector<gwn::AxisCache> axis_cache;   // most recent grids, at most 64
     cudaEvent_t ev[8];
     bool events = false;
+    // lifetime: geometries keep their context alive; gwn_ctx_destroy releases
+    // it once no geometry refers to it (guarded by a library-wide mutex)
+    int64_t geom_refs = 0;
+    bool destroy_requested = false;
 };
 
 struct gwn_geom {
@@ -183,11 +195,14 @@ void bvh_free(MeshBvh &b);
 // Crossing counts chi[q.n].  defer / defer_count: the same deferred-list
 // scratch as launch_bterm3d (used and emptied before it returns in stream
 // order, so the two may share it); pairs / pair_count: GWN_TPAIR_CAP
-// unsettled (query, triangle) pairs.
+// unsettled (query, triangle) pairs; lines: scratch of
+// traverse_lines_bytes(b, q) bytes for grid queries with d parallel to a grid
+// axis (one traversal per grid line), or NULL to traverse every query.
 #define GWN_TPAIR_CAP 65536
+size_t traverse_lines_bytes(const MeshBvh &b, const QuerySrc &q);
 cudaError_t launch_traverse(const MeshBvh &b, const QuerySrc &q, int32_t *chi, int32_t *defer,
-                            int32_t *defer_count, int2 *pairs, int32_t *pair_count, unsigned long long *cnt,
-                            int *status, int sm_count, cudaStream_t st);
+                            int32_t *defer_count, int2 *pairs, int32_t *pair_count, int32_t *lines,
+                            unsigned long long *cnt, int *status, int sm_count, cudaStream_t st);
 
 // Boundary term + epilogue (w = chi + B).  defer: int32 scratch of q.n
 // entries for the deferred-query list; defer_count: one device int32.
@@ -209,6 +224,9 @@ cudaError_t launch_bruteforce3d(const float *V, const int32_t *F, int64_t nf, co
                                 int sm_count, cudaStream_t st);
 
 // 2D
+// 2D evaluation at point queries (one +x ray per query, y-bucket index).
+cudaError_t launch_eval2d_points(const ChainSet &cs, const QuerySrc &q, void *w_out, int32_t *chi_out, void *b_out,
+                                 unsigned long long *cnt, int *status, cudaStream_t st);
 // 2D evaluation over work items: either a device work list (d_sets, d_items)
 // or one set passed by value (single, items = its row blocks).
 cudaError_t launch_eval2d_items(const ChainSet &cs, const Set2D *d_sets, const int2 *d_items, const Set2D *single,

@@ -354,6 +354,181 @@ __global__ void __launch_bounds__(256) traverse_packet_kernel(const BvhNode *__r
     }
 }
 
+// Ray reuse for grid queries when d is parallel to grid axis k: every
+// query on a grid line along k shares the ray line (the "Optimization" of
+// the one-shot algorithm, in 3D).  For an edge AB,
+//   det[A-p, B-p, d] = d_k ((A x B)_k + ((B-A) x p)_k)
+// does not depend on p_k, so the edge signs, hence which triangles the line
+// crosses and with which sign, are the same for every query on the line.
+// traverse_lines_kernel: one thread per line traverses once from the line's
+// first query (the one farthest back along d) and stores the crossed
+// triangles, GWN_LINE_MAX per line: the crossing's coordinate along axis k
+// (float64 plane intersection, stored as float) with a conservative band,
+// and (triangle << 2 | code), code 0: +1, 1: -1, 2: an exactly zero edge
+// determinant (the perturbed tie-break depends on p_k, so each query settles
+// that pair on its own); a count of -1 marks a line with more crossings, -2 a
+// failed traversal.
+// lines_count_kernel: one thread per query counts the stored crossings in
+// front of it: a query outside a crossing's band compares coordinates; one
+// inside it takes the orientation of the query against the triangle (float32
+// filter on edge vectors, then float64 and exact).
+#define GWN_LINE_MAX 24
+#define GWN_LINE_REC (1 + 3 * GWN_LINE_MAX)   // ints per line record
+__global__ void __launch_bounds__(128) traverse_lines_kernel(const BvhNode *__restrict__ nodes,
+                                                             const float4 *__restrict__ tris, int root, Frame fr,
+                                                             TravParams tp, QuerySrc q, int k,
+                                                             int32_t *__restrict__ lines, unsigned long long *cnt,
+                                                             int *status) {
+    const int ia = k == 0 ? 1 : 0, ib = k == 2 ? 1 : 2;           // the other two axes
+    const int64_t na = q.dims[ia], nb = q.dims[ib], nk = q.dims[k];
+    const int64_t line = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (line >= na * nb) return;
+    const int64_t stride[3] = {1, q.dims[0], q.dims[0] * q.dims[1]};
+    const int64_t base = (line % na) * stride[ia] + (line / na) * stride[ib];
+    const float3 D = make_float3(fr.d[0], fr.d[1], fr.d[2]);
+    const int64_t m_first = comp(D, k) > 0.f ? 0 : nk - 1;      // farthest back along d
+    const float3 p = query_point3(q, base + m_first * stride[k]);
+    float p1 = fmaf(p.z, fr.e1[2], fmaf(p.y, fr.e1[1], p.x * fr.e1[0]));
+    float p2 = fmaf(p.z, fr.e2[2], fmaf(p.y, fr.e2[1], p.x * fr.e2[0]));
+    float p3 = fmaf(p.z, fr.dh[2], fmaf(p.y, fr.dh[1], p.x * fr.dh[0]));
+    float pad = fmaf(tp.pad_rel, fabsf(p.x) + fabsf(p.y) + fabsf(p.z), tp.pad_abs);
+    float xlo = p1 - pad, xhi = p1 + pad, ylo = p2 - pad, yhi = p2 + pad, zlo = p3 - pad;
+    int32_t *out = lines + line * GWN_LINE_REC;
+    int n = 0, ntests = 0;
+    bool overflow = false, bad = false;
+    int stack[GWN_STACK];
+    int sp = 0, node = root;
+    for (int64_t iter = 0;; iter++) {
+        if (iter > tp.max_iter) {
+            atomicOr(status, ST_TIMEOUT);
+            if (cnt) atomicAdd(&cnt[CNT_TIMEOUT], 1ull);
+            bad = true;
+            break;
+        }
+        if (node >= tp.n_internal || ~node >= tp.n_leaves) {
+            atomicOr(status, ST_BAD_INPUT);
+            bad = true;
+            break;
+        }
+        if (node < 0) {
+            const int t = ~node;
+            float4 a4 = __ldg(&tris[3 * t]), b4 = __ldg(&tris[3 * t + 1]), c4 = __ldg(&tris[3 * t + 2]);
+            const float3 V[3] = {make_float3(a4.x, a4.y, a4.z), make_float3(b4.x, b4.y, b4.z),
+                                 make_float3(c4.x, c4.y, c4.z)};
+            ntests++;
+            int sg[3];                                  // the line's three edge signs, exact
+#pragma unroll
+            for (int e = 0; e < 3; e++) {
+                float3 A = V[e], B = V[(e + 1) % 3];
+                float3 a = make_float3(A.x - p.x, A.y - p.y, A.z - p.z);
+                float3 E = make_float3(B.x - A.x, B.y - A.y, B.z - A.z);
+                sg[e] = edge_sign_f32(a, E, D);
+                if (sg[e] == 0) sg[e] = det_abd_sign_f64(A, B, p, D, cnt, status);
+            }
+            const bool differ = sg[0] * sg[1] < 0 || sg[1] * sg[2] < 0 || sg[0] * sg[2] < 0;
+            if (!differ) {
+                int code = (sg[0] == 0 || sg[1] == 0 || sg[2] == 0) ? 2 : (sg[0] > 0 ? 0 : 1);
+                float cT = 0.f, band = 0.f;
+                if (code != 2) {
+                    // plane of the triangle met by the line: c_T = p_k - nrm.(p - v0) / nrm_k, in float64
+                    // (differences and products of float32 values are exact there); the band covers that
+                    // rounding by a wide margin plus the rounding of c_T to float32
+                    double e1[3] = {(double)V[1].x - V[0].x, (double)V[1].y - V[0].y, (double)V[1].z - V[0].z};
+                    double e2[3] = {(double)V[2].x - V[0].x, (double)V[2].y - V[0].y, (double)V[2].z - V[0].z};
+                    double nr[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2],
+                                    e1[0] * e2[1] - e1[1] * e2[0]};
+                    double w[3] = {(double)p.x - V[0].x, (double)p.y - V[0].y, (double)p.z - V[0].z};
+                    double nk = nr[k];
+                    double num = nr[0] * w[0] + nr[1] * w[1] + nr[2] * w[2];
+                    double ct = (double)comp(p, k) - num / nk;
+                    double scale = (fabs(nr[0] * w[0]) + fabs(nr[1] * w[1]) + fabs(nr[2] * w[2])) / fabs(nk);
+                    cT = (float)ct;
+                    band = (float)(1e-6 * (fabs(ct) + scale) + 1e-30);
+                    if (!(fabs(nk) > 0.0) || !isfinite(ct)) band = INFINITY;   // no usable coordinate: exact test
+                }
+                if (n < GWN_LINE_MAX) {
+                    out[1 + 3 * n] = __float_as_int(cT);
+                    out[2 + 3 * n] = __float_as_int(band);
+                    out[3 + 3 * n] = (t << 2) | code;
+                    n++;
+                } else {
+                    overflow = true;
+                }
+            }
+            if (sp == 0) break;
+            node = stack[--sp];
+            continue;
+        }
+        const BvhNode nd = nodes[node];
+        bool h0 = box_hit(nd.lo.x, nd.lo.y, nd.lo.z, nd.lo.w, nd.z.x, xlo, xhi, ylo, yhi, zlo);
+        bool h1 = box_hit(nd.hi.x, nd.hi.y, nd.hi.z, nd.hi.w, nd.z.y, xlo, xhi, ylo, yhi, zlo);
+        int c0 = __float_as_int(nd.z.z), c1 = __float_as_int(nd.z.w);
+        if (h0 && h1) {
+            if (sp >= GWN_STACK) {
+                atomicOr(status, ST_STACK_OVERFLOW);
+                if (cnt) atomicAdd(&cnt[CNT_STACK_OVERFLOW], 1ull);
+                bad = true;
+                break;
+            }
+            stack[sp++] = c1;
+            node = c0;
+        } else if (h0) {
+            node = c0;
+        } else if (h1) {
+            node = c1;
+        } else {
+            if (sp == 0) break;
+            node = stack[--sp];
+        }
+    }
+    out[0] = bad ? -2 : (overflow ? -1 : n);
+    if (cnt) atomicAdd(&cnt[CNT_TRI_TESTS], (unsigned long long)ntests);
+}
+
+__global__ void __launch_bounds__(256) lines_count_kernel(const float4 *__restrict__ tris, Frame fr, QuerySrc q,
+                                                          int k, const int32_t *__restrict__ lines,
+                                                          int32_t *__restrict__ chi, int32_t *defer,
+                                                          int32_t *defer_count, int2 *pairs, int32_t *pair_count,
+                                                          unsigned long long *cnt, int *status) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= q.n) return;
+    const int ia = k == 0 ? 1 : 0, ib = k == 2 ? 1 : 2;
+    // grid coordinates in 32-bit arithmetic (q.n < 2^31)
+    const unsigned nx = (unsigned)q.dims[0], ny = (unsigned)q.dims[1], ui = (unsigned)idx;
+    const unsigned t = ui / nx;
+    const unsigned c[3] = {ui - t * nx, t % ny, t / ny};
+    const int64_t line = (int64_t)c[ia] + q.dims[ia] * (int64_t)c[ib];
+    const int32_t *L = lines + line * GWN_LINE_REC;
+    const int n = L[0];
+    if (n == -2) { chi[idx] = INT32_MIN; return; }
+    if (n < 0) { defer_query(defer, defer_count, idx); return; }
+    const float3 pm = query_point3(q, idx);
+    const float cm = comp(pm, k);
+    const bool fwd = fr.d[k] > 0.f;
+    int acc = 0;
+    bool whole = false;
+    for (int j = 0; j < n; j++) {
+        const int e = L[3 + 3 * j], t = e >> 2, code = e & 3;
+        if (code == 2) { defer_pair(pairs, pair_count, idx, t, whole); continue; }
+        const int s0 = code == 0 ? 1 : -1;
+        const float cT = __int_as_float(L[1 + 3 * j]), band = __int_as_float(L[2 + 3 * j]);
+        // ahead of the query along d: counted; behind: not; inside the band: orientation
+        if (fwd ? cm < cT - band : cm > cT + band) { acc += s0; continue; }
+        if (fwd ? cm > cT + band : cm < cT - band) continue;
+        float4 a4 = __ldg(&tris[3 * t]), b4 = __ldg(&tris[3 * t + 1]), c4 = __ldg(&tris[3 * t + 2]);
+        float3 v0 = make_float3(a4.x, a4.y, a4.z), v1 = make_float3(b4.x, b4.y, b4.z);
+        float3 v2 = make_float3(c4.x, c4.y, c4.z);
+        float3 a = make_float3(v0.x - pm.x, v0.y - pm.y, v0.z - pm.z);
+        float3 e0 = make_float3(v1.x - v0.x, v1.y - v0.y, v1.z - v0.z);
+        float3 e2 = make_float3(v0.x - v2.x, v0.y - v2.y, v0.z - v2.z);
+        int o = -det3_sign_f32(a, e0, e2);                   // orientation det[v0-p, v1-p, v2-p]
+        if (o == 0) o = orient_sign_f64(v0, v1, v2, pm, cnt, status);
+        if (o == s0) acc += s0;
+    }
+    if (whole) defer_query(defer, defer_count, idx);
+    else chi[idx] = acc;
+}
+
 // Root is a single leaf (one triangle) or the mesh is empty.
 __global__ void traverse_single_kernel(const float4 *__restrict__ tris, int ntri, Frame fr, QuerySrc q,
                                        int32_t *__restrict__ chi, unsigned long long *cnt, int *status) {
@@ -370,9 +545,26 @@ __global__ void traverse_single_kernel(const float4 *__restrict__ tris, int ntri
     chi[idx] = acc;
 }
 
+// grid axis parallel to d (d has exactly one nonzero component), or -1
+static int grid_axis_of(const Frame &fr) {
+    int axis = -1, nzero = 0;
+    for (int c = 0; c < 3; c++) {
+        if (fr.d[c] == 0.f) nzero++;
+        else axis = c;
+    }
+    return nzero == 2 ? axis : -1;
+}
+
+size_t traverse_lines_bytes(const MeshBvh &b, const QuerySrc &q) {
+    if (q.kind != GWN_QUERY_GRID || b.n <= 1) return 0;
+    int axis = grid_axis_of(b.frame);
+    if (axis < 0 || q.dims[axis] < 2) return 0;
+    return sizeof(int32_t) * GWN_LINE_REC * (size_t)(q.n / q.dims[axis]);
+}
+
 cudaError_t launch_traverse(const MeshBvh &b, const QuerySrc &q, int32_t *chi, int32_t *defer,
-                            int32_t *defer_count, int2 *pairs, int32_t *pair_count, unsigned long long *cnt,
-                            int *status, int sm_count, cudaStream_t st) {
+                            int32_t *defer_count, int2 *pairs, int32_t *pair_count, int32_t *lines,
+                            unsigned long long *cnt, int *status, int sm_count, cudaStream_t st) {
     if (q.n == 0) return cudaSuccess;
     if (q.n > 0x7fffffff) return cudaErrorInvalidValue;
     const int threads = 128;
@@ -404,9 +596,20 @@ cudaError_t launch_traverse(const MeshBvh &b, const QuerySrc &q, int32_t *chi, i
     cudaError_t e = cudaMemsetAsync(defer_count, 0, sizeof(int32_t), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(pair_count, 0, sizeof(int32_t), st);
     if (e != cudaSuccess) return e;
+    // d parallel to a grid axis: one traversal per grid line along it
+    const int axis = grid_axis_of(fr);
     // Grid queries come in spatially coherent warp tiles: one warp-uniform
     // stack per tile.  Scattered points take one stack per thread.
-    if (q.kind == GWN_QUERY_GRID && b.tbox && b.n < (int64_t(1) << 26))
+    if (lines && traverse_lines_bytes(b, q) > 0) {
+        int64_t nlines = q.n / q.dims[axis];
+        traverse_lines_kernel<<<(unsigned)((nlines + 127) / 128), 128, 0, st>>>(b.nodes, b.tris, b.root, b.frame,
+                                                                                 tp, q, axis, lines, cnt, status);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        lines_count_kernel<<<(unsigned)((q.n + 255) / 256), 256, 0, st>>>(b.tris, b.frame, q, axis, lines, chi,
+                                                                           defer, defer_count, pairs, pair_count,
+                                                                           cnt, status);
+    } else if (q.kind == GWN_QUERY_GRID && b.tbox && b.n < (int64_t(1) << 26))
         traverse_packet_kernel<<<(unsigned)tblocks, 256, 0, st>>>(b.nodes, b.tris, b.tbox, b.root, b.frame, tp, q,
                                                                   chi, defer, defer_count, pairs, pair_count, cnt,
                                                                   status);

@@ -125,8 +125,8 @@ def test_errors_2d(gwn, ctx):
     c = gen.bezier_circle_chain(grid_n=8)
     ch = gwn.Bezier2D(ctx, c.ctrl, c.offsets)
     import torch
-    with pytest.raises(gwn.GwnError):
-        q = gwn.Points(torch.zeros((4, 2), dtype=torch.float64, device="cuda"))
+    with pytest.raises(gwn.GwnError):       # float32 points for a float64 chain
+        q = gwn.Points(torch.zeros((4, 2), dtype=torch.float32, device="cuda"))
         w = torch.empty(4, dtype=torch.float64, device="cuda")
         import ctypes as C
         gwn._capi.check(ch.lib.gwn_eval(ch.h, C.byref(q.to_c()), None, w.data_ptr(), None, None, None), "eval")
@@ -192,3 +192,52 @@ def test_binned_rows_overflow_fallback(gwn, ctx, n, dims):
     r = ch.eval(grid, want_chi=True)
     assert np.array_equal(r["chi"].cpu().numpy()[keep], chic[keep])
     assert np.array_equal(r["w"].cpu().numpy(), w_bin)
+
+
+def test_point_queries(gwn, ctx):
+    """One +x ray per query point (no ray reuse): crossing counts exact and
+    w against the oracle's closed form, float64 and float32 chains; grid
+    points given as points agree with the grid path away from the curve."""
+    import torch
+    c = gen.bezier_circle_chain()
+    ch = gwn.Bezier2D(ctx, c.ctrl, c.offsets)
+    rng = np.random.default_rng(21)
+    P = rng.uniform(-1.5, 1.5, (6000, 2))
+    # points on rows through control points and through piece end values
+    P[:200, 1] = c.ctrl[rng.integers(0, len(c.ctrl), 200), 1]
+    r = ch.eval(gwn.Points(torch.as_tensor(P).cuda()), want_chi=True)
+    w = r["w"].cpu().numpy()
+    chi = r["chi"].cpu().numpy()
+    wc, chic = oracle.w2d_closed_x(c.ctrl, P)
+    keep = oracle.dist2d(c.ctrl, P) > 1e-9
+    assert np.array_equal(chi[keep], chic[keep])
+    assert np.abs(w - wc)[keep].max() < 1e-12
+    # host points
+    wh = ch.eval(gwn.Points(torch.as_tensor(P))).cpu().numpy()
+    assert np.array_equal(wh, w)
+    # grid points as points vs the grid path
+    g = c.grids[0]
+    Pg = gen.grid_points(g, np.float64)
+    wg = ch.eval(_grid(gwn, g)).cpu().numpy()
+    wp = ch.eval(gwn.Points(torch.as_tensor(Pg).cuda())).cpu().numpy()
+    far = oracle.dist2d(c.ctrl, Pg) > 1e-6
+    assert np.abs(wg - wp)[far].max() < 1e-13
+    # float32, several chains (w sums over the chains)
+    cs = gen.star_chains(n_chains=3, seg_hi=300, grid_n=20, seed=9)
+    st = gwn.Bezier2D(ctx, cs.ctrl, cs.offsets)
+    Q = rng.uniform(-1.6, 1.6, (8000, 2)).astype(np.float32)
+    r = st.eval(gwn.Points(torch.as_tensor(Q).cuda()), want_chi=True)
+    w32 = r["w"].cpu().numpy().astype(np.float64)
+    tot = np.zeros(len(Q))
+    tchi = np.zeros(len(Q), np.int64)
+    keep = np.ones(len(Q), bool)
+    for k in range(3):
+        ctrl = cs.ctrl[cs.offsets[k]:cs.offsets[k + 1]].astype(np.float64)
+        wk, ck = oracle.w2d_closed_x(ctrl, Q.astype(np.float64))
+        tot += wk
+        tchi += ck
+        keep &= oracle.dist2d(ctrl, Q.astype(np.float64)) > 1e-4 * math.hypot(3.2, 3.2)
+    assert np.array_equal(r["chi"].cpu().numpy()[keep], tchi[keep])
+    assert np.abs(w32 - tot)[keep].max() <= 1e-6
+    # no points
+    assert st.eval(gwn.Points(torch.zeros((0, 2), device="cuda"))).numel() == 0

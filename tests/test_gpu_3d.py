@@ -290,3 +290,26 @@ def test_degenerate_rays_overflow_pair_list(gwn, ctx):
     torch.cuda.synchronize()
     ctx.check()
     assert np.array_equal(rp["chi"].cpu().numpy(), r["chi"].cpu().numpy())
+
+
+def test_axis_direction_line_reuse(gwn, ctx):
+    """d parallel to a grid axis: one traversal per grid line serves all its
+    queries.  Crossing counts on every query and w on a sample must match the
+    oracle for each axis and both senses."""
+    import torch
+    m = gen.icosphere_cap(subdiv=3, seed=5)
+    mesh = gwn.Mesh(ctx, m.V, m.F)
+    g = gen.Grid((-1.2, -1.1, -1.3), (1.2, 1.25, 1.15), (40, 36, 32))
+    grid = gwn.Grid(g.lo, g.hi, g.dims)
+    P = gen.grid_points(g)
+    rng = np.random.default_rng(11)
+    sub = np.sort(rng.choice(len(P), 1500, replace=False))
+    for d in ([0, 0, 1], [0, 0, -1], [1, 0, 0], [0, -1, 0]):
+        d = np.array(d, np.float32)
+        r = mesh.eval(grid, d, want_chi=True, want_b=True)
+        torch.cuda.synchronize()
+        ctx.check()
+        chio = oracle.chi3d(m.V, m.F, P, d)
+        assert np.array_equal(r["chi"].cpu().numpy(), chio), (d, int((r["chi"].cpu().numpy() != chio).sum()))
+        rr = {k: r[k].cpu().numpy()[sub] for k in ("w", "chi", "b")}
+        _check(m.V, m.F, P[sub], d, rr)
