@@ -433,6 +433,8 @@ def run_other(args):
             _, _, bst = geo.eval_batch(bq, out=w, stats=True)
             out["graph_launch_ms"] = bst["ms_total"]        # events around the graph launch alone
             out["autotuned_ms"] = bst["ms_prepare"]         # best candidate during autotuning
+            out["roots"] = bst["n_tri_tests"]               # row crossings found, all chains
+            out["newton_iters_per_root"] = bst["n_root_iters"] / max(1, bst["n_tri_tests"])
         # brute-force comparator (per-segment quadrature) on one chain's grid
         c0 = int(np.argmax(np.diff(ch.offsets))) if name == "star_chains" else 0
         ctrl0 = ch.ctrl[ch.offsets[c0]:ch.offsets[c0 + 1]]

@@ -118,6 +118,7 @@ typedef struct gwn_stats {
     int64_t n_deferred_traverse;  /* (query, triangle) pairs the float32 filter left unsettled, settled with the
                                      full predicates (plus any query recounted whole when the pair list is full) */
     int64_t n_deferred_boundary;  /* queries whose boundary term was recomputed by the careful pass */
+    int64_t n_root_iters;         /* 2D: safeguarded Newton steps over all roots (n_tri_tests counts the roots) */
 } gwn_stats;
 
 /* Geometry summary. */

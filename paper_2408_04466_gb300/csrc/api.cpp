@@ -911,6 +911,7 @@ static gwn_status read_stats(gwn_ctx *ctx, gwn_stats *st, int64_t nq, int64_t pa
     st->n_tri_tests = (int64_t)(c[CNT_TRI_TESTS] + c[CNT_ROOTS]);
     st->n_deferred_traverse = (int64_t)c[CNT_DEFER_TRAV];
     st->n_deferred_boundary = (int64_t)c[CNT_DEFER_BTERM];
+    st->n_root_iters = (int64_t)c[CNT_NEWTON];
     float a = 0, b = 0, t = 0, p = 0;
     cudaEventElapsedTime(&a, ctx->ev[1], ctx->ev[2]);
     cudaEventElapsedTime(&b, ctx->ev[2], ctx->ev[3]);

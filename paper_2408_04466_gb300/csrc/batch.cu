@@ -64,7 +64,11 @@ gwn_status eval2d_single(gwn_geom *g, const QuerySrc &src, void *w_out, int32_t 
     // one set, passed by value; its items are its row blocks (no work list to
     // upload, no host synchronisation)
     int64_t n_items = (S.ny + rows - 1) / rows;
-    cudaError_t e = launch_eval2d_items(cs, nullptr, nullptr, &S, n_items, ctx->d_work_counter, rows, 128, S.nx,
+    // four warps per block, fewer on wide grids (each warp keeps a row-wide
+    // difference array in shared memory)
+    int threads = 128;
+    while (threads > 32 && eval2d_smem(cs.dtype, S.nx, threads) > EVAL2D_SMEM_MAX) threads -= 32;
+    cudaError_t e = launch_eval2d_items(cs, nullptr, nullptr, &S, n_items, ctx->d_work_counter, rows, threads, S.nx,
                                         w_out, chi_out, b_out, cnt, ctx->d_status, ctx->sm_count, ctx->stream);
     if (e != cudaSuccess) return cuda_fail(e, "2D evaluation");
     return GWN_OK;
@@ -217,6 +221,24 @@ extern "C" GWN_API gwn_status gwn_eval_batch(gwn_geom *g, const gwn_queries *que
                 for (int r : rs)
                     if ((!want_threads || t == want_threads) && (!want_rows || r == want_rows)) cands.emplace_back(t, r);
         }
+        // shapes whose shared memory does not fit are dropped; wide grids get
+        // as many warps as fit
+        int64_t mx = 0;
+        for (int64_t c = 0; c < n_chains; c++) mx = std::max<int64_t>(mx, queries[c].dims[0]);
+        std::vector<std::pair<int, int>> fit;
+        for (auto &cd : cands)
+            if (eval2d_smem(g->cs.dtype, mx, cd.first) <= EVAL2D_SMEM_MAX) fit.push_back(cd);
+        if (fit.empty()) {
+            if (want_threads) {
+                set_error("gwn_eval_batch: threads_per_block too large for the grid width (shared memory)");
+                delete P;
+                return GWN_E_INVALID;
+            }
+            int t = 128;
+            while (t > 32 && eval2d_smem(g->cs.dtype, mx, t) > EVAL2D_SMEM_MAX) t -= 32;
+            for (auto &cd : cands) fit.emplace_back(t, cd.second);
+        }
+        cands = fit;
         float best = 1e30f;
         int bt = cands[0].first, br = cands[0].second;
         cudaEvent_t e0, e1;
@@ -294,6 +316,18 @@ extern "C" GWN_API gwn_status gwn_eval_batch(gwn_geom *g, const gwn_queries *que
         stats->ms_boundary = ms;
         stats->ms_total = ms;
         stats->ms_prepare = P->tuned_ms;
+        // one more launch, outside the timing, with the root counters on
+        e = cudaMemsetAsync(ctx->d_cnt, 0, sizeof(unsigned long long) * CNT_NUM, ctx->stream);
+        if (e == cudaSuccess)
+            e = launch_eval2d_items(g->cs, P->d_sets, P->d_items, nullptr, P->n_items, P->d_counter, P->rows,
+                                    P->threads, P->max_nx, w_out, nullptr, nullptr, ctx->d_cnt, ctx->d_status,
+                                    ctx->sm_count, ctx->stream);
+        unsigned long long c[CNT_NUM];
+        if (e == cudaSuccess) e = cudaMemcpyAsync(c, ctx->d_cnt, sizeof(c), cudaMemcpyDeviceToHost, ctx->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "batched counters");
+        stats->n_tri_tests = (int64_t)c[CNT_ROOTS];
+        stats->n_root_iters = (int64_t)c[CNT_NEWTON];
     }
     return GWN_OK;
 }

@@ -108,13 +108,16 @@ __device__ T piece_root_xu(const T *c, T u0, T u1, T ya, T yb, T yr, int *iters_
 
 constexpr int CHUNK = 1024;          // crossings per pass of the per-row fallback
 constexpr int MAX_ROWS = 256;        // rows per work item
-constexpr int CAP = 8192;            // crossings binned per work item
+constexpr int CAP = 4096;            // crossings binned per row sub-block
 
-// shared-memory layout: xs[CAP] (T), ys[MAX_ROWS] (T), roff[MAX_ROWS + 1],
-// rcur[MAX_ROWS] (int), dirs[CAP] (int8), then the fallback's chi_row
+// Shared-memory layout of eval2d_kernel (threads = block size):
+//   xs[CAP] (T), ys[MAX_ROWS] (T), roff[MAX_ROWS + 1], rcur[MAX_ROWS + 1],
+//   ofs[threads], ra[threads], wsum[32] (int), dirs[CAP] (int8), then per warp
+//   the difference array of row_queries (or the fallback's chi_row).
 template <typename T>
-__host__ __device__ constexpr size_t eval2d_fallback_off() {
-    return ((sizeof(T) * (CAP + MAX_ROWS) + sizeof(int) * (2 * MAX_ROWS + 1) + CAP) + 15) & ~(size_t)15;
+__host__ __device__ constexpr size_t eval2d_fallback_off(int threads) {
+    return ((sizeof(T) * (CAP + MAX_ROWS) + sizeof(int) * (2 * (MAX_ROWS + 1) + 2 * threads + 32) + CAP) + 15) &
+           ~(size_t)15;
 }
 
 // Fast float32 atan2 for the chord term (half-angle form: v = y/(|z| + |x|)
@@ -300,10 +303,16 @@ __device__ __forceinline__ void row_queries(const Set2D &S, const T *__restrict_
 // Work items are (set, block of rows).  An item finds the rows each of the
 // set's pieces crosses: a piece with end values y0, y1 is crossed by row r
 // iff min <= y_r < max, and since the row values are non-decreasing those
-// rows form one range, found by binary search in the item's row values.
-// Crossings are binned by row in shared memory (a counting pass, a prefix
-// sum, a filling pass that finds each root), so the work is proportional to
-// the pieces plus the crossings rather than to rows x pieces.
+// rows form one range [ra, rb), found by binary search in the item's row
+// values.  The per-row crossing counts come from a difference array (+1 at
+// ra, -1 at rb) and one scan, so the counting pass costs O(1) per piece
+// whatever the number of rows it spans.
+//
+// Roots: the (piece, row) pairs of a chunk of blockDim pieces are numbered
+// by a block-wide prefix sum of the pieces' row counts, and every thread
+// takes every blockDim-th pair (its owner piece found by binary search in the
+// prefix sums), so a piece spanning many rows is spread over many threads
+// instead of serialising one.  Each root is binned by row in shared memory.
 //
 // Queries: one warp per row.  Every crossing x_k of the row finds its column
 // j_k = first grid column with x >= x_k and adds its direction to a per-warp
@@ -315,7 +324,7 @@ __device__ __forceinline__ void row_queries(const Set2D &S, const T *__restrict_
 // single row with more than CAP crossings falls back to scanning the pieces
 // CHUNK crossings at a time.
 template <typename T>
-__global__ void eval2d_kernel(const T *__restrict__ ctrl, const int64_t *__restrict__ chain_off,
+__global__ void __launch_bounds__(1024) eval2d_kernel(const T *__restrict__ ctrl, const int64_t *__restrict__ chain_off,
                               const int64_t *__restrict__ piece_seg, const T *__restrict__ piece_u,
                               const T *__restrict__ piece_y, const Set2D *__restrict__ sets,
                               const int2 *__restrict__ items, const Set2D single, int64_t n_items,
@@ -323,16 +332,21 @@ __global__ void eval2d_kernel(const T *__restrict__ ctrl, const int64_t *__restr
                               int32_t *__restrict__ chi_out, T *__restrict__ b_out, unsigned long long *cnt,
                               int *status, int max_nx) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int nthr = blockDim.x;
     T *xs = (T *)smem_raw;                                    // CAP crossings
     T *ys = xs + CAP;                                         // MAX_ROWS row values
     int *roff = (int *)(ys + MAX_ROWS);                       // MAX_ROWS + 1 offsets
-    int *rcur = roff + MAX_ROWS + 1;                          // MAX_ROWS counts / cursors
-    signed char *dirs = (signed char *)(rcur + MAX_ROWS);     // CAP directions
-    int *s_D = (int *)(smem_raw + eval2d_fallback_off<T>());   // per warp: max_nx + 1 (fallback: chi_row)
+    int *rcur = roff + MAX_ROWS + 1;                          // MAX_ROWS + 1: difference array, then cursors
+    int *s_ofs = rcur + MAX_ROWS + 1;                         // per thread: first pair of its piece
+    int *s_ra = s_ofs + nthr;                                 // per thread: first row of its piece
+    int *s_wsum = s_ra + nthr;                                // per warp: pairs of its pieces
+    signed char *dirs = (signed char *)(s_wsum + 32);         // CAP directions
+    int *s_D = (int *)(smem_raw + eval2d_fallback_off<T>(nthr));   // per warp: max_nx + 1 (fallback: chi_row)
     const unsigned FULL = 0xffffffffu;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = nthr >> 5;
     __shared__ int ncross;
     __shared__ long long item_sh;
+    unsigned long long nroots_thread = 0;
     for (int64_t guard = 0; guard <= n_items; guard++) {
         if (threadIdx.x == 0) item_sh = (long long)atomicAdd(counter, 1ull);
         __syncthreads();
@@ -348,36 +362,44 @@ __global__ void eval2d_kernel(const T *__restrict__ ctrl, const int64_t *__restr
         int64_t r0 = (int64_t)it.y * rows_per_item;
         int64_t r1 = r0 + rows_per_item < S.ny ? r0 + rows_per_item : S.ny;
         const int nr = (int)(r1 - r0);
-        for (int i = threadIdx.x; i < nr; i += blockDim.x) {
-            ys[i] = ay[r0 + i];
+        for (int i = threadIdx.x; i <= nr; i += nthr) {
+            if (i < nr) ys[i] = ay[r0 + i];
             rcur[i] = 0;
         }
         __syncthreads();
-        // pass 1: crossings per row
-        for (int64_t p = S.p_lo + threadIdx.x; p < S.p_hi; p += blockDim.x) {
+        // pass 1: crossings per row, by a difference array over the rows
+        for (int64_t p = S.p_lo + threadIdx.x; p < S.p_hi; p += nthr) {
             T ya = piece_y[2 * p], yb = piece_y[2 * p + 1];
             T lo = ya < yb ? ya : yb, hi = ya < yb ? yb : ya;
             int ra = lower_bound_rows(ys, nr, lo), rb = lower_bound_rows(ys, nr, hi);
-            for (int r = ra; r < rb; r++) atomicAdd(&rcur[r], 1);
+            if (ra < rb) {
+                atomicAdd(&rcur[ra], 1);
+                atomicAdd(&rcur[rb], -1);
+            }
         }
         __syncthreads();
-        if (warp == 0) {                                      // exclusive prefix sum over the rows
-            int carry = 0;
+        if (warp == 0) {               // counts = scan of the differences; offsets = exclusive scan of the counts
+            int c1 = 0, c2 = 0;
             for (int base = 0; base < nr; base += 32) {
-                int r = base + lane;
-                int v = r < nr ? rcur[r] : 0, x = v;
+                const int r = base + lane;
+                int x = r < nr ? rcur[r] : 0;
                 for (int off = 1; off < 32; off <<= 1) {
                     int t = __shfl_up_sync(FULL, x, off);
                     if (lane >= off) x += t;
                 }
-                if (r < nr) roff[r] = carry + x - v;
-                carry += __shfl_sync(FULL, x, 31);
+                const int cr = r < nr ? c1 + x : 0;        // crossings of row r
+                c1 += __shfl_sync(FULL, x, 31);
+                int y = cr;
+                for (int off = 1; off < 32; off <<= 1) {
+                    int t = __shfl_up_sync(FULL, y, off);
+                    if (lane >= off) y += t;
+                }
+                if (r < nr) roff[r] = c2 + y - cr;
+                c2 += __shfl_sync(FULL, y, 31);
             }
-            if (lane == 0) roff[nr] = carry;
+            if (lane == 0) roff[nr] = c2;
         }
         __syncthreads();
-        const int total = roff[nr];
-        if (cnt && threadIdx.x == 0) atomicAdd(&cnt[CNT_ROOTS], (unsigned long long)total);
         const T a0 = ax[0];
         const T inv_step = nx > 1 ? T(nx - 1) / (ax[nx - 1] - ax[0]) : T(0);
         // rows in sub-blocks whose crossings fit in CAP (a single row with more
@@ -394,35 +416,60 @@ __global__ void eval2d_kernel(const T *__restrict__ ctrl, const int64_t *__restr
             const bool fits = roff[sb1] - roff[sb0] <= CAP;
             if (fits) {
                 const int base = roff[sb0];
-                for (int i = sb0 + threadIdx.x; i < sb1; i += blockDim.x) rcur[i] = 0;
-                __syncthreads();
-                // pass 2: the roots of rows [sb0, sb1), binned by row
-                for (int64_t p = S.p_lo + threadIdx.x; p < S.p_hi; p += blockDim.x) {
-                    T ya = piece_y[2 * p], yb = piece_y[2 * p + 1];
-                    T lo = ya < yb ? ya : yb, hi = ya < yb ? yb : ya;
-                    int ra = lower_bound_rows(ys, nr, lo), rb = lower_bound_rows(ys, nr, hi);
-                    if (ra < sb0) ra = sb0;
-                    if (rb > sb1) rb = sb1;
-                    if (ra >= rb) continue;
-                    const T *cp = ctrl + 2 * piece_seg[p];
-                    T c[8];
+                for (int i = sb0 + threadIdx.x; i < sb1; i += nthr) rcur[i] = 0;
+                // pass 2: the roots of rows [sb0, sb1), binned by row, over
+                // chunks of nthr pieces with the (piece, row) pairs spread
+                // evenly over the threads
+                for (int64_t pc = S.p_lo; pc < S.p_hi; pc += nthr) {
+                    const int64_t p = pc + threadIdx.x;
+                    int ra = 0, n = 0;
+                    if (p < S.p_hi) {
+                        T ya = piece_y[2 * p], yb = piece_y[2 * p + 1];
+                        T lo = ya < yb ? ya : yb, hi = ya < yb ? yb : ya;
+                        ra = lower_bound_rows(ys, nr, lo);
+                        int rb = lower_bound_rows(ys, nr, hi);
+                        if (ra < sb0) ra = sb0;
+                        if (rb > sb1) rb = sb1;
+                        n = rb > ra ? rb - ra : 0;
+                    }
+                    int x = n;
+                    for (int off = 1; off < 32; off <<= 1) {
+                        int t = __shfl_up_sync(FULL, x, off);
+                        if (lane >= off) x += t;
+                    }
+                    __syncthreads();                 // the previous chunk is done with s_wsum, s_ofs, s_ra
+                    if (lane == 31) s_wsum[warp] = x;
+                    __syncthreads();
+                    int before = 0, tot = 0;
+                    for (int w = 0; w < nwarps; w++) {
+                        const int sw = s_wsum[w];
+                        before += w < warp ? sw : 0;
+                        tot += sw;
+                    }
+                    if (tot == 0) continue;           // uniform over the block
+                    s_ofs[threadIdx.x] = before + x - n;
+                    s_ra[threadIdx.x] = ra;
+                    __syncthreads();
+                    for (int k = threadIdx.x; k < tot; k += nthr) {
+                        int lo = 0, hi = nthr - 1;       // owner: last thread with s_ofs <= k
+                        while (lo < hi) {
+                            const int mid = (lo + hi + 1) >> 1;
+                            if (s_ofs[mid] <= k) lo = mid; else hi = mid - 1;
+                        }
+                        const int64_t q = pc + lo;
+                        const int r = s_ra[lo] + (k - s_ofs[lo]);
+                        const T ya = piece_y[2 * q], yb = piece_y[2 * q + 1];
+                        const T *cp = ctrl + 2 * piece_seg[q];
+                        T c[8];
 #pragma unroll
-                    for (int k = 0; k < 8; k++) c[k] = cp[k];
-                    T u0 = piece_u[2 * p], u1 = piece_u[2 * p + 1];
-                    signed char dir = yb > ya ? 1 : -1;
-                    // rows ascend and the piece is monotone in y, so each root
-                    // brackets the next: the remaining part of the piece runs
-                    // from the last root (at the last row's y) to the far end
-                    T ua = u0, ub = u1, yla = ya, ylb = yb;
-                    for (int r = ra; r < rb; r++) {
+                        for (int m = 0; m < 8; m++) c[m] = cp[m];
                         int iters;
-                        T u;
-                        T x = piece_root_xu<T>(c, ua, ub, yla, ylb, ys[r], &iters, &u);
+                        const T xr = piece_root_x<T>(c, piece_u[2 * q], piece_u[2 * q + 1], ya, yb, ys[r], &iters);
                         if (iters >= Num<T>::max_iter && status) atomicOr(status, ST_TIMEOUT);
-                        if (dir > 0) { ua = u; yla = ys[r]; } else { ub = u; ylb = ys[r]; }
-                        int slot = roff[r] - base + atomicAdd(&rcur[r], 1);
-                        xs[slot] = x;
-                        dirs[slot] = dir;
+                        nroots_thread += (unsigned long long)iters << 32 | 1ull;
+                        const int slot = roff[r] - base + atomicAdd(&rcur[r], 1);
+                        xs[slot] = xr;
+                        dirs[slot] = yb > ya ? 1 : -1;
                     }
                 }
                 __syncthreads();
@@ -438,12 +485,12 @@ __global__ void eval2d_kernel(const T *__restrict__ ctrl, const int64_t *__restr
                 int *chi_row = s_D;
                 const int r = sb0;
                 const T yr = ys[r];
-                for (int64_t i = threadIdx.x; i < S.nx; i += blockDim.x) chi_row[i] = 0;
+                for (int64_t i = threadIdx.x; i < S.nx; i += nthr) chi_row[i] = 0;
                 for (int64_t c0 = S.p_lo; c0 < S.p_hi; c0 += CHUNK) {
                     if (threadIdx.x == 0) ncross = 0;
                     __syncthreads();
                     int64_t c1 = c0 + CHUNK < S.p_hi ? c0 + CHUNK : S.p_hi;
-                    for (int64_t p = c0 + threadIdx.x; p < c1; p += blockDim.x) {
+                    for (int64_t p = c0 + threadIdx.x; p < c1; p += nthr) {
                         T ya = piece_y[2 * p], yb = piece_y[2 * p + 1];
                         T lo = ya < yb ? ya : yb, hi = ya < yb ? yb : ya;
                         if (!(lo <= yr && yr < hi)) continue;
@@ -454,13 +501,14 @@ __global__ void eval2d_kernel(const T *__restrict__ ctrl, const int64_t *__restr
                         int iters;
                         T x = piece_root_x<T>(c, piece_u[2 * p], piece_u[2 * p + 1], ya, yb, yr, &iters);
                         if (iters >= Num<T>::max_iter && status) atomicOr(status, ST_TIMEOUT);
+                        nroots_thread += (unsigned long long)iters << 32 | 1ull;
                         int slot = atomicAdd(&ncross, 1);
                         xs[slot] = x;
                         dirs[slot] = yb > ya ? 1 : -1;
                     }
                     __syncthreads();
                     int nc = ncross;
-                    for (int64_t i = threadIdx.x; i < S.nx; i += blockDim.x) {
+                    for (int64_t i = threadIdx.x; i < S.nx; i += nthr) {
                         T xq = ax[i];
                         int acc = 0;
                         for (int k = 0; k < nc; k++) acc += xs[k] > xq ? (int)dirs[k] : 0;
@@ -468,7 +516,7 @@ __global__ void eval2d_kernel(const T *__restrict__ ctrl, const int64_t *__restr
                     }
                     __syncthreads();
                 }
-                for (int64_t i = threadIdx.x; i < S.nx; i += blockDim.x) {
+                for (int64_t i = threadIdx.x; i < S.nx; i += nthr) {
                     int chi = chi_row[i];
                     T term = chord_terms<T>(ctrl, chain_off, S, ax[i], yr, chi);
                     store_w<T>(S, r0 + r, i, chi, term, w_out, chi_out, b_out);
@@ -480,10 +528,14 @@ __global__ void eval2d_kernel(const T *__restrict__ ctrl, const int64_t *__restr
         }
         __syncthreads();
     }
+    if (cnt && nroots_thread) {
+        atomicAdd(&cnt[CNT_ROOTS], nroots_thread & 0xffffffffull);
+        atomicAdd(&cnt[CNT_NEWTON], nroots_thread >> 32);
+    }
 }
 
 size_t eval2d_smem(int dtype, int64_t max_nx, int threads) {
-    size_t off = dtype == GWN_F64 ? eval2d_fallback_off<double>() : eval2d_fallback_off<float>();
+    size_t off = dtype == GWN_F64 ? eval2d_fallback_off<double>(threads) : eval2d_fallback_off<float>(threads);
     size_t per_warp = sizeof(int) * (size_t)eval2d_dstride((int)max_nx);
     size_t d = per_warp * (size_t)(threads / 32);
     return off + (d > sizeof(int) * (size_t)max_nx ? d : sizeof(int) * (size_t)max_nx);

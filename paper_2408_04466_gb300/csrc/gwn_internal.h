@@ -22,6 +22,7 @@ enum {
     CNT_TIMEOUT = 7,
     CNT_DEFER_TRAV = 8,
     CNT_DEFER_BTERM = 9,
+    CNT_NEWTON = 10,         // 2D: root iterations (Newton or bisection steps)
     CNT_NUM = 16
 };
 
@@ -229,6 +230,10 @@ cudaError_t launch_eval2d_points(const ChainSet &cs, const QuerySrc &q, void *w_
                                  unsigned long long *cnt, int *status, cudaStream_t st);
 // 2D evaluation over work items: either a device work list (d_sets, d_items)
 // or one set passed by value (single, items = its row blocks).
+// shared memory of eval2d_kernel for a block of `threads` on grids up to
+// max_nx columns, and the most one block may take (sm_103a opt-in limit)
+size_t eval2d_smem(int dtype, int64_t max_nx, int threads);
+constexpr size_t EVAL2D_SMEM_MAX = 227 * 1024;
 cudaError_t launch_eval2d_items(const ChainSet &cs, const Set2D *d_sets, const int2 *d_items, const Set2D *single,
                                 int64_t n_items,
                                 unsigned long long *d_counter, int rows_per_item, int threads, int64_t max_nx,
