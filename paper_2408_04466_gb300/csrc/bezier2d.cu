@@ -44,16 +44,25 @@ template <typename T> struct Num;
 // (2.7 iterations per root on average on the star chains); float64 keeps
 // 1e-16.
 template <> struct Num<float> {
-    static __device__ __forceinline__ float atan2_(float y, float x) { return atan2f(y, x); }
     static constexpr float inv2pi = 0.15915494309189535f;
     static constexpr int max_iter = 60;
     static constexpr float tol = 1e-6f;
+    // Newton quotients: an approximate quotient (2 ulp) only perturbs the
+    // iterates; the stopping test on the step decides the accuracy
+    static __device__ __forceinline__ float div(float a, float b) { return __fdividef(a, b); }
+    // a product and a sum the compiler may not fuse (every path rounds alike)
+    static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+    static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+    static __device__ __forceinline__ float fma_(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 };
 template <> struct Num<double> {
-    static __device__ __forceinline__ double atan2_(double y, double x) { return atan2(y, x); }
     static constexpr double inv2pi = 0.15915494309189533577;
     static constexpr int max_iter = 200;
     static constexpr double tol = 1e-16;
+    static __device__ __forceinline__ double div(double a, double b) { return a / b; }
+    static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+    static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+    static __device__ __forceinline__ double fma_(double a, double b, double c) { return __fma_rn(a, b, c); }
 };
 
 template <typename T>
@@ -86,14 +95,14 @@ __device__ T piece_root_xu(const T *c, T u0, T u1, T ya, T yb, T yr, int *iters_
     bool inc = yb > ya;
     if (!inc) { lo = u1; hi = u0; }
     T yl = inc ? ya : yb, yh = inc ? yb : ya;
-    T u = lo + (hi - lo) * ((yr - yl) / (yh - yl));
+    T u = lo + (hi - lo) * Num<T>::div(yr - yl, yh - yl);
     int it = 0;
     for (; it < Num<T>::max_iter; it++) {
         T g = bern(c[1], c[3], c[5], c[7], u) - yr;
         if (g == T(0)) break;                       // exact root (a zero Newton step would fall to bisection)
         if (g < T(0)) lo = u; else hi = u;
         T dg = dbern(c[1], c[3], c[5], c[7], u);
-        T un = u - g / dg;
+        T un = u - Num<T>::div(g, dg);
         T mn = lo < hi ? lo : hi, mx = lo < hi ? hi : lo;
         if (!(un > mn && un < mx)) un = T(0.5) * (lo + hi);
         T step = un - u;
@@ -111,55 +120,123 @@ constexpr int MAX_ROWS = 256;        // rows per work item
 constexpr int CAP = 4096;            // crossings binned per row sub-block
 
 // Shared-memory layout of eval2d_kernel (threads = block size):
-//   xs[CAP] (T), ys[MAX_ROWS] (T), roff[MAX_ROWS + 1], rcur[MAX_ROWS + 1],
-//   ofs[threads], ra[threads], wsum[32] (int), dirs[CAP] (int8), then per warp
-//   the difference array of row_queries (or the fallback's chi_row).
+//   xs[CAP], ys[MAX_ROWS], pc[PC_FIELDS * threads] (T: crossings, row values,
+//   the staged data of each thread's piece), roff[MAX_ROWS + 1],
+//   rcur[MAX_ROWS + 1], ofs[threads], ra[threads], wsum[32] (int),
+//   dirs[CAP] (int8), then per warp the difference array of the row queries
+//   (or the fallback's chi_row).
+constexpr int PC_FIELDS = 12;        // control points (8), u0, u1, y(u0), y(u1)
 template <typename T>
 __host__ __device__ constexpr size_t eval2d_fallback_off(int threads) {
-    return ((sizeof(T) * (CAP + MAX_ROWS) + sizeof(int) * (2 * (MAX_ROWS + 1) + 2 * threads + 32) + CAP) + 15) &
-           ~(size_t)15;
+    return ((sizeof(T) * (CAP + MAX_ROWS + (size_t)PC_FIELDS * threads) +
+             sizeof(int) * (2 * (MAX_ROWS + 1) + 2 * threads + 32) + CAP) + 15) & ~(size_t)15;
 }
 
-// Fast float32 atan2 for the chord term (half-angle form: v = y/(|z| + |x|)
-// in [-1, 1], atan2 = 2 atan(v) or copysign(pi, y) - 2 atan(v) for x < 0;
-// atan(v) = v P(v^2) with the degree-8 odd minimax polynomial of the 3D
-// boundary term, relative error 1.5e-8; MUFU rsqrt and reciprocal, ~2 ulp).
-__device__ __forceinline__ float atan2_fast(float y, float x) {
-    float z2 = fmaf(x, x, y * y);
-    if (!(z2 > 1e-37f)) return 0.f;
-    float rz;
-    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(rz) : "f"(z2));
-    float d = fmaf(z2, rz, fabsf(x)), rd;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rd) : "f"(d));
-    float v = y * rd, v2 = v * v;
-    float q = fmaf(0.00284989f, v2, -0.01606863f);
-    q = fmaf(q, v2, 0.04269152f);
-    q = fmaf(q, v2, -0.07504295f);
-    q = fmaf(q, v2, 0.10640934f);
-    q = fmaf(q, v2, -0.14203644f);
-    q = fmaf(q, v2, 0.19992619f);
-    q = fmaf(q, v2, -0.33333073f);
-    q = fmaf(q, v2, 0.99999998f);
-    float a2 = 2.f * (q * v);
-    return x >= 0.f ? a2 : copysignf(3.14159265358979f, y) - a2;
+// Chord term arithmetic.  For the chord from s to e seen from p = (xq, yr),
+// with sy = s.y - yr, ey = e.y - yr (per row) and sx = s.x - xq, ex = e.x - xq:
+//   cr = cross(e - p, s - p) = ex sy - ey sx,   dt = dot(s - p, e - p),
+// and the term is atan2(-cr, dt) / 2 pi.  Every path (scalar, and the packed
+// float32 path of the row queries) evaluates these with the same fused
+// operations in the same order, so they round alike and agree bit for bit.
+template <typename T>
+__device__ __forceinline__ void chord_cd(T spx, T sy, T epx, T ney, T syey, T xq, T &cr, T &dt) {
+    const T sx = Num<T>::add(spx, -xq), ex = Num<T>::add(epx, -xq);
+    cr = Num<T>::fma_(ex, sy, Num<T>::mul(sx, ney));
+    dt = Num<T>::fma_(sx, ex, syey);
 }
+
+// Degree-8 odd minimax polynomial of the 3D boundary term: atan(v) ~ v P(v^2)
+// on [-1, 1], relative error 1.5e-8.
+#define GWN_ATC8 0.00284989f
+#define GWN_ATC7 -0.01606863f
+#define GWN_ATC6 0.04269152f
+#define GWN_ATC5 -0.07504295f
+#define GWN_ATC4 0.10640934f
+#define GWN_ATC3 -0.14203644f
+#define GWN_ATC2 0.19992619f
+#define GWN_ATC1 -0.33333073f
+#define GWN_ATC0 0.99999998f
+#define GWN_PI_F 3.14159265358979f
+
+// atan2(-cr, dt) in float32 by the half-angle form: with v = -cr/(|z| + |dt|)
+// in [-1, 1] (|z|^2 = cr^2 + dt^2), atan2 = 2 atan(v) for dt >= 0 and
+// copysign(pi, -cr) - 2 atan(v) otherwise; MUFU rsqrt and reciprocal (~2 ulp).
+// Written with u = cr/(|z| + |dt|) = -v.
+__device__ __forceinline__ float frsqrt_(float x) {
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float frcp_(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float chord_angle(float cr, float dt) {
+    const float z2 = __fmaf_rn(dt, dt, __fmul_rn(cr, cr));
+    if (!(z2 > 1e-37f)) return 0.f;
+    const float d = __fmaf_rn(z2, frsqrt_(z2), fabsf(dt));
+    const float u = __fmul_rn(cr, frcp_(d)), u2 = __fmul_rn(u, u);
+    float q = __fmaf_rn(GWN_ATC8, u2, GWN_ATC7);
+    q = __fmaf_rn(q, u2, GWN_ATC6);
+    q = __fmaf_rn(q, u2, GWN_ATC5);
+    q = __fmaf_rn(q, u2, GWN_ATC4);
+    q = __fmaf_rn(q, u2, GWN_ATC3);
+    q = __fmaf_rn(q, u2, GWN_ATC2);
+    q = __fmaf_rn(q, u2, GWN_ATC1);
+    q = __fmaf_rn(q, u2, GWN_ATC0);
+    const float a2n = __fmul_rn(2.f, __fmul_rn(q, u));     // -2 atan(v)
+    return dt >= 0.f ? -a2n : __fadd_rn(copysignf(GWN_PI_F, -cr), a2n);
+}
+
+// two chord angles at once: the same operations as chord_angle, the
+// add/mul/fma ones as packed f32x2 (fma.rn/mul.rn per element)
+__device__ __forceinline__ float2 chord_angle2(float2 cr, float2 dt) {
+    const float2 z2 = __ffma2_rn(dt, dt, __fmul2_rn(cr, cr));
+    const float2 ad = make_float2(fabsf(dt.x), fabsf(dt.y));
+    const float2 d = __ffma2_rn(z2, make_float2(frsqrt_(z2.x), frsqrt_(z2.y)), ad);
+    const float2 u = __fmul2_rn(cr, make_float2(frcp_(d.x), frcp_(d.y)));
+    const float2 u2 = __fmul2_rn(u, u);
+    float2 q = __ffma2_rn(make_float2(GWN_ATC8, GWN_ATC8), u2, make_float2(GWN_ATC7, GWN_ATC7));
+    q = __ffma2_rn(q, u2, make_float2(GWN_ATC6, GWN_ATC6));
+    q = __ffma2_rn(q, u2, make_float2(GWN_ATC5, GWN_ATC5));
+    q = __ffma2_rn(q, u2, make_float2(GWN_ATC4, GWN_ATC4));
+    q = __ffma2_rn(q, u2, make_float2(GWN_ATC3, GWN_ATC3));
+    q = __ffma2_rn(q, u2, make_float2(GWN_ATC2, GWN_ATC2));
+    q = __ffma2_rn(q, u2, make_float2(GWN_ATC1, GWN_ATC1));
+    q = __ffma2_rn(q, u2, make_float2(GWN_ATC0, GWN_ATC0));
+    const float2 a2n = __fmul2_rn(make_float2(2.f, 2.f), __fmul2_rn(q, u));
+    float2 r;
+    r.x = dt.x >= 0.f ? -a2n.x : __fadd_rn(copysignf(GWN_PI_F, -cr.x), a2n.x);
+    r.y = dt.y >= 0.f ? -a2n.y : __fadd_rn(copysignf(GWN_PI_F, -cr.y), a2n.y);
+    r.x = z2.x > 1e-37f ? r.x : 0.f;
+    r.y = z2.y > 1e-37f ? r.y : 0.f;
+    return r;
+}
+
 template <typename T> struct Chord;
 template <> struct Chord<float> {
-    static __device__ __forceinline__ float atan2_(float y, float x) { return atan2_fast(y, x); }
+    static __device__ __forceinline__ float angle(float cr, float dt) { return chord_angle(cr, dt); }
 };
 template <> struct Chord<double> {
-    static __device__ __forceinline__ double atan2_(double y, double x) { return atan2(y, x); }
+    static __device__ __forceinline__ double angle(double cr, double dt) { return atan2(-cr, dt); }
 };
 
-// first index i in [0, n) with ys[i] >= v (n if none); ys non-decreasing
+// first row i in [0, n) with ys[i] >= v (n if none), on the item's rows (a
+// run of a grid axis: non-decreasing, spaced ~uniformly, y0 = ys[0], inv_h =
+// (n - 1) / (ys[n-1] - ys[0])): a guess from the spacing, corrected against
+// the stored values, so the result is exactly the lower bound
 template <typename T>
-__device__ __forceinline__ int lower_bound_rows(const T *ys, int n, T v) {
-    int lo = 0, hi = n;
-    while (lo < hi) {
-        int mid = (lo + hi) >> 1;
-        if (ys[mid] < v) lo = mid + 1; else hi = mid;
-    }
-    return lo;
+__device__ __forceinline__ int lower_bound_rows_grid(const T *ys, int n, T y0, T inv_h, T v) {
+    if (!(v > y0)) return 0;
+    if (!(v <= ys[n - 1])) return n;
+    // here ys[0] < v <= ys[n-1], so the bound lies in [1, n-1]
+    T g = (v - y0) * inv_h;
+    int j = g >= T(n - 1) ? n - 1 : (int)ceil(g);
+    if (j < 1) j = 1;
+    while (j > 1 && ys[j - 1] >= v) j--;
+    while (ys[j] < v) j++;
+    return j;
 }
 
 // first column j in [0, nx] with ax[j] >= x, on a grid axis (non-decreasing,
@@ -176,35 +253,42 @@ __device__ __forceinline__ int lower_bound_cols(const T *__restrict__ ax, int nx
     return j;
 }
 
-// chord terms of the set's chains at (xq, yr): the chord's crossing with the
-// +x ray (half-open in y) and minus the angle it subtends, / 2 pi
+// chord terms of the set's chains at (xq, yr): each chord's crossing with the
+// +x ray (half-open in y) is added to chi; returns the sum A of the angles
+// atan2(-cr, dt) (w = chi + A / 2 pi)
 template <typename T>
-__device__ __forceinline__ T chord_terms(const T *__restrict__ ctrl, const int64_t *__restrict__ chain_off,
+__device__ __forceinline__ T chord_angles(const T *__restrict__ ctrl, const int64_t *__restrict__ chain_off,
                                          const Set2D &S, T xq, T yr, int &chi) {
-    T term = T(0);
+    T A = T(0);
     for (int64_t c = S.c_lo; c < S.c_hi; c++) {
         const T *sp = ctrl + 2 * chain_off[c];
         const T *ep = ctrl + 2 * (chain_off[c + 1] - 1);
-        T sx = sp[0] - xq, sy = sp[1] - yr, ex = ep[0] - xq, ey = ep[1] - yr;
-        T cr = ex * sy - ey * sx;             // cross(e - p, s - p)
+        const T sy = sp[1] - yr, ey = ep[1] - yr;
+        T cr, dt;
+        chord_cd<T>(sp[0], sy, ep[0], -ey, sy * ey, xq, cr, dt);
         T lo = ey < sy ? ey : sy, hi = ey < sy ? sy : ey;
         if (lo <= T(0) && T(0) < hi) {
             bool up = sy > ey;
             bool right = up ? (cr > T(0)) : (cr < T(0));
             if (right) chi += up ? 1 : -1;
         }
-        term += Chord<T>::atan2_(-cr, sx * ex + sy * ey) * Num<T>::inv2pi;
+        A = Num<T>::add(A, Chord<T>::angle(cr, dt));
     }
-    return term;
+    return A;
 }
 
+// w = chi + A / 2 pi, formed as one fused multiply-add on every path;
+// b = A / 2 pi
 template <typename T>
-__device__ __forceinline__ void store_w(const Set2D &S, int64_t row, int64_t i, int chi, T term, T *w_out,
+__device__ __forceinline__ T w_of(int chi, T A) { return Num<T>::fma_(A, Num<T>::inv2pi, (T)chi); }
+
+template <typename T>
+__device__ __forceinline__ void store_w(const Set2D &S, int64_t row, int64_t i, int chi, T A, T *w_out,
                                         int32_t *chi_out, T *b_out) {
     int64_t o = S.out_off + row * S.nx + i;
-    if (w_out) w_out[o] = (T)chi + term;
+    if (w_out) w_out[o] = w_of<T>(chi, A);
     if (chi_out) chi_out[o] = chi;
-    if (b_out) b_out[o] = term;
+    if (b_out) b_out[o] = Num<T>::mul(A, Num<T>::inv2pi);
 }
 
 // per-warp difference-array stride: the grid width rounded up to 256 columns
@@ -271,17 +355,17 @@ __device__ __forceinline__ void row_queries(const Set2D &S, const T *__restrict_
             const int i = i0 + m;
             if (i < nx) {
                 int chi = before + t[m];
-                T xq = ax[i], term;
+                T xq = ax[i], A;
                 if (one) {
-                    T sx = spx - xq, ex = epx - xq;
-                    T cr = ex * sy - ey * sx;                 // cross(e - p, s - p)
+                    T cr, dt;
+                    chord_cd<T>(spx, sy, epx, -ey, sy * ey, xq, cr, dt);
                     if (crosses && (up ? (cr > T(0)) : (cr < T(0)))) chi += up ? 1 : -1;
-                    term = Chord<T>::atan2_(-cr, sx * ex + sy * ey) * Num<T>::inv2pi;
+                    A = Chord<T>::angle(cr, dt);
                 } else {
-                    term = chord_terms<T>(ctrl, chain_off, S, xq, yr, chi);
+                    A = chord_angles<T>(ctrl, chain_off, S, xq, yr, chi);
                 }
-                out[m] = (T)chi + term;
-                if (b_out) b_out[obase + i] = term;
+                out[m] = w_of<T>(chi, A);
+                if (b_out) b_out[obase + i] = Num<T>::mul(A, Num<T>::inv2pi);
                 if (chi_out) chi_out[obase + i] = chi;
             }
         }
@@ -295,6 +379,89 @@ __device__ __forceinline__ void row_queries(const Set2D &S, const T *__restrict_
                 for (int m = 0; m < 8; m++)
                     if (i0 + m < nx) wp[m] = out[m];
             }
+        }
+    }
+    __syncwarp();
+}
+
+// The row queries on the float32 fast path (a set of one chain, w only): the
+// same steps as row_queries, with the difference array and the counts kept
+// as floats (exact: a row holds at most CAP crossings) and the chord terms of
+// two columns at a time in packed f32x2 arithmetic.  Rounds exactly as the
+// generic path does.  (spx, spy), (epx, epy): the chain's end points.
+__device__ __forceinline__ void row_queries_f32(const float *__restrict__ ax, int nx, float a0, float inv_step,
+                                                const float *xs, const signed char *dirs, int nk, float yr,
+                                                float spx, float spy, float epx, float epy,
+                                                float *__restrict__ wrow, float *D, int lane) {
+    const unsigned FULL = 0xffffffffu;
+    const int nxp = eval2d_dstride(nx);
+    for (int c0 = 0; c0 < nxp; c0 += 256) {
+        float4 *d4 = (float4 *)(D + c0 + 8 * lane);
+        d4[0] = make_float4(0.f, 0.f, 0.f, 0.f);
+        d4[1] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    __syncwarp();
+    for (int k = lane; k < nk; k += 32) {
+        int j = lower_bound_cols(ax, nx, a0, inv_step, xs[k]);
+        if (j > 0) atomicAdd(&D[j - 1], (float)dirs[k]);
+    }
+    __syncwarp();
+    const float sy = spy - yr, ey = epy - yr, ney = -ey, syey = sy * ey;
+    const float clo = ey < sy ? ey : sy, chi_ = ey < sy ? sy : ey;
+    const bool crosses = clo <= 0.f && 0.f < chi_;
+    const bool up = sy > ey;
+    const float dchi = up ? 1.f : -1.f;
+    const float2 spx2 = make_float2(spx, spx), epx2 = make_float2(epx, epx);
+    const float2 sy2 = make_float2(sy, sy), ney2 = make_float2(ney, ney), syey2 = make_float2(syey, syey);
+    const float2 inv2pi2 = make_float2(Num<float>::inv2pi, Num<float>::inv2pi);
+    float carry = 0.f;
+    for (int c0 = nxp - 256; c0 >= 0; c0 -= 256) {
+        const int i0 = c0 + 8 * lane;
+        const float4 da = *(const float4 *)(D + i0), db = *(const float4 *)(D + i0 + 4);
+        float t[8];
+        t[7] = db.w; t[6] = db.z + t[7]; t[5] = db.y + t[6]; t[4] = db.x + t[5];
+        t[3] = da.w + t[4]; t[2] = da.z + t[3]; t[1] = da.y + t[2]; t[0] = da.x + t[1];
+        float x = t[0];
+        for (int off = 1; off < 32; off <<= 1) {
+            float y = __shfl_down_sync(FULL, x, off);
+            if (lane + off < 32) x += y;
+        }
+        const float before = carry + x - t[0];       // crossings right of this lane's 8 columns
+        carry += __shfl_sync(FULL, x, 0);
+        if (i0 >= nx) continue;
+        const bool full = i0 + 8 <= nx;
+        float xq[8];
+        if (full && ((uintptr_t)(ax + i0) & 15) == 0) {
+            const float4 xa = *(const float4 *)(ax + i0), xb = *(const float4 *)(ax + i0 + 4);
+            xq[0] = xa.x; xq[1] = xa.y; xq[2] = xa.z; xq[3] = xa.w;
+            xq[4] = xb.x; xq[5] = xb.y; xq[6] = xb.z; xq[7] = xb.w;
+        } else {
+#pragma unroll
+            for (int m = 0; m < 8; m++) xq[m] = ax[i0 + m < nx ? i0 + m : nx - 1];
+        }
+        float out[8];
+#pragma unroll
+        for (int m = 0; m < 8; m += 2) {
+            const float2 nX = make_float2(-xq[m], -xq[m + 1]);
+            const float2 sx = __fadd2_rn(spx2, nX), ex = __fadd2_rn(epx2, nX);
+            const float2 cr = __ffma2_rn(ex, sy2, __fmul2_rn(sx, ney2));
+            const float2 dt = __ffma2_rn(sx, ex, syey2);
+            const float2 A = chord_angle2(cr, dt);
+            float k0 = before + t[m], k1 = before + t[m + 1];
+            if (crosses && (up ? (cr.x > 0.f) : (cr.x < 0.f))) k0 += dchi;
+            if (crosses && (up ? (cr.y > 0.f) : (cr.y < 0.f))) k1 += dchi;
+            const float2 o = __ffma2_rn(A, inv2pi2, make_float2(k0, k1));     // w = chi + A / 2 pi
+            out[m] = o.x;
+            out[m + 1] = o.y;
+        }
+        float *wp = wrow + i0;
+        if (full && ((uintptr_t)wp & 15) == 0) {
+            ((float4 *)wp)[0] = make_float4(out[0], out[1], out[2], out[3]);
+            ((float4 *)wp)[1] = make_float4(out[4], out[5], out[6], out[7]);
+        } else {
+#pragma unroll
+            for (int m = 0; m < 8; m++)
+                if (i0 + m < nx) wp[m] = out[m];
         }
     }
     __syncwarp();
@@ -335,7 +502,8 @@ __global__ void __launch_bounds__(1024) eval2d_kernel(const T *__restrict__ ctrl
     const int nthr = blockDim.x;
     T *xs = (T *)smem_raw;                                    // CAP crossings
     T *ys = xs + CAP;                                         // MAX_ROWS row values
-    int *roff = (int *)(ys + MAX_ROWS);                       // MAX_ROWS + 1 offsets
+    T *s_pc = ys + MAX_ROWS;                                  // PC_FIELDS x nthr: staged piece data
+    int *roff = (int *)(s_pc + PC_FIELDS * nthr);             // MAX_ROWS + 1 offsets
     int *rcur = roff + MAX_ROWS + 1;                          // MAX_ROWS + 1: difference array, then cursors
     int *s_ofs = rcur + MAX_ROWS + 1;                         // per thread: first pair of its piece
     int *s_ra = s_ofs + nthr;                                 // per thread: first row of its piece
@@ -347,12 +515,16 @@ __global__ void __launch_bounds__(1024) eval2d_kernel(const T *__restrict__ ctrl
     __shared__ int ncross;
     __shared__ long long item_sh;
     unsigned long long nroots_thread = 0;
+    // the next item is claimed while the current one runs (thread 0 keeps the
+    // claim in a register and publishes it at the end of the item)
+    if (threadIdx.x == 0) item_sh = (long long)atomicAdd(counter, 1ull);
+    __syncthreads();
     for (int64_t guard = 0; guard <= n_items; guard++) {
-        if (threadIdx.x == 0) item_sh = (long long)atomicAdd(counter, 1ull);
-        __syncthreads();
         long long item = item_sh;
         __syncthreads();
         if (item >= n_items) break;
+        long long next_item = 0;
+        if (threadIdx.x == 0) next_item = (long long)atomicAdd(counter, 1ull);
         // one set passed by value (items are its row blocks), or a work list
         int2 it = items ? items[item] : make_int2(0, (int)item);
         const Set2D S = sets ? sets[it.x] : single;
@@ -367,11 +539,17 @@ __global__ void __launch_bounds__(1024) eval2d_kernel(const T *__restrict__ ctrl
             rcur[i] = 0;
         }
         __syncthreads();
-        // pass 1: crossings per row, by a difference array over the rows
+        // pass 1: crossings per row, by a difference array over the rows.  A
+        // piece crosses row r iff lo <= y_r < hi; pieces wholly below the
+        // item's first row or above its last are skipped before the searches.
+        const T y_first = ys[0], y_last = ys[nr - 1];
+        const T inv_hy = nr > 1 && y_last > y_first ? T(nr - 1) / (y_last - y_first) : T(0);
         for (int64_t p = S.p_lo + threadIdx.x; p < S.p_hi; p += nthr) {
             T ya = piece_y[2 * p], yb = piece_y[2 * p + 1];
             T lo = ya < yb ? ya : yb, hi = ya < yb ? yb : ya;
-            int ra = lower_bound_rows(ys, nr, lo), rb = lower_bound_rows(ys, nr, hi);
+            if (!(hi > y_first && lo <= y_last)) continue;
+            int ra = lower_bound_rows_grid(ys, nr, y_first, inv_hy, lo);
+            int rb = lower_bound_rows_grid(ys, nr, y_first, inv_hy, hi);
             if (ra < rb) {
                 atomicAdd(&rcur[ra], 1);
                 atomicAdd(&rcur[rb], -1);
@@ -426,19 +604,30 @@ __global__ void __launch_bounds__(1024) eval2d_kernel(const T *__restrict__ ctrl
                     if (p < S.p_hi) {
                         T ya = piece_y[2 * p], yb = piece_y[2 * p + 1];
                         T lo = ya < yb ? ya : yb, hi = ya < yb ? yb : ya;
-                        ra = lower_bound_rows(ys, nr, lo);
-                        int rb = lower_bound_rows(ys, nr, hi);
-                        if (ra < sb0) ra = sb0;
-                        if (rb > sb1) rb = sb1;
-                        n = rb > ra ? rb - ra : 0;
+                        if (hi > ys[sb0] && lo <= ys[sb1 - 1]) {   // else no row of the sub-block
+                            ra = lower_bound_rows_grid(ys, nr, y_first, inv_hy, lo);
+                            int rb = lower_bound_rows_grid(ys, nr, y_first, inv_hy, hi);
+                            if (ra < sb0) ra = sb0;
+                            if (rb > sb1) rb = sb1;
+                            n = rb > ra ? rb - ra : 0;
+                        }
                     }
                     int x = n;
                     for (int off = 1; off < 32; off <<= 1) {
                         int t = __shfl_up_sync(FULL, x, off);
                         if (lane >= off) x += t;
                     }
-                    __syncthreads();                 // the previous chunk is done with s_wsum, s_ofs, s_ra
+                    __syncthreads();                 // the previous chunk is done with s_wsum, s_ofs, s_ra, s_pc
                     if (lane == 31) s_wsum[warp] = x;
+                    if (n > 0) {                      // stage the piece for the threads that take its roots
+                        const T *cp = ctrl + 2 * piece_seg[p];
+#pragma unroll
+                        for (int m = 0; m < 8; m++) s_pc[m * nthr + threadIdx.x] = cp[m];
+                        s_pc[8 * nthr + threadIdx.x] = piece_u[2 * p];
+                        s_pc[9 * nthr + threadIdx.x] = piece_u[2 * p + 1];
+                        s_pc[10 * nthr + threadIdx.x] = piece_y[2 * p];
+                        s_pc[11 * nthr + threadIdx.x] = piece_y[2 * p + 1];
+                    }
                     __syncthreads();
                     int before = 0, tot = 0;
                     for (int w = 0; w < nwarps; w++) {
@@ -456,15 +645,13 @@ __global__ void __launch_bounds__(1024) eval2d_kernel(const T *__restrict__ ctrl
                             const int mid = (lo + hi + 1) >> 1;
                             if (s_ofs[mid] <= k) lo = mid; else hi = mid - 1;
                         }
-                        const int64_t q = pc + lo;
                         const int r = s_ra[lo] + (k - s_ofs[lo]);
-                        const T ya = piece_y[2 * q], yb = piece_y[2 * q + 1];
-                        const T *cp = ctrl + 2 * piece_seg[q];
+                        const T ya = s_pc[10 * nthr + lo], yb = s_pc[11 * nthr + lo];
                         T c[8];
 #pragma unroll
-                        for (int m = 0; m < 8; m++) c[m] = cp[m];
+                        for (int m = 0; m < 8; m++) c[m] = s_pc[m * nthr + lo];
                         int iters;
-                        const T xr = piece_root_x<T>(c, piece_u[2 * q], piece_u[2 * q + 1], ya, yb, ys[r], &iters);
+                        const T xr = piece_root_x<T>(c, s_pc[8 * nthr + lo], s_pc[9 * nthr + lo], ya, yb, ys[r], &iters);
                         if (iters >= Num<T>::max_iter && status) atomicOr(status, ST_TIMEOUT);
                         nroots_thread += (unsigned long long)iters << 32 | 1ull;
                         const int slot = roff[r] - base + atomicAdd(&rcur[r], 1);
@@ -475,10 +662,21 @@ __global__ void __launch_bounds__(1024) eval2d_kernel(const T *__restrict__ ctrl
                 __syncthreads();
                 // queries: one warp per row
                 int *D = s_D + warp * eval2d_dstride(max_nx);
-                for (int r = sb0 + warp; r < sb1; r += nwarps)
-                    row_queries<T>(S, ctrl, chain_off, ax, nx, a0, inv_step, xs + roff[r] - base,
-                                   dirs + roff[r] - base, roff[r + 1] - roff[r], ys[r], r0 + r, D, lane, w_out,
-                                   chi_out, b_out);
+                if (sizeof(T) == 4 && S.c_hi - S.c_lo == 1 && !chi_out && !b_out && w_out) {
+                    const float *sp = (const float *)ctrl + 2 * chain_off[S.c_lo];
+                    const float *ep = (const float *)ctrl + 2 * (chain_off[S.c_lo + 1] - 1);
+                    const float spx = sp[0], spy = sp[1], epx = ep[0], epy = ep[1];
+                    for (int r = sb0 + warp; r < sb1; r += nwarps)
+                        row_queries_f32((const float *)ax, nx, (float)a0, (float)inv_step,
+                                        (const float *)xs + roff[r] - base, dirs + roff[r] - base,
+                                        roff[r + 1] - roff[r], (float)ys[r], spx, spy, epx, epy,
+                                        (float *)w_out + S.out_off + (r0 + r) * S.nx, (float *)D, lane);
+                } else {
+                    for (int r = sb0 + warp; r < sb1; r += nwarps)
+                        row_queries<T>(S, ctrl, chain_off, ax, nx, a0, inv_step, xs + roff[r] - base,
+                                       dirs + roff[r] - base, roff[r + 1] - roff[r], ys[r], r0 + r, D, lane, w_out,
+                                       chi_out, b_out);
+                }
                 __syncthreads();
             } else {
                 // fallback for row sb0 (more than CAP crossings): CHUNK crossings per pass
@@ -518,14 +716,15 @@ __global__ void __launch_bounds__(1024) eval2d_kernel(const T *__restrict__ ctrl
                 }
                 for (int64_t i = threadIdx.x; i < S.nx; i += nthr) {
                     int chi = chi_row[i];
-                    T term = chord_terms<T>(ctrl, chain_off, S, ax[i], yr, chi);
-                    store_w<T>(S, r0 + r, i, chi, term, w_out, chi_out, b_out);
+                    T A = chord_angles<T>(ctrl, chain_off, S, ax[i], yr, chi);
+                    store_w<T>(S, r0 + r, i, chi, A, w_out, chi_out, b_out);
                 }
                 __syncthreads();
                 sb1 = sb0 + 1;
             }
             sb0 = sb1;
         }
+        if (threadIdx.x == 0) item_sh = next_item;
         __syncthreads();
     }
     if (cnt && nroots_thread) {
@@ -632,10 +831,10 @@ __global__ void __launch_bounds__(256) eval2d_points_kernel(
     Set2D S;
     S.c_lo = 0;
     S.c_hi = n_chains;
-    const T term = chord_terms<T>(ctrl, chain_off, S, px, py, chi);
-    if (w_out) w_out[i] = (T)chi + term;
+    const T A = chord_angles<T>(ctrl, chain_off, S, px, py, chi);
+    if (w_out) w_out[i] = w_of<T>(chi, A);
     if (chi_out) chi_out[i] = chi;
-    if (b_out) b_out[i] = term;
+    if (b_out) b_out[i] = Num<T>::mul(A, Num<T>::inv2pi);
 }
 
 cudaError_t launch_eval2d_points(const ChainSet &cs, const QuerySrc &q, void *w_out, int32_t *chi_out, void *b_out,
