@@ -415,6 +415,7 @@ static void free_geom_device(gwn_geom *g) {
     if (cs.piece_uT && cs.piece_uT != (void *)cs.piece_u) cudaFree(cs.piece_uT);
     if (cs.piece_yT && cs.piece_yT != (void *)cs.piece_y) cudaFree(cs.piece_yT);
     if (cs.piece_xT) cudaFree(cs.piece_xT);
+    if (cs.piece_rec) cudaFree(cs.piece_rec);
     if (cs.bucket_off) cudaFree(cs.bucket_off);
     if (cs.bucket_idx) cudaFree(cs.bucket_idx);
     if (cs.piece_chain) cudaFree(cs.piece_chain);
@@ -737,6 +738,23 @@ GWN_API gwn_status gwn_bezier2d_create(gwn_ctx *ctx, const void *ctrl, int dtype
         if (e == cudaSuccess) e = cudaMalloc(&cs.piece_yT, sizeof(float) * 2 * np);
         if (e == cudaSuccess) e = cudaMemcpy(cs.piece_uT, fu.data(), sizeof(float) * 2 * np, cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemcpy(cs.piece_yT, fy.data(), sizeof(float) * 2 * np, cudaMemcpyHostToDevice);
+    }
+    if (e == cudaSuccess) {        // per-piece records for the row kernel
+        std::vector<double> rec(12 * np, 0.0);
+        for (int64_t q = 0; q < cs.n_pieces; q++) {
+            for (int k = 0; k < 8; k++) rec[12 * q + k] = P[2 * pseg[q] + k];
+            rec[12 * q + 8] = pu[2 * q];
+            rec[12 * q + 9] = pu[2 * q + 1];
+            rec[12 * q + 10] = py[2 * q];
+            rec[12 * q + 11] = py[2 * q + 1];
+        }
+        size_t bytes = esz * rec.size();
+        e = cudaMalloc(&cs.piece_rec, bytes);
+        if (e == cudaSuccess && dtype == GWN_F64) e = cudaMemcpy(cs.piece_rec, rec.data(), bytes, cudaMemcpyHostToDevice);
+        else if (e == cudaSuccess) {
+            std::vector<float> fr(rec.begin(), rec.end());
+            e = cudaMemcpy(cs.piece_rec, fr.data(), bytes, cudaMemcpyHostToDevice);
+        }
     }
     if (e == cudaSuccess) e = build_point_index(cs, P, pseg, py, dtype);
     if (e != cudaSuccess) {

@@ -36,17 +36,21 @@
 namespace gwn {
 
 template <typename T> struct Num;
-// Root tolerance in u: Newton stops once its step (or the bracket) is below
-// tol.  A Newton step that small leaves an error of order its square; a
-// bisection-terminated root is within tol in u, i.e. about tol |x'(u)| in x.
-// That only decides queries that close to the curve, far inside the band
-// (1e-4 of the grid diagonal) where w is not compared, so float32 uses 1e-6
-// (2.7 iterations per root on average on the star chains); float64 keeps
-// 1e-16.
+// Root tolerances.  Newton stops once the curve point at u lies within
+// ytol (|y(u0)| + |y(u1)|) of the row in y, or once its step (or the bracket)
+// is below tol in u.  A computed root whose curve point is within e of the
+// row can change the crossing count of a query on the row only if the query
+// lies between the computed and the true crossing, and every such query is
+// within e of the curve (the arc of the monotone piece between the two runs
+// over those x values with y within e of the row).  That is far inside the
+// band (1e-4 of the grid diagonal) where w is not compared.  The y test ends
+// the iteration early near a piece end, where dy/du vanishes (pieces are
+// split at the extrema of y) and the step in u shrinks slowly.
 template <> struct Num<float> {
     static constexpr float inv2pi = 0.15915494309189535f;
     static constexpr int max_iter = 60;
     static constexpr float tol = 1e-6f;
+    static constexpr float ytol = 1e-6f;
     // Newton quotients: an approximate quotient (2 ulp) only perturbs the
     // iterates; the stopping test on the step decides the accuracy
     static __device__ __forceinline__ float div(float a, float b) { return __fdividef(a, b); }
@@ -59,6 +63,7 @@ template <> struct Num<double> {
     static constexpr double inv2pi = 0.15915494309189533577;
     static constexpr int max_iter = 200;
     static constexpr double tol = 1e-16;
+    static constexpr double ytol = 1e-15;
     static __device__ __forceinline__ double div(double a, double b) { return a / b; }
     static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
     static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
@@ -96,10 +101,11 @@ __device__ T piece_root_xu(const T *c, T u0, T u1, T ya, T yb, T yr, int *iters_
     if (!inc) { lo = u1; hi = u0; }
     T yl = inc ? ya : yb, yh = inc ? yb : ya;
     T u = lo + (hi - lo) * Num<T>::div(yr - yl, yh - yl);
+    const T ytol = Num<T>::ytol * ((ya < T(0) ? -ya : ya) + (yb < T(0) ? -yb : yb));
     int it = 0;
     for (; it < Num<T>::max_iter; it++) {
         T g = bern(c[1], c[3], c[5], c[7], u) - yr;
-        if (g == T(0)) break;                       // exact root (a zero Newton step would fall to bisection)
+        if ((g < T(0) ? -g : g) <= ytol) break;     // the curve point is within ytol of the row
         if (g < T(0)) lo = u; else hi = u;
         T dg = dbern(c[1], c[3], c[5], c[7], u);
         T un = u - Num<T>::div(g, dg);
@@ -493,8 +499,9 @@ __device__ __forceinline__ void row_queries_f32(const float *__restrict__ ax, in
 template <typename T>
 __global__ void __launch_bounds__(1024) eval2d_kernel(const T *__restrict__ ctrl, const int64_t *__restrict__ chain_off,
                               const int64_t *__restrict__ piece_seg, const T *__restrict__ piece_u,
-                              const T *__restrict__ piece_y, const Set2D *__restrict__ sets,
-                              const int2 *__restrict__ items, const Set2D single, int64_t n_items,
+                              const T *__restrict__ piece_y, const T *__restrict__ piece_rec,
+                              const Set2D *__restrict__ sets, const int2 *__restrict__ items, const Set2D single,
+                              int64_t n_items,
                               unsigned long long *counter, int rows_per_item, T *__restrict__ w_out,
                               int32_t *__restrict__ chi_out, T *__restrict__ b_out, unsigned long long *cnt,
                               int *status, int max_nx) {
@@ -620,13 +627,14 @@ __global__ void __launch_bounds__(1024) eval2d_kernel(const T *__restrict__ ctrl
                     __syncthreads();                 // the previous chunk is done with s_wsum, s_ofs, s_ra, s_pc
                     if (lane == 31) s_wsum[warp] = x;
                     if (n > 0) {                      // stage the piece for the threads that take its roots
-                        const T *cp = ctrl + 2 * piece_seg[p];
+                        // (its record: 12 values, 16-byte aligned, read as 16-byte words)
+                        constexpr int W = PC_FIELDS * (int)sizeof(T) / 16;
+                        const uint4 *rp = (const uint4 *)(piece_rec + (int64_t)PC_FIELDS * p);
+                        T v[PC_FIELDS];
 #pragma unroll
-                        for (int m = 0; m < 8; m++) s_pc[m * nthr + threadIdx.x] = cp[m];
-                        s_pc[8 * nthr + threadIdx.x] = piece_u[2 * p];
-                        s_pc[9 * nthr + threadIdx.x] = piece_u[2 * p + 1];
-                        s_pc[10 * nthr + threadIdx.x] = piece_y[2 * p];
-                        s_pc[11 * nthr + threadIdx.x] = piece_y[2 * p + 1];
+                        for (int m = 0; m < W; m++) ((uint4 *)v)[m] = rp[m];
+#pragma unroll
+                        for (int m = 0; m < PC_FIELDS; m++) s_pc[m * nthr + threadIdx.x] = v[m];
                     }
                     __syncthreads();
                     int before = 0, tot = 0;
@@ -769,12 +777,14 @@ cudaError_t launch_eval2d_items(const ChainSet &cs, const Set2D *d_sets, const i
     if (cs.dtype == GWN_F64) {
         eval2d_kernel<double><<<(unsigned)blocks, threads, smem, st>>>(
             (const double *)cs.ctrl, cs.chain_off, cs.piece_seg, (const double *)cs.piece_uT,
-            (const double *)cs.piece_yT, d_sets, d_items, s0, n_items, d_counter, rows_per_item, (double *)w_out,
+            (const double *)cs.piece_yT, (const double *)cs.piece_rec, d_sets, d_items, s0, n_items, d_counter,
+            rows_per_item, (double *)w_out,
             chi_out, (double *)b_out, cnt, status, (int)max_nx);
     } else {
         eval2d_kernel<float><<<(unsigned)blocks, threads, smem, st>>>(
             (const float *)cs.ctrl, cs.chain_off, cs.piece_seg, (const float *)cs.piece_uT,
-            (const float *)cs.piece_yT, d_sets, d_items, s0, n_items, d_counter, rows_per_item, (float *)w_out,
+            (const float *)cs.piece_yT, (const float *)cs.piece_rec, d_sets, d_items, s0, n_items, d_counter,
+            rows_per_item, (float *)w_out,
             chi_out, (float *)b_out, cnt, status, (int)max_nx);
     }
     return cudaGetLastError();

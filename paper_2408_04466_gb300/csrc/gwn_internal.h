@@ -98,6 +98,10 @@ struct ChainSet {
     // point queries: the pieces' conservative x ranges (control hull of their
     // segment, chain dtype, [n_pieces][2]) and a y-bucket index of the pieces
     void *piece_xT = nullptr;
+    // per piece, in the chain dtype: its segment's control points (x0 y0 .. x3
+    // y3), u0, u1, y(u0), y(u1) -- one contiguous record, read by the row
+    // kernel without a dependent load through piece_seg
+    void *piece_rec = nullptr;
     int32_t *bucket_off = nullptr;     // [n_buckets + 1]
     int32_t *bucket_idx = nullptr;     // piece indices, bucket by bucket
     int32_t n_buckets = 0;
