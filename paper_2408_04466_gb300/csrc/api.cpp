@@ -685,7 +685,13 @@ GWN_API gwn_status gwn_bezier2d_create(gwn_ctx *ctx, const void *ctrl, int dtype
     std::vector<double> pu, py;
     std::vector<int32_t> pch;
     cs.h_chain_piece_off.assign(1, 0);
+    // a chain's pieces are kept in order of their lowest y (in the chain's
+    // precision), with the running maximum of their highest y: the pieces
+    // that can reach a band of rows are then one contiguous run
+    struct PieceH { int64_t seg; double u0, u1, y0, y1, lo_t; };
+    auto to_t = [dtype](double v) { return dtype == GWN_F64 ? v : (double)(float)v; };
     for (int64_t c = 0; c < n_chains; c++) {
+        std::vector<PieceH> ch;
         for (int64_t i = chain_offsets[c]; i + 3 < chain_offsets[c + 1]; i += 3) {
             double cc[8];
             for (int k = 0; k < 8; k++) cc[k] = P[2 * i + k];
@@ -695,13 +701,21 @@ GWN_API gwn_status gwn_bezier2d_create(gwn_ctx *ctx, const void *ctrl, int dtype
             for (int k = 0; k < np; k++) {
                 double y0 = bez_y(cc, u[2 * k]), y1 = bez_y(cc, u[2 * k + 1]);
                 if (y0 == y1) continue;   // flat piece: never crossed by the half-open rule
-                pseg.push_back(i);
-                pu.push_back(u[2 * k]);
-                pu.push_back(u[2 * k + 1]);
-                py.push_back(y0);
-                py.push_back(y1);
-                pch.push_back((int32_t)c);
+                ch.push_back({i, u[2 * k], u[2 * k + 1], y0, y1, to_t(std::min(y0, y1))});
             }
+        }
+        std::stable_sort(ch.begin(), ch.end(), [](const PieceH &a, const PieceH &b) { return a.lo_t < b.lo_t; });
+        double hmax = -INFINITY;
+        for (const PieceH &q : ch) {
+            pseg.push_back(q.seg);
+            pu.push_back(q.u0);
+            pu.push_back(q.u1);
+            py.push_back(q.y0);
+            py.push_back(q.y1);
+            pch.push_back((int32_t)c);
+            hmax = std::max(hmax, to_t(std::max(q.y0, q.y1)));
+            cs.h_piece_lo.push_back(q.lo_t);
+            cs.h_piece_hmax.push_back(hmax);
         }
         cs.h_chain_piece_off.push_back((int64_t)pch.size());
     }

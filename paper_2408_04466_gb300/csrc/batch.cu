@@ -20,17 +20,42 @@ namespace gwn {
 
 static const int64_t MAX_NX = 16384;
 
-// items (set, row block), most expensive sets first
-static void make_items(const std::vector<Set2D> &sets, int rows_per_item, std::vector<int2> &items) {
+// axis value i of a grid axis, as the axis tables hold it (float64 formula,
+// rounded to the chain's precision)
+static double axis_value(double lo, double hi, int64_t n, int64_t i, int dtype) {
+    double v = n == 1 ? lo : lo + (double)i * ((hi - lo) / (double)(n - 1));
+    return dtype == GWN_F64 ? v : (double)(float)v;
+}
+
+// items (set, row block, first piece, end piece), most expensive sets first.
+// A set's pieces are ordered by their lowest y; a piece can cross a row of
+// the block only if its lowest y is <= the block's last row and its highest
+// y > the block's first row, so the run [first, end) skips the pieces whose
+// lowest y lies above the block and the prefix whose running maximum of the
+// highest y stays at or below it (the same comparisons the kernel makes, in
+// the same precision).
+static void make_items(const std::vector<Set2D> &sets, const gwn_queries *qs, const ChainSet &cs, int rows_per_item,
+                       std::vector<int4> &items) {
     std::vector<std::pair<double, int>> order;
     for (size_t s = 0; s < sets.size(); s++)
         order.emplace_back(-(double)(sets[s].p_hi - sets[s].p_lo + 1) * (double)sets[s].nx, (int)s);
     std::stable_sort(order.begin(), order.end());
     items.clear();
+    const double *lo_t = cs.h_piece_lo.data(), *hmax_t = cs.h_piece_hmax.data();
     for (auto &o : order) {
         const Set2D &S = sets[o.second];
+        const gwn_queries &q = qs[o.second];
         int64_t nb = (S.ny + rows_per_item - 1) / rows_per_item;
-        for (int64_t b = 0; b < nb; b++) items.push_back(make_int2(o.second, (int)b));
+        for (int64_t b = 0; b < nb; b++) {
+            int64_t r0 = b * rows_per_item, r1 = std::min<int64_t>(r0 + rows_per_item, S.ny);
+            double y_first = axis_value(q.lo[1], q.hi[1], S.ny, r0, cs.dtype);
+            double y_last = axis_value(q.lo[1], q.hi[1], S.ny, r1 - 1, cs.dtype);
+            // first piece with hmax > y_first; first piece with lo > y_last
+            int64_t pa = std::upper_bound(hmax_t + S.p_lo, hmax_t + S.p_hi, y_first) - hmax_t;
+            int64_t pb = std::upper_bound(lo_t + S.p_lo, lo_t + S.p_hi, y_last) - lo_t;
+            if (pb < pa) pb = pa;
+            items.push_back(make_int4(o.second, (int)b, (int)pa, (int)pb));
+        }
     }
 }
 
@@ -81,7 +106,7 @@ struct BatchPlan {
     void *dev = nullptr;             // axis tables + sets + items + counter
     size_t dev_bytes = 0;
     Set2D *d_sets = nullptr;
-    int2 *d_items = nullptr;
+    int4 *d_items = nullptr;
     unsigned long long *d_counter = nullptr;
     int64_t n_items = 0, max_nx = 0;
     void *w_out = nullptr;
@@ -114,7 +139,7 @@ static gwn_status plan_upload(gwn_geom *g, const gwn_queries *qs, int64_t n, con
     size_t axis_bytes = 0;
     for (int64_t c = 0; c < n; c++) axis_bytes += esz * (qs[c].dims[0] + qs[c].dims[1]);
     axis_bytes = (axis_bytes + 255) & ~(size_t)255;
-    std::vector<int2> items;
+    std::vector<int4> items;
     int64_t max_nx = 0;
     for (int64_t c = 0; c < n; c++) {
         sets[c].nx = qs[c].dims[0];
@@ -126,9 +151,9 @@ static gwn_status plan_upload(gwn_geom *g, const gwn_queries *qs, int64_t n, con
         sets[c].out_off = out_off[c];
         max_nx = std::max(max_nx, sets[c].nx);
     }
-    make_items(sets, rows, items);
-    size_t sets_off = axis_bytes, items_off = sets_off + sizeof(Set2D) * n;
-    size_t ctr_off = (items_off + sizeof(int2) * items.size() + 15) & ~(size_t)15;
+    make_items(sets, qs, cs, rows, items);
+    size_t sets_off = axis_bytes, items_off = (sets_off + sizeof(Set2D) * n + 15) & ~(size_t)15;
+    size_t ctr_off = (items_off + sizeof(int4) * items.size() + 15) & ~(size_t)15;
     size_t total = ctr_off + 16;
     if (P->dev) { cudaFree(P->dev); P->dev = nullptr; }
     cudaError_t e = cudaMalloc(&P->dev, total);
@@ -144,12 +169,12 @@ static gwn_status plan_upload(gwn_geom *g, const gwn_queries *qs, int64_t n, con
         off += esz * qs[c].dims[1];
     }
     memcpy(host.data() + sets_off, sets.data(), sizeof(Set2D) * n);
-    memcpy(host.data() + items_off, items.data(), sizeof(int2) * items.size());
+    memcpy(host.data() + items_off, items.data(), sizeof(int4) * items.size());
     e = cudaMemcpy(P->dev, host.data(), total, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(e, "batch plan upload");
     P->dev_bytes = total;
     P->d_sets = (Set2D *)((char *)P->dev + sets_off);
-    P->d_items = (int2 *)((char *)P->dev + items_off);
+    P->d_items = (int4 *)((char *)P->dev + items_off);
     P->d_counter = (unsigned long long *)((char *)P->dev + ctr_off);
     P->n_items = (int64_t)items.size();
     P->max_nx = max_nx;

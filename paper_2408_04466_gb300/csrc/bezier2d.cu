@@ -129,8 +129,8 @@ constexpr int CAP = 4096;            // crossings binned per row sub-block
 //   xs[CAP], ys[MAX_ROWS], pc[PC_FIELDS * threads] (T: crossings, row values,
 //   the staged data of each thread's piece), roff[MAX_ROWS + 1],
 //   rcur[MAX_ROWS + 1], ofs[threads], ra[threads], wsum[32] (int),
-//   dirs[CAP] (int8), then per warp the difference array of the row queries
-//   (or the fallback's chi_row).
+//   dirs[CAP] (int8), then the item's column values ax[max_nx] (T), then per
+//   warp the difference array of the row queries (or the fallback's chi_row).
 constexpr int PC_FIELDS = 12;        // control points (8), u0, u1, y(u0), y(u1)
 template <typename T>
 __host__ __device__ constexpr size_t eval2d_fallback_off(int threads) {
@@ -246,14 +246,13 @@ __device__ __forceinline__ int lower_bound_rows_grid(const T *ys, int n, T y0, T
 }
 
 // first column j in [0, nx] with ax[j] >= x, on a grid axis (non-decreasing,
-// spaced ~uniformly): a guess from the spacing, corrected against the stored
-// values, so the result is exactly the lower bound
+// spaced ~uniformly; here the item's copy in shared memory): a guess from the
+// spacing, corrected against the stored values, so the result is exactly the
+// lower bound
 template <typename T>
-__device__ __forceinline__ int lower_bound_cols(const T *__restrict__ ax, int nx, T a0, T inv_step, T x) {
-    int j = nx;
-    if (!(x <= ax[nx - 1])) return nx;
-    T g = (x - a0) * inv_step;
-    j = g <= T(0) ? 0 : (g >= T(nx - 1) ? nx - 1 : (int)ceil(g));
+__device__ __forceinline__ int lower_bound_cols(const T *ax, int nx, T a0, T inv_step, T x) {
+    const T g = (x - a0) * inv_step;
+    int j = !(g > T(0)) ? 0 : (g >= T(nx) ? nx : (int)ceil(g));
     while (j > 0 && ax[j - 1] >= x) j--;
     while (j < nx && ax[j] < x) j++;
     return j;
@@ -390,26 +389,32 @@ __device__ __forceinline__ void row_queries(const Set2D &S, const T *__restrict_
     __syncwarp();
 }
 
+// exact float of a small integer (|n| < 2^22): n added to the bias 1.5 * 2^23
+// in the integer domain, the bias taken off in float (no conversion unit)
+__device__ __forceinline__ float small_int_to_float(int n) {
+    return __fadd_rn(__int_as_float(0x4B400000 + n), -12582912.f);
+}
+
 // The row queries on the float32 fast path (a set of one chain, w only): the
-// same steps as row_queries, with the difference array and the counts kept
-// as floats (exact: a row holds at most CAP crossings) and the chord terms of
-// two columns at a time in packed f32x2 arithmetic.  Rounds exactly as the
-// generic path does.  (spx, spy), (epx, epy): the chain's end points.
+// same steps as row_queries, with the counts turned to floats without the
+// conversion unit (exact: a row holds at most CAP crossings) and the chord
+// terms of two columns at a time in packed f32x2 arithmetic.  Rounds exactly
+// as the generic path does.  (spx, spy), (epx, epy): the chain's end points.
 __device__ __forceinline__ void row_queries_f32(const float *__restrict__ ax, int nx, float a0, float inv_step,
                                                 const float *xs, const signed char *dirs, int nk, float yr,
                                                 float spx, float spy, float epx, float epy,
-                                                float *__restrict__ wrow, float *D, int lane) {
+                                                float *__restrict__ wrow, int *D, int lane) {
     const unsigned FULL = 0xffffffffu;
     const int nxp = eval2d_dstride(nx);
     for (int c0 = 0; c0 < nxp; c0 += 256) {
-        float4 *d4 = (float4 *)(D + c0 + 8 * lane);
-        d4[0] = make_float4(0.f, 0.f, 0.f, 0.f);
-        d4[1] = make_float4(0.f, 0.f, 0.f, 0.f);
+        int4 *d4 = (int4 *)(D + c0 + 8 * lane);
+        d4[0] = make_int4(0, 0, 0, 0);
+        d4[1] = make_int4(0, 0, 0, 0);
     }
     __syncwarp();
     for (int k = lane; k < nk; k += 32) {
         int j = lower_bound_cols(ax, nx, a0, inv_step, xs[k]);
-        if (j > 0) atomicAdd(&D[j - 1], (float)dirs[k]);
+        if (j > 0) atomicAdd(&D[j - 1], (int)dirs[k]);
     }
     __syncwarp();
     const float sy = spy - yr, ey = epy - yr, ney = -ey, syey = sy * ey;
@@ -420,19 +425,19 @@ __device__ __forceinline__ void row_queries_f32(const float *__restrict__ ax, in
     const float2 spx2 = make_float2(spx, spx), epx2 = make_float2(epx, epx);
     const float2 sy2 = make_float2(sy, sy), ney2 = make_float2(ney, ney), syey2 = make_float2(syey, syey);
     const float2 inv2pi2 = make_float2(Num<float>::inv2pi, Num<float>::inv2pi);
-    float carry = 0.f;
+    int carry = 0;
     for (int c0 = nxp - 256; c0 >= 0; c0 -= 256) {
         const int i0 = c0 + 8 * lane;
-        const float4 da = *(const float4 *)(D + i0), db = *(const float4 *)(D + i0 + 4);
-        float t[8];
+        const int4 da = *(const int4 *)(D + i0), db = *(const int4 *)(D + i0 + 4);
+        int t[8];
         t[7] = db.w; t[6] = db.z + t[7]; t[5] = db.y + t[6]; t[4] = db.x + t[5];
         t[3] = da.w + t[4]; t[2] = da.z + t[3]; t[1] = da.y + t[2]; t[0] = da.x + t[1];
-        float x = t[0];
+        int x = t[0];
         for (int off = 1; off < 32; off <<= 1) {
-            float y = __shfl_down_sync(FULL, x, off);
+            int y = __shfl_down_sync(FULL, x, off);
             if (lane + off < 32) x += y;
         }
-        const float before = carry + x - t[0];       // crossings right of this lane's 8 columns
+        const int before = carry + x - t[0];         // crossings right of this lane's 8 columns
         carry += __shfl_sync(FULL, x, 0);
         if (i0 >= nx) continue;
         const bool full = i0 + 8 <= nx;
@@ -453,7 +458,7 @@ __device__ __forceinline__ void row_queries_f32(const float *__restrict__ ax, in
             const float2 cr = __ffma2_rn(ex, sy2, __fmul2_rn(sx, ney2));
             const float2 dt = __ffma2_rn(sx, ex, syey2);
             const float2 A = chord_angle2(cr, dt);
-            float k0 = before + t[m], k1 = before + t[m + 1];
+            float k0 = small_int_to_float(before + t[m]), k1 = small_int_to_float(before + t[m + 1]);
             if (crosses && (up ? (cr.x > 0.f) : (cr.x < 0.f))) k0 += dchi;
             if (crosses && (up ? (cr.y > 0.f) : (cr.y < 0.f))) k1 += dchi;
             const float2 o = __ffma2_rn(A, inv2pi2, make_float2(k0, k1));     // w = chi + A / 2 pi
@@ -500,7 +505,7 @@ template <typename T>
 __global__ void __launch_bounds__(1024) eval2d_kernel(const T *__restrict__ ctrl, const int64_t *__restrict__ chain_off,
                               const int64_t *__restrict__ piece_seg, const T *__restrict__ piece_u,
                               const T *__restrict__ piece_y, const T *__restrict__ piece_rec,
-                              const Set2D *__restrict__ sets, const int2 *__restrict__ items, const Set2D single,
+                              const Set2D *__restrict__ sets, const int4 *__restrict__ items, const Set2D single,
                               int64_t n_items,
                               unsigned long long *counter, int rows_per_item, T *__restrict__ w_out,
                               int32_t *__restrict__ chi_out, T *__restrict__ b_out, unsigned long long *cnt,
@@ -516,7 +521,9 @@ __global__ void __launch_bounds__(1024) eval2d_kernel(const T *__restrict__ ctrl
     int *s_ra = s_ofs + nthr;                                 // per thread: first row of its piece
     int *s_wsum = s_ra + nthr;                                // per warp: pairs of its pieces
     signed char *dirs = (signed char *)(s_wsum + 32);         // CAP directions
-    int *s_D = (int *)(smem_raw + eval2d_fallback_off<T>(nthr));   // per warp: max_nx + 1 (fallback: chi_row)
+    T *s_ax = (T *)(smem_raw + eval2d_fallback_off<T>(nthr));      // the item's column values
+    int *s_D = (int *)((unsigned char *)s_ax + ((sizeof(T) * (size_t)max_nx + 15) & ~(size_t)15));
+                                                                   // per warp: max_nx + 1 (fallback: chi_row)
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = nthr >> 5;
     __shared__ int ncross;
@@ -533,9 +540,10 @@ __global__ void __launch_bounds__(1024) eval2d_kernel(const T *__restrict__ ctrl
         long long next_item = 0;
         if (threadIdx.x == 0) next_item = (long long)atomicAdd(counter, 1ull);
         // one set passed by value (items are its row blocks), or a work list
-        int2 it = items ? items[item] : make_int2(0, (int)item);
+        const int4 it = items ? items[item] : make_int4(0, (int)item, 0, 0);
         const Set2D S = sets ? sets[it.x] : single;
-        const T *ax = (const T *)S.ax;
+        // the pieces that can reach the item's rows (a work list carries them)
+        const int64_t pA = items ? (int64_t)it.z : S.p_lo, pB = items ? (int64_t)it.w : S.p_hi;
         const T *ay = (const T *)S.ay;
         const int nx = (int)S.nx;
         int64_t r0 = (int64_t)it.y * rows_per_item;
@@ -545,13 +553,14 @@ __global__ void __launch_bounds__(1024) eval2d_kernel(const T *__restrict__ ctrl
             if (i < nr) ys[i] = ay[r0 + i];
             rcur[i] = 0;
         }
+        for (int i = threadIdx.x; i < nx; i += nthr) s_ax[i] = ((const T *)S.ax)[i];
         __syncthreads();
         // pass 1: crossings per row, by a difference array over the rows.  A
         // piece crosses row r iff lo <= y_r < hi; pieces wholly below the
         // item's first row or above its last are skipped before the searches.
         const T y_first = ys[0], y_last = ys[nr - 1];
         const T inv_hy = nr > 1 && y_last > y_first ? T(nr - 1) / (y_last - y_first) : T(0);
-        for (int64_t p = S.p_lo + threadIdx.x; p < S.p_hi; p += nthr) {
+        for (int64_t p = pA + threadIdx.x; p < pB; p += nthr) {
             T ya = piece_y[2 * p], yb = piece_y[2 * p + 1];
             T lo = ya < yb ? ya : yb, hi = ya < yb ? yb : ya;
             if (!(hi > y_first && lo <= y_last)) continue;
@@ -585,8 +594,8 @@ __global__ void __launch_bounds__(1024) eval2d_kernel(const T *__restrict__ ctrl
             if (lane == 0) roff[nr] = c2;
         }
         __syncthreads();
-        const T a0 = ax[0];
-        const T inv_step = nx > 1 ? T(nx - 1) / (ax[nx - 1] - ax[0]) : T(0);
+        const T a0 = s_ax[0];
+        const T inv_step = nx > 1 && s_ax[nx - 1] > s_ax[0] ? T(nx - 1) / (s_ax[nx - 1] - s_ax[0]) : T(0);
         // rows in sub-blocks whose crossings fit in CAP (a single row with more
         // than CAP crossings takes the per-row fallback)
         for (int sb0 = 0; sb0 < nr;) {
@@ -605,10 +614,10 @@ __global__ void __launch_bounds__(1024) eval2d_kernel(const T *__restrict__ ctrl
                 // pass 2: the roots of rows [sb0, sb1), binned by row, over
                 // chunks of nthr pieces with the (piece, row) pairs spread
                 // evenly over the threads
-                for (int64_t pc = S.p_lo; pc < S.p_hi; pc += nthr) {
+                for (int64_t pc = pA; pc < pB; pc += nthr) {
                     const int64_t p = pc + threadIdx.x;
                     int ra = 0, n = 0;
-                    if (p < S.p_hi) {
+                    if (p < pB) {
                         T ya = piece_y[2 * p], yb = piece_y[2 * p + 1];
                         T lo = ya < yb ? ya : yb, hi = ya < yb ? yb : ya;
                         if (hi > ys[sb0] && lo <= ys[sb1 - 1]) {   // else no row of the sub-block
@@ -675,13 +684,13 @@ __global__ void __launch_bounds__(1024) eval2d_kernel(const T *__restrict__ ctrl
                     const float *ep = (const float *)ctrl + 2 * (chain_off[S.c_lo + 1] - 1);
                     const float spx = sp[0], spy = sp[1], epx = ep[0], epy = ep[1];
                     for (int r = sb0 + warp; r < sb1; r += nwarps)
-                        row_queries_f32((const float *)ax, nx, (float)a0, (float)inv_step,
+                        row_queries_f32((const float *)s_ax, nx, (float)a0, (float)inv_step,
                                         (const float *)xs + roff[r] - base, dirs + roff[r] - base,
                                         roff[r + 1] - roff[r], (float)ys[r], spx, spy, epx, epy,
-                                        (float *)w_out + S.out_off + (r0 + r) * S.nx, (float *)D, lane);
+                                        (float *)w_out + S.out_off + (r0 + r) * S.nx, D, lane);
                 } else {
                     for (int r = sb0 + warp; r < sb1; r += nwarps)
-                        row_queries<T>(S, ctrl, chain_off, ax, nx, a0, inv_step, xs + roff[r] - base,
+                        row_queries<T>(S, ctrl, chain_off, s_ax, nx, a0, inv_step, xs + roff[r] - base,
                                        dirs + roff[r] - base, roff[r + 1] - roff[r], ys[r], r0 + r, D, lane, w_out,
                                        chi_out, b_out);
                 }
@@ -692,10 +701,10 @@ __global__ void __launch_bounds__(1024) eval2d_kernel(const T *__restrict__ ctrl
                 const int r = sb0;
                 const T yr = ys[r];
                 for (int64_t i = threadIdx.x; i < S.nx; i += nthr) chi_row[i] = 0;
-                for (int64_t c0 = S.p_lo; c0 < S.p_hi; c0 += CHUNK) {
+                for (int64_t c0 = pA; c0 < pB; c0 += CHUNK) {
                     if (threadIdx.x == 0) ncross = 0;
                     __syncthreads();
-                    int64_t c1 = c0 + CHUNK < S.p_hi ? c0 + CHUNK : S.p_hi;
+                    int64_t c1 = c0 + CHUNK < pB ? c0 + CHUNK : pB;
                     for (int64_t p = c0 + threadIdx.x; p < c1; p += nthr) {
                         T ya = piece_y[2 * p], yb = piece_y[2 * p + 1];
                         T lo = ya < yb ? ya : yb, hi = ya < yb ? yb : ya;
@@ -715,7 +724,7 @@ __global__ void __launch_bounds__(1024) eval2d_kernel(const T *__restrict__ ctrl
                     __syncthreads();
                     int nc = ncross;
                     for (int64_t i = threadIdx.x; i < S.nx; i += nthr) {
-                        T xq = ax[i];
+                        T xq = s_ax[i];
                         int acc = 0;
                         for (int k = 0; k < nc; k++) acc += xs[k] > xq ? (int)dirs[k] : 0;
                         chi_row[i] += acc;
@@ -724,7 +733,7 @@ __global__ void __launch_bounds__(1024) eval2d_kernel(const T *__restrict__ ctrl
                 }
                 for (int64_t i = threadIdx.x; i < S.nx; i += nthr) {
                     int chi = chi_row[i];
-                    T A = chord_angles<T>(ctrl, chain_off, S, ax[i], yr, chi);
+                    T A = chord_angles<T>(ctrl, chain_off, S, s_ax[i], yr, chi);
                     store_w<T>(S, r0 + r, i, chi, A, w_out, chi_out, b_out);
                 }
                 __syncthreads();
@@ -743,12 +752,13 @@ __global__ void __launch_bounds__(1024) eval2d_kernel(const T *__restrict__ ctrl
 
 size_t eval2d_smem(int dtype, int64_t max_nx, int threads) {
     size_t off = dtype == GWN_F64 ? eval2d_fallback_off<double>(threads) : eval2d_fallback_off<float>(threads);
+    off += ((dtype == GWN_F64 ? 8 : 4) * (size_t)max_nx + 15) & ~(size_t)15;      // ax
     size_t per_warp = sizeof(int) * (size_t)eval2d_dstride((int)max_nx);
     size_t d = per_warp * (size_t)(threads / 32);
     return off + (d > sizeof(int) * (size_t)max_nx ? d : sizeof(int) * (size_t)max_nx);
 }
 
-cudaError_t launch_eval2d_items(const ChainSet &cs, const Set2D *d_sets, const int2 *d_items, const Set2D *single,
+cudaError_t launch_eval2d_items(const ChainSet &cs, const Set2D *d_sets, const int4 *d_items, const Set2D *single,
                                 int64_t n_items, unsigned long long *d_counter, int rows_per_item, int threads,
                                 int64_t max_nx, void *w_out, int32_t *chi_out, void *b_out, unsigned long long *cnt,
                                 int *status, int sm_count, cudaStream_t st) {

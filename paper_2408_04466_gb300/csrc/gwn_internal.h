@@ -109,6 +109,10 @@ struct ChainSet {
     int32_t *piece_chain = nullptr;
     int64_t *chain_piece_off = nullptr;  // device [n_chains + 1]
     std::vector<int64_t> h_chain_off, h_chain_piece_off;
+    // host, per piece (pieces of a chain ordered by their lowest y): that
+    // lowest y and the running maximum of the highest y over the chain's
+    // pieces so far, both rounded to the chain's precision
+    std::vector<double> h_piece_lo, h_piece_hmax;
 };
 
 // One 2D evaluation set: chains [c_lo, c_hi) (their pieces [p_lo, p_hi)) on
@@ -238,7 +242,7 @@ cudaError_t launch_eval2d_points(const ChainSet &cs, const QuerySrc &q, void *w_
 // max_nx columns, and the most one block may take (sm_103a opt-in limit)
 size_t eval2d_smem(int dtype, int64_t max_nx, int threads);
 constexpr size_t EVAL2D_SMEM_MAX = 227 * 1024;
-cudaError_t launch_eval2d_items(const ChainSet &cs, const Set2D *d_sets, const int2 *d_items, const Set2D *single,
+cudaError_t launch_eval2d_items(const ChainSet &cs, const Set2D *d_sets, const int4 *d_items, const Set2D *single,
                                 int64_t n_items,
                                 unsigned long long *d_counter, int rows_per_item, int threads, int64_t max_nx,
                                 void *w_out, int32_t *chi_out, void *b_out, unsigned long long *cnt, int *status,
