@@ -754,13 +754,34 @@ GWN_API gwn_status gwn_bezier2d_create(gwn_ctx *ctx, const void *ctrl, int dtype
         if (e == cudaSuccess) e = cudaMemcpy(cs.piece_yT, fy.data(), sizeof(float) * 2 * np, cudaMemcpyHostToDevice);
     }
     if (e == cudaSuccess) {        // per-piece records for the row kernel
+        // the piece [u0, u1] reparametrised to t in [0, 1], u = u0 + t h, in
+        // power form: for B(u) = c3 u^3 + c2 u^2 + c1 u + c0 (c0 = P0,
+        // c1 = 3 (P1 - P0), c2 = 3 (P2 - 2 P1 + P0), c3 = P3 - 3 P2 + 3 P1 - P0),
+        // B(u0 + t h) = a3 t^3 + a2 t^2 + a1 t + a0 with a3 = c3 h^3,
+        // a2 = (3 c3 u0 + c2) h^2, a1 = (3 c3 u0^2 + 2 c2 u0 + c1) h, a0 = B(u0).
+        // Record: x3 x2 x1 x0, y3 y2 y1 y(u0), 3 y3, 2 y2, y(u1), 0.
         std::vector<double> rec(12 * np, 0.0);
         for (int64_t q = 0; q < cs.n_pieces; q++) {
-            for (int k = 0; k < 8; k++) rec[12 * q + k] = P[2 * pseg[q] + k];
-            rec[12 * q + 8] = pu[2 * q];
-            rec[12 * q + 9] = pu[2 * q + 1];
-            rec[12 * q + 10] = py[2 * q];
-            rec[12 * q + 11] = py[2 * q + 1];
+            const double *cc = &P[2 * pseg[q]];
+            const double u0 = pu[2 * q], h = pu[2 * q + 1] - pu[2 * q];
+            double a[2][4];
+            for (int d = 0; d < 2; d++) {
+                const double p0 = cc[d], p1 = cc[2 + d], p2 = cc[4 + d], p3 = cc[6 + d];
+                const double c1 = 3.0 * (p1 - p0), c2 = 3.0 * (p2 - 2.0 * p1 + p0), c3 = p3 - 3.0 * p2 + 3.0 * p1 - p0;
+                a[d][0] = c3 * h * h * h;
+                a[d][1] = (3.0 * c3 * u0 + c2) * h * h;
+                a[d][2] = ((3.0 * c3 * u0 + 2.0 * c2) * u0 + c1) * h;
+                a[d][3] = ((c3 * u0 + c2) * u0 + c1) * u0 + p0;
+            }
+            double *r = &rec[12 * q];
+            for (int k = 0; k < 4; k++) r[k] = a[0][k];
+            r[4] = a[1][0];
+            r[5] = a[1][1];
+            r[6] = a[1][2];
+            r[7] = py[2 * q];            // y(u0), the value the half-open row test uses
+            r[8] = 3.0 * a[1][0];
+            r[9] = 2.0 * a[1][1];
+            r[10] = py[2 * q + 1];       // y(u1)
         }
         size_t bytes = esz * rec.size();
         e = cudaMalloc(&cs.piece_rec, bytes);

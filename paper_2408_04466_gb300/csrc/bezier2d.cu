@@ -70,56 +70,51 @@ template <> struct Num<double> {
     static __device__ __forceinline__ double fma_(double a, double b, double c) { return __fma_rn(a, b, c); }
 };
 
-template <typename T>
-__device__ __forceinline__ T bern(T p0, T p1, T p2, T p3, T u) {
-    T v = T(1) - u;
-    return v * v * v * p0 + T(3) * u * v * v * p1 + T(3) * u * u * v * p2 + u * u * u * p3;
-}
-template <typename T>
-__device__ __forceinline__ T dbern(T p0, T p1, T p2, T p3, T u) {
-    T v = T(1) - u;
-    return T(3) * (v * v * (p1 - p0) + T(2) * u * v * (p2 - p1) + u * u * (p3 - p2));
-}
+// Piece records (PC_FIELDS values in the chain's precision, written at
+// creation in float64 and rounded): the monotone piece [u0, u1] of a segment
+// reparametrised to t in [0, 1] (u = u0 + t (u1 - u0)) in power form,
+//   x(t) = ((r0 t + r1) t + r2) t + r3,   y(t) = ((r4 t + r5) t + r6) t + r7,
+// r7 = y(u0), r8 = 3 r4, r9 = 2 r5 (so y'(t) = (r8 t + r9) t + r6),
+// r10 = y(u1), r11 unused.  Local coefficients scale with the piece, so the
+// evaluation error is a few ulps of |y| rather than of the segment's size.
+constexpr int PC_FIELDS = 12;
 
-// x of the crossing of the monotone piece [u0, u1] of the segment with
-// control points c[0..7] (x0 y0 x1 y1 ...) with the row y = yr.
+// x of the crossing of the piece with record r and the row y = yr
+// (min(r7, r10) <= yr < max(r7, r10)): safeguarded Newton from the linear
+// guess, the bracket oriented so that g(lo) <= 0 < g(hi), g = y(t) - yr.
 template <typename T>
-__device__ T piece_root_xu(const T *c, T u0, T u1, T ya, T yb, T yr, int *iters_out, T *u_out);
-
-template <typename T>
-__device__ T piece_root_x(const T *c, T u0, T u1, T ya, T yb, T yr, int *iters_out) {
-    T u;
-    return piece_root_xu<T>(c, u0, u1, ya, yb, yr, iters_out, &u);
-}
-
-// the same, also returning the parameter of the root
-template <typename T>
-__device__ T piece_root_xu(const T *c, T u0, T u1, T ya, T yb, T yr, int *iters_out, T *u_out) {
-    // orient the bracket so that g(lo) <= 0 < g(hi) with g = y(u) - yr
-    T lo = u0, hi = u1;
-    bool inc = yb > ya;
-    if (!inc) { lo = u1; hi = u0; }
-    T yl = inc ? ya : yb, yh = inc ? yb : ya;
-    T u = lo + (hi - lo) * Num<T>::div(yr - yl, yh - yl);
+__device__ __forceinline__ T piece_root_rec(const T *r, T yr, int *iters_out) {
+    const T ya = r[7], yb = r[10];
+    const bool inc = yb > ya;
+    T lo = inc ? T(0) : T(1), hi = inc ? T(1) : T(0);
+    const T c0 = ya - yr;
+    T t = Num<T>::div(yr - ya, yb - ya);
     const T ytol = Num<T>::ytol * ((ya < T(0) ? -ya : ya) + (yb < T(0) ? -yb : yb));
     int it = 0;
     for (; it < Num<T>::max_iter; it++) {
-        T g = bern(c[1], c[3], c[5], c[7], u) - yr;
+        const T g = Num<T>::fma_(Num<T>::fma_(Num<T>::fma_(r[4], t, r[5]), t, r[6]), t, c0);
         if ((g < T(0) ? -g : g) <= ytol) break;     // the curve point is within ytol of the row
-        if (g < T(0)) lo = u; else hi = u;
-        T dg = dbern(c[1], c[3], c[5], c[7], u);
-        T un = u - Num<T>::div(g, dg);
-        T mn = lo < hi ? lo : hi, mx = lo < hi ? hi : lo;
-        if (!(un > mn && un < mx)) un = T(0.5) * (lo + hi);
-        T step = un - u;
-        u = un;
+        if (g < T(0)) lo = t; else hi = t;
+        const T dg = Num<T>::fma_(Num<T>::fma_(r[8], t, r[9]), t, r[6]);
+        T tn = t - Num<T>::div(g, dg);
+        const T mn = lo < hi ? lo : hi, mx = lo < hi ? hi : lo;
+        if (!(tn > mn && tn < mx)) tn = T(0.5) * (lo + hi);
+        const T step = tn - t;
+        t = tn;
         if ((step < T(0) ? -step : step) <= Num<T>::tol || (mx - mn) <= Num<T>::tol) break;
     }
     *iters_out = it;
-    *u_out = u;
-    return bern(c[0], c[2], c[4], c[6], u);
+    return Num<T>::fma_(Num<T>::fma_(Num<T>::fma_(r[0], t, r[1]), t, r[2]), t, r[3]);
 }
 
+// a piece record from global memory (16-byte aligned, read as 16-byte words)
+template <typename T>
+__device__ __forceinline__ void load_rec(const T *__restrict__ piece_rec, int64_t p, T *v) {
+    constexpr int W = PC_FIELDS * (int)sizeof(T) / 16;
+    const uint4 *rp = (const uint4 *)(piece_rec + (int64_t)PC_FIELDS * p);
+#pragma unroll
+    for (int m = 0; m < W; m++) ((uint4 *)v)[m] = rp[m];
+}
 
 constexpr int CHUNK = 1024;          // crossings per pass of the per-row fallback
 constexpr int MAX_ROWS = 256;        // rows per work item
@@ -131,7 +126,6 @@ constexpr int CAP = 4096;            // crossings binned per row sub-block
 //   rcur[MAX_ROWS + 1], ofs[threads], ra[threads], wsum[32] (int),
 //   dirs[CAP] (int8), then the item's column values ax[max_nx] (T), then per
 //   warp the difference array of the row queries (or the fallback's chi_row).
-constexpr int PC_FIELDS = 12;        // control points (8), u0, u1, y(u0), y(u1)
 template <typename T>
 __host__ __device__ constexpr size_t eval2d_fallback_off(int threads) {
     return ((sizeof(T) * (CAP + MAX_ROWS + (size_t)PC_FIELDS * threads) +
@@ -503,7 +497,6 @@ __device__ __forceinline__ void row_queries_f32(const float *__restrict__ ax, in
 // CHUNK crossings at a time.
 template <typename T>
 __global__ void __launch_bounds__(1024) eval2d_kernel(const T *__restrict__ ctrl, const int64_t *__restrict__ chain_off,
-                              const int64_t *__restrict__ piece_seg, const T *__restrict__ piece_u,
                               const T *__restrict__ piece_y, const T *__restrict__ piece_rec,
                               const Set2D *__restrict__ sets, const int4 *__restrict__ items, const Set2D single,
                               int64_t n_items,
@@ -636,12 +629,8 @@ __global__ void __launch_bounds__(1024) eval2d_kernel(const T *__restrict__ ctrl
                     __syncthreads();                 // the previous chunk is done with s_wsum, s_ofs, s_ra, s_pc
                     if (lane == 31) s_wsum[warp] = x;
                     if (n > 0) {                      // stage the piece for the threads that take its roots
-                        // (its record: 12 values, 16-byte aligned, read as 16-byte words)
-                        constexpr int W = PC_FIELDS * (int)sizeof(T) / 16;
-                        const uint4 *rp = (const uint4 *)(piece_rec + (int64_t)PC_FIELDS * p);
                         T v[PC_FIELDS];
-#pragma unroll
-                        for (int m = 0; m < W; m++) ((uint4 *)v)[m] = rp[m];
+                        load_rec<T>(piece_rec, p, v);
 #pragma unroll
                         for (int m = 0; m < PC_FIELDS; m++) s_pc[m * nthr + threadIdx.x] = v[m];
                     }
@@ -663,12 +652,12 @@ __global__ void __launch_bounds__(1024) eval2d_kernel(const T *__restrict__ ctrl
                             if (s_ofs[mid] <= k) lo = mid; else hi = mid - 1;
                         }
                         const int r = s_ra[lo] + (k - s_ofs[lo]);
-                        const T ya = s_pc[10 * nthr + lo], yb = s_pc[11 * nthr + lo];
-                        T c[8];
+                        T rec[PC_FIELDS - 1];
 #pragma unroll
-                        for (int m = 0; m < 8; m++) c[m] = s_pc[m * nthr + lo];
+                        for (int m = 0; m < PC_FIELDS - 1; m++) rec[m] = s_pc[m * nthr + lo];
+                        const T ya = rec[7], yb = rec[10];
                         int iters;
-                        const T xr = piece_root_x<T>(c, s_pc[8 * nthr + lo], s_pc[9 * nthr + lo], ya, yb, ys[r], &iters);
+                        const T xr = piece_root_rec<T>(rec, ys[r], &iters);
                         if (iters >= Num<T>::max_iter && status) atomicOr(status, ST_TIMEOUT);
                         nroots_thread += (unsigned long long)iters << 32 | 1ull;
                         const int slot = roff[r] - base + atomicAdd(&rcur[r], 1);
@@ -709,12 +698,10 @@ __global__ void __launch_bounds__(1024) eval2d_kernel(const T *__restrict__ ctrl
                         T ya = piece_y[2 * p], yb = piece_y[2 * p + 1];
                         T lo = ya < yb ? ya : yb, hi = ya < yb ? yb : ya;
                         if (!(lo <= yr && yr < hi)) continue;
-                        const T *cp = ctrl + 2 * piece_seg[p];
-                        T c[8];
-#pragma unroll
-                        for (int k = 0; k < 8; k++) c[k] = cp[k];
+                        T rec[PC_FIELDS];
+                        load_rec<T>(piece_rec, p, rec);
                         int iters;
-                        T x = piece_root_x<T>(c, piece_u[2 * p], piece_u[2 * p + 1], ya, yb, yr, &iters);
+                        T x = piece_root_rec<T>(rec, yr, &iters);
                         if (iters >= Num<T>::max_iter && status) atomicOr(status, ST_TIMEOUT);
                         nroots_thread += (unsigned long long)iters << 32 | 1ull;
                         int slot = atomicAdd(&ncross, 1);
@@ -786,13 +773,13 @@ cudaError_t launch_eval2d_items(const ChainSet &cs, const Set2D *d_sets, const i
     if (blocks > n_items) blocks = n_items;
     if (cs.dtype == GWN_F64) {
         eval2d_kernel<double><<<(unsigned)blocks, threads, smem, st>>>(
-            (const double *)cs.ctrl, cs.chain_off, cs.piece_seg, (const double *)cs.piece_uT,
+            (const double *)cs.ctrl, cs.chain_off,
             (const double *)cs.piece_yT, (const double *)cs.piece_rec, d_sets, d_items, s0, n_items, d_counter,
             rows_per_item, (double *)w_out,
             chi_out, (double *)b_out, cnt, status, (int)max_nx);
     } else {
         eval2d_kernel<float><<<(unsigned)blocks, threads, smem, st>>>(
-            (const float *)cs.ctrl, cs.chain_off, cs.piece_seg, (const float *)cs.piece_uT,
+            (const float *)cs.ctrl, cs.chain_off,
             (const float *)cs.piece_yT, (const float *)cs.piece_rec, d_sets, d_items, s0, n_items, d_counter,
             rows_per_item, (float *)w_out,
             chi_out, (float *)b_out, cnt, status, (int)max_nx);
@@ -820,7 +807,7 @@ __device__ __forceinline__ int bucket_of_dev(T y, T y0, T inv_h, int nb) {
 template <typename T>
 __global__ void __launch_bounds__(256) eval2d_points_kernel(
     const T *__restrict__ ctrl, const int64_t *__restrict__ chain_off, int64_t n_chains,
-    const int64_t *__restrict__ piece_seg, const T *__restrict__ piece_u, const T *__restrict__ piece_y,
+    const T *__restrict__ piece_y, const T *__restrict__ piece_rec,
     const T *__restrict__ piece_x, const int32_t *__restrict__ bucket_off, const int32_t *__restrict__ bucket_idx,
     int nb, T y0, T inv_h, const T *__restrict__ pts, int64_t n, T *__restrict__ w_out, int32_t *__restrict__ chi_out,
     T *__restrict__ b_out, unsigned long long *cnt, int *status) {
@@ -837,12 +824,10 @@ __global__ void __launch_bounds__(256) eval2d_points_kernel(
         const int dir = yb > ya ? 1 : -1;
         if (px < piece_x[2 * p]) { chi += dir; continue; }      // crossing certainly to the right
         if (px >= piece_x[2 * p + 1]) continue;                 // certainly not to the right
-        const T *cp = ctrl + 2 * piece_seg[p];
-        T c[8];
-#pragma unroll
-        for (int k = 0; k < 8; k++) c[k] = cp[k];
+        T rec[PC_FIELDS];
+        load_rec<T>(piece_rec, p, rec);
         int iters;
-        T x = piece_root_x<T>(c, piece_u[2 * p], piece_u[2 * p + 1], ya, yb, py, &iters);
+        T x = piece_root_rec<T>(rec, py, &iters);
         if (iters >= Num<T>::max_iter && status) atomicOr(status, ST_TIMEOUT);
         if (x > px) chi += dir;
         nroots++;
@@ -864,16 +849,28 @@ cudaError_t launch_eval2d_points(const ChainSet &cs, const QuerySrc &q, void *w_
     if (blocks > 0x7fffffff) return cudaErrorInvalidValue;
     if (cs.dtype == GWN_F64)
         eval2d_points_kernel<double><<<(unsigned)blocks, 256, 0, st>>>(
-            (const double *)cs.ctrl, cs.chain_off, cs.n_chains, cs.piece_seg, (const double *)cs.piece_uT,
-            (const double *)cs.piece_yT, (const double *)cs.piece_xT, cs.bucket_off, cs.bucket_idx, cs.n_buckets,
+            (const double *)cs.ctrl, cs.chain_off, cs.n_chains, (const double *)cs.piece_yT,
+            (const double *)cs.piece_rec, (const double *)cs.piece_xT, cs.bucket_off, cs.bucket_idx, cs.n_buckets,
             cs.bucket_y0, cs.bucket_inv_h, q.pts64, q.n, (double *)w_out, chi_out, (double *)b_out, cnt, status);
     else
         eval2d_points_kernel<float><<<(unsigned)blocks, 256, 0, st>>>(
-            (const float *)cs.ctrl, cs.chain_off, cs.n_chains, cs.piece_seg, (const float *)cs.piece_uT,
-            (const float *)cs.piece_yT, (const float *)cs.piece_xT, cs.bucket_off, cs.bucket_idx, cs.n_buckets,
+            (const float *)cs.ctrl, cs.chain_off, cs.n_chains, (const float *)cs.piece_yT,
+            (const float *)cs.piece_rec, (const float *)cs.piece_xT, cs.bucket_off, cs.bucket_idx, cs.n_buckets,
             (float)cs.bucket_y0, (float)cs.bucket_inv_h, q.pts, q.n, (float *)w_out, chi_out, (float *)b_out, cnt,
             status);
     return cudaGetLastError();
+}
+
+// cubic Bernstein polynomial and its derivative (comparator quadrature)
+template <typename T>
+__device__ __forceinline__ T bern(T p0, T p1, T p2, T p3, T u) {
+    T v = T(1) - u;
+    return v * v * v * p0 + T(3) * u * v * v * p1 + T(3) * u * u * v * p2 + u * u * u * p3;
+}
+template <typename T>
+__device__ __forceinline__ T dbern(T p0, T p1, T p2, T p3, T u) {
+    T v = T(1) - u;
+    return T(3) * (v * v * (p1 - p0) + T(2) * u * v * (p2 - p1) + u * u * (p3 - p2));
 }
 
 // ---------------------------------------------------------------------------
