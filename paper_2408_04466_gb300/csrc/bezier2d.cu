@@ -25,10 +25,11 @@
 // chain's precision.
 //
 // Work: a persistent kernel pops work items (set, block of rows) from an
-// atomic counter.  Per row, pieces are scanned in chunks of at most
-// CHUNK pieces (each contributes at most one crossing), crossings are
-// collected in shared memory, and every query of the row adds the signed
-// crossings to its right.  The epilogue adds the chord terms and writes w.
+// atomic counter.  An item counts the crossings of its rows, finds each
+// (piece, row) root with the work spread over the whole block, bins the
+// roots by row and column in shared memory, and then one warp per row turns
+// the binned crossings into each query's count of crossings to its right,
+// adds the chord terms and writes w (details at eval2d_kernel).
 #include <string.h>
 
 #include "gwn_internal.h"
@@ -293,8 +294,8 @@ __device__ __forceinline__ void store_w(const Set2D &S, int64_t row, int64_t i, 
 // per-warp difference-array stride: the grid width rounded up to 256 columns
 __host__ __device__ constexpr int eval2d_dstride(int max_nx) { return (max_nx + 255) & ~255; }
 
-// The queries of one grid row, by one warp.  The row's nk crossings (x, dir)
-// are binned by column: crossing k lies to the right of the queries
+// The queries of one grid row, by one warp.  The row's nk crossings come as
+// (column, direction) pairs: crossing k lies to the right of the queries
 // i < j_k (j_k = first column with x >= x_k), so D[j_k - 1] += dir_k and
 //   chi(i) = sum_{j >= i} D[j].
 // Lane l takes 8 consecutive columns of every 256: local suffix sums in
@@ -304,7 +305,7 @@ __host__ __device__ constexpr int eval2d_dstride(int max_nx) { return (max_nx + 
 template <typename T>
 __device__ __forceinline__ void row_queries(const Set2D &S, const T *__restrict__ ctrl,
                                             const int64_t *__restrict__ chain_off, const T *__restrict__ ax,
-                                            int nx, T a0, T inv_step, const T *xs, const signed char *dirs, int nk,
+                                            int nx, const int *xj, const signed char *dirs, int nk,
                                             T yr, int64_t row, int *D, int lane, T *w_out, int32_t *chi_out,
                                             T *b_out) {
     const unsigned FULL = 0xffffffffu;
@@ -316,7 +317,7 @@ __device__ __forceinline__ void row_queries(const Set2D &S, const T *__restrict_
     }
     __syncwarp();
     for (int k = lane; k < nk; k += 32) {
-        int j = lower_bound_cols(ax, nx, a0, inv_step, xs[k]);
+        const int j = xj[k];
         if (j > 0) atomicAdd(&D[j - 1], (int)dirs[k]);
     }
     __syncwarp();
@@ -394,8 +395,8 @@ __device__ __forceinline__ float small_int_to_float(int n) {
 // conversion unit (exact: a row holds at most CAP crossings) and the chord
 // terms of two columns at a time in packed f32x2 arithmetic.  Rounds exactly
 // as the generic path does.  (spx, spy), (epx, epy): the chain's end points.
-__device__ __forceinline__ void row_queries_f32(const float *__restrict__ ax, int nx, float a0, float inv_step,
-                                                const float *xs, const signed char *dirs, int nk, float yr,
+__device__ __forceinline__ void row_queries_f32(const float *__restrict__ ax, int nx,
+                                                const int *xj, const signed char *dirs, int nk, float yr,
                                                 float spx, float spy, float epx, float epy,
                                                 float *__restrict__ wrow, int *D, int lane) {
     const unsigned FULL = 0xffffffffu;
@@ -407,7 +408,7 @@ __device__ __forceinline__ void row_queries_f32(const float *__restrict__ ax, in
     }
     __syncwarp();
     for (int k = lane; k < nk; k += 32) {
-        int j = lower_bound_cols(ax, nx, a0, inv_step, xs[k]);
+        const int j = xj[k];
         if (j > 0) atomicAdd(&D[j - 1], (int)dirs[k]);
     }
     __syncwarp();
@@ -472,25 +473,29 @@ __device__ __forceinline__ void row_queries_f32(const float *__restrict__ ax, in
     __syncwarp();
 }
 
-// Work items are (set, block of rows).  An item finds the rows each of the
-// set's pieces crosses: a piece with end values y0, y1 is crossed by row r
-// iff min <= y_r < max, and since the row values are non-decreasing those
-// rows form one range [ra, rb), found by binary search in the item's row
-// values.  The per-row crossing counts come from a difference array (+1 at
-// ra, -1 at rb) and one scan, so the counting pass costs O(1) per piece
-// whatever the number of rows it spans.
+// Work items are (set, block of rows[, run of pieces]).  An item finds the
+// rows each of the set's pieces crosses: a piece with end values y0, y1 is
+// crossed by row r iff min <= y_r < max, and since the row values are
+// non-decreasing those rows form one range [ra, rb), found from the row
+// spacing and corrected against the item's row values.  The per-row crossing
+// counts come from a difference array (+1 at ra, -1 at rb) and one scan, so
+// the counting pass costs O(1) per piece whatever the number of rows it
+// spans.  A work list gives each item the run of pieces that can reach its
+// rows (pieces are ordered by their lowest y per chain); a single set scans
+// all of its pieces.
 //
 // Roots: the (piece, row) pairs of a chunk of blockDim pieces are numbered
 // by a block-wide prefix sum of the pieces' row counts, and every thread
 // takes every blockDim-th pair (its owner piece found by binary search in the
 // prefix sums), so a piece spanning many rows is spread over many threads
-// instead of serialising one.  Each root is binned by row in shared memory.
+// instead of serialising one.  The chunk's pieces are staged in shared
+// memory by their owners.  Each root x_k is turned into its column j_k =
+// first grid column with x >= x_k and binned by row.
 //
-// Queries: one warp per row.  Every crossing x_k of the row finds its column
-// j_k = first grid column with x >= x_k and adds its direction to a per-warp
-// difference array D[j_k]; a suffix sum over the columns then gives each
+// Queries: one warp per row.  Every crossing adds its direction to a per-warp
+// difference array D[j_k - 1]; a suffix sum over the columns then gives each
 // query i its signed count of crossings to the right,
-//   chi(i) = sum_{k : x_k > xq_i} dir_k = sum_{j > i} D[j],
+//   chi(i) = sum_{k : x_k > xq_i} dir_k = sum_{j >= i} D[j],
 // in O(1) per query.  The chord terms are added and w is stored (coalesced).
 // The item's rows are processed in sub-blocks whose crossings fit in CAP; a
 // single row with more than CAP crossings falls back to scanning the pieces
@@ -505,7 +510,8 @@ __global__ void __launch_bounds__(1024) eval2d_kernel(const T *__restrict__ ctrl
                               int *status, int max_nx) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nthr = blockDim.x;
-    T *xs = (T *)smem_raw;                                    // CAP crossings
+    T *xs = (T *)smem_raw;                                    // CAP crossings (x; the per-row fallback)
+    int *xj = (int *)smem_raw;                                // CAP crossings (their columns; binned rows)
     T *ys = xs + CAP;                                         // MAX_ROWS row values
     T *s_pc = ys + MAX_ROWS;                                  // PC_FIELDS x nthr: staged piece data
     int *roff = (int *)(s_pc + PC_FIELDS * nthr);             // MAX_ROWS + 1 offsets
@@ -661,7 +667,7 @@ __global__ void __launch_bounds__(1024) eval2d_kernel(const T *__restrict__ ctrl
                         if (iters >= Num<T>::max_iter && status) atomicOr(status, ST_TIMEOUT);
                         nroots_thread += (unsigned long long)iters << 32 | 1ull;
                         const int slot = roff[r] - base + atomicAdd(&rcur[r], 1);
-                        xs[slot] = xr;
+                        xj[slot] = lower_bound_cols(s_ax, nx, a0, inv_step, xr);   // its column
                         dirs[slot] = yb > ya ? 1 : -1;
                     }
                 }
@@ -673,13 +679,13 @@ __global__ void __launch_bounds__(1024) eval2d_kernel(const T *__restrict__ ctrl
                     const float *ep = (const float *)ctrl + 2 * (chain_off[S.c_lo + 1] - 1);
                     const float spx = sp[0], spy = sp[1], epx = ep[0], epy = ep[1];
                     for (int r = sb0 + warp; r < sb1; r += nwarps)
-                        row_queries_f32((const float *)s_ax, nx, (float)a0, (float)inv_step,
-                                        (const float *)xs + roff[r] - base, dirs + roff[r] - base,
+                        row_queries_f32((const float *)s_ax, nx,
+                                        xj + roff[r] - base, dirs + roff[r] - base,
                                         roff[r + 1] - roff[r], (float)ys[r], spx, spy, epx, epy,
                                         (float *)w_out + S.out_off + (r0 + r) * S.nx, D, lane);
                 } else {
                     for (int r = sb0 + warp; r < sb1; r += nwarps)
-                        row_queries<T>(S, ctrl, chain_off, s_ax, nx, a0, inv_step, xs + roff[r] - base,
+                        row_queries<T>(S, ctrl, chain_off, s_ax, nx, xj + roff[r] - base,
                                        dirs + roff[r] - base, roff[r + 1] - roff[r], ys[r], r0 + r, D, lane, w_out,
                                        chi_out, b_out);
                 }
