@@ -16,6 +16,10 @@ on first use and wraps it with ctypes.  Functions and the passages they follow:
 * ``bterm3d``        boundary term relative to d (Lemma 1, Lemma 2, and the
                      closure argument of the proof in Appendix A).
 * ``w3d_oneshot``    chi3d + bterm3d.
+* ``w3d_alg1``       Algorithm 1 in 3D, literally: arrangement of the
+                     projected boundary on the unit sphere, region areas,
+                     one ray in the largest region, counts propagated across
+                     the arcs (Lemma 2), area-weighted sum (tiny inputs).
 * ``grad3d_vos``     gradient of the 3D definition (chain rule on the
                      per-triangle solid angle).
 * ``w2d_quad``       2D definition, adaptive Gauss-Kronrod per segment
@@ -79,6 +83,7 @@ def _load():
                 "oracle_chain_ray_crossings": (I, [P, I64, P, P]),
                 "oracle_dist3d": (None, [P, P, I64, P, I64, P, I]),
                 "oracle_dist2d": (None, [P, I64, P, I64, P, I]),
+                "oracle_w3d_alg1": (I, [P, I64, P, I64, P, P, P]),
             }
             for name, (res, args) in sigs.items():
                 fn = getattr(lib, name)
@@ -163,6 +168,26 @@ def w3d_oneshot(V, F, P, d, threads: int | None = None, edges=None):
     chi = chi3d(V, F, P, d, threads)
     B = bterm3d(V, edges, P, d, threads)
     return chi + B, chi, B
+
+
+def w3d_alg1(V, F, P):
+    """Algorithm 1 in 3D by a spherical arrangement, one query at a time
+    (tiny, generic inputs).  Returns (w, info) with info[q] = (regions, area
+    of the largest region, its crossing count); raises on degenerate input."""
+    V = _f32(V, 3)
+    F = _i32(F).reshape(-1, 3)
+    P = _f32(P, 3).reshape(-1, 3)
+    w = np.empty(len(P), np.float64)
+    info = np.zeros((len(P), 3), np.float64)
+    lib = _load()
+    for q in range(len(P)):
+        out = C.c_double(0.0)
+        rc = lib.oracle_w3d_alg1(_ptr(V), len(V), _ptr(F), len(F), _ptr(P[q]), C.byref(out),
+                                 _ptr(info[q]))
+        if rc != 0:
+            raise ValueError(f"w3d_alg1: query {q}: status {rc}")
+        w[q] = out.value
+    return w, info
 
 
 def grad3d_vos(V, F, P, gw=None, want_p=True, want_V=True, threads: int | None = None):

@@ -24,6 +24,10 @@
  *   - 2D one-shot by Algorithm 1 (project the boundary points on the circle,
  *     two regions, one ray in the largest region, pairwise difference, sum).
  *   - 2D closed form relative to the +x ray (chord closure).
+ *   - 3D one-shot by Algorithm 1 literally (arrangement of the projected
+ *     boundary on the unit sphere, region areas, one ray in the largest
+ *     region, counts propagated across the arcs by Lemma 2, area-weighted
+ *     sum of Eq. wn_discrete_sum), for tiny inputs.
  */
 #include <math.h>
 #include <pthread.h>
@@ -1091,4 +1095,366 @@ ORACLE_API void oracle_dist2d(const double *ctrl, int64_t nseg, const double *P,
                               double *out, int nthreads) {
     dist2_ctx c = {ctrl, nseg, P, out};
     parallel_for(nq, nthreads, dist2_range, &c);
+}
+
+/* ======================================================================== */
+/* 3D Algorithm 1 by a spherical arrangement (tiny inputs)                  */
+/* ======================================================================== */
+/* The one-shot algorithm as the paper states it (Algorithm 1, with the
+ * region structure of Lemma 1 and Lemma 2 and the discrete sum of
+ * Eq. wn_discrete_sum): project the boundary of M onto the unit sphere around
+ * p (each boundary edge A->B becomes the minor great-circle arc a->b), build
+ * the arrangement of these arcs, take the area of every region, shoot ONE ray
+ * into the largest region to get its crossing count, propagate the counts to
+ * all regions across the arcs (Lemma 2), and return
+ *     w(p) = (1/4 pi) sum_i Area(A_i) chi_i.
+ * It is a third, independent evaluation (no boundary-term formula) used to
+ * pin the other two on tiny inputs.
+ *
+ * Details of this implementation:
+ *   - arrangement: all pairwise proper intersections of the arcs (float64),
+ *     each arc split at its intersections; the planar map is a half-edge
+ *     structure whose faces are the cycles of next(h) = the out-edge at the
+ *     head of h immediately clockwise (seen from outside) from the reverse of
+ *     h, so every face lies on the left of its half-edges;
+ *   - separate components of the projected boundary (several loops whose
+ *     images do not meet) are joined by arcs of weight zero, across which
+ *     chi does not change, so every region is bounded by one cycle;
+ *   - area of a region from its corners (Gauss-Bonnet for a geodesic
+ *     polygon): A = 2 pi - sum_i (pi - alpha_i), alpha_i the interior angle;
+ *     the printed formula in the implementation section has the sign of the
+ *     corner term reversed (it gives the complement), so the standard form is
+ *     used;
+ *   - across a boundary arc a->b of multiplicity m, chi on its left exceeds
+ *     chi on its right by m: a ray just on the triangle's side of the arc
+ *     hits the triangle next to edge A->B and the hit counts sign(d . n) =
+ *     sign(n . (A - p)), while the triangle's image lies on the left of a->b
+ *     exactly when n . (A - p) > 0 (both cases give +m);
+ *   - the ray into the largest region starts at the midpoint of its longest
+ *     side, offset into the region by a small angle checked to cross no arc,
+ *     and its direction rounded to float32 for the exact crossing count.
+ * Inputs must be generic: no two arcs on one great circle, no endpoint
+ * antipodal to another, no three arcs through one point.
+ * Returns 0, or -1 (degenerate input), -2 (inconsistent arrangement),
+ * -3 (out of memory). */
+typedef struct { int a, b, w; } sarc_t;
+typedef struct { int arc, other; double t; int vid; } sxing_t;
+typedef struct { int u, v, w; } spiece_t;
+
+static void cross3d(const double *a, const double *b, double *o) {
+    o[0] = a[1] * b[2] - a[2] * b[1];
+    o[1] = a[2] * b[0] - a[0] * b[2];
+    o[2] = a[0] * b[1] - a[1] * b[0];
+}
+static double dot3d(const double *a, const double *b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+static int normalize3d(double *a) {
+    double n = sqrt(dot3d(a, a));
+    if (!(n > 0.0)) return -1;
+    a[0] /= n; a[1] /= n; a[2] /= n;
+    return 0;
+}
+/* angle from a to b along the great circle (both unit) */
+static double arc_angle(const double *a, const double *b) {
+    double c[3];
+    cross3d(a, b, c);
+    return atan2(sqrt(dot3d(c, c)), dot3d(a, b));
+}
+/* x (unit) strictly inside the minor arc a->b (n = a x b) */
+static int on_minor_arc(const double *a, const double *b, const double *n, const double *x) {
+    double c1[3], c2[3];
+    cross3d(a, x, c1);
+    cross3d(x, b, c2);
+    return dot3d(c1, n) > 0.0 && dot3d(c2, n) > 0.0;
+}
+/* proper intersection of minor arcs (a, b) and (c, d); 1 and the point in x */
+static int arcs_cross(const double *a, const double *b, const double *c, const double *d, double *x, int *degen) {
+    double n1[3], n2[3], s[3];
+    cross3d(a, b, n1);
+    cross3d(c, d, n2);
+    cross3d(n1, n2, s);
+    if (sqrt(dot3d(s, s)) < 1e-14 * sqrt(dot3d(n1, n1) * dot3d(n2, n2))) { *degen = 1; return 0; }
+    normalize3d(s);
+    for (int k = 0; k < 2; k++) {
+        double y[3] = {k ? -s[0] : s[0], k ? -s[1] : s[1], k ? -s[2] : s[2]};
+        if (on_minor_arc(a, b, n1, y) && on_minor_arc(c, d, n2, y)) {
+            memcpy(x, y, sizeof(y));
+            return 1;
+        }
+    }
+    return 0;
+}
+/* tangent angle at x (unit) of the great circle toward y, in a frame at x */
+static double tangent_angle(const double *x, const double *y) {
+    double e1[3], e2[3], ax[3] = {1.0, 0.0, 0.0};
+    if (fabs(x[0]) > 0.6) { ax[0] = 0.0; ax[1] = 1.0; }
+    cross3d(x, ax, e1);
+    normalize3d(e1);
+    cross3d(x, e1, e2);
+    double t[3], xy = dot3d(x, y);
+    for (int k = 0; k < 3; k++) t[k] = y[k] - xy * x[k];
+    return atan2(dot3d(t, e2), dot3d(t, e1));
+}
+
+static int uf_find(int *par, int i) {
+    while (par[i] != i) { par[i] = par[par[i]]; i = par[i]; }
+    return i;
+}
+
+static int cmp_xing(const void *x, const void *y) {
+    const sxing_t *a = (const sxing_t *)x, *b = (const sxing_t *)y;
+    if (a->arc != b->arc) return a->arc < b->arc ? -1 : 1;
+    return a->t < b->t ? -1 : (a->t > b->t ? 1 : 0);
+}
+
+typedef struct { int h; double ang; } sout_t;
+static int cmp_out(const void *x, const void *y) {
+    const sout_t *a = (const sout_t *)x, *b = (const sout_t *)y;
+    return a->ang < b->ang ? -1 : (a->ang > b->ang ? 1 : 0);
+}
+
+ORACLE_API int oracle_w3d_alg1(const float *V, int64_t nv, const int32_t *F, int64_t nf, const float *p,
+                               double *w_out, double *info) {
+    (void)nv;
+    int rc = 0;
+    int32_t *src = NULL, *dst = NULL, *mul = NULL, *vmap = NULL, *par = NULL, *vis = NULL;
+    double *pts = NULL, *area = NULL;
+    sarc_t *arcs = NULL;
+    sxing_t *xs = NULL;
+    spiece_t *pc = NULL;
+    int *hnext = NULL, *hface = NULL, *ostart = NULL, *ocnt = NULL, *chi = NULL, *queue = NULL;
+    sout_t *outs = NULL;
+    int64_t ncap = 3 * (nf > 0 ? nf : 1);
+    src = (int32_t *)malloc(sizeof(int32_t) * ncap);
+    dst = (int32_t *)malloc(sizeof(int32_t) * ncap);
+    mul = (int32_t *)malloc(sizeof(int32_t) * ncap);
+    if (!src || !dst || !mul) { rc = -3; goto done; }
+    int64_t ne = oracle_boundary_edges(F, nf, src, dst, mul);
+    if (ne < 0) { rc = -3; goto done; }
+    const double P3[3] = {p[0], p[1], p[2]};
+    const double fourpi = 4.0 * M_PI;
+    if (ne == 0) {
+        /* closed: one region, the whole sphere; chi of any ray */
+        float d[3] = {0.48f, 0.6f, 0.64f};
+        int c = 0;
+        for (int64_t t = 0; t < nf; t++)
+            c += tri_crossing(V + 3 * (int64_t)F[3 * t], V + 3 * (int64_t)F[3 * t + 1], V + 3 * (int64_t)F[3 * t + 2],
+                              p, d);
+        *w_out = (double)c;
+        if (info) { info[0] = 1; info[1] = fourpi; info[2] = c; }
+        goto done;
+    }
+    /* 1. projected boundary vertices (one point per mesh vertex) */
+    int64_t nvm = 0;
+    for (int64_t e = 0; e < ne; e++) { if (src[e] + 1 > nvm) nvm = src[e] + 1; if (dst[e] + 1 > nvm) nvm = dst[e] + 1; }
+    vmap = (int32_t *)malloc(sizeof(int32_t) * nvm);
+    if (!vmap) { rc = -3; goto done; }
+    for (int64_t i = 0; i < nvm; i++) vmap[i] = -1;
+    int npt = 0;
+    for (int64_t e = 0; e < ne; e++) {
+        if (vmap[src[e]] < 0) vmap[src[e]] = npt++;
+        if (vmap[dst[e]] < 0) vmap[dst[e]] = npt++;
+    }
+    int narc_b = (int)ne, ncomp_max = npt;
+    int pt_cap = npt + 4 * (narc_b + ncomp_max) * (narc_b + ncomp_max) + 16;
+    pts = (double *)malloc(sizeof(double) * 3 * pt_cap);
+    arcs = (sarc_t *)malloc(sizeof(sarc_t) * (narc_b + ncomp_max));
+    par = (int32_t *)malloc(sizeof(int32_t) * npt);
+    if (!pts || !arcs || !par) { rc = -3; goto done; }
+    for (int64_t i = 0; i < nvm; i++) {
+        if (vmap[i] < 0) continue;
+        double *x = pts + 3 * vmap[i];
+        for (int k = 0; k < 3; k++) x[k] = (double)V[3 * i + k] - P3[k];
+        if (normalize3d(x)) { rc = -1; goto done; }         /* p on a boundary vertex */
+    }
+    int narc = 0;
+    for (int64_t e = 0; e < ne; e++) {
+        arcs[narc].a = vmap[src[e]]; arcs[narc].b = vmap[dst[e]]; arcs[narc].w = mul[e];
+        if (dot3d(pts + 3 * arcs[narc].a, pts + 3 * arcs[narc].b) < -1.0 + 1e-12) { rc = -1; goto done; }
+        narc++;
+    }
+    /* 2. join separate components with arcs of weight zero */
+    for (int i = 0; i < npt; i++) par[i] = i;
+    for (int i = 0; i < narc; i++) {
+        int ra = uf_find(par, arcs[i].a), rb = uf_find(par, arcs[i].b);
+        if (ra != rb) par[ra] = rb;
+    }
+    int root0 = uf_find(par, 0);
+    for (int i = 1; i < npt; i++) {
+        int ri = uf_find(par, i);
+        if (ri == root0) continue;
+        /* bridge from point 0 to the first point of this component that is not antipodal to it */
+        int j = -1;
+        for (int k = i; k < npt; k++)
+            if (uf_find(par, k) == ri && dot3d(pts, pts + 3 * k) > -1.0 + 1e-6) { j = k; break; }
+        if (j < 0) { rc = -1; goto done; }
+        arcs[narc].a = 0; arcs[narc].b = j; arcs[narc].w = 0;
+        narc++;
+        par[ri] = root0;
+    }
+    /* 3. pairwise proper intersections */
+    int xcap = 2 * narc * narc + 2;
+    xs = (sxing_t *)malloc(sizeof(sxing_t) * xcap);
+    if (!xs) { rc = -3; goto done; }
+    int nx = 0;
+    for (int i = 0; i < narc; i++)
+        for (int j = i + 1; j < narc; j++) {
+            const sarc_t *A = &arcs[i], *B = &arcs[j];
+            if (A->a == B->a || A->a == B->b || A->b == B->a || A->b == B->b) continue;
+            double x[3];
+            int degen = 0;
+            if (arcs_cross(pts + 3 * A->a, pts + 3 * A->b, pts + 3 * B->a, pts + 3 * B->b, x, &degen)) {
+                if (npt >= pt_cap) { rc = -3; goto done; }
+                int vid = npt++;
+                memcpy(pts + 3 * vid, x, sizeof(x));
+                xs[nx].arc = i; xs[nx].other = j; xs[nx].t = arc_angle(pts + 3 * A->a, x); xs[nx].vid = vid; nx++;
+                xs[nx].arc = j; xs[nx].other = i; xs[nx].t = arc_angle(pts + 3 * B->a, x); xs[nx].vid = vid; nx++;
+            } else if (degen) { rc = -1; goto done; }
+        }
+    qsort(xs, (size_t)nx, sizeof(sxing_t), cmp_xing);
+    /* 4. arc pieces */
+    int npc = 0, pcap = narc + nx;
+    pc = (spiece_t *)malloc(sizeof(spiece_t) * pcap);
+    if (!pc) { rc = -3; goto done; }
+    for (int i = 0, k = 0; i < narc; i++) {
+        int prev = arcs[i].a;
+        while (k < nx && xs[k].arc == i) {
+            pc[npc].u = prev; pc[npc].v = xs[k].vid; pc[npc].w = arcs[i].w; npc++;
+            prev = xs[k].vid;
+            k++;
+        }
+        pc[npc].u = prev; pc[npc].v = arcs[i].b; pc[npc].w = arcs[i].w; npc++;
+    }
+    /* 5. half-edges (2k: u->v, 2k+1: v->u), out-edges sorted by tangent angle */
+    int nh = 2 * npc;
+    hnext = (int *)malloc(sizeof(int) * nh);
+    hface = (int *)malloc(sizeof(int) * nh);
+    ostart = (int *)calloc((size_t)npt + 1, sizeof(int));
+    ocnt = (int *)calloc((size_t)npt, sizeof(int));
+    outs = (sout_t *)malloc(sizeof(sout_t) * nh);
+    int *hpos = (int *)malloc(sizeof(int) * nh);
+    if (!hnext || !hface || !ostart || !ocnt || !outs || !hpos) { free(hpos); rc = -3; goto done; }
+#define H_ORIG(h) (((h) & 1) ? pc[(h) >> 1].v : pc[(h) >> 1].u)
+#define H_DEST(h) (((h) & 1) ? pc[(h) >> 1].u : pc[(h) >> 1].v)
+    for (int h = 0; h < nh; h++) ostart[H_ORIG(h) + 1]++;
+    for (int i = 0; i < npt; i++) ostart[i + 1] += ostart[i];
+    for (int h = 0; h < nh; h++) {
+        int o = H_ORIG(h);
+        int slot = ostart[o] + ocnt[o]++;
+        outs[slot].h = h;
+        outs[slot].ang = tangent_angle(pts + 3 * o, pts + 3 * H_DEST(h));
+    }
+    for (int i = 0; i < npt; i++) {
+        qsort(outs + ostart[i], (size_t)(ostart[i + 1] - ostart[i]), sizeof(sout_t), cmp_out);
+        for (int s = ostart[i]; s < ostart[i + 1]; s++) hpos[outs[s].h] = s;
+    }
+    /* next(h): at the head v of h, the out-edge just clockwise from twin(h) */
+    for (int h = 0; h < nh; h++) {
+        int v = H_DEST(h), tw = h ^ 1;
+        int s = hpos[tw], lo = ostart[v], n = ostart[v + 1] - ostart[v];
+        int sp = lo + ((s - lo) - 1 + n) % n;
+        hnext[h] = outs[sp].h;
+    }
+    /* 6. faces and their areas */
+    for (int h = 0; h < nh; h++) hface[h] = -1;
+    int nfc = 0;
+    area = (double *)malloc(sizeof(double) * nh);
+    if (!area) { free(hpos); rc = -3; goto done; }
+    for (int h0 = 0; h0 < nh; h0++) {
+        if (hface[h0] >= 0) continue;
+        double turn = 0.0;
+        int h = h0, guard = 0;
+        do {
+            hface[h] = nfc;
+            int hn = hnext[h], v = H_DEST(h);
+            /* interior angle at v: from the outgoing direction counter-clockwise to the reversed incoming one */
+            double a_out = outs[hpos[hn]].ang, a_in = outs[hpos[h ^ 1]].ang;
+            double alpha = fmod(a_in - a_out + 4.0 * M_PI, 2.0 * M_PI);
+            if (alpha <= 0.0) alpha += 2.0 * M_PI;
+            turn += M_PI - alpha;
+            (void)v;
+            h = hn;
+            if (++guard > nh + 1) { free(hpos); rc = -2; goto done; }
+        } while (h != h0);
+        area[nfc++] = 2.0 * M_PI - turn;
+    }
+    double asum = 0.0;
+    int big = 0;
+    for (int f = 0; f < nfc; f++) {
+        asum += area[f];
+        if (area[f] > area[big]) big = f;
+    }
+    if (fabs(asum - fourpi) > 1e-9) { free(hpos); rc = -2; goto done; }
+    /* 7. one ray into the largest region: midpoint of its longest side,
+     *    offset to the left by an angle that crosses no arc */
+    int hl = -1;
+    double best = -1.0;
+    for (int h = 0; h < nh; h++)
+        if (hface[h] == big) {
+            double L = arc_angle(pts + 3 * H_ORIG(h), pts + 3 * H_DEST(h));
+            if (L > best) { best = L; hl = h; }
+        }
+    double m[3], t[3], l[3], q[3];
+    {
+        const double *u = pts + 3 * H_ORIG(hl), *v = pts + 3 * H_DEST(hl);
+        for (int k = 0; k < 3; k++) m[k] = u[k] + v[k];
+        normalize3d(m);
+        double vm = 0.0;
+        for (int k = 0; k < 3; k++) t[k] = v[k] - u[k];
+        vm = dot3d(t, m);
+        for (int k = 0; k < 3; k++) t[k] -= vm * m[k];
+        normalize3d(t);
+        cross3d(m, t, l);
+    }
+    double delta = 0.25 * best;
+    int ok = 0;
+    for (int it = 0; it < 60 && !ok; it++, delta *= 0.5) {
+        for (int k = 0; k < 3; k++) q[k] = cos(delta) * m[k] + sin(delta) * l[k];
+        normalize3d(q);
+        ok = 1;
+        for (int k = 0; k < npc && ok; k++) {
+            if (k == (hl >> 1)) continue;
+            double x[3];
+            int degen = 0;
+            if (arcs_cross(m, q, pts + 3 * pc[k].u, pts + 3 * pc[k].v, x, &degen) || degen) ok = 0;
+        }
+        if (delta < 1e-5) break;
+    }
+    if (!ok) { free(hpos); rc = -1; goto done; }
+    float dq[3] = {(float)q[0], (float)q[1], (float)q[2]};
+    int c0 = 0;
+    for (int64_t tr = 0; tr < nf; tr++)
+        c0 += tri_crossing(V + 3 * (int64_t)F[3 * tr], V + 3 * (int64_t)F[3 * tr + 1], V + 3 * (int64_t)F[3 * tr + 2],
+                           p, dq);
+    /* 8. chi of every region from the largest one across the arcs (Lemma 2):
+     *    chi(left of a piece) - chi(right of it) = its weight */
+    chi = (int *)malloc(sizeof(int) * nfc);
+    vis = (int32_t *)calloc((size_t)nfc, sizeof(int32_t));
+    queue = (int *)malloc(sizeof(int) * nfc);
+    if (!chi || !vis || !queue) { free(hpos); rc = -3; goto done; }
+    int qh = 0, qt = 0;
+    chi[big] = c0; vis[big] = 1; queue[qt++] = big;
+    while (qh < qt) {
+        int f = queue[qh++];
+        for (int h = 0; h < nh; h++) {
+            if (hface[h] != f) continue;
+            int g = hface[h ^ 1];
+            int wgt = (h & 1) ? -pc[h >> 1].w : pc[h >> 1].w;    /* along the arc: f is its left side */
+            int cg = chi[f] - wgt;
+            if (!vis[g]) { vis[g] = 1; chi[g] = cg; queue[qt++] = g; }
+            else if (chi[g] != cg) { free(hpos); rc = -2; goto done; }
+        }
+    }
+    if (qt != nfc) { free(hpos); rc = -2; goto done; }
+    /* 9. the area-weighted sum */
+    double acc = 0.0;
+    for (int f = 0; f < nfc; f++) acc += area[f] * (double)chi[f];
+    *w_out = acc / fourpi;
+    if (info) { info[0] = nfc; info[1] = area[big]; info[2] = c0; }
+    free(hpos);
+#undef H_ORIG
+#undef H_DEST
+done:
+    free(src); free(dst); free(mul); free(vmap); free(par); free(vis); free(pts); free(area); free(arcs); free(xs);
+    free(pc); free(hnext); free(hface); free(ostart); free(ocnt); free(chi); free(queue); free(outs);
+    return rc;
 }

@@ -398,3 +398,56 @@ def test_rays_exactly_through_boundary_vertices():
     for d in ([0, 0, 1], [0, 0, -1], [1, 0, 0], [0, 1, 1], [1, 1, 0], [0, 0, 3]):
         w, chi, B = oracle.w3d_oneshot(V, F, P, np.array(d, np.float32))
         assert np.abs(w - wv).max() < 1e-12, d
+
+
+# ---- Algorithm 1 in 3D by a spherical arrangement (third evaluation) --------
+
+def test_alg1_closed_forms():
+    """Algorithm 1 (arrangement, one ray, propagation across the arcs,
+    area-weighted sum) reproduces the closed forms: the octant triangle seen
+    from the origin (1/8; its image splits the sphere into two regions), the
+    hemisphere seen from just off its centre (equal to the definition, both
+    orientations) and a closed mesh (integer, one region)."""
+    V = np.array([[1, 0, 0], [0, 1, 0], [0, 0, 1]], np.float32)
+    F = np.array([[0, 1, 2]], np.int32)
+    w, info = oracle.w3d_alg1(V, F, np.zeros((1, 3), np.float32))
+    assert abs(w[0] - 0.125) < 1e-14 and info[0, 0] == 2
+    assert abs(info[0, 1] - 3.5 * math.pi) < 1e-12          # largest region: 4 pi - pi / 2
+    Vh, Fh = _hemisphere(n_ring=24, n_lat=6)
+    P0 = np.zeros((1, 3), np.float32)
+    # from the centre itself the rim's arcs would share one great circle (a
+    # degenerate arrangement); just above it they lie on a small circle
+    w, info = oracle.w3d_alg1(Vh, Fh, P0 + np.float32([0, 0, 1e-3]))
+    assert abs(w[0] - oracle.w3d_vos(Vh, Fh, P0 + np.float32([0, 0, 1e-3]))[0]) < 1e-12
+    w, _ = oracle.w3d_alg1(Vh, Fh[:, [0, 2, 1]], P0 + np.float32([0, 0, -1e-3]))
+    assert abs(w[0] - oracle.w3d_vos(Vh, Fh[:, [0, 2, 1]], P0 + np.float32([0, 0, -1e-3]))[0]) < 1e-12
+    Vs, Fs = gen.icosphere(2)
+    w, info = oracle.w3d_alg1(Vs, Fs, np.array([[0.1, -0.2, 0.05], [1.7, 0.3, 0.2]], np.float32))
+    assert np.array_equal(w, [1.0, 0.0]) and np.all(info[:, 0] == 1)
+
+
+def test_alg1_matches_definition_on_soups_and_meshes():
+    """On random soups (several loops joined by zero-weight bridges,
+    self-crossing projections, multiplicity-2 edges, non-manifold edges) and on
+    the capped icosphere (one loop of 252 arcs), the arrangement evaluation
+    equals the per-triangle solid-angle sum and the closed form chi + B."""
+    rng = np.random.default_rng(11)
+    for trial in range(3):
+        nv = 14
+        V = rng.standard_normal((nv, 3)).astype(np.float32)
+        F = rng.integers(0, nv, (10, 3)).astype(np.int32)
+        F = F[(F[:, 0] != F[:, 1]) & (F[:, 1] != F[:, 2]) & (F[:, 0] != F[:, 2])]
+        F = np.concatenate([F, F[:2]])
+        P = (1.5 * rng.standard_normal((40, 3))).astype(np.float32)
+        P = P[oracle.dist3d(V, F, P) > 1e-3][:12]
+        wa, info = oracle.w3d_alg1(V, F, P)
+        wv = oracle.w3d_vos(V, F, P)
+        wo, _, _ = oracle.w3d_oneshot(V, F, P, DIRS[0])
+        assert np.abs(wa - wv).max() < 1e-11, trial
+        assert np.abs(wa - wo).max() < 1e-11, trial
+        assert info[:, 0].max() > 4                # a real arrangement, not one split
+    m = gen.icosphere_cap(subdiv=2)
+    P = np.array([[0.0, 0.0, 0.2], [0.3, -0.2, 1.3], [0.9, 0.9, 0.1], [0.05, 0.02, -1.6]], np.float32)
+    wa, info = oracle.w3d_alg1(m.V, m.F, P)
+    wv = oracle.w3d_vos(m.V, m.F, P)
+    assert np.abs(wa - wv).max() < 1e-11
