@@ -194,6 +194,7 @@ extern "C" GWN_API gwn_status gwn_eval_batch(gwn_geom *g, const gwn_queries *que
         return GWN_E_INVALID;
     }
     if (n_chains != g->cs.n_chains) { set_error("gwn_eval_batch: one query grid per chain is required"); return GWN_E_INVALID; }
+    if (g->cs.n_pieces > 0x7fffffff) { set_error("gwn_eval_batch: more than 2^31 - 1 monotone pieces"); return GWN_E_UNSUPPORTED; }
     for (int64_t c = 0; c < n_chains; c++) {
         const gwn_queries &q = queries[c];
         if (q.kind != GWN_QUERY_GRID || q.dim != 2 || q.dims[0] < 1 || q.dims[1] < 1 || q.dims[0] > MAX_NX ||
