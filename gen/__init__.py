@@ -17,6 +17,9 @@ model for shapes and sizes; its datasets are not available, so these stand in):
   star-shaped curves, each with its own regular grid (N=1000 random curves).
 * ``slit_torus``           torus cut along one meridian: a two-loop boundary.
 * ``holey_heightfield``    large heightfield disk with circular holes.
+* ``patch_spheroid``       closed (or opened) surface of bicubic Bezier patches
+  over the six faces of a cube, pushed onto a wavy sphere (parametric
+  surfaces, Sec. "Parametric Surfaces").
 
 Grid coordinates follow one rule everywhere: coordinate ``i`` of an axis with
 ``n`` samples on ``[lo, hi]`` is ``lo + i * ((hi - lo) / (n - 1))`` evaluated
@@ -32,7 +35,7 @@ import numpy as np
 __all__ = [
     "grid_axis", "grid_points", "random_direction", "icosphere",
     "icosphere_cap", "slit_torus", "holey_heightfield", "bezier_circle_chain",
-    "star_chains", "Mesh", "Grid", "Chains", "config",
+    "star_chains", "patch_spheroid", "Mesh", "Grid", "Chains", "Patches", "config",
 ]
 
 
@@ -71,6 +74,16 @@ class Chains:
     ctrl: np.ndarray         # float32 or float64 [n_ctrl, 2]
     offsets: np.ndarray      # int64 [n_chains + 1]
     grids: list              # one Grid per chain
+    meta: dict = field(default_factory=dict)
+
+
+@dataclass
+class Patches:
+    """Bicubic Bezier patches: ctrl[t, i, j] is control point P_ij of patch t
+    (i along u, j along v); the normal is f_u x f_v."""
+    ctrl: np.ndarray         # float32 [n_patches, 4, 4, 3]
+    d: np.ndarray            # float32 [3] ray direction
+    grid: Grid | None = None
     meta: dict = field(default_factory=dict)
 
 
@@ -336,6 +349,38 @@ def star_chains(n_chains: int = 1024, seg_lo: int = 8, seg_hi: int = 2048, amp: 
 # ----------------------------------------------------------------------------
 # named workloads
 # ----------------------------------------------------------------------------
+def patch_spheroid(n: int = 2, amp: float = 0.08, open_faces: tuple = (), grid_n: int = 32,
+                   extent: float = 1.3, seed: int = 0) -> Patches:
+    """Six cube faces, each an n x n array of bicubic patches whose control
+    points are the points of a (3n+1)^2 grid on the face, pushed radially onto
+    r(x) = 1 + amp sin(3x + a) sin(2y + b) cos(z + c) (a, b, c from the seed).
+    Neighbouring patches (also across cube edges) share their edge control
+    points bit for bit, so the closed surface has no boundary; the faces
+    listed in ``open_faces`` (0..5: +x, -x, +y, -y, +z, -z) are left out.
+    Normals point outwards."""
+    rng = np.random.default_rng(seed)
+    ph = rng.uniform(0.0, 2.0 * math.pi, 3)
+    m = 3 * n
+    s = np.array([-1.0 + 2.0 * k / m for k in range(m + 1)])
+    S, T = np.meshgrid(s, s, indexing="ij")
+    one = np.ones_like(S)
+    faces = [np.stack([one, S, T], -1), np.stack([-one, T, S], -1), np.stack([T, one, S], -1),
+             np.stack([S, -one, T], -1), np.stack([S, T, one], -1), np.stack([T, S, -one], -1)]
+    ctrl = []
+    for f, G in enumerate(faces):
+        if f in open_faces:
+            continue
+        X = G / np.linalg.norm(G, axis=-1, keepdims=True)
+        r = 1.0 + amp * np.sin(3 * X[..., 0] + ph[0]) * np.sin(2 * X[..., 1] + ph[1]) * np.cos(X[..., 2] + ph[2])
+        X = (X * r[..., None]).astype(np.float32)
+        for a in range(n):
+            for b in range(n):
+                ctrl.append(X[3 * a:3 * a + 4, 3 * b:3 * b + 4])
+    ctrl = np.ascontiguousarray(np.array(ctrl, np.float32))
+    return Patches(ctrl=ctrl, d=random_direction(seed), grid=Grid((-extent,) * 3, (extent,) * 3, (grid_n,) * 3),
+                   meta={"n": n, "amp": amp, "open_faces": tuple(open_faces), "n_patches": len(ctrl)})
+
+
 def config(name: str, seed: int = 0, small: bool = False):
     """The five workloads by name; ``small=True`` gives a reduced variant of
     the same construction for fast tests."""

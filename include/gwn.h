@@ -76,7 +76,7 @@ typedef enum gwn_status {
 enum { GWN_MEM_HOST = 0, GWN_MEM_DEVICE = 1 };
 enum { GWN_F32 = 0, GWN_F64 = 1 };
 enum { GWN_QUERY_POINTS = 0, GWN_QUERY_GRID = 1 };
-enum { GWN_GEOM_MESH = 1, GWN_GEOM_BEZIER2D = 2 };
+enum { GWN_GEOM_MESH = 1, GWN_GEOM_BEZIER2D = 2, GWN_GEOM_PATCHES = 3 };
 
 typedef struct gwn_ctx gwn_ctx;
 typedef struct gwn_geom gwn_geom;
@@ -123,7 +123,7 @@ typedef struct gwn_stats {
 
 /* Geometry summary. */
 typedef struct gwn_geom_info {
-    int32_t kind;               /* GWN_GEOM_MESH or GWN_GEOM_BEZIER2D */
+    int32_t kind;               /* GWN_GEOM_MESH, GWN_GEOM_BEZIER2D or GWN_GEOM_PATCHES */
     int32_t dtype;
     int64_t n_vertices;         /* mesh vertices / 2D control points */
     int64_t n_primitives;       /* triangles / cubic segments */
@@ -173,6 +173,19 @@ GWN_API gwn_status gwn_mesh_prepare(gwn_geom *g, const float d[3]);
 GWN_API gwn_status gwn_bezier2d_create(gwn_ctx *ctx, const void *ctrl, int dtype,
                                        const int64_t *chain_offsets, int64_t n_chains,
                                        int mem_kind, gwn_geom **out);
+
+/* Surfaces of bicubic Bezier patches (parametric surfaces, "Parametric
+ * Surfaces" in the paper's implementation section): ctrl [n_patches][4][4][3]
+ * float32, control point P_ij of a patch at [i][j] (i along u, j along v),
+ * normal f_u x f_v.  The crossing count is taken on the patches themselves
+ * (no surface discretisation); the boundary term on the boundary curves (the
+ * patch edge curves that no other patch cancels: a curve and its reverse,
+ * bit for bit, cancel) sampled at `segments` intervals each (1 .. 65536),
+ * which perturbs w by O(segments^-2) near the boundary.  Copies the input.
+ * gwn_eval takes float32 points or a 3D grid and a direction d.  Fails with
+ * GWN_E_INVALID on a non-finite control point. */
+GWN_API gwn_status gwn_patches_create(gwn_ctx *ctx, const float *ctrl, int64_t n_patches, int segments,
+                                      int mem_kind, gwn_geom **out);
 
 GWN_API gwn_status gwn_geom_info_get(const gwn_geom *g, gwn_geom_info *out);
 GWN_API void gwn_geom_destroy(gwn_geom *g);

@@ -16,6 +16,10 @@ on first use and wraps it with ctypes.  Functions and the passages they follow:
 * ``bterm3d``        boundary term relative to d (Lemma 1, Lemma 2, and the
                      closure argument of the proof in Appendix A).
 * ``w3d_oneshot``    chi3d + bterm3d.
+* ``w3d_patches_quad`` 3D definition for bicubic Bezier patches (adaptive
+                     tensor Gauss-Legendre of the solid-angle element).
+* ``patch_boundary``  boundary curves of a patch set (net multiplicity of
+                     the patch edge curves) sampled as a polyline.
 * ``w3d_alg1``       Algorithm 1 in 3D, literally: arrangement of the
                      projected boundary on the unit sphere, region areas,
                      one ray in the largest region, counts propagated across
@@ -84,6 +88,7 @@ def _load():
                 "oracle_dist3d": (None, [P, P, I64, P, I64, P, I]),
                 "oracle_dist2d": (None, [P, I64, P, I64, P, I]),
                 "oracle_w3d_alg1": (I, [P, I64, P, I64, P, P, P]),
+                "oracle_w3d_patches_quad": (None, [P, I64, P, I64, P, C.c_double, I]),
             }
             for name, (res, args) in sigs.items():
                 fn = getattr(lib, name)
@@ -188,6 +193,63 @@ def w3d_alg1(V, F, P):
             raise ValueError(f"w3d_alg1: query {q}: status {rc}")
         w[q] = out.value
     return w, info
+
+
+def w3d_patches_quad(ctrl, P, tol: float = 1e-13, threads: int | None = None) -> np.ndarray:
+    """Definition for bicubic patches ctrl [n, 4, 4, 3] (float32)."""
+    ctrl = _f32(ctrl).reshape(-1, 48)
+    P = _f32(P, 3).reshape(-1, 3)
+    w = np.empty(len(P), np.float64)
+    _load().oracle_w3d_patches_quad(_ptr(ctrl), len(ctrl), _ptr(P), len(P), _ptr(w), tol,
+                                    threads or default_threads())
+    return w
+
+
+def patch_boundary(ctrl, k: int):
+    """Boundary of a set of bicubic patches as a polyline (V float32, edges
+    (src, dst, mult) int32 arrays) for the FP64 boundary term.  Each patch
+    contributes its four edge curves in the direction of the counter-clockwise
+    boundary of the (u, v) square (the orientation of f_u x f_v); a curve and
+    its reverse cancel; a curve with net multiplicity m != 0 is sampled at k
+    segments (float64 Bernstein evaluation rounded to float32, so its ends are
+    its end control points exactly)."""
+    ctrl = np.asarray(ctrl, np.float32).reshape(-1, 4, 4, 3)
+    net = {}
+    for t in range(len(ctrl)):
+        P = ctrl[t]
+        for cur in (P[:, 0], P[3, :], P[::-1, 3], P[0, ::-1]):
+            fwd = tuple(cur.reshape(-1).view(np.uint32).tolist())
+            rev = tuple(cur[::-1].reshape(-1).view(np.uint32).tolist())
+            key, sgn = (fwd, 1) if fwd <= rev else (rev, -1)
+            net[key] = net.get(key, 0) + sgn
+    pts, index = [], {}
+
+    def vid(x):
+        key = tuple(np.asarray(x, np.float32).view(np.uint32).tolist())
+        if key not in index:
+            index[key] = len(pts)
+            pts.append(np.asarray(x, np.float32))
+        return index[key]
+
+    src, dst, mul = [], [], []
+    s = np.arange(k + 1) / k
+    B = np.stack([(1 - s) ** 3, 3 * s * (1 - s) ** 2, 3 * s ** 2 * (1 - s), s ** 3], 1)
+    for key, m in sorted(net.items()):
+        if m == 0:
+            continue
+        c = np.array(key, np.uint32).view(np.float32).reshape(4, 3).astype(np.float64)
+        if np.all(c == c[0]):
+            continue                                  # a collapsed edge bounds nothing
+        X = (B @ c).astype(np.float32)
+        X[0], X[-1] = c[0].astype(np.float32), c[3].astype(np.float32)
+        ids = [vid(x) for x in X]
+        for a, b in zip(ids[:-1], ids[1:]):
+            if m > 0:
+                src.append(a); dst.append(b); mul.append(m)
+            else:
+                src.append(b); dst.append(a); mul.append(-m)
+    V = np.array(pts, np.float32).reshape(-1, 3)
+    return V, (np.array(src, np.int32), np.array(dst, np.int32), np.array(mul, np.int32))
 
 
 def grad3d_vos(V, F, P, gw=None, want_p=True, want_V=True, threads: int | None = None):

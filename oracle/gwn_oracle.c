@@ -1458,3 +1458,91 @@ done:
     free(pc); free(hnext); free(hface); free(ostart); free(ocnt); free(chi); free(queue); free(outs);
     return rc;
 }
+
+/* ======================================================================== */
+/* 3D definition for bicubic Bezier patches (parametric surfaces)           */
+/* ======================================================================== */
+/* w(p) = (1/4 pi) sum_patches int_0^1 int_0^1 (f - p) . (f_u x f_v) / |f - p|^3 du dv
+ * (Background: w_M(p) = (1/4 pi) int_M dOmega; for a parametric patch f(u, v)
+ * the solid-angle element is (f - p) . (f_u x f_v) du dv / |f - p|^3).
+ * f(u, v) = sum_ij B_i(u) B_j(v) P_ij with cubic Bernstein B; ctrl holds
+ * P_ij at ((patch * 4 + i) * 4 + j) * 3, float32 promoted exactly.
+ * Quadrature: tensor 8-point Gauss-Legendre on a cell, accepted when it agrees
+ * with the sum over the cell's four quarters to tol (scaled by the cell's
+ * share of the domain), else the quarters are refined (depth <= 12). */
+static const double GL8X[8] = {-0.9602898564975363, -0.7966664774136267, -0.5255324099163290, -0.1834346424956498,
+                               0.1834346424956498, 0.5255324099163290, 0.7966664774136267, 0.9602898564975363};
+static const double GL8W[8] = {0.1012285362903763, 0.2223810344533745, 0.3137066458778873, 0.3626837833783620,
+                               0.3626837833783620, 0.3137066458778873, 0.2223810344533745, 0.1012285362903763};
+
+static void bern3_basis(double u, double *b, double *db) {
+    double v = 1.0 - u;
+    b[0] = v * v * v; b[1] = 3.0 * u * v * v; b[2] = 3.0 * u * u * v; b[3] = u * u * u;
+    db[0] = -3.0 * v * v; db[1] = 3.0 * v * v - 6.0 * u * v; db[2] = 6.0 * u * v - 3.0 * u * u; db[3] = 3.0 * u * u;
+}
+
+static double patch_integrand(const double *P, const double *p, double u, double v) {
+    double bu[4], dbu[4], bv[4], dbv[4];
+    bern3_basis(u, bu, dbu);
+    bern3_basis(v, bv, dbv);
+    double f[3] = {0, 0, 0}, fu[3] = {0, 0, 0}, fv[3] = {0, 0, 0};
+    for (int i = 0; i < 4; i++)
+        for (int j = 0; j < 4; j++) {
+            const double *q = P + 3 * (4 * i + j);
+            double w0 = bu[i] * bv[j], w1 = dbu[i] * bv[j], w2 = bu[i] * dbv[j];
+            for (int k = 0; k < 3; k++) { f[k] += w0 * q[k]; fu[k] += w1 * q[k]; fv[k] += w2 * q[k]; }
+        }
+    double r[3] = {f[0] - p[0], f[1] - p[1], f[2] - p[2]}, n[3];
+    cross3d(fu, fv, n);
+    double r2 = dot3d(r, r);
+    return dot3d(r, n) / (r2 * sqrt(r2));
+}
+
+static double patch_cell_gl8(const double *P, const double *p, double u0, double v0, double h) {
+    double s = 0.0;
+    for (int a = 0; a < 8; a++) {
+        double u = u0 + 0.5 * h * (1.0 + GL8X[a]);
+        for (int b = 0; b < 8; b++) {
+            double v = v0 + 0.5 * h * (1.0 + GL8X[b]);
+            s += GL8W[a] * GL8W[b] * patch_integrand(P, p, u, v);
+        }
+    }
+    return s * 0.25 * h * h;
+}
+
+static double patch_adapt(const double *P, const double *p, double u0, double v0, double h, double whole,
+                          double tol, int depth) {
+    double hh = 0.5 * h;
+    double q[4] = {patch_cell_gl8(P, p, u0, v0, hh), patch_cell_gl8(P, p, u0 + hh, v0, hh),
+                   patch_cell_gl8(P, p, u0, v0 + hh, hh), patch_cell_gl8(P, p, u0 + hh, v0 + hh, hh)};
+    double fine = q[0] + q[1] + q[2] + q[3];
+    if (fabs(fine - whole) <= tol * h * h || depth >= 12) return fine;
+    return patch_adapt(P, p, u0, v0, hh, q[0], tol, depth + 1) + patch_adapt(P, p, u0 + hh, v0, hh, q[1], tol, depth + 1) +
+           patch_adapt(P, p, u0, v0 + hh, hh, q[2], tol, depth + 1) +
+           patch_adapt(P, p, u0 + hh, v0 + hh, hh, q[3], tol, depth + 1);
+}
+
+typedef struct {
+    const float *ctrl; int64_t npatch; const float *P; double *w; double tol;
+} pq_ctx;
+
+static void patch_quad_range(void *vp, int64_t lo, int64_t hi) {
+    pq_ctx *c = (pq_ctx *)vp;
+    double Pd[48];
+    for (int64_t q = lo; q < hi; q++) {
+        double p[3] = {c->P[3 * q], c->P[3 * q + 1], c->P[3 * q + 2]};
+        double acc = 0.0;
+        for (int64_t t = 0; t < c->npatch; t++) {
+            for (int k = 0; k < 48; k++) Pd[k] = (double)c->ctrl[48 * t + k];
+            double whole = patch_cell_gl8(Pd, p, 0.0, 0.0, 1.0);
+            acc += patch_adapt(Pd, p, 0.0, 0.0, 1.0, whole, c->tol, 0);
+        }
+        c->w[q] = acc / (4.0 * M_PI);
+    }
+}
+
+ORACLE_API void oracle_w3d_patches_quad(const float *ctrl, int64_t npatch, const float *P, int64_t nq, double *w,
+                                        double tol, int nthreads) {
+    pq_ctx c = {ctrl, npatch, P, w, tol};
+    parallel_for(nq, nthreads, patch_quad_range, &c);
+}

@@ -24,7 +24,7 @@ from . import _capi
 from ._capi import (F32, F64, MEM_DEVICE, MEM_HOST, QUERY_GRID, QUERY_POINTS, GwnError, check, gwn_geom_info,
                     gwn_plan, gwn_queries, gwn_stats, load)
 
-__all__ = ["Context", "Mesh", "Bezier2D", "Grid", "Points", "GwnFunction", "gwn_apply", "GwnError", "load",
+__all__ = ["Context", "Mesh", "Bezier2D", "Patches", "Grid", "Points", "GwnFunction", "gwn_apply", "GwnError", "load",
            "boundary_extract_host", "monotone_split_host"]
 
 
@@ -275,6 +275,29 @@ class Mesh(_Geom):
         w = torch.empty(queries.n, dtype=torch.float32, device=torch.device("cuda", self.ctx.device))
         check(self.lib.gwn_eval_bruteforce(self.h, C.byref(qc), w.data_ptr()), "gwn_eval_bruteforce")
         return w
+
+
+class Patches(_Geom):
+    """Surface of bicubic Bezier patches: ctrl [n, 4, 4, 3] float32 (P_ij at
+    [t, i, j], i along u, j along v; normal f_u x f_v); boundary curves sampled
+    at `segments` intervals for the boundary term."""
+
+    def __init__(self, ctx: Context, ctrl, segments: int = 64):
+        torch = _torch()
+        self.ctx = ctx
+        self.lib = ctx.lib
+        ct = _as_tensor(np.asarray(ctrl, np.float32).reshape(-1, 48) if not hasattr(ctrl, "is_cuda") else ctrl,
+                        torch.float32).reshape(-1, 48).contiguous()
+        mem = MEM_DEVICE if ct.is_cuda else MEM_HOST
+        self.n = int(ct.shape[0])
+        h = C.c_void_p()
+        check(self.lib.gwn_patches_create(ctx.h, ct.data_ptr() if self.n else None, self.n, int(segments), mem,
+                                          C.byref(h)), "gwn_patches_create")
+        self.h = h
+        _live_geoms.add(self)
+
+    def eval(self, queries, d, want_chi=False, want_b=False, stats=False, out=None):
+        return Mesh.eval(self, queries, d, want_chi=want_chi, want_b=want_b, stats=stats, out=out)
 
 
 class Bezier2D(_Geom):

@@ -59,6 +59,7 @@ _SIGS = {
     "gwn_mesh_create": (ST, [P, P, I64, P, I64, C.c_int, C.POINTER(P)]),
     "gwn_mesh_prepare": (ST, [P, P]),
     "gwn_bezier2d_create": (ST, [P, P, C.c_int, P, I64, C.c_int, C.POINTER(P)]),
+    "gwn_patches_create": (ST, [P, P, I64, C.c_int, C.c_int, C.POINTER(P)]),
     "gwn_geom_info_get": (ST, [P, C.POINTER(gwn_geom_info)]),
     "gwn_geom_destroy": (None, [P]),
     "gwn_mesh_boundary": (ST, [P, P, P]),

@@ -121,10 +121,6 @@ Frame64 make_frame64(const float d[3]) {
 // of its sign.  Unit edges are chained into closed loops by walking unused
 // out-edges from the smallest vertex that still has one; since every vertex
 // has equal in- and out-degree, a walk can only stop at its start.
-struct BoundaryLoops {
-    std::vector<int64_t> off;   // n_loops + 1, in edges
-    std::vector<int32_t> vid;   // loop vertex ids
-};
 
 static gwn_status extract_boundary(const int32_t *F, int64_t nf, int64_t nv, BoundaryLoops &out) {
     out.off.assign(1, 0);
@@ -172,6 +168,15 @@ static gwn_status extract_boundary(const int32_t *F, int64_t nf, int64_t nv, Bou
             i = j;
         }
     }
+    return chain_unit_edges(bedges, nv, out);
+}
+
+// Unit edges are chained into closed loops by walking unused out-edges from
+// the smallest vertex that still has one; since every vertex has equal in- and
+// out-degree, a walk can only stop at its start.
+gwn_status chain_unit_edges(std::vector<std::pair<int32_t, int32_t>> &bedges, int64_t nv, BoundaryLoops &out) {
+    out.off.assign(1, 0);
+    out.vid.clear();
     if (bedges.empty()) return GWN_OK;
     std::vector<int64_t> ooff(nv + 1, 0);
     for (auto &e : bedges) ooff[e.first + 1]++;
@@ -361,6 +366,13 @@ static void ctx_ref(gwn_ctx *ctx) {
     ctx->geom_refs++;
 }
 
+}  // extern "C"
+
+// for geometry constructors in other translation units
+void gwn::ctx_add_geometry(gwn_ctx *ctx) { ctx_ref(ctx); }
+
+extern "C" {
+
 static void ctx_unref(gwn_ctx *ctx) {
     bool now;
     {
@@ -420,6 +432,7 @@ static void free_geom_device(gwn_geom *g) {
     if (cs.bucket_idx) cudaFree(cs.bucket_idx);
     if (cs.piece_chain) cudaFree(cs.piece_chain);
     if (cs.chain_piece_off) cudaFree(cs.chain_piece_off);
+    patches_free(g->ps);
 }
 
 GWN_API void gwn_geom_destroy(gwn_geom *g) {
@@ -811,6 +824,11 @@ GWN_API gwn_status gwn_geom_info_get(const gwn_geom *g, gwn_geom_info *out) {
         out->n_primitives = g->nf;
         out->n_boundary_edges = (int64_t)g->loop_vid.size();
         out->n_loops = (int64_t)g->loop_off.size() - 1;
+    } else if (g->kind == GWN_GEOM_PATCHES) {
+        out->n_vertices = g->nv;                      // boundary polyline vertices
+        out->n_primitives = g->ps.n;
+        out->n_boundary_edges = (int64_t)g->loop_vid.size();
+        out->n_loops = (int64_t)g->loop_off.size() - 1;
     } else {
         out->n_vertices = g->cs.n_ctrl;
         out->n_primitives = g->cs.n_seg;
@@ -1031,6 +1049,43 @@ GWN_API gwn_status gwn_eval(gwn_geom *g, const gwn_queries *q, const float *d, v
         int64_t edges = (int64_t)g->loop_vid.size();
         return read_stats(ctx, stats, nq, nq * edges, prepared);
     }
+    if (g->kind == GWN_GEOM_PATCHES) {
+        gwn_status s = check_queries(q, 3);
+        if (s != GWN_OK) return s;
+        if (q->kind == GWN_QUERY_POINTS && q->dtype != GWN_F32) { set_error("gwn_eval: patch queries are float32"); return GWN_E_INVALID; }
+        if (!d) { set_error("gwn_eval: patch evaluation needs a direction"); return GWN_E_INVALID; }
+        int64_t nq = query_count(q);
+        if (nq > 0 && !w_out && !chi_out && !b_out) { set_error("gwn_eval: no output requested"); return GWN_E_INVALID; }
+        if (stats) {
+            CK(cudaMemsetAsync(ctx->d_cnt, 0, sizeof(unsigned long long) * CNT_NUM, ctx->stream), "clear counters");
+            CK(cudaEventRecord(ctx->ev[0], ctx->stream), "event");
+        }
+        bool prepared = !(g->ps.valid && memcmp(g->ps.dkey, d, sizeof(float) * 3) == 0);
+        s = patches_prepare(g, d);
+        if (s != GWN_OK) return s;
+        QuerySrc src;
+        s = make_query_src(ctx, q, GWN_F32, src);
+        if (s != GWN_OK) return s;
+        if (nq == 0) return read_stats(ctx, stats, 0, 0, prepared);
+        int32_t *chi = chi_out;
+        cudaError_t e;
+        if (!chi) {
+            chi = (int32_t *)arena_get(ctx, 0, sizeof(int32_t) * nq, &e);
+            if (!chi) return cuda_fail(e, "chi buffer");
+        }
+        int32_t *defer = (int32_t *)arena_get(ctx, 4, sizeof(int32_t) * nq, &e);
+        if (!defer) return cuda_fail(e, "deferred-query list");
+        if (stats) CK(cudaEventRecord(ctx->ev[1], ctx->stream), "event");
+        e = launch_chi_patches(g->ps, src, chi, stats ? ctx->d_cnt : nullptr, ctx->d_status, ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "patch crossings");
+        if (stats) CK(cudaEventRecord(ctx->ev[2], ctx->stream), "event");
+        e = launch_bterm3d(g->bseq, g->ps.bframe, g->n_bseq, g->ps.frame, make_frame64(d), src, chi, (float *)w_out,
+                           (float *)b_out, defer, ctx->d_defer_count, stats ? ctx->d_cnt : nullptr, ctx->d_status,
+                           ctx->sm_count, ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "boundary term");
+        if (stats) CK(cudaEventRecord(ctx->ev[3], ctx->stream), "event");
+        return read_stats(ctx, stats, nq, nq * (int64_t)g->loop_vid.size(), prepared);
+    }
     if (g->kind == GWN_GEOM_BEZIER2D) {
         gwn_status s = check_queries(q, 2);
         if (s != GWN_OK) return s;
@@ -1085,6 +1140,7 @@ GWN_API gwn_status gwn_eval_host(gwn_geom *g, const gwn_queries *q, const float 
 
 GWN_API gwn_status gwn_eval_bruteforce(gwn_geom *g, const gwn_queries *q, void *w_out) {
     if (!g || !w_out) { set_error("gwn_eval_bruteforce: NULL argument"); return GWN_E_INVALID; }
+    if (g->kind == GWN_GEOM_PATCHES) { set_error("gwn_eval_bruteforce: not provided for patches"); return GWN_E_UNSUPPORTED; }
     gwn_ctx *ctx = g->ctx;
     CK(cudaSetDevice(ctx->device), "cudaSetDevice");
     if (g->kind == GWN_GEOM_MESH) {

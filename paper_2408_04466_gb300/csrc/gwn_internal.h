@@ -82,6 +82,37 @@ struct MeshBvh {
     float4 *bframe = nullptr;  // 2 float4 per boundary record: A.(e1, e2, n) hi (+ w), lo
 };
 
+// Bicubic Bezier patches (parametric surfaces): control nets, and per ray
+// direction their projection into the frame of d with a 2D bin grid over the
+// projected boxes (all rays share d, so a ray is a point of the plane).
+struct PatchSet {
+    int64_t n = 0;                   // patches
+    std::vector<float> h_ctrl;       // host [n][4][4][3]
+    int segments = 0;                // polyline segments per boundary curve
+    bool valid = false;
+    float dkey[3] = {0, 0, 0};
+    Frame frame;
+    float4 *bframe = nullptr;        // 2 float4 per boundary record (as MeshBvh::bframe)
+    float4 *qnet = nullptr;          // [n][16]: (e1.P, e2.P, dh.P, 0) per control point
+    float4 *box = nullptr;           // [n]: (xmin, xmax, ymin, ymax) of the projected net
+    float *zmax = nullptr;           // [n]: max dh.P
+    int32_t *bin_off = nullptr;      // [nbx * nby + 1]
+    int32_t *bin_idx = nullptr;
+    int nbx = 0, nby = 0;
+    float bx0 = 0.f, by0 = 0.f, binv = 0.f;   // cell (i, j) = [bx0 + i / binv, ...) x [by0 + j / binv, ...)
+};
+
+// Boundary loops as vertex sequences: loop j is vid[off[j] .. off[j+1]-1],
+// closing back to its first vertex.
+struct BoundaryLoops {
+    std::vector<int64_t> off;   // n_loops + 1, in edges
+    std::vector<int32_t> vid;   // loop vertex ids
+};
+
+// Chain unit directed edges (every vertex with equal in- and out-degree)
+// into closed loops.
+gwn_status chain_unit_edges(std::vector<std::pair<int32_t, int32_t>> &bedges, int64_t nv, BoundaryLoops &out);
+
 // Device pointers of one 2D chain set.
 struct ChainSet {
     int dtype = GWN_F32;
@@ -184,6 +215,8 @@ struct gwn_geom {
     gwn::MeshBvh bvh;
     // 2D
     gwn::ChainSet cs;
+    // parametric patches
+    gwn::PatchSet ps;
     // batched launch cache
     void *batch_cache = nullptr;
 };
@@ -195,6 +228,7 @@ void set_error(const std::string &msg);
 gwn_status cuda_fail(cudaError_t e, const char *what);
 void *arena_get(gwn_ctx *ctx, int slot, size_t bytes, cudaError_t *err);
 Frame make_frame(const float d[3]);
+void ctx_add_geometry(gwn_ctx *ctx);      // a geometry now refers to ctx (released by gwn_geom_destroy)
 Frame64 make_frame64(const float d[3]);
 
 // ---- launchers (return the first CUDA error) -------------------------------
@@ -234,6 +268,13 @@ cudaError_t launch_bruteforce3d(const float *V, const int32_t *F, int64_t nf, co
 
 // 2D
 // 2D evaluation at point queries (one +x ray per query, y-bucket index).
+// Parametric patches: prepare the per-direction tables of g->ps (host and
+// device), and the signed crossing counts chi[q.n] of the rays p + t d.
+gwn_status patches_prepare(gwn_geom *g, const float d[3]);
+cudaError_t launch_chi_patches(const PatchSet &ps, const QuerySrc &q, int32_t *chi, unsigned long long *cnt,
+                               int *status, cudaStream_t st);
+void patches_free(PatchSet &ps);
+
 cudaError_t launch_eval2d_points(const ChainSet &cs, const QuerySrc &q, void *w_out, int32_t *chi_out, void *b_out,
                                  unsigned long long *cnt, int *status, cudaStream_t st);
 // 2D evaluation over work items: either a device work list (d_sets, d_items)

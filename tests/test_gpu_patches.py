@@ -1,0 +1,116 @@
+"""GPU parity of the parametric-surface path (bicubic Bezier patches) against
+the FP64 oracle.  The oracle's definition is the adaptive quadrature of the
+solid-angle element over the patches; its crossing count is round(w - B) with
+B the FP64 boundary term on a fine sampling of the boundary curves (2048
+segments per curve, error ~1e-8), so it shares no step with the library's
+degree computation.  Bars: crossing counts equal on every query away from the
+surface; w equal to chi + B(the library's own polyline) to 1e-6 (float32
+boundary term) and to the definition within the boundary sampling error."""
+import numpy as np
+import pytest
+
+import gen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gwn(cuda_available):
+    import paper_2408_04466_gb300 as pkg
+    from paper_2408_04466_gb300 import build
+    build.build()
+    return pkg
+
+
+@pytest.fixture(scope="module")
+def ctx(gwn):
+    return gwn.Context(0)
+
+
+def _away(P, band):
+    """queries whose distance from the origin differs from 1 by more than
+    `band` (the spheroids lie within 1 +- amp of the unit sphere, so band =
+    amp + margin keeps the queries at least the margin from the surface)"""
+    r = np.linalg.norm(P.astype(np.float64), axis=1)
+    return np.abs(r - 1.0) > band
+
+
+def _oracle_chi(ctrl, P, d):
+    wd = oracle.w3d_patches_quad(ctrl, P)
+    V, E = oracle.patch_boundary(ctrl, 2048)
+    Bf = oracle.bterm3d(V, E, P, d) if len(E[0]) else np.zeros(len(P))
+    chi = np.rint(wd - Bf)
+    assert np.abs(wd - Bf - chi).max() < 1e-6          # the oracle's own consistency
+    return wd, chi.astype(np.int64)
+
+
+def test_closed_patch_surface_is_integer(gwn, ctx):
+    pc = gen.patch_spheroid(n=2, amp=0.08, seed=1)
+    ps = gwn.Patches(ctx, pc.ctrl, segments=16)
+    assert ps.info()["n_boundary_edges"] == 0
+    g = gen.Grid((-1.3,) * 3, (1.3,) * 3, (14, 14, 14))
+    r = ps.eval(gwn.Grid(g.lo, g.hi, g.dims), pc.d, want_chi=True)
+    w, chi = r["w"].cpu().numpy(), r["chi"].cpu().numpy()
+    P = gen.grid_points(g)
+    keep = _away(P, 0.08 + 0.03)
+    wd, chio = _oracle_chi(pc.ctrl, P[keep], pc.d)
+    assert np.array_equal(chi[keep], chio)
+    assert np.array_equal(w[keep], chi[keep].astype(np.float32))      # no boundary: w = chi exactly
+    assert set(np.unique(chio)) <= {0, 1}
+
+
+@pytest.mark.parametrize("seed, n, amp", [(2, 2, 0.08), (3, 3, 0.15)])
+def test_open_patch_surface(gwn, ctx, seed, n, amp):
+    pc = gen.patch_spheroid(n=n, amp=amp, open_faces=(4,), seed=seed)
+    seg = 64
+    ps = gwn.Patches(ctx, pc.ctrl, segments=seg)
+    info = ps.info()
+    assert info["n_loops"] == 1 and info["n_boundary_edges"] == 4 * n * seg
+    g = gen.Grid((-1.3,) * 3, (1.3,) * 3, (13, 13, 13))
+    P = gen.grid_points(g)
+    keep = _away(P, amp + 0.03)
+    Pk = P[keep]
+    wd, chio = _oracle_chi(pc.ctrl, Pk, pc.d)
+    V, E = oracle.patch_boundary(pc.ctrl, seg)
+    B64 = oracle.bterm3d(V, E, Pk, pc.d)
+    for q in (gwn.Grid(g.lo, g.hi, g.dims), gwn.Points(P)):
+        r = ps.eval(q, pc.d, want_chi=True)
+        w, chi = r["w"].cpu().numpy()[keep], r["chi"].cpu().numpy()[keep]
+        assert np.array_equal(chi, chio)
+        assert np.abs(w - (chio + B64)).max() <= 1e-6          # float32 boundary term on the same polyline
+        assert np.abs(w - wd).max() <= 2e-5                     # boundary sampling (64 segments per curve)
+    assert np.any(chio != 0)
+
+
+def test_direction_independence_and_near_queries(gwn, ctx):
+    """w does not depend on d while chi does; queries 0.02 from the shell make
+    the patches straddle the plane through the query (subdivision)."""
+    pc = gen.patch_spheroid(n=2, amp=0.05, open_faces=(1, 4), seed=5)
+    ps = gwn.Patches(ctx, pc.ctrl, segments=128)
+    rng = np.random.default_rng(9)
+    v = rng.standard_normal((400, 3))
+    P = (rng.uniform(0.5, 1.3, (400, 1)) * v / np.linalg.norm(v, axis=1, keepdims=True)).astype(np.float32)
+    P = P[_away(P, 0.05 + 0.02)]
+    wd, _ = _oracle_chi(pc.ctrl, P, pc.d)
+    ws, chis = [], []
+    for k in range(3):
+        d = gen.random_direction(100 + k)
+        r = ps.eval(gwn.Points(P), d, want_chi=True)
+        ws.append(r["w"].cpu().numpy())
+        chis.append(r["chi"].cpu().numpy())
+        _, chio = _oracle_chi(pc.ctrl, P, d)
+        assert np.array_equal(chis[-1], chio)
+        assert np.abs(ws[-1] - wd).max() <= 1e-5
+    assert np.abs(ws[0] - ws[1]).max() <= 2e-6 and np.abs(ws[0] - ws[2]).max() <= 2e-6
+    assert np.any(chis[0] != chis[1]) or np.any(chis[0] != chis[2])
+
+
+def test_patch_errors(gwn, ctx):
+    import paper_2408_04466_gb300 as pkg
+    bad = gen.patch_spheroid(n=1).ctrl.copy()
+    bad[0, 1, 1, 0] = np.nan
+    with pytest.raises(pkg.GwnError):
+        gwn.Patches(ctx, bad)
+    with pytest.raises(pkg.GwnError):
+        gwn.Patches(ctx, gen.patch_spheroid(n=1).ctrl, segments=0)

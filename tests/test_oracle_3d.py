@@ -451,3 +451,48 @@ def test_alg1_matches_definition_on_soups_and_meshes():
     wa, info = oracle.w3d_alg1(m.V, m.F, P)
     wv = oracle.w3d_vos(m.V, m.F, P)
     assert np.abs(wa - wv).max() < 1e-11
+
+
+# ---- parametric surfaces: bicubic Bezier patches ----------------------------
+
+def test_patch_quadrature_closed_forms():
+    """The patch definition (adaptive quadrature of (f - p).(f_u x f_v) /
+    |f - p|^3) against closed forms: a flat square patch (control points on a
+    uniform grid, so f is the square itself, normal +z) seen from its axis,
+    Omega = 4 atan(a^2 / (h sqrt(2 a^2 + h^2))) (below the square: behind its
+    normal, +); a closed surface of patches gives 0 or 1."""
+    a = 0.7
+    s = np.linspace(-a, a, 4)
+    ctrl = np.zeros((1, 4, 4, 3), np.float32)
+    for i in range(4):
+        for j in range(4):
+            ctrl[0, i, j] = (s[i], s[j], 0.0)
+    for h in (2.0, 0.4, 0.05):
+        P = np.array([[0.0, 0.0, -h]], np.float32)
+        hh = -float(P[0, 2])
+        aa = float(np.float32(a))
+        expect = 4 * math.atan(aa * aa / (hh * math.sqrt(2 * aa * aa + hh * hh))) / (4 * math.pi)
+        assert abs(oracle.w3d_patches_quad(ctrl, P)[0] - expect) < 1e-12
+        assert abs(oracle.w3d_patches_quad(ctrl, -P)[0] + expect) < 1e-12
+    pc = gen.patch_spheroid(n=2, amp=0.1, seed=3)
+    P = np.array([[0, 0, 0], [0.2, -0.3, 0.1], [1.5, 0.2, 0.0], [0.0, -1.4, 0.3]], np.float32)
+    w = oracle.w3d_patches_quad(pc.ctrl, P)
+    assert np.abs(w - np.array([1, 1, 0, 0])).max() < 1e-12
+    V, E = oracle.patch_boundary(pc.ctrl, 8)
+    assert len(E[0]) == 0
+
+
+def test_patch_boundary_sampling_converges():
+    """With one cube face left out, the definition minus the FP64 boundary term
+    on the sampled boundary curves tends to an integer (the crossing count) at
+    the rate of the polyline's sagitta, O(K^-2)."""
+    po = gen.patch_spheroid(n=2, amp=0.08, open_faces=(4,), seed=0)
+    P = np.array([[0.3, -0.2, 0.1], [1.5, 0, 0], [0.2, 0.1, 1.25], [-0.9, 0.9, 0.9], [0.1, 0.2, -0.3]], np.float32)
+    w = oracle.w3d_patches_quad(po.ctrl, P)
+    errs = []
+    for K in (32, 128, 512):
+        V, E = oracle.patch_boundary(po.ctrl, K)
+        assert len(E[0]) == 4 * 2 * K                 # one loop of the 8 edge curves around the hole
+        r = w - oracle.bterm3d(V, E, P, po.d)
+        errs.append(np.abs(r - np.rint(r)).max())
+    assert errs[2] < 1e-6 and errs[0] / errs[1] > 10 and errs[1] / errs[2] > 10
