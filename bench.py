@@ -471,6 +471,33 @@ def run_other(args):
                     "boundary_edges": info["n_boundary_edges"], "triangles": int(len(m.F)),
                     "kernels": {"traverse_ms": st["ms_traverse"], "bterm3d_ms": st["ms_boundary"]},
                     "roofline_bterm": _alu_roofline(len(Pt), info, st["ms_boundary"])})
+    elif name == "patch_spheroid":
+        # parametric surface: 384 bicubic Bezier patches (8 x 8 per cube face,
+        # one face left open: one boundary loop of 32 curves x 64 segments),
+        # 256^3 grid on [-1.3, 1.3]^3, seeded random d
+        pc = gen.patch_spheroid(n=8, amp=0.08, open_faces=(4,), grid_n=args.grid, seed=0)
+        ps = gwn.Patches(ctx, pc.ctrl, segments=64)
+        g = gwn.Grid(pc.grid.lo, pc.grid.hi, pc.grid.dims)
+        w = torch.empty(g.n, dtype=torch.float32, device=dev)
+        st = ps.eval(g, pc.d, stats=True, out=w)["stats"]
+        ms = _timed(lambda: ps.eval(g, pc.d, out=w), args.steps, args.warmup, stream)
+        st = ps.eval(g, pc.d, stats=True, out=w)["stats"]
+        info = ps.info()
+        Pq = gen.grid_points(pc.grid)[::max(1, g.n // 64)][:64]
+        t0 = time.perf_counter()
+        oracle.w3d_patches_quad(pc.ctrl, Pq)
+        dto = time.perf_counter() - t0
+        out.update({"metric": "GWN queries/s, bicubic patch surface (crossings by projection degree)", "dtype": "f32",
+                    "ms_per_step": statistics.median(ms), "value": g.n / (statistics.median(ms) * 1e-3),
+                    "queries_per_step": g.n, "patches": int(len(pc.ctrl)),
+                    "boundary_edges": info["n_boundary_edges"], "boundary_loops": info["n_loops"],
+                    "kernels": {"chi_patches_ms": st["ms_traverse"], "bterm3d_ms": st["ms_boundary"],
+                                "patch_tests_per_query": st["n_tri_tests"] / g.n,
+                                "near_surface_queries": st["n_stack_overflow"]},
+                    "roofline_bterm": _alu_roofline(g.n, info, st["ms_boundary"]),
+                    "cpu_baseline": {"value": len(Pq) / dto, "unit": UNIT, "cores": oracle.default_threads(),
+                                     "kind": "oracle", "sample": f"{len(Pq)} grid queries, FP64 adaptive quadrature "
+                                                                 "of the patch definition"}})
     elif name == "chain_points":
         # 2D point queries (one +x ray per point, no ray reuse): the largest
         # star chain (float32, 4,194,304 uniform points in its grid's box) and
@@ -564,7 +591,7 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip comparator, e2e and CPU baseline legs")
     ap.add_argument("--workload", default="icosphere_cap",
                     choices=["icosphere_cap", "circle_chain_fp64", "star_chains", "slit_torus", "holey_heightfield",
-                             "icosphere_cap_axis", "chain_points"],
+                             "icosphere_cap_axis", "chain_points", "patch_spheroid"],
                     help="icosphere_cap is the benchmark; the others print their own measurement line")
     args = ap.parse_args()
     if args.warmup < 3:

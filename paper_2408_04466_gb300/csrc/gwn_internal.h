@@ -100,6 +100,16 @@ struct PatchSet {
     int32_t *bin_idx = nullptr;
     int nbx = 0, nby = 0;
     float bx0 = 0.f, by0 = 0.f, binv = 0.f;   // cell (i, j) = [bx0 + i / binv, ...) x [by0 + j / binv, ...)
+    // boundary curves (patch edge curves of nonzero net multiplicity), each
+    // sampled at segments + 1 vertices in its canonical orientation
+    int64_t n_bcurves = 0;
+    std::vector<int32_t> h_bedge;    // [n][4]: curve << 1 | (edge runs against the canonical order), or -1
+    std::vector<float4> h_pl_xyz;    // [n_bcurves * (segments + 1)]: sample vertices (float32, w = 0)
+    std::vector<float> h_pl_dev;     // [n_bcurves * segments]: bound on the distance between arc and chord
+    int32_t *bedge = nullptr;        // device copies
+    float4 *pl_xyz = nullptr;
+    float *pl_dev = nullptr;
+    float4 *pl_proj = nullptr;       // per direction: (e1.v, e2.v, dh.v, 0) of the sample vertices
 };
 
 // Boundary loops as vertex sequences: loop j is vid[off[j] .. off[j+1]-1],

@@ -50,6 +50,7 @@
 #include <vector>
 
 #include "gwn_internal.h"
+#include "predicates.cuh"
 #include "query.cuh"
 
 namespace gwn {
@@ -60,8 +61,10 @@ namespace gwn {
 // ---- device ------------------------------------------------------------------
 
 // signed crossings of the half-line {y = 0, x > 0} with the cubic Bezier
-// (x[k], y[k]) in the given orientation (canonicalised by the caller)
-__device__ int cubic_crossings(const float *x, const float *y) {
+// (x[k], y[k]) in the given orientation (canonicalised by the caller); their
+// parameters and signs go to sl / gl when given (at most three)
+__device__ int cubic_crossings(const float *x, const float *y, float *sl = nullptr, int *gl = nullptr,
+                               int *nl = nullptr) {
     float ymin = fminf(fminf(y[0], y[1]), fminf(y[2], y[3])), ymax = fmaxf(fmaxf(y[0], y[1]), fmaxf(y[2], y[3]));
     if (ymin > 0.f || ymax <= 0.f) return 0;
     if (fmaxf(fmaxf(x[0], x[1]), fmaxf(x[2], x[3])) <= 0.f) return 0;
@@ -108,7 +111,11 @@ __device__ int cubic_crossings(const float *x, const float *y) {
                 if (mid == lo || mid == hi) break;
                 if (ev(y, mid) <= 0.f) lo = mid; else hi = mid;
             }
-            if (ev(x, 0.5f * (lo + hi)) > 0.f) count += up ? 1 : -1;
+            const float sr = 0.5f * (lo + hi);
+            if (ev(x, sr) > 0.f) {
+                count += up ? 1 : -1;
+                if (sl && *nl < 3) { sl[*nl] = sr; gl[*nl] = up ? 1 : -1; (*nl)++; }
+            }
         }
         ya = yb;
     }
@@ -117,9 +124,13 @@ __device__ int cubic_crossings(const float *x, const float *y) {
 
 // the same in canonical orientation: a curve and its reverse give exactly
 // opposite counts
+__device__ __forceinline__ bool canon_reversed(float x0, float y0, float x1, float y1, float x2, float y2, float x3,
+                                               float y3) {
+    return x3 < x0 || (x3 == x0 && (y3 < y0 || (y3 == y0 && (x2 < x1 || (x2 == x1 && y2 < y1)))));
+}
 __device__ __forceinline__ int curve_crossings(float x0, float y0, float x1, float y1, float x2, float y2, float x3,
                                                float y3) {
-    const bool rev = x3 < x0 || (x3 == x0 && (y3 < y0 || (y3 == y0 && (x2 < x1 || (x2 == x1 && y2 < y1)))));
+    const bool rev = canon_reversed(x0, y0, x1, y1, x2, y2, x3, y3);
     float x[4], y[4];
     if (rev) {
         x[0] = x3; x[1] = x2; x[2] = x1; x[3] = x0;
@@ -210,45 +221,191 @@ __device__ int patch_winding(const float *X, const float *Y, const float *Z, boo
     return total;
 }
 
+// Boundary correction of one patch edge that lies on the surface boundary.
+// The boundary term runs over the sampled boundary (chords v_k -> v_{k+1} of
+// the edge curve), so the crossing count must be that of the surface whose
+// boundary is the polyline: the patch edge's curve crossings are replaced by
+// the chords' crossings.  The two differ only for a ray inside the thin
+// region between a chord and its arc; per chord k that difference counts when
+// the region lies in front of the query, is dropped behind it, and marks the
+// query as on the surface when the region straddles it (depth range of the
+// chord's ends widened by a host bound on the arc's distance from the chord).
+// Curve crossings come from the same canonical evaluation as the winding
+// number, attributed to chords by their parameter; a chord crossing takes its
+// side from the exact sign of det[v_k - p, v_{k+1} - p, d], the predicate the
+// boundary term uses for its branch, so chi and B jump together.
+// ex, ey: the edge's control points in the patch's edge order (relative to
+// the query); pv: the curve's projected samples (canonical order); xv: the
+// same samples in 3D; dev: per chord arc-chord bound; against: the patch edge
+// runs against the canonical order.
+__device__ int boundary_edge_correction(const float *ex, const float *ey, const float4 *__restrict__ pv,
+                                        const float4 *__restrict__ xv, const float *__restrict__ dev, int K,
+                                        bool against, float qa, float qb, float qc, float3 P, float3 D,
+                                        unsigned long long *cnt, int *status, bool *near) {
+    // curve crossings (as the winding number evaluates them), in the canonical sample order
+    const bool rev = canon_reversed(ex[0], ey[0], ex[1], ey[1], ex[2], ey[2], ex[3], ey[3]);
+    float x[4], y[4];
+    for (int k = 0; k < 4; k++) { x[k] = rev ? ex[3 - k] : ex[k]; y[k] = rev ? ey[3 - k] : ey[k]; }
+    float sl[3];
+    int gl[3], nl = 0;
+    cubic_crossings(x, y, sl, gl, &nl);
+    const bool flip = rev != against;          // device-canonical order against the sample order
+    int corr = 0;
+    float yk = __ldg(&pv[0]).y - qb;
+    for (int k = 0; k < K; k++) {
+        const float4 v0 = __ldg(&pv[k]), v1 = __ldg(&pv[k + 1]);
+        const float yk1 = v1.y - qb;
+        int d = 0;
+        if (yk <= 0.f && 0.f < yk1) {              // upward chord: crossing right of q iff det[a, b, d] < 0
+            const float4 A = __ldg(&xv[k]), B = __ldg(&xv[k + 1]);
+            const float3 Af = make_float3(A.x, A.y, A.z), Bf = make_float3(B.x, B.y, B.z);
+            const float3 a = make_float3(A.x - P.x, A.y - P.y, A.z - P.z), b = make_float3(B.x - P.x, B.y - P.y, B.z - P.z);
+            if (edge_sign(a, b, Af, Bf, P, D, cnt, status) < 0) d += 1;
+        } else if (yk1 <= 0.f && 0.f < yk) {       // downward chord: iff det[a, b, d] > 0
+            const float4 A = __ldg(&xv[k]), B = __ldg(&xv[k + 1]);
+            const float3 Af = make_float3(A.x, A.y, A.z), Bf = make_float3(B.x, B.y, B.z);
+            const float3 a = make_float3(A.x - P.x, A.y - P.y, A.z - P.z), b = make_float3(B.x - P.x, B.y - P.y, B.z - P.z);
+            if (edge_sign(a, b, Af, Bf, P, D, cnt, status) > 0) d -= 1;
+        }
+        for (int j = 0; j < nl; j++) {             // arc crossings attributed to this chord
+            const float sh = flip ? 1.f - sl[j] : sl[j];
+            int kk = (int)(sh * (float)K);
+            kk = kk < 0 ? 0 : (kk >= K ? K - 1 : kk);
+            if (kk == k) d -= flip ? -gl[j] : gl[j];
+        }
+        if (d) {
+            const float z0 = v0.z - qc, z1 = v1.z - qc, dv = __ldg(&dev[k]);
+            const float zlo = fminf(z0, z1) - dv, zhi = fmaxf(z0, z1) + dv;
+            if (zlo > 0.f) corr += d;
+            else if (!(zhi <= 0.f)) *near = true;
+        }
+        yk = yk1;
+    }
+    (void)qa;
+    return against ? -corr : corr;
+}
+
+// One ray per thread, with the (ray, patch) work compacted per warp: each
+// lane walks the patches listed in its bin cell and keeps those whose
+// projected box holds its ray and that reach in front of it; the kept pairs
+// go to a per-warp buffer, and whenever 32 are pending every lane takes one
+// (the ray's coordinates fetched from its lane by a shuffle) and adds the
+// patch's winding number to that ray's total in shared memory.  The winding
+// computation is long and most rays meet no patch, so this keeps the lanes
+// busy instead of one lane per warp.
 __global__ void __launch_bounds__(128) chi_patches_kernel(const float4 *__restrict__ qnet,
                                                           const float4 *__restrict__ box,
                                                           const float *__restrict__ zmax,
                                                           const int32_t *__restrict__ bin_off,
                                                           const int32_t *__restrict__ bin_idx, int nbx, int nby,
-                                                          float bx0, float by0, float binv, Frame fr, QuerySrc q,
-                                                          int32_t *__restrict__ chi, unsigned long long *cnt,
-                                                          int *status) {
+                                                          float bx0, float by0, float binv,
+                                                          const int32_t *__restrict__ bedge,
+                                                          const float4 *__restrict__ pl_proj,
+                                                          const float4 *__restrict__ pl_xyz,
+                                                          const float *__restrict__ pl_dev, int K, Frame fr,
+                                                          QuerySrc q, int32_t *__restrict__ chi,
+                                                          unsigned long long *cnt, int *status) {
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= q.n) return;
-    const float3 p = query_point3(q, i);
-    const float a = fmaf(p.z, fr.e1[2], fmaf(p.y, fr.e1[1], p.x * fr.e1[0]));
-    const float b = fmaf(p.z, fr.e2[2], fmaf(p.y, fr.e2[1], p.x * fr.e2[0]));
-    const float c = fmaf(p.z, fr.dh[2], fmaf(p.y, fr.dh[1], p.x * fr.dh[0]));
-    int wsum = 0, tests = 0;
-    bool near = false;
-    const float fx = (a - bx0) * binv, fy = (b - by0) * binv;
-    if (fx >= 0.f && fy >= 0.f && fx < (float)nbx && fy < (float)nby) {
-        const int cell = (int)fy * nbx + (int)fx;
-        for (int k = bin_off[cell]; k < bin_off[cell + 1]; k++) {
-            const int t = bin_idx[k];
-            const float4 bb = __ldg(&box[t]);
-            if (a < bb.x || a > bb.y || b < bb.z || b > bb.w || !(__ldg(&zmax[t]) > c)) continue;
-            float X[16], Y[16], Z[16];
-#pragma unroll
-            for (int m = 0; m < 16; m++) {
-                const float4 v = __ldg(&qnet[16 * (int64_t)t + m]);
-                X[m] = v.x - a;
-                Y[m] = v.y - b;
-                Z[m] = v.z - c;
-            }
-            wsum += patch_winding(X, Y, Z, &near);
-            tests++;
+    const bool valid = i < q.n;
+    float a = 0.f, b = 0.f, c = 0.f;
+    float3 p = make_float3(0.f, 0.f, 0.f);
+    int k0 = 0, k1 = 0;
+    if (valid) {
+        p = query_point3(q, i);
+        a = fmaf(p.z, fr.e1[2], fmaf(p.y, fr.e1[1], p.x * fr.e1[0]));
+        b = fmaf(p.z, fr.e2[2], fmaf(p.y, fr.e2[1], p.x * fr.e2[0]));
+        c = fmaf(p.z, fr.dh[2], fmaf(p.y, fr.dh[1], p.x * fr.dh[0]));
+        const float fx = (a - bx0) * binv, fy = (b - by0) * binv;
+        if (fx >= 0.f && fy >= 0.f && fx < (float)nbx && fy < (float)nby) {
+            const int cell = (int)fy * nbx + (int)fx;
+            k0 = bin_off[cell];
+            k1 = bin_off[cell + 1];
         }
     }
-    chi[i] = -wsum;                      // e1 x e2 = -dh
+    __shared__ int s_pair[128 / 32][64];
+    __shared__ int s_acc[128 / 32][32];
+    __shared__ unsigned s_near[128 / 32];
+    int *pairs = s_pair[w];
+    s_acc[w][lane] = 0;
+    if (lane == 0) s_near[w] = 0u;
+    __syncwarp();
+    int npairs = 0, tests = 0;
+    // process the first min(n, 32) pending pairs, one per lane; returns how many remain
+    auto flush = [&](int n) -> int {
+        const int m = n < 32 ? n : 32;
+        const int pr = lane < m ? pairs[lane] : -1;
+        const int ql = pr >= 0 ? (pr & 31) : lane;
+        const float qa = __shfl_sync(FULL, a, ql), qb = __shfl_sync(FULL, b, ql), qc = __shfl_sync(FULL, c, ql);
+        const float3 qp = make_float3(__shfl_sync(FULL, p.x, ql), __shfl_sync(FULL, p.y, ql),
+                                      __shfl_sync(FULL, p.z, ql));
+        if (pr >= 0) {
+            const int t = pr >> 5;
+            float X[16], Y[16], Z[16];
+#pragma unroll
+            for (int m2 = 0; m2 < 16; m2++) {
+                const float4 v = __ldg(&qnet[16 * (int64_t)t + m2]);
+                X[m2] = v.x - qa;
+                Y[m2] = v.y - qb;
+                Z[m2] = v.z - qc;
+            }
+            bool near = false;
+            int wn = patch_winding(X, Y, Z, &near);
+            if (bedge) {
+                // edges on the surface boundary: chords instead of the curve
+                static const int EIDX[4][4] = {{0, 4, 8, 12}, {12, 13, 14, 15}, {15, 11, 7, 3}, {3, 2, 1, 0}};
+                const int4 be = *(const int4 *)&bedge[4 * (int64_t)t];
+                const int codes[4] = {be.x, be.y, be.z, be.w};
+                for (int e = 0; e < 4; e++) {
+                    if (codes[e] < 0) continue;
+                    float ex[4], ey[4];
+                    for (int m2 = 0; m2 < 4; m2++) { ex[m2] = X[EIDX[e][m2]]; ey[m2] = Y[EIDX[e][m2]]; }
+                    const int cv = codes[e] >> 1;
+                    const int64_t o = (int64_t)cv * (K + 1);
+                    wn += boundary_edge_correction(ex, ey, pl_proj + o, pl_xyz + o, pl_dev + (int64_t)cv * K, K,
+                                                   (codes[e] & 1) != 0, qa, qb, qc, qp,
+                                                   make_float3(fr.d[0], fr.d[1], fr.d[2]), cnt, status, &near);
+                }
+            }
+            if (wn) atomicAdd(&s_acc[w][ql], wn);
+            if (near) atomicOr(&s_near[w], 1u << ql);
+        }
+        const int rem = n - m;
+        __syncwarp();
+        const int moved = lane < rem ? pairs[m + lane] : 0;
+        __syncwarp();
+        if (lane < rem) pairs[lane] = moved;
+        __syncwarp();
+        return rem;
+    };
+    // all lanes step through their own candidate lists together
+    for (int k = k0;; k++) {
+        const bool more = k < k1;
+        if (!__any_sync(FULL, more)) break;
+        bool keep = false;
+        int t = 0;
+        if (more) {
+            t = bin_idx[k];
+            const float4 bb = __ldg(&box[t]);
+            keep = !(a < bb.x || a > bb.y || b < bb.z || b > bb.w) && __ldg(&zmax[t]) > c;
+        }
+        const unsigned mk = __ballot_sync(FULL, keep);
+        if (mk) {
+            if (keep) pairs[npairs + __popc(mk & ((1u << lane) - 1u))] = (t << 5) | lane;
+            npairs += __popc(mk);
+            tests += keep;
+            __syncwarp();
+            if (npairs >= 32) npairs = flush(npairs);
+        }
+    }
+    while (npairs > 0) npairs = flush(npairs);
+    __syncwarp();
+    const bool near = (s_near[w] >> lane) & 1u;
+    if (valid) chi[i] = -s_acc[w][lane];          // e1 x e2 = -dh
     if (cnt) {
         if (tests) atomicAdd(&cnt[CNT_TRI_TESTS], (unsigned long long)tests);
-        if (near) atomicAdd(&cnt[CNT_STACK_OVERFLOW], 1ull);
+        if (valid && near) atomicAdd(&cnt[CNT_STACK_OVERFLOW], 1ull);
     }
     (void)status;
 }
@@ -259,14 +416,18 @@ cudaError_t launch_chi_patches(const PatchSet &ps, const QuerySrc &q, int32_t *c
     const int64_t blocks = (q.n + 127) / 128;
     if (blocks > 0x7fffffff) return cudaErrorInvalidValue;
     chi_patches_kernel<<<(unsigned)blocks, 128, 0, st>>>(ps.qnet, ps.box, ps.zmax, ps.bin_off, ps.bin_idx, ps.nbx,
-                                                         ps.nby, ps.bx0, ps.by0, ps.binv, ps.frame, q, chi, cnt,
-                                                         status);
+                                                         ps.nby, ps.bx0, ps.by0, ps.binv,
+                                                         ps.n_bcurves ? ps.bedge : nullptr, ps.pl_proj, ps.pl_xyz,
+                                                         ps.pl_dev, ps.segments, ps.frame, q, chi, cnt, status);
     return cudaGetLastError();
 }
 
 // ---- host ----------------------------------------------------------------------
 
-void patches_free(PatchSet &ps) {
+// the per-direction tables
+static void patches_free_dir(PatchSet &ps) {
+    if (ps.pl_proj) cudaFree(ps.pl_proj);
+    ps.pl_proj = nullptr;
     if (ps.bframe) cudaFree(ps.bframe);
     if (ps.qnet) cudaFree(ps.qnet);
     if (ps.box) cudaFree(ps.box);
@@ -278,6 +439,14 @@ void patches_free(PatchSet &ps) {
     ps.valid = false;
 }
 
+void patches_free(PatchSet &ps) {
+    patches_free_dir(ps);
+    if (ps.bedge) cudaFree(ps.bedge);
+    if (ps.pl_xyz) cudaFree(ps.pl_xyz);
+    if (ps.pl_dev) cudaFree(ps.pl_dev);
+    ps.bedge = nullptr; ps.pl_xyz = nullptr; ps.pl_dev = nullptr;
+}
+
 gwn_status patches_prepare(gwn_geom *g, const float d[3]) {
     PatchSet &ps = g->ps;
     if (!isfinite(d[0]) || !isfinite(d[1]) || !isfinite(d[2]) || (d[0] == 0.f && d[1] == 0.f && d[2] == 0.f)) {
@@ -285,7 +454,7 @@ gwn_status patches_prepare(gwn_geom *g, const float d[3]) {
         return GWN_E_INVALID;
     }
     if (ps.valid && memcmp(ps.dkey, d, sizeof(float) * 3) == 0) return GWN_OK;
-    patches_free(ps);
+    patches_free_dir(ps);
     const Frame fr = make_frame(d);
     const int64_t n = ps.n;
     // projected control nets (float64 dot products rounded once) and boxes
@@ -351,12 +520,23 @@ gwn_status patches_prepare(gwn_geom *g, const float d[3]) {
     up((void **)&ps.zmax, zm.data(), sizeof(float) * zm.size());
     up((void **)&ps.bin_off, cnt.data(), sizeof(int32_t) * cnt.size());
     up((void **)&ps.bin_idx, idx.data(), sizeof(int32_t) * idx.size());
+    if (e == cudaSuccess && !ps.h_pl_xyz.empty()) {       // projected boundary samples
+        std::vector<float4> pp(ps.h_pl_xyz.size());
+        const float *e3[3] = {fr.e1, fr.e2, fr.dh};
+        for (size_t k = 0; k < pp.size(); k++) {
+            const float4 v = ps.h_pl_xyz[k];
+            double r[3];
+            for (int c = 0; c < 3; c++) r[c] = (double)v.x * e3[c][0] + (double)v.y * e3[c][1] + (double)v.z * e3[c][2];
+            pp[k] = make_float4((float)r[0], (float)r[1], (float)r[2], 0.f);
+        }
+        up((void **)&ps.pl_proj, pp.data(), sizeof(float4) * pp.size());
+    }
     if (e == cudaSuccess && g->n_bseq > 0) {
         e = cudaMalloc(&ps.bframe, sizeof(float4) * 2 * g->n_bseq);
         if (e == cudaSuccess) e = launch_bframe(g->bseq, g->n_bseq, fr, ps.bframe, g->ctx->stream);
     }
     if (e != cudaSuccess) {
-        patches_free(ps);
+        patches_free_dir(ps);
         return cuda_fail(e, "patch preparation");
     }
     ps.frame = fr;
@@ -449,6 +629,7 @@ extern "C" GWN_API gwn_status gwn_patches_create(gwn_ctx *ctx, const float *ctrl
         return id;
     };
     std::vector<std::pair<int32_t, int32_t>> bedges;
+    std::map<Key, int32_t> curve_id;             // boundary curves: id in the sample tables
     for (auto &kv : net) {
         const int m = kv.second;
         if (m == 0) continue;
@@ -459,6 +640,7 @@ extern "C" GWN_API gwn_status gwn_patches_create(gwn_ctx *ctx, const float *ctrl
             for (int q = 0; q < 3; q++) flat = flat && c[k][q] == c[0][q];
         if (flat) continue;                       // a collapsed edge bounds nothing
         std::vector<int32_t> ids(segments + 1);
+        std::vector<float4> xs(segments + 1);
         for (int s = 0; s <= segments; s++) {
             float x[3];
             if (s == 0 || s == segments) {
@@ -470,7 +652,42 @@ extern "C" GWN_API gwn_status gwn_patches_create(gwn_ctx *ctx, const float *ctrl
                     x[q] = (float)(b[0] * c[0][q] + b[1] * c[1][q] + b[2] * c[2][q] + b[3] * c[3][q]);
             }
             ids[s] = vertex(x);
+            xs[s] = make_float4(x[0], x[1], x[2], 0.f);
         }
+        // per chord, a bound on the distance between the arc over [s_k, s_k+1]
+        // and the chord: the arc lies in the hull of its own control points
+        // (the cubic restricted to the interval), each within the bound of the
+        // chord segment; widened for the float32 rounding of the samples
+        curve_id[kv.first] = (int32_t)ps.n_bcurves++;
+        for (int s = 0; s < segments; s++) {
+            const double u0 = (double)s / segments, u1 = (double)(s + 1) / segments;
+            double r[4][3];
+            for (int q = 0; q < 3; q++) {
+                // de Casteljau: split at u0 (right part), then at (u1 - u0) / (1 - u0) (left part)
+                double p0 = c[0][q], p1 = c[1][q], p2 = c[2][q], p3 = c[3][q];
+                double a = p0 + u0 * (p1 - p0), b = p1 + u0 * (p2 - p1), cc = p2 + u0 * (p3 - p2);
+                double d2 = a + u0 * (b - a), e2 = b + u0 * (cc - b), m0 = d2 + u0 * (e2 - d2);
+                p0 = m0; p1 = e2; p2 = cc;   // right part [u0, 1]: m0, e2, cc, p3
+                const double t = (u1 - u0) / (1.0 - u0);
+                a = p0 + t * (p1 - p0); b = p1 + t * (p2 - p1); cc = p2 + t * (p3 - p2);
+                d2 = a + t * (b - a); e2 = b + t * (cc - b);
+                r[0][q] = p0; r[1][q] = a; r[2][q] = d2; r[3][q] = d2 + t * (e2 - d2);
+            }
+            const float4 A = xs[s], B = xs[s + 1];
+            const double ab[3] = {(double)B.x - A.x, (double)B.y - A.y, (double)B.z - A.z};
+            const double L2 = ab[0] * ab[0] + ab[1] * ab[1] + ab[2] * ab[2];
+            double dmax = 0.0, scale = 0.0;
+            for (int k = 0; k < 4; k++) {
+                const double w[3] = {r[k][0] - A.x, r[k][1] - A.y, r[k][2] - A.z};
+                double tt = L2 > 0.0 ? (w[0] * ab[0] + w[1] * ab[1] + w[2] * ab[2]) / L2 : 0.0;
+                tt = tt < 0.0 ? 0.0 : (tt > 1.0 ? 1.0 : tt);
+                const double dd[3] = {w[0] - tt * ab[0], w[1] - tt * ab[1], w[2] - tt * ab[2]};
+                dmax = std::max(dmax, sqrt(dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2]));
+                scale = std::max(scale, fabs(r[k][0]) + fabs(r[k][1]) + fabs(r[k][2]));
+            }
+            ps.h_pl_dev.push_back((float)(dmax * (1.0 + 1e-3) + 4e-7 * scale));
+        }
+        ps.h_pl_xyz.insert(ps.h_pl_xyz.end(), xs.begin(), xs.end());
         for (int r = 0; r < (m > 0 ? m : -m); r++)
             for (int s = 0; s < segments; s++) {
                 if (ids[s] == ids[s + 1]) continue;
@@ -478,6 +695,22 @@ extern "C" GWN_API gwn_status gwn_patches_create(gwn_ctx *ctx, const float *ctrl
                 else bedges.emplace_back(ids[s + 1], ids[s]);
             }
     }
+    ps.h_bedge.assign(4 * (size_t)n_patches, -1);
+    for (int64_t t = 0; t < n_patches && ps.n_bcurves > 0; t++)
+        for (int e = 0; e < 4; e++) {
+            Key fwd, rev;
+            for (int k = 0; k < 4; k++) {
+                const float *P = &ps.h_ctrl[48 * t + 3 * (4 * EDGE[e][k][0] + EDGE[e][k][1])];
+                const float *R = &ps.h_ctrl[48 * t + 3 * (4 * EDGE[e][3 - k][0] + EDGE[e][3 - k][1])];
+                for (int c = 0; c < 3; c++) {
+                    memcpy(&fwd[3 * k + c], &P[c], 4);
+                    memcpy(&rev[3 * k + c], &R[c], 4);
+                }
+            }
+            const bool against = !(fwd <= rev);
+            auto it = curve_id.find(against ? rev : fwd);
+            if (it != curve_id.end()) ps.h_bedge[4 * t + e] = (it->second << 1) | (against ? 1 : 0);
+        }
     BoundaryLoops bl;
     gwn_status s = chain_unit_edges(bedges, (int64_t)(hv.size() / 3), bl);
     if (s != GWN_OK) return s;
@@ -495,13 +728,21 @@ extern "C" GWN_API gwn_status gwn_patches_create(gwn_ctx *ctx, const float *ctrl
     g->n_bseq = (int64_t)rec.size();
     g->nv = (int64_t)(hv.size() / 3);
     cudaError_t e = cudaSuccess;
-    if (g->n_bseq) {
-        e = cudaMalloc(&g->bseq, sizeof(float4) * g->n_bseq);
-        if (e == cudaSuccess) e = cudaMemcpy(g->bseq, rec.data(), sizeof(float4) * g->n_bseq, cudaMemcpyHostToDevice);
+    auto up = [&](void **dst, const void *src, size_t bytes) {
+        if (e != cudaSuccess || bytes == 0) return;
+        e = cudaMalloc(dst, bytes);
+        if (e == cudaSuccess) e = cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice);
+    };
+    up((void **)&g->bseq, rec.data(), sizeof(float4) * rec.size());
+    if (ps.n_bcurves > 0) {
+        up((void **)&ps.bedge, ps.h_bedge.data(), sizeof(int32_t) * ps.h_bedge.size());
+        up((void **)&ps.pl_xyz, ps.h_pl_xyz.data(), sizeof(float4) * ps.h_pl_xyz.size());
+        up((void **)&ps.pl_dev, ps.h_pl_dev.data(), sizeof(float) * ps.h_pl_dev.size());
     }
     if (e != cudaSuccess) {
         if (g->bseq) cudaFree(g->bseq);
         g->bseq = nullptr;
+        patches_free(ps);
         return cuda_fail(e, "gwn_patches_create");
     }
     ctx_add_geometry(ctx);

@@ -114,3 +114,26 @@ def test_patch_errors(gwn, ctx):
         gwn.Patches(ctx, bad)
     with pytest.raises(pkg.GwnError):
         gwn.Patches(ctx, gen.patch_spheroid(n=1).ctrl, segments=0)
+
+
+def test_boundary_sampling_has_no_jumps(gwn, ctx):
+    """The boundary term runs over the sampled boundary, so the crossing count
+    must be that of the surface bounded by the samples: a ray through the thin
+    region between a boundary curve and its chords must not see w jump by one.
+    With 8 and 16 segments per curve the regions are wide (sagitta ~1e-3):
+    across a 96^3 grid the two results may differ only by the sampling error,
+    never by a jump, and both match the definition within that error."""
+    pc = gen.patch_spheroid(n=2, amp=0.08, open_faces=(4,), seed=7)
+    g = gen.Grid((-1.3,) * 3, (1.3,) * 3, (96, 96, 96))
+    grid = gwn.Grid(g.lo, g.hi, g.dims)
+    w8 = gwn.Patches(ctx, pc.ctrl, segments=8).eval(grid, pc.d).cpu().numpy()
+    w16 = gwn.Patches(ctx, pc.ctrl, segments=16).eval(grid, pc.d).cpu().numpy()
+    P = gen.grid_points(g)
+    away = _away(P, 0.08 + 0.05)
+    dw = np.abs(w8 - w16)[away]
+    assert dw.max() < 0.05, dw.max()
+    rng = np.random.default_rng(1)
+    idx = np.nonzero(away)[0]
+    idx = np.concatenate([idx[np.argsort(-np.abs(w8 - w16)[idx])[:40]], rng.choice(idx, 200, replace=False)])
+    wd = oracle.w3d_patches_quad(pc.ctrl, P[idx])
+    assert np.abs(w16[idx] - wd).max() < 0.02
