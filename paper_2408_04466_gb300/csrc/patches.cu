@@ -104,14 +104,25 @@ __device__ int cubic_crossings(const float *x, const float *y, float *sl = nullp
         const float yb = k + 2 == nc ? y[3] : ev(y, sb);
         const bool up = ya <= 0.f && 0.f < yb, down = yb <= 0.f && 0.f < ya;
         if (up || down) {
-            // the root of y on [cut[k], sb]: bisection keeping y(lo) <= 0 < y(hi)
+            // the root of y on the monotone piece: Newton from the linear
+            // guess, kept inside the bracket y(lo) <= 0 < y(hi) (bisection
+            // when a step leaves it); the side decision x(s) > 0 needs the
+            // root only to the accuracy of the curve itself
             float lo = up ? cut[k] : sb, hi = up ? sb : cut[k];
+            const float yl = up ? ya : yb, yh = up ? yb : ya;
+            float sr = lo + (hi - lo) * __fdividef(-yl, yh - yl);
             for (int it = 0; it < 40; it++) {
-                const float mid = 0.5f * (lo + hi);
-                if (mid == lo || mid == hi) break;
-                if (ev(y, mid) <= 0.f) lo = mid; else hi = mid;
+                const float g = ev(y, sr);
+                if (g <= 0.f) lo = sr; else hi = sr;
+                const float v = 1.f - sr;
+                const float dg = 3.f * (v * v * (y[1] - y[0]) + 2.f * sr * v * (y[2] - y[1]) + sr * sr * (y[3] - y[2]));
+                float sn = sr - __fdividef(g, dg);
+                const float mn = fminf(lo, hi), mx = fmaxf(lo, hi);
+                if (!(sn > mn && sn < mx)) sn = 0.5f * (lo + hi);
+                const float step = fabsf(sn - sr);
+                sr = sn;
+                if (step <= 1e-7f || mx - mn <= 1e-7f) break;
             }
-            const float sr = 0.5f * (lo + hi);
             if (ev(x, sr) > 0.f) {
                 count += up ? 1 : -1;
                 if (sl && *nl < 3) { sl[*nl] = sr; gl[*nl] = up ? 1 : -1; (*nl)++; }
@@ -242,6 +253,11 @@ __device__ int boundary_edge_correction(const float *ex, const float *ey, const 
                                         const float4 *__restrict__ xv, const float *__restrict__ dev, int K,
                                         bool against, float qa, float qb, float qc, float3 P, float3 D,
                                         unsigned long long *cnt, int *status, bool *near) {
+    // the half-line y = 0, x > 0 misses the edge's control hull (which holds
+    // the arc and its chords): nothing to replace
+    if (fminf(fminf(ey[0], ey[1]), fminf(ey[2], ey[3])) > 0.f || fmaxf(fmaxf(ey[0], ey[1]), fmaxf(ey[2], ey[3])) < 0.f ||
+        fmaxf(fmaxf(ex[0], ex[1]), fmaxf(ex[2], ex[3])) < 0.f)
+        return 0;
     // curve crossings (as the winding number evaluates them), in the canonical sample order
     const bool rev = canon_reversed(ex[0], ey[0], ex[1], ey[1], ex[2], ey[2], ex[3], ey[3]);
     float x[4], y[4];
