@@ -192,15 +192,23 @@ __device__ void subnet(const float *R, int level, int iu, int iv, float *N) {
     }
 }
 
+// winding count of a patch cut by the plane through the query (out of line:
+// rare, and kept out of the hot loop's instruction footprint)
+__device__ __noinline__ int patch_winding_straddling(const float *X, const float *Y, const float *Z, bool *near);
+
 // signed crossing count (winding convention) of one patch with the ray of the
 // query at the origin of (X, Y, Z); *near set when a straddling quarter
 // reached PATCH_MAXL
-__device__ int patch_winding(const float *X, const float *Y, const float *Z, bool *near) {
+__device__ __forceinline__ int patch_winding(const float *X, const float *Y, const float *Z, bool *near) {
     float zmin = Z[0], zmax = Z[0];
     for (int k = 1; k < 16; k++) { zmin = fminf(zmin, Z[k]); zmax = fmaxf(zmax, Z[k]); }
     if (zmax <= 0.f) return 0;
     if (zmin > 0.f) return net_winding(X, Y);
-    // straddling: depth-first over quarters (level, iu, iv) packed as
+    return patch_winding_straddling(X, Y, Z, near);
+}
+
+__device__ __noinline__ int patch_winding_straddling(const float *X, const float *Y, const float *Z, bool *near) {
+    // depth-first over quarters (level, iu, iv) packed as
     // level << 48 | iu << 24 | iv
     long long stack[PATCH_STACK];
     int sp = 0, total = 0;
@@ -249,7 +257,7 @@ __device__ int patch_winding(const float *X, const float *Y, const float *Z, boo
 // the query); pv: the curve's projected samples (canonical order); xv: the
 // same samples in 3D; dev: per chord arc-chord bound; against: the patch edge
 // runs against the canonical order.
-__device__ int boundary_edge_correction(const float *ex, const float *ey, const float4 *__restrict__ pv,
+__device__ __noinline__ int boundary_edge_correction(const float *ex, const float *ey, const float4 *__restrict__ pv,
                                         const float4 *__restrict__ xv, const float *__restrict__ dev, int K,
                                         bool against, float qa, float qb, float qc, float3 P, float3 D,
                                         unsigned long long *cnt, int *status, bool *near) {
