@@ -421,17 +421,12 @@ static void free_geom_device(gwn_geom *g) {
     ChainSet &cs = g->cs;
     if (cs.ctrl) cudaFree(cs.ctrl);
     if (cs.chain_off) cudaFree(cs.chain_off);
-    if (cs.piece_seg) cudaFree(cs.piece_seg);
-    if (cs.piece_u) cudaFree(cs.piece_u);
     if (cs.piece_y) cudaFree(cs.piece_y);
-    if (cs.piece_uT && cs.piece_uT != (void *)cs.piece_u) cudaFree(cs.piece_uT);
     if (cs.piece_yT && cs.piece_yT != (void *)cs.piece_y) cudaFree(cs.piece_yT);
     if (cs.piece_xT) cudaFree(cs.piece_xT);
     if (cs.piece_rec) cudaFree(cs.piece_rec);
     if (cs.bucket_off) cudaFree(cs.bucket_off);
     if (cs.bucket_idx) cudaFree(cs.bucket_idx);
-    if (cs.piece_chain) cudaFree(cs.piece_chain);
-    if (cs.chain_piece_off) cudaFree(cs.chain_piece_off);
     patches_free(g->ps);
 }
 
@@ -738,32 +733,17 @@ GWN_API gwn_status gwn_bezier2d_create(gwn_ctx *ctx, const void *ctrl, int dtype
     if (e == cudaSuccess) e = cudaMalloc(&cs.chain_off, sizeof(int64_t) * (n_chains + 1));
     if (e == cudaSuccess)
         e = cudaMemcpy(cs.chain_off, chain_offsets, sizeof(int64_t) * (n_chains + 1), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMalloc(&cs.chain_piece_off, sizeof(int64_t) * (n_chains + 1));
-    if (e == cudaSuccess)
-        e = cudaMemcpy(cs.chain_piece_off, cs.h_chain_piece_off.data(), sizeof(int64_t) * (n_chains + 1),
-                       cudaMemcpyHostToDevice);
     size_t np = (size_t)std::max<int64_t>(cs.n_pieces, 1);
-    if (e == cudaSuccess) e = cudaMalloc(&cs.piece_seg, sizeof(int64_t) * np);
-    if (e == cudaSuccess) e = cudaMalloc(&cs.piece_u, sizeof(double) * 2 * np);
     if (e == cudaSuccess) e = cudaMalloc(&cs.piece_y, sizeof(double) * 2 * np);
-    if (e == cudaSuccess) e = cudaMalloc(&cs.piece_chain, sizeof(int32_t) * np);
-    if (e == cudaSuccess && cs.n_pieces) {
-        e = cudaMemcpy(cs.piece_seg, pseg.data(), sizeof(int64_t) * cs.n_pieces, cudaMemcpyHostToDevice);
-        if (e == cudaSuccess) e = cudaMemcpy(cs.piece_u, pu.data(), sizeof(double) * 2 * cs.n_pieces, cudaMemcpyHostToDevice);
-        if (e == cudaSuccess) e = cudaMemcpy(cs.piece_y, py.data(), sizeof(double) * 2 * cs.n_pieces, cudaMemcpyHostToDevice);
-        if (e == cudaSuccess) e = cudaMemcpy(cs.piece_chain, pch.data(), sizeof(int32_t) * cs.n_pieces, cudaMemcpyHostToDevice);
-    }
+    if (e == cudaSuccess && cs.n_pieces)
+        e = cudaMemcpy(cs.piece_y, py.data(), sizeof(double) * 2 * cs.n_pieces, cudaMemcpyHostToDevice);
     // the kernels read the piece tables in the chain's precision
     if (e == cudaSuccess && dtype == GWN_F64) {
-        cs.piece_uT = cs.piece_u;
         cs.piece_yT = cs.piece_y;
     } else if (e == cudaSuccess) {
-        std::vector<float> fu(pu.begin(), pu.end()), fy(py.begin(), py.end());
-        fu.resize(2 * np);
+        std::vector<float> fy(py.begin(), py.end());
         fy.resize(2 * np);
-        e = cudaMalloc(&cs.piece_uT, sizeof(float) * 2 * np);
-        if (e == cudaSuccess) e = cudaMalloc(&cs.piece_yT, sizeof(float) * 2 * np);
-        if (e == cudaSuccess) e = cudaMemcpy(cs.piece_uT, fu.data(), sizeof(float) * 2 * np, cudaMemcpyHostToDevice);
+        e = cudaMalloc(&cs.piece_yT, sizeof(float) * 2 * np);
         if (e == cudaSuccess) e = cudaMemcpy(cs.piece_yT, fy.data(), sizeof(float) * 2 * np, cudaMemcpyHostToDevice);
     }
     if (e == cudaSuccess) {        // per-piece records for the row kernel

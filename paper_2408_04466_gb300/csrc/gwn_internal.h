@@ -129,26 +129,20 @@ struct ChainSet {
     int64_t n_chains = 0, n_ctrl = 0, n_seg = 0, n_pieces = 0;
     void *ctrl = nullptr;          // [n_ctrl][2] of dtype
     int64_t *chain_off = nullptr;  // device [n_chains + 1] control point offsets
-    // y-monotone pieces: segment start index (control point index of P0),
-    // parameter interval, y range, direction, owning chain
-    int64_t *piece_seg = nullptr;
-    double *piece_u = nullptr;     // [n_pieces][2]
+    // y-monotone pieces (ordered by their lowest y within each chain): y at
+    // the ends of the piece's parameter interval
     double *piece_y = nullptr;     // [n_pieces][2] (y at u0, y at u1)
-    void *piece_uT = nullptr;      // piece_u in the chain dtype (aliases piece_u for float64)
     void *piece_yT = nullptr;      // piece_y in the chain dtype (aliases piece_y for float64)
     // point queries: the pieces' conservative x ranges (control hull of their
     // segment, chain dtype, [n_pieces][2]) and a y-bucket index of the pieces
     void *piece_xT = nullptr;
-    // per piece, in the chain dtype: its segment's control points (x0 y0 .. x3
-    // y3), u0, u1, y(u0), y(u1) -- one contiguous record, read by the row
-    // kernel without a dependent load through piece_seg
+    // per piece, in the chain dtype: the piece in local power form (see
+    // bezier2d.cu) -- one contiguous 16-byte aligned record per piece
     void *piece_rec = nullptr;
     int32_t *bucket_off = nullptr;     // [n_buckets + 1]
     int32_t *bucket_idx = nullptr;     // piece indices, bucket by bucket
     int32_t n_buckets = 0;
     double bucket_y0 = 0.0, bucket_inv_h = 0.0;   // bucket(y) = floor((y - y0) * inv_h), in the chain dtype
-    int32_t *piece_chain = nullptr;
-    int64_t *chain_piece_off = nullptr;  // device [n_chains + 1]
     std::vector<int64_t> h_chain_off, h_chain_piece_off;
     // host, per piece (pieces of a chain ordered by their lowest y): that
     // lowest y and the running maximum of the highest y over the chain's
