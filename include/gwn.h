@@ -109,7 +109,8 @@ typedef struct gwn_stats {
     int64_t n_cut_sign;         /* boundary-term pairs taken off the float32 path (exact branch or float64) */
     int64_t n_fp64_filter;      /* predicates settled by the float64 filter */
     int64_t n_exact;            /* predicates settled by exact expansion arithmetic */
-    int64_t n_stack_overflow;   /* traversals that overflowed (result invalid) */
+    int64_t n_stack_overflow;   /* traversals that overflowed (result invalid); patches: queries within the
+                                   subdivision limit of the surface (w undefined there) */
     int64_t n_tri_tests;        /* exact ray/triangle tests (3D) or roots (2D) */
     float ms_prepare;           /* per-direction preparation (BVH build) if it ran */
     float ms_traverse;          /* crossing counts */

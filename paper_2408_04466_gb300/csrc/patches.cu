@@ -259,7 +259,7 @@ __device__ __noinline__ int patch_winding_straddling(const float *X, const float
 // runs against the canonical order.
 __device__ __noinline__ int boundary_edge_correction(const float *ex, const float *ey, const float4 *__restrict__ pv,
                                         const float4 *__restrict__ xv, const float *__restrict__ dev, int K,
-                                        bool against, float qa, float qb, float qc, float3 P, float3 D,
+                                        bool against, float qb, float qc, float3 P, float3 D,
                                         unsigned long long *cnt, int *status, bool *near) {
     // the half-line y = 0, x > 0 misses the edge's control hull (which holds
     // the arc and its chords): nothing to replace
@@ -305,7 +305,6 @@ __device__ __noinline__ int boundary_edge_correction(const float *ex, const floa
         }
         yk = yk1;
     }
-    (void)qa;
     return against ? -corr : corr;
 }
 
@@ -388,7 +387,7 @@ __global__ void __launch_bounds__(128) chi_patches_kernel(const float4 *__restri
                     const int cv = codes[e] >> 1;
                     const int64_t o = (int64_t)cv * (K + 1);
                     wn += boundary_edge_correction(ex, ey, pl_proj + o, pl_xyz + o, pl_dev + (int64_t)cv * K, K,
-                                                   (codes[e] & 1) != 0, qa, qb, qc, qp,
+                                                   (codes[e] & 1) != 0, qb, qc, qp,
                                                    make_float3(fr.d[0], fr.d[1], fr.d[2]), cnt, status, &near);
                 }
             }
@@ -431,7 +430,6 @@ __global__ void __launch_bounds__(128) chi_patches_kernel(const float4 *__restri
         if (tests) atomicAdd(&cnt[CNT_TRI_TESTS], (unsigned long long)tests);
         if (valid && near) atomicAdd(&cnt[CNT_STACK_OVERFLOW], 1ull);
     }
-    (void)status;
 }
 
 cudaError_t launch_chi_patches(const PatchSet &ps, const QuerySrc &q, int32_t *chi, unsigned long long *cnt,

@@ -137,3 +137,60 @@ def test_boundary_sampling_has_no_jumps(gwn, ctx):
     idx = np.concatenate([idx[np.argsort(-np.abs(w8 - w16)[idx])[:40]], rng.choice(idx, 200, replace=False)])
     wd = oracle.w3d_patches_quad(pc.ctrl, P[idx])
     assert np.abs(w16[idx] - wd).max() < 0.02
+
+
+def test_flipped_face_and_collapsed_edge(gwn, ctx):
+    """Inconsistent orientation: one face's patches reversed (u and v swapped),
+    so the curves it shares with its neighbours run the same way on both sides
+    (net multiplicity 2, sampled twice) while its inner edges still cancel; and
+    a single patch with one edge collapsed to a point (that curve bounds
+    nothing).  Both against the oracle: exact chi, w within the sampling
+    error of the definition."""
+    pc = gen.patch_spheroid(n=2, amp=0.06, open_faces=(5,), seed=11)
+    ctrl = pc.ctrl.copy()
+    ctrl[:4] = np.swapaxes(ctrl[:4], 1, 2)                 # the first face, reversed
+    seg = 128
+    ps = gwn.Patches(ctx, ctrl, segments=seg)
+    info = ps.info()
+    # the open face's 8 curves once (2 of them on the flipped face), the 6 curves
+    # the flipped face shares with its 3 closed neighbours twice
+    assert info["n_boundary_edges"] == (8 + 2 * 6) * seg
+    rng = np.random.default_rng(4)
+    v = rng.standard_normal((600, 3))
+    P = (rng.uniform(0.3, 1.35, (600, 1)) * v / np.linalg.norm(v, axis=1, keepdims=True)).astype(np.float32)
+    P = P[_away(P, 0.06 + 0.04)]
+    wd, chio = _oracle_chi(ctrl, P, pc.d)
+    r = ps.eval(gwn.Points(P), pc.d, want_chi=True)
+    assert np.array_equal(r["chi"].cpu().numpy(), chio)
+    assert np.abs(r["w"].cpu().numpy() - wd).max() <= 1e-5
+    assert np.abs(np.rint(wd) - wd).max() > 0.1            # genuinely open: w not integer
+
+    # one patch, its u = 0 edge collapsed to the apex (a cone-like cap)
+    cap = np.zeros((1, 4, 4, 3), np.float32)
+    for i in range(4):
+        for j in range(4):
+            r_ = i / 3.0
+            th = 0.5 * np.pi * j / 3.0
+            cap[0, i, j] = (r_ * np.cos(th), r_ * np.sin(th), 0.4 * (1.0 - r_ * r_))
+    ps1 = gwn.Patches(ctx, cap, segments=256)
+    assert ps1.info()["n_boundary_edges"] == 3 * 256
+    Q = (rng.uniform(-1.0, 1.0, (400, 3)) * np.array([1.2, 1.2, 1.0])).astype(np.float32)
+    d1 = oracle.dist3d(*_cap_mesh(cap), Q)
+    Q = Q[d1 > 0.05]
+    wd1, chio1 = _oracle_chi(cap, Q, pc.d)
+    r1 = ps1.eval(gwn.Points(Q), pc.d, want_chi=True)
+    assert np.array_equal(r1["chi"].cpu().numpy(), chio1)
+    assert np.abs(r1["w"].cpu().numpy() - wd1).max() <= 1e-5
+
+
+def _cap_mesh(cap, k=64):
+    """a fine triangle mesh of the patch (only to keep test queries off it)"""
+    u = np.linspace(0, 1, k + 1)
+    b = np.stack([(1 - u) ** 3, 3 * u * (1 - u) ** 2, 3 * u ** 2 * (1 - u), u ** 3], 1)
+    X = np.einsum("ai,bj,ijc->abc", b, b, cap[0].astype(np.float64)).reshape(-1, 3).astype(np.float32)
+    F = []
+    for a in range(k):
+        for c in range(k):
+            i0 = a * (k + 1) + c
+            F += [(i0, i0 + k + 1, i0 + 1), (i0 + 1, i0 + k + 1, i0 + k + 2)]
+    return X, np.array(F, np.int32)
