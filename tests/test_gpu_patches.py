@@ -194,3 +194,26 @@ def _cap_mesh(cap, k=64):
             i0 = a * (k + 1) + c
             F += [(i0, i0 + k + 1, i0 + 1), (i0 + 1, i0 + k + 1, i0 + k + 2)]
     return X, np.array(F, np.int32)
+
+
+def test_patch_benchmark_workload_sampled(gwn, ctx):
+    """The benchmark configuration itself (320 patches, one face open, 64
+    segments per boundary curve, the full 256^3 grid in one call): exact chi
+    and w against the oracle on a seeded sample of the queries away from the
+    surface."""
+    pc = gen.patch_spheroid(n=8, amp=0.08, open_faces=(4,), grid_n=256, seed=0)
+    ps = gwn.Patches(ctx, pc.ctrl, segments=64)
+    g = pc.grid
+    r = ps.eval(gwn.Grid(g.lo, g.hi, g.dims), pc.d, want_chi=True)
+    rng = np.random.default_rng(17)
+    idx = rng.choice(g.n, 6000, replace=False)
+    P = gen.grid_points(g, index=idx)
+    keep = _away(P, 0.08 + 0.02)
+    idx, P = idx[keep][:1500], P[keep][:1500]
+    wd, chio = _oracle_chi(pc.ctrl, P, pc.d)
+    V, E = oracle.patch_boundary(pc.ctrl, 64)
+    B64 = oracle.bterm3d(V, E, P, pc.d)
+    w = r["w"].cpu().numpy()[idx]
+    assert np.array_equal(r["chi"].cpu().numpy()[idx], chio)
+    assert np.abs(w - (chio + B64)).max() <= 1e-6
+    assert np.abs(w - wd).max() <= 2e-5
