@@ -5,9 +5,9 @@
 //
 // The boundary term is taken over a polyline sampling of the surface's
 // boundary curves (the patch edge curves that no other patch cancels), as
-// the paper does for parametric surfaces ("we discretize the boundary ...
-// this boundary discretization may lead only to minor differences ... close
-// to the boundary"); it runs in the mesh boundary-term kernel.
+// the paper does for parametric surfaces (Sec. Implementation Details: only
+// the boundary is discretised, which changes w slightly near the boundary);
+// it runs in the mesh boundary-term kernel.
 //
 // Crossing count without root finding.  In the frame of d a ray is a point of
 // the projection plane (the query's (e1.p, e2.p)) plus the depths > dh.p.  A
