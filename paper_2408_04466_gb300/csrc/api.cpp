@@ -1191,6 +1191,24 @@ extern "C" GWN_API gwn_status gwn_backward(gwn_geom *g, const gwn_queries *q, co
     QuerySrc src;
     s = make_query_src(ctx, q, GWN_F32, src);
     if (s != GWN_OK) return s;
+    if (grad_p && grad_V && nq > 0 && g->n_bseq > 0) {
+        // both: one pass over the (query, edge) pairs
+        CK(cudaMemsetAsync(grad_V, 0, sizeof(float) * 3 * g->nv, ctx->stream), "clear grad_V");
+        s = ensure_vertex_lists(g);
+        if (s != GWN_OK) return s;
+        int chunks = grad_v_chunks(nq, g->n_bseq, ctx->sm_count);
+        size_t part = (sizeof(float) * 6 * (size_t)chunks * g->n_bseq + 255) & ~(size_t)255;
+        size_t partp = (grad_pv_partial_p_bytes(nq, g->n_bseq) + 255) & ~(size_t)255;
+        size_t recb = sizeof(float) * 3 * g->n_bseq;
+        cudaError_t e;
+        char *buf = (char *)arena_get(ctx, 0, part + partp + recb, &e);
+        if (!buf) return cuda_fail(e, "gradient workspace");
+        e = launch_grad_pv(g->bseq, g->n_bseq, src, grad_w, chunks, (float *)buf, (float *)(buf + part),
+                           (float *)(buf + part + partp), g->d_bvert, g->d_brec_off, g->d_brecs, g->n_bvert, grad_p,
+                           grad_V, ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "gradients");
+        return GWN_OK;
+    }
     if (grad_p) {
         cudaError_t e = launch_grad_p(g->bseq, g->n_bseq, src, grad_w, grad_p, ctx->stream);
         if (e != cudaSuccess) return cuda_fail(e, "grad_p");

@@ -161,6 +161,99 @@ __global__ void __launch_bounds__(GV_THREADS) grad_v_partial_kernel(const float4
     }
 }
 
+// Both gradients from one evaluation per (query, edge): the per-edge sums as
+// in grad_v_partial_kernel, and per query the sum of its dw/dp contributions
+// over the block's edges.  A warp takes its 32 edges against the tile's
+// queries 32 at a time: in step s lane l evaluates (its edge, query (l + s) mod
+// 32) and adds the contribution to the accumulator it holds, which is then
+// passed one lane down, so after 32 steps lane l holds query l's sum over the
+// warp's edges (3 shuffles per pair, a fixed order).  The warps are added in
+// order in shared memory, one value per (edge block, query, component) goes to
+// partial_p[(eb * 3 + c) * nq + q], and grad_p_reduce_kernel sums the edge
+// blocks in order.  Lanes without an edge, and queries past the tile's end,
+// contribute zero.
+__global__ void __launch_bounds__(GV_THREADS) grad_pv_partial_kernel(const float4 *__restrict__ bseq, int nb,
+                                                                     QuerySrc q, const float *__restrict__ grad_w,
+                                                                     int64_t chunk_len, float *__restrict__ partial,
+                                                                     float *__restrict__ partial_p) {
+    __shared__ float4 qs[GV_QTILE];
+    __shared__ float accp[GV_THREADS / 32][3][GV_QTILE];
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int k = blockIdx.x * GV_THREADS + threadIdx.x;
+    int chunk = blockIdx.y;
+    int64_t q0 = (int64_t)chunk * chunk_len;
+    int64_t q1 = q0 + chunk_len < q.n ? q0 + chunk_len : q.n;
+    bool active = k >= 1 && k < nb;
+    float4 A = active ? bseq[k - 1] : make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 B = active ? bseq[k] : make_float4(0.f, 0.f, 0.f, 0.f);
+    active = active && B.w != 0.f;
+    float ex = B.x - A.x, ey = B.y - A.y, ez = B.z - A.z;
+    float e2 = fmaxf(ex * ex + ey * ey + ez * ez, 1e-37f), inv_e2 = grcp(e2);
+    float sA[3] = {0.f, 0.f, 0.f}, sB[3] = {0.f, 0.f, 0.f};
+    for (int64_t t0 = q0; t0 < q1; t0 += GV_QTILE) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < GV_QTILE; i += GV_THREADS) {
+            int64_t qi = t0 + i;
+            if (qi < q1) {
+                float3 p = query_point3(q, qi);
+                qs[i] = make_float4(p.x, p.y, p.z, grad_w[qi] * GWN_INV_4PI);
+            } else {
+                qs[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        }
+        __syncthreads();
+        const int cnt = (int)(q1 - t0 < GV_QTILE ? q1 - t0 : GV_QTILE);
+        for (int base = 0; base < cnt; base += 32) {
+            float ax_ = 0.f, ay_ = 0.f, az_ = 0.f;      // accumulator of query base + ((lane + s) mod 32)
+            for (int st = 0; st < 32; st++) {
+                const int j = (lane + st) & 31;
+                if (active && base + j < cnt) {
+                    const float4 p = qs[base + j];
+                    EdgeGrad g = edge_grad(A.x - p.x, A.y - p.y, A.z - p.z, B.x - p.x, B.y - p.y, B.z - p.z, ex, ey,
+                                           ez, e2, inv_e2);
+                    float wa = -(g.i0 - g.i1) * p.w, wb = -g.i1 * p.w, wp = g.i0 * B.w * p.w;
+                    sA[0] = fmaf(g.cx, wa, sA[0]); sA[1] = fmaf(g.cy, wa, sA[1]); sA[2] = fmaf(g.cz, wa, sA[2]);
+                    sB[0] = fmaf(g.cx, wb, sB[0]); sB[1] = fmaf(g.cy, wb, sB[1]); sB[2] = fmaf(g.cz, wb, sB[2]);
+                    ax_ = fmaf(g.cx, wp, ax_); ay_ = fmaf(g.cy, wp, ay_); az_ = fmaf(g.cz, wp, az_);
+                }
+                // pass the accumulator one lane down: lane l now holds query (l + st + 1) mod 32
+                ax_ = __shfl_sync(FULL, ax_, (lane + 1) & 31);
+                ay_ = __shfl_sync(FULL, ay_, (lane + 1) & 31);
+                az_ = __shfl_sync(FULL, az_, (lane + 1) & 31);
+            }
+            // after 32 steps lane l holds query base + l
+            accp[warp][0][base + lane] = ax_;
+            accp[warp][1][base + lane] = ay_;
+            accp[warp][2][base + lane] = az_;
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < cnt; i += GV_THREADS)
+            for (int c = 0; c < 3; c++) {
+                float v = 0.f;
+                for (int w = 0; w < GV_THREADS / 32; w++) v += accp[w][c][i];
+                partial_p[((int64_t)blockIdx.x * 3 + c) * q.n + t0 + i] = v;
+            }
+    }
+    if (k < nb) {
+        float *o = partial + ((int64_t)chunk * nb + k) * 6;
+        o[0] = sA[0]; o[1] = sA[1]; o[2] = sA[2];
+        o[3] = sB[0]; o[4] = sB[1]; o[5] = sB[2];
+    }
+}
+
+// grad_p[q] = sum over the edge blocks, in order, of partial_p
+__global__ void grad_p_reduce_kernel(const float *__restrict__ partial_p, int n_eb, int64_t nq,
+                                     float *__restrict__ grad_p) {
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nq) return;
+    for (int c = 0; c < 3; c++) {
+        float v = 0.f;
+        for (int eb = 0; eb < n_eb; eb++) v += partial_p[((int64_t)eb * 3 + c) * nq + q];
+        grad_p[3 * q + c] = v;
+    }
+}
+
 // per record: total gradient of its vertex from the edge ending there (as B)
 // and the edge starting there (as A of record k+1), summed over chunks in
 // chunk order.
@@ -230,6 +323,28 @@ cudaError_t launch_grad_v(const float4 *bseq, int64_t nb, const QuerySrc &q, con
     grad_v_record_kernel<<<(unsigned)((nb + 255) / 256), 256, 0, st>>>(partial, n_chunks, (int)nb, bseq, rec_grad);
     grad_v_scatter_kernel<<<(unsigned)((n_bvert + 255) / 256), 256, 0, st>>>(rec_grad, bvert, rec_off, recs, n_bvert,
                                                                               grad_V);
+    return cudaGetLastError();
+}
+
+size_t grad_pv_partial_p_bytes(int64_t nq, int64_t nb) {
+    return sizeof(float) * 3 * (size_t)((nb + GV_THREADS - 1) / GV_THREADS) * (size_t)nq;
+}
+
+cudaError_t launch_grad_pv(const float4 *bseq, int64_t nb, const QuerySrc &q, const float *grad_w, int n_chunks,
+                           float *partial, float *partial_p, float *rec_grad, const int32_t *bvert,
+                           const int64_t *rec_off, const int32_t *recs, int64_t n_bvert, float *grad_p, float *grad_V,
+                           cudaStream_t st) {
+    if (nb == 0 || q.n == 0) return cudaSuccess;
+    int64_t chunk_len = (q.n + n_chunks - 1) / n_chunks;
+    const int n_eb = (int)((nb + GV_THREADS - 1) / GV_THREADS);
+    dim3 grid((unsigned)n_eb, (unsigned)n_chunks);
+    grad_pv_partial_kernel<<<grid, GV_THREADS, 0, st>>>(bseq, (int)nb, q, grad_w, chunk_len, partial, partial_p);
+    grad_p_reduce_kernel<<<(unsigned)((q.n + 255) / 256), 256, 0, st>>>(partial_p, n_eb, q.n, grad_p);
+    if (n_bvert > 0) {
+        grad_v_record_kernel<<<(unsigned)((nb + 255) / 256), 256, 0, st>>>(partial, n_chunks, (int)nb, bseq, rec_grad);
+        grad_v_scatter_kernel<<<(unsigned)((n_bvert + 255) / 256), 256, 0, st>>>(rec_grad, bvert, rec_off, recs,
+                                                                                  n_bvert, grad_V);
+    }
     return cudaGetLastError();
 }
 
