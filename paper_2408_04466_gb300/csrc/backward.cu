@@ -71,6 +71,38 @@ __device__ __forceinline__ EdgeGrad edge_grad(float ax, float ay, float az, floa
     return g;
 }
 
+// edge_grad for two queries at once (packed f32x2 add/mul/fma, MUFU per
+// element); the same formulas and clamps
+typedef float2 f2;
+struct EdgeGrad2 {
+    f2 cx, cy, cz, i0, i1;
+};
+__device__ __forceinline__ f2 mk2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ f2 mx2(f2 a, float lo) { return make_float2(fmaxf(a.x, lo), fmaxf(a.y, lo)); }
+__device__ __forceinline__ EdgeGrad2 edge_grad2(f2 ax, f2 ay, f2 az, f2 bx, f2 by, f2 bz, float ex, float ey,
+                                                float ez, float e2, float inv_e2) {
+    EdgeGrad2 g;
+    const f2 EX = mk2(ex), EY = mk2(ey), EZ = mk2(ez);
+    g.cx = __ffma2_rn(ay, EZ, __fmul2_rn(az, mk2(-ey)));
+    g.cy = __ffma2_rn(az, EX, __fmul2_rn(ax, mk2(-ez)));
+    g.cz = __ffma2_rn(ax, EY, __fmul2_rn(ay, mk2(-ex)));
+    const f2 del = mx2(__ffma2_rn(g.cx, g.cx, __ffma2_rn(g.cy, g.cy, __fmul2_rn(g.cz, g.cz))), 1e-37f);
+    const f2 ra2 = mx2(__ffma2_rn(ax, ax, __ffma2_rn(ay, ay, __fmul2_rn(az, az))), 1e-37f);
+    const f2 rb2 = mx2(__ffma2_rn(bx, bx, __ffma2_rn(by, by, __fmul2_rn(bz, bz))), 1e-37f);
+    const f2 ia = make_float2(grsqrt(ra2.x), grsqrt(ra2.y)), ib = make_float2(grsqrt(rb2.x), grsqrt(rb2.y));
+    const f2 la = __fmul2_rn(ra2, ia), lb = __fmul2_rn(rb2, ib);
+    const f2 ea = __ffma2_rn(EX, ax, __ffma2_rn(EY, ay, __fmul2_rn(EZ, az)));
+    const f2 eab = __ffma2_rn(mk2(2.f), ea, mk2(e2));
+    const f2 sab = __fadd2_rn(la, lb);
+    const f2 inv_s = make_float2(grcp(sab.x), grcp(sab.y));
+    const f2 inv_ab = __fmul2_rn(ia, ib);
+    const f2 num0 = __ffma2_rn(mk2(e2), la, __fmul2_rn(make_float2(-ea.x, -ea.y), __fmul2_rn(eab, inv_s)));
+    g.i0 = __fmul2_rn(__fmul2_rn(num0, inv_ab), make_float2(grcp(del.x), grcp(del.y)));
+    const f2 invdiff = __fmul2_rn(__fmul2_rn(eab, inv_ab), inv_s);
+    g.i1 = __fmul2_rn(__ffma2_rn(make_float2(-ea.x, -ea.y), g.i0, invdiff), mk2(inv_e2));
+    return g;
+}
+
 template <int K>
 __global__ void __launch_bounds__(256) grad_p_kernel(const float4 *__restrict__ bseq, int nb, QuerySrc q,
                                                      const float *__restrict__ grad_w, float *__restrict__ grad_p) {
@@ -164,14 +196,16 @@ __global__ void __launch_bounds__(GV_THREADS) grad_v_partial_kernel(const float4
 // Both gradients from one evaluation per (query, edge): the per-edge sums as
 // in grad_v_partial_kernel, and per query the sum of its dw/dp contributions
 // over the block's edges.  A warp takes its 32 edges against the tile's
-// queries 32 at a time: in step s lane l evaluates (its edge, query (l + s) mod
-// 32) and adds the contribution to the accumulator it holds, which is then
-// passed one lane down, so after 32 steps lane l holds query l's sum over the
-// warp's edges (3 shuffles per pair, a fixed order).  The warps are added in
-// order in shared memory, one value per (edge block, query, component) goes to
+// queries 64 at a time, two per lane in packed f32x2 arithmetic: in step s
+// lane l evaluates its edge against queries base + (l + s) mod 32 and
+// base + 32 + (l + s) mod 32, adds the contributions to the accumulators it
+// holds and passes them one lane down, so after 32 steps lane l holds the
+// sums over the warp's edges of queries base + l and base + 32 + l (3
+// shuffles per pair, a fixed order).  The warps are added in order in shared
+// memory, one value per (edge block, query, component) goes to
 // partial_p[(eb * 3 + c) * nq + q], and grad_p_reduce_kernel sums the edge
-// blocks in order.  Lanes without an edge, and queries past the tile's end,
-// contribute zero.
+// blocks in order.  Lanes without an edge contribute nothing; queries past
+// the tile's end sit far from the geometry with weight zero.
 __global__ void __launch_bounds__(GV_THREADS) grad_pv_partial_kernel(const float4 *__restrict__ bseq, int nb,
                                                                      QuerySrc q, const float *__restrict__ grad_w,
                                                                      int64_t chunk_len, float *__restrict__ partial,
@@ -190,7 +224,7 @@ __global__ void __launch_bounds__(GV_THREADS) grad_pv_partial_kernel(const float
     active = active && B.w != 0.f;
     float ex = B.x - A.x, ey = B.y - A.y, ez = B.z - A.z;
     float e2 = fmaxf(ex * ex + ey * ey + ez * ez, 1e-37f), inv_e2 = grcp(e2);
-    float sA[3] = {0.f, 0.f, 0.f}, sB[3] = {0.f, 0.f, 0.f};
+    f2 sA2[3] = {mk2(0.f), mk2(0.f), mk2(0.f)}, sB2[3] = {mk2(0.f), mk2(0.f), mk2(0.f)};
     for (int64_t t0 = q0; t0 < q1; t0 += GV_QTILE) {
         __syncthreads();
         for (int i = threadIdx.x; i < GV_QTILE; i += GV_THREADS) {
@@ -199,33 +233,42 @@ __global__ void __launch_bounds__(GV_THREADS) grad_pv_partial_kernel(const float
                 float3 p = query_point3(q, qi);
                 qs[i] = make_float4(p.x, p.y, p.z, grad_w[qi] * GWN_INV_4PI);
             } else {
-                qs[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+                qs[i] = make_float4(1e6f, 1e6f, 1e6f, 0.f);      // far from the geometry, weight zero
             }
         }
         __syncthreads();
         const int cnt = (int)(q1 - t0 < GV_QTILE ? q1 - t0 : GV_QTILE);
-        for (int base = 0; base < cnt; base += 32) {
-            float ax_ = 0.f, ay_ = 0.f, az_ = 0.f;      // accumulator of query base + ((lane + s) mod 32)
+        // queries base + j and base + 32 + j as one packed pair per step
+        for (int base = 0; base < cnt; base += 64) {
+            f2 acx = mk2(0.f), acy = mk2(0.f), acz = mk2(0.f);
             for (int st = 0; st < 32; st++) {
                 const int j = (lane + st) & 31;
-                if (active && base + j < cnt) {
-                    const float4 p = qs[base + j];
-                    EdgeGrad g = edge_grad(A.x - p.x, A.y - p.y, A.z - p.z, B.x - p.x, B.y - p.y, B.z - p.z, ex, ey,
-                                           ez, e2, inv_e2);
-                    float wa = -(g.i0 - g.i1) * p.w, wb = -g.i1 * p.w, wp = g.i0 * B.w * p.w;
-                    sA[0] = fmaf(g.cx, wa, sA[0]); sA[1] = fmaf(g.cy, wa, sA[1]); sA[2] = fmaf(g.cz, wa, sA[2]);
-                    sB[0] = fmaf(g.cx, wb, sB[0]); sB[1] = fmaf(g.cy, wb, sB[1]); sB[2] = fmaf(g.cz, wb, sB[2]);
-                    ax_ = fmaf(g.cx, wp, ax_); ay_ = fmaf(g.cy, wp, ay_); az_ = fmaf(g.cz, wp, az_);
+                if (active) {
+                    const float4 pa = qs[base + j], pb = qs[base + 32 + j];
+                    const f2 pw = make_float2(pa.w, pb.w);
+                    EdgeGrad2 g = edge_grad2(make_float2(A.x - pa.x, A.x - pb.x), make_float2(A.y - pa.y, A.y - pb.y),
+                                             make_float2(A.z - pa.z, A.z - pb.z), make_float2(B.x - pa.x, B.x - pb.x),
+                                             make_float2(B.y - pa.y, B.y - pb.y), make_float2(B.z - pa.z, B.z - pb.z),
+                                             ex, ey, ez, e2, inv_e2);
+                    const f2 wa = __fmul2_rn(__fadd2_rn(g.i1, make_float2(-g.i0.x, -g.i0.y)), pw);
+                    const f2 wb = __fmul2_rn(make_float2(-g.i1.x, -g.i1.y), pw);
+                    const f2 wp = __fmul2_rn(__fmul2_rn(g.i0, mk2(B.w)), pw);
+                    sA2[0] = __ffma2_rn(g.cx, wa, sA2[0]); sA2[1] = __ffma2_rn(g.cy, wa, sA2[1]);
+                    sA2[2] = __ffma2_rn(g.cz, wa, sA2[2]);
+                    sB2[0] = __ffma2_rn(g.cx, wb, sB2[0]); sB2[1] = __ffma2_rn(g.cy, wb, sB2[1]);
+                    sB2[2] = __ffma2_rn(g.cz, wb, sB2[2]);
+                    acx = __ffma2_rn(g.cx, wp, acx); acy = __ffma2_rn(g.cy, wp, acy); acz = __ffma2_rn(g.cz, wp, acz);
                 }
-                // pass the accumulator one lane down: lane l now holds query (l + st + 1) mod 32
-                ax_ = __shfl_sync(FULL, ax_, (lane + 1) & 31);
-                ay_ = __shfl_sync(FULL, ay_, (lane + 1) & 31);
-                az_ = __shfl_sync(FULL, az_, (lane + 1) & 31);
+                // pass the accumulators one lane down
+                const int src = (lane + 1) & 31;
+                acx = make_float2(__shfl_sync(FULL, acx.x, src), __shfl_sync(FULL, acx.y, src));
+                acy = make_float2(__shfl_sync(FULL, acy.x, src), __shfl_sync(FULL, acy.y, src));
+                acz = make_float2(__shfl_sync(FULL, acz.x, src), __shfl_sync(FULL, acz.y, src));
             }
-            // after 32 steps lane l holds query base + l
-            accp[warp][0][base + lane] = ax_;
-            accp[warp][1][base + lane] = ay_;
-            accp[warp][2][base + lane] = az_;
+            // after 32 steps lane l holds queries base + l and base + 32 + l
+            accp[warp][0][base + lane] = acx.x; accp[warp][0][base + 32 + lane] = acx.y;
+            accp[warp][1][base + lane] = acy.x; accp[warp][1][base + 32 + lane] = acy.y;
+            accp[warp][2][base + lane] = acz.x; accp[warp][2][base + 32 + lane] = acz.y;
         }
         __syncthreads();
         for (int i = threadIdx.x; i < cnt; i += GV_THREADS)
@@ -237,8 +280,10 @@ __global__ void __launch_bounds__(GV_THREADS) grad_pv_partial_kernel(const float
     }
     if (k < nb) {
         float *o = partial + ((int64_t)chunk * nb + k) * 6;
-        o[0] = sA[0]; o[1] = sA[1]; o[2] = sA[2];
-        o[3] = sB[0]; o[4] = sB[1]; o[5] = sB[2];
+        for (int c = 0; c < 3; c++) {
+            o[c] = sA2[c].x + sA2[c].y;
+            o[3 + c] = sB2[c].x + sB2[c].y;
+        }
     }
 }
 
