@@ -49,6 +49,12 @@ WORKLOAD = "icosphere_cap_s6_73724tris_256^3grid"
 #           cut test (2), compensated accumulation (4)                          -> 31
 W_VERTEX = 24
 W_EDGE = 31
+# FP32 lane operations per (query, boundary edge) pair of the fused backward
+# pass (both gradients): a = A - p, b = B - p (6); a x E, |a x E|^2 (10);
+# |a|^2, |b|^2 (8); rsqrt x 2, |a|, |b| (4); E.a, E.(a+b), |a|+|b| and its
+# reciprocal (6); 1/(|a||b|), I0 numerator, I0 (6); 1/|a| - 1/|b|, I1 (4);
+# weights (5); per-edge and per-query accumulation (9)                       -> 58
+W_GRAD_PAIR = 58
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one bterm3d_kernel
 # launch on this workload at full size, from an ncu capture (read 67.31 MB,
 # write 21.43 MB); reported only while csrc/bterm.cu is the source it was taken
@@ -471,8 +477,16 @@ def run_other(args):
                     "boundary_edges": info["n_boundary_edges"], "triangles": int(len(m.F)),
                     "kernels": {"traverse_ms": st["ms_traverse"], "bterm3d_ms": st["ms_boundary"]},
                     "roofline_bterm": _alu_roofline(len(Pt), info, st["ms_boundary"])})
+        bwd = statistics.median(ms) - statistics.median(fms)
+        peaks, kind = _peaks()
+        peak = SM_COUNT * FP32_LANES_PER_SM * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+        ach = len(Pt) * info["n_boundary_edges"] * W_GRAD_PAIR / (bwd * 1e-3) / 1e12
+        out["backward_ms"] = bwd
+        out["roofline_backward"] = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "Tops/s (FP32 lane ops)",
+                                    "frac": ach / peak, "peak_source": kind,
+                                    "note": "step minus forward; W_GRAD_PAIR lane-ops per (query, edge) pair"}
     elif name == "patch_spheroid":
-        # parametric surface: 384 bicubic Bezier patches (8 x 8 per cube face,
+        # parametric surface: 320 bicubic Bezier patches (8 x 8 per cube face,
         # one face left open: one boundary loop of 32 curves x 64 segments),
         # 256^3 grid on [-1.3, 1.3]^3, seeded random d
         pc = gen.patch_spheroid(n=8, amp=0.08, open_faces=(4,), grid_n=args.grid, seed=0)
