@@ -178,6 +178,18 @@ gwn_status chain_unit_edges(std::vector<std::pair<int32_t, int32_t>> &bedges, in
     out.off.assign(1, 0);
     out.vid.clear();
     if (bedges.empty()) return GWN_OK;
+    // the walk runs over the boundary's own vertices, renumbered in increasing
+    // order (a monotone map, so "smallest vertex first" is unchanged)
+    std::vector<int32_t> ids;
+    ids.reserve(2 * bedges.size());
+    for (auto &e : bedges) { ids.push_back(e.first); ids.push_back(e.second); }
+    std::sort(ids.begin(), ids.end());
+    ids.erase(std::unique(ids.begin(), ids.end()), ids.end());
+    for (auto &e : bedges) {
+        e.first = (int32_t)(std::lower_bound(ids.begin(), ids.end(), e.first) - ids.begin());
+        e.second = (int32_t)(std::lower_bound(ids.begin(), ids.end(), e.second) - ids.begin());
+    }
+    nv = (int64_t)ids.size();
     std::vector<int64_t> ooff(nv + 1, 0);
     for (auto &e : bedges) ooff[e.first + 1]++;
     for (int64_t v = 0; v < nv; v++) ooff[v + 1] += ooff[v];
@@ -206,6 +218,7 @@ gwn_status chain_unit_edges(std::vector<std::pair<int32_t, int32_t>> &bedges, in
             out.off.push_back((int64_t)out.vid.size());
         }
     }
+    for (auto &v : out.vid) v = ids[v];
     return GWN_OK;
 }
 
@@ -457,27 +470,6 @@ GWN_API gwn_status gwn_mesh_create(gwn_ctx *ctx, const float *V, int64_t nv, con
     }
     if (nv > 0x7fffffff || nf > 0x7fffffff / 3) { set_error("gwn_mesh_create: mesh too large"); return GWN_E_INVALID; }
     CK(cudaSetDevice(ctx->device), "cudaSetDevice");
-    // host copies for validation and boundary extraction
-    std::vector<float> hV;
-    std::vector<int32_t> hF;
-    try {
-        hV.resize(3 * nv);
-        hF.resize(3 * nf);
-    } catch (const std::bad_alloc &) {
-        set_error("gwn_mesh_create: out of host memory");
-        return GWN_E_OOM;
-    }
-    if (mem_kind == GWN_MEM_HOST) {
-        if (nv) memcpy(hV.data(), V, sizeof(float) * 3 * nv);
-        if (nf) memcpy(hF.data(), F, sizeof(int32_t) * 3 * nf);
-    } else {
-        if (nv) CK(cudaMemcpy(hV.data(), V, sizeof(float) * 3 * nv, cudaMemcpyDeviceToHost), "copy V");
-        if (nf) CK(cudaMemcpy(hF.data(), F, sizeof(int32_t) * 3 * nf, cudaMemcpyDeviceToHost), "copy F");
-    }
-    for (int64_t i = 0; i < 3 * nv; i++)
-        if (!isfinite(hV[i])) { set_error("gwn_mesh_create: non-finite vertex coordinate"); return GWN_E_INVALID; }
-    for (int64_t i = 0; i < 3 * nf; i++)
-        if (hF[i] < 0 || hF[i] >= nv) { set_error("gwn_mesh_create: face index out of range"); return GWN_E_INVALID; }
     std::unique_ptr<gwn_geom> g(new (std::nothrow) gwn_geom());
     if (!g) { set_error("gwn_mesh_create: out of host memory"); return GWN_E_OOM; }
     g->ctx = ctx;
@@ -485,47 +477,63 @@ GWN_API gwn_status gwn_mesh_create(gwn_ctx *ctx, const float *V, int64_t nv, con
     g->dtype = GWN_F32;
     g->nv = nv;
     g->nf = nf;
-    BoundaryLoops bl;
-    gwn_status s;
-    try {
-        s = extract_boundary(hF.data(), nf, nv, bl);
-    } catch (const std::bad_alloc &) {
-        set_error("gwn_mesh_create: out of host memory");
-        return GWN_E_OOM;
-    }
-    if (s != GWN_OK) return s;
-    g->loop_off = bl.off;
-    g->loop_vid = bl.vid;
-    // loop sequence records
-    int64_t L = (int64_t)bl.off.size() - 1, E = (int64_t)bl.vid.size();
-    std::vector<float4> rec;
-    std::vector<int32_t> rvid;
-    rec.reserve(E + L);
-    rvid.reserve(E + L);
-    for (int64_t j = 0; j < L; j++) {
-        int64_t lo = bl.off[j], hi = bl.off[j + 1];
-        for (int64_t i = lo; i <= hi; i++) {
-            int32_t v = bl.vid[i < hi ? i : lo];
-            rec.push_back(make_float4(hV[3 * (int64_t)v], hV[3 * (int64_t)v + 1], hV[3 * (int64_t)v + 2],
-                                      i == lo ? 0.f : 1.f));
-            rvid.push_back(v);
-        }
-    }
-    g->n_bseq = (int64_t)rec.size();
+    cudaStream_t st = ctx->stream;
+    // upload, then checks and boundary edges on the device (the intake
+    // synchronises, so the caller's buffers are free again on return)
+    const cudaMemcpyKind kind = mem_kind == GWN_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
     cudaError_t e = cudaSuccess;
     if (nv) e = cudaMalloc(&g->dV, sizeof(float) * 3 * nv);
     if (e == cudaSuccess && nf) e = cudaMalloc(&g->dF, sizeof(int32_t) * 3 * nf);
-    if (e == cudaSuccess && g->n_bseq) e = cudaMalloc(&g->bseq, sizeof(float4) * g->n_bseq);
-    if (e == cudaSuccess && g->n_bseq) e = cudaMalloc(&g->bseq_vid, sizeof(int32_t) * g->n_bseq);
-    if (e == cudaSuccess && nv) e = cudaMemcpy(g->dV, hV.data(), sizeof(float) * 3 * nv, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess && nf) e = cudaMemcpy(g->dF, hF.data(), sizeof(int32_t) * 3 * nf, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess && g->n_bseq)
-        e = cudaMemcpy(g->bseq, rec.data(), sizeof(float4) * g->n_bseq, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess && g->n_bseq)
-        e = cudaMemcpy(g->bseq_vid, rvid.data(), sizeof(int32_t) * g->n_bseq, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && nv) e = cudaMemcpyAsync(g->dV, V, sizeof(float) * 3 * nv, kind, st);
+    if (e == cudaSuccess && nf) e = cudaMemcpyAsync(g->dF, F, sizeof(int32_t) * 3 * nf, kind, st);
     if (e != cudaSuccess) {
         free_geom_device(g.get());
         return cuda_fail(e, "gwn_mesh_create");
+    }
+    BoundaryLoops bl;
+    std::vector<int32_t> code;
+    gwn_status s;
+    try {
+        std::vector<std::pair<int32_t, int32_t>> bedges;
+        s = mesh_intake_device(ctx, g->dV, nv, g->dF, nf, bedges);
+        if (s == GWN_OK) s = chain_unit_edges(bedges, nv, bl);
+        if (s == GWN_OK) {
+            // loop sequence records: each loop's vertices, then its first again
+            int64_t L = (int64_t)bl.off.size() - 1;
+            code.reserve(bl.vid.size() + L);
+            for (int64_t j = 0; j < L; j++)
+                for (int64_t i = bl.off[j]; i <= bl.off[j + 1]; i++) {
+                    int32_t v = bl.vid[i < bl.off[j + 1] ? i : bl.off[j]];
+                    code.push_back(i == bl.off[j] ? ~v : v);
+                }
+        }
+    } catch (const std::bad_alloc &) {
+        set_error("gwn_mesh_create: out of host memory");
+        s = GWN_E_OOM;
+    }
+    if (s != GWN_OK) {
+        free_geom_device(g.get());
+        return s;
+    }
+    g->loop_off = bl.off;
+    g->loop_vid = bl.vid;
+    g->n_bseq = (int64_t)code.size();
+    if (g->n_bseq) {
+        int32_t *dcode = (int32_t *)arena_get(ctx, 6, sizeof(int32_t) * g->n_bseq, &e);
+        if (!dcode) {
+            free_geom_device(g.get());
+            return cuda_fail(e, "gwn_mesh_create");
+        }
+        e = cudaMalloc(&g->bseq, sizeof(float4) * g->n_bseq);
+        if (e == cudaSuccess) e = cudaMalloc(&g->bseq_vid, sizeof(int32_t) * g->n_bseq);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(dcode, code.data(), sizeof(int32_t) * g->n_bseq, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = launch_bseq(g->dV, dcode, g->n_bseq, g->bseq, g->bseq_vid, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);   // the host copy of code goes out of scope
+        if (e != cudaSuccess) {
+            free_geom_device(g.get());
+            return cuda_fail(e, "gwn_mesh_create");
+        }
     }
     ctx_ref(ctx);
     *out = g.release();

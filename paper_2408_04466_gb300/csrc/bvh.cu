@@ -122,11 +122,15 @@ __global__ void hist_kernel(const unsigned long long *__restrict__ keys, int64_t
     for (int i = threadIdx.x; i < BINS; i += blockDim.x) hist[(int64_t)i * nblocks + blockIdx.x] = h[i];
 }
 
-// exclusive scan of `n` counts by one block (chunked, Hillis-Steele over the
-// per-thread chunk sums)
-__global__ void scan_kernel(unsigned *data, int64_t n) {
+// exclusive scan of the BINS x nblocks digit counts by one block (chunked,
+// Hillis-Steele over the per-thread chunk sums); the same block then flags
+// the pass as skippable when one digit value holds every key
+__global__ void scan_skip_kernel(unsigned *data, int nblocks, int64_t total, int *skip) {
     __shared__ unsigned long long partial[1024];
+    __shared__ int s_skip;
+    const int64_t n = (int64_t)BINS * nblocks;
     int tid = threadIdx.x;
+    if (tid == 0) s_skip = 0;
     int64_t chunk = (n + blockDim.x - 1) / blockDim.x;
     int64_t lo = tid * chunk, hi = lo + chunk < n ? lo + chunk : n;
     unsigned long long s = 0;
@@ -145,15 +149,14 @@ __global__ void scan_kernel(unsigned *data, int64_t n) {
         data[i] = (unsigned)run;
         run += v;
     }
-}
-
-// flags the pass as skippable when one digit value holds every key
-__global__ void bin_total_kernel(const unsigned *scanned, int nblocks, int64_t total, int *skip) {
-    int b = threadIdx.x;
-    if (b >= BINS) return;
-    unsigned long long start = scanned[(int64_t)b * nblocks];
-    unsigned long long end = b + 1 < BINS ? scanned[(int64_t)(b + 1) * nblocks] : (unsigned long long)total;
-    if (end - start == (unsigned long long)total) *skip = 1;
+    __syncthreads();                     // the block's global writes are visible to the block
+    for (int b = tid; b < BINS; b += blockDim.x) {
+        unsigned long long start = data[(int64_t)b * nblocks];
+        unsigned long long end = b + 1 < BINS ? data[(int64_t)(b + 1) * nblocks] : (unsigned long long)total;
+        if (end - start == (unsigned long long)total) s_skip = 1;
+    }
+    __syncthreads();
+    if (tid == 0) *skip = s_skip;
 }
 
 __global__ void scatter_kernel(const unsigned long long *__restrict__ kin, const int32_t *__restrict__ vin,
@@ -338,128 +341,262 @@ __global__ void radius_kernel(const float *__restrict__ V, int64_t nv, unsigned 
     if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(r));
 }
 
+// ---- mesh intake: checks and boundary unit edges ---------------------------
+// One thread per entry of max(3 nv, 3 nf): a vertex coordinate is checked for
+// being finite (flag bit 0), a face corner for indexing a vertex (bit 1), and
+// face corner i = 3t + k emits the directed edge (F[i], F[3t + (k+1) mod 3])
+// as the key (min << 32 | max) with value +1 if it runs from min to max, -1
+// if it runs from max to min, 0 if it is degenerate.
+__global__ void mesh_intake_kernel(const float *__restrict__ V, int64_t nv3, const int32_t *__restrict__ F,
+                                   int64_t nf3, int64_t nv, unsigned long long *__restrict__ keys,
+                                   int32_t *__restrict__ vals, unsigned *flags) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nv3 && !isfinite(V[i])) atomicOr(flags, 1u);
+    if (i < nf3) {
+        int64_t t = i / 3;
+        int k = (int)(i - 3 * t);
+        int32_t a = F[i], b = F[3 * t + (k == 2 ? 0 : k + 1)];
+        if (a < 0 || (int64_t)a >= nv) atomicOr(flags, 2u);
+        unsigned ua = (unsigned)a, ub = (unsigned)b;
+        unsigned lo = ua < ub ? ua : ub, hi = ua < ub ? ub : ua;
+        keys[i] = ((unsigned long long)lo << 32) | hi;
+        vals[i] = a == b ? 0 : (ua < ub ? 1 : -1);
+    }
+}
+
+// After the sort equal keys are adjacent: the first entry of each run adds
+// the run's values, the net multiplicity m of that undirected edge, and
+// emits |m| unit edges in the direction of m's sign.  The total is at most
+// the number of entries; the order of the output is not fixed (atomics), the
+// host sorts it.
+__global__ void edge_net_kernel(const unsigned long long *__restrict__ keys, const int32_t *__restrict__ vals,
+                                int64_t n, int2 *__restrict__ out, unsigned long long *count) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    unsigned long long k = keys[i];
+    if (i > 0 && keys[i - 1] == k) return;
+    long long m = 0;
+    for (int64_t j = i; j < n && keys[j] == k; j++) m += vals[j];
+    if (m == 0) return;
+    int32_t lo = (int32_t)(k >> 32), hi = (int32_t)(k & 0xffffffffull);
+    unsigned long long c = (unsigned long long)(m > 0 ? m : -m);
+    unsigned long long pos = atomicAdd(count, c);
+    for (unsigned long long r = 0; r < c && pos + r < (unsigned long long)n; r++)
+        out[pos + r] = m > 0 ? make_int2(lo, hi) : make_int2(hi, lo);
+}
+
+// Boundary records from the chained loops: code[i] is the vertex id, or its
+// complement at the first record of a loop (w = 0 there, 1 elsewhere).
+__global__ void bseq_kernel(const float *__restrict__ V, const int32_t *__restrict__ code, int64_t n,
+                            float4 *__restrict__ bseq, int32_t *__restrict__ bseq_vid) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int32_t c = code[i];
+    int32_t v = c < 0 ? ~c : c;
+    bseq[i] = make_float4(V[3 * (int64_t)v], V[3 * (int64_t)v + 1], V[3 * (int64_t)v + 2], c < 0 ? 0.f : 1.f);
+    bseq_vid[i] = v;
+}
+
+// zeroes the refit arrival counters and seeds the bound reductions
+__global__ void build_init_kernel(unsigned *bounds, unsigned *rad, unsigned *flags, int64_t nflags) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < 8) bounds[i] = i < 3 ? 0xffffffffu : 0u;
+    if (i == 0) *rad = 0u;
+    if (i < nflags) flags[i] = 0u;
+}
+
 inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+// Carves one scratch block into 256-byte aligned arrays; a pass with a null
+// base only adds up the size.
+struct Carve {
+    char *base = nullptr;
+    size_t off = 0;
+    template <typename T>
+    T *take(int64_t count) {
+        off = (off + 255) & ~(size_t)255;
+        T *r = base ? (T *)(base + off) : nullptr;
+        off += sizeof(T) * (size_t)(count > 0 ? count : 1);
+        return r;
+    }
+};
+
+// Stable LSD radix sort of n (key, value) pairs by the key bytes set in
+// byte_mask (bit b: byte b), one 8-bit digit per pass; three launches per
+// pass (digit histogram per tile, scan + skip test, scatter).  The pairs move
+// between (k0, v0) and (k1, v1); on return (k0, v0) names the sorted copy.
+cudaError_t radix_sort_pairs(unsigned long long *&k0, int32_t *&v0, unsigned long long *&k1, int32_t *&v1,
+                             int64_t n, unsigned *hist, int *skip, unsigned byte_mask, cudaStream_t st) {
+    if (n <= 1) return cudaSuccess;
+    const int nblocks = (int)((n + SORT_TILE - 1) / SORT_TILE);
+    for (int b = 0; b < 8; b++) {
+        if (!((byte_mask >> b) & 1u)) continue;
+        const int shift = 8 * b;
+        hist_kernel<<<nblocks, SORT_THREADS, 0, st>>>(k0, n, shift, hist, nblocks);
+        scan_skip_kernel<<<1, 1024, 0, st>>>(hist, nblocks, n, skip);
+        scatter_kernel<<<nblocks, SORT_THREADS, 0, st>>>(k0, v0, k1, v1, n, shift, hist, nblocks, skip);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        unsigned long long *tk = k0; k0 = k1; k1 = tk;
+        int32_t *tv = v0; v0 = v1; v1 = tv;
+    }
+    return cudaSuccess;
+}
+
+inline size_t sort_hist_count(int64_t n) { return (size_t)BINS * (size_t)((n + SORT_TILE - 1) / SORT_TILE); }
 
 }  // namespace
 
+gwn_status mesh_intake_device(gwn_ctx *ctx, const float *dV, int64_t nv, const int32_t *dF, int64_t nf,
+                              std::vector<std::pair<int32_t, int32_t>> &bedges) {
+    bedges.clear();
+    cudaStream_t st = ctx->stream;
+    const int64_t nv3 = 3 * nv, nh = 3 * nf, nthr = nv3 > nh ? nv3 : nh;
+    if (nthr == 0) return GWN_OK;
+    Carve c;
+    for (int pass = 0; pass < 2; pass++) {
+        if (pass == 1) {
+            cudaError_t e;
+            c.base = (char *)arena_get(ctx, 6, c.off, &e);
+            if (!c.base) return cuda_fail(e, "mesh intake scratch");
+            c.off = 0;
+        }
+        unsigned long long *hdr = c.take<unsigned long long>(2);   // edge count, flags
+        unsigned long long *k0 = c.take<unsigned long long>(nh), *k1 = c.take<unsigned long long>(nh);
+        int32_t *v0 = c.take<int32_t>(nh), *v1 = c.take<int32_t>(nh);
+        unsigned *hist = c.take<unsigned>((int64_t)sort_hist_count(nh));
+        int *skip = c.take<int>(1);
+        int2 *out = c.take<int2>(nh);
+        if (pass == 0) continue;
+        cudaError_t e = cudaMemsetAsync(hdr, 0, 2 * sizeof(unsigned long long), st);
+        if (e != cudaSuccess) return cuda_fail(e, "mesh intake");
+        mesh_intake_kernel<<<blocks_for(nthr, 256), 256, 0, st>>>(dV, nv3, dF, nh, nv, k0, v0, (unsigned *)(hdr + 1));
+        // only the bytes of min and max that can be nonzero take a pass
+        int bits = 0;
+        while (bits < 32 && ((int64_t)1 << bits) < nv) bits++;
+        unsigned nb = (unsigned)((bits + 7) / 8), m = (1u << nb) - 1u;
+        e = radix_sort_pairs(k0, v0, k1, v1, nh, hist, skip, m | (m << 4), st);
+        if (e != cudaSuccess) return cuda_fail(e, "mesh intake sort");
+        if (nh > 0) edge_net_kernel<<<blocks_for(nh, 256), 256, 0, st>>>(k0, v0, nh, out, hdr);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(e, "mesh intake");
+        unsigned long long h[2];
+        e = cudaMemcpyAsync(h, hdr, sizeof(h), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_fail(e, "mesh intake");
+        if (h[1] & 1u) { set_error("gwn_mesh_create: non-finite vertex coordinate"); return GWN_E_INVALID; }
+        if (h[1] & 2u) { set_error("gwn_mesh_create: face index out of range"); return GWN_E_INVALID; }
+        int64_t ne = (int64_t)(h[0] < (unsigned long long)nh ? h[0] : (unsigned long long)nh);
+        if (ne > 0) {
+            std::vector<int2> he(ne);
+            e = cudaMemcpyAsync(he.data(), out, sizeof(int2) * ne, cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) return cuda_fail(e, "mesh intake");
+            bedges.resize(ne);
+            for (int64_t j = 0; j < ne; j++) bedges[j] = std::make_pair(he[j].x, he[j].y);
+        }
+    }
+    return GWN_OK;
+}
+
+cudaError_t launch_bseq(const float *dV, const int32_t *code, int64_t n, float4 *bseq, int32_t *bseq_vid,
+                        cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    bseq_kernel<<<blocks_for(n, 256), 256, 0, st>>>(dV, code, n, bseq, bseq_vid);
+    return cudaGetLastError();
+}
+
 void bvh_free(MeshBvh &b) {
-    if (b.nodes) cudaFree(b.nodes);
-    if (b.tris) cudaFree(b.tris);
-    if (b.tri_id) cudaFree(b.tri_id);
-    if (b.tbox) cudaFree(b.tbox);
-    if (b.bframe) cudaFree(b.bframe);
+    if (b.block) cudaFree(b.block);
+    b.block = nullptr;
     b.tbox = nullptr;
     b.bframe = nullptr;
     b.nodes = nullptr;
     b.tris = nullptr;
-    b.tri_id = nullptr;
     b.valid = false;
 }
 
-#define GWN_TRY(x)                           \
-    do {                                     \
-        cudaError_t e_ = (x);                \
-        if (e_ != cudaSuccess) { err = e_; goto done; } \
-    } while (0)
-
 cudaError_t bvh_build(gwn_geom *g, const Frame &fr, cudaStream_t st) {
-    cudaError_t err = cudaSuccess;
     MeshBvh &b = g->bvh;
     bvh_free(b);
     const int64_t n = g->nf;
     b.n = n;
     b.frame = fr;
     for (int k = 0; k < 3; k++) b.dkey[k] = fr.d[k];
-    // temporaries
-    float4 *tbox_xy = nullptr, *cen = nullptr, *leaf_xy = nullptr, *int_xy = nullptr;
-    float *tbox_z = nullptr, *leaf_z = nullptr, *int_z = nullptr;
-    unsigned *bounds = nullptr, *hist = nullptr, *flags = nullptr, *rad = nullptr;
-    unsigned long long *k0 = nullptr, *k1 = nullptr;
-    int32_t *v0 = nullptr, *v1 = nullptr, *parent_int = nullptr, *parent_leaf = nullptr;
-    int2 *child = nullptr;
-    int *skip = nullptr;
-    int nblocks = (int)((n + SORT_TILE - 1) / SORT_TILE);
+    // the BVH's own arrays in one allocation
+    Carve keep;
+    for (int pass = 0; pass < 2; pass++) {
+        if (pass == 1) {
+            if (keep.off == 0) break;
+            cudaError_t e = cudaMalloc(&b.block, keep.off);
+            if (e != cudaSuccess) { b.block = nullptr; return e; }
+            keep.base = (char *)b.block;
+            keep.off = 0;
+        }
+        float4 *bf = g->n_bseq > 0 ? keep.take<float4>(2 * g->n_bseq) : nullptr;
+        float4 *tr = n > 0 ? keep.take<float4>(3 * n) : nullptr;
+        float4 *tb = n > 0 ? keep.take<float4>(2 * n) : nullptr;
+        BvhNode *nd = n > 1 ? keep.take<BvhNode>(n - 1) : nullptr;
+        if (pass == 1) { b.bframe = bf; b.tris = tr; b.tbox = tb; b.nodes = nd; }
+    }
+    cudaError_t err = cudaSuccess;
     if (g->n_bseq > 0) {                 // boundary records in this frame
-        GWN_TRY(cudaMalloc(&b.bframe, sizeof(float4) * 2 * g->n_bseq));
-        GWN_TRY(launch_bframe(g->bseq, g->n_bseq, fr, b.bframe, st));
+        err = launch_bframe(g->bseq, g->n_bseq, fr, b.bframe, st);
+        if (err != cudaSuccess) { bvh_free(b); return err; }
     }
     if (n == 0) {
         b.valid = true;
         return cudaSuccess;
     }
-    GWN_TRY(cudaMalloc(&b.tris, sizeof(float4) * 3 * n));
-    GWN_TRY(cudaMalloc(&b.tri_id, sizeof(int32_t) * n));
-    GWN_TRY(cudaMalloc(&b.tbox, sizeof(float4) * 2 * n));
-    GWN_TRY(cudaMalloc(&tbox_xy, sizeof(float4) * n));
-    GWN_TRY(cudaMalloc(&tbox_z, sizeof(float) * n));
-    GWN_TRY(cudaMalloc(&cen, sizeof(float4) * n));
-    GWN_TRY(cudaMalloc(&bounds, sizeof(unsigned) * 8));
-    GWN_TRY(cudaMalloc(&rad, sizeof(unsigned)));
-    GWN_TRY(cudaMalloc(&k0, sizeof(unsigned long long) * n));
-    GWN_TRY(cudaMalloc(&k1, sizeof(unsigned long long) * n));
-    GWN_TRY(cudaMalloc(&v0, sizeof(int32_t) * n));
-    GWN_TRY(cudaMalloc(&v1, sizeof(int32_t) * n));
-    GWN_TRY(cudaMalloc(&hist, sizeof(unsigned) * (size_t)BINS * nblocks));
-    GWN_TRY(cudaMalloc(&skip, sizeof(int)));
-    {
-        unsigned init[8] = {0xffffffffu, 0xffffffffu, 0xffffffffu, 0u, 0u, 0u, 0u, 0u};
-        GWN_TRY(cudaMemcpyAsync(bounds, init, sizeof(init), cudaMemcpyHostToDevice, st));
-        GWN_TRY(cudaMemsetAsync(rad, 0, sizeof(unsigned), st));
+    // temporaries from the context's build scratch
+    const int64_t ni = n > 1 ? n - 1 : 1;
+    Carve c;
+    for (int pass = 0; pass < 2; pass++) {
+        if (pass == 1) {
+            c.base = (char *)arena_get(g->ctx, 6, c.off, &err);
+            if (!c.base) { bvh_free(b); return err; }
+            c.off = 0;
+        }
+        float4 *tbox_xy = c.take<float4>(n), *cen = c.take<float4>(n);
+        float *tbox_z = c.take<float>(n);
+        unsigned *bounds = c.take<unsigned>(8), *rad = c.take<unsigned>(1), *hist = c.take<unsigned>(sort_hist_count(n));
+        unsigned long long *k0 = c.take<unsigned long long>(n), *k1 = c.take<unsigned long long>(n);
+        int32_t *v0 = c.take<int32_t>(n), *v1 = c.take<int32_t>(n);
+        int *skip = c.take<int>(1);
+        int2 *child = c.take<int2>(ni);
+        int32_t *parent_int = c.take<int32_t>(ni), *parent_leaf = c.take<int32_t>(n);
+        float4 *leaf_xy = c.take<float4>(n), *int_xy = c.take<float4>(ni);
+        float *leaf_z = c.take<float>(n), *int_z = c.take<float>(ni);
+        unsigned *flags = c.take<unsigned>(ni);
+        if (pass == 0) continue;
+        build_init_kernel<<<blocks_for(ni > 8 ? ni : 8, 256), 256, 0, st>>>(bounds, rad, flags, n > 1 ? n - 1 : 0);
         radius_kernel<<<blocks_for(g->nv, 256), 256, 0, st>>>(g->dV, g->nv, rad);
         tri_prep_kernel<<<blocks_for(n, 256), 256, 0, st>>>(g->dV, g->dF, n, fr, tbox_xy, tbox_z, cen, bounds);
         morton_kernel<<<blocks_for(n, 256), 256, 0, st>>>(cen, n, bounds, k0, v0);
-        GWN_TRY(cudaGetLastError());
-        for (int pass = 0; pass < 8; pass++) {
-            int shift = pass * 8;
-            hist_kernel<<<nblocks, SORT_THREADS, 0, st>>>(k0, n, shift, hist, nblocks);
-            scan_kernel<<<1, 1024, 0, st>>>(hist, (int64_t)BINS * nblocks);
-            GWN_TRY(cudaMemsetAsync(skip, 0, sizeof(int), st));
-            bin_total_kernel<<<1, BINS, 0, st>>>(hist, nblocks, n, skip);
-            scatter_kernel<<<nblocks, SORT_THREADS, 0, st>>>(k0, v0, k1, v1, n, shift, hist, nblocks, skip);
-            GWN_TRY(cudaGetLastError());
-            unsigned long long *tk = k0; k0 = k1; k1 = tk;
-            int32_t *tv = v0; v0 = v1; v1 = tv;
+        err = cudaGetLastError();
+        if (err == cudaSuccess) err = radix_sort_pairs(k0, v0, k1, v1, n, hist, skip, 0xffu, st);
+        if (err == cudaSuccess) {
+            tris_kernel<<<blocks_for(n, 256), 256, 0, st>>>(g->dV, g->dF, v0, n, b.tris, tbox_xy, tbox_z, b.tbox);
+            if (n > 1) {
+                karras_kernel<<<blocks_for(n - 1, 256), 256, 0, st>>>(k0, n, child, parent_int, parent_leaf);
+                refit_kernel<<<blocks_for(n, 256), 256, 0, st>>>(v0, n, tbox_xy, tbox_z, child, parent_int,
+                                                                parent_leaf, leaf_xy, leaf_z, int_xy, int_z, flags);
+                pack_kernel<<<blocks_for(n - 1, 256), 256, 0, st>>>(child, n, leaf_xy, leaf_z, int_xy, int_z,
+                                                                   b.nodes);
+            }
+            err = cudaGetLastError();
         }
-        GWN_TRY(cudaMemcpyAsync(b.tri_id, v0, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, st));
-        tris_kernel<<<blocks_for(n, 256), 256, 0, st>>>(g->dV, g->dF, v0, n, b.tris, tbox_xy, tbox_z, b.tbox);
-        GWN_TRY(cudaGetLastError());
         unsigned rbits = 0;
-        GWN_TRY(cudaMemcpyAsync(&rbits, rad, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
-        GWN_TRY(cudaStreamSynchronize(st));
+        if (err == cudaSuccess) err = cudaMemcpyAsync(&rbits, rad, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
+        if (err == cudaSuccess) err = cudaStreamSynchronize(st);
+        if (err != cudaSuccess) { bvh_free(b); return err; }
         float rr;
         memcpy(&rr, &rbits, sizeof(float));
         b.scene_radius = rr;
-        if (n == 1) {
-            b.root = ~0;
-            b.valid = true;
-            goto done;
-        }
-        GWN_TRY(cudaMalloc(&b.nodes, sizeof(BvhNode) * (n - 1)));
-        GWN_TRY(cudaMalloc(&child, sizeof(int2) * (n - 1)));
-        GWN_TRY(cudaMalloc(&parent_int, sizeof(int32_t) * (n - 1)));
-        GWN_TRY(cudaMalloc(&parent_leaf, sizeof(int32_t) * n));
-        GWN_TRY(cudaMalloc(&leaf_xy, sizeof(float4) * n));
-        GWN_TRY(cudaMalloc(&leaf_z, sizeof(float) * n));
-        GWN_TRY(cudaMalloc(&int_xy, sizeof(float4) * (n - 1)));
-        GWN_TRY(cudaMalloc(&int_z, sizeof(float) * (n - 1)));
-        GWN_TRY(cudaMalloc(&flags, sizeof(unsigned) * (n - 1)));
-        GWN_TRY(cudaMemsetAsync(flags, 0, sizeof(unsigned) * (n - 1), st));
-        karras_kernel<<<blocks_for(n - 1, 256), 256, 0, st>>>(k0, n, child, parent_int, parent_leaf);
-        refit_kernel<<<blocks_for(n, 256), 256, 0, st>>>(v0, n, tbox_xy, tbox_z, child, parent_int, parent_leaf,
-                                                        leaf_xy, leaf_z, int_xy, int_z, flags);
-        pack_kernel<<<blocks_for(n - 1, 256), 256, 0, st>>>(child, n, leaf_xy, leaf_z, int_xy, int_z, b.nodes);
-        GWN_TRY(cudaGetLastError());
-        GWN_TRY(cudaStreamSynchronize(st));
-        b.root = 0;
-        b.valid = true;
     }
-done:
-    cudaFree(tbox_xy); cudaFree(tbox_z); cudaFree(cen); cudaFree(bounds); cudaFree(rad);
-    cudaFree(k0); cudaFree(k1); cudaFree(v0); cudaFree(v1); cudaFree(hist); cudaFree(skip);
-    cudaFree(child); cudaFree(parent_int); cudaFree(parent_leaf);
-    cudaFree(leaf_xy); cudaFree(leaf_z); cudaFree(int_xy); cudaFree(int_z); cudaFree(flags);
-    if (err != cudaSuccess) bvh_free(b);
-    return err;
+    b.root = n == 1 ? ~0 : 0;
+    b.valid = true;
+    return cudaSuccess;
 }
 
 }  // namespace gwn

@@ -73,8 +73,8 @@ struct MeshBvh {
     float dkey[3] = {0, 0, 0};
     int64_t n = 0;             // triangles
     BvhNode *nodes = nullptr;  // n - 1
+    void *block = nullptr;     // one allocation holding bframe, tris, tbox and nodes
     float4 *tris = nullptr;    // 3 float4 per sorted triangle (xyz of v0, v1, v2)
-    int32_t *tri_id = nullptr; // original triangle index per sorted position
     float4 *tbox = nullptr;    // 2 float4 per sorted triangle: (x0, x1, y0, y1), (zmax, 0, 0, 0)
     int root = 0;              // ref of the root
     float scene_radius = 0.f;  // max |v|_2 over the mesh vertices
@@ -187,8 +187,8 @@ struct gwn_ctx {
     int2 *d_tpairs = nullptr;                 // traversal: unsettled (query, triangle) pairs [GWN_TPAIR_CAP]
     unsigned long long *d_work_counter = nullptr;   // 2D work-item counter
     int32_t *d_tpair_count = nullptr;
-    gwn::Arena scratch[6];                    // 0 chi, 1 staged points, 2 2D batch, 3 host-eval w, 4 deferred list,
-                                              // 5 per-line crossing lists
+    gwn::Arena scratch[7];                    // 0 chi, 1 staged points, 2 2D batch, 3 host-eval w, 4 deferred list,
+                                              // 5 per-line crossing lists, 6 mesh intake and LBVH build
     std::vector<gwn::AxisCache> axis_cache;   // most recent grids, at most 64
     cudaEvent_t ev[8];
     bool events = false;
@@ -238,6 +238,17 @@ Frame64 make_frame64(const float d[3]);
 // ---- launchers (return the first CUDA error) -------------------------------
 cudaError_t bvh_build(gwn_geom *g, const Frame &fr, cudaStream_t st);
 void bvh_free(MeshBvh &b);
+// Mesh intake on the device (V: nv x 3 float32, F: nf x 3 int32, both on the
+// device): fails with GWN_E_INVALID on a non-finite coordinate or a face index
+// outside [0, nv); otherwise returns the boundary unit edges (each undirected
+// edge with net multiplicity m over the faces' directed edges, as |m| copies
+// in the direction of m's sign), in no fixed order.  Synchronises the stream.
+gwn_status mesh_intake_device(gwn_ctx *ctx, const float *dV, int64_t nv, const int32_t *dF, int64_t nf,
+                              std::vector<std::pair<int32_t, int32_t>> &bedges);
+// bseq[i] = (V[v], w), bseq_vid[i] = v for code[i] = v (w = 1) or ~v (w = 0,
+// the first record of a loop).
+cudaError_t launch_bseq(const float *dV, const int32_t *code, int64_t n, float4 *bseq, int32_t *bseq_vid,
+                        cudaStream_t st);
 
 // Crossing counts chi[q.n].  defer / defer_count: the same deferred-list
 // scratch as launch_bterm3d (used and emptied before it returns in stream

@@ -216,6 +216,72 @@ def test_invalid_inputs_are_errors(gwn, ctx):
     ctx.check()
 
 
+def _unit_edges_of_loops(off, vid):
+    out = []
+    for j in range(len(off) - 1):
+        lo, hi = int(off[j]), int(off[j + 1])
+        for i in range(lo, hi):
+            out.append((int(vid[i]), int(vid[i + 1] if i + 1 < hi else vid[lo])))
+    return sorted(out)
+
+
+def _oracle_unit_edge_list(F):
+    src, dst, m = oracle.boundary_edges(F)
+    out = []
+    for s, t, k in zip(src, dst, m):
+        out += [(int(s), int(t))] * int(k)
+    return sorted(out)
+
+
+@pytest.mark.parametrize("name", ["cap", "torus", "heightfield", "closed", "soup", "wide_ids", "one_vertex", "empty"])
+def test_device_boundary_extraction(gwn, ctx, name):
+    """The mesh's boundary loops come from the device intake (half-edge keys,
+    radix sort over the key bytes that vertex ids of this size occupy, net
+    multiplicities): the unit edges equal the oracle's, and the loops equal the
+    host extraction's exactly."""
+    rng = np.random.default_rng(11)
+    if name == "cap":
+        m = gen.icosphere_cap(subdiv=4)
+        V, F = m.V, m.F
+    elif name == "torus":
+        m = gen.slit_torus(n_u=48, n_v=40, n_queries=16)
+        V, F = m.V, m.F
+    elif name == "heightfield":
+        m = gen.holey_heightfield(n=96, n_holes=3)
+        V, F = m.V, m.F
+    elif name == "closed":
+        V, F = gen.icosphere(3)
+    elif name == "soup":          # multiplicities 2 and 0, degenerate faces; ids < 256
+        V = rng.standard_normal((200, 3)).astype(np.float32)
+        F = rng.integers(0, 200, (600, 3)).astype(np.int32)
+        F = np.concatenate([F, F[:40], F[:9, [0, 2, 1]], np.array([[5, 5, 7], [9, 9, 9]], np.int32)])
+    elif name == "wide_ids":      # ids up to 70,000: three bytes of each id vary
+        V = rng.standard_normal((70000, 3)).astype(np.float32)
+        F = rng.integers(0, 70000, (5000, 3)).astype(np.int32)
+        F = np.concatenate([F, F[:500, [1, 0, 2]], F[500:800]])
+    elif name == "one_vertex":
+        V = np.zeros((1, 3), np.float32)
+        F = np.zeros((3, 3), np.int32)
+    else:
+        V = rng.standard_normal((4, 3)).astype(np.float32)
+        F = np.zeros((0, 3), np.int32)
+    V = np.ascontiguousarray(V, np.float32)
+    F = np.ascontiguousarray(F, np.int32)
+    mesh = gwn.Mesh(ctx, V, F)
+    off, vid = mesh.boundary()
+    hoff, hvid = gwn.boundary_extract_host(F, len(V))
+    assert np.array_equal(np.asarray(off), np.asarray(hoff)) and np.array_equal(np.asarray(vid), np.asarray(hvid))
+    assert _unit_edges_of_loops(off, vid) == _oracle_unit_edge_list(F)
+    info = mesh.info()
+    assert info["n_boundary_edges"] == len(vid) and info["n_loops"] == len(off) - 1
+    # device-resident input takes the same path
+    import torch
+    md = gwn.Mesh(ctx, torch.as_tensor(V).cuda(), torch.as_tensor(F).cuda())
+    doff, dvid = md.boundary()
+    assert np.array_equal(np.asarray(doff), np.asarray(off)) and np.array_equal(np.asarray(dvid), np.asarray(vid))
+    ctx.check()
+
+
 def test_bruteforce_comparator(gwn, ctx):
     m = gen.icosphere_cap(subdiv=3, grid_n=16, seed=1)
     mesh = gwn.Mesh(ctx, m.V, m.F)
