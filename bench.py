@@ -313,7 +313,8 @@ def run_gpu(args):
                 times.append(b - a)
         e2e = {"value": nq / statistics.median(times), "unit": UNIT,
                "h2d_bytes_per_step": int(m.V.nbytes + m.F.nbytes), "d2h_bytes_per_step": int(nq * 4),
-               "includes": "host boundary extraction, uploads, LBVH build, traversal, boundary term, copy of w"}
+               "includes": "upload of V and F, mesh checks and boundary extraction, LBVH build, traversal, "
+                           "boundary term writing w into the pinned host buffer"}
 
         # CPU baseline: the oracle on this host's cores, bounded sample
         import oracle

@@ -230,7 +230,11 @@ GWN_API gwn_status gwn_eval(gwn_geom *g, const gwn_queries *q, const float *d, v
                             int32_t *chi_out, void *b_out, gwn_stats *stats);
 
 /* Same, reading queries from HOST memory and writing w to HOST memory:
- * copies in, evaluates, copies back, synchronises.  (End-to-end entry point.) */
+ * copies in, evaluates, copies back, synchronises.  (End-to-end entry point.)
+ * For meshes and patches, a page-locked w_host (cudaHostAlloc /
+ * cudaHostRegister) is written directly by the kernels instead of through a
+ * device buffer and a copy; the result is the same.  w_host is complete when
+ * the call returns. */
 GWN_API gwn_status gwn_eval_host(gwn_geom *g, const gwn_queries *q, const float *d, void *w_host);
 
 /* Tuning plan for batched evaluation. */

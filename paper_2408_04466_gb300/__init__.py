@@ -234,8 +234,10 @@ class Mesh(_Geom):
             res["stats"] = st.as_dict()
         return res if (want_chi or want_b or stats) else w
 
-    def eval_host(self, queries, d) -> np.ndarray:
-        """End-to-end entry point: host queries in, host w out."""
+    def eval_host(self, queries, d, out=None):
+        """End-to-end entry point: host queries in, host w out.  out: an
+        optional host float32 buffer of n entries (numpy array or CPU tensor;
+        a page-locked one is written by the kernels directly)."""
         if isinstance(queries, Grid):
             qc = queries.to_c(F32)
             n = queries.n
@@ -250,9 +252,17 @@ class Mesh(_Geom):
             qc.pts = keep.ctypes.data_as(C.c_void_p)
             qc.n = len(keep)
             n = len(keep)
-        out = np.empty(n, np.float32)
+        if out is None:
+            out = np.empty(n, np.float32)
+        if isinstance(out, np.ndarray):
+            assert out.dtype == np.float32 and out.size == n and out.flags["C_CONTIGUOUS"]
+            ptr = out.ctypes.data
+        else:
+            assert (not out.is_cuda and out.dtype == _torch().float32 and out.numel() == n
+                    and out.is_contiguous())
+            ptr = out.data_ptr()
         dd, dp = _dir(d)
-        check(self.lib.gwn_eval_host(self.h, C.byref(qc), dp, out.ctypes.data_as(C.c_void_p)), "gwn_eval_host")
+        check(self.lib.gwn_eval_host(self.h, C.byref(qc), dp, C.c_void_p(ptr)), "gwn_eval_host")
         return out
 
     def backward(self, P, grad_w, want_p=True, want_V=True):
@@ -298,6 +308,9 @@ class Patches(_Geom):
 
     def eval(self, queries, d, want_chi=False, want_b=False, stats=False, out=None):
         return Mesh.eval(self, queries, d, want_chi=want_chi, want_b=want_b, stats=stats, out=out)
+
+    def eval_host(self, queries, d, out=None):
+        return Mesh.eval_host(self, queries, d, out=out)
 
 
 class Bezier2D(_Geom):

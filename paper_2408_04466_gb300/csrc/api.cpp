@@ -1115,13 +1115,32 @@ GWN_API gwn_status gwn_eval_host(gwn_geom *g, const gwn_queries *q, const float 
     int64_t nq = query_count(q);
     size_t esz = (g->kind == GWN_GEOM_BEZIER2D && g->dtype == GWN_F64) ? 8 : 4;
     cudaError_t e;
-    void *w = arena_get(ctx, 3, esz * (nq > 0 ? nq : 1), &e);
-    if (!w) return cuda_fail(e, "gwn_eval_host output");
+    // A page-locked output buffer is written by the boundary-term kernels
+    // themselves (on Grace-Blackwell over the coherent CPU-GPU link, while the
+    // kernel runs); other memory gets a device buffer and one copy.  The mesh
+    // and patch paths only ever store to w, one plain store per query.
+    void *w = nullptr;
+    bool direct = false;
+    if (nq > 0 && (g->kind == GWN_GEOM_MESH || g->kind == GWN_GEOM_PATCHES)) {
+        cudaPointerAttributes pa;
+        if (cudaPointerGetAttributes(&pa, w_host) == cudaSuccess) {
+            if (pa.type == cudaMemoryTypeHost && pa.devicePointer) {
+                w = pa.devicePointer;
+                direct = true;
+            }
+        } else {
+            cudaGetLastError();
+        }
+    }
+    if (!direct) {
+        w = arena_get(ctx, 3, esz * (nq > 0 ? nq : 1), &e);
+        if (!w) return cuda_fail(e, "gwn_eval_host output");
+    }
     gwn_queries qq = *q;
     if (q->kind == GWN_QUERY_POINTS) qq.mem_kind = GWN_MEM_HOST;   // staged by make_query_src
     gwn_status s = gwn_eval(g, &qq, d, w, nullptr, nullptr, nullptr);
     if (s != GWN_OK) return s;
-    if (nq > 0) CK(cudaMemcpyAsync(w_host, w, esz * nq, cudaMemcpyDeviceToHost, ctx->stream), "copy w");
+    if (nq > 0 && !direct) CK(cudaMemcpyAsync(w_host, w, esz * nq, cudaMemcpyDeviceToHost, ctx->stream), "copy w");
     CK(cudaStreamSynchronize(ctx->stream), "sync");
     return GWN_OK;
 }

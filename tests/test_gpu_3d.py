@@ -198,6 +198,26 @@ def test_edge_cases(gwn, ctx):
     assert np.array_equal(wd, wh) and np.array_equal(wd, we)
 
 
+def test_eval_host_pinned_output(gwn, ctx):
+    """A page-locked host output is written by the kernels directly; the
+    values are the device path's, bit for bit (grid and point queries)."""
+    import torch
+    m = gen.icosphere_cap(subdiv=3, grid_n=24, seed=2)
+    mesh = gwn.Mesh(ctx, m.V, m.F)
+    g = gwn.Grid(m.grid.lo, m.grid.hi, m.grid.dims)
+    wd = mesh.eval(g, m.d).cpu().numpy()
+    wp = torch.full((g.n,), float("nan")).pin_memory()
+    mesh.eval_host(g, m.d, out=wp)
+    assert np.array_equal(wp.numpy(), wd)
+    assert np.array_equal(mesh.eval_host(g, m.d), wd)        # pageable: device buffer + copy
+    P = gen.grid_points(m.grid)[::7].astype(np.float32)
+    wq = mesh.eval(gwn.Points(torch.as_tensor(P).cuda()), m.d).cpu().numpy()
+    wpp = torch.empty(len(P)).pin_memory()
+    mesh.eval_host(P, m.d, out=wpp)
+    assert np.array_equal(wpp.numpy(), wq)
+    ctx.check()
+
+
 def test_invalid_inputs_are_errors(gwn, ctx):
     V = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0]], np.float32)
     with pytest.raises(gwn.GwnError):

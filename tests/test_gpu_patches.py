@@ -58,6 +58,10 @@ def test_closed_patch_surface_is_integer(gwn, ctx):
     assert np.array_equal(chi[keep], chio)
     assert np.array_equal(w[keep], chi[keep].astype(np.float32))      # no boundary: w = chi exactly
     assert set(np.unique(chio)) <= {0, 1}
+    import torch
+    wp = torch.empty(g.n).pin_memory()                                 # kernels write the pinned buffer
+    ps.eval_host(gwn.Grid(g.lo, g.hi, g.dims), pc.d, out=wp)
+    assert np.array_equal(wp.numpy(), w)
 
 
 @pytest.mark.parametrize("seed, n, amp", [(2, 2, 0.08), (3, 3, 0.15)])
