@@ -132,6 +132,9 @@ typedef struct gwn_geom_info {
     int64_t n_loops;            /* 3D: boundary loops; 2D: chains */
     int64_t n_pieces;           /* 2D: y-monotone pieces; 3D: 0 */
     int64_t n_chains;           /* 2D: chains; 3D: 0 */
+    int64_t n_bins;             /* mesh, after preparation: bins of the 2D crossing index (0: tree only) */
+    int64_t n_bin_entries;      /* (bin, triangle) entries */
+    int64_t bin_maxlen;         /* longest bin list */
 } gwn_geom_info;
 
 /* Library version string (static storage). */
@@ -161,6 +164,19 @@ GWN_API void gwn_ctx_destroy(gwn_ctx *ctx);
  * built per direction d on first use (or by gwn_mesh_prepare). */
 GWN_API gwn_status gwn_mesh_create(gwn_ctx *ctx, const float *V, int64_t nv, const int32_t *F,
                                    int64_t nf, int mem_kind, gwn_geom **out);
+
+/* Crossing index of a mesh.  All rays share d, so the crossing search is a
+ * 2D point location in the plane normal to d plus a depth test.  AUTO (the
+ * default): an evaluation with at least 4 queries per triangle (and d not
+ * parallel to a grid axis of grid queries, which reuse rays per grid line)
+ * builds once, besides the LBVH, a bin grid over the projected triangle boxes
+ * (lists by decreasing depth) and uses it when it is compact (at most 12
+ * entries per triangle + 4096; no list longer than both 512 and 64 times the
+ * mean); TREE always uses the LBVH traversal.  Both test exactly the same
+ * (query, triangle) pairs, so the crossing counts are identical.  Takes effect
+ * at the next evaluation. */
+enum { GWN_INDEX_AUTO = 0, GWN_INDEX_TREE = 1 };
+GWN_API gwn_status gwn_mesh_set_index(gwn_geom *g, int index);
 
 /* Build (or reuse) the on-device LBVH of the mesh in the frame of direction
  * d (float32[3], any nonzero length).  Optional: gwn_eval prepares lazily. */

@@ -197,6 +197,11 @@ class Mesh(_Geom):
         self.h = h
         _live_geoms.add(self)
 
+    def set_index(self, index: str):
+        """Crossing index: "auto" (2D bins when compact, else the LBVH) or
+        "tree" (always the LBVH); the crossing counts are the same."""
+        check(self.lib.gwn_mesh_set_index(self.h, {"auto": 0, "tree": 1}[index]), "gwn_mesh_set_index")
+
     def prepare(self, d):
         dd, dp = _dir(d)
         check(self.lib.gwn_mesh_prepare(self.h, dp), "gwn_mesh_prepare")

@@ -37,7 +37,8 @@ class gwn_stats(C.Structure):
 class gwn_geom_info(C.Structure):
     _fields_ = [("kind", C.c_int32), ("dtype", C.c_int32), ("n_vertices", C.c_int64), ("n_primitives", C.c_int64),
                 ("n_boundary_edges", C.c_int64), ("n_loops", C.c_int64), ("n_pieces", C.c_int64),
-                ("n_chains", C.c_int64)]
+                ("n_chains", C.c_int64), ("n_bins", C.c_int64), ("n_bin_entries", C.c_int64),
+                ("bin_maxlen", C.c_int64)]
 
 
 class gwn_plan(C.Structure):
@@ -62,6 +63,7 @@ _SIGS = {
     "gwn_patches_create": (ST, [P, P, I64, C.c_int, C.c_int, C.POINTER(P)]),
     "gwn_geom_info_get": (ST, [P, C.POINTER(gwn_geom_info)]),
     "gwn_geom_destroy": (None, [P]),
+    "gwn_mesh_set_index": (ST, [P, I32]),
     "gwn_mesh_boundary": (ST, [P, P, P]),
     "gwn_boundary_extract_host": (ST, [P, I64, I64, P, P, C.POINTER(I64), C.POINTER(I64)]),
     "gwn_bezier_monotone_split_host": (ST, [P, P, C.POINTER(I32)]),

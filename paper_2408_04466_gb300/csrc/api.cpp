@@ -540,6 +540,15 @@ GWN_API gwn_status gwn_mesh_create(gwn_ctx *ctx, const float *V, int64_t nv, con
     return GWN_OK;
 }
 
+GWN_API gwn_status gwn_mesh_set_index(gwn_geom *g, int index) {
+    if (!g || g->kind != GWN_GEOM_MESH || (index != GWN_INDEX_AUTO && index != GWN_INDEX_TREE)) {
+        set_error("gwn_mesh_set_index: bad arguments");
+        return GWN_E_INVALID;
+    }
+    g->crossing_index = index;
+    return GWN_OK;
+}
+
 GWN_API gwn_status gwn_mesh_prepare(gwn_geom *g, const float d[3]) {
     if (!g || g->kind != GWN_GEOM_MESH || !d) { set_error("gwn_mesh_prepare: bad arguments"); return GWN_E_INVALID; }
     if (!isfinite(d[0]) || !isfinite(d[1]) || !isfinite(d[2]) || (d[0] == 0.f && d[1] == 0.f && d[2] == 0.f)) {
@@ -812,6 +821,11 @@ GWN_API gwn_status gwn_geom_info_get(const gwn_geom *g, gwn_geom_info *out) {
         out->n_primitives = g->nf;
         out->n_boundary_edges = (int64_t)g->loop_vid.size();
         out->n_loops = (int64_t)g->loop_off.size() - 1;
+        if (g->bvh.valid && g->bvh.n_bin_entries > 0) {
+            out->n_bins = (int64_t)g->bvh.bins.nbx * g->bvh.bins.nby;
+            out->n_bin_entries = g->bvh.n_bin_entries;
+            out->bin_maxlen = g->bvh.bin_maxlen;
+        }
     } else if (g->kind == GWN_GEOM_PATCHES) {
         out->n_vertices = g->nv;                      // boundary polyline vertices
         out->n_primitives = g->ps.n;
@@ -1018,15 +1032,20 @@ GWN_API gwn_status gwn_eval(gwn_geom *g, const gwn_queries *q, const float *d, v
         }
         int32_t *defer = (int32_t *)arena_get(ctx, 4, sizeof(int32_t) * nq, &e);
         if (!defer) return cuda_fail(e, "deferred-query list");
-        if (stats) CK(cudaEventRecord(ctx->ev[1], ctx->stream), "event");
         int32_t *lines = nullptr;
         size_t lbytes = traverse_lines_bytes(g->bvh, src);
         if (lbytes) {
             lines = (int32_t *)arena_get(ctx, 5, lbytes, &e);
             if (!lines) return cuda_fail(e, "per-line crossing lists");
+        } else if (g->crossing_index == GWN_INDEX_AUTO && !g->bvh.bins_tried && nq >= 4 * g->nf) {
+            // enough queries per triangle for the 2D bins to repay their build
+            e = bins_build(g, ctx->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "crossing bins");
         }
+        if (stats) CK(cudaEventRecord(ctx->ev[1], ctx->stream), "event");
         e = launch_traverse(g->bvh, src, chi, defer, ctx->d_defer_count, ctx->d_tpairs, ctx->d_tpair_count, lines,
-                            stats ? ctx->d_cnt : nullptr, ctx->d_status, ctx->sm_count, ctx->stream);
+                            stats ? ctx->d_cnt : nullptr, ctx->d_status, ctx->sm_count, ctx->stream,
+                            g->crossing_index != GWN_INDEX_TREE);
         if (e != cudaSuccess) return cuda_fail(e, "crossing traversal");
         if (stats) CK(cudaEventRecord(ctx->ev[2], ctx->stream), "event");
         e = launch_bterm3d(g->bseq, g->bvh.bframe, g->n_bseq, g->bvh.frame, make_frame64(d), src, chi, (float *)w_out,

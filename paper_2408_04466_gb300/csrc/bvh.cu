@@ -19,6 +19,7 @@
 #include <string.h>
 
 #include "gwn_internal.h"
+#include "query.cuh"
 
 namespace gwn {
 
@@ -37,11 +38,13 @@ __device__ __forceinline__ float ord2f(unsigned u) {
     return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
 }
 
+// bounds: [0..2] min and [3..5] max centroid, [6] min x0, [7] max x1, [8] min
+// y0, [9] max y1 of the padded boxes (order-preserving unsigned)
 __global__ void tri_prep_kernel(const float *__restrict__ V, const int32_t *__restrict__ F, int64_t nf, Frame fr,
                                 float4 *__restrict__ box_xy, float *__restrict__ box_z,
                                 float4 *__restrict__ cen, unsigned *bounds) {
-    __shared__ unsigned smin[3], smax[3];
-    if (threadIdx.x < 3) { smin[threadIdx.x] = 0xffffffffu; smax[threadIdx.x] = 0u; }
+    __shared__ unsigned smin[5], smax[5];
+    if (threadIdx.x < 5) { smin[threadIdx.x] = 0xffffffffu; smax[threadIdx.x] = 0u; }
     __syncthreads();
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t < nf) {
@@ -61,6 +64,8 @@ __global__ void tri_prep_kernel(const float *__restrict__ V, const int32_t *__re
         }
         pad = pad * 4e-7f + 1e-30f;
         box_xy[t] = make_float4(x0 - pad, x1 + pad, y0 - pad, y1 + pad);
+        atomicMin(&smin[3], f2ord(x0 - pad)); atomicMax(&smax[3], f2ord(x1 + pad));
+        atomicMin(&smin[4], f2ord(y0 - pad)); atomicMax(&smax[4], f2ord(y1 + pad));
         box_z[t] = z1 + pad;
         cx *= (1.f / 3.f); cy *= (1.f / 3.f); cz *= (1.f / 3.f);
         cen[t] = make_float4(cx, cy, cz, 0.f);
@@ -72,6 +77,10 @@ __global__ void tri_prep_kernel(const float *__restrict__ V, const int32_t *__re
     if (threadIdx.x < 3) {
         atomicMin(&bounds[threadIdx.x], smin[threadIdx.x]);
         atomicMax(&bounds[3 + threadIdx.x], smax[threadIdx.x]);
+    } else if (threadIdx.x < 5) {
+        int k = threadIdx.x - 3;
+        atomicMin(&bounds[6 + 2 * k], smin[threadIdx.x]);
+        atomicMax(&bounds[7 + 2 * k], smax[threadIdx.x]);
     }
 }
 
@@ -400,9 +409,88 @@ __global__ void bseq_kernel(const float *__restrict__ V, const int32_t *__restri
 // zeroes the refit arrival counters and seeds the bound reductions
 __global__ void build_init_kernel(unsigned *bounds, unsigned *rad, unsigned *flags, int64_t nflags) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < 8) bounds[i] = i < 3 ? 0xffffffffu : 0u;
+    if (i < 12) bounds[i] = (i < 3 || i == 6 || i == 8) ? 0xffffffffu : 0u;
     if (i == 0) *rad = 0u;
     if (i < nflags) flags[i] = 0u;
+}
+
+// ---- 2D bins over the projection plane --------------------------------------
+// All rays share d, so a ray is a point of the (e1, e2) plane and the
+// crossing search is a 2D point location plus a depth test.  The bounding
+// rectangle of the padded triangle boxes is cut into nbx x nby bins (about
+// BIN_TRIS triangles per bin); bin (i, j) lists every triangle whose padded box
+// overlaps it, by decreasing zmax.  bin_of (query.cuh) is monotone in its
+// argument, which makes the lookup exact (see chi_bins_kernel).
+constexpr int BIN_TRIS = 2;
+
+// number of (bin, triangle) entries: the bins of each padded box, summed
+__global__ void bin_count_kernel(const float4 *__restrict__ tbox, int64_t n, BinParams bp,
+                                 unsigned long long *total) {
+    __shared__ unsigned long long s;
+    if (threadIdx.x == 0) s = 0;
+    __syncthreads();
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) {
+        float4 b = tbox[2 * t];
+        unsigned long long c = (unsigned long long)(bin_of(b.y, bp.x0, bp.invx, bp.nbx) -
+                                                    bin_of(b.x, bp.x0, bp.invx, bp.nbx) + 1) *
+                               (unsigned long long)(bin_of(b.w, bp.y0, bp.invy, bp.nby) -
+                                                    bin_of(b.z, bp.y0, bp.invy, bp.nby) + 1);
+        atomicAdd(&s, c);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && s) atomicAdd(total, s);
+}
+
+// one (key, triangle) per entry: key = bin << 32 | ~order(zmax), so the sort
+// puts each bin's triangles by decreasing zmax; triangles in sorted order
+__global__ void bin_emit_kernel(const float4 *__restrict__ tbox, int64_t n, BinParams bp, int64_t cap,
+                                unsigned long long *__restrict__ keys, int32_t *__restrict__ vals,
+                                unsigned long long *counter) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    float4 b = tbox[2 * t];
+    float zm = tbox[2 * t + 1].x;
+    int bx0 = bin_of(b.x, bp.x0, bp.invx, bp.nbx), bx1 = bin_of(b.y, bp.x0, bp.invx, bp.nbx);
+    int by0 = bin_of(b.z, bp.y0, bp.invy, bp.nby), by1 = bin_of(b.w, bp.y0, bp.invy, bp.nby);
+    unsigned long long c = (unsigned long long)(bx1 - bx0 + 1) * (unsigned long long)(by1 - by0 + 1);
+    unsigned long long pos = atomicAdd(counter, c);
+    unsigned zk = ~f2ord(zm);
+    for (int by = by0; by <= by1; by++)
+        for (int bx = bx0; bx <= bx1; bx++, pos++)
+            if ((int64_t)pos < cap) {
+                keys[pos] = ((unsigned long long)((int64_t)by * bp.nbx + bx) << 32) | zk;
+                vals[pos] = (int32_t)t;
+            }
+}
+
+// sorted entries -> (zmax, triangle) and the padded box of each entry
+__global__ void bin_pack_kernel(const int32_t *__restrict__ vals, int64_t m, const float4 *__restrict__ tbox,
+                                float2 *__restrict__ zt, float4 *__restrict__ box) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    int t = vals[i];
+    box[i] = tbox[2 * (int64_t)t];
+    zt[i] = make_float2(tbox[2 * (int64_t)t + 1].x, __int_as_float(t));
+}
+
+// start[b] = first entry of bin b (b = nbins: the entry count), by binary
+// search over the sorted keys; the longest list goes to *maxlen
+__global__ void bin_start_kernel(const unsigned long long *__restrict__ keys, int64_t m, int64_t nbins,
+                                 int32_t *__restrict__ start, unsigned *maxlen) {
+    int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b > nbins) return;
+    auto lower = [&](unsigned long long k) {
+        int64_t lo = 0, hi = m;
+        while (lo < hi) {
+            int64_t mid = (lo + hi) >> 1;
+            if (keys[mid] < k) lo = mid + 1; else hi = mid;
+        }
+        return lo;
+    };
+    int64_t s = lower((unsigned long long)b << 32);
+    start[b] = (int32_t)s;
+    if (b < nbins) atomicMax(maxlen, (unsigned)(lower((unsigned long long)(b + 1) << 32) - s));
 }
 
 inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
@@ -506,6 +594,17 @@ cudaError_t launch_bseq(const float *dV, const int32_t *code, int64_t n, float4 
     return cudaGetLastError();
 }
 
+static void bins_free(MeshBvh &b) {
+    if (b.bin_block) cudaFree(b.bin_block);
+    b.bin_block = nullptr;
+    b.bin_start = nullptr;
+    b.bin_zt = nullptr;
+    b.bin_box = nullptr;
+    b.n_bin_entries = 0;
+    b.bin_maxlen = 0;
+    b.bins = BinParams();
+}
+
 void bvh_free(MeshBvh &b) {
     if (b.block) cudaFree(b.block);
     b.block = nullptr;
@@ -513,7 +612,16 @@ void bvh_free(MeshBvh &b) {
     b.bframe = nullptr;
     b.nodes = nullptr;
     b.tris = nullptr;
+    bins_free(b);
+    b.bins_tried = false;
     b.valid = false;
+}
+
+static float ord2f_host(unsigned u) {
+    unsigned v = (u & 0x80000000u) ? (u & 0x7fffffffu) : ~u;
+    float f;
+    memcpy(&f, &v, sizeof(f));
+    return f;
 }
 
 cudaError_t bvh_build(gwn_geom *g, const Frame &fr, cudaStream_t st) {
@@ -523,13 +631,14 @@ cudaError_t bvh_build(gwn_geom *g, const Frame &fr, cudaStream_t st) {
     b.n = n;
     b.frame = fr;
     for (int k = 0; k < 3; k++) b.dkey[k] = fr.d[k];
-    // the BVH's own arrays in one allocation
+    cudaError_t err = cudaSuccess;
+    // the structure's own arrays, in one allocation
     Carve keep;
     for (int pass = 0; pass < 2; pass++) {
         if (pass == 1) {
             if (keep.off == 0) break;
-            cudaError_t e = cudaMalloc(&b.block, keep.off);
-            if (e != cudaSuccess) { b.block = nullptr; return e; }
+            err = cudaMalloc(&b.block, keep.off);
+            if (err != cudaSuccess) { b.block = nullptr; return err; }
             keep.base = (char *)b.block;
             keep.off = 0;
         }
@@ -539,7 +648,6 @@ cudaError_t bvh_build(gwn_geom *g, const Frame &fr, cudaStream_t st) {
         BvhNode *nd = n > 1 ? keep.take<BvhNode>(n - 1) : nullptr;
         if (pass == 1) { b.bframe = bf; b.tris = tr; b.tbox = tb; b.nodes = nd; }
     }
-    cudaError_t err = cudaSuccess;
     if (g->n_bseq > 0) {                 // boundary records in this frame
         err = launch_bframe(g->bseq, g->n_bseq, fr, b.bframe, st);
         if (err != cudaSuccess) { bvh_free(b); return err; }
@@ -559,7 +667,7 @@ cudaError_t bvh_build(gwn_geom *g, const Frame &fr, cudaStream_t st) {
         }
         float4 *tbox_xy = c.take<float4>(n), *cen = c.take<float4>(n);
         float *tbox_z = c.take<float>(n);
-        unsigned *bounds = c.take<unsigned>(8), *rad = c.take<unsigned>(1), *hist = c.take<unsigned>(sort_hist_count(n));
+        unsigned *bounds = c.take<unsigned>(12), *rad = c.take<unsigned>(1), *hist = c.take<unsigned>(sort_hist_count(n));
         unsigned long long *k0 = c.take<unsigned long long>(n), *k1 = c.take<unsigned long long>(n);
         int32_t *v0 = c.take<int32_t>(n), *v1 = c.take<int32_t>(n);
         int *skip = c.take<int>(1);
@@ -569,7 +677,7 @@ cudaError_t bvh_build(gwn_geom *g, const Frame &fr, cudaStream_t st) {
         float *leaf_z = c.take<float>(n), *int_z = c.take<float>(ni);
         unsigned *flags = c.take<unsigned>(ni);
         if (pass == 0) continue;
-        build_init_kernel<<<blocks_for(ni > 8 ? ni : 8, 256), 256, 0, st>>>(bounds, rad, flags, n > 1 ? n - 1 : 0);
+        build_init_kernel<<<blocks_for(ni > 12 ? ni : 12, 256), 256, 0, st>>>(bounds, rad, flags, n > 1 ? n - 1 : 0);
         radius_kernel<<<blocks_for(g->nv, 256), 256, 0, st>>>(g->dV, g->nv, rad);
         tri_prep_kernel<<<blocks_for(n, 256), 256, 0, st>>>(g->dV, g->dF, n, fr, tbox_xy, tbox_z, cen, bounds);
         morton_kernel<<<blocks_for(n, 256), 256, 0, st>>>(cen, n, bounds, k0, v0);
@@ -586,16 +694,124 @@ cudaError_t bvh_build(gwn_geom *g, const Frame &fr, cudaStream_t st) {
             }
             err = cudaGetLastError();
         }
-        unsigned rbits = 0;
-        if (err == cudaSuccess) err = cudaMemcpyAsync(&rbits, rad, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
+        unsigned h[12];
+        if (err == cudaSuccess) err = cudaMemcpyAsync(h, bounds, sizeof(unsigned) * 10, cudaMemcpyDeviceToHost, st);
+        if (err == cudaSuccess) err = cudaMemcpyAsync(&h[10], rad, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
         if (err == cudaSuccess) err = cudaStreamSynchronize(st);
         if (err != cudaSuccess) { bvh_free(b); return err; }
-        float rr;
-        memcpy(&rr, &rbits, sizeof(float));
-        b.scene_radius = rr;
+        memcpy(&b.scene_radius, &h[10], sizeof(float));
+        for (int k = 0; k < 4; k++) b.box_bounds[k] = ord2f_host(h[6 + k]);
     }
     b.root = n == 1 ? ~0 : 0;
     b.valid = true;
+    return cudaSuccess;
+}
+
+// Bin grid for n triangles over the box bounds (x0, x1, y0, y1): about
+// BIN_TRIS triangles per bin, bins near square, at most 2^22 of them.
+static BinParams bin_params(const float bb[4], int64_t n) {
+    double W = (double)bb[1] - bb[0], H = (double)bb[3] - bb[2];
+    double T = (double)(n / BIN_TRIS > 0 ? n / BIN_TRIS : 1);
+    if (T > (double)(1 << 22)) T = (double)(1 << 22);
+    int nbx = 1, nby = 1;
+    if (W > 0 && H > 0) {
+        nbx = (int)fmin(fmax(rint(sqrt(T * W / H)), 1.0), 16384.0);
+        nby = (int)fmin(fmax(rint(T / nbx), 1.0), 16384.0);
+    } else if (W > 0) {
+        nbx = (int)fmin(T, 65536.0);
+    } else if (H > 0) {
+        nby = (int)fmin(T, 65536.0);
+    }
+    BinParams r;
+    r.x0 = bb[0]; r.x1 = bb[1]; r.y0 = bb[2]; r.y1 = bb[3];
+    r.invx = W > 0 ? (float)(nbx / W) : 0.f;
+    r.invy = H > 0 ? (float)(nby / H) : 0.f;
+    if (!(r.invx <= 3.0e38f)) { r.invx = 0.f; nbx = 1; }   // a width too small for float bins
+    if (!(r.invy <= 3.0e38f)) { r.invy = 0.f; nby = 1; }
+    r.nbx = nbx; r.nby = nby;
+    return r;
+}
+
+cudaError_t bins_build(gwn_geom *g, cudaStream_t st) {
+    MeshBvh &b = g->bvh;
+    if (!b.valid || b.bins_tried) return cudaSuccess;
+    b.bins_tried = true;
+    const int64_t n = b.n;
+    if (n < 2 || n >= (int64_t(1) << 26)) return cudaSuccess;
+    const BinParams bp = bin_params(b.box_bounds, n);
+    const int64_t nbins = (int64_t)bp.nbx * bp.nby;
+    cudaError_t err = cudaSuccess;
+    // entry count first: it sizes everything else
+    unsigned long long *dtotal = (unsigned long long *)arena_get(g->ctx, 7, 2 * sizeof(unsigned long long), &err);
+    if (!dtotal) return err;
+    err = cudaMemsetAsync(dtotal, 0, 2 * sizeof(unsigned long long), st);
+    if (err != cudaSuccess) return err;
+    bin_count_kernel<<<blocks_for(n, 256), 256, 0, st>>>(b.tbox, n, bp, dtotal);
+    unsigned long long total = 0;
+    err = cudaGetLastError();
+    if (err == cudaSuccess) err = cudaMemcpyAsync(&total, dtotal, sizeof(total), cudaMemcpyDeviceToHost, st);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(st);
+    if (err != cudaSuccess) return err;
+    if (total == 0 || total > (unsigned long long)(12 * n + 4096)) return cudaSuccess;   // not compact: the tree
+    const int64_t m = (int64_t)total;
+    Carve keep;
+    for (int pass = 0; pass < 2; pass++) {
+        if (pass == 1) {
+            err = cudaMalloc(&b.bin_block, keep.off);
+            if (err != cudaSuccess) { b.bin_block = nullptr; return err; }
+            keep.base = (char *)b.bin_block;
+            keep.off = 0;
+        }
+        int32_t *bs = keep.take<int32_t>(nbins + 1);
+        float2 *bz = keep.take<float2>(m);
+        float4 *bb = keep.take<float4>(m);
+        if (pass == 1) { b.bin_start = bs; b.bin_zt = bz; b.bin_box = bb; }
+    }
+    Carve c;
+    unsigned long long *bk0 = nullptr, *bk1 = nullptr, *counter = nullptr;
+    int32_t *bv0 = nullptr, *bv1 = nullptr;
+    unsigned *bhist = nullptr;
+    int *bskip = nullptr;
+    for (int pass = 0; pass < 2; pass++) {
+        if (pass == 1) {
+            c.base = (char *)arena_get(g->ctx, 7, c.off, &err);
+            if (!c.base) { bins_free(b); return err; }
+            c.off = 0;
+        }
+        counter = c.take<unsigned long long>(2);
+        bk0 = c.take<unsigned long long>(m); bk1 = c.take<unsigned long long>(m);
+        bv0 = c.take<int32_t>(m); bv1 = c.take<int32_t>(m);
+        bhist = c.take<unsigned>(sort_hist_count(m));
+        bskip = c.take<int>(1);
+    }
+    unsigned *maxlen = (unsigned *)(counter + 1);
+    err = cudaMemsetAsync(counter, 0, 2 * sizeof(unsigned long long), st);
+    if (err != cudaSuccess) { bins_free(b); return err; }
+    bin_emit_kernel<<<blocks_for(n, 256), 256, 0, st>>>(b.tbox, n, bp, m, bk0, bv0, counter);
+    int bits = 0;
+    while (bits < 40 && (int64_t(1) << bits) < nbins) bits++;
+    const unsigned nb = (unsigned)((bits + 7) / 8);
+    const unsigned mask = 0x0fu | (((1u << nb) - 1u) << 4);   // 4 bytes of depth, then the bin bytes
+    err = cudaGetLastError();
+    if (err == cudaSuccess) err = radix_sort_pairs(bk0, bv0, bk1, bv1, m, bhist, bskip, mask, st);
+    if (err == cudaSuccess) {
+        bin_pack_kernel<<<blocks_for(m, 256), 256, 0, st>>>(bv0, m, b.tbox, b.bin_zt, b.bin_box);
+        bin_start_kernel<<<blocks_for(nbins + 1, 256), 256, 0, st>>>(bk0, m, nbins, b.bin_start, maxlen);
+        err = cudaGetLastError();
+    }
+    unsigned hmax = 0;
+    if (err == cudaSuccess) err = cudaMemcpyAsync(&hmax, maxlen, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(st);
+    if (err != cudaSuccess) { bins_free(b); return err; }
+    // a list far longer than the mean (a dense cluster in a sparse domain)
+    // would be scanned by every query in its bin: the tree serves then
+    if (hmax > 512 && (double)hmax > 64.0 * (double)m / (double)nbins) {
+        bins_free(b);
+        return cudaSuccess;
+    }
+    b.bins = bp;
+    b.n_bin_entries = m;
+    b.bin_maxlen = (int64_t)hmax;
     return cudaSuccess;
 }
 

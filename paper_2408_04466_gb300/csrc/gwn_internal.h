@@ -68,6 +68,14 @@ struct BvhNode {          // internal node: boxes of both children in the d-fram
 };
 // child ref: >= 0 internal node index; < 0 leaf ~(sorted triangle index)
 
+// Bin grid of the projection plane (frame of d): the bin of a coordinate v
+// along x is clamp(floor((v - x0) * invx), 0, nbx - 1), likewise along y;
+// [x0, x1] x [y0, y1] bounds every padded triangle box.
+struct BinParams {
+    float x0 = 0.f, y0 = 0.f, x1 = 0.f, y1 = 0.f, invx = 0.f, invy = 0.f;
+    int nbx = 0, nby = 0;   // 0: no bins
+};
+
 struct MeshBvh {
     bool valid = false;
     float dkey[3] = {0, 0, 0};
@@ -80,6 +88,18 @@ struct MeshBvh {
     float scene_radius = 0.f;  // max |v|_2 over the mesh vertices
     Frame frame;
     float4 *bframe = nullptr;  // 2 float4 per boundary record: A.(e1, e2, n) hi (+ w), lo
+    float box_bounds[4] = {0, 0, 0, 0};   // min x0, max x1, min y0, max y1 of the padded boxes
+    // bins, built on demand by bins_build (n_bin_entries = 0: none, the tree
+    // is used): bin b = j * nbx + i lists entries [bin_start[b],
+    // bin_start[b + 1]) by decreasing zmax
+    bool bins_tried = false;
+    void *bin_block = nullptr;      // one allocation holding the three bin arrays
+    BinParams bins;
+    int64_t n_bin_entries = 0;
+    int64_t bin_maxlen = 0;
+    int32_t *bin_start = nullptr;   // nbx * nby + 1
+    float2 *bin_zt = nullptr;       // (zmax, sorted triangle index as int bits) per entry
+    float4 *bin_box = nullptr;      // padded box (x0, x1, y0, y1) per entry
 };
 
 // Bicubic Bezier patches (parametric surfaces): control nets, and per ray
@@ -187,8 +207,8 @@ struct gwn_ctx {
     int2 *d_tpairs = nullptr;                 // traversal: unsettled (query, triangle) pairs [GWN_TPAIR_CAP]
     unsigned long long *d_work_counter = nullptr;   // 2D work-item counter
     int32_t *d_tpair_count = nullptr;
-    gwn::Arena scratch[7];                    // 0 chi, 1 staged points, 2 2D batch, 3 host-eval w, 4 deferred list,
-                                              // 5 per-line crossing lists, 6 mesh intake and LBVH build
+    gwn::Arena scratch[8];                    // 0 chi, 1 staged points, 2 2D batch, 3 host-eval w, 4 deferred list,
+                                              // 5 per-line crossing lists, 6 mesh intake and LBVH build, 7 bin sort
     std::vector<gwn::AxisCache> axis_cache;   // most recent grids, at most 64
     cudaEvent_t ev[8];
     bool events = false;
@@ -204,6 +224,7 @@ struct gwn_geom {
     int dtype = GWN_F32;
     // mesh
     int64_t nv = 0, nf = 0;
+    int crossing_index = GWN_INDEX_AUTO;   // GWN_INDEX_TREE: never the bins
     float *dV = nullptr;
     int32_t *dF = nullptr;
     std::vector<int64_t> loop_off;     // host, n_loops + 1 (in edges)
@@ -238,6 +259,10 @@ Frame64 make_frame64(const float d[3]);
 // ---- launchers (return the first CUDA error) -------------------------------
 cudaError_t bvh_build(gwn_geom *g, const Frame &fr, cudaStream_t st);
 void bvh_free(MeshBvh &b);
+// Builds the 2D bin index of a built tree once (a later call returns at
+// once); keeps it when it is compact, else leaves n_bin_entries = 0.
+// Synchronises the stream.
+cudaError_t bins_build(gwn_geom *g, cudaStream_t st);
 // Mesh intake on the device (V: nv x 3 float32, F: nf x 3 int32, both on the
 // device): fails with GWN_E_INVALID on a non-finite coordinate or a face index
 // outside [0, nv); otherwise returns the boundary unit edges (each undirected
@@ -260,7 +285,7 @@ cudaError_t launch_bseq(const float *dV, const int32_t *code, int64_t n, float4 
 size_t traverse_lines_bytes(const MeshBvh &b, const QuerySrc &q);
 cudaError_t launch_traverse(const MeshBvh &b, const QuerySrc &q, int32_t *chi, int32_t *defer,
                             int32_t *defer_count, int2 *pairs, int32_t *pair_count, int32_t *lines,
-                            unsigned long long *cnt, int *status, int sm_count, cudaStream_t st);
+                            unsigned long long *cnt, int *status, int sm_count, cudaStream_t st, bool use_bins = true);
 
 // Boundary term + epilogue (w = chi + B).  defer: int32 scratch of q.n
 // entries for the deferred-query list; defer_count: one device int32.

@@ -89,7 +89,8 @@ extern "C" GWN_API gwn_status gwn_eval_points_noalloc(gwn_geom *g, const float *
     src.pts = pts;
     src.n = n;
     e = launch_traverse(g->bvh, src, chi, chi + GWN_NOALLOC_MAX_QUERIES, ctx->d_defer_count, ctx->d_tpairs,
-                        ctx->d_tpair_count, nullptr, nullptr, ctx->d_status, ctx->sm_count, ctx->stream);
+                        ctx->d_tpair_count, nullptr, nullptr, ctx->d_status, ctx->sm_count, ctx->stream,
+                        g->crossing_index != GWN_INDEX_TREE);
     if (e != cudaSuccess) return cuda_fail(e, "gwn_eval_points_noalloc: traversal");
     e = launch_bterm3d(g->bseq, g->bvh.bframe, g->n_bseq, g->bvh.frame, make_frame64(d), src, chi, w_out, nullptr,
                        chi + GWN_NOALLOC_MAX_QUERIES, ctx->d_defer_count, nullptr, ctx->d_status, ctx->sm_count,

@@ -18,6 +18,15 @@ __device__ __forceinline__ float3 query_point3(const QuerySrc &q, int64_t i) {
     return make_float3(__ldg(p), __ldg(p + 1), __ldg(p + 2));
 }
 
+// Bin of coordinate v on a bin axis starting at v0 with inv = bins per unit:
+// clamp(floor((v - v0) * inv), 0, nb - 1) with explicitly rounded operations,
+// so it is monotone non-decreasing in v (fmaxf maps NaN to bin 0).
+__device__ __forceinline__ int bin_of(float v, float v0, float inv, int nb) {
+    float f = floorf(__fmul_rn(__fsub_rn(v, v0), inv));
+    f = fminf(fmaxf(f, 0.f), (float)(nb - 1));
+    return (int)f;
+}
+
 // Spatially coherent thread -> grid point mapping for the crossing traversal:
 // a 256-thread block covers an 8 x 8 x 4 tile of the grid and each warp a
 // 4 x 4 x 2 sub-tile, so the 32 rays of a warp are neighbours in the

@@ -354,6 +354,135 @@ __global__ void __launch_bounds__(256) traverse_packet_kernel(const BvhNode *__r
     }
 }
 
+// Crossing count from the 2D bins (bvh.cu): the query's padded ray box
+// [xlo, xhi] x [ylo, yhi] covers bins [bin(xlo), bin(xhi)] x [bin(ylo),
+// bin(yhi)] (usually one).  A triangle box overlapping the ray box shares
+// with it the point (max(x0, xlo), max(y0, ylo)), whose bin, by the
+// monotonicity of bin_of, is (max(bin(x0), bin(xlo)), max(bin(y0), bin(ylo)))
+// and lies in both bin ranges: the pair is tested in that bin only, so every
+// triangle that passes the tree's leaf test (the same box_hit) is tested
+// exactly once, and the count equals the tree traversal's.  A bin's list runs
+// by decreasing zmax, so its scan stops at the first box behind the query.
+// The leaf tests go through the same per-warp (triangle, lane) compaction as
+// traverse_packet_kernel.  GRID: warp tiles of the grid; otherwise one point
+// per thread.  Requires fewer than 2^26 triangles.
+template <bool GRID>
+__global__ void __launch_bounds__(256) chi_bins_kernel(const int32_t *__restrict__ bin_start,
+                                                       const float2 *__restrict__ bin_zt,
+                                                       const float4 *__restrict__ bin_box, BinParams bp,
+                                                       const float4 *__restrict__ tris, Frame fr, TravParams tp,
+                                                       QuerySrc q, int32_t *__restrict__ chi, int32_t *defer,
+                                                       int32_t *defer_count, int2 *tpairs, int32_t *tpair_count,
+                                                       unsigned long long *cnt) {
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int64_t idx = GRID ? grid_tile_query(q) : (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    bool valid = idx >= 0 && idx < q.n;
+    float3 p = valid ? query_point3(q, idx) : make_float3(0.f, 0.f, 0.f);
+    float3 D = make_float3(fr.d[0], fr.d[1], fr.d[2]);
+    float p1 = fmaf(p.z, fr.e1[2], fmaf(p.y, fr.e1[1], p.x * fr.e1[0]));
+    float p2 = fmaf(p.z, fr.e2[2], fmaf(p.y, fr.e2[1], p.x * fr.e2[0]));
+    float p3 = fmaf(p.z, fr.dh[2], fmaf(p.y, fr.dh[1], p.x * fr.dh[0]));
+    float pad = fmaf(tp.pad_rel, fabsf(p.x) + fabsf(p.y) + fabsf(p.z), tp.pad_abs);
+    float xlo = p1 - pad, xhi = p1 + pad, ylo = p2 - pad, yhi = p2 + pad, zlo = p3 - pad;
+    __shared__ int s_pair[256 / 32][64];
+    __shared__ int s_acc[256 / 32][32];
+    __shared__ unsigned s_uns[256 / 32];
+    int *pairs = s_pair[w];
+    s_acc[w][lane] = 0;
+    if (lane == 0) s_uns[w] = 0u;
+    __syncwarp();
+    auto flush = [&](int n) -> int {            // as in traverse_packet_kernel
+        int m = n < 32 ? n : 32;
+        int pr = lane < m ? pairs[lane] : -1;
+        int ql = pr >= 0 ? (pr & 31) : lane;
+        float qx = __shfl_sync(FULL, p.x, ql), qy = __shfl_sync(FULL, p.y, ql), qz = __shfl_sync(FULL, p.z, ql);
+        int qi = __shfl_sync(FULL, (int)idx, ql);
+        if (pr >= 0) {
+            int t = pr >> 5;
+            float4 a = __ldg(&tris[3 * t]), b = __ldg(&tris[3 * t + 1]), c = __ldg(&tris[3 * t + 2]);
+            bool uns = false;
+            int r = tri_crossing_fast(make_float3(a.x, a.y, a.z), make_float3(b.x, b.y, b.z),
+                                      make_float3(c.x, c.y, c.z), make_float3(qx, qy, qz), D, uns);
+            if (r) atomicAdd(&s_acc[w][ql], r);
+            if (uns) {
+                bool whole = false;
+                defer_pair(tpairs, tpair_count, qi, t, whole);
+                if (whole) atomicOr(&s_uns[w], 1u << ql);
+            }
+        }
+        int rem = n - m;
+        __syncwarp();
+        int moved = lane < rem ? pairs[m + lane] : 0;
+        __syncwarp();
+        if (lane < rem) pairs[lane] = moved;
+        __syncwarp();
+        return rem;
+    };
+    // the query's bin range; a ray box outside every triangle box has nothing to test
+    bool live = valid && xlo <= bp.x1 && xhi >= bp.x0 && ylo <= bp.y1 && yhi >= bp.y0;
+    const int qbx0 = bin_of(xlo, bp.x0, bp.invx, bp.nbx), qbx1 = bin_of(xhi, bp.x0, bp.invx, bp.nbx);
+    const int qby0 = bin_of(ylo, bp.y0, bp.invy, bp.nby), qby1 = bin_of(yhi, bp.y0, bp.invy, bp.nby);
+    const bool multi = qbx0 != qbx1 || qby0 != qby1;
+    int bx = qbx0 - 1, by = qby0, i = 0, e = 0;
+    auto settle = [&]() {                       // on to the next non-empty bin of the range
+        while (live && i >= e) {
+            if (++bx > qbx1) {
+                bx = qbx0;
+                if (++by > qby1) { live = false; break; }
+            }
+            int b = by * bp.nbx + bx;
+            i = __ldg(&bin_start[b]);
+            e = __ldg(&bin_start[b + 1]);
+        }
+    };
+    settle();
+    int ntests = 0, npairs = 0;                 // npairs: warp-uniform
+    while (__any_sync(FULL, live)) {
+        bool hit = false;
+        int t = 0;
+        if (live) {
+            float2 zt = __ldg(&bin_zt[i]);
+            if (zt.x < zlo) {
+                i = e;                          // the rest of this bin lies behind the query
+            } else {
+                float4 bb = __ldg(&bin_box[i]);
+                hit = box_hit(bb.x, bb.y, bb.z, bb.w, zt.x, xlo, xhi, ylo, yhi, zlo);
+                if (hit && multi)
+                    hit = max(bin_of(bb.x, bp.x0, bp.invx, bp.nbx), qbx0) == bx &&
+                          max(bin_of(bb.z, bp.y0, bp.invy, bp.nby), qby0) == by;
+                t = __float_as_int(zt.y);
+                i++;
+            }
+            settle();
+        }
+        unsigned m = __ballot_sync(FULL, hit);
+        if (m) {
+            if (hit) pairs[npairs + __popc(m & ((1u << lane) - 1u))] = (t << 5) | lane;
+            npairs += __popc(m);
+            ntests += hit;
+            __syncwarp();
+            if (npairs >= 32) npairs = flush(npairs);
+        }
+    }
+    while (npairs > 0) npairs = flush(npairs);
+    __syncwarp();
+    int acc = s_acc[w][lane];
+    bool unsure = (s_uns[w] >> lane) & 1u;
+    if (valid) {
+        if (unsure) defer_query(defer, defer_count, idx);
+        else chi[idx] = acc;
+    }
+    if (cnt) {                                   // statistics: one atomic per block
+        __shared__ unsigned s_tests;
+        if (threadIdx.x == 0) s_tests = 0;
+        __syncthreads();
+        atomicAdd(&s_tests, (unsigned)ntests);
+        __syncthreads();
+        if (threadIdx.x == 0) atomicAdd(&cnt[CNT_TRI_TESTS], (unsigned long long)s_tests);
+    }
+}
+
 // Ray reuse for grid queries when d is parallel to grid axis k: every
 // query on a grid line along k shares the ray line (the "Optimization" of
 // the one-shot algorithm, in 3D).  For an edge AB,
@@ -564,7 +693,7 @@ size_t traverse_lines_bytes(const MeshBvh &b, const QuerySrc &q) {
 
 cudaError_t launch_traverse(const MeshBvh &b, const QuerySrc &q, int32_t *chi, int32_t *defer,
                             int32_t *defer_count, int2 *pairs, int32_t *pair_count, int32_t *lines,
-                            unsigned long long *cnt, int *status, int sm_count, cudaStream_t st) {
+                            unsigned long long *cnt, int *status, int sm_count, cudaStream_t st, bool use_bins) {
     if (q.n == 0) return cudaSuccess;
     if (q.n > 0x7fffffff) return cudaErrorInvalidValue;
     const int threads = 128;
@@ -609,6 +738,15 @@ cudaError_t launch_traverse(const MeshBvh &b, const QuerySrc &q, int32_t *chi, i
         lines_count_kernel<<<(unsigned)((q.n + 255) / 256), 256, 0, st>>>(b.tris, b.frame, q, axis, lines, chi,
                                                                            defer, defer_count, pairs, pair_count,
                                                                            cnt, status);
+    } else if (use_bins && b.n_bin_entries > 0 && b.n < (int64_t(1) << 26)) {
+        if (q.kind == GWN_QUERY_GRID)
+            chi_bins_kernel<true><<<(unsigned)tblocks, 256, 0, st>>>(b.bin_start, b.bin_zt, b.bin_box, b.bins, b.tris,
+                                                                     b.frame, tp, q, chi, defer, defer_count, pairs,
+                                                                     pair_count, cnt);
+        else
+            chi_bins_kernel<false><<<(unsigned)tblocks, 256, 0, st>>>(b.bin_start, b.bin_zt, b.bin_box, b.bins,
+                                                                      b.tris, b.frame, tp, q, chi, defer, defer_count,
+                                                                      pairs, pair_count, cnt);
     } else if (q.kind == GWN_QUERY_GRID && b.tbox && b.n < (int64_t(1) << 26))
         traverse_packet_kernel<<<(unsigned)tblocks, 256, 0, st>>>(b.nodes, b.tris, b.tbox, b.root, b.frame, tp, q,
                                                                   chi, defer, defer_count, pairs, pair_count, cnt,

@@ -302,6 +302,56 @@ def test_device_boundary_extraction(gwn, ctx, name):
     ctx.check()
 
 
+@pytest.mark.parametrize("case", ["cap_grid", "cap_points", "lattice_soup", "torus_points", "heightfield_grid"])
+def test_bins_equal_tree(gwn, ctx, case):
+    """The 2D bin index (built by the first evaluation with at least 4 queries
+    per triangle) and the LBVH traversal test the same (query, triangle)
+    pairs: crossing counts and w are identical, grid and point queries,
+    including a lattice soup whose rays pass through vertices and edges and
+    whose query boxes straddle bin boundaries."""
+    import torch
+    rng = np.random.default_rng(5)
+    d = gen.random_direction(9)
+    if case.startswith("cap"):
+        m = gen.icosphere_cap(subdiv=5, grid_n=72, seed=3)
+        V, F, d = m.V, m.F, m.d
+        q = gwn.Grid(m.grid.lo, m.grid.hi, m.grid.dims) if case == "cap_grid" else \
+            gwn.Points(torch.as_tensor(gen.grid_points(m.grid)[::3].copy()).cuda())
+    elif case == "lattice_soup":
+        # triangles inside the cells of an 11^3 lattice; d = (1, 2, 3) maps
+        # lattice points to lattice points, so rays from the lattice queries
+        # pass through vertices
+        L = np.stack(np.meshgrid(*(np.arange(11.0),) * 3, indexing="ij"), -1).reshape(-1, 3)
+        V = (L / 10.0).astype(np.float32)
+        c = rng.integers(0, 10, (900, 3))
+        steps = np.array([[1, 0, 0], [0, 1, 0], [0, 0, 1], [1, 1, 0], [1, 0, 1], [0, 1, 1], [1, 1, 1]])
+        a, b = steps[rng.integers(0, 7, 900)], steps[rng.integers(0, 7, 900)]
+        cid = lambda x: (x[:, 0] * 11 + x[:, 1]) * 11 + x[:, 2]
+        F = np.stack([cid(c), cid(c + a), cid(c + b)], 1).astype(np.int32)
+        F = np.concatenate([F, F[:50], F[:20, [0, 2, 1]]])
+        d = np.array([1.0, 2.0, 3.0], np.float32)
+        P = np.concatenate([V, (rng.integers(0, 21, (6000, 3)) / 20.0).astype(np.float32)])
+        q = gwn.Points(torch.as_tensor(P).cuda())
+    elif case == "torus_points":
+        m = gen.slit_torus(n_u=96, n_v=64, n_queries=60000, seed=2)
+        V, F, d = m.V, m.F, m.d
+        q = gwn.Points(torch.as_tensor(m.points).cuda())
+    else:
+        m = gen.holey_heightfield(n=160, n_holes=5, grid_n=64, seed=4)
+        V, F, d = m.V, m.F, m.d
+        q = gwn.Grid(m.grid.lo, m.grid.hi, m.grid.dims)
+    mesh = gwn.Mesh(ctx, V, F)
+    r_auto = mesh.eval(q, d, want_chi=True)
+    info = mesh.info()
+    mesh.set_index("tree")
+    r_tree = mesh.eval(q, d, want_chi=True)
+    torch.cuda.synchronize()
+    ctx.check()
+    assert info["n_bins"] > 0 and info["n_bin_entries"] >= len(F) - 100 and info["bin_maxlen"] > 0
+    assert torch.equal(r_auto["chi"], r_tree["chi"])
+    assert torch.equal(r_auto["w"], r_tree["w"])
+
+
 def test_bruteforce_comparator(gwn, ctx):
     m = gen.icosphere_cap(subdiv=3, grid_n=16, seed=1)
     mesh = gwn.Mesh(ctx, m.V, m.F)
