@@ -239,6 +239,18 @@ class Mesh(_Geom):
             res["stats"] = st.as_dict()
         return res if (want_chi or want_b or stats) else w
 
+    def inside(self, queries, d, out=None):
+        """Inside test (voxelization): uint8 tensor, 1 where w >= 0.5."""
+        torch = _torch()
+        if not isinstance(queries, (Grid, Points)):
+            queries = Points(queries)
+        qc = queries.to_c(F32)
+        n = queries.n
+        r = out if out is not None else torch.empty(n, dtype=torch.uint8, device=torch.device("cuda", self.ctx.device))
+        dd, dp = _dir(d)
+        check(self.lib.gwn_eval_inside(self.h, C.byref(qc), dp, r.data_ptr() if n else None), "gwn_eval_inside")
+        return r
+
     def eval_host(self, queries, d, out=None):
         """End-to-end entry point: host queries in, host w out.  out: an
         optional host float32 buffer of n entries (numpy array or CPU tensor;
@@ -316,6 +328,9 @@ class Patches(_Geom):
 
     def eval_host(self, queries, d, out=None):
         return Mesh.eval_host(self, queries, d, out=out)
+
+    def inside(self, queries, d, out=None):
+        return Mesh.inside(self, queries, d, out=out)
 
 
 class Bezier2D(_Geom):

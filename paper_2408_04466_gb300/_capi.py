@@ -69,6 +69,7 @@ _SIGS = {
     "gwn_bezier_monotone_split_host": (ST, [P, P, C.POINTER(I32)]),
     "gwn_eval": (ST, [P, C.POINTER(gwn_queries), P, P, P, P, C.POINTER(gwn_stats)]),
     "gwn_eval_host": (ST, [P, C.POINTER(gwn_queries), P, P]),
+    "gwn_eval_inside": (ST, [P, C.POINTER(gwn_queries), P, P]),
     "gwn_eval_batch": (ST, [P, C.POINTER(gwn_queries), I64, P, P, C.POINTER(gwn_plan), C.POINTER(gwn_stats)]),
     "gwn_batch_plan_get": (ST, [P, C.POINTER(I32), C.POINTER(I32)]),
     "gwn_backward": (ST, [P, C.POINTER(gwn_queries), P, P, P, P]),

@@ -1001,8 +1001,8 @@ static gwn_status read_stats(gwn_ctx *ctx, gwn_stats *st, int64_t nq, int64_t pa
 
 extern "C" {
 
-GWN_API gwn_status gwn_eval(gwn_geom *g, const gwn_queries *q, const float *d, void *w_out, int32_t *chi_out,
-                            void *b_out, gwn_stats *stats) {
+static gwn_status eval_impl(gwn_geom *g, const gwn_queries *q, const float *d, void *w_out, int32_t *chi_out,
+                            void *b_out, uint8_t *inside_out, gwn_stats *stats) {
     if (!g) { set_error("gwn_eval: NULL geometry"); return GWN_E_INVALID; }
     gwn_ctx *ctx = g->ctx;
     CK(cudaSetDevice(ctx->device), "cudaSetDevice");
@@ -1012,7 +1012,10 @@ GWN_API gwn_status gwn_eval(gwn_geom *g, const gwn_queries *q, const float *d, v
         if (q->kind == GWN_QUERY_POINTS && q->dtype != GWN_F32) { set_error("gwn_eval: mesh queries are float32"); return GWN_E_INVALID; }
         if (!d) { set_error("gwn_eval: mesh evaluation needs a direction"); return GWN_E_INVALID; }
         int64_t nq = query_count(q);
-        if (nq > 0 && !w_out && !chi_out && !b_out) { set_error("gwn_eval: no output requested"); return GWN_E_INVALID; }
+        if (nq > 0 && !w_out && !chi_out && !b_out && !inside_out) {
+            set_error("gwn_eval: no output requested");
+            return GWN_E_INVALID;
+        }
         if (stats) {
             CK(cudaMemsetAsync(ctx->d_cnt, 0, sizeof(unsigned long long) * CNT_NUM, ctx->stream), "clear counters");
             CK(cudaEventRecord(ctx->ev[0], ctx->stream), "event");
@@ -1050,7 +1053,7 @@ GWN_API gwn_status gwn_eval(gwn_geom *g, const gwn_queries *q, const float *d, v
         if (stats) CK(cudaEventRecord(ctx->ev[2], ctx->stream), "event");
         e = launch_bterm3d(g->bseq, g->bvh.bframe, g->n_bseq, g->bvh.frame, make_frame64(d), src, chi, (float *)w_out,
                            (float *)b_out, defer, ctx->d_defer_count, stats ? ctx->d_cnt : nullptr, ctx->d_status,
-                           ctx->sm_count, ctx->stream);
+                           ctx->sm_count, ctx->stream, inside_out);
         if (e != cudaSuccess) return cuda_fail(e, "boundary term");
         if (stats) CK(cudaEventRecord(ctx->ev[3], ctx->stream), "event");
         int64_t edges = (int64_t)g->loop_vid.size();
@@ -1062,7 +1065,10 @@ GWN_API gwn_status gwn_eval(gwn_geom *g, const gwn_queries *q, const float *d, v
         if (q->kind == GWN_QUERY_POINTS && q->dtype != GWN_F32) { set_error("gwn_eval: patch queries are float32"); return GWN_E_INVALID; }
         if (!d) { set_error("gwn_eval: patch evaluation needs a direction"); return GWN_E_INVALID; }
         int64_t nq = query_count(q);
-        if (nq > 0 && !w_out && !chi_out && !b_out) { set_error("gwn_eval: no output requested"); return GWN_E_INVALID; }
+        if (nq > 0 && !w_out && !chi_out && !b_out && !inside_out) {
+            set_error("gwn_eval: no output requested");
+            return GWN_E_INVALID;
+        }
         if (stats) {
             CK(cudaMemsetAsync(ctx->d_cnt, 0, sizeof(unsigned long long) * CNT_NUM, ctx->stream), "clear counters");
             CK(cudaEventRecord(ctx->ev[0], ctx->stream), "event");
@@ -1088,7 +1094,7 @@ GWN_API gwn_status gwn_eval(gwn_geom *g, const gwn_queries *q, const float *d, v
         if (stats) CK(cudaEventRecord(ctx->ev[2], ctx->stream), "event");
         e = launch_bterm3d(g->bseq, g->ps.bframe, g->n_bseq, g->ps.frame, make_frame64(d), src, chi, (float *)w_out,
                            (float *)b_out, defer, ctx->d_defer_count, stats ? ctx->d_cnt : nullptr, ctx->d_status,
-                           ctx->sm_count, ctx->stream);
+                           ctx->sm_count, ctx->stream, inside_out);
         if (e != cudaSuccess) return cuda_fail(e, "boundary term");
         if (stats) CK(cudaEventRecord(ctx->ev[3], ctx->stream), "event");
         return read_stats(ctx, stats, nq, nq * (int64_t)g->loop_vid.size(), prepared);
@@ -1125,6 +1131,21 @@ GWN_API gwn_status gwn_eval(gwn_geom *g, const gwn_queries *q, const float *d, v
     }
     set_error("gwn_eval: unknown geometry kind");
     return GWN_E_INVALID;
+}
+
+GWN_API gwn_status gwn_eval(gwn_geom *g, const gwn_queries *q, const float *d, void *w_out, int32_t *chi_out,
+                            void *b_out, gwn_stats *stats) {
+    return eval_impl(g, q, d, w_out, chi_out, b_out, nullptr, stats);
+}
+
+GWN_API gwn_status gwn_eval_inside(gwn_geom *g, const gwn_queries *q, const float *d, uint8_t *inside_out) {
+    if (!g || !q) { set_error("gwn_eval_inside: NULL argument"); return GWN_E_INVALID; }
+    if (g->kind != GWN_GEOM_MESH && g->kind != GWN_GEOM_PATCHES) {
+        set_error("gwn_eval_inside: meshes and patch surfaces only");
+        return GWN_E_UNSUPPORTED;
+    }
+    if (query_count(q) > 0 && !inside_out) { set_error("gwn_eval_inside: NULL output"); return GWN_E_INVALID; }
+    return eval_impl(g, q, d, nullptr, nullptr, nullptr, inside_out, nullptr);
 }
 
 GWN_API gwn_status gwn_eval_host(gwn_geom *g, const gwn_queries *q, const float *d, void *w_host) {

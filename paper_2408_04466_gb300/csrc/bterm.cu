@@ -347,6 +347,7 @@ __global__ void __launch_bounds__(256, MINB) bterm3d_kernel(const float4 *__rest
                                                             const __grid_constant__ PackedConsts Kp, QuerySrc q,
                                                             const int32_t *__restrict__ chi,
                                                             float *__restrict__ w_out, float *__restrict__ b_out,
+                                                            uint8_t *__restrict__ in_out,
                                                             int32_t *__restrict__ defer, int32_t *defer_count) {
     const int64_t base = (int64_t)blockIdx.x * blockDim.x * (2 * KP) + threadIdx.x;
     const PackedConsts K = Kp;           // materialised in registers once per thread
@@ -393,8 +394,10 @@ __global__ void __launch_bounds__(256, MINB) bterm3d_kernel(const float4 *__rest
                     int slot = atomicAdd(defer_count, 1);       // < q.n: one slot per query at most
                     defer[slot] = (int32_t)idx;
                 } else {
+                    float wv = Bv[h] + (chi ? (float)chi[idx] : 0.f);
                     if (b_out) b_out[idx] = Bv[h];
-                    if (w_out) w_out[idx] = Bv[h] + (chi ? (float)chi[idx] : 0.f);
+                    if (w_out) w_out[idx] = wv;
+                    if (in_out) in_out[idx] = wv >= 0.5f ? 1 : 0;   // inside test (voxelization)
                 }
             }
         }
@@ -478,7 +481,7 @@ __device__ __forceinline__ float edge_theta_careful(const VState1 &A, const VSta
 // its two edges.  The lanes' compensated sums are combined by a TwoSum tree.
 __global__ void __launch_bounds__(128) bterm3d_careful_kernel(const float4 *__restrict__ bseq, int nb, Frame fr,
                                                               Frame64 f64, QuerySrc q, const int32_t *chi,
-                                                              float *w_out, float *b_out,
+                                                              float *w_out, float *b_out, uint8_t *in_out,
                                                               const int32_t *__restrict__ defer,
                                                               const int32_t *defer_count, unsigned long long *cnt,
                                                               int *status) {
@@ -525,8 +528,10 @@ __global__ void __launch_bounds__(128) bterm3d_careful_kernel(const float4 *__re
         }
         if (lane == 0) {
             float Bv = (s + e) * GWN_INV_2PI;
+            float wv = Bv + (chi ? (float)chi[idx] : 0.f);
             if (b_out) b_out[idx] = Bv;
-            if (w_out) w_out[idx] = Bv + (chi ? (float)chi[idx] : 0.f);
+            if (w_out) w_out[idx] = wv;
+            if (in_out) in_out[idx] = wv >= 0.5f ? 1 : 0;
         }
     }
 }
@@ -534,8 +539,8 @@ __global__ void __launch_bounds__(128) bterm3d_careful_kernel(const float4 *__re
 template <int KP, int MINB>
 static cudaError_t launch_bt(const float4 *bseq, const float4 *bframe, int64_t n_bseq, const Frame &fr,
                              const Frame64 &f64, const QuerySrc &q, const int32_t *chi, float *w_out, float *b_out,
-                             int32_t *defer, int32_t *defer_count, unsigned long long *cnt, int *status,
-                             int sm_count, cudaStream_t st) {
+                             uint8_t *in_out, int32_t *defer, int32_t *defer_count, unsigned long long *cnt,
+                             int *status, int sm_count, cudaStream_t st) {
     const int threads = 256;
     int64_t per_block = (int64_t)threads * 2 * KP;
     int64_t blocks = (q.n + per_block - 1) / per_block;
@@ -551,25 +556,25 @@ static cudaError_t launch_bt(const float4 *bseq, const float4 *bframe, int64_t n
     cudaError_t e = cudaMemsetAsync(defer_count, 0, sizeof(int32_t), st);
     if (e != cudaSuccess) return e;
     bterm3d_kernel<KP, MINB><<<(unsigned)blocks, threads, 0, st>>>(bframe, (int)n_bseq, fr, K, q, chi, w_out, b_out,
-                                                                   defer, defer_count);
+                                                                   in_out, defer, defer_count);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     // deferred queries (a fraction of a percent): persistent grid over the list
     int cblocks = (sm_count > 0 ? sm_count : 152) * 4;
-    bterm3d_careful_kernel<<<cblocks, 128, 0, st>>>(bseq, (int)n_bseq, fr, f64, q, chi, w_out, b_out, defer,
-                                                    defer_count, cnt, status);
+    bterm3d_careful_kernel<<<cblocks, 128, 0, st>>>(bseq, (int)n_bseq, fr, f64, q, chi, w_out, b_out, in_out,
+                                                    defer, defer_count, cnt, status);
     return cudaGetLastError();
 }
 
 cudaError_t launch_bterm3d(const float4 *bseq, const float4 *bframe, int64_t n_bseq, const Frame &fr,
                            const Frame64 &f64, const QuerySrc &q, const int32_t *chi, float *w_out, float *b_out,
                            int32_t *defer, int32_t *defer_count, unsigned long long *cnt, int *status, int sm_count,
-                           cudaStream_t st) {
+                           cudaStream_t st, uint8_t *inside_out) {
     if (q.n == 0) return cudaSuccess;
     // Two query pairs per thread at two blocks per SM: the fastest of the
     // (pairs, blocks) shapes measured for 16.8M queries x 252 boundary edges.
-    return launch_bt<2, 2>(bseq, bframe, n_bseq, fr, f64, q, chi, w_out, b_out, defer, defer_count, cnt, status,
-                           sm_count, st);
+    return launch_bt<2, 2>(bseq, bframe, n_bseq, fr, f64, q, chi, w_out, b_out, inside_out, defer, defer_count, cnt,
+                           status, sm_count, st);
 }
 
 }  // namespace gwn

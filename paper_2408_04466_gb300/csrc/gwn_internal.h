@@ -287,12 +287,13 @@ cudaError_t launch_traverse(const MeshBvh &b, const QuerySrc &q, int32_t *chi, i
                             int32_t *defer_count, int2 *pairs, int32_t *pair_count, int32_t *lines,
                             unsigned long long *cnt, int *status, int sm_count, cudaStream_t st, bool use_bins = true);
 
-// Boundary term + epilogue (w = chi + B).  defer: int32 scratch of q.n
-// entries for the deferred-query list; defer_count: one device int32.
+// Boundary term + epilogue (w = chi + B; inside_out, when given, gets
+// w >= 0.5 as one byte per query).  defer: int32 scratch of q.n entries for
+// the deferred-query list; defer_count: one device int32.
 cudaError_t launch_bterm3d(const float4 *bseq, const float4 *bframe, int64_t n_bseq, const Frame &fr,
                            const Frame64 &f64, const QuerySrc &q, const int32_t *chi, float *w_out, float *b_out,
                            int32_t *defer, int32_t *defer_count, unsigned long long *cnt, int *status, int sm_count,
-                           cudaStream_t st);
+                           cudaStream_t st, uint8_t *inside_out = nullptr);
 // Boundary records in the frame of d (double-float), 2 float4 per record.
 cudaError_t launch_bframe(const float4 *bseq, int64_t n, const Frame &fr, float4 *out, cudaStream_t st);
 

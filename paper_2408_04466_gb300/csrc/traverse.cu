@@ -367,7 +367,7 @@ __global__ void __launch_bounds__(256) traverse_packet_kernel(const BvhNode *__r
 // traverse_packet_kernel.  GRID: warp tiles of the grid; otherwise one point
 // per thread.  Requires fewer than 2^26 triangles.
 template <bool GRID>
-__global__ void __launch_bounds__(256) chi_bins_kernel(const int32_t *__restrict__ bin_start,
+__global__ void __launch_bounds__(256, 5) chi_bins_kernel(const int32_t *__restrict__ bin_start,
                                                        const float2 *__restrict__ bin_zt,
                                                        const float4 *__restrict__ bin_box, BinParams bp,
                                                        const float4 *__restrict__ tris, Frame fr, TravParams tp,

@@ -352,6 +352,45 @@ def test_bins_equal_tree(gwn, ctx, case):
     assert torch.equal(r_auto["w"], r_tree["w"])
 
 
+def test_inside_voxelization(gwn, ctx):
+    """The inside test (w >= 1/2) fused into the boundary term: bit-exact
+    against the float32 w of the same path, and equal to the FP64 oracle's
+    decision wherever the oracle's w is more than 1e-5 from the threshold."""
+    import torch
+    m = gen.icosphere_cap(subdiv=3, grid_n=20, seed=6)
+    mesh = gwn.Mesh(ctx, m.V, m.F)
+    g = gwn.Grid(m.grid.lo, m.grid.hi, m.grid.dims)
+    w = mesh.eval(g, m.d)
+    ins = mesh.inside(g, m.d)
+    torch.cuda.synchronize()
+    ctx.check()
+    assert ins.dtype == torch.uint8
+    assert torch.equal(ins, (w >= 0.5).to(torch.uint8))
+    P = gen.grid_points(m.grid)
+    wo, _, _ = oracle.w3d_oneshot(m.V, m.F, P, m.d)
+    far = np.abs(wo - 0.5) > 1e-5
+    assert np.array_equal(ins.cpu().numpy()[far], (wo[far] >= 0.5).astype(np.uint8))
+    assert 0 < int(ins.sum()) < g.n
+    # closed surface: inside exactly where w = 1
+    V, F = gen.icosphere(3)
+    closed = gwn.Mesh(ctx, V.astype(np.float32), F.astype(np.int32))
+    Pq = (np.random.default_rng(1).random((5000, 3)) * 2.6 - 1.3).astype(np.float32)
+    r = np.linalg.norm(Pq.astype(np.float64), axis=1)
+    keep = np.abs(r - 1.0) > 0.05
+    ci = closed.inside(gwn.Points(torch.as_tensor(Pq).cuda()), m.d).cpu().numpy()
+    assert np.array_equal(ci[keep], (r[keep] < 1.0).astype(np.uint8))
+    # patch surfaces take the same epilogue; 2D chains are not supported
+    pc = gen.patch_spheroid(n=2, amp=0.08, seed=1)
+    ps = gwn.Patches(ctx, pc.ctrl, segments=16)
+    gp = gwn.Grid((-1.3,) * 3, (1.3,) * 3, (12, 12, 12))
+    assert torch.equal(ps.inside(gp, pc.d), (ps.eval(gp, pc.d) >= 0.5).to(torch.uint8))
+    ch = gen.bezier_circle_chain(n_seg=8, grid_n=8)
+    geo = gwn.Bezier2D(ctx, ch.ctrl, ch.offsets)
+    with pytest.raises(gwn.GwnError):
+        gwn.Mesh.inside(geo, gwn.Grid(ch.grids[0].lo, ch.grids[0].hi, ch.grids[0].dims), [1, 0, 0])
+    ctx.check()
+
+
 def test_bruteforce_comparator(gwn, ctx):
     m = gen.icosphere_cap(subdiv=3, grid_n=16, seed=1)
     mesh = gwn.Mesh(ctx, m.V, m.F)
