@@ -245,8 +245,9 @@ GWN_API gwn_status gwn_bezier_monotone_split_host(const double ctrl[8], double u
 GWN_API gwn_status gwn_eval(gwn_geom *g, const gwn_queries *q, const float *d, void *w_out,
                             int32_t *chi_out, void *b_out, gwn_stats *stats);
 
-/* Inside test (voxelization, the w >= 1/2 threshold of the paper's
- * applications): inside_out[i] = 1 if the float32 w(q_i) of gwn_eval is
+/* Inside test (voxelization: the paper's voxel figure in Sec. Curve Networks
+ * marks winding number 1 occupied and 0 empty; the threshold taken is the
+ * midpoint): inside_out[i] = 1 if the float32 w(q_i) of gwn_eval is
  * >= 0.5, else 0; uint8, device memory, one byte per query, written by the
  * boundary-term kernels in place of w (no float w array is stored).  Meshes
  * and patch surfaces; GWN_E_UNSUPPORTED for 2D chains.  Asynchronous like
