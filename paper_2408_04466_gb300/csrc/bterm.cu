@@ -474,33 +474,34 @@ __device__ __forceinline__ float edge_theta_careful(const VState1 &A, const VSta
     return th;
 }
 
-// One warp per deferred query: lane l sums the edges ending at records
-// [k0, k1), a contiguous run of about (nb - 1)/32 records, starting from the
-// projection of record k0 - 1.  A vertex on a run boundary is projected by
-// both lanes with the same arithmetic, so its rounding still cancels between
-// its two edges.  The lanes' compensated sums are combined by a TwoSum tree.
+// One block of 128 threads per deferred query: thread l sums the edges
+// ending at records [k0, k1), a contiguous run of about (nb - 1)/128
+// records, starting from the projection of record k0 - 1.  A vertex on a run
+// boundary is projected by both threads with the same arithmetic, so its
+// rounding still cancels between its two edges.  The threads' compensated
+// sums are combined by a TwoSum tree in a fixed order (warp shuffles, then
+// the four warps in turn).
 __global__ void __launch_bounds__(128) bterm3d_careful_kernel(const float4 *__restrict__ bseq, int nb, Frame fr,
                                                               Frame64 f64, QuerySrc q, const int32_t *chi,
                                                               float *w_out, float *b_out, uint8_t *in_out,
                                                               const int32_t *__restrict__ defer,
                                                               const int32_t *defer_count, unsigned long long *cnt,
                                                               int *status) {
-    const int lane = threadIdx.x & 31;
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __shared__ float s_part[2][128 / 32];
     int64_t n = *defer_count;
     if (n > q.n) n = q.n;
     if (cnt && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&cnt[CNT_DEFER_BTERM], (unsigned long long)n);
-    const int per = nb > 1 ? (nb - 1 + 31) / 32 : 0;
-    for (int64_t i = warp; i < n; i += nwarps) {
+    const int per = nb > 1 ? (nb - 1 + 127) / 128 : 0;
+    for (int64_t i = blockIdx.x; i < n; i += gridDim.x) {   // block-uniform loop
         int64_t idx = defer[i];
         if (idx < 0 || idx >= q.n) {
-            if (lane == 0) atomicOr(status, ST_BAD_INPUT);
+            if (threadIdx.x == 0) atomicOr(status, ST_BAD_INPUT);
             continue;
         }
         float3 p = query_point3(q, idx);
         float sum = 0.f, cmp = 0.f;
-        int k0 = 1 + lane * per, k1 = k0 + per < nb ? k0 + per : nb;
+        int k0 = 1 + threadIdx.x * per, k1 = k0 + per < nb ? k0 + per : nb;
         if (k0 < k1) {
             float4 vp = __ldg(&bseq[k0 - 1]);
             VState1 A = project1(vp, p, fr);
@@ -518,7 +519,8 @@ __global__ void __launch_bounds__(128) bterm3d_careful_kernel(const float4 *__re
                 vp = v;
             }
         }
-        // combine (value, error) pairs across the warp with TwoSum
+        // combine (value, error) pairs across the warp, then across the
+        // block's warps in fixed order, with TwoSum
         float s = sum, e = -cmp;
         for (int off = 16; off > 0; off >>= 1) {
             float s2 = __shfl_down_sync(0xffffffffu, s, off), e2 = __shfl_down_sync(0xffffffffu, e, off);
@@ -526,13 +528,22 @@ __global__ void __launch_bounds__(128) bterm3d_careful_kernel(const float4 *__re
             s = t;
             e = e + e2 + err;
         }
-        if (lane == 0) {
+        if (lane == 0) { s_part[0][wid] = s; s_part[1][wid] = e; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int w = 1; w < 128 / 32; w++) {
+                float s2 = s_part[0][w], e2 = s_part[1][w];
+                float t = s + s2, bv = t - s, err = (s - (t - bv)) + (s2 - bv);
+                s = t;
+                e = e + e2 + err;
+            }
             float Bv = (s + e) * GWN_INV_2PI;
             float wv = Bv + (chi ? (float)chi[idx] : 0.f);
             if (b_out) b_out[idx] = Bv;
             if (w_out) w_out[idx] = wv;
             if (in_out) in_out[idx] = wv >= 0.5f ? 1 : 0;
         }
+        __syncthreads();
     }
 }
 
