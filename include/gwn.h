@@ -167,9 +167,11 @@ GWN_API gwn_status gwn_mesh_create(gwn_ctx *ctx, const float *V, int64_t nv, con
 
 /* Crossing index of a mesh.  All rays share d, so the crossing search is a
  * 2D point location in the plane normal to d plus a depth test.  AUTO (the
- * default): an evaluation with at least 4 queries per triangle (and d not
- * parallel to a grid axis of grid queries, which reuse rays per grid line)
- * builds once, besides the LBVH, a bin grid over the projected triangle boxes
+ * default): once the evaluations of a (mesh, d) have asked for at least 4
+ * queries per triangle in total (grid queries with d parallel to a grid axis,
+ * which reuse rays per grid line, do not count), the evaluation reaching
+ * that total builds once, besides the LBVH, a bin grid over the projected
+ * triangle boxes
  * (lists by decreasing depth) and uses it when it is compact (at most 12
  * entries per triangle + 4096; no list longer than both 512 and 64 times the
  * mean); TREE always uses the LBVH traversal.  Both test exactly the same

@@ -1040,8 +1040,10 @@ static gwn_status eval_impl(gwn_geom *g, const gwn_queries *q, const float *d, v
         if (lbytes) {
             lines = (int32_t *)arena_get(ctx, 5, lbytes, &e);
             if (!lines) return cuda_fail(e, "per-line crossing lists");
-        } else if (g->crossing_index == GWN_INDEX_AUTO && !g->bvh.bins_tried && nq >= 4 * g->nf) {
-            // enough queries per triangle for the 2D bins to repay their build
+        } else if (g->crossing_index == GWN_INDEX_AUTO && !g->bvh.bins_tried &&
+                   (g->bvh.queries_seen += nq) >= 4 * g->nf) {
+            // enough queries per triangle, over the evaluations of this
+            // (mesh, d), for the 2D bins to repay their build
             e = bins_build(g, ctx->stream);
             if (e != cudaSuccess) return cuda_fail(e, "crossing bins");
         }

@@ -614,6 +614,7 @@ void bvh_free(MeshBvh &b) {
     b.tris = nullptr;
     bins_free(b);
     b.bins_tried = false;
+    b.queries_seen = 0;
     b.valid = false;
 }
 

@@ -93,6 +93,7 @@ struct MeshBvh {
     // is used): bin b = j * nbx + i lists entries [bin_start[b],
     // bin_start[b + 1]) by decreasing zmax
     bool bins_tried = false;
+    int64_t queries_seen = 0;       // queries evaluated since this (mesh, d) was prepared
     void *bin_block = nullptr;      // one allocation holding the three bin arrays
     BinParams bins;
     int64_t n_bin_entries = 0;

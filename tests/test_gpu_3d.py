@@ -304,8 +304,8 @@ def test_device_boundary_extraction(gwn, ctx, name):
 
 @pytest.mark.parametrize("case", ["cap_grid", "cap_points", "lattice_soup", "torus_points", "heightfield_grid"])
 def test_bins_equal_tree(gwn, ctx, case):
-    """The 2D bin index (built by the first evaluation with at least 4 queries
-    per triangle) and the LBVH traversal test the same (query, triangle)
+    """The 2D bin index (built once the evaluations reach 4 queries per
+    triangle) and the LBVH traversal test the same (query, triangle)
     pairs: crossing counts and w are identical, grid and point queries,
     including a lattice soup whose rays pass through vertices and edges and
     whose query boxes straddle bin boundaries."""
@@ -388,6 +388,27 @@ def test_inside_voxelization(gwn, ctx):
     geo = gwn.Bezier2D(ctx, ch.ctrl, ch.offsets)
     with pytest.raises(gwn.GwnError):
         gwn.Mesh.inside(geo, gwn.Grid(ch.grids[0].lo, ch.grids[0].hi, ch.grids[0].dims), [1, 0, 0])
+    ctx.check()
+
+
+def test_bins_built_once_enough_queries(gwn, ctx):
+    """The bins are built by the evaluation at which the queries evaluated on
+    a (mesh, d) reach 4 per triangle; a new direction starts the count again;
+    the crossing counts do not change when they appear."""
+    import torch
+    m = gen.icosphere_cap(subdiv=4, grid_n=8, seed=8)
+    nf = len(m.F)
+    P = torch.as_tensor((np.random.default_rng(2).random((3 * nf, 3)) * 2.4 - 1.2).astype(np.float32)).cuda()
+    mesh = gwn.Mesh(ctx, m.V, m.F)
+    q = gwn.Points(P)
+    c1 = mesh.eval(q, m.d, want_chi=True)["chi"].clone()
+    assert mesh.info()["n_bins"] == 0                         # 3 queries per triangle so far
+    c2 = mesh.eval(q, m.d, want_chi=True)["chi"].clone()
+    assert mesh.info()["n_bins"] > 0                          # 6: built by this call
+    assert torch.equal(c1, c2)
+    d2 = gen.random_direction(77)
+    mesh.eval(q, d2)
+    assert mesh.info()["n_bins"] == 0                         # a new direction: a new count
     ctx.check()
 
 
