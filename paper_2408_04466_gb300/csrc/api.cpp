@@ -427,6 +427,7 @@ static void free_geom_device(gwn_geom *g) {
     if (g->dF) cudaFree(g->dF);
     if (g->bseq) cudaFree(g->bseq);
     if (g->bseq_vid) cudaFree(g->bseq_vid);
+    if (g->d_edge_rec) cudaFree(g->d_edge_rec);
     if (g->d_bvert) cudaFree(g->d_bvert);
     if (g->d_brec_off) cudaFree(g->d_brec_off);
     if (g->d_brecs) cudaFree(g->d_brecs);
@@ -1236,6 +1237,15 @@ static gwn_status ensure_vertex_lists(gwn_geom *g) {
         recs.push_back(vr[i].second);
     }
     off.push_back((int64_t)recs.size());
+    // edge i of loop j ends at record i + j + 1 (each loop's first record
+    // ends no edge)
+    std::vector<int32_t> er(g->loop_vid.size());
+    for (size_t j = 0; j + 1 < g->loop_off.size(); j++)
+        for (int64_t i = g->loop_off[j]; i < g->loop_off[j + 1]; i++) er[i] = (int32_t)(i + (int64_t)j + 1);
+    if (!er.empty()) {
+        CK(cudaMalloc(&g->d_edge_rec, sizeof(int32_t) * er.size()), "edge records");
+        CK(cudaMemcpy(g->d_edge_rec, er.data(), sizeof(int32_t) * er.size(), cudaMemcpyHostToDevice), "edge records");
+    }
     g->n_bvert = (int64_t)bv.size();
     CK(cudaMalloc(&g->d_bvert, sizeof(int32_t) * bv.size()), "vertex lists");
     CK(cudaMalloc(&g->d_brec_off, sizeof(int64_t) * off.size()), "vertex lists");
@@ -1265,16 +1275,17 @@ extern "C" GWN_API gwn_status gwn_backward(gwn_geom *g, const gwn_queries *q, co
         CK(cudaMemsetAsync(grad_V, 0, sizeof(float) * 3 * g->nv, ctx->stream), "clear grad_V");
         s = ensure_vertex_lists(g);
         if (s != GWN_OK) return s;
-        int chunks = grad_v_chunks(nq, g->n_bseq, ctx->sm_count);
+        const int64_t ne = (int64_t)g->loop_vid.size();
+        int chunks = grad_pv_chunks(nq, ne, ctx->sm_count);
         size_t part = (sizeof(float) * 6 * (size_t)chunks * g->n_bseq + 255) & ~(size_t)255;
-        size_t partp = (grad_pv_partial_p_bytes(nq, g->n_bseq) + 255) & ~(size_t)255;
+        size_t partp = (grad_pv_partial_p_bytes(nq, ne) + 255) & ~(size_t)255;
         size_t recb = sizeof(float) * 3 * g->n_bseq;
         cudaError_t e;
         char *buf = (char *)arena_get(ctx, 0, part + partp + recb, &e);
         if (!buf) return cuda_fail(e, "gradient workspace");
-        e = launch_grad_pv(g->bseq, g->n_bseq, src, grad_w, chunks, (float *)buf, (float *)(buf + part),
-                           (float *)(buf + part + partp), g->d_bvert, g->d_brec_off, g->d_brecs, g->n_bvert, grad_p,
-                           grad_V, ctx->stream);
+        e = launch_grad_pv(g->bseq, g->n_bseq, g->d_edge_rec, ne, src, grad_w, chunks, (float *)buf,
+                           (float *)(buf + part), (float *)(buf + part + partp), g->d_bvert, g->d_brec_off,
+                           g->d_brecs, g->n_bvert, grad_p, grad_V, ctx->stream);
         if (e != cudaSuccess) return cuda_fail(e, "gradients");
         return GWN_OK;
     }

@@ -207,18 +207,24 @@ __global__ void __launch_bounds__(GV_THREADS) grad_v_partial_kernel(const float4
 // blocks in order.  Lanes without an edge contribute nothing; queries past
 // the tile's end sit far from the geometry with weight zero.
 __global__ void __launch_bounds__(GV_THREADS) grad_pv_partial_kernel(const float4 *__restrict__ bseq, int nb,
-                                                                     QuerySrc q, const float *__restrict__ grad_w,
+                                                                     const int32_t *__restrict__ edge_rec,
+                                                                     int n_edges, QuerySrc q,
+                                                                     const float *__restrict__ grad_w,
                                                                      int64_t chunk_len, float *__restrict__ partial,
                                                                      float *__restrict__ partial_p) {
     __shared__ float4 qs[GV_QTILE];
     __shared__ float accp[GV_THREADS / 32][3][GV_QTILE];
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int k = blockIdx.x * GV_THREADS + threadIdx.x;
+    // thread t takes edge t, the edge ending at record edge_rec[t] (the
+    // records that start a loop end no edge, so every thread of a full block
+    // has one)
+    const int t = blockIdx.x * GV_THREADS + threadIdx.x;
     int chunk = blockIdx.y;
     int64_t q0 = (int64_t)chunk * chunk_len;
     int64_t q1 = q0 + chunk_len < q.n ? q0 + chunk_len : q.n;
-    bool active = k >= 1 && k < nb;
+    const int k = t < n_edges ? __ldg(&edge_rec[t]) : 0;
+    bool active = t < n_edges && k >= 1 && k < nb;
     float4 A = active ? bseq[k - 1] : make_float4(0.f, 0.f, 0.f, 0.f);
     float4 B = active ? bseq[k] : make_float4(0.f, 0.f, 0.f, 0.f);
     active = active && B.w != 0.f;
@@ -278,7 +284,7 @@ __global__ void __launch_bounds__(GV_THREADS) grad_pv_partial_kernel(const float
                 partial_p[((int64_t)blockIdx.x * 3 + c) * q.n + t0 + i] = v;
             }
     }
-    if (k < nb) {
+    if (active) {
         float *o = partial + ((int64_t)chunk * nb + k) * 6;
         for (int c = 0; c < 3; c++) {
             o[c] = sA2[c].x + sA2[c].y;
@@ -371,19 +377,54 @@ cudaError_t launch_grad_v(const float4 *bseq, int64_t nb, const QuerySrc &q, con
     return cudaGetLastError();
 }
 
-size_t grad_pv_partial_p_bytes(int64_t nq, int64_t nb) {
-    return sizeof(float) * 3 * (size_t)((nb + GV_THREADS - 1) / GV_THREADS) * (size_t)nq;
+size_t grad_pv_partial_p_bytes(int64_t nq, int64_t n_edges) {
+    return sizeof(float) * 3 * (size_t)((n_edges + GV_THREADS - 1) / GV_THREADS) * (size_t)nq;
 }
 
-cudaError_t launch_grad_pv(const float4 *bseq, int64_t nb, const QuerySrc &q, const float *grad_w, int n_chunks,
-                           float *partial, float *partial_p, float *rec_grad, const int32_t *bvert,
-                           const int64_t *rec_off, const int32_t *recs, int64_t n_bvert, float *grad_p, float *grad_V,
-                           cudaStream_t st) {
-    if (nb == 0 || q.n == 0) return cudaSuccess;
+// Query chunks for the fused pass: n_eb edge blocks x chunks blocks, sized to
+// whole waves of the blocks that fit on the GPU at once (every block of a
+// chunk row does the same work), the fewest waves that come within 3% of
+// full, at least 256 queries per chunk.
+int grad_pv_chunks(int64_t nq, int64_t n_edges, int sm_count) {
+    static int per_sm = 0;
+    if (per_sm == 0) {
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, grad_pv_partial_kernel, GV_THREADS, 0) != cudaSuccess ||
+            b < 1) {
+            cudaGetLastError();
+            b = 1;
+        }
+        per_sm = b;
+    }
+    const int64_t n_eb = (n_edges + GV_THREADS - 1) / GV_THREADS;
+    const int64_t cap = (int64_t)(sm_count > 0 ? sm_count : 152) * per_sm;
+    int64_t maxc = (nq + GV_QTILE - 1) / GV_QTILE;
+    if (maxc > 4096) maxc = 4096;
+    if (maxc < 1) maxc = 1;
+    int64_t best = 1;
+    double best_fill = 0.0;
+    for (int64_t w = 1; w <= 8; w++) {
+        int64_t c = w * cap / (n_eb > 0 ? n_eb : 1);
+        if (c < 1) c = 1;
+        if (c > maxc) c = maxc;
+        int64_t blocks = c * n_eb, waves = (blocks + cap - 1) / cap;
+        double fill = (double)blocks / (double)(waves * cap);
+        if (fill > best_fill + 1e-9) { best_fill = fill; best = c; }
+        if (fill >= 0.97 || c == maxc) break;
+    }
+    return (int)best;
+}
+
+cudaError_t launch_grad_pv(const float4 *bseq, int64_t nb, const int32_t *edge_rec, int64_t n_edges,
+                           const QuerySrc &q, const float *grad_w, int n_chunks, float *partial, float *partial_p,
+                           float *rec_grad, const int32_t *bvert, const int64_t *rec_off, const int32_t *recs,
+                           int64_t n_bvert, float *grad_p, float *grad_V, cudaStream_t st) {
+    if (nb == 0 || n_edges == 0 || q.n == 0) return cudaSuccess;
     int64_t chunk_len = (q.n + n_chunks - 1) / n_chunks;
-    const int n_eb = (int)((nb + GV_THREADS - 1) / GV_THREADS);
+    const int n_eb = (int)((n_edges + GV_THREADS - 1) / GV_THREADS);
     dim3 grid((unsigned)n_eb, (unsigned)n_chunks);
-    grad_pv_partial_kernel<<<grid, GV_THREADS, 0, st>>>(bseq, (int)nb, q, grad_w, chunk_len, partial, partial_p);
+    grad_pv_partial_kernel<<<grid, GV_THREADS, 0, st>>>(bseq, (int)nb, edge_rec, (int)n_edges, q, grad_w, chunk_len,
+                                                        partial, partial_p);
     grad_p_reduce_kernel<<<(unsigned)((q.n + 255) / 256), 256, 0, st>>>(partial_p, n_eb, q.n, grad_p);
     if (n_bvert > 0) {
         grad_v_record_kernel<<<(unsigned)((nb + 255) / 256), 256, 0, st>>>(partial, n_chunks, (int)nb, bseq, rec_grad);

@@ -234,6 +234,7 @@ struct gwn_geom {
     int32_t *bseq_vid = nullptr;       // device vertex id per record
     int64_t n_bseq = 0;
     // boundary vertex -> records lists (gradient scatter), built on demand
+    int32_t *d_edge_rec = nullptr;     // device: record index ending each boundary edge, in edge order
     int32_t *d_bvert = nullptr;
     int64_t *d_brec_off = nullptr;
     int32_t *d_brecs = nullptr;
@@ -301,13 +302,16 @@ cudaError_t launch_bframe(const float4 *bseq, int64_t n, const Frame &fr, float4
 cudaError_t launch_grad_p(const float4 *bseq, int64_t nb, const QuerySrc &q, const float *grad_w, float *grad_p,
                           cudaStream_t st);
 int grad_v_chunks(int64_t nq, int64_t nb, int sm_count);
-// both gradients from one pass over the (query, edge) pairs; partial_p holds
-// grad_pv_partial_p_bytes(nq, nb) bytes
-size_t grad_pv_partial_p_bytes(int64_t nq, int64_t nb);
-cudaError_t launch_grad_pv(const float4 *bseq, int64_t nb, const QuerySrc &q, const float *grad_w, int n_chunks,
-                           float *partial, float *partial_p, float *rec_grad, const int32_t *bvert,
-                           const int64_t *rec_off, const int32_t *recs, int64_t n_bvert, float *grad_p, float *grad_V,
-                           cudaStream_t st);
+// both gradients from one pass over the (query, edge) pairs, thread per edge
+// (edge_rec: the record ending each edge); partial_p holds
+// grad_pv_partial_p_bytes(nq, n_edges) bytes, partial 6 floats per (chunk,
+// record); grad_pv_chunks gives the number of query chunks
+size_t grad_pv_partial_p_bytes(int64_t nq, int64_t n_edges);
+int grad_pv_chunks(int64_t nq, int64_t n_edges, int sm_count);
+cudaError_t launch_grad_pv(const float4 *bseq, int64_t nb, const int32_t *edge_rec, int64_t n_edges,
+                           const QuerySrc &q, const float *grad_w, int n_chunks, float *partial, float *partial_p,
+                           float *rec_grad, const int32_t *bvert, const int64_t *rec_off, const int32_t *recs,
+                           int64_t n_bvert, float *grad_p, float *grad_V, cudaStream_t st);
 cudaError_t launch_grad_v(const float4 *bseq, int64_t nb, const QuerySrc &q, const float *grad_w, int n_chunks,
                           float *partial, float *rec_grad, const int32_t *bvert, const int64_t *rec_off,
                           const int32_t *recs, int64_t n_bvert, float *grad_V, cudaStream_t st);
