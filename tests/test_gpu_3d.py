@@ -302,7 +302,8 @@ def test_device_boundary_extraction(gwn, ctx, name):
     ctx.check()
 
 
-@pytest.mark.parametrize("case", ["cap_grid", "cap_points", "lattice_soup", "torus_points", "heightfield_grid"])
+@pytest.mark.parametrize("case", ["cap_grid", "cap_points", "lattice_soup", "torus_points", "heightfield_grid",
+                                  "far_points"])
 def test_bins_equal_tree(gwn, ctx, case):
     """The 2D bin index (built once the evaluations reach 4 queries per
     triangle) and the LBVH traversal test the same (query, triangle)
@@ -331,6 +332,18 @@ def test_bins_equal_tree(gwn, ctx, case):
         F = np.concatenate([F, F[:50], F[:20, [0, 2, 1]]])
         d = np.array([1.0, 2.0, 3.0], np.float32)
         P = np.concatenate([V, (rng.integers(0, 21, (6000, 3)) / 20.0).astype(np.float32)])
+        q = gwn.Points(torch.as_tensor(P).cuda())
+    elif case == "far_points":
+        # points 1e4 along -d and +d from points of the mesh's box: their rays
+        # cross the whole surface (or nothing), and their padded boxes (pad
+        # grows with |p|) span several bins, so a pair must be counted in one
+        # bin only
+        m = gen.icosphere_cap(subdiv=3, grid_n=8, seed=12)
+        V, F, d = m.V, m.F, m.d
+        dh = d.astype(np.float64) / np.linalg.norm(d.astype(np.float64))
+        c = rng.random((6000, 3)) * 2.0 - 1.0
+        s_ = np.where(rng.random(6000) < 0.5, -1e4, 1e4)[:, None]
+        P = (c + s_ * dh).astype(np.float32)
         q = gwn.Points(torch.as_tensor(P).cuda())
     elif case == "torus_points":
         m = gen.slit_torus(n_u=96, n_v=64, n_queries=60000, seed=2)
