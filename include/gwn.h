@@ -243,7 +243,12 @@ GWN_API gwn_status gwn_bezier_monotone_split_host(const double ctrl[8], double u
  *   chi_out (optional, device int32[n]): the signed crossing count.
  *   b_out   (optional, device, same dtype as w_out): the boundary term
  *           (3D: B_d; 2D: chord term).
- *   stats   (optional): counters; synchronises the stream. */
+ *   stats   (optional): counters; synchronises the stream.
+ * A mesh evaluation for a new d first builds the LBVH (gwn_mesh_prepare), and
+ * one evaluation per (mesh, d) may build the crossing bins
+ * (gwn_mesh_set_index); those one-time builds synchronise the stream, so an
+ * evaluation that must only enqueue work (e.g. under stream capture) needs a
+ * prepared mesh and GWN_INDEX_TREE or bins already built. */
 GWN_API gwn_status gwn_eval(gwn_geom *g, const gwn_queries *q, const float *d, void *w_out,
                             int32_t *chi_out, void *b_out, gwn_stats *stats);
 
