@@ -568,21 +568,27 @@ gwn_status mesh_intake_device(gwn_ctx *ctx, const float *dV, int64_t nv, const i
         if (nh > 0) edge_net_kernel<<<blocks_for(nh, 256), 256, 0, st>>>(k0, v0, nh, out, hdr);
         e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_fail(e, "mesh intake");
+        // the header and the first edges come back together (boundaries are
+        // usually short); a longer boundary takes a second copy
+        const int64_t spec = nh < 4096 ? nh : 4096;
         unsigned long long h[2];
+        std::vector<int2> he((size_t)(spec > 0 ? spec : 1));
         e = cudaMemcpyAsync(h, hdr, sizeof(h), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess && spec > 0)
+            e = cudaMemcpyAsync(he.data(), out, sizeof(int2) * spec, cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) return cuda_fail(e, "mesh intake");
         if (h[1] & 1u) { set_error("gwn_mesh_create: non-finite vertex coordinate"); return GWN_E_INVALID; }
         if (h[1] & 2u) { set_error("gwn_mesh_create: face index out of range"); return GWN_E_INVALID; }
         int64_t ne = (int64_t)(h[0] < (unsigned long long)nh ? h[0] : (unsigned long long)nh);
-        if (ne > 0) {
-            std::vector<int2> he(ne);
+        if (ne > spec) {
+            he.resize((size_t)ne);
             e = cudaMemcpyAsync(he.data(), out, sizeof(int2) * ne, cudaMemcpyDeviceToHost, st);
             if (e == cudaSuccess) e = cudaStreamSynchronize(st);
             if (e != cudaSuccess) return cuda_fail(e, "mesh intake");
-            bedges.resize(ne);
-            for (int64_t j = 0; j < ne; j++) bedges[j] = std::make_pair(he[j].x, he[j].y);
         }
+        bedges.resize((size_t)ne);
+        for (int64_t j = 0; j < ne; j++) bedges[j] = std::make_pair(he[j].x, he[j].y);
     }
     return GWN_OK;
 }
