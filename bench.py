@@ -458,7 +458,7 @@ def run_other(args):
         out["cpu_baseline"] = {"value": len(P) / dt, "unit": UNIT, "cores": oracle.default_threads(), "kind": "oracle",
                                "sample": f"{len(P)} queries of chain {c0}, FP64 closed form (+x ray per query)"}
     elif name == "slit_torus":
-        m = gen.slit_torus()
+        m = gen.slit_torus(n_queries=args.queries)
         mesh = gwn.Mesh(ctx, m.V, m.F)
         mesh.prepare(m.d)
         Pt = torch.as_tensor(m.points).to(dev)
@@ -604,6 +604,8 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=1024)
     ap.add_argument("--grid", type=int, default=256, help="grid resolution (256 = the benchmark workload; "
                                                           "smaller values only for profiling captures)")
+    ap.add_argument("--queries", type=int, default=1 << 20, help="slit_torus point queries (1,048,576 = the "
+                                                                   "measured configuration; fewer only for profiling)")
     ap.add_argument("--no-extras", action="store_true", help="skip comparator, e2e and CPU baseline legs")
     ap.add_argument("--workload", default="icosphere_cap",
                     choices=["icosphere_cap", "circle_chain_fp64", "star_chains", "slit_torus", "holey_heightfield",
