@@ -174,7 +174,8 @@ GWN_API gwn_status gwn_mesh_create(gwn_ctx *ctx, const float *V, int64_t nv, con
  * triangle boxes
  * (lists by decreasing depth) and uses it when it is compact (at most 12
  * entries per triangle + 4096; no list longer than both 512 and 64 times the
- * mean); TREE always uses the LBVH traversal.  Both test exactly the same
+ * mean; without device memory for them the tree serves); TREE always uses
+ * the LBVH traversal.  Both test exactly the same
  * (query, triangle) pairs, so the crossing counts are identical.  Takes effect
  * at the next evaluation. */
 enum { GWN_INDEX_AUTO = 0, GWN_INDEX_TREE = 1 };

@@ -1046,7 +1046,8 @@ static gwn_status eval_impl(gwn_geom *g, const gwn_queries *q, const float *d, v
             // enough queries per triangle, over the evaluations of this
             // (mesh, d), for the 2D bins to repay their build
             e = bins_build(g, ctx->stream);
-            if (e != cudaSuccess) return cuda_fail(e, "crossing bins");
+            if (e == cudaErrorMemoryAllocation) cudaGetLastError();   // no room for the bins: the tree serves
+            else if (e != cudaSuccess) return cuda_fail(e, "crossing bins");
         }
         if (stats) CK(cudaEventRecord(ctx->ev[1], ctx->stream), "event");
         e = launch_traverse(g->bvh, src, chi, defer, ctx->d_defer_count, ctx->d_tpairs, ctx->d_tpair_count, lines,
