@@ -166,18 +166,18 @@ GWN_API gwn_status gwn_mesh_create(gwn_ctx *ctx, const float *V, int64_t nv, con
                                    int64_t nf, int mem_kind, gwn_geom **out);
 
 /* Crossing index of a mesh.  All rays share d, so the crossing search is a
- * 2D point location in the plane normal to d plus a depth test.  AUTO (the
- * default): once the evaluations of a (mesh, d) have asked for at least 4
- * queries per triangle in total (grid queries with d parallel to a grid axis,
- * which reuse rays per grid line, do not count), the evaluation reaching
- * that total builds once, besides the LBVH, a bin grid over the projected
- * triangle boxes
- * (lists by decreasing depth) and uses it when it is compact (at most 12
- * entries per triangle + 4096; no list longer than both 512 and 64 times the
- * mean; without device memory for them the tree serves); TREE always uses
- * the LBVH traversal.  Both test exactly the same
- * (query, triangle) pairs, so the crossing counts are identical.  Takes effect
- * at the next evaluation. */
+ * 2D point location in the plane normal to d plus a depth test.
+ *   AUTO (the default): once the evaluations of a (mesh, d) have asked for
+ *     at least 4 queries per triangle in total (grid queries with d parallel
+ *     to a grid axis, which reuse rays per grid line, do not count), the
+ *     evaluation reaching that total builds once, besides the LBVH, a bin
+ *     grid over the projected triangle boxes (lists by decreasing depth) and
+ *     uses it when it is compact: at most 12 entries per triangle + 4096, and
+ *     no list longer than both 512 and 64 times the mean.  Without device
+ *     memory for the bins the tree serves.
+ *   TREE: always the LBVH traversal.
+ * Both test exactly the same (query, triangle) pairs, so the crossing counts
+ * are identical.  Takes effect at the next evaluation. */
 enum { GWN_INDEX_AUTO = 0, GWN_INDEX_TREE = 1 };
 GWN_API gwn_status gwn_mesh_set_index(gwn_geom *g, int index);
 
