@@ -382,17 +382,23 @@ def _alu_roofline(nq, info, ms):
             "frac": achieved / peak, "peak_source": kind}
 
 
+_TIMED_CLOCKS = []     # clock samples of each _timed region, for the workload's JSON line
+
+
 def _timed(fn, steps, warmup, stream):
     import torch
     for _ in range(warmup):
         fn()
     torch.cuda.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
     for a, b in ev:
         a.record(stream)
         fn()
         b.record(stream)
     torch.cuda.synchronize()
+    _TIMED_CLOCKS.append(clocks.stop())
     return [a.elapsed_time(b) for a, b in ev]
 
 
@@ -590,6 +596,8 @@ def run_other(args):
                     "roofline_bterm": _alu_roofline(g.n, info, st["ms_boundary"])})
     else:
         raise SystemExit(f"unknown workload {name}")
+    if _TIMED_CLOCKS:      # SM clocks sampled (every 100 ms) during the first timed region
+        out["clocks"] = _TIMED_CLOCKS[0]
     print(json.dumps(out))
     return 0
 
