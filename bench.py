@@ -81,7 +81,18 @@ class ClockSampler:
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, gpu_index: int):
-        self.gpu = gpu_index
+        # nvidia-smi numbers GPUs by PCI order and ignores CUDA_VISIBLE_DEVICES,
+        # so the device is named by its UUID (a read-only query either way)
+        self.uuid = _gpu_uuid(gpu_index)
+        self.gpu = str(gpu_index)
+        if self.uuid:
+            try:
+                r = subprocess.run(["nvidia-smi", f"--id={self.uuid}", "--query-gpu=uuid", "--format=csv,noheader"],
+                                   capture_output=True, text=True, timeout=20)
+                if r.returncode == 0 and self.uuid in r.stdout:
+                    self.gpu = self.uuid
+            except Exception:
+                pass
         self.proc = None
         self.path = os.path.join("/tmp", f"gwn_clocks_{os.getpid()}.csv")
 
@@ -119,7 +130,19 @@ class ClockSampler:
                     reasons.add(nm)
         os.unlink(self.path)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm), "gpu_uuid": self.uuid,
+                "smi_id": self.gpu}
+
+
+def _gpu_uuid(index: int):
+    """UUID string of torch's CUDA device `index` ("GPU-xxxxxxxx-..."), or None."""
+    try:
+        import torch
+        u = torch.cuda.get_device_properties(index).uuid
+        s = str(u)
+        return s if s.startswith("GPU-") else "GPU-" + s
+    except Exception:
+        return None
 
 
 def workload(rank: int = 0, world: int = 1, grid_n: int = 256):

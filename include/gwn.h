@@ -157,11 +157,21 @@ GWN_API gwn_status gwn_ctx_check(gwn_ctx *ctx);
 GWN_API void gwn_ctx_destroy(gwn_ctx *ctx);
 
 /* Triangle mesh: V float32 [nv x 3], F int32 [nf x 3] in `mem_kind` memory.
- * Copies the inputs, extracts the boundary loops on the host (directed edge
- * multiplicities, edges of multiplicity m split into m unit edges, chained
- * into loops) and uploads them.  Fails with GWN_E_INVALID on a non-finite
- * coordinate or an index outside [0, nv).  The ray-crossing hierarchy is
- * built per direction d on first use (or by gwn_mesh_prepare). */
+ * Defining passages: the boundary of the surface is what the method sums
+ * over -- segments that belong to only one loop are boundary, interior
+ * segments are traversed once in each direction and cancel (Curve Networks,
+ * Preprocessing); several disconnected boundaries enter one and the same sum
+ * (Implementation Details, "Multiple Boundaries").
+ * Copies the inputs to the device and extracts the boundary there: V is
+ * checked finite and F in range, every directed edge becomes a key (smaller
+ * id, larger id), a device radix sort groups the keys and each run's net
+ * multiplicity m = #(A->B) - #(B->A) is taken; an edge with |m| > 1 is split
+ * into |m| unit edges.  Only the unit boundary edges are copied back to the
+ * host, which chains them into loops (walk of unused out-edges); the loop
+ * records are gathered on the device.  The call synchronises the context's
+ * stream.  Fails with GWN_E_INVALID on a non-finite coordinate or an index
+ * outside [0, nv).  The ray-crossing hierarchy is built per direction d on
+ * first use (or by gwn_mesh_prepare). */
 GWN_API gwn_status gwn_mesh_create(gwn_ctx *ctx, const float *V, int64_t nv, const int32_t *F,
                                    int64_t nf, int mem_kind, gwn_geom **out);
 
@@ -185,7 +195,11 @@ GWN_API gwn_status gwn_mesh_set_index(gwn_geom *g, int index);
  * d (float32[3], any nonzero length).  Optional: gwn_eval prepares lazily. */
 GWN_API gwn_status gwn_mesh_prepare(gwn_geom *g, const float d[3]);
 
-/* Cubic Bezier chains: ctrl [n_ctrl x 2] of type dtype (GWN_F32|GWN_F64);
+/* Cubic Bezier chains.  Defining passage: the winding number of a 2D curve,
+ * w_C(p) = (1/2pi) * (angle swept by the curve around p), and its crossing
+ * count form with one ray (Background, 2D winding number; Validation and
+ * Results, 2D parametric geometry: cubic Bezier curves on regular grids).
+ * ctrl [n_ctrl x 2] of type dtype (GWN_F32|GWN_F64);
  * chain c owns control points chain_offsets[c] .. chain_offsets[c+1]-1, a
  * C0 chain of (count-1)/3 cubic segments (count = 3k+1, k >= 1).
  * chain_offsets is a host array of n_chains + 1 int64.  Each chain is split
@@ -279,7 +293,11 @@ typedef struct gwn_plan {
 } gwn_plan;
 
 /* Evaluate many 2D chain sets (one geometry, chain c with its own grid
- * queries[c]) in one persistent launch; w_out is one device buffer holding
+ * queries[c]) in one persistent launch.  Defining passage: the 2D experiment
+ * of Validation and Results evaluates a thousand random curves, each on its
+ * own regular grid in the curve's bounding box; here they are one launch
+ * whose work items (chain, block of grid rows, run of pieces) are claimed
+ * from an atomic counter.  w_out is one device buffer holding
  * chain c's grid at offset out_offsets[c] (host int64[n_chains]).  plan may be
  * NULL (autotuned and cached per shape).  The launch sequence is captured
  * once in a CUDA graph and replayed on later calls with the same shapes. */
@@ -293,6 +311,11 @@ GWN_API gwn_status gwn_batch_plan_get(gwn_geom *g, int32_t *threads, int32_t *ro
 
 /* Gradient of w (mesh, POINTS queries) w.r.t. the query points and the mesh
  * vertices, given the upstream gradient grad_w (device float32[n]).
+ * Defining passage: Conclusions (moving geometry: w recomputed as the
+ * geometry moves); the derivative is that of the closed form above, whose
+ * crossing count is piecewise constant, so only the boundary term varies:
+ * d/dp of (1/4pi) sum Omega(A-p, B-p, -d) is the Biot-Savart line integral
+ * over the boundary, independent of d.
  *   grad_p (device float32[n x 3] or NULL):  grad_w[q] * dw_q/dp
  *   grad_V (device float32[nv x 3] or NULL): sum_q grad_w[q] * dw_q/dV
  *            (rows of vertices not on the boundary are 0).
@@ -320,9 +343,12 @@ GWN_API gwn_status gwn_backward(gwn_geom *g, const gwn_queries *q, const float *
  *          GWN_E_INVALID.
  *   w_out: device float32 [n]; same values as gwn_eval on the same input.
  * The array takes 32 MiB on every GPU that loads the library, until the
- * process exits.  The first call on a device resolves the array's device
- * address (cudaGetSymbolAddress with that device current); make that first
- * call before any stream capture.  All calls share the one array and it keeps
+ * process exits.  Every call whose stream is not capturing looks up the
+ * array's device address (cudaGetSymbolAddress with the device current; it
+ * allocates nothing), so a device reset between calls is picked up; the
+ * first call on a device must come before any stream capture, and a call on
+ * a capturing stream reuses the last address looked up on that device.  All
+ * calls share the one array and it keeps
  * the last call's contents: calls whose work overlaps on the GPU (other
  * streams or contexts on the same device) race on it -- serialise them. */
 #define GWN_NOALLOC_MAX_QUERIES 4194304

@@ -17,8 +17,9 @@
 //     the library, until the process exits;
 //   * query points must already be in device memory, and the mesh's
 //     hierarchy must already be built for d (gwn_mesh_prepare);
-//   * the first call on a device resolves the array's device address (and
-//     loads its code module); make that first call before any stream capture;
+//   * a call not under stream capture looks up the array's device address
+//     (and on the first call loads its code module); the first call on a
+//     device must come before any stream capture;
 //   * every call shares the one array, whose contents persist between calls:
 //     calls whose work overlaps on the GPU (different streams, or contexts on
 //     the same device) race on it.  Serialise them.
@@ -38,18 +39,28 @@ static __device__ __align__(256) int32_t g_noalloc_chi[2 * GWN_NOALLOC_MAX_QUERI
 static std::mutex g_noalloc_mu;
 static int32_t *g_noalloc_ptr[256];
 
-// device address of the array on `device` (current), resolved once
-static gwn_status noalloc_scratch(int device, int32_t **out) {
+// Device address of the array on `device` (current).  It is looked up again
+// on every call that is not being captured into a CUDA graph, so a device
+// reset or a new primary context between calls is picked up (the lookup
+// allocates nothing).  A call under stream capture uses the address cached by
+// the last uncaptured call on that device, and fails if there was none.
+static gwn_status noalloc_scratch(int device, cudaStream_t stream, int32_t **out) {
     if (device < 0 || device >= 256) {
         set_error("gwn_eval_points_noalloc: device ordinal out of range");
         return GWN_E_INVALID;
     }
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(stream, &cs);
+    if (e != cudaSuccess) return cuda_fail(e, "gwn_eval_points_noalloc: cudaStreamIsCapturing");
     std::lock_guard<std::mutex> lk(g_noalloc_mu);
-    if (!g_noalloc_ptr[device]) {
+    if (cs == cudaStreamCaptureStatusNone) {
         int32_t *ptr = nullptr;
-        cudaError_t e = cudaGetSymbolAddress((void **)&ptr, g_noalloc_chi);
+        e = cudaGetSymbolAddress((void **)&ptr, g_noalloc_chi);
         if (e != cudaSuccess) return cuda_fail(e, "gwn_eval_points_noalloc: cudaGetSymbolAddress");
         g_noalloc_ptr[device] = ptr;
+    } else if (!g_noalloc_ptr[device]) {
+        set_error("gwn_eval_points_noalloc: the first call on a device must not be under stream capture");
+        return GWN_E_INVALID;
     }
     *out = g_noalloc_ptr[device];
     return GWN_OK;
@@ -79,7 +90,7 @@ extern "C" GWN_API gwn_status gwn_eval_points_noalloc(gwn_geom *g, const float *
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
     int32_t *chi = nullptr;
-    gwn_status s = noalloc_scratch(ctx->device, &chi);
+    gwn_status s = noalloc_scratch(ctx->device, ctx->stream, &chi);
     if (s != GWN_OK) return s;
     if (n == 0) return GWN_OK;
     QuerySrc src;

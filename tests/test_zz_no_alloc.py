@@ -15,7 +15,6 @@ import pytest
 import gen
 
 pytestmark = pytest.mark.gpu
-TOL = 1e-6          # the float32 bar of the other parity tests
 
 
 def test_noalloc_matches_gwn_eval_on_two_calls(cuda_available):
@@ -32,15 +31,29 @@ def test_noalloc_matches_gwn_eval_on_two_calls(cuda_available):
     dptr = d.ctypes.data_as(C.c_void_p)
     mesh.prepare(d)                       # allocates; must precede the allocation-free calls
     rng = np.random.default_rng(4)
-    for n in (200_000, 77_777):           # two calls in a row, different sizes and points
-        P = torch.as_tensor(rng.uniform(-1.3, 1.3, (n, 3)).astype(np.float32)).cuda()
-        ref = mesh.eval(gwn.Points(P), d)
-        w = torch.full((n,), float("nan"), dtype=torch.float32, device="cuda")
-        rc = lib.gwn_eval_points_noalloc(mesh.h, C.c_void_p(P.data_ptr()), n, dptr, C.c_void_p(w.data_ptr()))
+    sizes = (200_000, 77_777)             # two calls in a row, different sizes and points
+    Ps = [torch.as_tensor(rng.uniform(-1.3, 1.3, (n, 3)).astype(np.float32)).cuda() for n in sizes]
+    refs = [mesh.eval(gwn.Points(P), d) for P in Ps]
+    outs = [torch.full((n,), float("nan"), dtype=torch.float32, device="cuda") for n in sizes]
+
+    def call(P, w):
+        rc = lib.gwn_eval_points_noalloc(mesh.h, C.c_void_p(P.data_ptr()), P.shape[0], dptr,
+                                         C.c_void_p(w.data_ptr()))
         _capi.check(rc, "gwn_eval_points_noalloc")
-        torch.cuda.synchronize()
-        assert torch.isfinite(w).all()
-        assert (w - ref).abs().max().item() <= TOL
+
+    call(Ps[1], outs[1])                  # warm call: the first launch may load code modules
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    outs[1].fill_(float("nan"))
+    for P, w in zip(Ps, outs):
+        call(P, w)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()    # read before any comparison allocates temporaries
+    assert free1 == free0, f"device memory changed by {free0 - free1} bytes across the calls"
+    for w, ref in zip(outs, refs):
+        # the same kernels on the same input as gwn_eval: identical bits
+        assert torch.equal(w, ref)
+    P, w = Ps[1], outs[1]
     ctx.check()
     # more queries than the fixed array holds: rejected before any work
     rc = lib.gwn_eval_points_noalloc(mesh.h, C.c_void_p(P.data_ptr()), _capi.NOALLOC_MAX_QUERIES + 1, dptr,
