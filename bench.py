@@ -1,24 +1,29 @@
 #!/usr/bin/env python3
-"""Benchmark: one-shot GWN queries/s on the capped-icosphere workload.
+"""Benchmark: one-shot GWN queries/s on one GPU.
 
-Workload (one step): the generalized winding number of an icosphere at
-subdivision 6 with the polar cap z > 0.8 removed (73,724 triangles, 252
-boundary edges, vertex noise 1e-3) at every point of a 256^3 grid on
-[-1.2, 1.2]^3 (16,777,216 queries), for one seeded ray direction: exact
-crossing counts (LBVH traversal) + float32 boundary term + epilogue, with the
-mesh, its boundary loops and its LBVH resident on the device.
+Default workload (one step), the largest single-GPU configuration: the
+generalized winding number of a heightfield disk (2049^2 vertex grid mapped to
+the unit disk, 16 sinusoids of amplitude 0.05; 32 circular holes remove
+triangles, leaving 8,102,716 triangles and 33 boundary loops of 17,478 edges)
+at every point of a 512^3 grid on [-1.1, 1.1]^3 (134,217,728 queries), for one
+seeded ray direction: exact crossing counts + float32 boundary term +
+epilogue, with the mesh, its boundary loops and its crossing index resident on
+the device.  ``--workload icosphere_cap`` runs the same measurement on the
+capped icosphere (73,724 triangles, 252 boundary edges, 256^3 grid).
 
 JSON keys beyond the common contract:
   roofline      dominant kernel (boundary term) vs the FP32 issue roofline
   kernels       per-kernel average time from CUDA events on the launch stream
-  prep_ms       per-geometry preparation (host boundary extraction + upload,
-                device LBVH build), outside `value`
+  prep_ms       per-geometry preparation (mesh upload with device boundary
+                extraction, LBVH build, crossing-bin build), outside `value`
   bruteforce_gpu  the brute-force per-triangle solid-angle sum on the same GPU
   cpu_baseline  the FP64 oracle on this host's cores (bounded sample)
   e2e           through the C ABI from host buffers: mesh creation from host
-                V/F, LBVH build, evaluation and the copy of w back, per step
+                V/F, LBVH and bin builds, evaluation, w into a pinned host
+                buffer, per step
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                       [--workload NAME]
 """
 from __future__ import annotations
 
@@ -37,7 +42,30 @@ import numpy as np  # noqa: E402
 
 METRIC = "GWN queries/sec, one-shot vs brute-force solid-angle sum on 1 GB300 at |Δw|≤1e-6"
 UNIT = "queries/s"
-WORKLOAD = "icosphere_cap_s6_73724tris_256^3grid"
+# The two workloads of the main measurement: each one mesh on a full 3D grid.
+#   grid      default grid resolution per axis
+#   traffic   DRAM bytes of one bterm3d_kernel launch at that grid, from ncu
+#             (dram__bytes_read.sum + dram__bytes_write.sum), valid only
+#             while csrc/bterm.cu hashes to `bterm_cu_sha256`
+#   bf_planes grid planes (of z) timed for the brute-force comparator
+#   cpu/ref   oracle queries for the CPU baseline and per reference-arm step
+MAIN = {
+    "holey_heightfield": {
+        "label": "holey_heightfield_8102716tris_512^3grid", "grid": 512,
+        "desc": "heightfield disk, 8,102,716 triangles, 33 boundary loops (17,478 edges), 512^3 grid on [-1.1,1.1]^3",
+        "traffic": None, "bf_rows": 16, "cpu_sample": 192, "ref_sample": 48, "steps": 10,
+    },
+    "icosphere_cap": {
+        "label": "icosphere_cap_s6_73724tris_256^3grid", "grid": 256,
+        "desc": "icosphere s6 with the cap z>0.8 removed, 73,724 triangles, 252 boundary edges, 256^3 grid on "
+                "[-1.2,1.2]^3",
+        # read 67.31 MB, write 21.43 MB: DRAM writes fall below the 8 algorithmic
+        # bytes per query because L2 still holds part of w when the kernel ends
+        "traffic": {"bytes": 88.45e6,
+                    "bterm_cu_sha256": "7cd7454dc9e001c16a324a659322c7013b857607627133edf9fcaf9e428ee2ee"},
+        "bf_rows": 1024, "cpu_sample": 4096, "ref_sample": 1024, "steps": 100,
+    },
+}
 
 # FP32 lane operations per boundary record (vertex) and per boundary edge of
 # the boundary-term kernel, counted from its formulation (an FMA counts as
@@ -55,12 +83,6 @@ W_EDGE = 31
 # reciprocal (6); 1/(|a||b|), I0 numerator, I0 (6); 1/|a| - 1/|b|, I1 (4);
 # weights (5); per-edge and per-query accumulation (9)                       -> 58
 W_GRAD_PAIR = 58
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one bterm3d_kernel
-# launch on this workload at full size, from an ncu capture (read 67.31 MB,
-# write 21.43 MB); reported only while csrc/bterm.cu is the source it was taken
-# on.  Algorithmic bytes are 8 per query (chi in, w out: 134 MB); DRAM writes
-# fall below that because L2 still holds part of w when the kernel ends.
-BTERM_TRAFFIC = {"bytes": 88.45e6, "bterm_cu_sha256": "7cd7454dc9e001c16a324a659322c7013b857607627133edf9fcaf9e428ee2ee"}
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 
@@ -145,10 +167,17 @@ def _gpu_uuid(index: int):
         return None
 
 
-def workload(rank: int = 0, world: int = 1, grid_n: int = 256):
+def make_mesh(name: str, grid_n: int | None = None):
     import gen
+    grid_n = grid_n or MAIN[name]["grid"]
+    if name == "holey_heightfield":
+        return gen.holey_heightfield(grid_n=grid_n)
+    return gen.icosphere_cap(grid_n=grid_n)
+
+
+def workload(name: str = "holey_heightfield", rank: int = 0, world: int = 1, grid_n: int | None = None):
     from paper_2408_04466_gb300.shard import shard_grid
-    m = gen.icosphere_cap(grid_n=grid_n)
+    m = make_mesh(name, grid_n)
     lo, hi, dims, span = shard_grid(m.grid.lo, m.grid.hi, m.grid.dims, rank, world, weak=True)
     return m, (lo, hi, dims)
 
@@ -177,9 +206,10 @@ def run_reference(args):
         return 0
     import oracle
     oracle.build()
-    m, _ = workload()
+    spec = MAIN[args.workload]
+    m, _ = workload(args.workload, grid_n=args.grid)
     cores = oracle.default_threads()
-    n = args.ref_sample
+    n = args.ref_sample or spec["ref_sample"]
     for w in range(args.warmup):
         oracle_rate(m, n, 1000 + w)
     times = []
@@ -192,10 +222,10 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "queries_per_step": n, "l2": "n/a (host)"},
+        "config": {"workload": spec["label"], "queries_per_step": n, "l2": "n/a (host)"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": f"{n} seeded queries of the 256^3 grid per step; FP64 one-shot "
-                                   f"(exact crossing count by brute force over all 73,724 triangles + "
+                         "sample": f"{n} seeded queries of the {m.grid.dims[0]}^3 grid per step; FP64 one-shot "
+                                   f"(exact crossing count by brute force over all {len(m.F):,} triangles + "
                                    f"boundary term)"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -225,7 +255,8 @@ def run_gpu(args):
         dist.barrier()
     import paper_2408_04466_gb300 as gwn
 
-    m, (lo, hi, dims) = workload(rank, world, args.grid)
+    spec = MAIN[args.workload]
+    m, (lo, hi, dims) = workload(args.workload, rank, world, args.grid)
     nq = int(np.prod(dims))
     stream = torch.cuda.Stream(device=dev)
     torch.cuda.set_stream(stream)
@@ -236,15 +267,18 @@ def run_gpu(args):
     mesh.prepare(m.d)
     torch.cuda.synchronize()
     t2 = time.perf_counter()
-    prep = {"boundary_extract_upload_ms": 1e3 * (t1 - t0), "lbvh_build_ms": 1e3 * (t2 - t1)}
+    prep = {"mesh_create_ms": 1e3 * (t1 - t0), "lbvh_build_ms": 1e3 * (t2 - t1)}
     info = mesh.info()
     E, L = info["n_boundary_edges"], info["n_loops"]
     grid = gwn.Grid(lo, hi, dims)
     w = torch.empty(nq, dtype=torch.float32, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
-    # stats run (also a warm-up): per-kernel times and counters
+    # stats run (also a warm-up): per-kernel times and counters; on this first
+    # evaluation the crossing bins are built (timed as its ms_prepare)
     st = mesh.eval(grid, m.d, stats=True, out=w)["stats"]
+    prep["bins_build_ms"] = st["ms_prepare"]
+    prep["bins"] = {k: mesh.info()[k] for k in ("n_bins", "n_bin_entries", "bin_maxlen")}
     for _ in range(args.warmup):
         mesh.eval(grid, m.d, out=w)
     torch.cuda.synchronize()
@@ -278,7 +312,7 @@ def run_gpu(args):
 
     # per-kernel split: a stats call times traverse and boundary separately
     ks = []
-    for _ in range(5):
+    for _ in range(5 if nq <= (1 << 25) else 2):
         ks.append(mesh.eval(grid, m.d, stats=True, out=w)["stats"])
     ms_trav = statistics.median(k["ms_traverse"] for k in ks)
     ms_bterm = statistics.median(k["ms_boundary"] for k in ks)
@@ -296,14 +330,25 @@ def run_gpu(args):
         achieved = ops / (ms_bterm * 1e-3) / 1e12
         import hashlib
         with open(os.path.join(ROOT, "paper_2408_04466_gb300", "csrc", "bterm.cu"), "rb") as f:
-            same_src = hashlib.sha256(f.read()).hexdigest() == BTERM_TRAFFIC["bterm_cu_sha256"]
+            src_hash = hashlib.sha256(f.read()).hexdigest()
+        tr = spec["traffic"]
+        same_src = tr is not None and src_hash == tr["bterm_cu_sha256"] and nq == MAIN[args.workload]["grid"] ** 3
         roof = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tops/s (FP32 lane ops)",
-                "frac": achieved / alu_peak, "traffic": BTERM_TRAFFIC["bytes"] if same_src else None,
+                "frac": achieved / alu_peak, "traffic": tr["bytes"] if same_src else None,
                 "traffic_unit": "bytes per launch (DRAM, ncu)", "kernel": "bterm3d_kernel",
                 "peak_source": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x sm_max_mhz "
                                f"({peak_kind} MEASURED_PEAKS)" if peak_kind == "measured" else "fallback clock"}
-        # brute-force comparator on a sub-grid (first 4 planes: 262,144 queries)
-        sub = gwn.Grid(lo, (hi[0], hi[1], lo[2] + (hi[2] - lo[2]) * 3 / (dims[2] - 1)), (dims[0], dims[1], 4))
+        # brute-force comparator on a sub-grid: the first bf_rows rows (of x)
+        # of the grid's middle z-plane
+        nr = min(spec["bf_rows"], dims[1] * dims[2])
+        zc = lo[2] + (hi[2] - lo[2]) * (dims[2] // 2) / (dims[2] - 1)
+        if nr >= dims[1]:
+            nz = nr // dims[1]
+            sub = gwn.Grid(lo, (hi[0], hi[1], lo[2] + (hi[2] - lo[2]) * (nz - 1) / (dims[2] - 1)),
+                           (dims[0], dims[1], nz))
+        else:
+            sub = gwn.Grid((lo[0], lo[1], zc), (hi[0], lo[1] + (hi[1] - lo[1]) * (nr - 1) / (dims[1] - 1), zc),
+                           (dims[0], nr, 1))
         bw = torch.empty(sub.n, dtype=torch.float32, device=dev)
         mesh.bruteforce(sub)
         torch.cuda.synchronize()
@@ -321,7 +366,7 @@ def run_gpu(args):
         wh = torch.empty(nq, dtype=torch.float32).pin_memory()
         import ctypes as C
         from paper_2408_04466_gb300 import _capi
-        e2e_steps = max(3, min(args.steps, 10))
+        e2e_steps = max(3, min(args.steps, 10 if nq <= (1 << 25) else 3))
         times = []
         for s in range(e2e_steps + 1):
             torch.cuda.synchronize()
@@ -342,7 +387,7 @@ def run_gpu(args):
         # CPU baseline: the oracle on this host's cores, bounded sample
         import oracle
         oracle.build()
-        n_cpu = args.cpu_sample
+        n_cpu = args.cpu_sample or spec["cpu_sample"]
         rate, dt, (sidx, sP, wo, chio) = oracle_rate(m, n_cpu, 7, want=True)
         # parity on the same sample: crossing counts exactly, |dw| beyond 1e-4 x diagonal
         r = mesh.eval(grid, m.d, want_chi=True)
@@ -356,13 +401,13 @@ def run_gpu(args):
                   "max_abs_dw": float(np.abs(wg - wo)[far].max()) if far.any() else None,
                   "n_within_1e-4_diag": int((~far).sum()), "reference": "FP64 oracle on the cpu_baseline sample"}
         cpu = {"value": rate, "unit": UNIT, "cores": oracle.default_threads(), "kind": "oracle",
-               "sample": f"{n_cpu} seeded queries of the 256^3 grid; FP64 one-shot (brute-force exact crossing "
+               "sample": f"{n_cpu} seeded queries of the {dims[0]}^3 grid; FP64 one-shot (brute-force exact crossing "
                          f"count over all triangles + boundary term); {dt:.1f} s"}
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "queries_per_gpu": nq, "boundary_edges": E, "boundary_loops": L,
+            "config": {"workload": spec["label"], "description": spec["desc"], "queries_per_gpu": nq, "boundary_edges": E, "boundary_loops": L,
                        "triangles": int(len(m.F)), "l2": "flushed (256 MiB write before every step)",
                        "parallelism": f"queries sharded in z-slabs over {world} GPU(s), geometry replicated"},
             "roofline": roof,
@@ -373,7 +418,8 @@ def run_gpu(args):
                         "deferred_traverse_per_query": st["n_deferred_traverse"] / nq,
                         "deferred_boundary_per_query": st["n_deferred_boundary"] / nq},
             "prep_ms": prep,
-            "bruteforce_gpu": {"value": bf_rate, "unit": UNIT, "sample": f"{sub.n} grid queries x 73,724 triangles"},
+            "bruteforce_gpu": {"value": bf_rate, "unit": UNIT,
+                               "sample": f"{sub.n} grid queries x {len(m.F):,} triangles"},
             "speedup_vs_bruteforce_gpu": value / world / bf_rate,
             "cpu_baseline": cpu,
             "parity_sample": parity,
@@ -519,7 +565,7 @@ def run_other(args):
         # parametric surface: 320 bicubic Bezier patches (8 x 8 per cube face,
         # one face left open: one boundary loop of 32 curves x 64 segments),
         # 256^3 grid on [-1.3, 1.3]^3, seeded random d
-        pc = gen.patch_spheroid(n=8, amp=0.08, open_faces=(4,), grid_n=args.grid, seed=0)
+        pc = gen.patch_spheroid(n=8, amp=0.08, open_faces=(4,), grid_n=args.grid or 256, seed=0)
         ps = gwn.Patches(ctx, pc.ctrl, segments=64)
         g = gwn.Grid(pc.grid.lo, pc.grid.hi, pc.grid.dims)
         w = torch.empty(g.n, dtype=torch.float32, device=dev)
@@ -570,7 +616,7 @@ def run_other(args):
                     "ms_per_step": res["star_chain_f32"]["ms"]})
     elif name == "icosphere_cap_axis":
         # the benchmark mesh and grid with d = +z: one ray per grid line
-        m, (lo, hi, dims) = workload(0, 1, args.grid)
+        m, (lo, hi, dims) = workload("icosphere_cap", 0, 1, args.grid)
         mesh = gwn.Mesh(ctx, m.V, m.F)
         g = gwn.Grid(lo, hi, dims)
         w = torch.empty(g.n, dtype=torch.float32, device=dev)
@@ -599,24 +645,6 @@ def run_other(args):
                     "directions": out_k,
                     "note": "d = +z reuses one ray per grid line; the random-d run of the same mesh and grid is "
                             "beside it"})
-    elif name == "holey_heightfield":
-        m = gen.holey_heightfield()
-        mesh = gwn.Mesh(ctx, m.V, m.F)
-        t0 = time.perf_counter()
-        mesh.prepare(m.d)
-        torch.cuda.synchronize()
-        prep = time.perf_counter() - t0
-        g = gwn.Grid(m.grid.lo, m.grid.hi, m.grid.dims)
-        w = torch.empty(g.n, dtype=torch.float32, device=dev)
-        st = mesh.eval(g, m.d, stats=True, out=w)["stats"]
-        ms = _timed(lambda: mesh.eval(g, m.d, out=w), args.steps, min(args.warmup, 1), stream)
-        info = mesh.info()
-        out.update({"metric": METRIC, "dtype": "f32", "ms_per_step": statistics.median(ms),
-                    "value": g.n / (statistics.median(ms) * 1e-3), "queries_per_step": g.n,
-                    "boundary_edges": info["n_boundary_edges"], "boundary_loops": info["n_loops"],
-                    "triangles": int(len(m.F)), "lbvh_build_ms": 1e3 * prep,
-                    "kernels": {"traverse_ms": st["ms_traverse"], "bterm3d_ms": st["ms_boundary"]},
-                    "roofline_bterm": _alu_roofline(g.n, info, st["ms_boundary"])})
     else:
         raise SystemExit(f"unknown workload {name}")
     if _TIMED_CLOCKS:      # SM clocks sampled (every 100 ms) during the first timed region
@@ -628,26 +656,35 @@ def run_other(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=0, help="timed steps (0: 10 for the heightfield, 100 for the "
+                                                          "icosphere, 20 for the other workloads)")
+    ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--cpu-sample", type=int, default=4096)
-    ap.add_argument("--ref-sample", type=int, default=1024)
-    ap.add_argument("--grid", type=int, default=256, help="grid resolution (256 = the benchmark workload; "
-                                                          "smaller values only for profiling captures)")
+    ap.add_argument("--cpu-sample", type=int, default=0, help="oracle queries of the CPU baseline (0: the "
+                                                                "workload's default)")
+    ap.add_argument("--ref-sample", type=int, default=0, help="oracle queries per reference-arm step (0: the "
+                                                                "workload's default)")
+    ap.add_argument("--grid", type=int, default=0, help="grid resolution per axis (0: the workload's own, 512 for "
+                                                          "the heightfield, 256 for the icosphere; smaller values "
+                                                          "only for profiling captures)")
     ap.add_argument("--queries", type=int, default=1 << 20, help="slit_torus point queries (1,048,576 = the "
                                                                    "measured configuration; fewer only for profiling)")
     ap.add_argument("--no-extras", action="store_true", help="skip comparator, e2e and CPU baseline legs")
-    ap.add_argument("--workload", default="icosphere_cap",
-                    choices=["icosphere_cap", "circle_chain_fp64", "star_chains", "slit_torus", "holey_heightfield",
+    ap.add_argument("--workload", default="holey_heightfield",
+                    choices=["holey_heightfield", "icosphere_cap", "circle_chain_fp64", "star_chains", "slit_torus",
                              "icosphere_cap_axis", "chain_points", "patch_spheroid"],
-                    help="icosphere_cap is the benchmark; the others print their own measurement line")
+                    help="holey_heightfield (default, the largest single-GPU configuration) and icosphere_cap are "
+                         "the main measurement; the others print their own measurement line")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.steps <= 0:
+        args.steps = MAIN[args.workload]["steps"] if args.workload in MAIN else 20
     if args.impl == "reference":
+        if args.workload not in MAIN:
+            raise SystemExit("--impl reference measures the main workloads only")
         return run_reference(args)
-    if args.workload != "icosphere_cap":
+    if args.workload not in MAIN:
         return run_other(args)
     return run_gpu(args)
 

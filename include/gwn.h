@@ -112,7 +112,7 @@ typedef struct gwn_stats {
     int64_t n_stack_overflow;   /* traversals that overflowed (result invalid); patches: queries within the
                                    subdivision limit of the surface (w undefined there) */
     int64_t n_tri_tests;        /* exact ray/triangle tests (3D) or roots (2D) */
-    float ms_prepare;           /* per-direction preparation (BVH build) if it ran */
+    float ms_prepare;           /* per-direction preparation (BVH build, crossing bins) if it ran in this call */
     float ms_traverse;          /* crossing counts */
     float ms_boundary;          /* boundary term + epilogue */
     float ms_total;

@@ -1045,6 +1045,7 @@ static gwn_status eval_impl(gwn_geom *g, const gwn_queries *q, const float *d, v
                    (g->bvh.queries_seen += nq) >= 4 * g->nf) {
             // enough queries per triangle, over the evaluations of this
             // (mesh, d), for the 2D bins to repay their build
+            prepared = true;                 // ms_prepare covers the bin build
             e = bins_build(g, ctx->stream);
             if (e == cudaErrorMemoryAllocation) cudaGetLastError();   // no room for the bins: the tree serves
             else if (e != cudaSuccess) return cuda_fail(e, "crossing bins");
