@@ -71,18 +71,19 @@ MAIN = {
 # the boundary-term kernel, counted from its formulation (an FMA counts as
 # one operation):
 #   vertex: a = A - p (3), projection on e1, e2, n (9), |a_perp|^2, |a|^2 (3),
-#           rsqrt + scale + clamp (3), s = |a|+a_n or |a_perp|^2/(|a|-a_n) (6)  -> 24
+#           rsqrt + scale + clamp (3), s = |a|+a_n or |a_perp|^2/(|a|-a_n) (6),
+#           q = s |a| and the near-ray test (2)                               -> 26
 #   edge:   num (2), den (3), atan2 (20: min/max 2, reciprocal + product 2,
 #           degree-8 polynomial 10, reduction/quadrant fix-ups 6),
-#           cut test (2), compensated accumulation (4)                          -> 31
-W_VERTEX = 24
+#           cut and spindle tests (2), compensated accumulation (4)             -> 31
+W_VERTEX = 26
 W_EDGE = 31
 # FP32 lane operations per (query, boundary edge) pair of the fused backward
 # pass (both gradients): a = A - p, b = B - p (6); a x E, |a x E|^2 (10);
-# |a|^2, |b|^2 (8); rsqrt x 2, |a|, |b| (4); E.a, E.(a+b), |a|+|b| and its
-# reciprocal (6); 1/(|a||b|), I0 numerator, I0 (6); 1/|a| - 1/|b|, I1 (4);
-# weights (5); per-edge and per-query accumulation (9)                       -> 58
-W_GRAD_PAIR = 58
+# |a|^2, |b|^2 (8); rsqrt x 2, |a|, |b| (4); |a||b|, a.b (4); Q = |a||b| + a.b
+# or |a x E|^2 / (|a||b| - a.b) and its reciprocal (4); J_A, J_B (2);
+# weights (5); per-edge and per-query accumulation (9)                     -> 52
+W_GRAD_PAIR = 52
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 

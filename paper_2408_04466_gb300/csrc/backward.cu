@@ -3,16 +3,21 @@
 // contributes, and its derivative does not depend on d.
 //
 // Moving the boundary by delta x changes the solid angle by the flux of the
-// swept strip; for a straight edge r(s) = a + s E (a = A - p, E = B - A,
-// s in [0, 1]) with linearly interpolated motion this gives
-//     dOmega/dA = -(a x E) (I0 - I1),   dOmega/dB = -(a x E) I1,
-//     dOmega/dp =  (a x E) I0           (= -(dOmega/dA + dOmega/dB))
-// with I0 = int_0^1 |r|^-3 ds and I1 = int_0^1 s |r|^-3 ds in closed form:
-//     I0 = (E.b/|b| - E.a/|a|) / |a x E|^2,
-//     I1 = ((1/|a| - 1/|b|) - (a.E) I0) / |E|^2.
-// Both are evaluated without cancellation for short edges:
-//     E.b/|b| - E.a/|a| = (|E|^2 |a| - (E.a) E.(a+b) / (|a|+|b|)) / (|a||b|)
-//     1/|a| - 1/|b|     = E.(a+b) / (|a||b| (|a|+|b|)).
+// swept strip; for a straight edge r(s) = a + s E (a = A - p, b = B - p,
+// E = B - A, s in [0, 1]) with linearly interpolated motion this gives
+//     dOmega/dA = -(a x E) J_A,   dOmega/dB = -(a x E) J_B,
+//     dOmega/dp =  (a x E) (J_A + J_B)   (= -(dOmega/dA + dOmega/dB))
+// with J_A = int_0^1 (1 - s) |r|^-3 ds and J_B = int_0^1 s |r|^-3 ds.  Their
+// closed forms share one denominator Q = |a||b| + a.b:
+//     J_A = 1 / (|a| Q),   J_B = 1 / (|b| Q),
+// (from the antiderivatives (L s + c)/(D |r|) and -(c s + |a|^2)/(D |r|),
+// L = |E|^2, c = a.E, D = |a x E|^2 = (|a||b| - a.b) Q).  Neither form
+// subtracts nearly equal terms, so J_A and J_B keep a few ulps of relative
+// accuracy at any distance; the earlier difference form of J_B, ((1/|a| -
+// 1/|b|) - (a.E) I0) / |E|^2, lost a factor |a|/|E| to cancellation for
+// queries far from short edges.  Q itself cancels only when a and b point
+// nearly opposite ways (p close to the edge's interior); there it is taken
+// as D / (|a||b| - a.b), with D = |a x E|^2 computed from E.
 // The p-gradient sum over edges is the Biot-Savart line integral of the
 // boundary; it is checked against finite differences and against the
 // gradient of the per-triangle solid-angle sum.
@@ -30,12 +35,12 @@ namespace gwn {
 #define GWN_INV_4PI 0.07957747154594767f
 
 struct EdgeGrad {
-    float cx, cy, cz, i0, i1;
+    float cx, cy, cz, ja, jb;
 };
 
 // MUFU reciprocal and reciprocal square root (rcp/rsqrt.approx, ~1-2 ulp):
 // the gradient is needed to ~1e-4 relative, and these replace two IEEE
-// square roots and five divisions per (query, edge) pair.  Arguments are
+// square roots and several divisions per (query, edge) pair.  Arguments are
 // clamped to normal floats.
 __device__ __forceinline__ float grcp(float x) {
     float r;
@@ -48,9 +53,8 @@ __device__ __forceinline__ float grsqrt(float x) {
     return r;
 }
 
-// inv_e2 = 1/|E|^2 of the edge (computed once per edge)
 __device__ __forceinline__ EdgeGrad edge_grad(float ax, float ay, float az, float bx, float by, float bz,
-                                              float ex, float ey, float ez, float e2, float inv_e2) {
+                                              float ex, float ey, float ez) {
     EdgeGrad g;
     g.cx = ay * ez - az * ey;
     g.cy = az * ex - ax * ez;
@@ -59,15 +63,12 @@ __device__ __forceinline__ EdgeGrad edge_grad(float ax, float ay, float az, floa
     float ra2 = fmaxf(ax * ax + ay * ay + az * az, 1e-37f);
     float rb2 = fmaxf(bx * bx + by * by + bz * bz, 1e-37f);
     float ia = grsqrt(ra2), ib = grsqrt(rb2);
-    float la = ra2 * ia, lb = rb2 * ib;
-    float ea = ex * ax + ey * ay + ez * az;
-    float eab = 2.f * ea + e2;                       // E.(a+b) = |b|^2 - |a|^2
-    float inv_s = grcp(la + lb);
-    float inv_ab = ia * ib;                          // 1/(|a||b|)
-    float num0 = e2 * la - ea * eab * inv_s;
-    g.i0 = num0 * inv_ab * grcp(del);
-    float invdiff = eab * inv_ab * inv_s;            // 1/|a| - 1/|b|
-    g.i1 = (invdiff - ea * g.i0) * inv_e2;
+    float lab = (ra2 * ia) * (rb2 * ib);             // |a||b|
+    float ab = ax * bx + ay * by + az * bz;
+    float q = ab >= 0.f ? lab + ab : del * grcp(lab - ab);
+    float iq = grcp(fmaxf(q, 1e-37f));
+    g.ja = ia * iq;
+    g.jb = ib * iq;
     return g;
 }
 
@@ -75,12 +76,12 @@ __device__ __forceinline__ EdgeGrad edge_grad(float ax, float ay, float az, floa
 // element); the same formulas and clamps
 typedef float2 f2;
 struct EdgeGrad2 {
-    f2 cx, cy, cz, i0, i1;
+    f2 cx, cy, cz, ja, jb;
 };
 __device__ __forceinline__ f2 mk2(float a) { return make_float2(a, a); }
 __device__ __forceinline__ f2 mx2(f2 a, float lo) { return make_float2(fmaxf(a.x, lo), fmaxf(a.y, lo)); }
 __device__ __forceinline__ EdgeGrad2 edge_grad2(f2 ax, f2 ay, f2 az, f2 bx, f2 by, f2 bz, float ex, float ey,
-                                                float ez, float e2, float inv_e2) {
+                                                float ez) {
     EdgeGrad2 g;
     const f2 EX = mk2(ex), EY = mk2(ey), EZ = mk2(ez);
     g.cx = __ffma2_rn(ay, EZ, __fmul2_rn(az, mk2(-ey)));
@@ -90,16 +91,14 @@ __device__ __forceinline__ EdgeGrad2 edge_grad2(f2 ax, f2 ay, f2 az, f2 bx, f2 b
     const f2 ra2 = mx2(__ffma2_rn(ax, ax, __ffma2_rn(ay, ay, __fmul2_rn(az, az))), 1e-37f);
     const f2 rb2 = mx2(__ffma2_rn(bx, bx, __ffma2_rn(by, by, __fmul2_rn(bz, bz))), 1e-37f);
     const f2 ia = make_float2(grsqrt(ra2.x), grsqrt(ra2.y)), ib = make_float2(grsqrt(rb2.x), grsqrt(rb2.y));
-    const f2 la = __fmul2_rn(ra2, ia), lb = __fmul2_rn(rb2, ib);
-    const f2 ea = __ffma2_rn(EX, ax, __ffma2_rn(EY, ay, __fmul2_rn(EZ, az)));
-    const f2 eab = __ffma2_rn(mk2(2.f), ea, mk2(e2));
-    const f2 sab = __fadd2_rn(la, lb);
-    const f2 inv_s = make_float2(grcp(sab.x), grcp(sab.y));
-    const f2 inv_ab = __fmul2_rn(ia, ib);
-    const f2 num0 = __ffma2_rn(mk2(e2), la, __fmul2_rn(make_float2(-ea.x, -ea.y), __fmul2_rn(eab, inv_s)));
-    g.i0 = __fmul2_rn(__fmul2_rn(num0, inv_ab), make_float2(grcp(del.x), grcp(del.y)));
-    const f2 invdiff = __fmul2_rn(__fmul2_rn(eab, inv_ab), inv_s);
-    g.i1 = __fmul2_rn(__ffma2_rn(make_float2(-ea.x, -ea.y), g.i0, invdiff), mk2(inv_e2));
+    const f2 lab = __fmul2_rn(__fmul2_rn(ra2, ia), __fmul2_rn(rb2, ib));
+    const f2 ab = __ffma2_rn(ax, bx, __ffma2_rn(ay, by, __fmul2_rn(az, bz)));
+    const f2 qp = __fadd2_rn(lab, ab), qm = __fadd2_rn(lab, make_float2(-ab.x, -ab.y));
+    const float q0 = ab.x >= 0.f ? qp.x : del.x * grcp(qm.x);
+    const float q1 = ab.y >= 0.f ? qp.y : del.y * grcp(qm.y);
+    const f2 iq = make_float2(grcp(fmaxf(q0, 1e-37f)), grcp(fmaxf(q1, 1e-37f)));
+    g.ja = __fmul2_rn(ia, iq);
+    g.jb = __fmul2_rn(ib, iq);
     return g;
 }
 
@@ -119,12 +118,11 @@ __global__ void __launch_bounds__(256) grad_p_kernel(const float4 *__restrict__ 
         float4 A = __ldg(&bseq[k - 1]), B = __ldg(&bseq[k]);
         if (B.w == 0.f) continue;
         float ex = B.x - A.x, ey = B.y - A.y, ez = B.z - A.z;
-        float e2 = fmaxf(ex * ex + ey * ey + ez * ez, 1e-37f), inv_e2 = grcp(e2);
 #pragma unroll
         for (int j = 0; j < K; j++) {
             EdgeGrad g = edge_grad(A.x - px[j], A.y - py[j], A.z - pz[j], B.x - px[j], B.y - py[j], B.z - pz[j],
-                                   ex, ey, ez, e2, inv_e2);
-            float w = g.i0 * B.w;
+                                   ex, ey, ez);
+            float w = (g.ja + g.jb) * B.w;
             gx[j] = fmaf(g.cx, w, gx[j]);
             gy[j] = fmaf(g.cy, w, gy[j]);
             gz[j] = fmaf(g.cz, w, gz[j]);
@@ -160,7 +158,6 @@ __global__ void __launch_bounds__(GV_THREADS) grad_v_partial_kernel(const float4
     float4 B = active ? bseq[k] : make_float4(0.f, 0.f, 0.f, 0.f);
     active = active && B.w != 0.f;
     float ex = B.x - A.x, ey = B.y - A.y, ez = B.z - A.z;
-    float e2 = fmaxf(ex * ex + ey * ey + ez * ez, 1e-37f), inv_e2 = grcp(e2);
     float sA[3] = {0.f, 0.f, 0.f}, sB[3] = {0.f, 0.f, 0.f};
     for (int64_t t0 = q0; t0 < q1; t0 += GV_QTILE) {
         __syncthreads();
@@ -178,9 +175,8 @@ __global__ void __launch_bounds__(GV_THREADS) grad_v_partial_kernel(const float4
             int cnt = (int)(q1 - t0 < GV_QTILE ? q1 - t0 : GV_QTILE);
             for (int i = 0; i < cnt; i++) {
                 float4 p = qs[i];
-                EdgeGrad g = edge_grad(A.x - p.x, A.y - p.y, A.z - p.z, B.x - p.x, B.y - p.y, B.z - p.z, ex, ey, ez,
-                                       e2, inv_e2);
-                float wa = -(g.i0 - g.i1) * p.w, wb = -g.i1 * p.w;
+                EdgeGrad g = edge_grad(A.x - p.x, A.y - p.y, A.z - p.z, B.x - p.x, B.y - p.y, B.z - p.z, ex, ey, ez);
+                float wa = -g.ja * p.w, wb = -g.jb * p.w;
                 sA[0] = fmaf(g.cx, wa, sA[0]); sA[1] = fmaf(g.cy, wa, sA[1]); sA[2] = fmaf(g.cz, wa, sA[2]);
                 sB[0] = fmaf(g.cx, wb, sB[0]); sB[1] = fmaf(g.cy, wb, sB[1]); sB[2] = fmaf(g.cz, wb, sB[2]);
             }
@@ -229,7 +225,6 @@ __global__ void __launch_bounds__(GV_THREADS) grad_pv_partial_kernel(const float
     float4 B = active ? bseq[k] : make_float4(0.f, 0.f, 0.f, 0.f);
     active = active && B.w != 0.f;
     float ex = B.x - A.x, ey = B.y - A.y, ez = B.z - A.z;
-    float e2 = fmaxf(ex * ex + ey * ey + ez * ez, 1e-37f), inv_e2 = grcp(e2);
     f2 sA2[3] = {mk2(0.f), mk2(0.f), mk2(0.f)}, sB2[3] = {mk2(0.f), mk2(0.f), mk2(0.f)};
     for (int64_t t0 = q0; t0 < q1; t0 += GV_QTILE) {
         __syncthreads();
@@ -255,10 +250,10 @@ __global__ void __launch_bounds__(GV_THREADS) grad_pv_partial_kernel(const float
                     EdgeGrad2 g = edge_grad2(make_float2(A.x - pa.x, A.x - pb.x), make_float2(A.y - pa.y, A.y - pb.y),
                                              make_float2(A.z - pa.z, A.z - pb.z), make_float2(B.x - pa.x, B.x - pb.x),
                                              make_float2(B.y - pa.y, B.y - pb.y), make_float2(B.z - pa.z, B.z - pb.z),
-                                             ex, ey, ez, e2, inv_e2);
-                    const f2 wa = __fmul2_rn(__fadd2_rn(g.i1, make_float2(-g.i0.x, -g.i0.y)), pw);
-                    const f2 wb = __fmul2_rn(make_float2(-g.i1.x, -g.i1.y), pw);
-                    const f2 wp = __fmul2_rn(__fmul2_rn(g.i0, mk2(B.w)), pw);
+                                             ex, ey, ez);
+                    const f2 wa = __fmul2_rn(make_float2(-g.ja.x, -g.ja.y), pw);
+                    const f2 wb = __fmul2_rn(make_float2(-g.jb.x, -g.jb.y), pw);
+                    const f2 wp = __fmul2_rn(__fmul2_rn(__fadd2_rn(g.ja, g.jb), mk2(B.w)), pw);
                     sA2[0] = __ffma2_rn(g.cx, wa, sA2[0]); sA2[1] = __ffma2_rn(g.cy, wa, sA2[1]);
                     sA2[2] = __ffma2_rn(g.cz, wa, sA2[2]);
                     sB2[0] = __ffma2_rn(g.cx, wb, sB2[0]); sB2[1] = __ffma2_rn(g.cy, wb, sB2[1]);

@@ -112,9 +112,14 @@ __device__ __forceinline__ float branch_fix(float th, int s_num) {
 // float32 projection (fa*, fb*), the values their other edge uses, so the
 // first-order cancellation of their rounding between their two edges holds.
 // The decision depends only on the vertex and the query, so both edges of a
-// vertex make the same one.
+// vertex make the same one.  A spindle edge (p close to the edge relative to
+// its length: a and b nearly opposite) takes both endpoints in float64: its
+// angle rests on the small sum of their directions, which float32 rounding
+// would perturb by ~u / sqrt(2 (1 + cos phi)); the float32/float64 mismatch
+// this leaves at a shared endpoint moves that endpoint's direction by ~u,
+// which changes w by ~u only.
 static __device__ __noinline__ float slow_theta(float4 va, float4 vb, float fa1, float fa2, float fsa, float fb1,
-                                                float fb2, float fsb, float3 p, Frame fr, Frame64 f,
+                                                float fb2, float fsb, float3 p, Frame fr, Frame64 f, bool spindle,
                                                 unsigned long long *cnt, int *status) {
     float3 A = make_float3(va.x, va.y, va.z), B = make_float3(vb.x, vb.y, vb.z);
     float3 D = make_float3(fr.d[0], fr.d[1], fr.d[2]);
@@ -132,8 +137,13 @@ static __device__ __noinline__ float slow_theta(float4 va, float4 vb, float fa1,
         double an = x[0] * f.n[0] + x[1] * f.n[1] + x[2] * f.n[2];
         double rp = a1 * a1 + a2 * a2;
         bool near = an < 0.0 && rp < 4e-8 * (rp + an * an);          // sin^2 < T^2
-        if (!near) {
+        if (!near && !spindle) {
             x1[e] = f1[e]; x2[e] = f2v[e]; xs[e] = fs[e];
+            continue;
+        }
+        if (!near) {                                                  // spindle edge: float64 endpoint
+            double r = sqrt(rp + an * an);
+            x1[e] = a1; x2[e] = a2; xs[e] = an >= 0.0 ? r + an : rp / (r - an);
             continue;
         }
         if (on_forward_ray(X, p, D)) {
@@ -211,7 +221,8 @@ __device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) { return __ffma2_rn(a, b, c
 struct PackedConsts {
     f2 c[9];
     f2 pi;
-    f2 near2n;   // -(1.01 T)^2
+    f2 nearv;    // -T^2 / 2: a vertex within T of the forward ray
+    f2 spin;     // -tau: an edge seen from p at an angle within ~sqrt(tau) of pi
     f2 cut2n;    // -1e-4
 };
 
@@ -226,9 +237,9 @@ __device__ __forceinline__ float frsqrt(float x) {
 
 // One boundary record seen from a query pair: frame coordinates (a1, a2),
 // stereographic scale s = |a| + a_n (or |a_perp|^2 / (|a| - a_n) when
-// a_n < 0) and |a|^2.
+// a_n < 0) and q = s |a|.
 struct VState {
-    f2 a1, a2, s, r2;
+    f2 a1, a2, s, q;
 };
 
 // Frame coordinates of a = A - p as double-float differences: the record
@@ -242,7 +253,11 @@ struct QPair {
     f2 n1h, n2h, nnh, n1l, n2l, nnl;      // -(p.e1), -(p.e2), -(p.n) as hi + lo, two queries
 };
 
-__device__ __forceinline__ void project(float4 rh, float4 rl, const QPair &Q, VState &o) {
+// The sign bits of f0 / f1 are set when the vertex lies within T of the
+// forward ray of query element 0 / 1: there 1 + a_n/|a| ~ delta^2 / 2, so the
+// test is s < (T^2 / 2) |a|.
+__device__ __forceinline__ void project(float4 rh, float4 rl, const QPair &Q, VState &o, const PackedConsts &K,
+                                        unsigned &f0, unsigned &f1) {
     f2 h1 = pk(rh.x, rh.x), h2 = pk(rh.y, rh.y), hn = pk(rh.z, rh.z);
     f2 l1 = pk(rl.x, rl.x), l2 = pk(rl.y, rl.y), ln = pk(rl.z, rl.z);
     o.a1 = add2(add2(h1, Q.n1h), add2(l1, Q.n1l));
@@ -251,11 +266,14 @@ __device__ __forceinline__ void project(float4 rh, float4 rl, const QPair &Q, VS
     f2 rp = fma2(o.a1, o.a1, mul2(o.a2, o.a2));
     f2 r2 = fma2(an, an, rp);
     float r20 = fmaxf(lo2(r2), 1e-37f), r21 = fmaxf(hi2(r2), 1e-37f);
-    o.r2 = pk(r20, r21);
-    f2 r = mul2(o.r2, pk(frsqrt(r20), frsqrt(r21)));
+    f2 r = mul2(pk(r20, r21), pk(frsqrt(r20), frsqrt(r21)));
     f2 sp = add2(r, an), dm = sub2(r, an);
     f2 sn = mul2(rp, pk(frcp(lo2(dm)), frcp(hi2(dm))));
     o.s = pk(lo2(an) >= 0.f ? lo2(sp) : lo2(sn), hi2(an) >= 0.f ? hi2(sp) : hi2(sn));
+    o.q = mul2(o.s, r);
+    f2 tv = fma2(r, K.nearv, o.s);
+    f0 |= __float_as_uint(lo2(tv));
+    f1 |= __float_as_uint(hi2(tv));
 }
 
 // -(p.e) as hi + lo from float32 arithmetic: exact products (FMA), TwoSum
@@ -281,8 +299,15 @@ __device__ __forceinline__ void neg_dot_df(float3 p, const float e[3], float &hi
 // f0 / f1 get a set sign bit when element 0 / 1 needs the slow path:
 //   cut:  den < 0 and num^2 < 1e-4 |z|^2 (|Omega/2| within ~0.01 of pi: the
 //         ray passes close to the edge, the branch needs the exact sign);
-//   near: |z|^2 < (1.01 T)^2 |a|^2 |b|^2 (an endpoint within T of the forward
-//         ray, T = 1e-6 here).
+//   spindle: |z|^2 < tau q_a q_b.  Since |z|^2 = 2 (1 + a.b/(|a||b|)) q_a q_b
+//         (q = s |a|), this holds when the edge is seen from p at an angle
+//         phi with 2 (1 + cos phi) < tau: p close to the edge relative to
+//         the edge's length.  There a and b are nearly opposite and the plane
+//         they span (the great circle of the edge's image) rests on their
+//         small sum, whose float32 rounding error grows like
+//         1 / sqrt(2 (1 + cos phi)); with tau = 1e-2 the float32 error of
+//         an unflagged edge stays below ~1e-7 in w.
+// (Vertices near the forward ray are flagged in project.)
 __device__ __forceinline__ f2 edge_theta(const VState &P, const VState &Q, const PackedConsts &K, unsigned &f0,
                                          unsigned &f1) {
     f2 num = sub2(mul2(P.a1, Q.a2), mul2(P.a2, Q.a1));
@@ -307,7 +332,7 @@ __device__ __forceinline__ f2 edge_theta(const VState &P, const VState &Q, const
     f2 cpi = make_float2(copysignf(lo2(K.pi), num.x), copysignf(hi2(K.pi), num.y));   // copysign(pi, num)
     f2 neg = sub2(cpi, a2);
     f2 tc = fma2(z2, K.cut2n, nn);
-    f2 ts = fma2(mul2(P.r2, Q.r2), K.near2n, z2);
+    f2 ts = fma2(mul2(P.q, Q.q), K.spin, z2);
     f0 = (__float_as_uint(lo2(den)) & __float_as_uint(lo2(tc))) | __float_as_uint(lo2(ts));
     f1 = (__float_as_uint(hi2(den)) & __float_as_uint(hi2(tc))) | __float_as_uint(hi2(ts));
     float d0 = lo2(den), d1 = hi2(den);
@@ -323,7 +348,7 @@ __device__ __forceinline__ void bterm_step(const VState (&P)[KP], VState (&Q)[KP
                                            const QPair (&qp)[KP], f2 (&sum)[KP], f2 (&cmp)[KP],
                                            unsigned (&fl)[KP][2], const PackedConsts &K) {
 #pragma unroll
-    for (int j = 0; j < KP; j++) project(rh, rl, qp[j], Q[j]);
+    for (int j = 0; j < KP; j++) project(rh, rl, qp[j], Q[j], K, fl[j][0], fl[j][1]);
     float4 vq = rh;
     if (vq.w == 0.f) return;                  // first record of a loop (uniform)
 #pragma unroll
@@ -374,7 +399,7 @@ __global__ void __launch_bounds__(256, MINB) bterm3d_kernel(const float4 *__rest
         {
             float4 rh = __ldg(&bframe[0]), rl = __ldg(&bframe[1]);
 #pragma unroll
-            for (int j = 0; j < KP; j++) project(rh, rl, qp[j], SA[j]);
+            for (int j = 0; j < KP; j++) project(rh, rl, qp[j], SA[j], K, fl[j][0], fl[j][1]);
         }
         int k = 1;
         for (; k + 1 < nb; k += 2) {         // two records per trip: SA -> SB -> SA
@@ -429,7 +454,7 @@ cudaError_t launch_bframe(const float4 *bseq, int64_t n, const Frame &fr, float4
 
 // ---- careful pass: deferred queries, scalar ------------------------------------
 struct VState1 {
-    float a1, a2, s, r2;
+    float a1, a2, s, r2, q;
 };
 
 __device__ __forceinline__ VState1 project1(float4 v, float3 p, const Frame &fr) {
@@ -442,12 +467,14 @@ __device__ __forceinline__ VState1 project1(float4 v, float3 p, const Frame &fr)
     o.r2 = fmaxf(fmaf(an, an, rp), 1e-37f);
     float r = o.r2 * frsqrt(o.r2);
     o.s = an >= 0.f ? r + an : rp * frcp(r - an);
+    o.q = o.s * r;
     return o;
 }
 
 // the same float32 formulation as edge_theta (one element), with the
-// flagged cases resolved: float64 near the forward ray, exact branch at the
-// cut
+// flagged cases resolved: float64 near the forward ray and for spindle edges
+// (2 (1 + cos phi) < 2e-2, twice the main pass's bar, for the plain float32
+// projections here), exact branch at the cut
 __device__ __forceinline__ float edge_theta_careful(const VState1 &A, const VState1 &B, float4 va, float4 vb,
                                                     float3 p, const Frame &fr, const Frame64 &f64,
                                                     unsigned long long *cnt, int *status) {
@@ -455,8 +482,9 @@ __device__ __forceinline__ float edge_theta_careful(const VState1 &A, const VSta
     float den = fmaf(A.s, B.s, fmaf(A.a1, B.a1, A.a2 * B.a2));
     float nn = num * num;
     float z2 = fmaf(den, den, nn);
-    if (fmaf(A.r2 * B.r2, -4.1e-8f, z2) < 0.f)           // T = 2e-4 for float32 projections
-        return slow_theta(va, vb, A.a1, A.a2, A.s, B.a1, B.a2, B.s, p, fr, f64, cnt, status);
+    bool spindle = fmaf(A.q * B.q, -2e-2f, z2) < 0.f;
+    if (spindle || fmaf(A.r2 * B.r2, -4.1e-8f, z2) < 0.f)    // T = 2e-4 for float32 projections
+        return slow_theta(va, vb, A.a1, A.a2, A.s, B.a1, B.a2, B.s, p, fr, f64, spindle, cnt, status);
     float zc = fmaxf(z2, 1e-37f);
     float v = num * frcp(zc * frsqrt(zc) + fabsf(den));
     float v2 = v * v;
@@ -562,7 +590,8 @@ static cudaError_t launch_bt(const float4 *bseq, const float4 *bframe, int64_t n
                         GWN_AT_C8};
     for (int i = 0; i < 9; i++) K.c[i] = dup(c[i]);
     K.pi = dup(3.14159265358979f);
-    K.near2n = dup(-1.0201e-12f);   // -(1.01 T)^2, T = 1e-6 (double-float projections)
+    K.nearv = dup(-5e-13f);         // -T^2 / 2, T = 1e-6 (double-float projections)
+    K.spin = dup(-1e-2f);           // tau
     K.cut2n = dup(-1e-4f);
     cudaError_t e = cudaMemsetAsync(defer_count, 0, sizeof(int32_t), st);
     if (e != cudaSuccess) return e;

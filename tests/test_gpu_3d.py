@@ -92,31 +92,41 @@ def test_small_cap_full_grid(gwn, ctx):
     assert st["n_pairs"] == len(P) * mesh.info()["n_boundary_edges"]
 
 
-def _fp32_bound(V, F, P):
-    """Conditioning of the float32 boundary term: rounding a = A - p, b = B - p
-    (relative 2^-24 each) moves an edge's line by ~2^-24 (|a| + |b|) near p,
-    which changes its angle by that over h, p's distance to the edge.  Summed
-    over the boundary (with multiplicity), with a factor 2 for the projection
-    and the atan2: |dw| <= 1e-6 + (2^-22 / 2pi) sum_e m_e (|a_e| + |b_e|) / h_e.
-    For the workloads (edges <= 0.03 long, queries >= 1e-4 diag from M) the
-    sum term is far below 1e-6; it matters for long edges passing near p."""
-    src, dst, m = oracle.boundary_edges(F)
-    A = V[src].astype(np.float64)
-    B = V[dst].astype(np.float64)
-    out = np.empty(len(P))
-    for i, p in enumerate(P.astype(np.float64)):
-        a, b = A - p, B - p
-        E = B - A
-        t = np.clip(-(a * E).sum(1) / np.maximum((E * E).sum(1), 1e-300), 0, 1)
-        h = np.linalg.norm(a + t[:, None] * E, axis=1)
-        out[i] = 1e-6 + 2.0 ** -22 / (2 * np.pi) * (m * (np.linalg.norm(a, axis=1) + np.linalg.norm(b, axis=1))
-                                                     / np.maximum(h, 1e-9)).sum()
-    return out
+def test_queries_beside_long_edges(gwn, ctx):
+    """A 2 x 2 square (two triangles, four boundary edges of length 2) seen
+    from queries 3e-4 .. 1e-2 from the interior of its boundary edges, on
+    their outer side in every direction about the edge: a and b nearly
+    opposite, the float32 boundary term's worst conditioning.  |dw| <= 1e-6 on every query."""
+    V = np.array([[-1, -1, 0], [1, -1, 0], [1, 1, 0], [-1, 1, 0]], np.float32)
+    F = np.array([[0, 1, 2], [0, 2, 3]], np.int32)
+    rng = np.random.default_rng(21)
+    n = 4000
+    e = rng.integers(0, 4, n)
+    t = rng.uniform(-0.9, 0.9, n)
+    h = 10 ** rng.uniform(np.log10(3e-4), -2, n)
+    # edge k runs along axis (k % 2) at the fixed other coordinate +-1
+    along = np.where(e % 2 == 0, 0, 1)
+    other = np.where((e == 0) | (e == 3), -1.0, 1.0)
+    ang = rng.uniform(-np.pi / 2, np.pi / 2, n)       # on the outer side of the edge: distance h from M
+    P = np.zeros((n, 3))
+    P[np.arange(n), along] = t
+    P[np.arange(n), 1 - along] = other * (1.0 + h * np.cos(ang))
+    P[:, 2] = h * np.sin(ang)
+    P = P.astype(np.float32)
+    for s in range(3):
+        d = gen.random_direction(300 + s)
+        r = _run(gwn, ctx, V, F, P, d)
+        keep = _check(V, F, P, d, r)
+        assert keep.mean() > 0.95
 
 
 def test_soups_with_multiplicities(gwn, ctx):
-    """Random soups: long edges (up to ~5 units) pass close to queries, so the
-    bar is the float32 conditioning bound of _fp32_bound (>= 1e-6)."""
+    """Random soups (non-manifold, repeated faces): long edges (up to ~5
+    units) pass close to queries, the case where a float32 boundary term is
+    ill-conditioned (a and b nearly opposite); the library recomputes those
+    pairs in float64, so the bar is the workload bar, 1e-6, on every query
+    beyond 1e-4 x diagonal, against both the one-shot oracle and the
+    definition."""
     rng = np.random.default_rng(11)
     for trial in range(3):
         V = rng.standard_normal((40, 3)).astype(np.float32)
@@ -126,16 +136,10 @@ def test_soups_with_multiplicities(gwn, ctx):
         P = (2.5 * rng.standard_normal((3000, 3))).astype(np.float32)
         d = gen.random_direction(200 + trial)
         r = _run(gwn, ctx, V, F, P, d)
-        wo, chio, Bo = oracle.w3d_oneshot(V, F, P, d)
-        assert np.array_equal(r["chi"], chio)
-        keep = oracle.dist3d(V, F, P) > 1e-4 * _diag(V)
-        bound = _fp32_bound(V, F, P)
-        err = np.abs(r["w"].astype(np.float64) - wo)
-        assert np.all(err[keep] <= bound[keep]), (err[keep] / bound[keep]).max()
+        keep = _check(V, F, P, d, r)
         wv = oracle.w3d_vos(V, F, P)
-        assert np.all(np.abs(r["w"] - wv)[keep] <= bound[keep])
-        # most queries meet the workload bar itself
-        assert np.mean(err[keep] <= TOL) > 0.999
+        errv = np.abs(r["w"].astype(np.float64) - wv)[keep]
+        assert errv.max() <= TOL, errv.max()
 
 
 def test_near_cut_and_axis_directions(gwn, ctx):
