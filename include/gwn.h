@@ -120,6 +120,9 @@ typedef struct gwn_stats {
                                      full predicates (plus any query recounted whole when the pair list is full) */
     int64_t n_deferred_boundary;  /* queries whose boundary term was recomputed by the careful pass */
     int64_t n_root_iters;         /* 2D: safeguarded Newton steps over all roots (n_tri_tests counts the roots) */
+    int64_t n_cert;               /* 2D: crossings (or rows at a rounded extremum value) decided again in float64
+                                     because a query lies within their float error bound */
+    int64_t n_cert_fixed;         /* 2D: query counts that float64 decision changed */
 } gwn_stats;
 
 /* Geometry summary. */

@@ -77,7 +77,7 @@ def _load():
                 "oracle_grad3d_vos": (I, [P, I64, P, I64, P, I64, P, P, P, I]),
                 "oracle_w2d_quad": (None, [P, I64, P, I64, P, C.c_double, I]),
                 "oracle_w2d_alg1": (None, [P, I64, P, I64, P, I]),
-                "oracle_w2d_closed_x": (None, [P, I64, P, I64, P, P, I]),
+                "oracle_w2d_closed_x": (None, [P, I64, P, I64, P, P, P, I]),
                 "oracle_sign_edge": (I, [P, P, P, P]),
                 "oracle_exact_det_abd": (I, [P, P, P, P]),
                 "oracle_sign_orient": (I, [P, P, P, P]),
@@ -323,14 +323,20 @@ def w2d_alg1(ctrl, P, threads: int | None = None) -> np.ndarray:
     return w
 
 
-def w2d_closed_x(ctrl, P, threads: int | None = None):
-    """Returns (w, chi) with chi = crossings of the +x ray with chain + chord."""
+def w2d_closed_x(ctrl, P, threads: int | None = None, want_unc: bool = False):
+    """Returns (w, chi) with chi = crossings of the +x ray with chain + chord
+    (and, with want_unc, a bool array marking the queries whose count is not
+    certified: a crossing, or the chord, within its float64 error bound of
+    the query -- the query lies on the geometry at float64 resolution)."""
     ctrl, nseg = _chain(ctrl)
     P = _f64(P)
     w = np.empty(len(P), np.float64)
     chi = np.empty(len(P), np.int32)
-    _load().oracle_w2d_closed_x(_ptr(ctrl), nseg, _ptr(P), len(P), _ptr(w), _ptr(chi),
+    unc = np.zeros(len(P), np.int8)
+    _load().oracle_w2d_closed_x(_ptr(ctrl), nseg, _ptr(P), len(P), _ptr(w), _ptr(chi), _ptr(unc),
                                 threads or default_threads())
+    if want_unc:
+        return w, chi, unc.astype(bool)
     return w, chi
 
 

@@ -29,6 +29,7 @@
  *     region, counts propagated across the arcs by Lemma 2, area-weighted
  *     sum of Eq. wn_discrete_sum), for tiny inputs.
  */
+#include <float.h>
 #include <math.h>
 #include <pthread.h>
 #include <stdint.h>
@@ -806,13 +807,33 @@ ORACLE_API void oracle_w2d_quad(const double *ctrl, int64_t nseg, const double *
  * half-open rule of a ray perturbed towards g > 0 (the ray is taken as
  * g = 0+): an interval from g(u0) to g(u1) holds a crossing iff
  * min(g0, g1) <= 0 < max(g0, g1).  Returns the number of crossings; for
- * each, the parameter and the direction (+1 when g increases). */
+ * each, the parameter, the direction (+1 when g increases) and a
+ * certification radius in u: the exact root lies within rad[i] of us[i]
+ * (INFINITY when that cannot be bounded, or when the interval's end value at
+ * an interior cut is within its evaluation error of zero, so that even the
+ * existence of the crossing is uncertain). */
 static double bern3(const double *g, double u) {
     double v = 1.0 - u;
     return v * v * v * g[0] + 3 * u * v * v * g[1] + 3 * u * u * v * g[2] + u * u * u * g[3];
 }
 
-static int monotone_crossings(const double *g, double *us, int *dirs) {
+/* derivative of the cubic Bernstein polynomial, and a bound on |second
+ * derivative| over [0, 1] */
+static double bern3_d(const double *g, double u) {
+    double v = 1.0 - u;
+    return 3.0 * ((g[1] - g[0]) * v * v + 2.0 * (g[2] - g[1]) * u * v + (g[3] - g[2]) * u * u);
+}
+static double bern3_d2max(const double *g) {
+    double a = fabs(g[2] - 2.0 * g[1] + g[0]), b = fabs(g[3] - 2.0 * g[2] + g[1]);
+    return 6.0 * (a > b ? a : b);
+}
+/* bound on the float64 evaluation error of bern3 (and of forming the
+ * coefficients by one subtraction each) */
+static double bern3_err(const double *g) {
+    return 12.0 * DBL_EPSILON * (fabs(g[0]) + fabs(g[1]) + fabs(g[2]) + fabs(g[3]));
+}
+
+static int monotone_crossings(const double *g, double *us, int *dirs, double *rad) {
     /* derivative coefficients (quadratic Bernstein, times 3) */
     double d0 = g[1] - g[0], d1 = g[2] - g[1], d2 = g[3] - g[2];
     /* power basis of d(u) = d0 (1-u)^2 + 2 d1 u (1-u) + d2 u^2 */
@@ -836,14 +857,35 @@ static int monotone_crossings(const double *g, double *us, int *dirs) {
     if (nr == 2 && r[0] > r[1]) { double t = r[0]; r[0] = r[1]; r[1] = t; }
     for (int i = 0; i < nr; i++) if (r[i] > 0.0 && r[i] < 1.0) cuts[nc++] = r[i];
     cuts[nc++] = 1.0;
+    const double eg = bern3_err(g), m2 = bern3_d2max(g);
     int n = 0;
     for (int i = 0; i + 1 < nc; i++) {
         double u0 = cuts[i], u1 = cuts[i + 1];
         double g0 = bern3(g, u0), g1 = bern3(g, u1);
         if (i == 0) g0 = g[0];
         if (i + 2 == nc) g1 = g[3];
+        /* an end at an interior cut (an extremum of g) is only known to eg:
+         * whether the interval crosses zero there is uncertain, and so are the
+         * crossings within du of the cut, du the half-width of the
+         * neighbourhood where |g| <= 2 eg (found by doubling) */
+        double uc = -1.0, du = 0.0;
+        if (i > 0 && fabs(g0) <= eg) uc = u0;
+        else if (i + 2 < nc && fabs(g1) <= eg) uc = u1;
+        if (uc >= 0.0) {
+            du = 1e-17;
+            while (du < 1.0 && (fabs(bern3(g, uc - du)) <= 2.0 * eg || fabs(bern3(g, uc + du)) <= 2.0 * eg))
+                du *= 2.0;
+        }
         double lo = g0 < g1 ? g0 : g1, hi = g0 < g1 ? g1 : g0;
-        if (!(lo <= 0.0 && 0.0 < hi)) continue;
+        if (!(lo <= 0.0 && 0.0 < hi)) {
+            if (uc >= 0.0) {            /* a crossing the rounding may have hidden */
+                us[n] = uc;
+                dirs[n] = 0;
+                rad[n] = du;
+                n++;
+            }
+            continue;
+        }
         double a = u0, b = u1;
         int inc = g1 > g0;
         for (int it = 0; it < 200 && b - a > 0.0; it++) {
@@ -852,37 +894,55 @@ static int monotone_crossings(const double *g, double *us, int *dirs) {
             double gm = bern3(g, m);
             if ((gm > 0.0) == inc) b = m; else a = m;
         }
-        us[n] = 0.5 * (a + b);
+        double u = 0.5 * (a + b);
+        us[n] = u;
         dirs[n] = inc ? 1 : -1;
+        /* the exact root: g changes by at least |g'(u)|/2 per unit of u within
+         * del of u when m2 del <= |g'(u)|/2, so it lies within
+         * del = 2 (|g(u)| + eg) / |g'(u)| of u (the derivative's own error
+         * taken off first) */
+        double dg = fabs(bern3_d(g, u)) - 12.0 * DBL_EPSILON * (fabs(d0) + fabs(d1) + fabs(d2)) * 3.0;
+        double del = dg > 0.0 ? 2.0 * (fabs(bern3(g, u)) + eg) / dg : INFINITY;
+        if (!(m2 * del <= 0.5 * dg)) del = INFINITY;
+        if (del < b - a) del = b - a;
+        if (uc >= 0.0) {                /* the crossing itself may be spurious */
+            double r2 = fabs(u - uc) + du;
+            if (r2 > del) del = r2;
+        }
+        rad[n] = del;
         n++;
     }
     return n;
 }
 
 /* signed crossings of the ray p + t q (t > 0) with one cubic segment; the
- * ray is perturbed to its left (towards cross(q, x - p) > 0). */
-static int seg_ray_crossings(const double *c, const double *p, const double *q) {
-    double g[4];
+ * ray is perturbed to its left (towards cross(q, x - p) > 0).  *unc is set
+ * when a crossing lies within its certification bound of p along the ray (or
+ * its existence is uncertain): the count is then not certified. */
+static int seg_ray_crossings(const double *c, const double *p, const double *q, int *unc) {
+    double g[4], h[4];
     for (int k = 0; k < 4; k++) {
         double x = c[2 * k] - p[0], y = c[2 * k + 1] - p[1];
         g[k] = q[0] * y - q[1] * x;            /* cross(q, B_k - p) */
+        h[k] = q[0] * x + q[1] * y;            /* (B_k - p) . q: position along the ray */
     }
-    double us[3];
+    double us[3], rad[3];
     int dirs[3];
-    int n = monotone_crossings(g, us, dirs);
+    int n = monotone_crossings(g, us, dirs, rad);
+    const double eh = bern3_err(h), m2h = bern3_d2max(h);
     int chi = 0;
     for (int i = 0; i < n; i++) {
-        double x, y;
-        bez_eval(c, us[i], &x, &y);
-        double t = (x - p[0]) * q[0] + (y - p[1]) * q[1];
+        double t = bern3(h, us[i]);
+        double band = (fabs(bern3_d(h, us[i])) + m2h * rad[i]) * rad[i] + eh;
+        if (unc && !(fabs(t) > band)) *unc = 1;
         if (t > 0.0) chi += dirs[i];
     }
     return chi;
 }
 
-static int chain_ray_crossings(const double *ctrl, int64_t nseg, const double *p, const double *q) {
+static int chain_ray_crossings(const double *ctrl, int64_t nseg, const double *p, const double *q, int *unc) {
     int chi = 0;
-    for (int64_t s = 0; s < nseg; s++) chi += seg_ray_crossings(ctrl + 6 * s, p, q);
+    for (int64_t s = 0; s < nseg; s++) chi += seg_ray_crossings(ctrl + 6 * s, p, q, unc);
     return chi;
 }
 
@@ -913,12 +973,12 @@ static void alg1_range(void *pv, int64_t lo, int64_t hi) {
         if (L1 >= L2) {
             mid = ae + 0.5 * L1;
             double q[2] = {cos(mid), sin(mid)};
-            chi1 = chain_ray_crossings(c->ctrl, c->nseg, p, q);
+            chi1 = chain_ray_crossings(c->ctrl, c->nseg, p, q, NULL);
             chi2 = chi1 + 1;
         } else {
             mid = as + 0.5 * L2;
             double q[2] = {cos(mid), sin(mid)};
-            chi2 = chain_ray_crossings(c->ctrl, c->nseg, p, q);
+            chi2 = chain_ray_crossings(c->ctrl, c->nseg, p, q, NULL);
             chi1 = chi2 - 1;
         }
         c->w[qi] = (L1 * chi1 + L2 * chi2) / (2 * M_PI);
@@ -937,16 +997,19 @@ ORACLE_API void oracle_w2d_alg1(const double *ctrl, int64_t nseg, const double *
  *   w = chi_x(C) + chi_x(chord e->s) + atan2(cross(s-p, e-p), dot(s-p, e-p))/2pi.
  * chi_out receives chi_x(C) + chi_x(chord). */
 typedef struct {
-    const double *ctrl; int64_t nseg; const double *P; double *w; int32_t *chi;
+    const double *ctrl; int64_t nseg; const double *P; double *w; int32_t *chi; int8_t *unc;
 } cx_ctx;
 
-static int chord_crossing_x(const double *e, const double *s, const double *p) {
+static int chord_crossing_x(const double *e, const double *s, const double *p, int *unc) {
     /* segment e -> s against the ray p + t(1,0), perturbed to y_p + 0 */
     double y0 = e[1] - p[1], y1 = s[1] - p[1];
     double lo = y0 < y1 ? y0 : y1, hi = y0 < y1 ? y1 : y0;
     if (!(lo <= 0.0 && 0.0 < hi)) return 0;
-    /* x at y = y_p on the segment, compared with x_p via the orientation */
-    double cr = (e[0] - p[0]) * (s[1] - p[1]) - (e[1] - p[1]) * (s[0] - p[0]);
+    /* x at y = y_p on the segment, compared with x_p via the orientation;
+     * the sign of cr is certified beyond its rounding bound */
+    double t1 = (e[0] - p[0]) * (s[1] - p[1]), t2 = (e[1] - p[1]) * (s[0] - p[0]);
+    double cr = t1 - t2;
+    if (unc && !(fabs(cr) > 8.0 * DBL_EPSILON * (fabs(t1) + fabs(t2)))) *unc = 1;
     int up = y1 > y0;
     /* the crossing is to the right of p iff p is left of the upward segment */
     int right = up ? (cr > 0) : (cr < 0);
@@ -960,7 +1023,9 @@ static void cx_range(void *pv, int64_t lo, int64_t hi) {
     const double q[2] = {1.0, 0.0};
     for (int64_t qi = lo; qi < hi; qi++) {
         const double *p = c->P + 2 * qi;
-        int chi = chain_ray_crossings(c->ctrl, c->nseg, p, q) + chord_crossing_x(e, s, p);
+        int unc = 0;
+        int chi = chain_ray_crossings(c->ctrl, c->nseg, p, q, &unc) + chord_crossing_x(e, s, p, &unc);
+        if (c->unc) c->unc[qi] = (int8_t)unc;
         double sx = s[0] - p[0], sy = s[1] - p[1], ex = e[0] - p[0], ey = e[1] - p[1];
         double ang = atan2(sx * ey - sy * ex, sx * ex + sy * ey);
         c->w[qi] = (double)chi + ang / (2 * M_PI);
@@ -969,15 +1034,15 @@ static void cx_range(void *pv, int64_t lo, int64_t hi) {
 }
 
 ORACLE_API void oracle_w2d_closed_x(const double *ctrl, int64_t nseg, const double *P, int64_t nq,
-                                    double *w, int32_t *chi, int nthreads) {
-    cx_ctx c = {ctrl, nseg, P, w, chi};
+                                    double *w, int32_t *chi, int8_t *unc, int nthreads) {
+    cx_ctx c = {ctrl, nseg, P, w, chi, unc};
     parallel_for(nq, nthreads, cx_range, &c);
 }
 
 /* signed crossings of an arbitrary ray with a chain (exposed for tests) */
 ORACLE_API int oracle_chain_ray_crossings(const double *ctrl, int64_t nseg, const double *p,
                                           const double *q) {
-    return chain_ray_crossings(ctrl, nseg, p, q);
+    return chain_ray_crossings(ctrl, nseg, p, q, NULL);
 }
 
 /* ======================================================================== */

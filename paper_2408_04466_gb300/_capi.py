@@ -28,7 +28,8 @@ class gwn_stats(C.Structure):
                 ("n_fp64_filter", C.c_int64), ("n_exact", C.c_int64), ("n_stack_overflow", C.c_int64),
                 ("n_tri_tests", C.c_int64), ("ms_prepare", C.c_float), ("ms_traverse", C.c_float),
                 ("ms_boundary", C.c_float), ("ms_total", C.c_float), ("n_deferred_traverse", C.c_int64),
-                ("n_deferred_boundary", C.c_int64), ("n_root_iters", C.c_int64)]
+                ("n_deferred_boundary", C.c_int64), ("n_root_iters", C.c_int64), ("n_cert", C.c_int64),
+                ("n_cert_fixed", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

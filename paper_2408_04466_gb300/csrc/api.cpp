@@ -305,6 +305,8 @@ GWN_API gwn_status gwn_ctx_create(gwn_ctx **out, int device, void *cuda_stream) 
     if (e == cudaSuccess) e = cudaMalloc(&c->d_tpairs, sizeof(int2) * GWN_TPAIR_CAP);
     if (e == cudaSuccess) e = cudaMalloc(&c->d_tpair_count, sizeof(int32_t));
     if (e == cudaSuccess) e = cudaMalloc(&c->d_work_counter, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_cert, sizeof(int4) * 2 * GWN_CERT_CAP);
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_cert_count, sizeof(int32_t));
     if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(c->d_cnt, 0, sizeof(unsigned long long) * CNT_NUM);
     for (int i = 0; i < 8 && e == cudaSuccess; i++) e = cudaEventCreate(&c->ev[i]);
@@ -335,6 +337,11 @@ GWN_API gwn_status gwn_ctx_check(gwn_ctx *ctx) {
     if (st & ST_TIMEOUT) { set_error("device iteration limit reached"); return GWN_E_TIMEOUT; }
     if (st & ST_EXPANSION_OVERFLOW) { set_error("exact predicate expansion overflow"); return GWN_E_INTERNAL; }
     if (st & ST_BAD_INPUT) { set_error("invalid input detected on device"); return GWN_E_INVALID; }
+    if (st & ST_CERT_OVERFLOW) {
+        set_error("2D certification list overflow: crossing counts of queries within float rounding of a curve "
+                  "may be off");
+        return GWN_E_INTERNAL;
+    }
     return GWN_OK;
 }
 
@@ -355,6 +362,8 @@ static void ctx_release(gwn_ctx *ctx) {
     if (ctx->d_tpairs) cudaFree(ctx->d_tpairs);
     if (ctx->d_tpair_count) cudaFree(ctx->d_tpair_count);
     if (ctx->d_work_counter) cudaFree(ctx->d_work_counter);
+    if (ctx->d_cert) cudaFree(ctx->d_cert);
+    if (ctx->d_cert_count) cudaFree(ctx->d_cert_count);
     for (auto &c : ctx->axis_cache)
         if (c.dev) cudaFree(c.dev);
     if (ctx->events)
@@ -439,6 +448,10 @@ static void free_geom_device(gwn_geom *g) {
     if (cs.piece_yT && cs.piece_yT != (void *)cs.piece_y) cudaFree(cs.piece_yT);
     if (cs.piece_xT) cudaFree(cs.piece_xT);
     if (cs.piece_rec) cudaFree(cs.piece_rec);
+    if (cs.piece_seg) cudaFree(cs.piece_seg);
+    if (cs.piece_u) cudaFree(cs.piece_u);
+    if (cs.piece_part) cudaFree(cs.piece_part);
+    if (cs.piece_eps) cudaFree(cs.piece_eps);
     if (cs.bucket_off) cudaFree(cs.bucket_off);
     if (cs.bucket_idx) cudaFree(cs.bucket_idx);
     patches_free(g->ps);
@@ -714,8 +727,17 @@ GWN_API gwn_status gwn_bezier2d_create(gwn_ctx *ctx, const void *ctrl, int dtype
     // a chain's pieces are kept in order of their lowest y (in the chain's
     // precision), with the running maximum of their highest y: the pieces
     // that can reach a band of rows are then one contiguous run
-    struct PieceH { int64_t seg; double u0, u1, y0, y1, lo_t; };
+    // An end of a piece strictly inside (0, 1) is an extremum of y: its value
+    // y(u) is rounded (to the chain's precision, after a float64 evaluation),
+    // so the row test of the two pieces that share it is uncertain within
+    // eps of it; eps bounds |stored value - curve value| there (the float64
+    // evaluation error of B_y is below 4 ulps of sum |P_y|).  Ends at u = 0 or
+    // 1 are control points, stored exactly.
+    struct PieceH { int64_t seg; double u0, u1, y0, y1, lo_t, eps0, eps1; int64_t id, part0, part1; };
     auto to_t = [dtype](double v) { return dtype == GWN_F64 ? v : (double)(float)v; };
+    std::vector<int2> ppart;
+    std::vector<double> peps;
+    int64_t next_id = 0;
     for (int64_t c = 0; c < n_chains; c++) {
         std::vector<PieceH> ch;
         for (int64_t i = chain_offsets[c]; i + 3 < chain_offsets[c + 1]; i += 3) {
@@ -724,13 +746,33 @@ GWN_API gwn_status gwn_bezier2d_create(gwn_ctx *ctx, const void *ctrl, int dtype
             double u[6];
             int np = monotone_split(cc, u);
             cs.n_seg++;
+            const double sy = fabs(cc[1]) + fabs(cc[3]) + fabs(cc[5]) + fabs(cc[7]);
+            auto end_eps = [&](double uu, double y) {
+                if (uu <= 0.0 || uu >= 1.0) return 0.0;
+                cs.eps_abs = std::max(cs.eps_abs, 8e-15 * sy);
+                return fabs(to_t(y) - y) + 4e-15 * sy;
+            };
+            int64_t prev_id = -1;          // the last kept piece of this segment
+            double prev_u1 = -1.0;
             for (int k = 0; k < np; k++) {
                 double y0 = bez_y(cc, u[2 * k]), y1 = bez_y(cc, u[2 * k + 1]);
-                if (y0 == y1) continue;   // flat piece: never crossed by the half-open rule
-                ch.push_back({i, u[2 * k], u[2 * k + 1], y0, y1, to_t(std::min(y0, y1))});
+                if (y0 == y1) { prev_id = -1; continue; }   // flat piece: never crossed by the half-open rule
+                PieceH h{i, u[2 * k], u[2 * k + 1], y0, y1, to_t(std::min(y0, y1)), end_eps(u[2 * k], y0),
+                         end_eps(u[2 * k + 1], y1), next_id++, -1, -1};
+                if (prev_id >= 0 && prev_u1 == h.u0 && h.eps0 > 0.0) {
+                    h.part0 = prev_id;
+                    ch.back().part1 = h.id;
+                }
+                ch.push_back(h);
+                prev_id = h.id;
+                prev_u1 = h.u1;
             }
         }
         std::stable_sort(ch.begin(), ch.end(), [](const PieceH &a, const PieceH &b) { return a.lo_t < b.lo_t; });
+        // partner ids -> indices in the sorted order (partners share a segment,
+        // hence a chain)
+        std::map<int64_t, int64_t> where;
+        for (size_t k = 0; k < ch.size(); k++) where[ch[k].id] = (int64_t)pch.size() + (int64_t)k;
         double hmax = -INFINITY;
         for (const PieceH &q : ch) {
             pseg.push_back(q.seg);
@@ -739,7 +781,12 @@ GWN_API gwn_status gwn_bezier2d_create(gwn_ctx *ctx, const void *ctrl, int dtype
             py.push_back(q.y0);
             py.push_back(q.y1);
             pch.push_back((int32_t)c);
-            hmax = std::max(hmax, to_t(std::max(q.y0, q.y1)));
+            ppart.push_back(make_int2(q.part0 >= 0 ? (int)where[q.part0] : -1, q.part1 >= 0 ? (int)where[q.part1] : -1));
+            peps.push_back(q.eps0);
+            peps.push_back(q.eps1);
+            // the run of pieces a block of rows can reach is widened by eps, so
+            // a row just past a rounded extremum still sees both its pieces
+            hmax = std::max(hmax, to_t(std::max(q.y0, q.y1) + std::max(q.eps0, q.eps1)));
             cs.h_piece_lo.push_back(q.lo_t);
             cs.h_piece_hmax.push_back(hmax);
         }
@@ -800,6 +847,33 @@ GWN_API gwn_status gwn_bezier2d_create(gwn_ctx *ctx, const void *ctrl, int dtype
         else if (e == cudaSuccess) {
             std::vector<float> fr(rec.begin(), rec.end());
             e = cudaMemcpy(cs.piece_rec, fr.data(), bytes, cudaMemcpyHostToDevice);
+        }
+    }
+    if (e == cudaSuccess) {        // per-piece data of the float64 certification
+        std::vector<double2> pu2(np);
+        for (int64_t q = 0; q < cs.n_pieces; q++) pu2[q] = make_double2(pu[2 * q], pu[2 * q + 1]);
+        std::vector<int64_t> ps(pseg.begin(), pseg.end());
+        ps.resize(np, 0);
+        ppart.resize(np, make_int2(-1, -1));
+        e = cudaMalloc(&cs.piece_seg, sizeof(int64_t) * np);
+        if (e == cudaSuccess) e = cudaMemcpy(cs.piece_seg, ps.data(), sizeof(int64_t) * np, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMalloc(&cs.piece_u, sizeof(double2) * np);
+        if (e == cudaSuccess) e = cudaMemcpy(cs.piece_u, pu2.data(), sizeof(double2) * np, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMalloc(&cs.piece_part, sizeof(int2) * np);
+        if (e == cudaSuccess) e = cudaMemcpy(cs.piece_part, ppart.data(), sizeof(int2) * np, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMalloc(&cs.piece_eps, esz * 2 * np);
+        if (e == cudaSuccess) {
+            peps.resize(2 * np, 0.0);
+            if (dtype == GWN_F64) {
+                e = cudaMemcpy(cs.piece_eps, peps.data(), esz * 2 * np, cudaMemcpyHostToDevice);
+            } else {        // rounded up, so the float bound still covers the double one
+                std::vector<float> fe(2 * np);
+                for (size_t k = 0; k < fe.size(); k++) {
+                    float f = (float)peps[k];
+                    fe[k] = (double)f < peps[k] ? nextafterf(f, INFINITY) : f;
+                }
+                e = cudaMemcpy(cs.piece_eps, fe.data(), esz * 2 * np, cudaMemcpyHostToDevice);
+            }
         }
     }
     if (e == cudaSuccess) e = build_point_index(cs, P, pseg, py, dtype);
@@ -986,6 +1060,8 @@ static gwn_status read_stats(gwn_ctx *ctx, gwn_stats *st, int64_t nq, int64_t pa
     st->n_deferred_traverse = (int64_t)c[CNT_DEFER_TRAV];
     st->n_deferred_boundary = (int64_t)c[CNT_DEFER_BTERM];
     st->n_root_iters = (int64_t)c[CNT_NEWTON];
+    st->n_cert = (int64_t)c[CNT_CERT];
+    st->n_cert_fixed = (int64_t)c[CNT_CERT_FIX];
     float a = 0, b = 0, t = 0, p = 0;
     cudaEventElapsedTime(&a, ctx->ev[1], ctx->ev[2]);
     cudaEventElapsedTime(&b, ctx->ev[2], ctx->ev[3]);
@@ -1119,7 +1195,7 @@ static gwn_status eval_impl(gwn_geom *g, const gwn_queries *q, const float *d, v
                 for (int k = 0; k < 3; k++) CK(cudaEventRecord(ctx->ev[k], ctx->stream), "event");
             }
             CK(launch_eval2d_points(g->cs, src, w_out, chi_out, b_out, stats ? ctx->d_cnt : nullptr, ctx->d_status,
-                                    ctx->stream), "2D point evaluation");
+                                    ctx->stream, ctx->d_cert, ctx->d_cert_count), "2D point evaluation");
             if (stats) CK(cudaEventRecord(ctx->ev[3], ctx->stream), "event");
             return read_stats(ctx, stats, nq, 0, false);
         }

@@ -94,7 +94,8 @@ gwn_status eval2d_single(gwn_geom *g, const QuerySrc &src, void *w_out, int32_t 
     int threads = 128;
     while (threads > 32 && eval2d_smem(cs.dtype, S.nx, threads) > EVAL2D_SMEM_MAX) threads -= 32;
     cudaError_t e = launch_eval2d_items(cs, nullptr, nullptr, &S, n_items, ctx->d_work_counter, rows, threads, S.nx,
-                                        w_out, chi_out, b_out, cnt, ctx->d_status, ctx->sm_count, ctx->stream);
+                                        w_out, chi_out, b_out, cnt, ctx->d_status, ctx->sm_count, ctx->stream,
+                                        ctx->d_cert, ctx->d_cert_count);
     if (e != cudaSuccess) return cuda_fail(e, "2D evaluation");
     return GWN_OK;
 }
@@ -278,7 +279,7 @@ extern "C" GWN_API gwn_status gwn_eval_batch(gwn_geom *g, const gwn_queries *que
                 cudaEventRecord(e0, ctx->stream);
                 e = launch_eval2d_items(g->cs, P->d_sets, P->d_items, nullptr, P->n_items, P->d_counter, cd.second, cd.first,
                                         P->max_nx, w_out, nullptr, nullptr, nullptr, ctx->d_status, ctx->sm_count,
-                                        ctx->stream);
+                                        ctx->stream, ctx->d_cert, ctx->d_cert_count);
                 cudaEventRecord(e1, ctx->stream);
                 if (e != cudaSuccess) break;
                 cudaEventSynchronize(e1);
@@ -314,7 +315,7 @@ extern "C" GWN_API gwn_status gwn_eval_batch(gwn_geom *g, const gwn_queries *que
         if (e == cudaSuccess) {
             cudaError_t le = launch_eval2d_items(g->cs, P->d_sets, P->d_items, nullptr, P->n_items, P->d_counter, P->rows,
                                                  P->threads, P->max_nx, w_out, nullptr, nullptr, nullptr,
-                                                 ctx->d_status, ctx->sm_count, cap);
+                                                 ctx->d_status, ctx->sm_count, cap, ctx->d_cert, ctx->d_cert_count);
             e = cudaStreamEndCapture(cap, &P->graph);
             if (le != cudaSuccess) e = le;
         }
@@ -327,7 +328,8 @@ extern "C" GWN_API gwn_status gwn_eval_batch(gwn_geom *g, const gwn_queries *que
     if (use_graph) e = cudaGraphLaunch(P->exec, ctx->stream);
     else
         e = launch_eval2d_items(g->cs, P->d_sets, P->d_items, nullptr, P->n_items, P->d_counter, P->rows, P->threads, P->max_nx,
-                                w_out, nullptr, nullptr, nullptr, ctx->d_status, ctx->sm_count, ctx->stream);
+                                w_out, nullptr, nullptr, nullptr, ctx->d_status, ctx->sm_count, ctx->stream,
+                                ctx->d_cert, ctx->d_cert_count);
     if (e != cudaSuccess) return cuda_fail(e, "batched launch");
     if (stats) {
         cudaEventRecord(ctx->ev[3], ctx->stream);
@@ -347,13 +349,15 @@ extern "C" GWN_API gwn_status gwn_eval_batch(gwn_geom *g, const gwn_queries *que
         if (e == cudaSuccess)
             e = launch_eval2d_items(g->cs, P->d_sets, P->d_items, nullptr, P->n_items, P->d_counter, P->rows,
                                     P->threads, P->max_nx, w_out, nullptr, nullptr, ctx->d_cnt, ctx->d_status,
-                                    ctx->sm_count, ctx->stream);
+                                    ctx->sm_count, ctx->stream, ctx->d_cert, ctx->d_cert_count);
         unsigned long long c[CNT_NUM];
         if (e == cudaSuccess) e = cudaMemcpyAsync(c, ctx->d_cnt, sizeof(c), cudaMemcpyDeviceToHost, ctx->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
         if (e != cudaSuccess) return cuda_fail(e, "batched counters");
         stats->n_tri_tests = (int64_t)c[CNT_ROOTS];
         stats->n_root_iters = (int64_t)c[CNT_NEWTON];
+        stats->n_cert = (int64_t)c[CNT_CERT];
+        stats->n_cert_fixed = (int64_t)c[CNT_CERT_FIX];
     }
     return GWN_OK;
 }

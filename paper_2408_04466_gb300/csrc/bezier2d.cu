@@ -33,6 +33,7 @@
 #include <string.h>
 
 #include "gwn_internal.h"
+#include "predicates.cuh"
 
 namespace gwn {
 
@@ -84,7 +85,7 @@ constexpr int PC_FIELDS = 12;
 // (min(r7, r10) <= yr < max(r7, r10)): safeguarded Newton from the linear
 // guess, the bracket oriented so that g(lo) <= 0 < g(hi), g = y(t) - yr.
 template <typename T>
-__device__ __forceinline__ T piece_root_rec(const T *r, T yr, int *iters_out) {
+__device__ __forceinline__ T piece_root_rec(const T *r, T yr, int *iters_out, T *t_out = nullptr) {
     const T ya = r[7], yb = r[10];
     const bool inc = yb > ya;
     T lo = inc ? T(0) : T(1), hi = inc ? T(1) : T(0);
@@ -105,7 +106,152 @@ __device__ __forceinline__ T piece_root_rec(const T *r, T yr, int *iters_out) {
         if ((step < T(0) ? -step : step) <= Num<T>::tol || (mx - mn) <= Num<T>::tol) break;
     }
     *iters_out = it;
+    if (t_out) *t_out = t;
     return Num<T>::fma_(Num<T>::fma_(Num<T>::fma_(r[0], t, r[1]), t, r[2]), t, r[3]);
+}
+
+// ---- certification of crossings ---------------------------------------------
+// A crossing computed from a piece record can sit on the wrong side of a
+// query for three reasons: Newton stops at a tolerance, the record's
+// coefficients are rounded, and the row test uses end values rounded at
+// interior extrema of y.  The kernels bound the first two per crossing
+// (root_band) and hand every (piece, row) whose bound contains a query
+// column -- and every row within rounding of an interior extremum value -- to
+// the certification pass, which decides those queries in float64 from the
+// control points.
+template <typename T> struct Unit;
+template <> struct Unit<float> { static constexpr float u = 5.9604645e-8f; };              // 2^-24
+template <> struct Unit<double> { static constexpr double u = 1.1102230246251565e-16; };   // 2^-53
+
+// Half-width of an interval about the computed crossing x_r that contains the
+// crossing of the exact curve, or +inf where the bound below does not apply.
+// With g(t) = y(t) - yr evaluated at Newton's final t: |g_exact(t)| <= |g| +
+// eg, eg covering the evaluation and the rounded coefficients; |y''| <= m2 on
+// [0, 1], so if m2 bt <= |y'(t)| / 2 (y' shrunk by its own error), y' keeps
+// at least half its size on [t - bt, t + bt] and the root lies within
+// bt = 2 (|g| + eg) / |y'(t)| of t; x moves by at most (|x'(t)| + m2x bt) bt
+// there, plus the error ex of x itself.
+// Error terms: Horner's rule on t in [0, 1] errs by at most ~3u of the sum of
+// the absolute terms, the coefficients carry half an ulp each from rounding
+// (the constant term y(u0) or x(u0) included: exact at control points, one
+// rounding at an extremum), so eg = 8u (|r4| + |r5| + |r6| + |r7 - yr|) +
+// u |r7| and ex = 8u (|r0| + |r1| + |r2|) + u |r3| cover them with margin.
+template <typename T>
+__device__ __forceinline__ T root_band(const T *r, T yr, T t) {
+    const T u = Unit<T>::u;
+    const T c0 = r[7] - yr;
+    const T g = Num<T>::fma_(Num<T>::fma_(Num<T>::fma_(r[4], t, r[5]), t, r[6]), t, c0);
+    const T dg = Num<T>::fma_(Num<T>::fma_(r[8], t, r[9]), t, r[6]);
+    const T eg = T(8) * u * (fabs(r[4]) + fabs(r[5]) + fabs(r[6]) + fabs(c0)) + u * fabs(r[7]);
+    const T adg = fabs(dg) - T(8) * u * (fabs(r[8]) + fabs(r[9]) + fabs(r[6]));
+    const T m2 = T(6) * fabs(r[4]) + T(2) * fabs(r[5]);
+    const T bt = T(2) * (fabs(g) + eg) / adg;
+    if (!(adg > T(0)) || !(m2 * bt <= T(0.5) * adg)) return T(INFINITY);
+    const T dx = Num<T>::fma_(Num<T>::fma_(T(3) * r[0], t, T(2) * r[1]), t, r[2]);
+    const T m2x = T(6) * fabs(r[0]) + T(2) * fabs(r[1]);
+    return (fabs(dx) + m2x * bt) * bt + T(8) * u * (fabs(r[0]) + fabs(r[1]) + fabs(r[2])) + u * fabs(r[3]);
+}
+
+// the row yr lies within the rounding of one of the piece's interior-extremum
+// end values (ya = y(u0), yb = y(u1) as stored, eps their bounds).  The
+// bounds are read only when yr is within 8u (|ya| + |yb|) + eps_abs of an
+// end, which every bound is below.
+template <typename T>
+__device__ __forceinline__ T near_window(T ya, T yb, T eps_abs) {
+    return T(8) * Unit<T>::u * (fabs(ya) + fabs(yb)) + eps_abs;
+}
+template <typename T>
+__device__ __forceinline__ bool near_extremum(T yr, T ya, T yb, const T *eps_p, T eps_abs) {
+    const T win = near_window<T>(ya, yb, eps_abs);
+    if (!(fabs(yr - ya) <= win || fabs(yr - yb) <= win)) return false;
+    const T e0 = eps_p[0], e1 = eps_p[1];
+    return (e0 > T(0) && fabs(yr - ya) <= e0) || (e1 > T(0) && fabs(yr - yb) <= e1);
+}
+
+// first column j in [0, nx] with ax[j] > x
+template <typename T>
+__device__ __forceinline__ int upper_bound_cols_lin(const T *ax, int nx, T x) {
+    int lo = 0, hi = nx;
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (ax[mid] > x) hi = mid; else lo = mid + 1;
+    }
+    return lo;
+}
+// first column j in [0, nx] with ax[j] >= x
+template <typename T>
+__device__ __forceinline__ int lower_bound_cols_lin(const T *ax, int nx, T x) {
+    int lo = 0, hi = nx;
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (ax[mid] >= x) hi = mid; else lo = mid + 1;
+    }
+    return lo;
+}
+
+// append one certification entry: queries (set, row, columns [c0, c1)) against
+// piece p (and its partner q >= 0 at an interior extremum)
+__device__ __forceinline__ void cert_push(int4 *cert, int32_t *cert_count, int *status, unsigned long long *cnt,
+                                          int set, int row, int p, int q, int c0, int c1) {
+    if (c1 <= c0) return;
+    const int slot = atomicAdd(cert_count, 1);
+    if (slot >= GWN_CERT_CAP) {
+        if (status) atomicOr(status, ST_CERT_OVERFLOW);
+        return;
+    }
+    cert[2 * slot] = make_int4(set, row, p, q);
+    cert[2 * slot + 1] = make_int4(c0, c1, 0, 0);
+    if (cnt) atomicAdd(&cnt[CNT_CERT], 1ull);
+}
+
+// Certification (see root_band): pass 1 lists the rows within rounding of a
+// piece's interior-extremum end value, once per pair of pieces sharing it,
+// with the columns of both pieces' x-ranges; pass 2 (and the per-row
+// fallback) lists each crossing whose error bound contains a query column.
+struct CertArgs2D {
+    double eps_abs;            // see near_window
+    const void *piece_eps;     // [n_pieces][2], chain dtype
+    const int2 *piece_part;    // [n_pieces]
+    const void *piece_x;       // [n_pieces][2] conservative x-ranges, chain dtype
+    int4 *cert;
+    int32_t *count;
+};
+
+// float64 decision for one piece on the row yr: whether the exact curve
+// crosses the row there (half-open in y) and, if so, the x of the crossing and
+// its direction.  From the segment's control points: the row test on the end
+// values y(u0), y(u1) (exact at control points), then bisection of the
+// monotone y(u) - yr on [u0, u1] to the resolution of float64 and x there.
+// A query (xq, yr) counts the crossing iff x > xq.
+struct ExactCross {
+    double x;
+    int dir;          // 0: the row does not cross the piece
+};
+template <typename T>
+__device__ __noinline__ ExactCross piece_exact(const T *__restrict__ ctrl, int64_t seg, double2 uu, double yr) {
+    double c[8];
+    for (int k = 0; k < 8; k++) c[k] = (double)ctrl[2 * seg + k];
+    auto bez = [&](int d, double u) {
+        const double v = 1.0 - u;
+        const double p01 = v * c[d] + u * c[2 + d], p12 = v * c[2 + d] + u * c[4 + d], p23 = v * c[4 + d] + u * c[6 + d];
+        const double q0 = v * p01 + u * p12, q1 = v * p12 + u * p23;
+        return v * q0 + u * q1;
+    };
+    ExactCross r{0.0, 0};
+    const double y0 = uu.x <= 0.0 ? c[1] : bez(1, uu.x), y1 = uu.y >= 1.0 ? c[7] : bez(1, uu.y);
+    const double lo = y0 < y1 ? y0 : y1, hi = y0 < y1 ? y1 : y0;
+    if (!(lo <= yr && yr < hi)) return r;
+    const bool inc = y1 > y0;
+    double a = uu.x, b = uu.y;                        // y(a) <= yr < y(b) in the increasing sense
+    for (int it = 0; it < 128; it++) {
+        const double m = 0.5 * (a + b);
+        if (!(m > a && m < b)) break;
+        const double ym = bez(1, m);
+        if ((ym > yr) == inc) b = m; else a = m;
+    }
+    r.x = bez(0, 0.5 * (a + b));
+    r.dir = inc ? 1 : -1;
+    return r;
 }
 
 // a piece record from global memory (16-byte aligned, read as 16-byte words)
@@ -145,6 +291,88 @@ __device__ __forceinline__ void chord_cd(T spx, T sy, T epx, T ney, T syey, T xq
     cr = Num<T>::fma_(ex, sy, Num<T>::mul(sx, ney));
     dt = Num<T>::fma_(sx, ex, syey);
 }
+
+// piece_exact by one warp: each step evaluates y at 32 interior points of
+// the bracket (one per lane) and keeps the sub-interval where y - yr changes
+// sign, shrinking the bracket 33-fold, so about eleven steps reach the
+// resolution of float64 (the scalar bisection needs about 53).  Every lane
+// returns the same result.
+template <typename T>
+__device__ __noinline__ ExactCross piece_exact_warp(const T *__restrict__ ctrl, int64_t seg, double2 uu, double yr) {
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const double x0 = (double)ctrl[2 * seg], y0c = (double)ctrl[2 * seg + 1];
+    const double x1 = (double)ctrl[2 * seg + 2], y1c = (double)ctrl[2 * seg + 3];
+    const double x2 = (double)ctrl[2 * seg + 4], y2c = (double)ctrl[2 * seg + 5];
+    const double x3 = (double)ctrl[2 * seg + 6], y3c = (double)ctrl[2 * seg + 7];
+    auto casteljau = [](double p0, double p1, double p2, double p3, double u) {
+        const double v = 1.0 - u;
+        const double p01 = v * p0 + u * p1, p12 = v * p1 + u * p2, p23 = v * p2 + u * p3;
+        return v * (v * p01 + u * p12) + u * (v * p12 + u * p23);
+    };
+    ExactCross r{0.0, 0};
+    const double ya = uu.x <= 0.0 ? y0c : casteljau(y0c, y1c, y2c, y3c, uu.x);
+    const double yb = uu.y >= 1.0 ? y3c : casteljau(y0c, y1c, y2c, y3c, uu.y);
+    const double lo = ya < yb ? ya : yb, hi = ya < yb ? yb : ya;
+    if (!(lo <= yr && yr < hi)) return r;
+    const bool inc = yb > ya;
+    double a = uu.x, b = uu.y;                        // y(a) <= yr < y(b) in the increasing sense
+    for (int it = 0; it < 24; it++) {                 // warp-uniform: a, b are the same on every lane
+        const double m = a + (b - a) * ((double)(lane + 1) / 33.0);
+        const bool interior = m > a && m < b;        // the points are non-decreasing in the lane
+        const unsigned ib = __ballot_sync(FULL, interior);
+        if (!ib) break;                               // float64 resolution reached
+        const bool right = (casteljau(y0c, y1c, y2c, y3c, m) > yr) == inc;   // the crossing is at or left of m
+        const unsigned rb = __ballot_sync(FULL, interior && right);
+        if (rb) {
+            const int k = __ffs(rb) - 1;
+            const double nb = __shfl_sync(FULL, m, k);
+            const double na = __shfl_sync(FULL, m, k > 0 ? k - 1 : 0);
+            if (k > 0 && ((ib >> (k - 1)) & 1u)) a = na;
+            b = nb;
+        } else {
+            a = __shfl_sync(FULL, m, 31 - __clz(ib));  // the last interior point
+        }
+    }
+    r.x = casteljau(x0, x1, x2, x3, 0.5 * (a + b));
+    r.dir = inc ? 1 : -1;
+    return r;
+}
+
+// Side of the chord for the crossing count.  The chord e -> s crosses the
+// ray to the right of p iff cr = cross(e - p, s - p) has the sign of the
+// chord's direction in y; the angle term takes its branch from the same cr,
+// so w is the same on either side (the count's step and the angle's 2 pi
+// step cancel) and only the count itself depends on the sign.  cr as
+// computed (two rounded differences, a product and a fused product-add) is
+// off by at most 8u (|ex sy| + |sx ey|); within that its sign is uncertain,
+// and the certification pass takes it exactly: cr expands into six products
+// of the input coordinates (the p.x p.y terms cancel), each split into an
+// exact hi + lo pair by FMA, summed as a nonoverlapping expansion.
+template <typename T>
+__device__ __noinline__ int chord_sign_exact(T spx, T spy, T epx, T epy, T xq, T yr) {
+    const double a[6] = {(double)epx, -(double)epx, -(double)xq, -(double)spx, (double)spx, (double)xq};
+    const double b[6] = {(double)spy, (double)yr, (double)spy, (double)epy, (double)yr, (double)epy};
+    Expansion<16> E;
+    E.init();
+    for (int k = 0; k < 6; k++) {
+        const double hi = a[k] * b[k];
+        E.add(fma(a[k], b[k], -hi));
+        E.add(hi);
+    }
+    return E.sign();
+}
+
+template <typename T>
+__device__ __forceinline__ bool chord_uncertain(T cr, T sx, T ex, T sy, T ey) {
+    return !(fabs(cr) > T(8) * Unit<T>::u * (fabs(ex * sy) + fabs(sx * ey)));
+}
+
+// the float path's chord crossing at (xq, yr) for chain c, as chord_angles
+// counts it, and the exact one: (float, exact) signed counts
+template <typename T>
+__device__ __forceinline__ int2 chord_counts(const T *__restrict__ ctrl, const int64_t *__restrict__ chain_off,
+                                             int64_t c, T xq, T yr);
 
 // Degree-8 odd minimax polynomial of the 3D boundary term: atan(v) ~ v P(v^2)
 // on [-1, 1], relative error 1.5e-8.
@@ -256,9 +484,11 @@ __device__ __forceinline__ int lower_bound_cols(const T *ax, int nx, T a0, T inv
 // chord terms of the set's chains at (xq, yr): each chord's crossing with the
 // +x ray (half-open in y) is added to chi; returns the sum A of the angles
 // atan2(-cr, dt) (w = chi + A / 2 pi)
-template <typename T>
+// (on_unc(c) is called for each chain whose chord side is uncertain at the
+// query; see chord_uncertain)
+template <typename T, typename F>
 __device__ __forceinline__ T chord_angles(const T *__restrict__ ctrl, const int64_t *__restrict__ chain_off,
-                                         const Set2D &S, T xq, T yr, int &chi) {
+                                         const Set2D &S, T xq, T yr, int &chi, F on_unc) {
     T A = T(0);
     for (int64_t c = S.c_lo; c < S.c_hi; c++) {
         const T *sp = ctrl + 2 * chain_off[c];
@@ -271,10 +501,29 @@ __device__ __forceinline__ T chord_angles(const T *__restrict__ ctrl, const int6
             bool up = sy > ey;
             bool right = up ? (cr > T(0)) : (cr < T(0));
             if (right) chi += up ? 1 : -1;
+            if (chord_uncertain<T>(cr, Num<T>::add(sp[0], -xq), Num<T>::add(ep[0], -xq), sy, ey)) on_unc(c);
         }
         A = Num<T>::add(A, Chord<T>::angle(cr, dt));
     }
     return A;
+}
+
+template <typename T>
+__device__ __forceinline__ int2 chord_counts(const T *__restrict__ ctrl, const int64_t *__restrict__ chain_off,
+                                             int64_t c, T xq, T yr) {
+    const T *sp = ctrl + 2 * chain_off[c];
+    const T *ep = ctrl + 2 * (chain_off[c + 1] - 1);
+    const T sy = sp[1] - yr, ey = ep[1] - yr;
+    T cr, dt;
+    chord_cd<T>(sp[0], sy, ep[0], -ey, sy * ey, xq, cr, dt);
+    const T lo = ey < sy ? ey : sy, hi = ey < sy ? sy : ey;
+    if (!(lo <= T(0) && T(0) < hi)) return make_int2(0, 0);
+    const bool up = sy > ey;
+    const int d = up ? 1 : -1;
+    const int f = (up ? (cr > T(0)) : (cr < T(0))) ? d : 0;
+    const int sg = chord_sign_exact<T>(sp[0], sp[1], ep[0], ep[1], xq, yr);
+    const int e = (up ? (sg > 0) : (sg < 0)) ? d : 0;
+    return make_int2(f, e);
 }
 
 // w = chi + A / 2 pi, formed as one fused multiply-add on every path;
@@ -307,7 +556,8 @@ __device__ __forceinline__ void row_queries(const Set2D &S, const T *__restrict_
                                             const int64_t *__restrict__ chain_off, const T *__restrict__ ax,
                                             int nx, const int *xj, const signed char *dirs, int nk,
                                             T yr, int64_t row, int *D, int lane, T *w_out, int32_t *chi_out,
-                                            T *b_out) {
+                                            T *b_out, const CertArgs2D &ca, int *status, unsigned long long *cnt,
+                                            int set) {
     const unsigned FULL = 0xffffffffu;
     const int nxp = eval2d_dstride(nx);
     for (int c0 = 0; c0 < nxp; c0 += 256) {
@@ -360,9 +610,14 @@ __device__ __forceinline__ void row_queries(const Set2D &S, const T *__restrict_
                     T cr, dt;
                     chord_cd<T>(spx, sy, epx, -ey, sy * ey, xq, cr, dt);
                     if (crosses && (up ? (cr > T(0)) : (cr < T(0)))) chi += up ? 1 : -1;
+                    if (crosses && chi_out &&
+                        chord_uncertain<T>(cr, Num<T>::add(spx, -xq), Num<T>::add(epx, -xq), sy, ey))
+                        cert_push(ca.cert, ca.count, status, cnt, set, (int)row, (int)(-2 - S.c_lo), -1, i, i + 1);
                     A = Chord<T>::angle(cr, dt);
                 } else {
-                    A = chord_angles<T>(ctrl, chain_off, S, xq, yr, chi);
+                    A = chord_angles<T>(ctrl, chain_off, S, xq, yr, chi, [&](int64_t c) {
+                        if (chi_out) cert_push(ca.cert, ca.count, status, cnt, set, (int)row, (int)(-2 - c), -1, i, i + 1);
+                    });
                 }
                 out[m] = w_of<T>(chi, A);
                 if (b_out) b_out[obase + i] = Num<T>::mul(A, Num<T>::inv2pi);
@@ -500,6 +755,20 @@ __device__ __forceinline__ void row_queries_f32(const float *__restrict__ ax, in
 // The item's rows are processed in sub-blocks whose crossings fit in CAP; a
 // single row with more than CAP crossings falls back to scanning the pieces
 // CHUNK crossings at a time.
+
+template <typename T>
+__device__ __forceinline__ void cert_hull_cols(const T *px, int64_t p, int64_t q, const T *ax, int nx, int &c0,
+                                               int &c1) {
+    T lo = px[2 * p], hi = px[2 * p + 1];
+    if (q >= 0) {
+        lo = px[2 * q] < lo ? px[2 * q] : lo;
+        hi = px[2 * q + 1] > hi ? px[2 * q + 1] : hi;
+    }
+    const T m = T(16) * Unit<T>::u * (fabs(lo) + fabs(hi));
+    c0 = lower_bound_cols_lin(ax, nx, lo - m);
+    c1 = upper_bound_cols_lin(ax, nx, hi + m);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(1024) eval2d_kernel(const T *__restrict__ ctrl, const int64_t *__restrict__ chain_off,
                               const T *__restrict__ piece_y, const T *__restrict__ piece_rec,
@@ -507,7 +776,7 @@ __global__ void __launch_bounds__(1024) eval2d_kernel(const T *__restrict__ ctrl
                               int64_t n_items,
                               unsigned long long *counter, int rows_per_item, T *__restrict__ w_out,
                               int32_t *__restrict__ chi_out, T *__restrict__ b_out, unsigned long long *cnt,
-                              int *status, int max_nx) {
+                              int *status, int max_nx, const CertArgs2D ca) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nthr = blockDim.x;
     T *xs = (T *)smem_raw;                                    // CAP crossings (x; the per-row fallback)
@@ -562,12 +831,51 @@ __global__ void __launch_bounds__(1024) eval2d_kernel(const T *__restrict__ ctrl
         for (int64_t p = pA + threadIdx.x; p < pB; p += nthr) {
             T ya = piece_y[2 * p], yb = piece_y[2 * p + 1];
             T lo = ya < yb ? ya : yb, hi = ya < yb ? yb : ya;
-            if (!(hi > y_first && lo <= y_last)) continue;
-            int ra = lower_bound_rows_grid(ys, nr, y_first, inv_hy, lo);
-            int rb = lower_bound_rows_grid(ys, nr, y_first, inv_hy, hi);
-            if (ra < rb) {
-                atomicAdd(&rcur[ra], 1);
-                atomicAdd(&rcur[rb], -1);
+            const bool overlap = hi > y_first && lo <= y_last;
+            int ra = 0, rb = 0;
+            if (overlap) {
+                ra = lower_bound_rows_grid(ys, nr, y_first, inv_hy, lo);
+                rb = lower_bound_rows_grid(ys, nr, y_first, inv_hy, hi);
+                if (ra < rb) {
+                    atomicAdd(&rcur[ra], 1);
+                    atomicAdd(&rcur[rb], -1);
+                }
+            }
+            // certification: a row of the item within rounding of an
+            // interior-extremum end value (the nearest rows to each end
+            // decide whether any row is within near_window of it)
+            const T win = near_window<T>(ya, yb, (T)ca.eps_abs);
+            if (!(hi > y_first - win && lo <= y_last + win)) continue;
+            if (!overlap) {
+                ra = lower_bound_rows_grid(ys, nr, y_first, inv_hy, lo);
+                rb = lower_bound_rows_grid(ys, nr, y_first, inv_hy, hi);
+            }
+            const bool close = (ra < nr && ys[ra] - lo <= win) || (ra > 0 && lo - ys[ra - 1] <= win) ||
+                               (rb < nr && ys[rb] - hi <= win) || (rb > 0 && hi - ys[rb - 1] <= win);
+            if (close) {
+                const T *ep = (const T *)ca.piece_eps + 2 * p;
+                const int2 pq = ca.piece_part[p];
+#pragma unroll 1
+                for (int end = 0; end < 2; end++) {
+                    const T ev = end ? ep[1] : ep[0], yv = end ? yb : ya;
+                    const int q = end ? pq.y : pq.x;
+                    // an exact end, or a partner in this item's run lists it
+                    if (!(ev > T(0)) || (q >= 0 && q < p && q >= pA)) continue;
+                    if (!(yv + T(2) * ev >= y_first && yv - T(2) * ev <= y_last)) continue;
+                    int c0 = 0, c1 = 0;
+                    bool have = false;
+                    // the rows near_extremum selects (the same comparison), searched in a wider window
+                    for (int i = lower_bound_rows_grid(ys, nr, y_first, inv_hy, yv - T(2) * ev);
+                         i < nr && ys[i] <= yv + T(2) * ev; i++) {
+                        if (!(fabs(ys[i] - yv) <= ev)) continue;
+                        if (!have) {
+                            cert_hull_cols<T>((const T *)ca.piece_x, p, q, s_ax, nx, c0, c1);
+                            have = true;
+                        }
+                        cert_push(ca.cert, ca.count, status, cnt, sets ? it.x : -1, (int)(r0 + i), (int)p, q, c0,
+                                  c1);
+                    }
+                }
             }
         }
         __syncthreads();
@@ -663,12 +971,32 @@ __global__ void __launch_bounds__(1024) eval2d_kernel(const T *__restrict__ ctrl
                         for (int m = 0; m < PC_FIELDS - 1; m++) rec[m] = s_pc[m * nthr + lo];
                         const T ya = rec[7], yb = rec[10];
                         int iters;
-                        const T xr = piece_root_rec<T>(rec, ys[r], &iters);
+                        T tf;
+                        const T xr = piece_root_rec<T>(rec, ys[r], &iters, &tf);
                         if (iters >= Num<T>::max_iter && status) atomicOr(status, ST_TIMEOUT);
                         nroots_thread += (unsigned long long)iters << 32 | 1ull;
                         const int slot = roff[r] - base + atomicAdd(&rcur[r], 1);
-                        xj[slot] = lower_bound_cols(s_ax, nx, a0, inv_step, xr);   // its column
+                        const int col = lower_bound_cols(s_ax, nx, a0, inv_step, xr);   // its column
+                        xj[slot] = col;
                         dirs[slot] = yb > ya ? 1 : -1;
+                        {
+                            const T band = root_band<T>(rec, ys[r], tf);
+                            const bool amb = !(band < T(INFINITY)) || (col > 0 && s_ax[col - 1] >= xr - band) ||
+                                             (col < nx && s_ax[col] <= xr + band);
+                            const int64_t p = pc + lo;
+                            if (amb && !near_extremum<T>(ys[r], ya, yb, (const T *)ca.piece_eps + 2 * p,
+                                                         (T)ca.eps_abs)) {
+                                int c0, c1;
+                                if (band < T(INFINITY)) {
+                                    c0 = lower_bound_cols_lin(s_ax, nx, xr - band);
+                                    c1 = upper_bound_cols_lin(s_ax, nx, xr + band);
+                                } else {
+                                    cert_hull_cols<T>((const T *)ca.piece_x, p, -1, s_ax, nx, c0, c1);
+                                }
+                                cert_push(ca.cert, ca.count, status, cnt, sets ? it.x : -1, (int)(r0 + r), (int)p,
+                                          -1, c0, c1);
+                            }
+                        }
                     }
                 }
                 __syncthreads();
@@ -687,7 +1015,7 @@ __global__ void __launch_bounds__(1024) eval2d_kernel(const T *__restrict__ ctrl
                     for (int r = sb0 + warp; r < sb1; r += nwarps)
                         row_queries<T>(S, ctrl, chain_off, s_ax, nx, xj + roff[r] - base,
                                        dirs + roff[r] - base, roff[r + 1] - roff[r], ys[r], r0 + r, D, lane, w_out,
-                                       chi_out, b_out);
+                                       chi_out, b_out, ca, status, cnt, sets ? it.x : -1);
                 }
                 __syncthreads();
             } else {
@@ -707,12 +1035,26 @@ __global__ void __launch_bounds__(1024) eval2d_kernel(const T *__restrict__ ctrl
                         T rec[PC_FIELDS];
                         load_rec<T>(piece_rec, p, rec);
                         int iters;
-                        T x = piece_root_rec<T>(rec, yr, &iters);
+                        T tf;
+                        T x = piece_root_rec<T>(rec, yr, &iters, &tf);
                         if (iters >= Num<T>::max_iter && status) atomicOr(status, ST_TIMEOUT);
                         nroots_thread += (unsigned long long)iters << 32 | 1ull;
                         int slot = atomicAdd(&ncross, 1);
                         xs[slot] = x;
                         dirs[slot] = yb > ya ? 1 : -1;
+                        {
+                            const T band = root_band<T>(rec, yr, tf);
+                            int c0, c1;
+                            if (band < T(INFINITY)) {
+                                c0 = lower_bound_cols_lin(s_ax, nx, x - band);
+                                c1 = upper_bound_cols_lin(s_ax, nx, x + band);
+                            } else {
+                                cert_hull_cols<T>((const T *)ca.piece_x, p, -1, s_ax, nx, c0, c1);
+                            }
+                            if (c1 > c0 && !near_extremum<T>(yr, ya, yb, (const T *)ca.piece_eps + 2 * p, (T)ca.eps_abs))
+                                cert_push(ca.cert, ca.count, status, cnt, sets ? it.x : -1, (int)(r0 + r), (int)p,
+                                          -1, c0, c1);
+                        }
                     }
                     __syncthreads();
                     int nc = ncross;
@@ -726,7 +1068,11 @@ __global__ void __launch_bounds__(1024) eval2d_kernel(const T *__restrict__ ctrl
                 }
                 for (int64_t i = threadIdx.x; i < S.nx; i += nthr) {
                     int chi = chi_row[i];
-                    T A = chord_angles<T>(ctrl, chain_off, S, s_ax[i], yr, chi);
+                    T A = chord_angles<T>(ctrl, chain_off, S, s_ax[i], yr, chi, [&](int64_t c) {
+                        if (chi_out)
+                            cert_push(ca.cert, ca.count, status, cnt, sets ? it.x : -1, (int)(r0 + r), (int)(-2 - c),
+                                      -1, (int)i, (int)i + 1);
+                    });
                     store_w<T>(S, r0 + r, i, chi, A, w_out, chi_out, b_out);
                 }
                 __syncthreads();
@@ -743,6 +1089,83 @@ __global__ void __launch_bounds__(1024) eval2d_kernel(const T *__restrict__ ctrl
     }
 }
 
+// Certification pass: one warp per listed (set, row, piece [, partner],
+// columns).  Per piece, once: the float path's own crossing (the same row
+// test and the same root as eval2d_kernel; a query counts it iff xq < x) and
+// the float64 one (piece_exact); then the lanes take the columns, and where
+// the two counts differ the query's count, and w, are corrected by the
+// difference.  Entries are rare (a crossing within its error bound of a
+// query, or a row within rounding of an extremum value).
+// An entry with piece index -2 - c lists the chord of chain c instead: its
+// side is taken exactly (chord_counts) and only the count changes (w is the
+// same on both sides of the chord).
+template <typename T>
+__global__ void __launch_bounds__(128) eval2d_cert_kernel(
+    const T *__restrict__ ctrl, const int64_t *__restrict__ chain_off, const T *__restrict__ piece_y,
+    const T *__restrict__ piece_rec, const int64_t *__restrict__ piece_seg, const double2 *__restrict__ piece_u,
+    const Set2D *__restrict__ sets, const Set2D single, const int4 *__restrict__ cert,
+    const int32_t *__restrict__ cert_count, T *w_out, int32_t *chi_out, unsigned long long *cnt) {
+    int n = *cert_count;
+    if (n > GWN_CERT_CAP) n = GWN_CERT_CAP;
+    const int lane = threadIdx.x & 31;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int i = warp; i < n; i += nwarps) {               // warp-uniform
+        const int4 a = cert[2 * i], b = cert[2 * i + 1];
+        const Set2D S = a.x >= 0 ? sets[a.x] : single;
+        const T *ax = (const T *)S.ax;
+        const T yr = ((const T *)S.ay)[a.y];
+        if (a.z <= -2) {                                    // a chord side
+            if (lane == 0 && chi_out) {
+                for (int c = b.x; c < b.y; c++) {
+                    const int2 fe = chord_counts<T>(ctrl, chain_off, (int64_t)(-2 - a.z), ax[c], yr);
+                    if (fe.x != fe.y) {
+                        atomicAdd(&chi_out[S.out_off + (int64_t)a.y * S.nx + c], fe.y - fe.x);
+                        if (cnt) atomicAdd(&cnt[CNT_CERT_FIX], 1ull);
+                    }
+                }
+            }
+            continue;
+        }
+        T fx[2];
+        int fdir[2];
+        ExactCross ec[2];
+        for (int k = 0; k < 2; k++) {
+            const int pp = k ? a.w : a.z;
+            fdir[k] = 0;
+            fx[k] = T(0);
+            ec[k].dir = 0;
+            ec[k].x = 0.0;
+            if (pp < 0) continue;
+            const T ya = piece_y[2 * pp], yb = piece_y[2 * pp + 1];
+            const T lo = ya < yb ? ya : yb, hi = ya < yb ? yb : ya;
+            if (lo <= yr && yr < hi) {
+                T rec[PC_FIELDS];
+                load_rec<T>(piece_rec, pp, rec);
+                int iters;
+                fx[k] = piece_root_rec<T>(rec, yr, &iters);
+                fdir[k] = yb > ya ? 1 : -1;
+            }
+            ec[k] = piece_exact_warp<T>(ctrl, piece_seg[pp], piece_u[pp], (double)yr);
+        }
+        int nfix = 0;
+        for (int c = b.x + lane; c < b.y; c += 32) {
+            const T xq = ax[c];
+            int f = 0, e = 0;
+            for (int k = 0; k < 2; k++) {
+                if (fdir[k] && xq < fx[k]) f += fdir[k];
+                if (ec[k].dir && ec[k].x > (double)xq) e += ec[k].dir;
+            }
+            if (e != f) {
+                const int64_t o = S.out_off + (int64_t)a.y * S.nx + c;
+                if (w_out) atomicAdd(&w_out[o], (T)(e - f));
+                if (chi_out) atomicAdd(&chi_out[o], e - f);
+                nfix++;
+            }
+        }
+        if (cnt && nfix) atomicAdd(&cnt[CNT_CERT_FIX], (unsigned long long)nfix);
+    }
+}
+
 size_t eval2d_smem(int dtype, int64_t max_nx, int threads) {
     size_t off = dtype == GWN_F64 ? eval2d_fallback_off<double>(threads) : eval2d_fallback_off<float>(threads);
     off += ((dtype == GWN_F64 ? 8 : 4) * (size_t)max_nx + 15) & ~(size_t)15;      // ax
@@ -754,16 +1177,25 @@ size_t eval2d_smem(int dtype, int64_t max_nx, int threads) {
 cudaError_t launch_eval2d_items(const ChainSet &cs, const Set2D *d_sets, const int4 *d_items, const Set2D *single,
                                 int64_t n_items, unsigned long long *d_counter, int rows_per_item, int threads,
                                 int64_t max_nx, void *w_out, int32_t *chi_out, void *b_out, unsigned long long *cnt,
-                                int *status, int sm_count, cudaStream_t st) {
+                                int *status, int sm_count, cudaStream_t st, int4 *cert, int32_t *cert_count) {
     if (n_items == 0) return cudaSuccess;
     if (!d_sets && !single) return cudaErrorInvalidValue;
     if (rows_per_item < 1 || rows_per_item > MAX_ROWS || threads < 32 || threads % 32) return cudaErrorInvalidValue;
     Set2D s0;
     memset(&s0, 0, sizeof(s0));
     if (single) s0 = *single;
+    if (!cert || !cert_count) return cudaErrorInvalidValue;
     size_t smem = eval2d_smem(cs.dtype, max_nx, threads);
     cudaError_t e = cudaMemsetAsync(d_counter, 0, sizeof(unsigned long long), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(cert_count, 0, sizeof(int32_t), st);
     if (e != cudaSuccess) return e;
+    CertArgs2D ca;
+    ca.eps_abs = cs.eps_abs;
+    ca.piece_eps = cs.piece_eps;
+    ca.piece_part = cs.piece_part;
+    ca.piece_x = cs.piece_xT;
+    ca.cert = cert;
+    ca.count = cert_count;
     // persistent grid: as many blocks as fit on the device at once
     int per_sm = 0;
     if (cs.dtype == GWN_F64) {
@@ -782,14 +1214,25 @@ cudaError_t launch_eval2d_items(const ChainSet &cs, const Set2D *d_sets, const i
             (const double *)cs.ctrl, cs.chain_off,
             (const double *)cs.piece_yT, (const double *)cs.piece_rec, d_sets, d_items, s0, n_items, d_counter,
             rows_per_item, (double *)w_out,
-            chi_out, (double *)b_out, cnt, status, (int)max_nx);
+            chi_out, (double *)b_out, cnt, status, (int)max_nx, ca);
     } else {
         eval2d_kernel<float><<<(unsigned)blocks, threads, smem, st>>>(
             (const float *)cs.ctrl, cs.chain_off,
             (const float *)cs.piece_yT, (const float *)cs.piece_rec, d_sets, d_items, s0, n_items, d_counter,
             rows_per_item, (float *)w_out,
-            chi_out, (float *)b_out, cnt, status, (int)max_nx);
+            chi_out, (float *)b_out, cnt, status, (int)max_nx, ca);
     }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    // certification pass: a small fixed grid over the (rare) listed entries
+    if (cs.dtype == GWN_F64)
+        eval2d_cert_kernel<double><<<(unsigned)((sm_count > 0 ? sm_count : 152) * 2), 128, 0, st>>>((const double *)cs.ctrl, cs.chain_off, (const double *)cs.piece_yT,
+                                                      (const double *)cs.piece_rec, cs.piece_seg, cs.piece_u, d_sets,
+                                                      s0, cert, cert_count, (double *)w_out, chi_out, cnt);
+    else
+        eval2d_cert_kernel<float><<<(unsigned)((sm_count > 0 ? sm_count : 152) * 2), 128, 0, st>>>((const float *)cs.ctrl, cs.chain_off, (const float *)cs.piece_yT,
+                                                     (const float *)cs.piece_rec, cs.piece_seg, cs.piece_u, d_sets,
+                                                     s0, cert, cert_count, (float *)w_out, chi_out, cnt);
     return cudaGetLastError();
 }
 
@@ -810,13 +1253,19 @@ __device__ __forceinline__ int bucket_of_dev(T y, T y0, T inv_h, int nb) {
     return b < nb ? b : nb - 1;
 }
 
+// Certification, per query and piece: a row within rounding of one of the
+// piece's interior-extremum end values, or a root whose error bound contains
+// the query, is listed (query, piece) for eval2d_points_cert_kernel, which
+// decides it in float64 from the control points and corrects the count; the
+// float contribution made here stays in the count until then.
 template <typename T>
 __global__ void __launch_bounds__(256) eval2d_points_kernel(
     const T *__restrict__ ctrl, const int64_t *__restrict__ chain_off, int64_t n_chains,
     const T *__restrict__ piece_y, const T *__restrict__ piece_rec,
     const T *__restrict__ piece_x, const int32_t *__restrict__ bucket_off, const int32_t *__restrict__ bucket_idx,
     int nb, T y0, T inv_h, const T *__restrict__ pts, int64_t n, T *__restrict__ w_out, int32_t *__restrict__ chi_out,
-    T *__restrict__ b_out, unsigned long long *cnt, int *status) {
+    T *__restrict__ b_out, unsigned long long *cnt, int *status, const T *__restrict__ piece_eps, T eps_abs,
+    int4 *cert, int32_t *cert_count) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const T px = pts[2 * i], py = pts[2 * i + 1];
@@ -826,44 +1275,124 @@ __global__ void __launch_bounds__(256) eval2d_points_kernel(
         const int p = bucket_idx[j];
         const T ya = piece_y[2 * p], yb = piece_y[2 * p + 1];
         const T lo = ya < yb ? ya : yb, hi = ya < yb ? yb : ya;
-        if (!(lo <= py && py < hi)) continue;
+        const bool crossed = lo <= py && py < hi;
+        if (near_extremum<T>(py, ya, yb, piece_eps + 2 * p, eps_abs)) {
+            cert_push(cert, cert_count, status, cnt, -2, (int)i, p, -1, 0, 1);
+            if (!crossed) continue;                              // the float path's count stands until then
+        } else if (!crossed) {
+            continue;
+        }
         const int dir = yb > ya ? 1 : -1;
         if (px < piece_x[2 * p]) { chi += dir; continue; }      // crossing certainly to the right
         if (px >= piece_x[2 * p + 1]) continue;                 // certainly not to the right
         T rec[PC_FIELDS];
         load_rec<T>(piece_rec, p, rec);
         int iters;
-        T x = piece_root_rec<T>(rec, py, &iters);
+        T tf;
+        T x = piece_root_rec<T>(rec, py, &iters, &tf);
         if (iters >= Num<T>::max_iter && status) atomicOr(status, ST_TIMEOUT);
-        if (x > px) chi += dir;
         nroots++;
+        if (!(fabs(x - px) > root_band<T>(rec, py, tf)) && !near_extremum<T>(py, ya, yb, piece_eps + 2 * p, eps_abs))
+            cert_push(cert, cert_count, status, cnt, -2, (int)i, p, -1, 0, 1);
+        if (x > px) chi += dir;
     }
     if (cnt && nroots) atomicAdd(&cnt[CNT_ROOTS], (unsigned long long)nroots);
     Set2D S;
     S.c_lo = 0;
     S.c_hi = n_chains;
-    const T A = chord_angles<T>(ctrl, chain_off, S, px, py, chi);
+    const T A = chord_angles<T>(ctrl, chain_off, S, px, py, chi, [&](int64_t c) {
+        if (chi_out) cert_push(cert, cert_count, status, cnt, -3, (int)i, (int)c, -1, 0, 1);
+    });
     if (w_out) w_out[i] = w_of<T>(chi, A);
     if (chi_out) chi_out[i] = chi;
     if (b_out) b_out[i] = Num<T>::mul(A, Num<T>::inv2pi);
 }
 
+// Listed (query, piece) pairs of the point path: the float path's own
+// decision (the same tests as eval2d_points_kernel, including its x-range
+// shortcuts) against the float64 one; the count, and w, corrected by the
+// difference.
+template <typename T>
+__global__ void __launch_bounds__(128) eval2d_points_cert_kernel(
+    const T *__restrict__ ctrl, const int64_t *__restrict__ chain_off, const T *__restrict__ piece_y,
+    const T *__restrict__ piece_rec, const T *__restrict__ piece_x, const int64_t *__restrict__ piece_seg,
+    const double2 *__restrict__ piece_u, const T *__restrict__ pts, const int4 *__restrict__ cert,
+    const int32_t *__restrict__ cert_count, T *w_out, int32_t *chi_out, unsigned long long *cnt) {
+    int n = *cert_count;
+    if (n > GWN_CERT_CAP) n = GWN_CERT_CAP;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const int4 a = cert[2 * k];
+        const int64_t i = a.y;
+        const int p = a.z;
+        const T px = pts[2 * i], py = pts[2 * i + 1];
+        if (a.x == -3) {                                    // the chord of chain p: the count only
+            const int2 fe = chord_counts<T>(ctrl, chain_off, (int64_t)p, px, py);
+            if (fe.x != fe.y && chi_out) {
+                atomicAdd(&chi_out[i], fe.y - fe.x);
+                if (cnt) atomicAdd(&cnt[CNT_CERT_FIX], 1ull);
+            }
+            continue;
+        }
+        const T ya = piece_y[2 * p], yb = piece_y[2 * p + 1];
+        const T lo = ya < yb ? ya : yb, hi = ya < yb ? yb : ya;
+        int f = 0;
+        if (lo <= py && py < hi) {
+            const int dir = yb > ya ? 1 : -1;
+            if (px < piece_x[2 * p]) {
+                f = dir;
+            } else if (px < piece_x[2 * p + 1]) {
+                T rec[PC_FIELDS];
+                load_rec<T>(piece_rec, p, rec);
+                int iters;
+                const T x = piece_root_rec<T>(rec, py, &iters);
+                f = x > px ? dir : 0;
+            }
+        }
+        const ExactCross ec = piece_exact<T>(ctrl, piece_seg[p], piece_u[p], (double)py);
+        const int e = ec.dir && ec.x > (double)px ? ec.dir : 0;
+        if (e != f) {
+            if (w_out) atomicAdd(&w_out[i], (T)(e - f));
+            if (chi_out) atomicAdd(&chi_out[i], e - f);
+            if (cnt) atomicAdd(&cnt[CNT_CERT_FIX], 1ull);
+        }
+    }
+}
+
 cudaError_t launch_eval2d_points(const ChainSet &cs, const QuerySrc &q, void *w_out, int32_t *chi_out, void *b_out,
-                                 unsigned long long *cnt, int *status, cudaStream_t st) {
+                                 unsigned long long *cnt, int *status, cudaStream_t st, int4 *cert,
+                                 int32_t *cert_count) {
     if (q.n == 0) return cudaSuccess;
+    if (!cert || !cert_count) return cudaErrorInvalidValue;
     int64_t blocks = (q.n + 255) / 256;
-    if (blocks > 0x7fffffff) return cudaErrorInvalidValue;
-    if (cs.dtype == GWN_F64)
+    if (blocks > 0x7fffffff || q.n > 0x7fffffff) return cudaErrorInvalidValue;
+    cudaError_t e = cudaMemsetAsync(cert_count, 0, sizeof(int32_t), st);
+    if (e != cudaSuccess) return e;
+    if (cs.dtype == GWN_F64) {
         eval2d_points_kernel<double><<<(unsigned)blocks, 256, 0, st>>>(
             (const double *)cs.ctrl, cs.chain_off, cs.n_chains, (const double *)cs.piece_yT,
             (const double *)cs.piece_rec, (const double *)cs.piece_xT, cs.bucket_off, cs.bucket_idx, cs.n_buckets,
-            cs.bucket_y0, cs.bucket_inv_h, q.pts64, q.n, (double *)w_out, chi_out, (double *)b_out, cnt, status);
-    else
+            cs.bucket_y0, cs.bucket_inv_h, q.pts64, q.n, (double *)w_out, chi_out, (double *)b_out, cnt, status,
+            (const double *)cs.piece_eps, cs.eps_abs, cert, cert_count);
+        e = cudaGetLastError();
+        if (e == cudaSuccess)
+            eval2d_points_cert_kernel<double><<<64, 128, 0, st>>>(
+                (const double *)cs.ctrl, cs.chain_off, (const double *)cs.piece_yT, (const double *)cs.piece_rec,
+                (const double *)cs.piece_xT, cs.piece_seg, cs.piece_u, q.pts64, cert, cert_count, (double *)w_out,
+                chi_out, cnt);
+    } else {
         eval2d_points_kernel<float><<<(unsigned)blocks, 256, 0, st>>>(
             (const float *)cs.ctrl, cs.chain_off, cs.n_chains, (const float *)cs.piece_yT,
             (const float *)cs.piece_rec, (const float *)cs.piece_xT, cs.bucket_off, cs.bucket_idx, cs.n_buckets,
             (float)cs.bucket_y0, (float)cs.bucket_inv_h, q.pts, q.n, (float *)w_out, chi_out, (float *)b_out, cnt,
-            status);
+            status, (const float *)cs.piece_eps, (float)cs.eps_abs, cert, cert_count);
+        e = cudaGetLastError();
+        if (e == cudaSuccess)
+            eval2d_points_cert_kernel<float><<<64, 128, 0, st>>>(
+                (const float *)cs.ctrl, cs.chain_off, (const float *)cs.piece_yT, (const float *)cs.piece_rec,
+                (const float *)cs.piece_xT, cs.piece_seg, cs.piece_u, q.pts, cert, cert_count, (float *)w_out,
+                chi_out, cnt);
+    }
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 

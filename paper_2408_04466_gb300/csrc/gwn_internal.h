@@ -23,6 +23,8 @@ enum {
     CNT_DEFER_TRAV = 8,
     CNT_DEFER_BTERM = 9,
     CNT_NEWTON = 10,         // 2D: root iterations (Newton or bisection steps)
+    CNT_CERT = 11,           // 2D: crossings (or extremum rows) handed to the float64 certification
+    CNT_CERT_FIX = 12,       // 2D: query counts the certification changed
     CNT_NUM = 16
 };
 
@@ -31,7 +33,8 @@ enum {
     ST_STACK_OVERFLOW = 1,
     ST_TIMEOUT = 2,
     ST_EXPANSION_OVERFLOW = 4,
-    ST_BAD_INPUT = 8
+    ST_BAD_INPUT = 8,
+    ST_CERT_OVERFLOW = 16    // 2D: more uncertain crossings than the certification list holds
 };
 
 // Orthonormal frame of the ray direction: n = -d/|d| (pole of the boundary
@@ -160,6 +163,20 @@ struct ChainSet {
     // per piece, in the chain dtype: the piece in local power form (see
     // bezier2d.cu) -- one contiguous 16-byte aligned record per piece
     void *piece_rec = nullptr;
+    // per piece, for the float64 certification of uncertain crossings: the
+    // index of its segment's first control point, its parameter interval
+    // [u0, u1] on the segment, the pieces sharing its ends when an end is an
+    // interior extremum of y (else -1), and per end the bound on the
+    // difference between the stored end value (piece_yT) and the curve's
+    // value there (0 at control points; chain dtype)
+    int64_t *piece_seg = nullptr;
+    double2 *piece_u = nullptr;
+    // every end bound is below 8u (|y_a| + |y_b|) + eps_abs (u the unit
+    // roundoff of the chain dtype, y_a, y_b the piece's end values): a test
+    // that needs no table read rules out almost every row first
+    double eps_abs = 0.0;
+    int2 *piece_part = nullptr;
+    void *piece_eps = nullptr;
     int32_t *bucket_off = nullptr;     // [n_buckets + 1]
     int32_t *bucket_idx = nullptr;     // piece indices, bucket by bucket
     int32_t n_buckets = 0;
@@ -207,6 +224,8 @@ struct gwn_ctx {
     int32_t *d_defer_count = nullptr;         // length of the deferred-query list
     int2 *d_tpairs = nullptr;                 // traversal: unsettled (query, triangle) pairs [GWN_TPAIR_CAP]
     unsigned long long *d_work_counter = nullptr;   // 2D work-item counter
+    int4 *d_cert = nullptr;                   // 2D certification list [2 * GWN_CERT_CAP] (two int4 per entry)
+    int32_t *d_cert_count = nullptr;
     int32_t *d_tpair_count = nullptr;
     gwn::Arena scratch[8];                    // 0 chi, 1 staged points, 2 2D batch, 3 host-eval w, 4 deferred list,
                                               // 5 per-line crossing lists, 6 mesh intake and LBVH build, 7 bin sort
@@ -329,18 +348,26 @@ cudaError_t launch_chi_patches(const PatchSet &ps, const QuerySrc &q, int32_t *c
 void patches_free(PatchSet &ps);
 
 cudaError_t launch_eval2d_points(const ChainSet &cs, const QuerySrc &q, void *w_out, int32_t *chi_out, void *b_out,
-                                 unsigned long long *cnt, int *status, cudaStream_t st);
+                                 unsigned long long *cnt, int *status, cudaStream_t st, int4 *cert,
+                                 int32_t *cert_count);
 // 2D evaluation over work items: either a device work list (d_sets, d_items)
 // or one set passed by value (single, items = its row blocks).
 // shared memory of eval2d_kernel for a block of `threads` on grids up to
 // max_nx columns, and the most one block may take (sm_103a opt-in limit)
 size_t eval2d_smem(int dtype, int64_t max_nx, int threads);
 constexpr size_t EVAL2D_SMEM_MAX = 227 * 1024;
+// The launch is followed by the certification pass: crossings whose float
+// position lies within its error bound of a query column (and rows within
+// rounding of an interior extremum of y) were listed in cert by the main
+// kernel; each listed (piece, row, column) is decided again in float64 from
+// the control points and the count of a query corrected where it differs.
+// cert holds 2 * GWN_CERT_CAP int4; cert_count is reset by the launch.
+#define GWN_CERT_CAP (1 << 18)
 cudaError_t launch_eval2d_items(const ChainSet &cs, const Set2D *d_sets, const int4 *d_items, const Set2D *single,
                                 int64_t n_items,
                                 unsigned long long *d_counter, int rows_per_item, int threads, int64_t max_nx,
                                 void *w_out, int32_t *chi_out, void *b_out, unsigned long long *cnt, int *status,
-                                int sm_count, cudaStream_t st);
+                                int sm_count, cudaStream_t st, int4 *cert, int32_t *cert_count);
 gwn_status eval2d_single(gwn_geom *g, const QuerySrc &src, void *w_out, int32_t *chi_out, void *b_out,
                          unsigned long long *cnt);
 void batch_cache_free(void *p);

@@ -99,3 +99,42 @@ def test_star_chains_small_three_methods():
         wa = oracle.w2d_alg1(ctrl, P)
         assert np.abs(wq - wc)[keep].max() < 1e-12
         assert np.abs(wa - wc)[keep].max() < 1e-12
+
+
+def test_crossing_counts_certified_near_the_curve():
+    """The +x-ray count with its certification, on curves whose crossings are
+    known exactly.  (a) Two straight cubic segments (0,0)-(3,3)-(6,0): on the
+    row y = 3/2 the crossings are at x = 3/2 (upward) and 9/2 (downward); a
+    query 2^-40 to either side of x = 3/2 is decided correctly and certified,
+    one 2^-50 away is flagged (it lies on the curve at float64 resolution).
+    (b) y = x - x^2/3 on [0, 3] (one cubic, apex (3/2, 3/4)): just below the
+    apex a query between the two crossings counts -1, outside them 0; on the
+    apex row the count is 0 and only queries within float64 resolution of
+    the apex are flagged.  (c) The chord side: a chain from (0,0) to (2,2)
+    bulging to the right closes with the chord along y = x; a query 2^-40
+    left or right of it is decided exactly."""
+    line = np.array([[0, 0], [1, 1], [2, 2], [3, 3], [4, 2], [5, 1], [6, 0]], np.float64)
+    eps = 2.0 ** -40
+    P = np.array([[1.5 - eps, 1.5], [1.5 + eps, 1.5], [1.5 - 2.0 ** -50, 1.5], [1.5 + 2.0 ** -50, 1.5],
+                  [0.2, 1.5], [5.0, 1.5]])
+    _, chi, unc = oracle.w2d_closed_x(line, P, want_unc=True)
+    assert chi[:2].tolist() == [0, -1] and not unc[:2].any()
+    assert unc[2] and unc[3]
+    assert chi[4:].tolist() == [0, 0] and not unc[4:].any()
+    para = np.array([[0, 0], [1, 1], [2, 1], [3, 0]], np.float64)    # x = 3u, y = 3u(1-u)
+    for d in (2.0 ** -30, 2.0 ** -44):
+        half = math.sqrt(3.0 * d)                                   # crossings at 3/2 -+ sqrt(3 d)
+        yr = 0.75 - d
+        P = np.array([[1.5, yr], [1.5 - 2 * half, yr], [1.5 + 2 * half, yr]])
+        _, chi, unc = oracle.w2d_closed_x(para, P, want_unc=True)
+        assert chi.tolist() == [-1, 0, 0] and not unc.any(), (d, chi, unc)
+    P = np.array([[0.2, 0.75], [2.9, 0.75], [1.5, 0.75 + 2.0 ** -40], [1.5, 0.75]])
+    _, chi, unc = oracle.w2d_closed_x(para, P, want_unc=True)
+    assert chi[:3].tolist() == [0, 0, 0] and not unc[:3].any()
+    assert unc[3]                                                    # the apex itself
+    bulge = np.array([[0, 0], [2, 0], [2, 0], [2, 2]], np.float64)
+    P = np.array([[1.0 - eps, 1.0], [1.0 + eps, 1.0]])
+    _, chi, unc = oracle.w2d_closed_x(bulge, P, want_unc=True)
+    # row y = 1: the curve crosses at x = 2 - ... > 1 (upward, +1); the chord
+    # (2,2) -> (0,0) crosses at x = 1 (downward): counted only left of it
+    assert chi.tolist() == [0, 1] and not unc.any(), (chi, unc)
