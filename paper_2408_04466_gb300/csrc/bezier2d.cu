@@ -152,6 +152,31 @@ __device__ __forceinline__ T root_band(const T *r, T yr, T t) {
     return (fabs(dx) + m2x * bt) * bt + T(8) * u * (fabs(r[0]) + fabs(r[1]) + fabs(r[2])) + u * fabs(r[3]);
 }
 
+// An interval that contains the exact crossing and the float one (x, the
+// root the float path counts with).  Where root_band at Newton's own stopping
+// point is too wide to settle a query, two more Newton steps from t usually
+// shrink it to the rounding level: the interval is then the hull of x and
+// the refined root's band.  Returns false (no bound) where the bound does not
+// apply.
+template <typename T>
+__device__ __forceinline__ bool cert_interval(const T *r, T yr, T t, T x, T &lo, T &hi) {
+    T t2 = t;
+#pragma unroll
+    for (int k = 0; k < 2; k++) {
+        const T g = Num<T>::fma_(Num<T>::fma_(Num<T>::fma_(r[4], t2, r[5]), t2, r[6]), t2, r[7] - yr);
+        const T dg = Num<T>::fma_(Num<T>::fma_(r[8], t2, r[9]), t2, r[6]);
+        T tn = t2 - g / dg;
+        tn = tn < T(0) ? T(0) : (tn > T(1) ? T(1) : tn);
+        t2 = tn == tn ? tn : t2;
+    }
+    const T b2 = root_band<T>(r, yr, t2);
+    if (!(b2 < T(INFINITY))) return false;
+    const T x2 = Num<T>::fma_(Num<T>::fma_(Num<T>::fma_(r[0], t2, r[1]), t2, r[2]), t2, r[3]);
+    lo = x2 - b2 < x ? x2 - b2 : x;
+    hi = x2 + b2 > x ? x2 + b2 : x;
+    return true;
+}
+
 // the row yr lies within the rounding of one of the piece's interior-extremum
 // end values (ya = y(u0), yb = y(u1) as stored, eps their bounds).  The
 // bounds are read only when yr is within 8u (|ya| + |yb|) + eps_abs of an
@@ -987,9 +1012,10 @@ __global__ void __launch_bounds__(1024) eval2d_kernel(const T *__restrict__ ctrl
                             if (amb && !near_extremum<T>(ys[r], ya, yb, (const T *)ca.piece_eps + 2 * p,
                                                          (T)ca.eps_abs)) {
                                 int c0, c1;
-                                if (band < T(INFINITY)) {
-                                    c0 = lower_bound_cols_lin(s_ax, nx, xr - band);
-                                    c1 = upper_bound_cols_lin(s_ax, nx, xr + band);
+                                T xlo, xhi;
+                                if (cert_interval<T>(rec, ys[r], tf, xr, xlo, xhi)) {
+                                    c0 = lower_bound_cols_lin(s_ax, nx, xlo);
+                                    c1 = upper_bound_cols_lin(s_ax, nx, xhi);
                                 } else {
                                     cert_hull_cols<T>((const T *)ca.piece_x, p, -1, s_ax, nx, c0, c1);
                                 }
@@ -1044,12 +1070,19 @@ __global__ void __launch_bounds__(1024) eval2d_kernel(const T *__restrict__ ctrl
                         dirs[slot] = yb > ya ? 1 : -1;
                         {
                             const T band = root_band<T>(rec, yr, tf);
-                            int c0, c1;
+                            int c0 = 0, c1 = 0;
                             if (band < T(INFINITY)) {
                                 c0 = lower_bound_cols_lin(s_ax, nx, x - band);
                                 c1 = upper_bound_cols_lin(s_ax, nx, x + band);
-                            } else {
-                                cert_hull_cols<T>((const T *)ca.piece_x, p, -1, s_ax, nx, c0, c1);
+                            }
+                            T xlo, xhi;
+                            if (!(band < T(INFINITY)) || c1 > c0) {
+                                if (cert_interval<T>(rec, yr, tf, x, xlo, xhi)) {
+                                    c0 = lower_bound_cols_lin(s_ax, nx, xlo);
+                                    c1 = upper_bound_cols_lin(s_ax, nx, xhi);
+                                } else {
+                                    cert_hull_cols<T>((const T *)ca.piece_x, p, -1, s_ax, nx, c0, c1);
+                                }
                             }
                             if (c1 > c0 && !near_extremum<T>(yr, ya, yb, (const T *)ca.piece_eps + 2 * p, (T)ca.eps_abs))
                                 cert_push(ca.cert, ca.count, status, cnt, sets ? it.x : -1, (int)(r0 + r), (int)p,
@@ -1253,13 +1286,46 @@ __device__ __forceinline__ int bucket_of_dev(T y, T y0, T inv_h, int nb) {
     return b < nb ? b : nb - 1;
 }
 
-// Certification, per query and piece: a row within rounding of one of the
-// piece's interior-extremum end values, or a root whose error bound contains
-// the query, is listed (query, piece) for eval2d_points_cert_kernel, which
-// decides it in float64 from the control points and corrects the count; the
-// float contribution made here stays in the count until then.
+// One listed piece seen from a point query: its contribution to the float
+// count, and whether that contribution is uncertain (a row within rounding
+// of an interior-extremum end value, or a root whose error bound contains the
+// query).  The same tests serve the counting loop and the listing loop.
 template <typename T>
-__global__ void __launch_bounds__(256) eval2d_points_kernel(
+__device__ __forceinline__ int point_piece(const T *__restrict__ piece_y, const T *__restrict__ piece_rec,
+                                           const T *__restrict__ piece_x, const T *__restrict__ piece_eps,
+                                           T eps_abs, int p, T px, T py, int *status, int &nroots, bool &unc) {
+    unc = false;
+    const T ya = piece_y[2 * p], yb = piece_y[2 * p + 1];
+    const T lo = ya < yb ? ya : yb, hi = ya < yb ? yb : ya;
+    const bool crossed = lo <= py && py < hi;
+    const bool near = near_extremum<T>(py, ya, yb, piece_eps + 2 * p, eps_abs);
+    unc = near;
+    if (!crossed) return 0;
+    const int dir = yb > ya ? 1 : -1;
+    if (px < piece_x[2 * p]) return dir;                      // crossing certainly to the right
+    if (px >= piece_x[2 * p + 1]) return 0;                   // certainly not to the right
+    T rec[PC_FIELDS];
+    load_rec<T>(piece_rec, p, rec);
+    int iters;
+    T tf;
+    const T x = piece_root_rec<T>(rec, py, &iters, &tf);
+    if (iters >= Num<T>::max_iter && status) atomicOr(status, ST_TIMEOUT);
+    nroots++;
+    if (!near && !(fabs(x - px) > root_band<T>(rec, py, tf))) {
+        T xlo, xhi;
+        unc = !cert_interval<T>(rec, py, tf, x, xlo, xhi) || (xlo <= px && px <= xhi);
+    }
+    return x > px ? dir : 0;
+}
+
+// Certification: the uncertain (query, piece) pairs are listed for
+// eval2d_points_cert_kernel, which decides them in float64 from the control
+// points and corrects the count; the float contribution made here stays in
+// the count until then.  The counting loop only notes that a query has such
+// a pair; the (rare) listing loop runs the same tests again and lists them,
+// so the hot loop has no memory side effects.
+template <typename T>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 8 : 3) eval2d_points_kernel(
     const T *__restrict__ ctrl, const int64_t *__restrict__ chain_off, int64_t n_chains,
     const T *__restrict__ piece_y, const T *__restrict__ piece_rec,
     const T *__restrict__ piece_x, const int32_t *__restrict__ bucket_off, const int32_t *__restrict__ bucket_idx,
@@ -1271,30 +1337,20 @@ __global__ void __launch_bounds__(256) eval2d_points_kernel(
     const T px = pts[2 * i], py = pts[2 * i + 1];
     const int b = bucket_of_dev<T>(py, y0, inv_h, nb);
     int chi = 0, nroots = 0;
+    bool any_unc = false;
     for (int j = bucket_off[b]; j < bucket_off[b + 1]; j++) {
-        const int p = bucket_idx[j];
-        const T ya = piece_y[2 * p], yb = piece_y[2 * p + 1];
-        const T lo = ya < yb ? ya : yb, hi = ya < yb ? yb : ya;
-        const bool crossed = lo <= py && py < hi;
-        if (near_extremum<T>(py, ya, yb, piece_eps + 2 * p, eps_abs)) {
-            cert_push(cert, cert_count, status, cnt, -2, (int)i, p, -1, 0, 1);
-            if (!crossed) continue;                              // the float path's count stands until then
-        } else if (!crossed) {
-            continue;
+        bool unc;
+        chi += point_piece<T>(piece_y, piece_rec, piece_x, piece_eps, eps_abs, bucket_idx[j], px, py, status, nroots,
+                              unc);
+        any_unc = any_unc || unc;
+    }
+    if (any_unc) {
+        int nr2 = 0;
+        for (int j = bucket_off[b]; j < bucket_off[b + 1]; j++) {
+            bool unc;
+            point_piece<T>(piece_y, piece_rec, piece_x, piece_eps, eps_abs, bucket_idx[j], px, py, nullptr, nr2, unc);
+            if (unc) cert_push(cert, cert_count, status, cnt, -2, (int)i, bucket_idx[j], -1, 0, 1);
         }
-        const int dir = yb > ya ? 1 : -1;
-        if (px < piece_x[2 * p]) { chi += dir; continue; }      // crossing certainly to the right
-        if (px >= piece_x[2 * p + 1]) continue;                 // certainly not to the right
-        T rec[PC_FIELDS];
-        load_rec<T>(piece_rec, p, rec);
-        int iters;
-        T tf;
-        T x = piece_root_rec<T>(rec, py, &iters, &tf);
-        if (iters >= Num<T>::max_iter && status) atomicOr(status, ST_TIMEOUT);
-        nroots++;
-        if (!(fabs(x - px) > root_band<T>(rec, py, tf)) && !near_extremum<T>(py, ya, yb, piece_eps + 2 * p, eps_abs))
-            cert_push(cert, cert_count, status, cnt, -2, (int)i, p, -1, 0, 1);
-        if (x > px) chi += dir;
     }
     if (cnt && nroots) atomicAdd(&cnt[CNT_ROOTS], (unsigned long long)nroots);
     Set2D S;
