@@ -312,6 +312,38 @@ GWN_API gwn_status gwn_eval_batch(gwn_geom *g, const gwn_queries *queries, int64
  * (threads per block, grid rows per work item). */
 GWN_API gwn_status gwn_batch_plan_get(gwn_geom *g, int32_t *threads, int32_t *rows);
 
+/* Evaluate many meshes, each at its own queries, in one persistent launch.
+ * Defining passage: the winding number of each mesh as gwn_eval computes it;
+ * batching many inputs of uneven sizes follows the 2D experiment of
+ * Validation and Results (many random inputs, each on its own grid), here for
+ * meshes.  Work items are (mesh, run of 1024-query tiles), ordered by
+ * boundary size and claimed from an atomic counter; a block counts the
+ * crossings of its tile and runs the boundary term's main pass; list-driven
+ * kernels then settle deferred work and form w.  Each query gets the same
+ * bits as from gwn_eval on its mesh with the same d.
+ *   meshes: n mesh geometries of ctx, each already prepared for d
+ *           (gwn_mesh_prepare; GWN_E_INVALID otherwise); a mesh whose
+ *           crossing bins exist (and whose index is AUTO) uses them, else its
+ *           LBVH.
+ *   qs:     n query sets: 3D grids, or float32 points in device memory.
+ *   d:      float32[3], the direction every mesh was prepared for.
+ *   w_outs: n device float32 buffers, w_outs[i] holding qs[i]'s count.
+ *   plan:   NULL (tile run length and blocks per SM autotuned, graph on), or
+ *           rows_per_item = tiles per work item, threads_per_block = blocks
+ *           per SM (1 or 2), use_graph.
+ *   stats:  optional: n_queries, ms_total, deferred counts (synchronises).
+ * The first call with a given (meshes, queries, outputs, d) uploads a plan,
+ * times the candidate shapes and captures the launch sequence in a CUDA
+ * graph (it synchronises the stream and must not run under stream capture);
+ * later calls with the same arguments replay the graph and only enqueue
+ * work.  Up to 2^31 - 1 queries per batch. */
+GWN_API gwn_status gwn_eval_meshes(gwn_ctx *ctx, gwn_geom *const *meshes, const gwn_queries *qs, int64_t n,
+                                   const float d[3], float *const *w_outs, const gwn_plan *plan, gwn_stats *stats);
+
+/* Shape chosen for the most recent gwn_eval_meshes plan on ctx (tiles per
+ * work item, blocks per SM). */
+GWN_API gwn_status gwn_meshes_plan_get(gwn_ctx *ctx, int32_t *tiles_per_item, int32_t *blocks_per_sm);
+
 /* Gradient of w (mesh, POINTS queries) w.r.t. the query points and the mesh
  * vertices, given the upstream gradient grad_w (device float32[n]).
  * Defining passage: Conclusions (moving geometry: w recomputed as the

@@ -462,6 +462,44 @@ class _Lazy:
 GwnFunction = _Lazy()
 
 
+def eval_meshes(ctx: Context, meshes, queries, d, outs=None, tiles_per_item=0, blocks_per_sm=0, use_graph=True,
+                stats=False):
+    """w of every mesh at its own queries (Grid or device Points) in one
+    persistent launch (gwn_eval_meshes).  The meshes must be prepared for d.
+    Returns the list of float32 outputs (and the stats when asked)."""
+    torch = _torch()
+    n = len(meshes)
+    assert n == len(queries) and n >= 1
+    arr = (gwn_queries * n)()
+    keep = []
+    for i, q in enumerate(queries):
+        if not isinstance(q, (Grid, Points)):
+            raise TypeError("queries must be Grid or Points")
+        arr[i] = q.to_c(F32)
+        keep.append(q)
+    dev = torch.device("cuda", ctx.device)
+    if outs is None:
+        outs = [torch.empty(q.n, dtype=torch.float32, device=dev) for q in queries]
+    hs = (C.c_void_p * n)(*[m.h for m in meshes])
+    ws = (C.c_void_p * n)(*[o.data_ptr() for o in outs])
+    dd, dptr = _dir(d)
+    plan = gwn_plan(blocks_per_sm, tiles_per_item, 0, 1 if use_graph else 0)
+    st = gwn_stats() if stats else None
+    check(ctx.lib.gwn_eval_meshes(ctx.h, hs, arr, n, dptr, ws,
+                                  C.byref(plan) if (tiles_per_item or blocks_per_sm or not use_graph) else None,
+                                  C.byref(st) if st is not None else None), "gwn_eval_meshes")
+    if stats:
+        return outs, st.as_dict()
+    return outs
+
+
+def meshes_plan(ctx: Context):
+    """(tiles per work item, blocks per SM) of the most recent batched mesh plan."""
+    t, b = C.c_int32(), C.c_int32()
+    check(ctx.lib.gwn_meshes_plan_get(ctx.h, C.byref(t), C.byref(b)), "gwn_meshes_plan_get")
+    return t.value, b.value
+
+
 def gwn_apply(mesh: Mesh, P, V, d):
     """Differentiable w at query points P (CUDA float32 [n,3]); V must be the
     vertex tensor the mesh was built from (its gradient is dw/dV)."""

@@ -76,6 +76,8 @@ _SIGS = {
     "gwn_backward": (ST, [P, C.POINTER(gwn_queries), P, P, P, P]),
     "gwn_eval_bruteforce": (ST, [P, C.POINTER(gwn_queries), P]),
     "gwn_eval_points_noalloc": (ST, [P, P, I64, P, P]),
+    "gwn_eval_meshes": (ST, [P, P, C.POINTER(gwn_queries), I64, P, P, C.POINTER(gwn_plan), C.POINTER(gwn_stats)]),
+    "gwn_meshes_plan_get": (ST, [P, C.POINTER(I32), C.POINTER(I32)]),
 }
 
 _lib = None

@@ -18,7 +18,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libgwn.so")
-SOURCES = ["api.cpp", "bterm.cu", "traverse.cu", "bvh.cu", "backward.cu", "brute.cu", "bezier2d.cu", "batch.cu", "noalloc.cu", "patches.cu"]
+SOURCES = ["api.cpp", "bterm.cu", "traverse.cu", "bvh.cu", "backward.cu", "brute.cu", "bezier2d.cu", "batch.cu", "noalloc.cu", "patches.cu", "meshbatch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -362,6 +362,7 @@ static void ctx_release(gwn_ctx *ctx) {
     if (ctx->d_tpairs) cudaFree(ctx->d_tpairs);
     if (ctx->d_tpair_count) cudaFree(ctx->d_tpair_count);
     if (ctx->d_work_counter) cudaFree(ctx->d_work_counter);
+    if (ctx->mesh_batch_cache) mesh_batch_cache_free(ctx->mesh_batch_cache);
     if (ctx->d_cert) cudaFree(ctx->d_cert);
     if (ctx->d_cert_count) cudaFree(ctx->d_cert_count);
     for (auto &c : ctx->axis_cache)
@@ -932,7 +933,7 @@ GWN_API gwn_status gwn_mesh_boundary(const gwn_geom *g, int64_t *loop_offsets, i
 namespace gwn {
 
 // per-axis coordinate tables for a grid (float64 rule, rounded to dtype)
-static void axis_table(double lo, double hi, int64_t n, std::vector<double> &out) {
+void axis_table(double lo, double hi, int64_t n, std::vector<double> &out) {
     out.resize(n);
     if (n == 1) { out[0] = lo; return; }
     double step = (hi - lo) / (double)(n - 1);

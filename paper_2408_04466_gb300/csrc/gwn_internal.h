@@ -224,6 +224,7 @@ struct gwn_ctx {
     int32_t *d_defer_count = nullptr;         // length of the deferred-query list
     int2 *d_tpairs = nullptr;                 // traversal: unsettled (query, triangle) pairs [GWN_TPAIR_CAP]
     unsigned long long *d_work_counter = nullptr;   // 2D work-item counter
+    void *mesh_batch_cache = nullptr;         // plans of gwn_eval_meshes (meshbatch.cu)
     int4 *d_cert = nullptr;                   // 2D certification list [2 * GWN_CERT_CAP] (two int4 per entry)
     int32_t *d_cert_count = nullptr;
     int32_t *d_tpair_count = nullptr;
@@ -371,6 +372,9 @@ cudaError_t launch_eval2d_items(const ChainSet &cs, const Set2D *d_sets, const i
 gwn_status eval2d_single(gwn_geom *g, const QuerySrc &src, void *w_out, int32_t *chi_out, void *b_out,
                          unsigned long long *cnt);
 void batch_cache_free(void *p);
+void mesh_batch_cache_free(void *p);
+// coordinate table of a grid axis: lo + i ((hi - lo) / (n - 1)) in float64
+void axis_table(double lo, double hi, int64_t n, std::vector<double> &out);
 
 cudaError_t launch_bruteforce2d(const ChainSet &cs, const QuerySrc &q, void *w_out, int sm_count,
                                 cudaStream_t st);
