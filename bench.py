@@ -46,14 +46,18 @@ UNIT = "queries/s"
 #   grid      default grid resolution per axis
 #   traffic   DRAM bytes of one bterm3d_kernel launch at that grid, from ncu
 #             (dram__bytes_read.sum + dram__bytes_write.sum), valid only
-#             while csrc/bterm.cu hashes to `bterm_cu_sha256`
+#             while the boundary-term sources (csrc/bterm.cu, bterm.cuh,
+#             bterm_main_pass.inc) hash to `bterm_cu_sha256`
 #   bf_planes grid planes (of z) timed for the brute-force comparator
 #   cpu/ref   oracle queries for the CPU baseline and per reference-arm step
 MAIN = {
     "holey_heightfield": {
         "label": "holey_heightfield_8102716tris_512^3grid", "grid": 512,
         "desc": "heightfield disk, 8,102,716 triangles, 33 boundary loops (17,478 edges), 512^3 grid on [-1.1,1.1]^3",
-        "traffic": None, "bf_rows": 16, "cpu_sample": 192, "ref_sample": 48, "steps": 10,
+        # read 582.47 MB, write 503.97 MB: the 8 algorithmic bytes per query
+        # (chi in, w out: 1073.7 MB) and nothing re-read
+        "traffic": {"bytes": 1086.44e6, "bterm_cu_sha256": "994550d7d44c7a8bf1e72d1e66e500b7ac993c1c2f0a991fa72a48f01f78912f"},
+        "bf_rows": 16, "cpu_sample": 192, "ref_sample": 48, "steps": 10,
     },
     "icosphere_cap": {
         "label": "icosphere_cap_s6_73724tris_256^3grid", "grid": 256,
@@ -330,8 +334,11 @@ def run_gpu(args):
         ops = nq * ((E + L) * W_VERTEX + E * W_EDGE)
         achieved = ops / (ms_bterm * 1e-3) / 1e12
         import hashlib
-        with open(os.path.join(ROOT, "paper_2408_04466_gb300", "csrc", "bterm.cu"), "rb") as f:
-            src_hash = hashlib.sha256(f.read()).hexdigest()
+        hsh = hashlib.sha256()
+        for fn in ("bterm.cu", "bterm.cuh", "bterm_main_pass.inc"):
+            with open(os.path.join(ROOT, "paper_2408_04466_gb300", "csrc", fn), "rb") as f:
+                hsh.update(f.read())
+        src_hash = hsh.hexdigest()
         tr = spec["traffic"]
         same_src = tr is not None and src_hash == tr["bterm_cu_sha256"] and nq == MAIN[args.workload]["grid"] ** 3
         roof = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tops/s (FP32 lane ops)",
@@ -646,6 +653,43 @@ def run_other(args):
                     "directions": out_k,
                     "note": "d = +z reuses one ray per grid line; the random-d run of the same mesh and grid is "
                             "beside it"})
+    elif name == "mesh_batch":
+        # nine meshes of 1,148 to 1,035,360 triangles (icosphere caps, slit tori,
+        # holey heightfields), each with its own grid or point list, in one
+        # persistent launch replayed from a CUDA graph; the same meshes and
+        # queries as nine gwn_eval calls beside it
+        d = gen.random_direction(31)
+        specs = []
+        for sd in (3, 4, 5, 6):
+            m = gen.icosphere_cap(subdiv=sd, seed=sd)
+            specs.append((m.V, m.F, gwn.Grid((-1.2, -1.15, -1.25), (1.2, 1.3, 1.1), (24 + 8 * sd, 20 + 8 * sd, 28))))
+        for nu, nv, nq in ((96, 64, 20000), (512, 512, 300000), (720, 720, 1 << 20)):
+            m = gen.slit_torus(n_u=nu, n_v=nv, n_queries=nq, seed=nu)
+            specs.append((m.V, m.F, gwn.Points(torch.as_tensor(m.points).to(dev))))
+        for nn, holes in ((128, 6), (256, 10)):
+            m = gen.holey_heightfield(n=nn, n_holes=holes, grid_n=40, seed=nn)
+            specs.append((m.V, m.F, gwn.Grid(m.grid.lo, m.grid.hi, (48, 40, 36))))
+        meshes = [gwn.Mesh(ctx, V, F) for V, F, _ in specs]
+        for mh in meshes:
+            mh.prepare(d)
+        qs = [q for _, _, q in specs]
+        outs = [torch.empty(q.n, dtype=torch.float32, device=dev) for q in qs]
+        nq = sum(q.n for q in qs)
+        gwn.eval_meshes(ctx, meshes, qs, d, outs=outs)              # plan, autotune, capture
+        ms = _timed(lambda: gwn.eval_meshes(ctx, meshes, qs, d, outs=outs), args.steps, args.warmup, stream)
+
+        def seq():
+            for mh, q, o in zip(meshes, qs, outs):
+                mh.eval(q, d, out=o)
+        sms = _timed(seq, args.steps, args.warmup, stream)
+        out.update({"metric": "GWN queries/s, many meshes of uneven sizes in one persistent launch (CUDA graph)",
+                    "dtype": "f32", "ms_per_step": statistics.median(ms), "queries_per_step": nq,
+                    "value": nq / (statistics.median(ms) * 1e-3), "meshes": len(meshes),
+                    "triangles": [int(len(F)) for _, F, _ in specs], "plan": dict(zip(("tiles_per_item",
+                                                                                         "blocks_per_sm"),
+                                                                                        gwn.meshes_plan(ctx))),
+                    "sequential_gwn_eval_ms": statistics.median(sms),
+                    "speedup_vs_sequential": statistics.median(sms) / statistics.median(ms)})
     else:
         raise SystemExit(f"unknown workload {name}")
     if _TIMED_CLOCKS:      # SM clocks sampled (every 100 ms) during the first timed region
@@ -673,7 +717,7 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip comparator, e2e and CPU baseline legs")
     ap.add_argument("--workload", default="holey_heightfield",
                     choices=["holey_heightfield", "icosphere_cap", "circle_chain_fp64", "star_chains", "slit_torus",
-                             "icosphere_cap_axis", "chain_points", "patch_spheroid"],
+                             "icosphere_cap_axis", "chain_points", "patch_spheroid", "mesh_batch"],
                     help="holey_heightfield (default, the largest single-GPU configuration) and icosphere_cap are "
                          "the main measurement; the others print their own measurement line")
     args = ap.parse_args()
