@@ -289,8 +289,10 @@ GWN_API gwn_status gwn_eval_host(gwn_geom *g, const gwn_queries *q, const float 
 
 /* Tuning plan for batched evaluation. */
 typedef struct gwn_plan {
-    int32_t threads_per_block;  /* 0 = autotuned (128 or 256) */
-    int32_t rows_per_item;      /* 2D work item height in grid rows, 1..256; 0 = autotuned */
+    int32_t threads_per_block;  /* 2D: 32..256, a multiple of 32; 0 = autotuned (128 or 256) */
+    int32_t rows_per_item;      /* 2D work item height in grid rows, 1..256, with rows x (widest grid's
+                                   columns rounded up to 256) x 4 bytes at most 227 KB (the item's
+                                   difference cells in shared memory); 0 = autotuned (4..64) */
     int32_t pieces_per_item;    /* reserved, 0 */
     int32_t use_graph;          /* 1 = capture the launch sequence in a CUDA graph */
 } gwn_plan;

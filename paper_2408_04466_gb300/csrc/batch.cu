@@ -83,16 +83,16 @@ gwn_status eval2d_single(gwn_geom *g, const QuerySrc &src, void *w_out, int32_t 
     S.ax = cs.dtype == GWN_F64 ? (const void *)src.ax64[0] : (const void *)src.ax[0];
     S.ay = cs.dtype == GWN_F64 ? (const void *)src.ax64[1] : (const void *)src.ax[1];
     S.out_off = 0;
-    // rows per work item: enough items to fill the device twice, at most 32
+    // rows per work item: enough items to fill the device twice, at most 32,
+    // and at most 64 KB of difference cells per block.  One set, passed by
+    // value; its items are its row blocks (no work list to upload, no host
+    // synchronisation).
     int64_t rows64 = S.ny / (2 * (int64_t)(ctx->sm_count > 0 ? ctx->sm_count : 152));
-    const int rows = (int)(rows64 < 1 ? 1 : (rows64 > 32 ? 32 : rows64));
-    // one set, passed by value; its items are its row blocks (no work list to
-    // upload, no host synchronisation)
+    const int rows0 = (int)(rows64 < 1 ? 1 : (rows64 > 32 ? 32 : rows64));
+    const int cap_rows = (int)std::max<int64_t>(1, 16384 / (((int64_t)S.nx + 255) & ~(int64_t)255));
+    const int rows = std::min(rows0, cap_rows);
     int64_t n_items = (S.ny + rows - 1) / rows;
-    // four warps per block, fewer on wide grids (each warp keeps a row-wide
-    // difference array in shared memory)
-    int threads = 128;
-    while (threads > 32 && eval2d_smem(cs.dtype, S.nx, threads) > EVAL2D_SMEM_MAX) threads -= 32;
+    const int threads = 128;
     cudaError_t e = launch_eval2d_items(cs, nullptr, nullptr, &S, n_items, ctx->d_work_counter, rows, threads, S.nx,
                                         w_out, chi_out, b_out, cnt, ctx->d_status, ctx->sm_count, ctx->stream,
                                         ctx->d_cert, ctx->d_cert_count);
@@ -221,10 +221,10 @@ extern "C" GWN_API gwn_status gwn_eval_batch(gwn_geom *g, const gwn_queries *que
     }
     int want_threads = plan && plan->threads_per_block > 0 ? plan->threads_per_block : 0;
     int want_rows = plan && plan->rows_per_item > 0 ? plan->rows_per_item : 0;
-    if (want_rows > 256 || (plan && (plan->threads_per_block < 0 || plan->threads_per_block > 1024 ||
+    if (want_rows > 256 || (plan && (plan->threads_per_block < 0 || plan->threads_per_block > 256 ||
                                      plan->threads_per_block % 32 != 0))) {
         set_error("gwn_eval_batch: plan rows_per_item must be 0..256 and threads_per_block 0 or a multiple of 32 up "
-                  "to 1024");
+                  "to 256");
         return GWN_E_INVALID;
     }
     int use_graph = plan ? plan->use_graph : 1;
@@ -243,27 +243,29 @@ extern "C" GWN_API gwn_status gwn_eval_batch(gwn_geom *g, const gwn_queries *que
         if (want_threads && want_rows) cands.emplace_back(want_threads, want_rows);
         else {
             int ts[2] = {128, 256};
-            int rs[5] = {1, 4, 16, 64, 256};
+            int rs[5] = {4, 8, 16, 32, 64};
             for (int t : ts)
                 for (int r : rs)
                     if ((!want_threads || t == want_threads) && (!want_rows || r == want_rows)) cands.emplace_back(t, r);
         }
-        // shapes whose shared memory does not fit are dropped; wide grids get
-        // as many warps as fit
+        // shapes whose difference cells do not fit are dropped; wide grids get
+        // as many rows per item as fit
         int64_t mx = 0;
         for (int64_t c = 0; c < n_chains; c++) mx = std::max<int64_t>(mx, queries[c].dims[0]);
         std::vector<std::pair<int, int>> fit;
         for (auto &cd : cands)
-            if (eval2d_smem(g->cs.dtype, mx, cd.first) <= EVAL2D_SMEM_MAX) fit.push_back(cd);
+            if (eval2d_smem(g->cs.dtype, mx, cd.second) <= EVAL2D_SMEM_MAX) fit.push_back(cd);
         if (fit.empty()) {
-            if (want_threads) {
-                set_error("gwn_eval_batch: threads_per_block too large for the grid width (shared memory)");
+            if (want_rows) {
+                set_error("gwn_eval_batch: rows_per_item too large for the grid width (shared memory)");
                 delete P;
                 return GWN_E_INVALID;
             }
-            int t = 128;
-            while (t > 32 && eval2d_smem(g->cs.dtype, mx, t) > EVAL2D_SMEM_MAX) t -= 32;
-            for (auto &cd : cands) fit.emplace_back(t, cd.second);
+            int r = 64;
+            while (r > 1 && eval2d_smem(g->cs.dtype, mx, r) > EVAL2D_SMEM_MAX) r--;
+            for (auto &cd : cands) fit.emplace_back(cd.first, r);
+            std::sort(fit.begin(), fit.end());
+            fit.erase(std::unique(fit.begin(), fit.end()), fit.end());
         }
         cands = fit;
         float best = 1e30f;

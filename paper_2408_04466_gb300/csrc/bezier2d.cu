@@ -288,20 +288,14 @@ __device__ __forceinline__ void load_rec(const T *__restrict__ piece_rec, int64_
     for (int m = 0; m < W; m++) ((uint4 *)v)[m] = rp[m];
 }
 
-constexpr int CHUNK = 1024;          // crossings per pass of the per-row fallback
 constexpr int MAX_ROWS = 256;        // rows per work item
-constexpr int CAP = 4096;            // crossings binned per row sub-block
 
-// Shared-memory layout of eval2d_kernel (threads = block size):
-//   xs[CAP], ys[MAX_ROWS], pc[PC_FIELDS * threads] (T: crossings, row values,
-//   the staged data of each thread's piece), roff[MAX_ROWS + 1],
-//   rcur[MAX_ROWS + 1], ofs[threads], ra[threads], wsum[32] (int),
-//   dirs[CAP] (int8), then the item's column values ax[max_nx] (T), then per
-//   warp the difference array of the row queries (or the fallback's chi_row).
+// a piece record into L1 ahead of its use (no registers held)
 template <typename T>
-__host__ __device__ constexpr size_t eval2d_fallback_off(int threads) {
-    return ((sizeof(T) * (CAP + MAX_ROWS + (size_t)PC_FIELDS * threads) +
-             sizeof(int) * (2 * (MAX_ROWS + 1) + 2 * threads + 32) + CAP) + 15) & ~(size_t)15;
+__device__ __forceinline__ void prefetch_rec(const T *__restrict__ piece_rec, int64_t p) {
+    const char *a = (const char *)(piece_rec + (int64_t)PC_FIELDS * p);
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(a));
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(a + PC_FIELDS * sizeof(T) - 1));
 }
 
 // Chord term arithmetic.  For the chord from s to e seen from p = (xq, yr),
@@ -565,37 +559,27 @@ __device__ __forceinline__ void store_w(const Set2D &S, int64_t row, int64_t i, 
     if (b_out) b_out[o] = Num<T>::mul(A, Num<T>::inv2pi);
 }
 
-// per-warp difference-array stride: the grid width rounded up to 256 columns
-__host__ __device__ constexpr int eval2d_dstride(int max_nx) { return (max_nx + 255) & ~255; }
+// Row stride of a work item's difference cells: the grid width rounded up to
+// 256 columns (int cells).
+__host__ __device__ constexpr int eval2d_dstride(int nx) { return (nx + 255) & ~255; }
 
-// The queries of one grid row, by one warp.  The row's nk crossings come as
-// (column, direction) pairs: crossing k lies to the right of the queries
-// i < j_k (j_k = first column with x >= x_k), so D[j_k - 1] += dir_k and
+// The queries of one grid row, by one warp.  D holds the row's difference
+// cells: crossing k lies to the right of the queries i < j_k (j_k = first
+// column with x >= x_k), and added its direction to D[j_k - 1], so
 //   chi(i) = sum_{j >= i} D[j].
 // Lane l takes 8 consecutive columns of every 256: local suffix sums in
 // registers, one warp suffix scan of the lane totals per 256 columns, the
-// chunks taken from the right so the carry is known.  Then the chord term
-// is added and w stored (two 16-byte stores per lane when aligned).
+// chunks taken from the right so the carry is known; each lane resets the
+// cells it read.  Then the chord term is added and w stored (two 16-byte
+// stores per lane when aligned).
 template <typename T>
 __device__ __forceinline__ void row_queries(const Set2D &S, const T *__restrict__ ctrl,
                                             const int64_t *__restrict__ chain_off, const T *__restrict__ ax,
-                                            int nx, const int *xj, const signed char *dirs, int nk,
-                                            T yr, int64_t row, int *D, int lane, T *w_out, int32_t *chi_out,
-                                            T *b_out, const CertArgs2D &ca, int *status, unsigned long long *cnt,
-                                            int set) {
+                                            int nx, int *D, T yr, int64_t row, int lane, T *w_out,
+                                            int32_t *chi_out, T *b_out, const CertArgs2D &ca, int *status,
+                                            unsigned long long *cnt, int set) {
     const unsigned FULL = 0xffffffffu;
     const int nxp = eval2d_dstride(nx);
-    for (int c0 = 0; c0 < nxp; c0 += 256) {
-        int4 *d4 = (int4 *)(D + c0 + 8 * lane);
-        d4[0] = make_int4(0, 0, 0, 0);
-        d4[1] = make_int4(0, 0, 0, 0);
-    }
-    __syncwarp();
-    for (int k = lane; k < nk; k += 32) {
-        const int j = xj[k];
-        if (j > 0) atomicAdd(&D[j - 1], (int)dirs[k]);
-    }
-    __syncwarp();
     // chord of a single-chain set: end points and row constants hoisted
     const bool one = S.c_hi - S.c_lo == 1;
     T spx = T(0), sy = T(0), epx = T(0), ey = T(0);
@@ -612,7 +596,10 @@ __device__ __forceinline__ void row_queries(const Set2D &S, const T *__restrict_
     int carry = 0;
     for (int c0 = nxp - 256; c0 >= 0; c0 -= 256) {
         const int i0 = c0 + 8 * lane;
-        const int4 da = *(const int4 *)(D + i0), db = *(const int4 *)(D + i0 + 4);
+        int4 *d4 = (int4 *)(D + i0);
+        const int4 da = d4[0], db = d4[1];
+        d4[0] = make_int4(0, 0, 0, 0);
+        d4[1] = make_int4(0, 0, 0, 0);
         int t[8];
         t[7] = db.w; t[6] = db.z + t[7]; t[5] = db.y + t[6]; t[4] = db.x + t[5];
         t[3] = da.w + t[4]; t[2] = da.z + t[3]; t[1] = da.y + t[2]; t[0] = da.x + t[1];
@@ -661,7 +648,6 @@ __device__ __forceinline__ void row_queries(const Set2D &S, const T *__restrict_
             }
         }
     }
-    __syncwarp();
 }
 
 // exact float of a small integer (|n| < 2^22): n added to the bias 1.5 * 2^23
@@ -672,26 +658,15 @@ __device__ __forceinline__ float small_int_to_float(int n) {
 
 // The row queries on the float32 fast path (a set of one chain, w only): the
 // same steps as row_queries, with the counts turned to floats without the
-// conversion unit (exact: a row holds at most CAP crossings) and the chord
-// terms of two columns at a time in packed f32x2 arithmetic.  Rounds exactly
-// as the generic path does.  (spx, spy), (epx, epy): the chain's end points.
-__device__ __forceinline__ void row_queries_f32(const float *__restrict__ ax, int nx,
-                                                const int *xj, const signed char *dirs, int nk, float yr,
-                                                float spx, float spy, float epx, float epy,
-                                                float *__restrict__ wrow, int *D, int lane) {
+// conversion unit (exact: the caller takes this path only when the item has
+// fewer than 2^22 - 1 pieces, which bounds every count) and the chord terms
+// of two columns at a time in packed f32x2 arithmetic.  Rounds exactly as
+// the generic path does.  (spx, spy), (epx, epy): the chain's end points.
+__device__ __forceinline__ void row_queries_f32(const float *__restrict__ ax, int nx, int *D, float yr, float spx,
+                                                float spy, float epx, float epy, float *__restrict__ wrow,
+                                                int lane) {
     const unsigned FULL = 0xffffffffu;
     const int nxp = eval2d_dstride(nx);
-    for (int c0 = 0; c0 < nxp; c0 += 256) {
-        int4 *d4 = (int4 *)(D + c0 + 8 * lane);
-        d4[0] = make_int4(0, 0, 0, 0);
-        d4[1] = make_int4(0, 0, 0, 0);
-    }
-    __syncwarp();
-    for (int k = lane; k < nk; k += 32) {
-        const int j = xj[k];
-        if (j > 0) atomicAdd(&D[j - 1], (int)dirs[k]);
-    }
-    __syncwarp();
     const float sy = spy - yr, ey = epy - yr, ney = -ey, syey = sy * ey;
     const float clo = ey < sy ? ey : sy, chi_ = ey < sy ? sy : ey;
     const bool crosses = clo <= 0.f && 0.f < chi_;
@@ -703,7 +678,10 @@ __device__ __forceinline__ void row_queries_f32(const float *__restrict__ ax, in
     int carry = 0;
     for (int c0 = nxp - 256; c0 >= 0; c0 -= 256) {
         const int i0 = c0 + 8 * lane;
-        const int4 da = *(const int4 *)(D + i0), db = *(const int4 *)(D + i0 + 4);
+        int4 *d4 = (int4 *)(D + i0);
+        const int4 da = d4[0], db = d4[1];
+        d4[0] = make_int4(0, 0, 0, 0);
+        d4[1] = make_int4(0, 0, 0, 0);
         int t[8];
         t[7] = db.w; t[6] = db.z + t[7]; t[5] = db.y + t[6]; t[4] = db.x + t[5];
         t[3] = da.w + t[4]; t[2] = da.z + t[3]; t[1] = da.y + t[2]; t[0] = da.x + t[1];
@@ -750,36 +728,29 @@ __device__ __forceinline__ void row_queries_f32(const float *__restrict__ ax, in
                 if (i0 + m < nx) wp[m] = out[m];
         }
     }
-    __syncwarp();
 }
 
-// Work items are (set, block of rows[, run of pieces]).  An item finds the
-// rows each of the set's pieces crosses: a piece with end values y0, y1 is
-// crossed by row r iff min <= y_r < max, and since the row values are
-// non-decreasing those rows form one range [ra, rb), found from the row
-// spacing and corrected against the item's row values.  The per-row crossing
-// counts come from a difference array (+1 at ra, -1 at rb) and one scan, so
-// the counting pass costs O(1) per piece whatever the number of rows it
-// spans.  A work list gives each item the run of pieces that can reach its
-// rows (pieces are ordered by their lowest y per chain); a single set scans
-// all of its pieces.
+// Work items are (set, block of rows[, run of pieces]).  A piece with end
+// values y0, y1 is crossed by row r iff min <= y_r < max, and since the row
+// values are non-decreasing those rows form one range [ra, rb), found from
+// the row spacing and corrected against the item's row values.  A work list
+// gives each item the run of pieces that can reach its rows (pieces are
+// ordered by their lowest y per chain); a single set scans all its pieces.
 //
-// Roots: the (piece, row) pairs of a chunk of blockDim pieces are numbered
-// by a block-wide prefix sum of the pieces' row counts, and every thread
-// takes every blockDim-th pair (its owner piece found by binary search in the
-// prefix sums), so a piece spanning many rows is spread over many threads
-// instead of serialising one.  The chunk's pieces are staged in shared
-// memory by their owners.  Each root x_k is turned into its column j_k =
-// first grid column with x >= x_k and binned by row.
+// Roots: each warp takes 32 pieces of the run at a time (a lane per piece),
+// numbers their (piece, row) pairs by a warp prefix sum of the pieces' row
+// counts, and then every lane takes every 32nd pair, its owner found by a
+// binary search over the lanes' prefix sums and the owner's record passed by
+// shuffles -- a piece spanning many rows is spread over the warp, and no
+// block-wide barrier is needed.  Each root x_k is turned into its column
+// j_k = first grid column with x >= x_k, and its direction is added to the
+// item's difference cell (row, j_k - 1) in shared memory.
 //
-// Queries: one warp per row.  Every crossing adds its direction to a per-warp
-// difference array D[j_k - 1]; a suffix sum over the columns then gives each
+// Queries: one warp per row.  A suffix sum over the row's cells gives each
 // query i its signed count of crossings to the right,
-//   chi(i) = sum_{k : x_k > xq_i} dir_k = sum_{j >= i} D[j],
-// in O(1) per query.  The chord terms are added and w is stored (coalesced).
-// The item's rows are processed in sub-blocks whose crossings fit in CAP; a
-// single row with more than CAP crossings falls back to scanning the pieces
-// CHUNK crossings at a time.
+//   chi(i) = sum_{k : x_k > xq_i} dir_k = sum_{j >= i} D[row][j],
+// in O(1) per query, whatever the number of crossings on the row.  The
+// chord terms are added and w is stored (coalesced).
 
 template <typename T>
 __device__ __forceinline__ void cert_hull_cols(const T *px, int64_t p, int64_t q, const T *ax, int nx, int &c0,
@@ -794,8 +765,14 @@ __device__ __forceinline__ void cert_hull_cols(const T *px, int64_t p, int64_t q
     c1 = upper_bound_cols_lin(ax, nx, hi + m);
 }
 
+// shared memory of eval2d_kernel: the difference cells (rows x stride ints),
+// then the item's row values
+__host__ __device__ constexpr size_t eval2d_d2_bytes(int rows, int max_nx) {
+    return (sizeof(int) * (size_t)rows * (size_t)eval2d_dstride(max_nx) + 15) & ~(size_t)15;
+}
+
 template <typename T>
-__global__ void __launch_bounds__(1024) eval2d_kernel(const T *__restrict__ ctrl, const int64_t *__restrict__ chain_off,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) eval2d_kernel(const T *__restrict__ ctrl, const int64_t *__restrict__ chain_off,
                               const T *__restrict__ piece_y, const T *__restrict__ piece_rec,
                               const Set2D *__restrict__ sets, const int4 *__restrict__ items, const Set2D single,
                               int64_t n_items,
@@ -804,24 +781,14 @@ __global__ void __launch_bounds__(1024) eval2d_kernel(const T *__restrict__ ctrl
                               int *status, int max_nx, const CertArgs2D ca) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nthr = blockDim.x;
-    T *xs = (T *)smem_raw;                                    // CAP crossings (x; the per-row fallback)
-    int *xj = (int *)smem_raw;                                // CAP crossings (their columns; binned rows)
-    T *ys = xs + CAP;                                         // MAX_ROWS row values
-    T *s_pc = ys + MAX_ROWS;                                  // PC_FIELDS x nthr: staged piece data
-    int *roff = (int *)(s_pc + PC_FIELDS * nthr);             // MAX_ROWS + 1 offsets
-    int *rcur = roff + MAX_ROWS + 1;                          // MAX_ROWS + 1: difference array, then cursors
-    int *s_ofs = rcur + MAX_ROWS + 1;                         // per thread: first pair of its piece
-    int *s_ra = s_ofs + nthr;                                 // per thread: first row of its piece
-    int *s_wsum = s_ra + nthr;                                // per warp: pairs of its pieces
-    signed char *dirs = (signed char *)(s_wsum + 32);         // CAP directions
-    T *s_ax = (T *)(smem_raw + eval2d_fallback_off<T>(nthr));      // the item's column values
-    int *s_D = (int *)((unsigned char *)s_ax + ((sizeof(T) * (size_t)max_nx + 15) & ~(size_t)15));
-                                                                   // per warp: max_nx + 1 (fallback: chi_row)
+    int *D2 = (int *)smem_raw;                                              // rows_per_item x stride cells
+    T *ys = (T *)(smem_raw + eval2d_d2_bytes(rows_per_item, max_nx));      // the item's row values
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = nthr >> 5;
-    __shared__ int ncross;
     __shared__ long long item_sh;
     unsigned long long nroots_thread = 0;
+    // the cells start at zero; the row queries reset every cell they read
+    for (int i = threadIdx.x, nc = rows_per_item * eval2d_dstride(max_nx); i < nc; i += nthr) D2[i] = 0;
     // the next item is claimed while the current one runs (thread 0 keeps the
     // claim in a register and publishes it at the end of the item)
     if (threadIdx.x == 0) item_sh = (long long)atomicAdd(counter, 1ull);
@@ -835,283 +802,132 @@ __global__ void __launch_bounds__(1024) eval2d_kernel(const T *__restrict__ ctrl
         // one set passed by value (items are its row blocks), or a work list
         const int4 it = items ? items[item] : make_int4(0, (int)item, 0, 0);
         const Set2D S = sets ? sets[it.x] : single;
+        const int set_id = sets ? it.x : -1;
         // the pieces that can reach the item's rows (a work list carries them)
         const int64_t pA = items ? (int64_t)it.z : S.p_lo, pB = items ? (int64_t)it.w : S.p_hi;
         const T *ay = (const T *)S.ay;
+        const T *ax = (const T *)S.ax;
         const int nx = (int)S.nx;
-        int64_t r0 = (int64_t)it.y * rows_per_item;
-        int64_t r1 = r0 + rows_per_item < S.ny ? r0 + rows_per_item : S.ny;
+        const int ds = eval2d_dstride(nx);
+        const int64_t r0 = (int64_t)it.y * rows_per_item;
+        const int64_t r1 = r0 + rows_per_item < S.ny ? r0 + rows_per_item : S.ny;
         const int nr = (int)(r1 - r0);
-        for (int i = threadIdx.x; i <= nr; i += nthr) {
-            if (i < nr) ys[i] = ay[r0 + i];
-            rcur[i] = 0;
-        }
-        for (int i = threadIdx.x; i < nx; i += nthr) s_ax[i] = ((const T *)S.ax)[i];
+        for (int i = threadIdx.x; i < nr; i += nthr) ys[i] = ay[r0 + i];
         __syncthreads();
-        // pass 1: crossings per row, by a difference array over the rows.  A
-        // piece crosses row r iff lo <= y_r < hi; pieces wholly below the
-        // item's first row or above its last are skipped before the searches.
         const T y_first = ys[0], y_last = ys[nr - 1];
         const T inv_hy = nr > 1 && y_last > y_first ? T(nr - 1) / (y_last - y_first) : T(0);
-        for (int64_t p = pA + threadIdx.x; p < pB; p += nthr) {
-            T ya = piece_y[2 * p], yb = piece_y[2 * p + 1];
-            T lo = ya < yb ? ya : yb, hi = ya < yb ? yb : ya;
-            const bool overlap = hi > y_first && lo <= y_last;
-            int ra = 0, rb = 0;
-            if (overlap) {
-                ra = lower_bound_rows_grid(ys, nr, y_first, inv_hy, lo);
-                rb = lower_bound_rows_grid(ys, nr, y_first, inv_hy, hi);
-                if (ra < rb) {
-                    atomicAdd(&rcur[ra], 1);
-                    atomicAdd(&rcur[rb], -1);
+        const T a0 = ax[0];
+        const T inv_step = nx > 1 && ax[nx - 1] > ax[0] ? T(nx - 1) / (ax[nx - 1] - ax[0]) : T(0);
+        for (int64_t pb = pA + 32 * warp; pb < pB; pb += nthr) {      // warp-uniform
+            const int64_t p = pb + lane;
+            int ra = 0, n = 0;
+            if (p < pB) {
+                const T ya = piece_y[2 * p], yb = piece_y[2 * p + 1];
+                const T lo = ya < yb ? ya : yb, hi = ya < yb ? yb : ya;
+                const bool overlap = hi > y_first && lo <= y_last;
+                int rb = 0;
+                if (overlap) {
+                    ra = lower_bound_rows_grid(ys, nr, y_first, inv_hy, lo);
+                    rb = lower_bound_rows_grid(ys, nr, y_first, inv_hy, hi);
+                    n = rb > ra ? rb - ra : 0;
                 }
-            }
-            // certification: a row of the item within rounding of an
-            // interior-extremum end value (the nearest rows to each end
-            // decide whether any row is within near_window of it)
-            const T win = near_window<T>(ya, yb, (T)ca.eps_abs);
-            if (!(hi > y_first - win && lo <= y_last + win)) continue;
-            if (!overlap) {
-                ra = lower_bound_rows_grid(ys, nr, y_first, inv_hy, lo);
-                rb = lower_bound_rows_grid(ys, nr, y_first, inv_hy, hi);
-            }
-            const bool close = (ra < nr && ys[ra] - lo <= win) || (ra > 0 && lo - ys[ra - 1] <= win) ||
-                               (rb < nr && ys[rb] - hi <= win) || (rb > 0 && hi - ys[rb - 1] <= win);
-            if (close) {
-                const T *ep = (const T *)ca.piece_eps + 2 * p;
-                const int2 pq = ca.piece_part[p];
+                if (n > 0) prefetch_rec<T>(piece_rec, p);     // read again below by the lanes taking its roots
+                // certification: a row of the item within rounding of an
+                // interior-extremum end value (the nearest rows to each end
+                // decide whether any row is within near_window of it)
+                const T win = near_window<T>(ya, yb, (T)ca.eps_abs);
+                if (hi > y_first - win && lo <= y_last + win) {
+                    int ca_ = ra, cb_ = rb;
+                    if (!overlap) {
+                        ca_ = lower_bound_rows_grid(ys, nr, y_first, inv_hy, lo);
+                        cb_ = lower_bound_rows_grid(ys, nr, y_first, inv_hy, hi);
+                    }
+                    const bool close = (ca_ < nr && ys[ca_] - lo <= win) || (ca_ > 0 && lo - ys[ca_ - 1] <= win) ||
+                                       (cb_ < nr && ys[cb_] - hi <= win) || (cb_ > 0 && hi - ys[cb_ - 1] <= win);
+                    if (close) {
+                        const T *ep = (const T *)ca.piece_eps + 2 * p;
+                        const int2 pq = ca.piece_part[p];
 #pragma unroll 1
-                for (int end = 0; end < 2; end++) {
-                    const T ev = end ? ep[1] : ep[0], yv = end ? yb : ya;
-                    const int q = end ? pq.y : pq.x;
-                    // an exact end, or a partner in this item's run lists it
-                    if (!(ev > T(0)) || (q >= 0 && q < p && q >= pA)) continue;
-                    if (!(yv + T(2) * ev >= y_first && yv - T(2) * ev <= y_last)) continue;
-                    int c0 = 0, c1 = 0;
-                    bool have = false;
-                    // the rows near_extremum selects (the same comparison), searched in a wider window
-                    for (int i = lower_bound_rows_grid(ys, nr, y_first, inv_hy, yv - T(2) * ev);
-                         i < nr && ys[i] <= yv + T(2) * ev; i++) {
-                        if (!(fabs(ys[i] - yv) <= ev)) continue;
-                        if (!have) {
-                            cert_hull_cols<T>((const T *)ca.piece_x, p, q, s_ax, nx, c0, c1);
-                            have = true;
-                        }
-                        cert_push(ca.cert, ca.count, status, cnt, sets ? it.x : -1, (int)(r0 + i), (int)p, q, c0,
-                                  c1);
-                    }
-                }
-            }
-        }
-        __syncthreads();
-        if (warp == 0) {               // counts = scan of the differences; offsets = exclusive scan of the counts
-            int c1 = 0, c2 = 0;
-            for (int base = 0; base < nr; base += 32) {
-                const int r = base + lane;
-                int x = r < nr ? rcur[r] : 0;
-                for (int off = 1; off < 32; off <<= 1) {
-                    int t = __shfl_up_sync(FULL, x, off);
-                    if (lane >= off) x += t;
-                }
-                const int cr = r < nr ? c1 + x : 0;        // crossings of row r
-                c1 += __shfl_sync(FULL, x, 31);
-                int y = cr;
-                for (int off = 1; off < 32; off <<= 1) {
-                    int t = __shfl_up_sync(FULL, y, off);
-                    if (lane >= off) y += t;
-                }
-                if (r < nr) roff[r] = c2 + y - cr;
-                c2 += __shfl_sync(FULL, y, 31);
-            }
-            if (lane == 0) roff[nr] = c2;
-        }
-        __syncthreads();
-        const T a0 = s_ax[0];
-        const T inv_step = nx > 1 && s_ax[nx - 1] > s_ax[0] ? T(nx - 1) / (s_ax[nx - 1] - s_ax[0]) : T(0);
-        // rows in sub-blocks whose crossings fit in CAP (a single row with more
-        // than CAP crossings takes the per-row fallback)
-        for (int sb0 = 0; sb0 < nr;) {
-            int sb1 = sb0 + 1;
-            {
-                int lo = sb0 + 1, hi = nr;               // largest sb1 with roff[sb1] - roff[sb0] <= CAP
-                while (lo <= hi) {
-                    int mid = (lo + hi) >> 1;
-                    if (roff[mid] - roff[sb0] <= CAP) { sb1 = mid; lo = mid + 1; } else hi = mid - 1;
-                }
-            }
-            const bool fits = roff[sb1] - roff[sb0] <= CAP;
-            if (fits) {
-                const int base = roff[sb0];
-                for (int i = sb0 + threadIdx.x; i < sb1; i += nthr) rcur[i] = 0;
-                // pass 2: the roots of rows [sb0, sb1), binned by row, over
-                // chunks of nthr pieces with the (piece, row) pairs spread
-                // evenly over the threads
-                for (int64_t pc = pA; pc < pB; pc += nthr) {
-                    const int64_t p = pc + threadIdx.x;
-                    int ra = 0, n = 0;
-                    if (p < pB) {
-                        T ya = piece_y[2 * p], yb = piece_y[2 * p + 1];
-                        T lo = ya < yb ? ya : yb, hi = ya < yb ? yb : ya;
-                        if (hi > ys[sb0] && lo <= ys[sb1 - 1]) {   // else no row of the sub-block
-                            ra = lower_bound_rows_grid(ys, nr, y_first, inv_hy, lo);
-                            int rb = lower_bound_rows_grid(ys, nr, y_first, inv_hy, hi);
-                            if (ra < sb0) ra = sb0;
-                            if (rb > sb1) rb = sb1;
-                            n = rb > ra ? rb - ra : 0;
-                        }
-                    }
-                    int x = n;
-                    for (int off = 1; off < 32; off <<= 1) {
-                        int t = __shfl_up_sync(FULL, x, off);
-                        if (lane >= off) x += t;
-                    }
-                    __syncthreads();                 // the previous chunk is done with s_wsum, s_ofs, s_ra, s_pc
-                    if (lane == 31) s_wsum[warp] = x;
-                    if (n > 0) {                      // stage the piece for the threads that take its roots
-                        T v[PC_FIELDS];
-                        load_rec<T>(piece_rec, p, v);
-#pragma unroll
-                        for (int m = 0; m < PC_FIELDS; m++) s_pc[m * nthr + threadIdx.x] = v[m];
-                    }
-                    __syncthreads();
-                    int before = 0, tot = 0;
-                    for (int w = 0; w < nwarps; w++) {
-                        const int sw = s_wsum[w];
-                        before += w < warp ? sw : 0;
-                        tot += sw;
-                    }
-                    if (tot == 0) continue;           // uniform over the block
-                    s_ofs[threadIdx.x] = before + x - n;
-                    s_ra[threadIdx.x] = ra;
-                    __syncthreads();
-                    for (int k = threadIdx.x; k < tot; k += nthr) {
-                        int lo = 0, hi = nthr - 1;       // owner: last thread with s_ofs <= k
-                        while (lo < hi) {
-                            const int mid = (lo + hi + 1) >> 1;
-                            if (s_ofs[mid] <= k) lo = mid; else hi = mid - 1;
-                        }
-                        const int r = s_ra[lo] + (k - s_ofs[lo]);
-                        T rec[PC_FIELDS - 1];
-#pragma unroll
-                        for (int m = 0; m < PC_FIELDS - 1; m++) rec[m] = s_pc[m * nthr + lo];
-                        const T ya = rec[7], yb = rec[10];
-                        int iters;
-                        T tf;
-                        const T xr = piece_root_rec<T>(rec, ys[r], &iters, &tf);
-                        if (iters >= Num<T>::max_iter && status) atomicOr(status, ST_TIMEOUT);
-                        nroots_thread += (unsigned long long)iters << 32 | 1ull;
-                        const int slot = roff[r] - base + atomicAdd(&rcur[r], 1);
-                        const int col = lower_bound_cols(s_ax, nx, a0, inv_step, xr);   // its column
-                        xj[slot] = col;
-                        dirs[slot] = yb > ya ? 1 : -1;
-                        {
-                            const T band = root_band<T>(rec, ys[r], tf);
-                            const bool amb = !(band < T(INFINITY)) || (col > 0 && s_ax[col - 1] >= xr - band) ||
-                                             (col < nx && s_ax[col] <= xr + band);
-                            const int64_t p = pc + lo;
-                            if (amb && !near_extremum<T>(ys[r], ya, yb, (const T *)ca.piece_eps + 2 * p,
-                                                         (T)ca.eps_abs)) {
-                                int c0, c1;
-                                T xlo, xhi;
-                                if (cert_interval<T>(rec, ys[r], tf, xr, xlo, xhi)) {
-                                    c0 = lower_bound_cols_lin(s_ax, nx, xlo);
-                                    c1 = upper_bound_cols_lin(s_ax, nx, xhi);
-                                } else {
-                                    cert_hull_cols<T>((const T *)ca.piece_x, p, -1, s_ax, nx, c0, c1);
-                                }
-                                cert_push(ca.cert, ca.count, status, cnt, sets ? it.x : -1, (int)(r0 + r), (int)p,
-                                          -1, c0, c1);
-                            }
-                        }
-                    }
-                }
-                __syncthreads();
-                // queries: one warp per row
-                int *D = s_D + warp * eval2d_dstride(max_nx);
-                if (sizeof(T) == 4 && S.c_hi - S.c_lo == 1 && !chi_out && !b_out && w_out) {
-                    const float *sp = (const float *)ctrl + 2 * chain_off[S.c_lo];
-                    const float *ep = (const float *)ctrl + 2 * (chain_off[S.c_lo + 1] - 1);
-                    const float spx = sp[0], spy = sp[1], epx = ep[0], epy = ep[1];
-                    for (int r = sb0 + warp; r < sb1; r += nwarps)
-                        row_queries_f32((const float *)s_ax, nx,
-                                        xj + roff[r] - base, dirs + roff[r] - base,
-                                        roff[r + 1] - roff[r], (float)ys[r], spx, spy, epx, epy,
-                                        (float *)w_out + S.out_off + (r0 + r) * S.nx, D, lane);
-                } else {
-                    for (int r = sb0 + warp; r < sb1; r += nwarps)
-                        row_queries<T>(S, ctrl, chain_off, s_ax, nx, xj + roff[r] - base,
-                                       dirs + roff[r] - base, roff[r + 1] - roff[r], ys[r], r0 + r, D, lane, w_out,
-                                       chi_out, b_out, ca, status, cnt, sets ? it.x : -1);
-                }
-                __syncthreads();
-            } else {
-                // fallback for row sb0 (more than CAP crossings): CHUNK crossings per pass
-                int *chi_row = s_D;
-                const int r = sb0;
-                const T yr = ys[r];
-                for (int64_t i = threadIdx.x; i < S.nx; i += nthr) chi_row[i] = 0;
-                for (int64_t c0 = pA; c0 < pB; c0 += CHUNK) {
-                    if (threadIdx.x == 0) ncross = 0;
-                    __syncthreads();
-                    int64_t c1 = c0 + CHUNK < pB ? c0 + CHUNK : pB;
-                    for (int64_t p = c0 + threadIdx.x; p < c1; p += nthr) {
-                        T ya = piece_y[2 * p], yb = piece_y[2 * p + 1];
-                        T lo = ya < yb ? ya : yb, hi = ya < yb ? yb : ya;
-                        if (!(lo <= yr && yr < hi)) continue;
-                        T rec[PC_FIELDS];
-                        load_rec<T>(piece_rec, p, rec);
-                        int iters;
-                        T tf;
-                        T x = piece_root_rec<T>(rec, yr, &iters, &tf);
-                        if (iters >= Num<T>::max_iter && status) atomicOr(status, ST_TIMEOUT);
-                        nroots_thread += (unsigned long long)iters << 32 | 1ull;
-                        int slot = atomicAdd(&ncross, 1);
-                        xs[slot] = x;
-                        dirs[slot] = yb > ya ? 1 : -1;
-                        {
-                            const T band = root_band<T>(rec, yr, tf);
+                        for (int end = 0; end < 2; end++) {
+                            const T ev = end ? ep[1] : ep[0], yv = end ? yb : ya;
+                            const int q = end ? pq.y : pq.x;
+                            // an exact end, or a partner in this item's run lists it
+                            if (!(ev > T(0)) || (q >= 0 && q < p && q >= pA)) continue;
+                            if (!(yv + T(2) * ev >= y_first && yv - T(2) * ev <= y_last)) continue;
                             int c0 = 0, c1 = 0;
-                            if (band < T(INFINITY)) {
-                                c0 = lower_bound_cols_lin(s_ax, nx, x - band);
-                                c1 = upper_bound_cols_lin(s_ax, nx, x + band);
-                            }
-                            T xlo, xhi;
-                            if (!(band < T(INFINITY)) || c1 > c0) {
-                                if (cert_interval<T>(rec, yr, tf, x, xlo, xhi)) {
-                                    c0 = lower_bound_cols_lin(s_ax, nx, xlo);
-                                    c1 = upper_bound_cols_lin(s_ax, nx, xhi);
-                                } else {
-                                    cert_hull_cols<T>((const T *)ca.piece_x, p, -1, s_ax, nx, c0, c1);
+                            bool have = false;
+                            // the rows near_extremum selects (the same comparison), searched in a wider window
+                            for (int i = lower_bound_rows_grid(ys, nr, y_first, inv_hy, yv - T(2) * ev);
+                                 i < nr && ys[i] <= yv + T(2) * ev; i++) {
+                                if (!(fabs(ys[i] - yv) <= ev)) continue;
+                                if (!have) {
+                                    cert_hull_cols<T>((const T *)ca.piece_x, p, q, ax, nx, c0, c1);
+                                    have = true;
                                 }
+                                cert_push(ca.cert, ca.count, status, cnt, set_id, (int)(r0 + i), (int)p, q, c0, c1);
                             }
-                            if (c1 > c0 && !near_extremum<T>(yr, ya, yb, (const T *)ca.piece_eps + 2 * p, (T)ca.eps_abs))
-                                cert_push(ca.cert, ca.count, status, cnt, sets ? it.x : -1, (int)(r0 + r), (int)p,
-                                          -1, c0, c1);
                         }
                     }
-                    __syncthreads();
-                    int nc = ncross;
-                    for (int64_t i = threadIdx.x; i < S.nx; i += nthr) {
-                        T xq = s_ax[i];
-                        int acc = 0;
-                        for (int k = 0; k < nc; k++) acc += xs[k] > xq ? (int)dirs[k] : 0;
-                        chi_row[i] += acc;
-                    }
-                    __syncthreads();
                 }
-                for (int64_t i = threadIdx.x; i < S.nx; i += nthr) {
-                    int chi = chi_row[i];
-                    T A = chord_angles<T>(ctrl, chain_off, S, s_ax[i], yr, chi, [&](int64_t c) {
-                        if (chi_out)
-                            cert_push(ca.cert, ca.count, status, cnt, sets ? it.x : -1, (int)(r0 + r), (int)(-2 - c),
-                                      -1, (int)i, (int)i + 1);
-                    });
-                    store_w<T>(S, r0 + r, i, chi, A, w_out, chi_out, b_out);
-                }
-                __syncthreads();
-                sb1 = sb0 + 1;
             }
-            sb0 = sb1;
+            // the warp's (piece, row) pairs: lane l's are [ex, ex + n)
+            int x = n;
+            for (int off = 1; off < 32; off <<= 1) {
+                const int t = __shfl_up_sync(FULL, x, off);
+                if (lane >= off) x += t;
+            }
+            const int tot = __shfl_sync(FULL, x, 31);
+            const int ex = x - n;
+            for (int k0 = 0; k0 < tot; k0 += 32) {                    // warp-uniform
+                const int k = k0 + lane;
+                int o = 0;                                             // owner: last lane with ex <= k
+#pragma unroll
+                for (int step = 16; step >= 1; step >>= 1) {
+                    const int e2 = __shfl_sync(FULL, ex, o + step);
+                    if (e2 <= k) o += step;
+                }
+                const int r = __shfl_sync(FULL, ra, o) + (k - __shfl_sync(FULL, ex, o));
+                if (k >= tot) continue;
+                const int64_t pp = pb + o;
+                T rec[PC_FIELDS];
+                load_rec<T>(piece_rec, pp, rec);
+                const T ya = rec[7], yb = rec[10];
+                int iters;
+                T tf;
+                const T xr = piece_root_rec<T>(rec, ys[r], &iters, &tf);
+                if (iters >= Num<T>::max_iter && status) atomicOr(status, ST_TIMEOUT);
+                nroots_thread += (unsigned long long)iters << 32 | 1ull;
+                const int col = lower_bound_cols(ax, nx, a0, inv_step, xr);     // its column
+                if (col > 0) atomicAdd(&D2[r * ds + col - 1], yb > ya ? 1 : -1);
+                const T band = root_band<T>(rec, ys[r], tf);
+                const bool amb = !(band < T(INFINITY)) || (col > 0 && ax[col - 1] >= xr - band) ||
+                                 (col < nx && ax[col] <= xr + band);
+                if (amb && !near_extremum<T>(ys[r], ya, yb, (const T *)ca.piece_eps + 2 * pp, (T)ca.eps_abs)) {
+                    int c0, c1;
+                    T xlo, xhi;
+                    if (cert_interval<T>(rec, ys[r], tf, xr, xlo, xhi)) {
+                        c0 = lower_bound_cols_lin(ax, nx, xlo);
+                        c1 = upper_bound_cols_lin(ax, nx, xhi);
+                    } else {
+                        cert_hull_cols<T>((const T *)ca.piece_x, pp, -1, ax, nx, c0, c1);
+                    }
+                    cert_push(ca.cert, ca.count, status, cnt, set_id, (int)(r0 + r), (int)pp, -1, c0, c1);
+                }
+            }
+        }
+        __syncthreads();
+        // queries: one warp per row
+        if (sizeof(T) == 4 && S.c_hi - S.c_lo == 1 && !chi_out && !b_out && w_out && pB - pA < (1 << 22) - 1) {
+            const float *sp = (const float *)ctrl + 2 * chain_off[S.c_lo];
+            const float *ep = (const float *)ctrl + 2 * (chain_off[S.c_lo + 1] - 1);
+            const float spx = sp[0], spy = sp[1], epx = ep[0], epy = ep[1];
+            for (int r = warp; r < nr; r += nwarps)
+                row_queries_f32((const float *)ax, nx, D2 + r * ds, (float)ys[r], spx, spy, epx, epy,
+                                (float *)w_out + S.out_off + (r0 + r) * S.nx, lane);
+        } else {
+            for (int r = warp; r < nr; r += nwarps)
+                row_queries<T>(S, ctrl, chain_off, ax, nx, D2 + r * ds, ys[r], r0 + r, lane, w_out, chi_out, b_out,
+                               ca, status, cnt, set_id);
         }
         if (threadIdx.x == 0) item_sh = next_item;
         __syncthreads();
@@ -1199,12 +1015,8 @@ __global__ void __launch_bounds__(128) eval2d_cert_kernel(
     }
 }
 
-size_t eval2d_smem(int dtype, int64_t max_nx, int threads) {
-    size_t off = dtype == GWN_F64 ? eval2d_fallback_off<double>(threads) : eval2d_fallback_off<float>(threads);
-    off += ((dtype == GWN_F64 ? 8 : 4) * (size_t)max_nx + 15) & ~(size_t)15;      // ax
-    size_t per_warp = sizeof(int) * (size_t)eval2d_dstride((int)max_nx);
-    size_t d = per_warp * (size_t)(threads / 32);
-    return off + (d > sizeof(int) * (size_t)max_nx ? d : sizeof(int) * (size_t)max_nx);
+size_t eval2d_smem(int dtype, int64_t max_nx, int rows) {
+    return eval2d_d2_bytes(rows, (int)max_nx) + (dtype == GWN_F64 ? 8 : 4) * (size_t)rows;
 }
 
 cudaError_t launch_eval2d_items(const ChainSet &cs, const Set2D *d_sets, const int4 *d_items, const Set2D *single,
@@ -1213,12 +1025,15 @@ cudaError_t launch_eval2d_items(const ChainSet &cs, const Set2D *d_sets, const i
                                 int *status, int sm_count, cudaStream_t st, int4 *cert, int32_t *cert_count) {
     if (n_items == 0) return cudaSuccess;
     if (!d_sets && !single) return cudaErrorInvalidValue;
-    if (rows_per_item < 1 || rows_per_item > MAX_ROWS || threads < 32 || threads % 32) return cudaErrorInvalidValue;
+    if (rows_per_item < 1 || rows_per_item > MAX_ROWS || threads < 32 || threads > 256 || threads % 32)
+        return cudaErrorInvalidValue;
     Set2D s0;
     memset(&s0, 0, sizeof(s0));
     if (single) s0 = *single;
     if (!cert || !cert_count) return cudaErrorInvalidValue;
-    size_t smem = eval2d_smem(cs.dtype, max_nx, threads);
+    if (max_nx < 1 || max_nx > 16384) return cudaErrorInvalidValue;
+    size_t smem = eval2d_smem(cs.dtype, max_nx, rows_per_item);
+    if (smem > EVAL2D_SMEM_MAX) return cudaErrorInvalidValue;
     cudaError_t e = cudaMemsetAsync(d_counter, 0, sizeof(unsigned long long), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(cert_count, 0, sizeof(int32_t), st);
     if (e != cudaSuccess) return e;

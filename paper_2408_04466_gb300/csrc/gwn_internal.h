@@ -353,9 +353,11 @@ cudaError_t launch_eval2d_points(const ChainSet &cs, const QuerySrc &q, void *w_
                                  int32_t *cert_count);
 // 2D evaluation over work items: either a device work list (d_sets, d_items)
 // or one set passed by value (single, items = its row blocks).
-// shared memory of eval2d_kernel for a block of `threads` on grids up to
-// max_nx columns, and the most one block may take (sm_103a opt-in limit)
-size_t eval2d_smem(int dtype, int64_t max_nx, int threads);
+// shared memory of eval2d_kernel for work items of `rows` grid rows on grids
+// up to max_nx columns (one int difference cell per row and column, the
+// width rounded up to 256), and the most one block may take (sm_103a opt-in
+// limit).  Blocks have at most 256 threads.
+size_t eval2d_smem(int dtype, int64_t max_nx, int rows);
 constexpr size_t EVAL2D_SMEM_MAX = 227 * 1024;
 // The launch is followed by the certification pass: crossings whose float
 // position lies within its error bound of a query column (and rows within
