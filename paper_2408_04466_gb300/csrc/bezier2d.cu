@@ -82,15 +82,20 @@ template <> struct Num<double> {
 constexpr int PC_FIELDS = 12;
 
 // x of the crossing of the piece with record r and the row y = yr
-// (min(r7, r10) <= yr < max(r7, r10)): safeguarded Newton from the linear
-// guess, the bracket oriented so that g(lo) <= 0 < g(hi), g = y(t) - yr.
+// (min(r7, r10) <= yr < max(r7, r10)): safeguarded Newton, the bracket
+// oriented so that g(lo) <= 0 < g(hi), g = y(t) - yr.  The bracket starts as
+// the half of [0, 1] that holds the root (g at t = 1/2 against 0), and the
+// first iterate is the secant on that half.
 template <typename T>
 __device__ __forceinline__ T piece_root_rec(const T *r, T yr, int *iters_out, T *t_out = nullptr) {
     const T ya = r[7], yb = r[10];
     const bool inc = yb > ya;
     T lo = inc ? T(0) : T(1), hi = inc ? T(1) : T(0);
     const T c0 = ya - yr;
-    T t = Num<T>::div(yr - ya, yb - ya);
+    const T gm = Num<T>::fma_(Num<T>::fma_(Num<T>::fma_(r[4], T(0.5), r[5]), T(0.5), r[6]), T(0.5), c0);
+    T glo = inc ? c0 : yb - yr, ghi = inc ? yb - yr : c0;
+    if (gm <= T(0)) { lo = T(0.5); glo = gm; } else { hi = T(0.5); ghi = gm; }
+    T t = lo + Num<T>::div(-glo, ghi - glo) * (hi - lo);
     const T ytol = Num<T>::ytol * ((ya < T(0) ? -ya : ya) + (yb < T(0) ? -yb : yb));
     int it = 0;
     for (; it < Num<T>::max_iter; it++) {
@@ -145,7 +150,9 @@ __device__ __forceinline__ T root_band(const T *r, T yr, T t) {
     const T eg = T(8) * u * (fabs(r[4]) + fabs(r[5]) + fabs(r[6]) + fabs(c0)) + u * fabs(r[7]);
     const T adg = fabs(dg) - T(8) * u * (fabs(r[8]) + fabs(r[9]) + fabs(r[6]));
     const T m2 = T(6) * fabs(r[4]) + T(2) * fabs(r[5]);
-    const T bt = T(2) * (fabs(g) + eg) / adg;
+    // (a quotient of at most 2 ulp error in float32, enlarged by 2^-21 so
+    // that bt is not below the exact value)
+    const T bt = T(2) * (fabs(g) + eg) * Num<T>::div(T(1) + T(4.76837158203125e-7) * (sizeof(T) == 4), adg);
     if (!(adg > T(0)) || !(m2 * bt <= T(0.5) * adg)) return T(INFINITY);
     const T dx = Num<T>::fma_(Num<T>::fma_(T(3) * r[0], t, T(2) * r[1]), t, r[2]);
     const T m2x = T(6) * fabs(r[0]) + T(2) * fabs(r[1]);
@@ -382,6 +389,13 @@ __device__ __noinline__ int chord_sign_exact(T spx, T spy, T epx, T epy, T xq, T
     return E.sign();
 }
 
+// The float path counts the chord's crossing with the ray (right of the
+// query) iff the sign bit of cr is that of a crossing in the chord's
+// direction in y (up: clear, down: set).  The angle term takes its sign from
+// the same bit, so w is continuous across the chord, cr = +0 and -0 included.
+template <typename T>
+__device__ __forceinline__ bool chord_right(T cr, bool up) { return up != (bool)signbit(cr); }
+
 template <typename T>
 __device__ __forceinline__ bool chord_uncertain(T cr, T sx, T ex, T sy, T ey) {
     return !(fabs(cr) > T(8) * Unit<T>::u * (fabs(ex * sy) + fabs(sx * ey)));
@@ -404,12 +418,18 @@ __device__ __forceinline__ int2 chord_counts(const T *__restrict__ ctrl, const i
 #define GWN_ATC2 0.19992619f
 #define GWN_ATC1 -0.33333073f
 #define GWN_ATC0 0.99999998f
-#define GWN_PI_F 3.14159265358979f
+#define GWN_PI_2_F 1.5707963267948966f
 
-// atan2(-cr, dt) in float32 by the half-angle form: with v = -cr/(|z| + |dt|)
-// in [-1, 1] (|z|^2 = cr^2 + dt^2), atan2 = 2 atan(v) for dt >= 0 and
-// copysign(pi, -cr) - 2 atan(v) otherwise; MUFU rsqrt and reciprocal (~2 ulp).
-// Written with u = cr/(|z| + |dt|) = -v.
+// atan2(-cr, dt) in float32.  With z = |(cr, dt)| and v = dt / (|cr| + z) in
+// [-1, 1] (no cancellation: the denominator is at least z),
+//   atan2(-cr, dt) = sign(-cr) (pi/2 - 2 atan(v)),
+// the half-angle identity for the angle between the direction (dt, |cr|)
+// and the axis (0, 1); its branch cut (-cr changing sign where dt < 0) is
+// where the chord's crossing count changes, so w stays continuous.  The sign
+// is applied by flipping the sign bit (multiplying by sign(-cr)).  MUFU
+// rsqrt and reciprocal (~2 ulp); z^2 is kept at least 1e-37 so that a query
+// on a chord end point (z = 0) gets a finite term (+-pi/2; w is undefined on
+// the curve).
 __device__ __forceinline__ float frsqrt_(float x) {
     float r;
     asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
@@ -420,46 +440,45 @@ __device__ __forceinline__ float frcp_(float x) {
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
     return r;
 }
+__device__ __forceinline__ float sign_of_neg(float phi, float cr) {      // sign(-cr) * phi
+    return __uint_as_float(__float_as_uint(phi) ^ (~__float_as_uint(cr) & 0x80000000u));
+}
 __device__ __forceinline__ float chord_angle(float cr, float dt) {
-    const float z2 = __fmaf_rn(dt, dt, __fmul_rn(cr, cr));
-    if (!(z2 > 1e-37f)) return 0.f;
-    const float d = __fmaf_rn(z2, frsqrt_(z2), fabsf(dt));
-    const float u = __fmul_rn(cr, frcp_(d)), u2 = __fmul_rn(u, u);
-    float q = __fmaf_rn(GWN_ATC8, u2, GWN_ATC7);
-    q = __fmaf_rn(q, u2, GWN_ATC6);
-    q = __fmaf_rn(q, u2, GWN_ATC5);
-    q = __fmaf_rn(q, u2, GWN_ATC4);
-    q = __fmaf_rn(q, u2, GWN_ATC3);
-    q = __fmaf_rn(q, u2, GWN_ATC2);
-    q = __fmaf_rn(q, u2, GWN_ATC1);
-    q = __fmaf_rn(q, u2, GWN_ATC0);
-    const float a2n = __fmul_rn(2.f, __fmul_rn(q, u));     // -2 atan(v)
-    return dt >= 0.f ? -a2n : __fadd_rn(copysignf(GWN_PI_F, -cr), a2n);
+    const float z2 = fmaxf(__fmaf_rn(dt, dt, __fmul_rn(cr, cr)), 1e-37f);
+    const float d = __fmaf_rn(z2, frsqrt_(z2), fabsf(cr));
+    const float v = __fmul_rn(dt, frcp_(d)), v2 = __fmul_rn(v, v);
+    float q = __fmaf_rn(GWN_ATC8, v2, GWN_ATC7);
+    q = __fmaf_rn(q, v2, GWN_ATC6);
+    q = __fmaf_rn(q, v2, GWN_ATC5);
+    q = __fmaf_rn(q, v2, GWN_ATC4);
+    q = __fmaf_rn(q, v2, GWN_ATC3);
+    q = __fmaf_rn(q, v2, GWN_ATC2);
+    q = __fmaf_rn(q, v2, GWN_ATC1);
+    q = __fmaf_rn(q, v2, GWN_ATC0);
+    const float phi = __fmaf_rn(-2.f, __fmul_rn(q, v), GWN_PI_2_F);     // pi/2 - 2 atan(v)
+    return sign_of_neg(phi, cr);
 }
 
 // two chord angles at once: the same operations as chord_angle, the
 // add/mul/fma ones as packed f32x2 (fma.rn/mul.rn per element)
 __device__ __forceinline__ float2 chord_angle2(float2 cr, float2 dt) {
-    const float2 z2 = __ffma2_rn(dt, dt, __fmul2_rn(cr, cr));
-    const float2 ad = make_float2(fabsf(dt.x), fabsf(dt.y));
-    const float2 d = __ffma2_rn(z2, make_float2(frsqrt_(z2.x), frsqrt_(z2.y)), ad);
-    const float2 u = __fmul2_rn(cr, make_float2(frcp_(d.x), frcp_(d.y)));
-    const float2 u2 = __fmul2_rn(u, u);
-    float2 q = __ffma2_rn(make_float2(GWN_ATC8, GWN_ATC8), u2, make_float2(GWN_ATC7, GWN_ATC7));
-    q = __ffma2_rn(q, u2, make_float2(GWN_ATC6, GWN_ATC6));
-    q = __ffma2_rn(q, u2, make_float2(GWN_ATC5, GWN_ATC5));
-    q = __ffma2_rn(q, u2, make_float2(GWN_ATC4, GWN_ATC4));
-    q = __ffma2_rn(q, u2, make_float2(GWN_ATC3, GWN_ATC3));
-    q = __ffma2_rn(q, u2, make_float2(GWN_ATC2, GWN_ATC2));
-    q = __ffma2_rn(q, u2, make_float2(GWN_ATC1, GWN_ATC1));
-    q = __ffma2_rn(q, u2, make_float2(GWN_ATC0, GWN_ATC0));
-    const float2 a2n = __fmul2_rn(make_float2(2.f, 2.f), __fmul2_rn(q, u));
-    float2 r;
-    r.x = dt.x >= 0.f ? -a2n.x : __fadd_rn(copysignf(GWN_PI_F, -cr.x), a2n.x);
-    r.y = dt.y >= 0.f ? -a2n.y : __fadd_rn(copysignf(GWN_PI_F, -cr.y), a2n.y);
-    r.x = z2.x > 1e-37f ? r.x : 0.f;
-    r.y = z2.y > 1e-37f ? r.y : 0.f;
-    return r;
+    float2 z2 = __ffma2_rn(dt, dt, __fmul2_rn(cr, cr));
+    z2.x = fmaxf(z2.x, 1e-37f);
+    z2.y = fmaxf(z2.y, 1e-37f);
+    const float2 acr = make_float2(fabsf(cr.x), fabsf(cr.y));
+    const float2 d = __ffma2_rn(z2, make_float2(frsqrt_(z2.x), frsqrt_(z2.y)), acr);
+    const float2 v = __fmul2_rn(dt, make_float2(frcp_(d.x), frcp_(d.y)));
+    const float2 v2 = __fmul2_rn(v, v);
+    float2 q = __ffma2_rn(make_float2(GWN_ATC8, GWN_ATC8), v2, make_float2(GWN_ATC7, GWN_ATC7));
+    q = __ffma2_rn(q, v2, make_float2(GWN_ATC6, GWN_ATC6));
+    q = __ffma2_rn(q, v2, make_float2(GWN_ATC5, GWN_ATC5));
+    q = __ffma2_rn(q, v2, make_float2(GWN_ATC4, GWN_ATC4));
+    q = __ffma2_rn(q, v2, make_float2(GWN_ATC3, GWN_ATC3));
+    q = __ffma2_rn(q, v2, make_float2(GWN_ATC2, GWN_ATC2));
+    q = __ffma2_rn(q, v2, make_float2(GWN_ATC1, GWN_ATC1));
+    q = __ffma2_rn(q, v2, make_float2(GWN_ATC0, GWN_ATC0));
+    const float2 phi = __ffma2_rn(make_float2(-2.f, -2.f), __fmul2_rn(q, v), make_float2(GWN_PI_2_F, GWN_PI_2_F));
+    return make_float2(sign_of_neg(phi.x, cr.x), sign_of_neg(phi.y, cr.y));
 }
 
 template <typename T> struct Chord;
@@ -518,7 +537,7 @@ __device__ __forceinline__ T chord_angles(const T *__restrict__ ctrl, const int6
         T lo = ey < sy ? ey : sy, hi = ey < sy ? sy : ey;
         if (lo <= T(0) && T(0) < hi) {
             bool up = sy > ey;
-            bool right = up ? (cr > T(0)) : (cr < T(0));
+            const bool right = chord_right<T>(cr, up);
             if (right) chi += up ? 1 : -1;
             if (chord_uncertain<T>(cr, Num<T>::add(sp[0], -xq), Num<T>::add(ep[0], -xq), sy, ey)) on_unc(c);
         }
@@ -539,7 +558,7 @@ __device__ __forceinline__ int2 chord_counts(const T *__restrict__ ctrl, const i
     if (!(lo <= T(0) && T(0) < hi)) return make_int2(0, 0);
     const bool up = sy > ey;
     const int d = up ? 1 : -1;
-    const int f = (up ? (cr > T(0)) : (cr < T(0))) ? d : 0;
+    const int f = chord_right<T>(cr, up) ? d : 0;
     const int sg = chord_sign_exact<T>(sp[0], sp[1], ep[0], ep[1], xq, yr);
     const int e = (up ? (sg > 0) : (sg < 0)) ? d : 0;
     return make_int2(f, e);
@@ -621,7 +640,7 @@ __device__ __forceinline__ void row_queries(const Set2D &S, const T *__restrict_
                 if (one) {
                     T cr, dt;
                     chord_cd<T>(spx, sy, epx, -ey, sy * ey, xq, cr, dt);
-                    if (crosses && (up ? (cr > T(0)) : (cr < T(0)))) chi += up ? 1 : -1;
+                    if (crosses && chord_right<T>(cr, up)) chi += up ? 1 : -1;
                     if (crosses && chi_out &&
                         chord_uncertain<T>(cr, Num<T>::add(spx, -xq), Num<T>::add(epx, -xq), sy, ey))
                         cert_push(ca.cert, ca.count, status, cnt, set, (int)row, (int)(-2 - S.c_lo), -1, i, i + 1);
@@ -650,82 +669,108 @@ __device__ __forceinline__ void row_queries(const Set2D &S, const T *__restrict_
     }
 }
 
-// exact float of a small integer (|n| < 2^22): n added to the bias 1.5 * 2^23
-// in the integer domain, the bias taken off in float (no conversion unit)
-__device__ __forceinline__ float small_int_to_float(int n) {
-    return __fadd_rn(__int_as_float(0x4B400000 + n), -12582912.f);
-}
-
 // The row queries on the float32 fast path (a set of one chain, w only): the
-// same steps as row_queries, with the counts turned to floats without the
-// conversion unit (exact: the caller takes this path only when the item has
-// fewer than 2^22 - 1 pieces, which bounds every count) and the chord terms
-// of two columns at a time in packed f32x2 arithmetic.  Rounds exactly as
-// the generic path does.  (spx, spy), (epx, epy): the chain's end points.
+// same counts and chord terms as row_queries, laid out for stores: of every
+// 256 columns lane l takes the 4 at 4l and the 4 at 128 + 4l, so that each
+// 16-byte store instruction of the warp writes 512 contiguous bytes.  The
+// suffix sums of both groups of 4 run in one warp scan of the lane totals
+// packed as lo + 2^16 hi (exact while every partial sum is below 2^15 in
+// magnitude: the caller passes pack only when the item has fewer than 32767
+// pieces, and a row crosses each piece at most once); otherwise two scans.
+// The counts become floats without the conversion unit (exact: the caller
+// takes this path only when the item has fewer than 2^22 - 1 pieces), and
+// the chord terms are computed two columns at a time in packed f32x2
+// arithmetic, rounding exactly as the generic path does.  (spx, spy), (epx,
+// epy): the chain's end points.
+__device__ __forceinline__ int warp_suffix_sum(int x, int lane) {
+    for (int off = 1; off < 32; off <<= 1) {
+        const int y = __shfl_down_sync(0xffffffffu, x, off);
+        if (lane + off < 32) x += y;
+    }
+    return x;
+}
 __device__ __forceinline__ void row_queries_f32(const float *__restrict__ ax, int nx, int *D, float yr, float spx,
                                                 float spy, float epx, float epy, float *__restrict__ wrow,
-                                                int lane) {
+                                                int lane, bool pack) {
     const unsigned FULL = 0xffffffffu;
     const int nxp = eval2d_dstride(nx);
     const float sy = spy - yr, ey = epy - yr, ney = -ey, syey = sy * ey;
     const float clo = ey < sy ? ey : sy, chi_ = ey < sy ? sy : ey;
     const bool crosses = clo <= 0.f && 0.f < chi_;
     const bool up = sy > ey;
-    const float dchi = up ? 1.f : -1.f;
+    // the chord's crossing (chord_right) in the integer domain: with s = 1
+    // where cr's sign bit is set, up adds 1 - s and down adds -s
+    const int cm = crosses ? 1 : 0, cup = crosses && up ? 1 : 0;
     const float2 spx2 = make_float2(spx, spx), epx2 = make_float2(epx, epx);
     const float2 sy2 = make_float2(sy, sy), ney2 = make_float2(ney, ney), syey2 = make_float2(syey, syey);
     const float2 inv2pi2 = make_float2(Num<float>::inv2pi, Num<float>::inv2pi);
+    const float2 unbias2 = make_float2(-12582912.f, -12582912.f);
     int carry = 0;
     for (int c0 = nxp - 256; c0 >= 0; c0 -= 256) {
-        const int i0 = c0 + 8 * lane;
-        int4 *d4 = (int4 *)(D + i0);
-        const int4 da = d4[0], db = d4[1];
-        d4[0] = make_int4(0, 0, 0, 0);
-        d4[1] = make_int4(0, 0, 0, 0);
+        const int ia = c0 + 4 * lane, ib = ia + 128;
+        int4 *da4 = (int4 *)(D + ia), *db4 = (int4 *)(D + ib);
+        const int4 da = *da4, db = *db4;
+        *da4 = make_int4(0, 0, 0, 0);
+        *db4 = make_int4(0, 0, 0, 0);
         int t[8];
+        t[3] = da.w; t[2] = da.z + t[3]; t[1] = da.y + t[2]; t[0] = da.x + t[1];
         t[7] = db.w; t[6] = db.z + t[7]; t[5] = db.y + t[6]; t[4] = db.x + t[5];
-        t[3] = da.w + t[4]; t[2] = da.z + t[3]; t[1] = da.y + t[2]; t[0] = da.x + t[1];
-        int x = t[0];
-        for (int off = 1; off < 32; off <<= 1) {
-            int y = __shfl_down_sync(FULL, x, off);
-            if (lane + off < 32) x += y;
-        }
-        const int before = carry + x - t[0];         // crossings right of this lane's 8 columns
-        carry += __shfl_sync(FULL, x, 0);
-        if (i0 >= nx) continue;
-        const bool full = i0 + 8 <= nx;
-        float xq[8];
-        if (full && ((uintptr_t)(ax + i0) & 15) == 0) {
-            const float4 xa = *(const float4 *)(ax + i0), xb = *(const float4 *)(ax + i0 + 4);
-            xq[0] = xa.x; xq[1] = xa.y; xq[2] = xa.z; xq[3] = xa.w;
-            xq[4] = xb.x; xq[5] = xb.y; xq[6] = xb.z; xq[7] = xb.w;
+        int ea, eb, ta, tb;               // sums over the lanes right of this one, and over all lanes
+        if (pack) {
+            const int own = t[0] + t[4] * 65536;
+            const int x = warp_suffix_sum(own, lane);
+            const int tot = __shfl_sync(FULL, x, 0), ex = x - own;
+            ea = (int)(short)(ex & 0xffff);
+            eb = (ex - ea) >> 16;
+            ta = (int)(short)(tot & 0xffff);
+            tb = (tot - ta) >> 16;
         } else {
-#pragma unroll
-            for (int m = 0; m < 8; m++) xq[m] = ax[i0 + m < nx ? i0 + m : nx - 1];
+            const int xa = warp_suffix_sum(t[0], lane), xb = warp_suffix_sum(t[4], lane);
+            ea = xa - t[0];
+            eb = xb - t[4];
+            ta = __shfl_sync(FULL, xa, 0);
+            tb = __shfl_sync(FULL, xb, 0);
         }
-        float out[8];
+        // float of (count + bias 1.5 * 2^23) by integer addition
+        const int ba = carry + tb + ea + cup + 0x4B400000, bb = carry + eb + cup + 0x4B400000;
+        carry += ta + tb;
 #pragma unroll
-        for (int m = 0; m < 8; m += 2) {
-            const float2 nX = make_float2(-xq[m], -xq[m + 1]);
-            const float2 sx = __fadd2_rn(spx2, nX), ex = __fadd2_rn(epx2, nX);
-            const float2 cr = __ffma2_rn(ex, sy2, __fmul2_rn(sx, ney2));
-            const float2 dt = __ffma2_rn(sx, ex, syey2);
-            const float2 A = chord_angle2(cr, dt);
-            float k0 = small_int_to_float(before + t[m]), k1 = small_int_to_float(before + t[m + 1]);
-            if (crosses && (up ? (cr.x > 0.f) : (cr.x < 0.f))) k0 += dchi;
-            if (crosses && (up ? (cr.y > 0.f) : (cr.y < 0.f))) k1 += dchi;
-            const float2 o = __ffma2_rn(A, inv2pi2, make_float2(k0, k1));     // w = chi + A / 2 pi
-            out[m] = o.x;
-            out[m + 1] = o.y;
-        }
-        float *wp = wrow + i0;
-        if (full && ((uintptr_t)wp & 15) == 0) {
-            ((float4 *)wp)[0] = make_float4(out[0], out[1], out[2], out[3]);
-            ((float4 *)wp)[1] = make_float4(out[4], out[5], out[6], out[7]);
-        } else {
+        for (int g = 0; g < 2; g++) {
+            const int i0 = g ? ib : ia;
+            if (i0 >= nx) continue;
+            const bool full = i0 + 4 <= nx;
+            float xq[4];
+            if (full && ((uintptr_t)(ax + i0) & 15) == 0) {
+                const float4 xa = *(const float4 *)(ax + i0);
+                xq[0] = xa.x; xq[1] = xa.y; xq[2] = xa.z; xq[3] = xa.w;
+            } else {
 #pragma unroll
-            for (int m = 0; m < 8; m++)
-                if (i0 + m < nx) wp[m] = out[m];
+                for (int m = 0; m < 4; m++) xq[m] = ax[i0 + m < nx ? i0 + m : nx - 1];
+            }
+            float out[4];
+#pragma unroll
+            for (int m = 0; m < 4; m += 2) {
+                const float2 nX = make_float2(-xq[m], -xq[m + 1]);
+                const float2 sx = __fadd2_rn(spx2, nX), ex = __fadd2_rn(epx2, nX);
+                const float2 cr = __ffma2_rn(ex, sy2, __fmul2_rn(sx, ney2));
+                const float2 dt = __ffma2_rn(sx, ex, syey2);
+                const float2 A = chord_angle2(cr, dt);
+                const int bias = g ? bb : ba;
+                const int s0 = (__float_as_int(cr.x) >> 31) & cm, s1 = (__float_as_int(cr.y) >> 31) & cm;
+                const float2 k = __fadd2_rn(make_float2(__int_as_float(bias + t[4 * g + m] - s0),
+                                                        __int_as_float(bias + t[4 * g + m + 1] - s1)), unbias2);
+                const float2 o = __ffma2_rn(A, inv2pi2, k);     // w = chi + A / 2 pi
+                out[m] = o.x;
+                out[m + 1] = o.y;
+            }
+            float *wp = wrow + i0;
+            if (full && ((uintptr_t)wp & 15) == 0) {
+                *(float4 *)wp = make_float4(out[0], out[1], out[2], out[3]);
+            } else {
+#pragma unroll
+                for (int m = 0; m < 4; m++)
+                    if (i0 + m < nx) wp[m] = out[m];
+            }
         }
     }
 }
@@ -923,7 +968,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) eval2d_kernel(con
             const float spx = sp[0], spy = sp[1], epx = ep[0], epy = ep[1];
             for (int r = warp; r < nr; r += nwarps)
                 row_queries_f32((const float *)ax, nx, D2 + r * ds, (float)ys[r], spx, spy, epx, epy,
-                                (float *)w_out + S.out_off + (r0 + r) * S.nx, lane);
+                                (float *)w_out + S.out_off + (r0 + r) * S.nx, lane, pB - pA < 32767);
         } else {
             for (int r = warp; r < nr; r += nwarps)
                 row_queries<T>(S, ctrl, chain_off, ax, nx, D2 + r * ds, ys[r], r0 + r, lane, w_out, chi_out, b_out,
