@@ -782,12 +782,14 @@ __device__ __forceinline__ void row_queries_f32(const float *__restrict__ ax, in
 // gives each item the run of pieces that can reach its rows (pieces are
 // ordered by their lowest y per chain); a single set scans all its pieces.
 //
-// Roots: each warp takes 32 pieces of the run at a time (a lane per piece),
+// Roots: each warp takes 32 pieces of the run at a time (a lane per piece,
+// the warps interleaved so that their shares of the run stay alike),
 // numbers their (piece, row) pairs by a warp prefix sum of the pieces' row
 // counts, and then every lane takes every 32nd pair, its owner found by a
-// binary search over the lanes' prefix sums and the owner's record passed by
-// shuffles -- a piece spanning many rows is spread over the warp, and no
-// block-wide barrier is needed.  Each root x_k is turned into its column
+// binary search over the lanes' prefix sums (the owner's record, prefetched
+// into L1 when its row count was found, is read again by the lanes that
+// take its pairs) -- a piece spanning many rows is spread over the warp, and
+// no block-wide barrier is needed.  Each root x_k is turned into its column
 // j_k = first grid column with x >= x_k, and its direction is added to the
 // item's difference cell (row, j_k - 1) in shared memory.
 //
@@ -863,8 +865,10 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) eval2d_kernel(con
         const T inv_hy = nr > 1 && y_last > y_first ? T(nr - 1) / (y_last - y_first) : T(0);
         const T a0 = ax[0];
         const T inv_step = nx > 1 && ax[nx - 1] > ax[0] ? T(nx - 1) / (ax[nx - 1] - ax[0]) : T(0);
-        for (int64_t pb = pA + 32 * warp; pb < pB; pb += nthr) {      // warp-uniform
-            const int64_t p = pb + lane;
+        // warp w takes pieces w, w + nwarps, ... of each group of nthr (the
+        // warps' shares of a run, and so of its pairs, stay alike)
+        for (int64_t pb = pA + warp; pb < pB; pb += nthr) {      // warp-uniform
+            const int64_t p = pb + (int64_t)nwarps * lane;
             int ra = 0, n = 0;
             if (p < pB) {
                 const T ya = piece_y[2 * p], yb = piece_y[2 * p + 1];
@@ -933,7 +937,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) eval2d_kernel(con
                 }
                 const int r = __shfl_sync(FULL, ra, o) + (k - __shfl_sync(FULL, ex, o));
                 if (k >= tot) continue;
-                const int64_t pp = pb + o;
+                const int64_t pp = pb + (int64_t)nwarps * o;
                 T rec[PC_FIELDS];
                 load_rec<T>(piece_rec, pp, rec);
                 const T ya = rec[7], yb = rec[10];
