@@ -1006,7 +1006,9 @@ __global__ void __launch_bounds__(128) eval2d_cert_kernel(
     int n = *cert_count;
     if (n > GWN_CERT_CAP) n = GWN_CERT_CAP;
     const int lane = threadIdx.x & 31;
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarps = (gridDim.x * blockDim.x) >> 5;
+    // consecutive entries go to different blocks (and so to different SMs:
+    // an entry's float64 bisection is bound by the SM's float64 rate)
+    const int warp = (threadIdx.x >> 5) * gridDim.x + blockIdx.x, nwarps = (gridDim.x * blockDim.x) >> 5;
     for (int i = warp; i < n; i += nwarps) {               // warp-uniform
         const int4 a = cert[2 * i], b = cert[2 * i + 1];
         const Set2D S = a.x >= 0 ? sets[a.x] : single;
