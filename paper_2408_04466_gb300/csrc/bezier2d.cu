@@ -782,16 +782,15 @@ __device__ __forceinline__ void row_queries_f32(const float *__restrict__ ax, in
 // gives each item the run of pieces that can reach its rows (pieces are
 // ordered by their lowest y per chain); a single set scans all its pieces.
 //
-// Roots: each warp takes 32 pieces of the run at a time (a lane per piece,
-// the warps interleaved so that their shares of the run stay alike),
-// numbers their (piece, row) pairs by a warp prefix sum of the pieces' row
-// counts, and then every lane takes every 32nd pair, its owner found by a
-// binary search over the lanes' prefix sums (the owner's record, prefetched
-// into L1 when its row count was found, is read again by the lanes that
-// take its pairs) -- a piece spanning many rows is spread over the warp, and
-// no block-wide barrier is needed.  Each root x_k is turned into its column
-// j_k = first grid column with x >= x_k, and its direction is added to the
-// item's difference cell (row, j_k - 1) in shared memory.
+// Roots: the run is taken in rounds of one piece per thread.  A block-wide
+// prefix sum of the pieces' row counts numbers the round's (piece, row)
+// pairs, and every thread takes every blockDim-th pair, its owner found by a
+// binary search over the prefix sums (the owner's record, prefetched into L1
+// when its row count was found, is read again by the threads that take its
+// pairs) -- a piece spanning many rows is spread over the block, and the
+// threads' shares stay alike.  Each root x_k is turned into its column j_k =
+// first grid column with x >= x_k, and its direction is added to the item's
+// difference cell (row, j_k - 1) in shared memory.
 //
 // Queries: one warp per row.  A suffix sum over the row's cells gives each
 // query i its signed count of crossings to the right,
@@ -833,6 +832,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) eval2d_kernel(con
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = nthr >> 5;
     __shared__ long long item_sh;
+    __shared__ int s_ofs[256], s_ra[256], s_wsum[8];       // a round's pair offsets and first rows
     unsigned long long nroots_thread = 0;
     // the cells start at zero; the row queries reset every cell they read
     for (int i = threadIdx.x, nc = rows_per_item * eval2d_dstride(max_nx); i < nc; i += nthr) D2[i] = 0;
@@ -865,10 +865,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) eval2d_kernel(con
         const T inv_hy = nr > 1 && y_last > y_first ? T(nr - 1) / (y_last - y_first) : T(0);
         const T a0 = ax[0];
         const T inv_step = nx > 1 && ax[nx - 1] > ax[0] ? T(nx - 1) / (ax[nx - 1] - ax[0]) : T(0);
-        // warp w takes pieces w, w + nwarps, ... of each group of nthr (the
-        // warps' shares of a run, and so of its pairs, stay alike)
-        for (int64_t pb = pA + warp; pb < pB; pb += nthr) {      // warp-uniform
-            const int64_t p = pb + (int64_t)nwarps * lane;
+        for (int64_t pc = pA; pc < pB; pc += nthr) {             // block-uniform
+            const int64_t p = pc + threadIdx.x;
             int ra = 0, n = 0;
             if (p < pB) {
                 const T ya = piece_y[2 * p], yb = piece_y[2 * p + 1];
@@ -919,25 +917,31 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) eval2d_kernel(con
                     }
                 }
             }
-            // the warp's (piece, row) pairs: lane l's are [ex, ex + n)
+            // the round's (piece, row) pairs: thread i's are [s_ofs[i], s_ofs[i] + n)
             int x = n;
             for (int off = 1; off < 32; off <<= 1) {
                 const int t = __shfl_up_sync(FULL, x, off);
                 if (lane >= off) x += t;
             }
-            const int tot = __shfl_sync(FULL, x, 31);
-            const int ex = x - n;
-            for (int k0 = 0; k0 < tot; k0 += 32) {                    // warp-uniform
-                const int k = k0 + lane;
-                int o = 0;                                             // owner: last lane with ex <= k
-#pragma unroll
-                for (int step = 16; step >= 1; step >>= 1) {
-                    const int e2 = __shfl_sync(FULL, ex, o + step);
-                    if (e2 <= k) o += step;
+            if (lane == 31) s_wsum[warp] = x;
+            __syncthreads();
+            int tot = 0, before = 0;
+            for (int w = 0; w < nwarps; w++) {
+                const int sw = s_wsum[w];
+                before += w < warp ? sw : 0;
+                tot += sw;
+            }
+            s_ofs[threadIdx.x] = before + x - n;
+            s_ra[threadIdx.x] = ra;
+            __syncthreads();
+            for (int k = threadIdx.x; k < tot; k += nthr) {
+                int o = 0, hi = nthr - 1;                              // owner: last thread with s_ofs <= k
+                while (o < hi) {
+                    const int mid = (o + hi + 1) >> 1;
+                    if (s_ofs[mid] <= k) o = mid; else hi = mid - 1;
                 }
-                const int r = __shfl_sync(FULL, ra, o) + (k - __shfl_sync(FULL, ex, o));
-                if (k >= tot) continue;
-                const int64_t pp = pb + (int64_t)nwarps * o;
+                const int r = s_ra[o] + (k - s_ofs[o]);
+                const int64_t pp = pc + o;
                 T rec[PC_FIELDS];
                 load_rec<T>(piece_rec, pp, rec);
                 const T ya = rec[7], yb = rec[10];
@@ -963,6 +967,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) eval2d_kernel(con
                     cert_push(ca.cert, ca.count, status, cnt, set_id, (int)(r0 + r), (int)pp, -1, c0, c1);
                 }
             }
+            __syncthreads();           // s_wsum, s_ofs, s_ra are rewritten by the next round
         }
         __syncthreads();
         // queries: one warp per row
