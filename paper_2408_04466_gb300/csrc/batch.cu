@@ -237,7 +237,7 @@ extern "C" GWN_API gwn_status gwn_eval_batch(gwn_geom *g, const gwn_queries *que
         P = new (std::nothrow) BatchPlan();
         if (!P) { set_error("gwn_eval_batch: out of host memory"); return GWN_E_OOM; }
         P->key = key;
-        // autotune: time each candidate shape once (after a warm-up) on the
+        // autotune: time each candidate shape (best of three after a warm-up) on the
         // real work list and keep the fastest
         std::vector<std::pair<int, int>> cands;
         if (want_threads && want_rows) cands.emplace_back(want_threads, want_rows);
@@ -276,8 +276,9 @@ extern "C" GWN_API gwn_status gwn_eval_batch(gwn_geom *g, const gwn_queries *que
         for (auto &cd : cands) {
             gwn_status s = plan_upload(g, queries, n_chains, out_offsets, P, cd.second);
             if (s != GWN_OK) { delete P; cudaEventDestroy(e0); cudaEventDestroy(e1); return s; }
-            float ms = 0.f;
-            for (int rep = 0; rep < 2; rep++) {
+            // one warm-up launch, then the fastest of three
+            float ms = 1e30f;
+            for (int rep = 0; rep < 4; rep++) {
                 cudaEventRecord(e0, ctx->stream);
                 e = launch_eval2d_items(g->cs, P->d_sets, P->d_items, nullptr, P->n_items, P->d_counter, cd.second, cd.first,
                                         P->max_nx, w_out, nullptr, nullptr, nullptr, ctx->d_status, ctx->sm_count,
@@ -285,7 +286,9 @@ extern "C" GWN_API gwn_status gwn_eval_batch(gwn_geom *g, const gwn_queries *que
                 cudaEventRecord(e1, ctx->stream);
                 if (e != cudaSuccess) break;
                 cudaEventSynchronize(e1);
-                cudaEventElapsedTime(&ms, e0, e1);
+                float t = 0.f;
+                cudaEventElapsedTime(&t, e0, e1);
+                if (rep > 0 && t < ms) ms = t;
             }
             if (e != cudaSuccess) { delete P; cudaEventDestroy(e0); cudaEventDestroy(e1); return cuda_fail(e, "autotune"); }
             if (ms < best) { best = ms; bt = cd.first; br = cd.second; }
