@@ -935,11 +935,10 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) eval2d_kernel(con
             s_ra[threadIdx.x] = ra;
             __syncthreads();
             for (int k = threadIdx.x; k < tot; k += nthr) {
-                int o = 0, hi = nthr - 1;                              // owner: last thread with s_ofs <= k
-                while (o < hi) {
-                    const int mid = (o + hi + 1) >> 1;
-                    if (s_ofs[mid] <= k) o = mid; else hi = mid - 1;
-                }
+                int o = 0;                     // owner: last thread with s_ofs <= k (s_ofs[0] = 0; blocks <= 256)
+#pragma unroll
+                for (int step = 128; step >= 1; step >>= 1)
+                    if (o + step < nthr && s_ofs[o + step] <= k) o += step;
                 const int r = s_ra[o] + (k - s_ofs[o]);
                 const int64_t pp = pc + o;
                 T rec[PC_FIELDS];
