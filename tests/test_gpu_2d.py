@@ -174,12 +174,15 @@ def _zigzag(n):
     return ctrl
 
 
-@pytest.mark.parametrize("n, dims", [(600, (64, 256)), (8500, (24, 12))])
-def test_many_crossings_per_row(gwn, ctx, n, dims):
-    """A zig-zag chain crossing every row n times (up to 8500 crossings on a
-    row, 150k in one work item).  64 rows per work item and 4 rows per work
-    item agree exactly, and with the oracle's closed form."""
-    ctrl = _zigzag(n)
+@pytest.mark.parametrize("n, dims, dtype", [(600, (64, 256), np.float64), (8500, (24, 12), np.float64),
+                                            (33000, (40, 8), np.float32)])
+def test_many_crossings_per_row(gwn, ctx, n, dims, dtype):
+    """A zig-zag chain crossing every row n times (up to 33000 crossings on a
+    row, 264k in one work item).  64 rows per work item and 4 rows per work
+    item agree exactly, and with the oracle's closed form; the float32 case
+    takes the fast row path with the two separate lane scans (more than 32766
+    pieces in an item), which must give the generic path's w bit for bit."""
+    ctrl = _zigzag(n).astype(dtype)
     ch = gwn.Bezier2D(ctx, ctrl, [0, len(ctrl)])
     g = gen.Grid((-1.0, -1.37), (n + 1.0, 1.41), dims)
     grid = gwn.Grid(g.lo, g.hi, g.dims)
@@ -188,11 +191,12 @@ def test_many_crossings_per_row(gwn, ctx, n, dims):
     w_big = w_big.cpu().numpy()
     w_bin = w_bin.cpu().numpy()
     assert np.array_equal(w_big, w_bin)
-    P = gen.grid_points(g, np.float64)
-    wc, chic, unc = oracle.w2d_closed_x(ctrl, P, want_unc=True)
+    P = gen.grid_points(g, dtype).astype(np.float64)
+    wc, chic, unc = oracle.w2d_closed_x(ctrl.astype(np.float64), P, want_unc=True)
     assert not unc.any()
-    keep = oracle.dist2d(ctrl, P) > 1e-6
-    assert np.abs(w_bin - wc)[keep].max() < 1e-11
+    if dtype == np.float64:
+        keep = oracle.dist2d(ctrl, P) > 1e-6
+        assert np.abs(w_bin - wc)[keep].max() < 1e-11
     r = ch.eval(grid, want_chi=True)
     assert np.array_equal(r["chi"].cpu().numpy(), chic)
     assert np.array_equal(r["w"].cpu().numpy(), w_bin)
