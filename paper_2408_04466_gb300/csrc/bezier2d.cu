@@ -236,10 +236,10 @@ __device__ __forceinline__ void cert_push(int4 *cert, int32_t *cert_count, int *
     if (cnt) atomicAdd(&cnt[CNT_CERT], 1ull);
 }
 
-// Certification (see root_band): pass 1 lists the rows within rounding of a
-// piece's interior-extremum end value, once per pair of pieces sharing it,
-// with the columns of both pieces' x-ranges; pass 2 (and the per-row
-// fallback) lists each crossing whose error bound contains a query column.
+// Certification (see root_band): the scan of an item's pieces lists the rows
+// within rounding of a piece's interior-extremum end value, once per pair of
+// pieces sharing it, with the columns of both pieces' x-ranges; the root pass
+// lists each crossing whose error bound contains a query column.
 struct CertArgs2D {
     double eps_abs;            // see near_window
     const void *piece_eps;     // [n_pieces][2], chain dtype
