@@ -1195,8 +1195,16 @@ static gwn_status eval_impl(gwn_geom *g, const gwn_queries *q, const float *d, v
                 CK(cudaMemsetAsync(ctx->d_cnt, 0, sizeof(unsigned long long) * CNT_NUM, ctx->stream), "clear counters");
                 for (int k = 0; k < 3; k++) CK(cudaEventRecord(ctx->ev[k], ctx->stream), "event");
             }
+            int32_t *order = nullptr;
+            const size_t ob = eval2d_points_order_bytes(g->cs, src.n);
+            if (ob > 0) {
+                cudaError_t ae = cudaSuccess;
+                order = (int32_t *)arena_get(ctx, 8, ob, &ae);
+                if (!order) return cuda_fail(ae, "2D point order scratch");
+            }
             CK(launch_eval2d_points(g->cs, src, w_out, chi_out, b_out, stats ? ctx->d_cnt : nullptr, ctx->d_status,
-                                    ctx->stream, ctx->d_cert, ctx->d_cert_count), "2D point evaluation");
+                                    ctx->stream, ctx->d_cert, ctx->d_cert_count, order, ctx->sm_count),
+               "2D point evaluation");
             if (stats) CK(cudaEventRecord(ctx->ev[3], ctx->stream), "event");
             return read_stats(ctx, stats, nq, 0, false);
         }

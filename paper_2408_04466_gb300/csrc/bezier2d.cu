@@ -32,6 +32,8 @@
 // adds the chord terms and writes w (details at eval2d_kernel).
 #include <string.h>
 
+#include <algorithm>
+
 #include "gwn_internal.h"
 #include "predicates.cuh"
 
@@ -1201,9 +1203,12 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 8 : 3) eval2d_points_ker
     const T *__restrict__ piece_x, const int32_t *__restrict__ bucket_off, const int32_t *__restrict__ bucket_idx,
     int nb, T y0, T inv_h, const T *__restrict__ pts, int64_t n, T *__restrict__ w_out, int32_t *__restrict__ chi_out,
     T *__restrict__ b_out, unsigned long long *cnt, int *status, const T *__restrict__ piece_eps, T eps_abs,
-    int4 *cert, int32_t *cert_count) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    int4 *cert, int32_t *cert_count, const int32_t *__restrict__ order) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    // the queries in bucket order when an order is given (the warps then walk
+    // the same bucket lists), else as given
+    const int64_t i = order ? (int64_t)order[k] : k;
     const T px = pts[2 * i], py = pts[2 * i + 1];
     const int b = bucket_of_dev<T>(py, y0, inv_h, nb);
     int chi = 0, nroots = 0;
@@ -1284,21 +1289,96 @@ __global__ void __launch_bounds__(128) eval2d_points_cert_kernel(
     }
 }
 
+// Bucket order of the point queries (a counting sort, one launch per step):
+// count the queries per bucket, an exclusive scan of the counts (one block),
+// then each query takes the next slot of its bucket.  The order within a
+// bucket is arbitrary; every query's result is the same in any order.
+template <typename T>
+__global__ void points_bucket_count_kernel(const T *__restrict__ pts, int64_t n, T y0, T inv_h, int nb,
+                                           int32_t *__restrict__ count) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(&count[bucket_of_dev<T>(pts[2 * i + 1], y0, inv_h, nb)], 1);
+}
+__global__ void __launch_bounds__(1024) points_bucket_scan_kernel(int32_t *__restrict__ count, int nb) {
+    // count[0 .. nb) -> exclusive prefix sums, in chunks of 1024 with a carry
+    __shared__ int32_t s_w[32];
+    __shared__ int32_t s_carry;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) s_carry = 0;
+    __syncthreads();
+    for (int base = 0; base < nb; base += 1024) {
+        const int i = base + threadIdx.x;
+        const int v = i < nb ? count[i] : 0;
+        int x = v;
+        for (int off = 1; off < 32; off <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, x, off);
+            if (lane >= off) x += t;
+        }
+        if (lane == 31) s_w[warp] = x;
+        __syncthreads();
+        int before = s_carry, tot = s_carry;
+        for (int w = 0; w < 32; w++) {
+            const int sw = s_w[w];
+            before += w < warp ? sw : 0;
+            tot += sw;
+        }
+        if (i < nb) count[i] = before + x - v;
+        __syncthreads();                              // every thread has read s_w and s_carry
+        if (threadIdx.x == 0) s_carry = tot;
+        __syncthreads();
+    }
+}
+template <typename T>
+__global__ void points_bucket_scatter_kernel(const T *__restrict__ pts, int64_t n, T y0, T inv_h, int nb,
+                                             int32_t *__restrict__ next, int32_t *__restrict__ order) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        order[atomicAdd(&next[bucket_of_dev<T>(pts[2 * i + 1], y0, inv_h, nb)], 1)] = (int32_t)i;
+}
+
+size_t eval2d_points_order_bytes(const ChainSet &cs, int64_t n) {
+    if (n < EVAL2D_POINTS_ORDER_MIN || cs.n_buckets < 2 || cs.n_buckets > EVAL2D_POINTS_ORDER_MAX_BUCKETS) return 0;
+    return sizeof(int32_t) * ((size_t)n + (size_t)cs.n_buckets);
+}
+
 cudaError_t launch_eval2d_points(const ChainSet &cs, const QuerySrc &q, void *w_out, int32_t *chi_out, void *b_out,
                                  unsigned long long *cnt, int *status, cudaStream_t st, int4 *cert,
-                                 int32_t *cert_count) {
+                                 int32_t *cert_count, int32_t *order_buf, int sm_count) {
     if (q.n == 0) return cudaSuccess;
     if (!cert || !cert_count) return cudaErrorInvalidValue;
     int64_t blocks = (q.n + 255) / 256;
     if (blocks > 0x7fffffff || q.n > 0x7fffffff) return cudaErrorInvalidValue;
     cudaError_t e = cudaMemsetAsync(cert_count, 0, sizeof(int32_t), st);
     if (e != cudaSuccess) return e;
+    // bucket order (order_buf: n + n_buckets ints from eval2d_points_order_bytes, or null)
+    const int32_t *order = nullptr;
+    if (order_buf && eval2d_points_order_bytes(cs, q.n) > 0) {
+        int32_t *count = order_buf + q.n;
+        const int nb = (int)cs.n_buckets;
+        const unsigned g = (unsigned)std::min<int64_t>(blocks, (int64_t)(sm_count > 0 ? sm_count : 152) * 8);
+        e = cudaMemsetAsync(count, 0, sizeof(int32_t) * nb, st);
+        if (e != cudaSuccess) return e;
+        if (cs.dtype == GWN_F64)
+            points_bucket_count_kernel<double><<<g, 256, 0, st>>>(q.pts64, q.n, cs.bucket_y0, cs.bucket_inv_h, nb, count);
+        else
+            points_bucket_count_kernel<float><<<g, 256, 0, st>>>(q.pts, q.n, (float)cs.bucket_y0, (float)cs.bucket_inv_h,
+                                                                 nb, count);
+        points_bucket_scan_kernel<<<1, 1024, 0, st>>>(count, nb);
+        if (cs.dtype == GWN_F64)
+            points_bucket_scatter_kernel<double><<<g, 256, 0, st>>>(q.pts64, q.n, cs.bucket_y0, cs.bucket_inv_h, nb,
+                                                                    count, order_buf);
+        else
+            points_bucket_scatter_kernel<float><<<g, 256, 0, st>>>(q.pts, q.n, (float)cs.bucket_y0,
+                                                                   (float)cs.bucket_inv_h, nb, count, order_buf);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        order = order_buf;
+    }
     if (cs.dtype == GWN_F64) {
         eval2d_points_kernel<double><<<(unsigned)blocks, 256, 0, st>>>(
             (const double *)cs.ctrl, cs.chain_off, cs.n_chains, (const double *)cs.piece_yT,
             (const double *)cs.piece_rec, (const double *)cs.piece_xT, cs.bucket_off, cs.bucket_idx, cs.n_buckets,
             cs.bucket_y0, cs.bucket_inv_h, q.pts64, q.n, (double *)w_out, chi_out, (double *)b_out, cnt, status,
-            (const double *)cs.piece_eps, cs.eps_abs, cert, cert_count);
+            (const double *)cs.piece_eps, cs.eps_abs, cert, cert_count, order);
         e = cudaGetLastError();
         if (e == cudaSuccess)
             eval2d_points_cert_kernel<double><<<64, 128, 0, st>>>(
@@ -1310,7 +1390,7 @@ cudaError_t launch_eval2d_points(const ChainSet &cs, const QuerySrc &q, void *w_
             (const float *)cs.ctrl, cs.chain_off, cs.n_chains, (const float *)cs.piece_yT,
             (const float *)cs.piece_rec, (const float *)cs.piece_xT, cs.bucket_off, cs.bucket_idx, cs.n_buckets,
             (float)cs.bucket_y0, (float)cs.bucket_inv_h, q.pts, q.n, (float *)w_out, chi_out, (float *)b_out, cnt,
-            status, (const float *)cs.piece_eps, (float)cs.eps_abs, cert, cert_count);
+            status, (const float *)cs.piece_eps, (float)cs.eps_abs, cert, cert_count, order);
         e = cudaGetLastError();
         if (e == cudaSuccess)
             eval2d_points_cert_kernel<float><<<64, 128, 0, st>>>(

@@ -228,8 +228,9 @@ struct gwn_ctx {
     int4 *d_cert = nullptr;                   // 2D certification list [2 * GWN_CERT_CAP] (two int4 per entry)
     int32_t *d_cert_count = nullptr;
     int32_t *d_tpair_count = nullptr;
-    gwn::Arena scratch[8];                    // 0 chi, 1 staged points, 2 2D batch, 3 host-eval w, 4 deferred list,
-                                              // 5 per-line crossing lists, 6 mesh intake and LBVH build, 7 bin sort
+    gwn::Arena scratch[9];                    // 0 chi, 1 staged points, 2 2D batch, 3 host-eval w, 4 deferred list,
+                                              // 5 per-line crossing lists, 6 mesh intake and LBVH build, 7 bin sort,
+                                              // 8 2D point order
     std::vector<gwn::AxisCache> axis_cache;   // most recent grids, at most 64
     cudaEvent_t ev[8];
     bool events = false;
@@ -348,9 +349,17 @@ cudaError_t launch_chi_patches(const PatchSet &ps, const QuerySrc &q, int32_t *c
                                int *status, cudaStream_t st);
 void patches_free(PatchSet &ps);
 
+// Point queries of a chain set (one +x ray each).  order_buf (optional):
+// eval2d_points_order_bytes(cs, q.n) bytes of device scratch; when given and
+// that size is nonzero, the queries are evaluated in the order of their
+// y-buckets (a counting sort per call) so that the warps walk the same
+// bucket lists.  Results do not depend on it.
+constexpr int64_t EVAL2D_POINTS_ORDER_MIN = 65536;            // fewer queries: as given
+constexpr int64_t EVAL2D_POINTS_ORDER_MAX_BUCKETS = 1 << 20;  // more buckets: as given
+size_t eval2d_points_order_bytes(const ChainSet &cs, int64_t n);
 cudaError_t launch_eval2d_points(const ChainSet &cs, const QuerySrc &q, void *w_out, int32_t *chi_out, void *b_out,
                                  unsigned long long *cnt, int *status, cudaStream_t st, int4 *cert,
-                                 int32_t *cert_count);
+                                 int32_t *cert_count, int32_t *order_buf, int sm_count);
 // 2D evaluation over work items: either a device work list (d_sets, d_items)
 // or one set passed by value (single, items = its row blocks).
 // shared memory of eval2d_kernel for work items of `rows` grid rows on grids
