@@ -202,6 +202,30 @@ def test_many_crossings_per_row(gwn, ctx, n, dims, dtype):
     assert np.array_equal(r["w"].cpu().numpy(), w_bin)
 
 
+def test_point_queries_bucket_order(gwn, ctx):
+    """From 65,536 points on, the point path evaluates the queries in the
+    order of their y-buckets: w and chi equal, bit for bit, those of the
+    same points evaluated in chunks below that size (the given order), float32
+    and float64; chi matches the oracle on a sample."""
+    import torch
+    rng = np.random.default_rng(33)
+    cs = gen.star_chains(n_chains=1, seg_lo=600, seg_hi=600, grid_n=16, seed=4)
+    circ = gen.bezier_circle_chain()
+    for ctrl, g, dt in ((cs.ctrl, cs.grids[0], np.float32), (circ.ctrl, circ.grids[0], np.float64)):
+        ch = gwn.Bezier2D(ctx, np.ascontiguousarray(ctrl, dt), [0, len(ctrl)])
+        n = 150000
+        P = np.stack([rng.uniform(g.lo[0], g.hi[0], n), rng.uniform(g.lo[1], g.hi[1], n)], 1).astype(dt)
+        Pt = torch.as_tensor(P).cuda()
+        r = ch.eval(gwn.Points(Pt), want_chi=True)
+        w, chi = r["w"].cpu().numpy(), r["chi"].cpu().numpy()
+        parts = [ch.eval(gwn.Points(Pt[a:a + 50000]), want_chi=True) for a in range(0, n, 50000)]
+        assert np.array_equal(w, np.concatenate([q["w"].cpu().numpy() for q in parts]))
+        assert np.array_equal(chi, np.concatenate([q["chi"].cpu().numpy() for q in parts]))
+        sub = rng.choice(n, 3000, replace=False)
+        _, chic, unc = oracle.w2d_closed_x(np.asarray(ctrl, np.float64), P[sub].astype(np.float64), want_unc=True)
+        assert np.array_equal(chi[sub][~unc], chic[~unc])
+
+
 def test_point_queries(gwn, ctx):
     """One +x ray per query point (no ray reuse): crossing counts exact and
     w against the oracle's closed form, float64 and float32 chains; grid
