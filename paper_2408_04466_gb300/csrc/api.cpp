@@ -1171,7 +1171,12 @@ static gwn_status eval_impl(gwn_geom *g, const gwn_queries *q, const float *d, v
         int32_t *defer = (int32_t *)arena_get(ctx, 4, sizeof(int32_t) * nq, &e);
         if (!defer) return cuda_fail(e, "deferred-query list");
         if (stats) CK(cudaEventRecord(ctx->ev[1], ctx->stream), "event");
-        e = launch_chi_patches(g->ps, src, chi, stats ? ctx->d_cnt : nullptr, ctx->d_status, ctx->stream);
+        // the long (ray, patch) pairs go to a list settled by a second kernel
+        // (scratch slot 7: counter, then PATCH_DEFER_CAP pairs)
+        char *dbuf = (char *)arena_get(ctx, 7, 16 + sizeof(int2) * (size_t)PATCH_DEFER_CAP, &e);
+        if (!dbuf) return cuda_fail(e, "deferred patch pairs");
+        e = launch_chi_patches(g->ps, src, chi, stats ? ctx->d_cnt : nullptr, ctx->d_status, ctx->stream,
+                               (int2 *)(dbuf + 16), (int32_t *)dbuf, PATCH_DEFER_CAP, ctx->sm_count);
         if (e != cudaSuccess) return cuda_fail(e, "patch crossings");
         if (stats) CK(cudaEventRecord(ctx->ev[2], ctx->stream), "event");
         e = launch_bterm3d(g->bseq, g->ps.bframe, g->n_bseq, g->ps.frame, make_frame64(d), src, chi, (float *)w_out,

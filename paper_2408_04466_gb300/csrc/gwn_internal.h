@@ -231,6 +231,7 @@ struct gwn_ctx {
     gwn::Arena scratch[9];                    // 0 chi, 1 staged points, 2 2D batch, 3 host-eval w, 4 deferred list,
                                               // 5 per-line crossing lists, 6 mesh intake and LBVH build, 7 bin sort,
                                               // 8 2D point order
+    // (slot 7 also holds the deferred (ray, patch) pairs of the patch path)
     std::vector<gwn::AxisCache> axis_cache;   // most recent grids, at most 64
     cudaEvent_t ev[8];
     bool events = false;
@@ -345,8 +346,13 @@ cudaError_t launch_bruteforce3d(const float *V, const int32_t *F, int64_t nf, co
 // Parametric patches: prepare the per-direction tables of g->ps (host and
 // device), and the signed crossing counts chi[q.n] of the rays p + t d.
 gwn_status patches_prepare(gwn_geom *g, const float d[3]);
+// dpairs: optional list (dcap int2 entries, counter dcount) of the long
+// (ray, patch) pairs, settled by a second kernel; without it every pair is
+// settled in place.  Results are the same.
+constexpr int PATCH_DEFER_CAP = 1 << 21;
 cudaError_t launch_chi_patches(const PatchSet &ps, const QuerySrc &q, int32_t *chi, unsigned long long *cnt,
-                               int *status, cudaStream_t st);
+                               int *status, cudaStream_t st, int2 *dpairs, int32_t *dcount, int dcap,
+                               int sm_count);
 void patches_free(PatchSet &ps);
 
 // Point queries of a chain set (one +x ray each).  order_buf (optional):

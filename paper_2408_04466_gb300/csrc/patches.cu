@@ -308,6 +308,35 @@ __device__ __noinline__ int boundary_edge_correction(const float *ex, const floa
     return against ? -corr : corr;
 }
 
+// The signed winding count of patch t seen from a query at the origin of
+// (X, Y, Z) (its control net relative to the query's frame coordinates),
+// with the boundary-edge corrections of its edges on the surface boundary.
+__device__ __forceinline__ int patch_pair_winding(int t, const float *X, const float *Y, const float *Z,
+                                                  const int32_t *__restrict__ bedge,
+                                                  const float4 *__restrict__ pl_proj,
+                                                  const float4 *__restrict__ pl_xyz, const float *__restrict__ pl_dev,
+                                                  int K, const Frame &fr, float qb, float qc, float3 qp,
+                                                  unsigned long long *cnt, int *status, bool *near) {
+    int wn = patch_winding(X, Y, Z, near);
+    if (bedge) {
+        // edges on the surface boundary: chords instead of the curve
+        static const int EIDX[4][4] = {{0, 4, 8, 12}, {12, 13, 14, 15}, {15, 11, 7, 3}, {3, 2, 1, 0}};
+        const int4 be = *(const int4 *)&bedge[4 * (int64_t)t];
+        const int codes[4] = {be.x, be.y, be.z, be.w};
+        for (int e = 0; e < 4; e++) {
+            if (codes[e] < 0) continue;
+            float ex[4], ey[4];
+            for (int m2 = 0; m2 < 4; m2++) { ex[m2] = X[EIDX[e][m2]]; ey[m2] = Y[EIDX[e][m2]]; }
+            const int cv = codes[e] >> 1;
+            const int64_t o = (int64_t)cv * (K + 1);
+            wn += boundary_edge_correction(ex, ey, pl_proj + o, pl_xyz + o, pl_dev + (int64_t)cv * K, K,
+                                           (codes[e] & 1) != 0, qb, qc, qp, make_float3(fr.d[0], fr.d[1], fr.d[2]),
+                                           cnt, status, near);
+        }
+    }
+    return wn;
+}
+
 // One ray per thread, with the (ray, patch) work compacted per warp: each
 // lane walks the patches listed in its bin cell and keeps those whose
 // projected box holds its ray and that reach in front of it; the kept pairs
@@ -315,7 +344,11 @@ __device__ __noinline__ int boundary_edge_correction(const float *ex, const floa
 // (the ray's coordinates fetched from its lane by a shuffle) and adds the
 // patch's winding number to that ray's total in shared memory.  The winding
 // computation is long and most rays meet no patch, so this keeps the lanes
-// busy instead of one lane per warp.
+// busy instead of one lane per warp.  A pair whose patch straddles the plane
+// through the query (subdivision) or has edges on the surface boundary
+// (chord corrections) is long and rare: it goes to a list (dpairs, up to
+// dcap) for chi_patches_deferred_kernel, so that one such lane does not hold
+// the other 31 of its warp; the kernel writes chi without those pairs.
 __global__ void __launch_bounds__(128) chi_patches_kernel(const float4 *__restrict__ qnet,
                                                           const float4 *__restrict__ box,
                                                           const float *__restrict__ zmax,
@@ -327,7 +360,8 @@ __global__ void __launch_bounds__(128) chi_patches_kernel(const float4 *__restri
                                                           const float4 *__restrict__ pl_xyz,
                                                           const float *__restrict__ pl_dev, int K, Frame fr,
                                                           QuerySrc q, int32_t *__restrict__ chi,
-                                                          unsigned long long *cnt, int *status) {
+                                                          unsigned long long *cnt, int *status, int2 *dpairs,
+                                                          int32_t *dcount, int dcap) {
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -363,36 +397,42 @@ __global__ void __launch_bounds__(128) chi_patches_kernel(const float4 *__restri
         const float qa = __shfl_sync(FULL, a, ql), qb = __shfl_sync(FULL, b, ql), qc = __shfl_sync(FULL, c, ql);
         const float3 qp = make_float3(__shfl_sync(FULL, p.x, ql), __shfl_sync(FULL, p.y, ql),
                                       __shfl_sync(FULL, p.z, ql));
+        const int qi = __shfl_sync(FULL, (int)i, ql);
         if (pr >= 0) {
             const int t = pr >> 5;
             float X[16], Y[16], Z[16];
+            float zmin = 3.4e38f, zmax = -3.4e38f;
 #pragma unroll
             for (int m2 = 0; m2 < 16; m2++) {
                 const float4 v = __ldg(&qnet[16 * (int64_t)t + m2]);
                 X[m2] = v.x - qa;
                 Y[m2] = v.y - qb;
                 Z[m2] = v.z - qc;
+                zmin = fminf(zmin, Z[m2]);
+                zmax = fmaxf(zmax, Z[m2]);
             }
-            bool near = false;
-            int wn = patch_winding(X, Y, Z, &near);
-            if (bedge) {
-                // edges on the surface boundary: chords instead of the curve
-                static const int EIDX[4][4] = {{0, 4, 8, 12}, {12, 13, 14, 15}, {15, 11, 7, 3}, {3, 2, 1, 0}};
-                const int4 be = *(const int4 *)&bedge[4 * (int64_t)t];
-                const int codes[4] = {be.x, be.y, be.z, be.w};
-                for (int e = 0; e < 4; e++) {
-                    if (codes[e] < 0) continue;
-                    float ex[4], ey[4];
-                    for (int m2 = 0; m2 < 4; m2++) { ex[m2] = X[EIDX[e][m2]]; ey[m2] = Y[EIDX[e][m2]]; }
-                    const int cv = codes[e] >> 1;
-                    const int64_t o = (int64_t)cv * (K + 1);
-                    wn += boundary_edge_correction(ex, ey, pl_proj + o, pl_xyz + o, pl_dev + (int64_t)cv * K, K,
-                                                   (codes[e] & 1) != 0, qb, qc, qp,
-                                                   make_float3(fr.d[0], fr.d[1], fr.d[2]), cnt, status, &near);
+            bool defer = false;
+            if (dpairs && zmax > 0.f) {
+                bool edge = false;
+                if (bedge) {
+                    const int4 be = *(const int4 *)&bedge[4 * (int64_t)t];
+                    edge = be.x >= 0 || be.y >= 0 || be.z >= 0 || be.w >= 0;
+                }
+                if (!(zmin > 0.f) || edge) {                  // straddling, or boundary edges
+                    const int slot = atomicAdd(dcount, 1);
+                    if (slot < dcap) {
+                        dpairs[slot] = make_int2(qi, t);
+                        defer = true;
+                    }
                 }
             }
-            if (wn) atomicAdd(&s_acc[w][ql], wn);
-            if (near) atomicOr(&s_near[w], 1u << ql);
+            if (!defer) {
+                bool near = false;
+                const int wn = patch_pair_winding(t, X, Y, Z, bedge, pl_proj, pl_xyz, pl_dev, K, fr, qb, qc, qp, cnt,
+                                                  status, &near);
+                if (wn) atomicAdd(&s_acc[w][ql], wn);
+                if (near) atomicOr(&s_near[w], 1u << ql);
+            }
         }
         const int rem = n - m;
         __syncwarp();
@@ -432,15 +472,59 @@ __global__ void __launch_bounds__(128) chi_patches_kernel(const float4 *__restri
     }
 }
 
+// The pairs chi_patches_kernel listed, one per thread: their winding counts
+// subtracted from chi (the kernel stores minus the sum: e1 x e2 = -dh).
+__global__ void __launch_bounds__(128) chi_patches_deferred_kernel(
+    const int2 *__restrict__ dpairs, const int32_t *__restrict__ dcount, int dcap, const float4 *__restrict__ qnet,
+    const int32_t *__restrict__ bedge, const float4 *__restrict__ pl_proj, const float4 *__restrict__ pl_xyz,
+    const float *__restrict__ pl_dev, int K, Frame fr, QuerySrc q, int32_t *__restrict__ chi,
+    unsigned long long *cnt, int *status) {
+    int n = *dcount;
+    if (n > dcap) n = dcap;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const int2 pr = dpairs[k];
+        const int64_t i = pr.x;
+        const int t = pr.y;
+        const float3 p = query_point3(q, i);
+        const float a = fmaf(p.z, fr.e1[2], fmaf(p.y, fr.e1[1], p.x * fr.e1[0]));
+        const float b = fmaf(p.z, fr.e2[2], fmaf(p.y, fr.e2[1], p.x * fr.e2[0]));
+        const float c = fmaf(p.z, fr.dh[2], fmaf(p.y, fr.dh[1], p.x * fr.dh[0]));
+        float X[16], Y[16], Z[16];
+        for (int m2 = 0; m2 < 16; m2++) {
+            const float4 v = __ldg(&qnet[16 * (int64_t)t + m2]);
+            X[m2] = v.x - a;
+            Y[m2] = v.y - b;
+            Z[m2] = v.z - c;
+        }
+        bool near = false;
+        const int wn = patch_pair_winding(t, X, Y, Z, bedge, pl_proj, pl_xyz, pl_dev, K, fr, b, c, p, cnt, status,
+                                          &near);
+        if (wn) atomicAdd(&chi[i], -wn);
+        if (near && cnt) atomicAdd(&cnt[CNT_STACK_OVERFLOW], 1ull);
+    }
+}
+
 cudaError_t launch_chi_patches(const PatchSet &ps, const QuerySrc &q, int32_t *chi, unsigned long long *cnt,
-                               int *status, cudaStream_t st) {
+                               int *status, cudaStream_t st, int2 *dpairs, int32_t *dcount, int dcap,
+                               int sm_count) {
     if (q.n == 0) return cudaSuccess;
     const int64_t blocks = (q.n + 127) / 128;
     if (blocks > 0x7fffffff) return cudaErrorInvalidValue;
+    const bool deferred = dpairs && dcount && dcap > 0 && q.n <= 0x7fffffff;
+    if (deferred) {
+        cudaError_t e = cudaMemsetAsync(dcount, 0, sizeof(int32_t), st);
+        if (e != cudaSuccess) return e;
+    }
     chi_patches_kernel<<<(unsigned)blocks, 128, 0, st>>>(ps.qnet, ps.box, ps.zmax, ps.bin_off, ps.bin_idx, ps.nbx,
                                                          ps.nby, ps.bx0, ps.by0, ps.binv,
                                                          ps.n_bcurves ? ps.bedge : nullptr, ps.pl_proj, ps.pl_xyz,
-                                                         ps.pl_dev, ps.segments, ps.frame, q, chi, cnt, status);
+                                                         ps.pl_dev, ps.segments, ps.frame, q, chi, cnt, status,
+                                                         deferred ? dpairs : nullptr, dcount, dcap);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || !deferred) return e;
+    chi_patches_deferred_kernel<<<(unsigned)((sm_count > 0 ? sm_count : 152) * 8), 128, 0, st>>>(
+        dpairs, dcount, dcap, ps.qnet, ps.n_bcurves ? ps.bedge : nullptr, ps.pl_proj, ps.pl_xyz, ps.pl_dev,
+        ps.segments, ps.frame, q, chi, cnt, status);
     return cudaGetLastError();
 }
 
