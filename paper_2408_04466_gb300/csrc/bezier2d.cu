@@ -691,6 +691,9 @@ __device__ __forceinline__ int warp_suffix_sum(int x, int lane) {
     }
     return x;
 }
+// ALIGNED: nx is a multiple of 256 and ax and the row's w are 16-byte
+// aligned (no bounds or alignment tests per group).
+template <bool ALIGNED>
 __device__ __forceinline__ void row_queries_f32(const float *__restrict__ ax, int nx, int *D, float yr, float spx,
                                                 float spy, float epx, float epy, float *__restrict__ wrow,
                                                 int lane, bool pack) {
@@ -739,10 +742,10 @@ __device__ __forceinline__ void row_queries_f32(const float *__restrict__ ax, in
 #pragma unroll
         for (int g = 0; g < 2; g++) {
             const int i0 = g ? ib : ia;
-            if (i0 >= nx) continue;
-            const bool full = i0 + 4 <= nx;
+            if (!ALIGNED && i0 >= nx) continue;
+            const bool full = ALIGNED || i0 + 4 <= nx;
             float xq[4];
-            if (full && ((uintptr_t)(ax + i0) & 15) == 0) {
+            if (ALIGNED || (full && ((uintptr_t)(ax + i0) & 15) == 0)) {
                 const float4 xa = *(const float4 *)(ax + i0);
                 xq[0] = xa.x; xq[1] = xa.y; xq[2] = xa.z; xq[3] = xa.w;
             } else {
@@ -766,7 +769,7 @@ __device__ __forceinline__ void row_queries_f32(const float *__restrict__ ax, in
                 out[m + 1] = o.y;
             }
             float *wp = wrow + i0;
-            if (full && ((uintptr_t)wp & 15) == 0) {
+            if (ALIGNED || (full && ((uintptr_t)wp & 15) == 0)) {
                 *(float4 *)wp = make_float4(out[0], out[1], out[2], out[3]);
             } else {
 #pragma unroll
@@ -976,9 +979,17 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) eval2d_kernel(con
             const float *sp = (const float *)ctrl + 2 * chain_off[S.c_lo];
             const float *ep = (const float *)ctrl + 2 * (chain_off[S.c_lo + 1] - 1);
             const float spx = sp[0], spy = sp[1], epx = ep[0], epy = ep[1];
-            for (int r = warp; r < nr; r += nwarps)
-                row_queries_f32((const float *)ax, nx, D2 + r * ds, (float)ys[r], spx, spy, epx, epy,
-                                (float *)w_out + S.out_off + (r0 + r) * S.nx, lane, pB - pA < 32767);
+            float *w0 = (float *)w_out + S.out_off + r0 * S.nx;
+            const bool aligned = (nx & 255) == 0 && ((uintptr_t)ax & 15) == 0 && ((uintptr_t)w0 & 15) == 0;
+            if (aligned) {
+                for (int r = warp; r < nr; r += nwarps)
+                    row_queries_f32<true>((const float *)ax, nx, D2 + r * ds, (float)ys[r], spx, spy, epx, epy,
+                                          w0 + (int64_t)r * nx, lane, pB - pA < 32767);
+            } else {
+                for (int r = warp; r < nr; r += nwarps)
+                    row_queries_f32<false>((const float *)ax, nx, D2 + r * ds, (float)ys[r], spx, spy, epx, epy,
+                                           w0 + (int64_t)r * nx, lane, pB - pA < 32767);
+            }
         } else {
             for (int r = warp; r < nr; r += nwarps)
                 row_queries<T>(S, ctrl, chain_off, ax, nx, D2 + r * ds, ys[r], r0 + r, lane, w_out, chi_out, b_out,
