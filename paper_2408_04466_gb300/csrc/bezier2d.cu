@@ -692,11 +692,12 @@ __device__ __forceinline__ int warp_suffix_sum(int x, int lane) {
     return x;
 }
 // ALIGNED: nx is a multiple of 256 and ax and the row's w are 16-byte
-// aligned (no bounds or alignment tests per group).
+// aligned (no bounds or alignment tests per group), and pack holds.
 template <bool ALIGNED>
 __device__ __forceinline__ void row_queries_f32(const float *__restrict__ ax, int nx, int *D, float yr, float spx,
                                                 float spy, float epx, float epy, float *__restrict__ wrow,
-                                                int lane, bool pack) {
+                                                int lane, bool pack_) {
+    const bool pack = ALIGNED || pack_;
     const unsigned FULL = 0xffffffffu;
     const int nxp = eval2d_dstride(nx);
     const float sy = spy - yr, ey = epy - yr, ney = -ey, syey = sy * ey;
@@ -980,7 +981,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) eval2d_kernel(con
             const float *ep = (const float *)ctrl + 2 * (chain_off[S.c_lo + 1] - 1);
             const float spx = sp[0], spy = sp[1], epx = ep[0], epy = ep[1];
             float *w0 = (float *)w_out + S.out_off + r0 * S.nx;
-            const bool aligned = (nx & 255) == 0 && ((uintptr_t)ax & 15) == 0 && ((uintptr_t)w0 & 15) == 0;
+            const bool aligned = (nx & 255) == 0 && ((uintptr_t)ax & 15) == 0 && ((uintptr_t)w0 & 15) == 0 &&
+                                 pB - pA < 32767;
             if (aligned) {
                 for (int r = warp; r < nr; r += nwarps)
                     row_queries_f32<true>((const float *)ax, nx, D2 + r * ds, (float)ys[r], spx, spy, epx, epy,
