@@ -823,7 +823,10 @@ __host__ __device__ constexpr size_t eval2d_d2_bytes(int rows, int max_nx) {
     return (sizeof(int) * (size_t)rows * (size_t)eval2d_dstride(max_nx) + 15) & ~(size_t)15;
 }
 
-template <typename T>
+// FAST: every set is one float32 chain, only w is written, and the chain set
+// has fewer than 2^22 - 1 pieces (the float32 row path serves every item;
+// the generic one is not compiled in).
+template <typename T, bool FAST>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) eval2d_kernel(const T *__restrict__ ctrl, const int64_t *__restrict__ chain_off,
                               const T *__restrict__ piece_y, const T *__restrict__ piece_rec,
                               const Set2D *__restrict__ sets, const int4 *__restrict__ items, const Set2D single,
@@ -976,7 +979,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) eval2d_kernel(con
         }
         __syncthreads();
         // queries: one warp per row
-        if (sizeof(T) == 4 && S.c_hi - S.c_lo == 1 && !chi_out && !b_out && w_out && pB - pA < (1 << 22) - 1) {
+        if (FAST || (sizeof(T) == 4 && S.c_hi - S.c_lo == 1 && !chi_out && !b_out && w_out && pB - pA < (1 << 22) - 1)) {
             const float *sp = (const float *)ctrl + 2 * chain_off[S.c_lo];
             const float *ep = (const float *)ctrl + 2 * (chain_off[S.c_lo + 1] - 1);
             const float spx = sp[0], spy = sp[1], epx = ep[0], epy = ep[1];
@@ -992,7 +995,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) eval2d_kernel(con
                     row_queries_f32<false>((const float *)ax, nx, D2 + r * ds, (float)ys[r], spx, spy, epx, epy,
                                            w0 + (int64_t)r * nx, lane, pB - pA < 32767);
             }
-        } else {
+        } else if (!FAST) {
             for (int r = warp; r < nr; r += nwarps)
                 row_queries<T>(S, ctrl, chain_off, ax, nx, D2 + r * ds, ys[r], r0 + r, lane, w_out, chi_out, b_out,
                                ca, status, cnt, set_id);
@@ -1114,27 +1117,34 @@ cudaError_t launch_eval2d_items(const ChainSet &cs, const Set2D *d_sets, const i
     ca.piece_x = cs.piece_xT;
     ca.cert = cert;
     ca.count = cert_count;
-    // persistent grid: as many blocks as fit on the device at once
+    // persistent grid: as many blocks as fit on the device at once; the
+    // instantiation without the generic row path when the float32
+    // single-chain path serves every item
+    const bool fast = cs.dtype != GWN_F64 && !chi_out && !b_out && w_out && cs.n_pieces < (1 << 22) - 1 &&
+                      (d_sets ? true : s0.c_hi - s0.c_lo == 1);
+    const void *kfn = cs.dtype == GWN_F64 ? (const void *)eval2d_kernel<double, false>
+                      : fast ? (const void *)eval2d_kernel<float, true> : (const void *)eval2d_kernel<float, false>;
     int per_sm = 0;
-    if (cs.dtype == GWN_F64) {
-        e = cudaFuncSetAttribute(eval2d_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, eval2d_kernel<double>, threads, smem);
-    } else {
-        e = cudaFuncSetAttribute(eval2d_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, eval2d_kernel<float>, threads, smem);
-    }
+    e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, threads, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     int64_t blocks = (int64_t)sm_count * per_sm;
     if (blocks > n_items) blocks = n_items;
     if (cs.dtype == GWN_F64) {
-        eval2d_kernel<double><<<(unsigned)blocks, threads, smem, st>>>(
+        eval2d_kernel<double, false><<<(unsigned)blocks, threads, smem, st>>>(
             (const double *)cs.ctrl, cs.chain_off,
             (const double *)cs.piece_yT, (const double *)cs.piece_rec, d_sets, d_items, s0, n_items, d_counter,
             rows_per_item, (double *)w_out,
             chi_out, (double *)b_out, cnt, status, (int)max_nx, ca);
+    } else if (fast) {
+        eval2d_kernel<float, true><<<(unsigned)blocks, threads, smem, st>>>(
+            (const float *)cs.ctrl, cs.chain_off,
+            (const float *)cs.piece_yT, (const float *)cs.piece_rec, d_sets, d_items, s0, n_items, d_counter,
+            rows_per_item, (float *)w_out,
+            chi_out, (float *)b_out, cnt, status, (int)max_nx, ca);
     } else {
-        eval2d_kernel<float><<<(unsigned)blocks, threads, smem, st>>>(
+        eval2d_kernel<float, false><<<(unsigned)blocks, threads, smem, st>>>(
             (const float *)cs.ctrl, cs.chain_off,
             (const float *)cs.piece_yT, (const float *)cs.piece_rec, d_sets, d_items, s0, n_items, d_counter,
             rows_per_item, (float *)w_out,
