@@ -21,7 +21,7 @@
 // the row, which makes shared end points count once); its direction is
 // sign(y1 - y0) (the curve's normal is the tangent turned clockwise: Eq. chi
 // counts +1 where the curve crosses the ray upward).  The crossing parameter
-// is found by safeguarded Newton iteration on the monotone piece, in the
+// is found by safeguarded Halley iteration on the monotone piece, in the
 // chain's precision.
 //
 // Work: a persistent kernel pops work items (set, block of rows) from an
@@ -40,7 +40,7 @@
 namespace gwn {
 
 template <typename T> struct Num;
-// Root tolerances.  Newton stops once the curve point at u lies within
+// Root tolerances.  The root iteration stops once the curve point at u lies within
 // ytol (|y(u0)| + |y(u1)|) of the row in y, or once its step (or the bracket)
 // is below tol in u.  A computed root whose curve point is within e of the
 // row can change the crossing count of a query on the row only if the query
@@ -55,7 +55,7 @@ template <> struct Num<float> {
     static constexpr int max_iter = 60;
     static constexpr float tol = 1e-6f;
     static constexpr float ytol = 1e-6f;
-    // Newton quotients: an approximate quotient (2 ulp) only perturbs the
+    // iteration quotients: an approximate quotient (2 ulp) only perturbs the
     // iterates; the stopping test on the step decides the accuracy
     static __device__ __forceinline__ float div(float a, float b) { return __fdividef(a, b); }
     // a product and a sum the compiler may not fuse (every path rounds alike)
@@ -84,10 +84,10 @@ template <> struct Num<double> {
 constexpr int PC_FIELDS = 12;
 
 // x of the crossing of the piece with record r and the row y = yr
-// (min(r7, r10) <= yr < max(r7, r10)): safeguarded Newton, the bracket
-// oriented so that g(lo) <= 0 < g(hi), g = y(t) - yr.  The bracket starts as
-// the half of [0, 1] that holds the root (g at t = 1/2 against 0), and the
-// first iterate is the secant on that half.
+// (min(r7, r10) <= yr < max(r7, r10)): safeguarded Halley iteration, the
+// bracket oriented so that g(lo) <= 0 < g(hi), g = y(t) - yr.  The bracket
+// starts as the half of [0, 1] that holds the root (g at t = 1/2 against 0),
+// and the first iterate is the secant on that half.
 template <typename T>
 __device__ __forceinline__ T piece_root_rec(const T *r, T yr, int *iters_out, T *t_out = nullptr) {
     const T ya = r[7], yb = r[10];
@@ -99,13 +99,17 @@ __device__ __forceinline__ T piece_root_rec(const T *r, T yr, int *iters_out, T 
     if (gm <= T(0)) { lo = T(0.5); glo = gm; } else { hi = T(0.5); ghi = gm; }
     T t = lo + Num<T>::div(-glo, ghi - glo) * (hi - lo);
     const T ytol = Num<T>::ytol * ((ya < T(0) ? -ya : ya) + (yb < T(0) ? -yb : yb));
+    const T r8x2 = T(2) * r[8];
     int it = 0;
     for (; it < Num<T>::max_iter; it++) {
         const T g = Num<T>::fma_(Num<T>::fma_(Num<T>::fma_(r[4], t, r[5]), t, r[6]), t, c0);
         if ((g < T(0) ? -g : g) <= ytol) break;     // the curve point is within ytol of the row
         if (g < T(0)) lo = t; else hi = t;
         const T dg = Num<T>::fma_(Num<T>::fma_(r[8], t, r[9]), t, r[6]);
-        T tn = t - Num<T>::div(g, dg);
+        const T d2g = Num<T>::fma_(r8x2, t, r[9]);
+        // Halley's step t - 2 g g' / (2 g'^2 - g g'') (cubic convergence)
+        const T gdg = g * dg;
+        T tn = t - Num<T>::div(gdg + gdg, Num<T>::fma_(dg + dg, dg, -g * d2g));
         const T mn = lo < hi ? lo : hi, mx = lo < hi ? hi : lo;
         if (!(tn > mn && tn < mx)) tn = T(0.5) * (lo + hi);
         const T step = tn - t;
@@ -119,7 +123,7 @@ __device__ __forceinline__ T piece_root_rec(const T *r, T yr, int *iters_out, T 
 
 // ---- certification of crossings ---------------------------------------------
 // A crossing computed from a piece record can sit on the wrong side of a
-// query for three reasons: Newton stops at a tolerance, the record's
+// query for three reasons: the iteration stops at a tolerance, the record's
 // coefficients are rounded, and the row test uses end values rounded at
 // interior extrema of y.  The kernels bound the first two per crossing
 // (root_band) and hand every (piece, row) whose bound contains a query
@@ -132,7 +136,7 @@ template <> struct Unit<double> { static constexpr double u = 1.1102230246251565
 
 // Half-width of an interval about the computed crossing x_r that contains the
 // crossing of the exact curve, or +inf where the bound below does not apply.
-// With g(t) = y(t) - yr evaluated at Newton's final t: |g_exact(t)| <= |g| +
+// With g(t) = y(t) - yr evaluated at the iteration's final t: |g_exact(t)| <= |g| +
 // eg, eg covering the evaluation and the rounded coefficients; |y''| <= m2 on
 // [0, 1], so if m2 bt <= |y'(t)| / 2 (y' shrunk by its own error), y' keeps
 // at least half its size on [t - bt, t + bt] and the root lies within
@@ -162,7 +166,7 @@ __device__ __forceinline__ T root_band(const T *r, T yr, T t) {
 }
 
 // An interval that contains the exact crossing and the float one (x, the
-// root the float path counts with).  Where root_band at Newton's own stopping
+// root the float path counts with).  Where root_band at the iteration's own stopping
 // point is too wide to settle a query, two more Newton steps from t usually
 // shrink it to the rounding level: the interval is then the hull of x and
 // the refined root's band.  Returns false (no bound) where the bound does not
