@@ -979,9 +979,11 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) eval2d_kernel(con
                     cert_push(ca.cert, ca.count, status, cnt, set_id, (int)(r0 + r), (int)pp, -1, c0, c1);
                 }
             }
-            __syncthreads();           // s_wsum, s_ofs, s_ra are rewritten by the next round
+            // s_wsum, s_ofs, s_ra are rewritten by the next round, and the
+            // row queries read the cells (when the run is empty no cell was
+            // written and no barrier is needed)
+            __syncthreads();
         }
-        __syncthreads();
         // queries: one warp per row
         if (FAST || (sizeof(T) == 4 && S.c_hi - S.c_lo == 1 && !chi_out && !b_out && w_out && pB - pA < (1 << 22) - 1)) {
             const float *sp = (const float *)ctrl + 2 * chain_off[S.c_lo];
