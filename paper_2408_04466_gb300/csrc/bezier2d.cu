@@ -854,8 +854,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) eval2d_kernel(con
     if (threadIdx.x == 0) item_sh = (long long)atomicAdd(counter, 1ull);
     __syncthreads();
     for (int64_t guard = 0; guard <= n_items; guard++) {
-        long long item = item_sh;
-        __syncthreads();
+        // (thread 0 overwrites item_sh only after the barriers below, which
+        // every thread reaches after this read)
+        const long long item = item_sh;
         if (item >= n_items) break;
         long long next_item = 0;
         if (threadIdx.x == 0) next_item = (long long)atomicAdd(counter, 1ull);
