@@ -361,7 +361,7 @@ void patches_free(PatchSet &ps);
 // y-buckets (a counting sort per call) so that the warps walk the same
 // bucket lists.  Results do not depend on it.
 constexpr int64_t EVAL2D_POINTS_ORDER_MIN = 65536;            // fewer queries: as given
-constexpr int64_t EVAL2D_POINTS_ORDER_MAX_BUCKETS = 1 << 20;  // more buckets: as given
+constexpr int64_t EVAL2D_POINTS_ORDER_MAX_BUCKETS = 1 << 16;  // more buckets: as given (one-block scan)
 size_t eval2d_points_order_bytes(const ChainSet &cs, int64_t n);
 cudaError_t launch_eval2d_points(const ChainSet &cs, const QuerySrc &q, void *w_out, int32_t *chi_out, void *b_out,
                                  unsigned long long *cnt, int *status, cudaStream_t st, int4 *cert,
