@@ -83,11 +83,14 @@ MAIN = {
 W_VERTEX = 26
 W_EDGE = 31
 # FP32 lane operations per (query, boundary edge) pair of the fused backward
-# pass (both gradients): a = A - p, b = B - p (6); a x E, |a x E|^2 (10);
-# |a|^2, |b|^2 (8); rsqrt x 2, |a|, |b| (4); |a||b|, a.b (4); Q = |a||b| + a.b
-# or |a x E|^2 / (|a||b| - a.b) and its reciprocal (4); J_A, J_B (2);
-# weights (5); per-edge and per-query accumulation (9)                     -> 52
-W_GRAD_PAIR = 52
+# pass (both gradients), on the path of the pairs with a.b >= 0 (every pair of
+# the timed workloads but those whose query lies inside the sphere on the
+# edge as diameter): a = A - p, b = B - p (6); c = a x E (6); |a|^2, |b|^2 with
+# the clamp constant in the first FMA (6); rsqrt x 2 (2); 1/|a||b| (1); a.b
+# (3); 1 + a.b/|a||b| (1); the sign test of a.b (1); reciprocal (1);
+# 1/Q x dL/dw (2); J_A g, J_B g and their sum (3); per-edge and per-query
+# accumulation (9)                                                        -> 41
+W_GRAD_PAIR = 41
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 

@@ -1369,7 +1369,7 @@ extern "C" GWN_API gwn_status gwn_backward(gwn_geom *g, const gwn_queries *q, co
         if (s != GWN_OK) return s;
         const int64_t ne = (int64_t)g->loop_vid.size();
         int chunks = grad_pv_chunks(nq, ne, ctx->sm_count);
-        size_t part = (sizeof(float) * 6 * (size_t)chunks * g->n_bseq + 255) & ~(size_t)255;
+        size_t part = (sizeof(float) * 8 * (size_t)chunks * g->n_bseq + 255) & ~(size_t)255;
         size_t partp = (grad_pv_partial_p_bytes(nq, ne) + 255) & ~(size_t)255;
         size_t recb = sizeof(float) * 3 * g->n_bseq;
         cudaError_t e;
@@ -1391,7 +1391,7 @@ extern "C" GWN_API gwn_status gwn_backward(gwn_geom *g, const gwn_queries *q, co
         if (s != GWN_OK) return s;
         if (nq > 0 && g->n_bseq > 0) {
             int chunks = grad_v_chunks(nq, g->n_bseq, ctx->sm_count);
-            size_t part = sizeof(float) * 6 * (size_t)chunks * g->n_bseq;
+            size_t part = sizeof(float) * 8 * (size_t)chunks * g->n_bseq;
             size_t recb = sizeof(float) * 3 * g->n_bseq;
             cudaError_t e;
             char *buf = (char *)arena_get(ctx, 0, part + recb + 256, &e);

@@ -72,36 +72,6 @@ __device__ __forceinline__ EdgeGrad edge_grad(float ax, float ay, float az, floa
     return g;
 }
 
-// edge_grad for two queries at once (packed f32x2 add/mul/fma, MUFU per
-// element); the same formulas and clamps
-typedef float2 f2;
-struct EdgeGrad2 {
-    f2 cx, cy, cz, ja, jb;
-};
-__device__ __forceinline__ f2 mk2(float a) { return make_float2(a, a); }
-__device__ __forceinline__ f2 mx2(f2 a, float lo) { return make_float2(fmaxf(a.x, lo), fmaxf(a.y, lo)); }
-__device__ __forceinline__ EdgeGrad2 edge_grad2(f2 ax, f2 ay, f2 az, f2 bx, f2 by, f2 bz, float ex, float ey,
-                                                float ez) {
-    EdgeGrad2 g;
-    const f2 EX = mk2(ex), EY = mk2(ey), EZ = mk2(ez);
-    g.cx = __ffma2_rn(ay, EZ, __fmul2_rn(az, mk2(-ey)));
-    g.cy = __ffma2_rn(az, EX, __fmul2_rn(ax, mk2(-ez)));
-    g.cz = __ffma2_rn(ax, EY, __fmul2_rn(ay, mk2(-ex)));
-    const f2 del = mx2(__ffma2_rn(g.cx, g.cx, __ffma2_rn(g.cy, g.cy, __fmul2_rn(g.cz, g.cz))), 1e-37f);
-    const f2 ra2 = mx2(__ffma2_rn(ax, ax, __ffma2_rn(ay, ay, __fmul2_rn(az, az))), 1e-37f);
-    const f2 rb2 = mx2(__ffma2_rn(bx, bx, __ffma2_rn(by, by, __fmul2_rn(bz, bz))), 1e-37f);
-    const f2 ia = make_float2(grsqrt(ra2.x), grsqrt(ra2.y)), ib = make_float2(grsqrt(rb2.x), grsqrt(rb2.y));
-    const f2 lab = __fmul2_rn(__fmul2_rn(ra2, ia), __fmul2_rn(rb2, ib));
-    const f2 ab = __ffma2_rn(ax, bx, __ffma2_rn(ay, by, __fmul2_rn(az, bz)));
-    const f2 qp = __fadd2_rn(lab, ab), qm = __fadd2_rn(lab, make_float2(-ab.x, -ab.y));
-    const float q0 = ab.x >= 0.f ? qp.x : del.x * grcp(qm.x);
-    const float q1 = ab.y >= 0.f ? qp.y : del.y * grcp(qm.y);
-    const f2 iq = make_float2(grcp(fmaxf(q0, 1e-37f)), grcp(fmaxf(q1, 1e-37f)));
-    g.ja = __fmul2_rn(ia, iq);
-    g.jb = __fmul2_rn(ib, iq);
-    return g;
-}
-
 template <int K>
 __global__ void __launch_bounds__(256) grad_p_kernel(const float4 *__restrict__ bseq, int nb, QuerySrc q,
                                                      const float *__restrict__ grad_w, float *__restrict__ grad_p) {
@@ -143,8 +113,9 @@ __global__ void __launch_bounds__(256) grad_p_kernel(const float4 *__restrict__ 
 constexpr int GV_THREADS = 128;
 constexpr int GV_QTILE = 256;
 
-// partial[(chunk * nb + k) * 6 + {0..2}] = sum over the chunk of dw/dA of the
-// edge ending at record k, {3..5} = dw/dB.
+// partial[(chunk * nb + k) * 8 + {0..2}] = sum over the chunk of dw/dA of the
+// edge ending at record k, {4..6} = dw/dB ({3} and {7} pad each half to a
+// float4).  Rows are written only for records that end an edge.
 __global__ void __launch_bounds__(GV_THREADS) grad_v_partial_kernel(const float4 *__restrict__ bseq, int nb,
                                                                     QuerySrc q, const float *__restrict__ grad_w,
                                                                     int64_t chunk_len, float *__restrict__ partial) {
@@ -183,93 +154,167 @@ __global__ void __launch_bounds__(GV_THREADS) grad_v_partial_kernel(const float4
         }
     }
     if (k < nb) {
-        float *o = partial + ((int64_t)chunk * nb + k) * 6;
-        o[0] = sA[0]; o[1] = sA[1]; o[2] = sA[2];
-        o[3] = sB[0]; o[4] = sB[1]; o[5] = sB[2];
+        float4 *o = reinterpret_cast<float4 *>(partial + ((int64_t)chunk * nb + k) * 8);
+        o[0] = make_float4(sA[0], sA[1], sA[2], 0.f);
+        o[1] = make_float4(sB[0], sB[1], sB[2], 0.f);
     }
 }
 
 // Both gradients from one evaluation per (query, edge): the per-edge sums as
 // in grad_v_partial_kernel, and per query the sum of its dw/dp contributions
-// over the block's edges.  A warp takes its 32 edges against the tile's
-// queries 64 at a time, two per lane in packed f32x2 arithmetic: in step s
-// lane l evaluates its edge against queries base + (l + s) mod 32 and
-// base + 32 + (l + s) mod 32, adds the contributions to the accumulators it
-// holds and passes them one lane down, so after 32 steps lane l holds the
-// sums over the warp's edges of queries base + l and base + 32 + l (3
-// shuffles per pair, a fixed order).  The warps are added in order in shared
-// memory, one value per (edge block, query, component) goes to
+// over the block's edges.
+//
+// A block holds GPV_EDGES = 256 edges, two per thread (edges t and t + 128 of
+// the block) as one packed f32x2 lane pair, so every packed operand of the
+// edge geometry is a register pair of two different edges and the query
+// enters as a duplicated pair (x, x) read straight from shared memory.  A warp
+// takes its 64 edges against the tile's queries 32 at a time: in step s lane l
+// evaluates both its edges against query base + (l ^ s), adds the two
+// contributions to the three accumulators it holds and hands them to lane
+// l ^ s ^ (s + 1), the lane that takes that query in step s + 1, so after 32
+// steps lane l holds the sums over the warp's edges of query base + (l ^ 31)
+// (3 shuffles per 2 pairs, a fixed order).  The warps are added in order in
+// shared memory, one value per (edge block, query, component) goes to
 // partial_p[(eb * 3 + c) * nq + q], and grad_p_reduce_kernel sums the edge
-// blocks in order.  Lanes without an edge contribute nothing; queries past
-// the tile's end sit far from the geometry with weight zero.
-__global__ void __launch_bounds__(GV_THREADS) grad_pv_partial_kernel(const float4 *__restrict__ bseq, int nb,
-                                                                     const int32_t *__restrict__ edge_rec,
-                                                                     int n_edges, QuerySrc q,
-                                                                     const float *__restrict__ grad_w,
-                                                                     int64_t chunk_len, float *__restrict__ partial,
-                                                                     float *__restrict__ partial_p) {
-    __shared__ float4 qs[GV_QTILE];
-    __shared__ float accp[GV_THREADS / 32][3][GV_QTILE];
+// blocks in order.
+//
+// Per (query, edge), with a = A - p, b = B - p: c = a x E, the clamped squares
+// |a|^2, |b|^2 (a tiny constant added, so a query on a vertex gives finite
+// weights), 1/|a|, 1/|b| by MUFU rsqrt, and 1/Q by one MUFU reciprocal.  When
+// a.b >= 0 for every pair of the warp's step (the query outside the sphere on
+// each edge as diameter: nearly always), 1/Q = (1/|a||b|) / (1 + a.b/|a||b|),
+// with no cancellation; otherwise the whole warp takes 1/Q = num / den with
+// (num, den) = (1, |a||b| + a.b) when a.b >= 0 and (|a||b| - a.b, |c|^2 + tiny)
+// when a.b < 0.  The per-edge sums collect c J_A g and c J_B g
+// (g = dL/dw / 4 pi) and are negated once at the end.  A block whose
+// edge slots are not all valid takes the instantiation that zeroes the
+// invalid slots' query contributions by a select; their edge sums are not
+// written.  Queries past the tile's end sit far from the geometry with weight
+// zero.
+constexpr int GPV_EDGES = 2 * GV_THREADS;
+
+typedef float2 f2;
+__device__ __forceinline__ f2 mk2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ f2 add2(f2 a, f2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ f2 mul2(f2 a, f2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) { return __ffma2_rn(a, b, c); }
+
+struct EdgePair {
+    f2 ax, ay, az, bx, by, bz;          // A and B of the two edges
+    f2 ex, ey, ez, nex, ney, nez;       // E = B - A and -E
+};
+
+template <bool MASK>
+__device__ __forceinline__ void gpv_group(const float4 *__restrict__ qxy, const float4 *__restrict__ qzw, int lb,
+                                          const EdgePair &G, bool m0, bool m1, f2 (&sA)[3], f2 (&sB)[3],
+                                          float (&acc)[3]) {
     const unsigned FULL = 0xffffffffu;
+    const f2 TINY = mk2(1e-37f), MONE = mk2(-1.f), ONE = mk2(1.f);
+    for (int o = 0; o < 32; o += 16) {
+        const int lo = lb ^ o;
+#pragma unroll
+        for (int i = 0; i < 16; i++) {
+            const int j = lo ^ i;
+            const float4 u = qxy[j], v = qzw[j];
+            const f2 px = make_float2(u.x, u.y), py = make_float2(u.z, u.w), pz = make_float2(v.x, v.y);
+            const f2 pw = make_float2(v.z, v.w);
+            // the tile holds -p
+            const f2 ax = add2(G.ax, px), ay = add2(G.ay, py), az = add2(G.az, pz);
+            const f2 bx = add2(G.bx, px), by = add2(G.by, py), bz = add2(G.bz, pz);
+            const f2 cx = fma2(ay, G.ez, mul2(az, G.ney));
+            const f2 cy = fma2(az, G.ex, mul2(ax, G.nez));
+            const f2 cz = fma2(ax, G.ey, mul2(ay, G.nex));
+            const f2 ra2 = fma2(ax, ax, fma2(ay, ay, fma2(az, az, TINY)));
+            const f2 rb2 = fma2(bx, bx, fma2(by, by, fma2(bz, bz, TINY)));
+            const f2 ab = fma2(ax, bx, fma2(ay, by, mul2(az, bz)));
+            const f2 ia = make_float2(grsqrt(ra2.x), grsqrt(ra2.y)), ib = make_float2(grsqrt(rb2.x), grsqrt(rb2.y));
+            f2 s;
+            if (__any_sync(FULL, ab.x < 0.f || ab.y < 0.f)) {
+                const f2 lab = mul2(mul2(ra2, ia), mul2(rb2, ib));
+                const f2 del = fma2(cx, cx, fma2(cy, cy, fma2(cz, cz, TINY)));
+                const f2 qp = add2(lab, ab), qm = fma2(ab, MONE, lab);
+                const f2 num = make_float2(ab.x >= 0.f ? 1.f : qm.x, ab.y >= 0.f ? 1.f : qm.y);
+                const f2 den = make_float2(ab.x >= 0.f ? qp.x : del.x, ab.y >= 0.f ? qp.y : del.y);
+                s = mul2(mul2(num, make_float2(grcp(den.x), grcp(den.y))), pw);
+            } else {
+                // 1/Q = (1/|a||b|) / (1 + a.b / |a||b|), no cancellation for a.b >= 0
+                const f2 iab = mul2(ia, ib), t = fma2(ab, iab, ONE);
+                s = mul2(mul2(iab, make_float2(grcp(t.x), grcp(t.y))), pw);
+            }
+            const f2 ta = mul2(ia, s), tb = mul2(ib, s);
+            f2 tp = add2(ta, tb);
+            if (MASK) tp = make_float2(m0 ? tp.x : 0.f, m1 ? tp.y : 0.f);
+            sA[0] = fma2(cx, ta, sA[0]); sA[1] = fma2(cy, ta, sA[1]); sA[2] = fma2(cz, ta, sA[2]);
+            sB[0] = fma2(cx, tb, sB[0]); sB[1] = fma2(cy, tb, sB[1]); sB[2] = fma2(cz, tb, sB[2]);
+            acc[0] = fmaf(cx.y, tp.y, fmaf(cx.x, tp.x, acc[0]));
+            acc[1] = fmaf(cy.y, tp.y, fmaf(cy.x, tp.x, acc[1]));
+            acc[2] = fmaf(cz.y, tp.y, fmaf(cz.x, tp.x, acc[2]));
+            // the query of this lane in step s + 1 is the one lane l ^ s ^ (s + 1) took now
+            if (o + i < 31) {
+                const int m = (o + i) ^ (o + i + 1);
+                acc[0] = __shfl_xor_sync(FULL, acc[0], m);
+                acc[1] = __shfl_xor_sync(FULL, acc[1], m);
+                acc[2] = __shfl_xor_sync(FULL, acc[2], m);
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(GV_THREADS, 7) grad_pv_partial_kernel(const float4 *__restrict__ bseq, int nb,
+                                                                        const int32_t *__restrict__ edge_rec,
+                                                                        int n_edges, QuerySrc q,
+                                                                        const float *__restrict__ grad_w,
+                                                                        int64_t chunk_len, float *__restrict__ partial,
+                                                                        float *__restrict__ partial_p) {
+    __shared__ float4 qs[2][GV_QTILE];                  // (-x, -x, -y, -y), (-z, -z, g, g)
+    __shared__ float accp[GV_THREADS / 32][3][GV_QTILE];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    // thread t takes edge t, the edge ending at record edge_rec[t] (the
-    // records that start a loop end no edge, so every thread of a full block
-    // has one)
-    const int t = blockIdx.x * GV_THREADS + threadIdx.x;
-    int chunk = blockIdx.y;
-    int64_t q0 = (int64_t)chunk * chunk_len;
-    int64_t q1 = q0 + chunk_len < q.n ? q0 + chunk_len : q.n;
-    const int k = t < n_edges ? __ldg(&edge_rec[t]) : 0;
-    bool active = t < n_edges && k >= 1 && k < nb;
-    float4 A = active ? bseq[k - 1] : make_float4(0.f, 0.f, 0.f, 0.f);
-    float4 B = active ? bseq[k] : make_float4(0.f, 0.f, 0.f, 0.f);
-    active = active && B.w != 0.f;
-    float ex = B.x - A.x, ey = B.y - A.y, ez = B.z - A.z;
-    f2 sA2[3] = {mk2(0.f), mk2(0.f), mk2(0.f)}, sB2[3] = {mk2(0.f), mk2(0.f), mk2(0.f)};
+    // the thread's two edges end at records edge_rec[e0] and edge_rec[e1]
+    // (the records that start a loop end no edge, so every slot of a full
+    // block is valid)
+    const int e0 = blockIdx.x * GPV_EDGES + threadIdx.x, e1 = e0 + GV_THREADS;
+    const int chunk = blockIdx.y;
+    const int64_t q0 = (int64_t)chunk * chunk_len;
+    const int64_t q1 = q0 + chunk_len < q.n ? q0 + chunk_len : q.n;
+    const int k0 = e0 < n_edges ? __ldg(&edge_rec[e0]) : 0, k1 = e1 < n_edges ? __ldg(&edge_rec[e1]) : 0;
+    const float4 Z = make_float4(0.f, 0.f, 0.f, 0.f), X = make_float4(1.f, 0.f, 0.f, 1.f);
+    float4 A0 = Z, B0 = X, A1 = Z, B1 = X;            // invalid slots: a unit edge, masked
+    bool m0 = k0 >= 1 && k0 < nb, m1 = k1 >= 1 && k1 < nb;
+    if (m0) { A0 = bseq[k0 - 1]; B0 = bseq[k0]; m0 = B0.w != 0.f; }
+    if (m1) { A1 = bseq[k1 - 1]; B1 = bseq[k1]; m1 = B1.w != 0.f; }
+    const bool full = __syncthreads_and(m0 && m1) != 0;
+    EdgePair G;
+    G.ax = make_float2(A0.x, A1.x); G.ay = make_float2(A0.y, A1.y); G.az = make_float2(A0.z, A1.z);
+    G.bx = make_float2(B0.x, B1.x); G.by = make_float2(B0.y, B1.y); G.bz = make_float2(B0.z, B1.z);
+    G.ex = make_float2(B0.x - A0.x, B1.x - A1.x); G.ey = make_float2(B0.y - A0.y, B1.y - A1.y);
+    G.ez = make_float2(B0.z - A0.z, B1.z - A1.z);
+    G.nex = make_float2(-G.ex.x, -G.ex.y); G.ney = make_float2(-G.ey.x, -G.ey.y); G.nez = make_float2(-G.ez.x, -G.ez.y);
+    f2 sA[3] = {mk2(0.f), mk2(0.f), mk2(0.f)}, sB[3] = {mk2(0.f), mk2(0.f), mk2(0.f)};
     for (int64_t t0 = q0; t0 < q1; t0 += GV_QTILE) {
         __syncthreads();
         for (int i = threadIdx.x; i < GV_QTILE; i += GV_THREADS) {
-            int64_t qi = t0 + i;
+            const int64_t qi = t0 + i;
+            float3 p = make_float3(1e6f, 1e6f, 1e6f);     // far from the geometry, weight zero
+            float g = 0.f;
             if (qi < q1) {
-                float3 p = query_point3(q, qi);
-                qs[i] = make_float4(p.x, p.y, p.z, grad_w[qi] * GWN_INV_4PI);
-            } else {
-                qs[i] = make_float4(1e6f, 1e6f, 1e6f, 0.f);      // far from the geometry, weight zero
+                p = query_point3(q, qi);
+                g = grad_w[qi] * GWN_INV_4PI;
             }
+            qs[0][i] = make_float4(-p.x, -p.x, -p.y, -p.y);
+            qs[1][i] = make_float4(-p.z, -p.z, g, g);
         }
         __syncthreads();
         const int cnt = (int)(q1 - t0 < GV_QTILE ? q1 - t0 : GV_QTILE);
-        // queries base + j and base + 32 + j as one packed pair per step
-        for (int base = 0; base < cnt; base += 64) {
-            f2 acx = mk2(0.f), acy = mk2(0.f), acz = mk2(0.f);
-            for (int st = 0; st < 32; st++) {
-                const int j = (lane + st) & 31;
-                if (active) {
-                    const float4 pa = qs[base + j], pb = qs[base + 32 + j];
-                    const f2 pw = make_float2(pa.w, pb.w);
-                    EdgeGrad2 g = edge_grad2(make_float2(A.x - pa.x, A.x - pb.x), make_float2(A.y - pa.y, A.y - pb.y),
-                                             make_float2(A.z - pa.z, A.z - pb.z), make_float2(B.x - pa.x, B.x - pb.x),
-                                             make_float2(B.y - pa.y, B.y - pb.y), make_float2(B.z - pa.z, B.z - pb.z),
-                                             ex, ey, ez);
-                    const f2 wa = __fmul2_rn(make_float2(-g.ja.x, -g.ja.y), pw);
-                    const f2 wb = __fmul2_rn(make_float2(-g.jb.x, -g.jb.y), pw);
-                    const f2 wp = __fmul2_rn(__fmul2_rn(__fadd2_rn(g.ja, g.jb), mk2(B.w)), pw);
-                    sA2[0] = __ffma2_rn(g.cx, wa, sA2[0]); sA2[1] = __ffma2_rn(g.cy, wa, sA2[1]);
-                    sA2[2] = __ffma2_rn(g.cz, wa, sA2[2]);
-                    sB2[0] = __ffma2_rn(g.cx, wb, sB2[0]); sB2[1] = __ffma2_rn(g.cy, wb, sB2[1]);
-                    sB2[2] = __ffma2_rn(g.cz, wb, sB2[2]);
-                    acx = __ffma2_rn(g.cx, wp, acx); acy = __ffma2_rn(g.cy, wp, acy); acz = __ffma2_rn(g.cz, wp, acz);
-                }
-                // pass the accumulators one lane down
-                const int src = (lane + 1) & 31;
-                acx = make_float2(__shfl_sync(FULL, acx.x, src), __shfl_sync(FULL, acx.y, src));
-                acy = make_float2(__shfl_sync(FULL, acy.x, src), __shfl_sync(FULL, acy.y, src));
-                acz = make_float2(__shfl_sync(FULL, acz.x, src), __shfl_sync(FULL, acz.y, src));
-            }
-            // after 32 steps lane l holds queries base + l and base + 32 + l
-            accp[warp][0][base + lane] = acx.x; accp[warp][0][base + 32 + lane] = acx.y;
-            accp[warp][1][base + lane] = acy.x; accp[warp][1][base + 32 + lane] = acy.y;
-            accp[warp][2][base + lane] = acz.x; accp[warp][2][base + 32 + lane] = acz.y;
+        for (int base = 0; base < cnt; base += 32) {
+            float acc[3] = {0.f, 0.f, 0.f};
+            if (full)
+                gpv_group<false>(qs[0], qs[1], base + lane, G, m0, m1, sA, sB, acc);
+            else
+                gpv_group<true>(qs[0], qs[1], base + lane, G, m0, m1, sA, sB, acc);
+            // after 32 steps lane l holds query base + (l ^ 31)
+            accp[warp][0][base + (lane ^ 31)] = acc[0];
+            accp[warp][1][base + (lane ^ 31)] = acc[1];
+            accp[warp][2][base + (lane ^ 31)] = acc[2];
         }
         __syncthreads();
         for (int i = threadIdx.x; i < cnt; i += GV_THREADS)
@@ -279,12 +324,15 @@ __global__ void __launch_bounds__(GV_THREADS) grad_pv_partial_kernel(const float
                 partial_p[((int64_t)blockIdx.x * 3 + c) * q.n + t0 + i] = v;
             }
     }
-    if (active) {
-        float *o = partial + ((int64_t)chunk * nb + k) * 6;
-        for (int c = 0; c < 3; c++) {
-            o[c] = sA2[c].x + sA2[c].y;
-            o[3 + c] = sB2[c].x + sB2[c].y;
-        }
+    if (m0) {
+        float4 *o = reinterpret_cast<float4 *>(partial + ((int64_t)chunk * nb + k0) * 8);
+        o[0] = make_float4(-sA[0].x, -sA[1].x, -sA[2].x, 0.f);
+        o[1] = make_float4(-sB[0].x, -sB[1].x, -sB[2].x, 0.f);
+    }
+    if (m1) {
+        float4 *o = reinterpret_cast<float4 *>(partial + ((int64_t)chunk * nb + k1) * 8);
+        o[0] = make_float4(-sA[0].y, -sA[1].y, -sA[2].y, 0.f);
+        o[1] = make_float4(-sB[0].y, -sB[1].y, -sB[2].y, 0.f);
     }
 }
 
@@ -301,26 +349,36 @@ __global__ void grad_p_reduce_kernel(const float *__restrict__ partial_p, int n_
 }
 
 // per record: total gradient of its vertex from the edge ending there (as B)
-// and the edge starting there (as A of record k+1), summed over chunks in
-// chunk order.
-__global__ void grad_v_record_kernel(const float *__restrict__ partial, int n_chunks, int nb,
-                                     const float4 *__restrict__ bseq, float *__restrict__ rec_grad) {
-    int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= nb) return;
+// and the edge starting there (as A of record k+1), summed over the chunks.  A
+// block takes 32 consecutive records, one per lane, so that a warp's loads of
+// one chunk cover 32 consecutive rows; warp w adds chunks w, w + 32, ... in
+// order, and the 32 warp sums are added in order (the order depends on
+// n_chunks only).
+constexpr int GV_REC_WARPS = 32;
+__global__ void __launch_bounds__(GV_REC_WARPS * 32) grad_v_record_kernel(const float *__restrict__ partial,
+                                                                          int n_chunks, int nb,
+                                                                          const float4 *__restrict__ bseq,
+                                                                          float *__restrict__ rec_grad) {
+    __shared__ float red[GV_REC_WARPS][3][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int k = blockIdx.x * 32 + lane;
+    const bool asB = k < nb && bseq[k].w != 0.f;
+    const bool asA = k + 1 < nb && bseq[k + 1].w != 0.f;
     float g[3] = {0.f, 0.f, 0.f};
-    bool asB = bseq[k].w != 0.f;
-    bool asA = k + 1 < nb && bseq[k + 1].w != 0.f;
-    for (int c = 0; c < n_chunks; c++) {
-        const float *pk = partial + ((int64_t)c * nb + k) * 6;
-        if (asB) { g[0] += pk[3]; g[1] += pk[4]; g[2] += pk[5]; }
-        if (asA) {
-            const float *pn = partial + ((int64_t)c * nb + k + 1) * 6;
-            g[0] += pn[0]; g[1] += pn[1]; g[2] += pn[2];
+    for (int c = warp; c < n_chunks; c += GV_REC_WARPS) {
+        const float4 *pk = reinterpret_cast<const float4 *>(partial + ((int64_t)c * nb + k) * 8);
+        if (asB) { const float4 b = pk[1]; g[0] += b.x; g[1] += b.y; g[2] += b.z; }
+        if (asA) { const float4 a = pk[2]; g[0] += a.x; g[1] += a.y; g[2] += a.z; }   // record k + 1, its A part
+    }
+    for (int i = 0; i < 3; i++) red[warp][i][lane] = g[i];
+    __syncthreads();
+    if (warp == 0 && k < nb) {
+        for (int i = 0; i < 3; i++) {
+            float v = 0.f;
+            for (int w = 0; w < GV_REC_WARPS; w++) v += red[w][i][lane];
+            rec_grad[3 * k + i] = v;
         }
     }
-    rec_grad[3 * k] = g[0];
-    rec_grad[3 * k + 1] = g[1];
-    rec_grad[3 * k + 2] = g[2];
 }
 
 // per boundary vertex: sum its records in list order
@@ -366,20 +424,25 @@ cudaError_t launch_grad_v(const float4 *bseq, int64_t nb, const QuerySrc &q, con
     int64_t chunk_len = (q.n + n_chunks - 1) / n_chunks;
     dim3 grid((unsigned)((nb + GV_THREADS - 1) / GV_THREADS), (unsigned)n_chunks);
     grad_v_partial_kernel<<<grid, GV_THREADS, 0, st>>>(bseq, (int)nb, q, grad_w, chunk_len, partial);
-    grad_v_record_kernel<<<(unsigned)((nb + 255) / 256), 256, 0, st>>>(partial, n_chunks, (int)nb, bseq, rec_grad);
+    grad_v_record_kernel<<<(unsigned)((nb + 31) / 32), GV_REC_WARPS * 32, 0, st>>>(partial, n_chunks, (int)nb,
+                                                                                   bseq, rec_grad);
     grad_v_scatter_kernel<<<(unsigned)((n_bvert + 255) / 256), 256, 0, st>>>(rec_grad, bvert, rec_off, recs, n_bvert,
                                                                               grad_V);
     return cudaGetLastError();
 }
 
 size_t grad_pv_partial_p_bytes(int64_t nq, int64_t n_edges) {
-    return sizeof(float) * 3 * (size_t)((n_edges + GV_THREADS - 1) / GV_THREADS) * (size_t)nq;
+    return sizeof(float) * 3 * (size_t)((n_edges + GPV_EDGES - 1) / GPV_EDGES) * (size_t)nq;
 }
 
 // Query chunks for the fused pass: n_eb edge blocks x chunks blocks, sized to
-// whole waves of the blocks that fit on the GPU at once (every block of a
-// chunk row does the same work), the fewest waves that come within 3% of
-// full, at least 256 queries per chunk.
+// whole waves of the blocks that fit on the GPU at once (every block does the
+// same work), at least GPV_MIN_WAVES waves: with one wave the blocks that the
+// warp schedulers favour finish early and the rest of each SM's work runs at
+// low occupancy, while each further chunk adds a partial row per record; the
+// fewest waves from there that come within 3% of full, at least 256 queries
+// per chunk.
+constexpr int GPV_MIN_WAVES = 8;
 int grad_pv_chunks(int64_t nq, int64_t n_edges, int sm_count) {
     static int per_sm = 0;
     if (per_sm == 0) {
@@ -391,14 +454,14 @@ int grad_pv_chunks(int64_t nq, int64_t n_edges, int sm_count) {
         }
         per_sm = b;
     }
-    const int64_t n_eb = (n_edges + GV_THREADS - 1) / GV_THREADS;
+    const int64_t n_eb = (n_edges + GPV_EDGES - 1) / GPV_EDGES;
     const int64_t cap = (int64_t)(sm_count > 0 ? sm_count : 152) * per_sm;
     int64_t maxc = (nq + GV_QTILE - 1) / GV_QTILE;
     if (maxc > 4096) maxc = 4096;
     if (maxc < 1) maxc = 1;
     int64_t best = 1;
     double best_fill = 0.0;
-    for (int64_t w = 1; w <= 8; w++) {
+    for (int64_t w = GPV_MIN_WAVES; w <= 4 * GPV_MIN_WAVES; w++) {
         int64_t c = w * cap / (n_eb > 0 ? n_eb : 1);
         if (c < 1) c = 1;
         if (c > maxc) c = maxc;
@@ -415,14 +478,17 @@ cudaError_t launch_grad_pv(const float4 *bseq, int64_t nb, const int32_t *edge_r
                            float *rec_grad, const int32_t *bvert, const int64_t *rec_off, const int32_t *recs,
                            int64_t n_bvert, float *grad_p, float *grad_V, cudaStream_t st) {
     if (nb == 0 || n_edges == 0 || q.n == 0) return cudaSuccess;
-    int64_t chunk_len = (q.n + n_chunks - 1) / n_chunks;
-    const int n_eb = (int)((n_edges + GV_THREADS - 1) / GV_THREADS);
+    // whole groups of 32 queries per chunk: only the last chunk has a ragged
+    // group (trailing chunks may be empty and write zero partial rows)
+    const int64_t chunk_len = ((q.n + n_chunks - 1) / n_chunks + 31) & ~(int64_t)31;
+    const int n_eb = (int)((n_edges + GPV_EDGES - 1) / GPV_EDGES);
     dim3 grid((unsigned)n_eb, (unsigned)n_chunks);
     grad_pv_partial_kernel<<<grid, GV_THREADS, 0, st>>>(bseq, (int)nb, edge_rec, (int)n_edges, q, grad_w, chunk_len,
                                                         partial, partial_p);
     grad_p_reduce_kernel<<<(unsigned)((q.n + 255) / 256), 256, 0, st>>>(partial_p, n_eb, q.n, grad_p);
     if (n_bvert > 0) {
-        grad_v_record_kernel<<<(unsigned)((nb + 255) / 256), 256, 0, st>>>(partial, n_chunks, (int)nb, bseq, rec_grad);
+        grad_v_record_kernel<<<(unsigned)((nb + 31) / 32), GV_REC_WARPS * 32, 0, st>>>(partial, n_chunks, (int)nb,
+                                                                                   bseq, rec_grad);
         grad_v_scatter_kernel<<<(unsigned)((n_bvert + 255) / 256), 256, 0, st>>>(rec_grad, bvert, rec_off, recs,
                                                                                   n_bvert, grad_V);
     }

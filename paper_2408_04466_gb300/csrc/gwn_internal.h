@@ -324,9 +324,9 @@ cudaError_t launch_bframe(const float4 *bseq, int64_t n, const Frame &fr, float4
 cudaError_t launch_grad_p(const float4 *bseq, int64_t nb, const QuerySrc &q, const float *grad_w, float *grad_p,
                           cudaStream_t st);
 int grad_v_chunks(int64_t nq, int64_t nb, int sm_count);
-// both gradients from one pass over the (query, edge) pairs, thread per edge
-// (edge_rec: the record ending each edge); partial_p holds
-// grad_pv_partial_p_bytes(nq, n_edges) bytes, partial 6 floats per (chunk,
+// both gradients from one pass over the (query, edge) pairs, two edges per
+// thread (edge_rec: the record ending each edge); partial_p holds
+// grad_pv_partial_p_bytes(nq, n_edges) bytes, partial 8 floats per (chunk,
 // record); grad_pv_chunks gives the number of query chunks
 size_t grad_pv_partial_p_bytes(int64_t nq, int64_t n_edges);
 int grad_pv_chunks(int64_t nq, int64_t n_edges, int sm_count);

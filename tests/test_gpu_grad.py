@@ -106,6 +106,49 @@ def test_small_torus_gradients(gwn, ctx):
     _assert_rows(g1.cpu().numpy(), fd, ATOL, "dw/dp vs finite differences")
 
 
+def test_gradients_near_edges(gwn, ctx):
+    """Queries inside the sphere on a boundary edge as diameter (a.b < 0, the
+    endpoint weights through |a x E|^2 / (|a||b| - a.b)), queries on the
+    extension of an edge (a, b nearly parallel) and random queries, in one
+    call: the warps then mix lanes of both branches.  320 boundary edges, so
+    one full block of edges and one partial block.  Per query and per vertex
+    against the FP64 oracle gradient."""
+    import torch
+    m = gen.slit_torus(n_u=48, n_v=160, n_queries=512, seed=5)
+    mesh = gwn.Mesh(ctx, m.V, m.F)
+    off, vid = mesh.boundary()
+    assert len(vid) == 320
+    rng = np.random.default_rng(11)
+    V = m.V.astype(np.float64)
+    pts = []
+    for lp in range(len(off) - 1):
+        loop = vid[off[lp]:off[lp + 1]]
+        for i in rng.choice(len(loop), 12, replace=False):
+            A, B = V[loop[i]], V[loop[(i + 1) % len(loop)]]
+            E = B - A
+            L = np.linalg.norm(E)
+            n = np.cross(E, rng.standard_normal(3))
+            n /= np.linalg.norm(n)
+            for t, dd in ((0.5, 0.02), (0.3, 0.1), (0.7, 0.3), (0.5, 0.45)):
+                pts.append(A + t * E + dd * L * n)          # a.b < 0
+            pts.append(B + 0.3 * E + 0.05 * L * n)          # beyond B, a.b > 0
+    P = np.concatenate([np.asarray(pts, np.float32), m.points[:136]])
+    rng.shuffle(P)
+    gw = rng.uniform(0.5, 1.5, len(P)).astype(np.float32)
+    gp, gV = mesh.backward(torch.as_tensor(P).cuda(), torch.as_tensor(gw).cuda())
+    torch.cuda.synchronize()
+    ctx.check()
+    ogp, ogV = oracle.grad3d_vos(m.V, m.F, P, gw=gw.astype(np.float64))
+    _assert_rows(gp.cpu().numpy(), ogp, ATOL, "dw/dp near edges")
+    _check_vertex_grad(gV.cpu().numpy(), ogV, vid, "dw/dV near edges")
+    # each gradient alone takes its own kernels
+    gp1, _ = mesh.backward(torch.as_tensor(P).cuda(), torch.as_tensor(gw).cuda(), want_V=False)
+    _, gV1 = mesh.backward(torch.as_tensor(P).cuda(), torch.as_tensor(gw).cuda(), want_p=False)
+    torch.cuda.synchronize()
+    _assert_rows(gp1.cpu().numpy(), ogp, ATOL, "dw/dp alone near edges")
+    _check_vertex_grad(gV1.cpu().numpy(), ogV, vid, "dw/dV alone near edges")
+
+
 def test_autograd_function(gwn, ctx):
     import torch
     m = gen.icosphere_cap(subdiv=2, seed=4)
