@@ -413,17 +413,19 @@ template <typename T>
 __device__ __forceinline__ int2 chord_counts(const T *__restrict__ ctrl, const int64_t *__restrict__ chain_off,
                                              int64_t c, T xq, T yr);
 
-// Degree-8 odd minimax polynomial of the 3D boundary term: atan(v) ~ v P(v^2)
-// on [-1, 1], relative error 1.5e-8.
-#define GWN_ATC8 0.00284989f
-#define GWN_ATC7 -0.01606863f
-#define GWN_ATC6 0.04269152f
-#define GWN_ATC5 -0.07504295f
-#define GWN_ATC4 0.10640934f
-#define GWN_ATC3 -0.14203644f
-#define GWN_ATC2 0.19992619f
-#define GWN_ATC1 -0.33333073f
-#define GWN_ATC0 0.99999998f
+// Odd polynomial atan(v) ~ v P(v^2) on [-1, 1] for the chord term, P of
+// degree 7 fitted by Lawson-weighted least squares to the relative error
+// (1.0e-7 in exact arithmetic).  Evaluated in float32 its error (1.5e-7
+// absolute) is that of the float32 rounding, as for a degree-8 fit: a query
+// adds a single chord angle, so w is off by at most ~5e-8 from it.
+#define GWN_ATC7 -0.0046932739f
+#define GWN_ATC6 0.024252396f
+#define GWN_ATC5 -0.059486382f
+#define GWN_ATC4 0.099142924f
+#define GWN_ATC3 -0.1401948f
+#define GWN_ATC2 0.19969724f
+#define GWN_ATC1 -0.3333199f
+#define GWN_ATC0 0.99999988f
 #define GWN_PI_2_F 1.5707963267948966f
 
 // atan2(-cr, dt) in float32.  With z = |(cr, dt)| and v = dt / (|cr| + z) in
@@ -433,9 +435,9 @@ __device__ __forceinline__ int2 chord_counts(const T *__restrict__ ctrl, const i
 // and the axis (0, 1); its branch cut (-cr changing sign where dt < 0) is
 // where the chord's crossing count changes, so w stays continuous.  The sign
 // is applied by flipping the sign bit (multiplying by sign(-cr)).  MUFU
-// rsqrt and reciprocal (~2 ulp); z^2 is kept at least 1e-37 so that a query
-// on a chord end point (z = 0) gets a finite term (+-pi/2; w is undefined on
-// the curve).
+// rsqrt and reciprocal (~2 ulp); z^2 = cr^2 + dt^2 + 1e-37 (the constant in
+// the first FMA) so that a query on a chord end point (z = 0) gets a finite
+// term (+-pi/2; w is undefined on the curve).
 __device__ __forceinline__ float frsqrt_(float x) {
     float r;
     asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
@@ -450,11 +452,10 @@ __device__ __forceinline__ float sign_of_neg(float phi, float cr) {      // sign
     return __uint_as_float(__float_as_uint(phi) ^ (~__float_as_uint(cr) & 0x80000000u));
 }
 __device__ __forceinline__ float chord_angle(float cr, float dt) {
-    const float z2 = fmaxf(__fmaf_rn(dt, dt, __fmul_rn(cr, cr)), 1e-37f);
+    const float z2 = __fmaf_rn(dt, dt, __fmaf_rn(cr, cr, 1e-37f));
     const float d = __fmaf_rn(z2, frsqrt_(z2), fabsf(cr));
     const float v = __fmul_rn(dt, frcp_(d)), v2 = __fmul_rn(v, v);
-    float q = __fmaf_rn(GWN_ATC8, v2, GWN_ATC7);
-    q = __fmaf_rn(q, v2, GWN_ATC6);
+    float q = __fmaf_rn(GWN_ATC7, v2, GWN_ATC6);
     q = __fmaf_rn(q, v2, GWN_ATC5);
     q = __fmaf_rn(q, v2, GWN_ATC4);
     q = __fmaf_rn(q, v2, GWN_ATC3);
@@ -468,15 +469,12 @@ __device__ __forceinline__ float chord_angle(float cr, float dt) {
 // two chord angles at once: the same operations as chord_angle, the
 // add/mul/fma ones as packed f32x2 (fma.rn/mul.rn per element)
 __device__ __forceinline__ float2 chord_angle2(float2 cr, float2 dt) {
-    float2 z2 = __ffma2_rn(dt, dt, __fmul2_rn(cr, cr));
-    z2.x = fmaxf(z2.x, 1e-37f);
-    z2.y = fmaxf(z2.y, 1e-37f);
+    const float2 z2 = __ffma2_rn(dt, dt, __ffma2_rn(cr, cr, make_float2(1e-37f, 1e-37f)));
     const float2 acr = make_float2(fabsf(cr.x), fabsf(cr.y));
     const float2 d = __ffma2_rn(z2, make_float2(frsqrt_(z2.x), frsqrt_(z2.y)), acr);
     const float2 v = __fmul2_rn(dt, make_float2(frcp_(d.x), frcp_(d.y)));
     const float2 v2 = __fmul2_rn(v, v);
-    float2 q = __ffma2_rn(make_float2(GWN_ATC8, GWN_ATC8), v2, make_float2(GWN_ATC7, GWN_ATC7));
-    q = __ffma2_rn(q, v2, make_float2(GWN_ATC6, GWN_ATC6));
+    float2 q = __ffma2_rn(make_float2(GWN_ATC7, GWN_ATC7), v2, make_float2(GWN_ATC6, GWN_ATC6));
     q = __ffma2_rn(q, v2, make_float2(GWN_ATC5, GWN_ATC5));
     q = __ffma2_rn(q, v2, make_float2(GWN_ATC4, GWN_ATC4));
     q = __ffma2_rn(q, v2, make_float2(GWN_ATC3, GWN_ATC3));
@@ -714,7 +712,7 @@ __device__ __forceinline__ void row_queries_f32(const float *__restrict__ ax, in
     const float2 spx2 = make_float2(spx, spx), epx2 = make_float2(epx, epx);
     const float2 sy2 = make_float2(sy, sy), ney2 = make_float2(ney, ney), syey2 = make_float2(syey, syey);
     const float2 inv2pi2 = make_float2(Num<float>::inv2pi, Num<float>::inv2pi);
-    const float2 unbias2 = make_float2(-12582912.f, -12582912.f);
+    const float2 unbias2 = make_float2(-12582912.f, -12582912.f), mone2 = make_float2(-1.f, -1.f);
     int carry = 0;
     for (int c0 = nxp - 256; c0 >= 0; c0 -= 256) {
         const int ia = c0 + 4 * lane, ib = ia + 128;
@@ -760,8 +758,8 @@ __device__ __forceinline__ void row_queries_f32(const float *__restrict__ ax, in
             float out[4];
 #pragma unroll
             for (int m = 0; m < 4; m += 2) {
-                const float2 nX = make_float2(-xq[m], -xq[m + 1]);
-                const float2 sx = __fadd2_rn(spx2, nX), ex = __fadd2_rn(epx2, nX);
+                const float2 X = make_float2(xq[m], xq[m + 1]);
+                const float2 sx = __ffma2_rn(X, mone2, spx2), ex = __ffma2_rn(X, mone2, epx2);   // spx - x, epx - x
                 const float2 cr = __ffma2_rn(ex, sy2, __fmul2_rn(sx, ney2));
                 const float2 dt = __ffma2_rn(sx, ex, syey2);
                 const float2 A = chord_angle2(cr, dt);

@@ -132,7 +132,7 @@ def test_gradients_near_edges(gwn, ctx):
             for t, dd in ((0.5, 0.02), (0.3, 0.1), (0.7, 0.3), (0.5, 0.45)):
                 pts.append(A + t * E + dd * L * n)          # a.b < 0
             pts.append(B + 0.3 * E + 0.05 * L * n)          # beyond B, a.b > 0
-    P = np.concatenate([np.asarray(pts, np.float32), m.points[:136]])
+    P = np.concatenate([np.asarray(pts, np.float32), m.points[:137]])     # 257 queries: a ragged group
     rng.shuffle(P)
     gw = rng.uniform(0.5, 1.5, len(P)).astype(np.float32)
     gp, gV = mesh.backward(torch.as_tensor(P).cuda(), torch.as_tensor(gw).cuda())
@@ -147,6 +147,37 @@ def test_gradients_near_edges(gwn, ctx):
     torch.cuda.synchronize()
     _assert_rows(gp1.cpu().numpy(), ogp, ATOL, "dw/dp alone near edges")
     _check_vertex_grad(gV1.cpu().numpy(), ogV, vid, "dw/dV alone near edges")
+
+
+def test_backward_degenerate_inputs(gwn, ctx):
+    """A closed surface has no boundary: both gradients are exactly zero (w is
+    piecewise constant off the surface).  No queries: dw/dV is zero and
+    nothing else is touched.  One query and one boundary loop of 3 edges
+    (the single triangle): per query and per vertex against the oracle."""
+    import torch
+    Vs, Fs = gen.icosphere(2)
+    mesh = gwn.Mesh(ctx, Vs.astype(np.float32), Fs.astype(np.int32))
+    assert mesh.info()["n_boundary_edges"] == 0
+    P = np.random.default_rng(3).uniform(-1.5, 1.5, (100, 3)).astype(np.float32)
+    gp, gV = mesh.backward(torch.as_tensor(P).cuda(), torch.ones(len(P), device="cuda"))
+    torch.cuda.synchronize()
+    assert torch.count_nonzero(gp).item() == 0 and torch.count_nonzero(gV).item() == 0
+    m = gen.slit_torus(n_u=16, n_v=12, n_queries=8, seed=1)
+    mesh = gwn.Mesh(ctx, m.V, m.F)
+    gp, gV = mesh.backward(torch.zeros((0, 3), device="cuda"), torch.zeros(0, device="cuda"))
+    torch.cuda.synchronize()
+    assert gp.shape == (0, 3) and torch.count_nonzero(gV).item() == 0
+    V = np.array([[1, 0, 0], [0, 1, 0], [0, 0, 1]], np.float32)
+    F = np.array([[0, 1, 2]], np.int32)
+    tri = gwn.Mesh(ctx, V, F)
+    _, vid = tri.boundary()
+    P = np.array([[0.2, 0.3, -0.4]], np.float32)
+    gw = np.array([0.7], np.float32)
+    gp, gV = tri.backward(torch.as_tensor(P).cuda(), torch.as_tensor(gw).cuda())
+    torch.cuda.synchronize()
+    ogp, ogV = oracle.grad3d_vos(V, F, P, gw=gw.astype(np.float64))
+    _assert_rows(gp.cpu().numpy(), ogp, ATOL, "dw/dp single triangle")
+    _check_vertex_grad(gV.cpu().numpy(), ogV, vid, "dw/dV single triangle")
 
 
 def test_autograd_function(gwn, ctx):
