@@ -131,37 +131,70 @@ __global__ void hist_kernel(const unsigned long long *__restrict__ keys, int64_t
     for (int i = threadIdx.x; i < BINS; i += blockDim.x) hist[(int64_t)i * nblocks + blockIdx.x] = h[i];
 }
 
-// exclusive scan of the BINS x nblocks digit counts by one block (chunked,
-// Hillis-Steele over the per-thread chunk sums); the same block then flags
-// the pass as skippable when one digit value holds every key
-__global__ void scan_skip_kernel(unsigned *data, int nblocks, int64_t total, int *skip) {
-    __shared__ unsigned long long partial[1024];
+// Exclusive scan, in place, of the BINS x nblocks digit counts (digit-major,
+// hist[digit * nblocks + tile]) by one block of SCAN_THREADS threads, in steps
+// of SCAN_THREADS x 8 consecutive counts: each thread takes 8 (two 16-byte
+// loads, coalesced across the block; the next step's loads are issued before
+// this step is scanned), a warp scan by shuffle over the threads' sums, one
+// warp scanning the 32 warp totals, and a running carry.  Counts and sums fit
+// in 32 bits (fewer than 2^31 keys).  Then the same block flags the pass as
+// skippable when one digit value holds every key.  hist's length BINS x
+// nblocks is a multiple of 4, and its start is 256-byte aligned.
+constexpr int SCAN_THREADS = 1024;
+__global__ void __launch_bounds__(SCAN_THREADS) scan_skip_kernel(unsigned *data, int nblocks, int64_t total,
+                                                                 int *skip) {
+    __shared__ unsigned wsum[2][32];                 // alternate steps: one barrier per step
     __shared__ int s_skip;
-    const int64_t n = (int64_t)BINS * nblocks;
-    int tid = threadIdx.x;
+    const unsigned FULL = 0xffffffffu;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t n4 = (int64_t)BINS * nblocks / 4;
+    uint4 *d4 = reinterpret_cast<uint4 *>(data);
+    const uint4 Z = make_uint4(0u, 0u, 0u, 0u);
     if (tid == 0) s_skip = 0;
-    int64_t chunk = (n + blockDim.x - 1) / blockDim.x;
-    int64_t lo = tid * chunk, hi = lo + chunk < n ? lo + chunk : n;
-    unsigned long long s = 0;
-    for (int64_t i = lo; i < hi; i++) s += data[i];
-    partial[tid] = s;
-    __syncthreads();
-    for (int off = 1; off < blockDim.x; off <<= 1) {
-        unsigned long long v = tid >= off ? partial[tid - off] : 0;
+    int64_t j4 = 2 * (int64_t)tid;
+    uint4 a = j4 < n4 ? d4[j4] : Z, b = j4 + 1 < n4 ? d4[j4 + 1] : Z;
+    unsigned carry = 0;                               // the same value in every thread
+    for (int step = 0; j4 - 2 * (int64_t)tid < n4; step++, j4 += 2 * SCAN_THREADS) {
+        const int64_t k4 = j4 + 2 * SCAN_THREADS;
+        const uint4 na = k4 < n4 ? d4[k4] : Z, nb = k4 + 1 < n4 ? d4[k4 + 1] : Z;
+        const unsigned v[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+        unsigned sum = 0;
+#pragma unroll
+        for (int k = 0; k < 8; k++) sum += v[k];
+        unsigned x = sum;                             // inclusive over the warp's threads
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const unsigned y = __shfl_up_sync(FULL, x, off);
+            if (lane >= off) x += y;
+        }
+        unsigned *ws = wsum[step & 1];
+        if (lane == 31) ws[warp] = x;
         __syncthreads();
-        partial[tid] += v;
-        __syncthreads();
-    }
-    unsigned long long run = tid > 0 ? partial[tid - 1] : 0;
-    for (int64_t i = lo; i < hi; i++) {
-        unsigned v = data[i];
-        data[i] = (unsigned)run;
-        run += v;
+        unsigned wprev = 0, wall = 0;                 // warps before this one, and all warps
+        {
+            unsigned w = ws[lane], wi = w;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const unsigned y = __shfl_up_sync(FULL, wi, off);
+                if (lane >= off) wi += y;
+            }
+            wprev = __shfl_sync(FULL, wi - w, warp);
+            wall = __shfl_sync(FULL, wi, 31);
+        }
+        unsigned r = carry + wprev + (x - sum);
+        unsigned o[8];
+#pragma unroll
+        for (int k = 0; k < 8; k++) { o[k] = r; r += v[k]; }
+        if (j4 < n4) d4[j4] = make_uint4(o[0], o[1], o[2], o[3]);
+        if (j4 + 1 < n4) d4[j4 + 1] = make_uint4(o[4], o[5], o[6], o[7]);
+        carry += wall;
+        a = na;
+        b = nb;
     }
     __syncthreads();                     // the block's global writes are visible to the block
-    for (int b = tid; b < BINS; b += blockDim.x) {
-        unsigned long long start = data[(int64_t)b * nblocks];
-        unsigned long long end = b + 1 < BINS ? data[(int64_t)(b + 1) * nblocks] : (unsigned long long)total;
+    for (int bn = tid; bn < BINS; bn += blockDim.x) {
+        const unsigned long long start = data[(int64_t)bn * nblocks];
+        const unsigned long long end = bn + 1 < BINS ? data[(int64_t)(bn + 1) * nblocks] : (unsigned long long)total;
         if (end - start == (unsigned long long)total) s_skip = 1;
     }
     __syncthreads();
@@ -521,7 +554,7 @@ cudaError_t radix_sort_pairs(unsigned long long *&k0, int32_t *&v0, unsigned lon
         if (!((byte_mask >> b) & 1u)) continue;
         const int shift = 8 * b;
         hist_kernel<<<nblocks, SORT_THREADS, 0, st>>>(k0, n, shift, hist, nblocks);
-        scan_skip_kernel<<<1, 1024, 0, st>>>(hist, nblocks, n, skip);
+        scan_skip_kernel<<<1, SCAN_THREADS, 0, st>>>(hist, nblocks, n, skip);
         scatter_kernel<<<nblocks, SORT_THREADS, 0, st>>>(k0, v0, k1, v1, n, shift, hist, nblocks, skip);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
