@@ -22,11 +22,16 @@
 // boundary; it is checked against finite differences and against the
 // gradient of the per-triangle solid-angle sum.
 //
-// Kernels: (1) grad_p, one thread per K queries looping over the boundary
-// records (deterministic per query); (2) grad_V partials, one thread per
-// boundary record looping over a chunk of queries staged in shared memory,
-// one partial per (chunk, record); (3) a fixed-order reduction over chunks
-// and a scatter to vertices through a per-vertex record list.
+// Kernels: when both gradients are asked for, (1) grad_pv_partial_kernel
+// evaluates every (query, edge) pair once, two edges per thread, and writes
+// per-query partial sums per block of 256 edges and per-edge partial sums per
+// query chunk; grad_p_reduce_kernel adds the edge blocks in order,
+// grad_v_record_kernel the chunks in a fixed order, and grad_v_scatter_kernel
+// sums each vertex's records.  For one gradient alone: (2) grad_p_kernel, one
+// thread per K queries looping over the boundary records (deterministic per
+// query); (3) grad_v_partial_kernel, one thread per boundary record looping
+// over a chunk of queries staged in shared memory, then the same record and
+// scatter kernels.
 #include "gwn_internal.h"
 #include "query.cuh"
 
