@@ -476,19 +476,38 @@ __global__ void bin_count_kernel(const float4 *__restrict__ tbox, int64_t n, Bin
 }
 
 // one (key, triangle) per entry: key = bin << 32 | ~order(zmax), so the sort
-// puts each bin's triangles by decreasing zmax; triangles in sorted order
+// puts each bin's triangles by decreasing zmax; triangles in sorted order.
+// Space is taken with one atomic per warp (the warp's entries counted by a
+// shuffle scan), not one per triangle on the single counter.  Launched with
+// whole warps; the order of the entries is fixed only by the sort.
 __global__ void bin_emit_kernel(const float4 *__restrict__ tbox, int64_t n, BinParams bp, int64_t cap,
                                 unsigned long long *__restrict__ keys, int32_t *__restrict__ vals,
                                 unsigned long long *counter) {
-    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n) return;
-    float4 b = tbox[2 * t];
-    float zm = tbox[2 * t + 1].x;
-    int bx0 = bin_of(b.x, bp.x0, bp.invx, bp.nbx), bx1 = bin_of(b.y, bp.x0, bp.invx, bp.nbx);
-    int by0 = bin_of(b.z, bp.y0, bp.invy, bp.nby), by1 = bin_of(b.w, bp.y0, bp.invy, bp.nby);
-    unsigned long long c = (unsigned long long)(bx1 - bx0 + 1) * (unsigned long long)(by1 - by0 + 1);
-    unsigned long long pos = atomicAdd(counter, c);
-    unsigned zk = ~f2ord(zm);
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool live = t < n;
+    int bx0 = 0, bx1 = -1, by0 = 0, by1 = -1;
+    unsigned zk = 0;
+    if (live) {
+        const float4 b = tbox[2 * t];
+        zk = ~f2ord(tbox[2 * t + 1].x);
+        bx0 = bin_of(b.x, bp.x0, bp.invx, bp.nbx); bx1 = bin_of(b.y, bp.x0, bp.invx, bp.nbx);
+        by0 = bin_of(b.z, bp.y0, bp.invy, bp.nby); by1 = bin_of(b.w, bp.y0, bp.invy, bp.nby);
+    }
+    const unsigned long long c = live ? (unsigned long long)(bx1 - bx0 + 1) * (unsigned long long)(by1 - by0 + 1)
+                                      : 0ull;
+    unsigned long long x = c;                     // inclusive over the warp's lanes
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const unsigned long long y = __shfl_up_sync(FULL, x, off);
+        if (lane >= off) x += y;
+    }
+    unsigned long long base = 0;
+    if (lane == 31 && x) base = atomicAdd(counter, x);
+    base = __shfl_sync(FULL, base, 31);
+    if (!live) return;
+    unsigned long long pos = base + (x - c);
     for (int by = by0; by <= by1; by++)
         for (int bx = bx0; bx <= bx1; bx++, pos++)
             if ((int64_t)pos < cap) {
