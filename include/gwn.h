@@ -357,7 +357,14 @@ GWN_API gwn_status gwn_meshes_plan_get(gwn_ctx *ctx, int32_t *tiles_per_item, in
  *   grad_V (device float32[nv x 3] or NULL): sum_q grad_w[q] * dw_q/dV
  *            (rows of vertices not on the boundary are 0).
  * Only the boundary term depends on the geometry continuously (chi is
- * piecewise constant), so both come from the boundary edges alone. */
+ * piecewise constant), so both come from the boundary edges alone.
+ * Workspace, from the context's grow-only scratch (kept for later calls):
+ * with both outputs, 12 * ceil(E / 256) bytes per query (E boundary edges:
+ * its sums over each block of 256 edges) plus 32 bytes per boundary record
+ * per query chunk (at most a few thousand chunks); with one output, at most
+ * the second part.  A request that does not fit returns GWN_E_OOM without
+ * computing anything (grad_V may already have been cleared): split the
+ * queries over several calls (grad_V is then the sum of the calls' results). */
 GWN_API gwn_status gwn_backward(gwn_geom *g, const gwn_queries *q, const float *d,
                                 const float *grad_w, float *grad_p, float *grad_V);
 
